@@ -1,0 +1,106 @@
+"""End-to-end FP64 DDA used by the tests: target -> incidence -> alpha -> solve -> Q.
+
+Steps in the guide's order (section "Choice of Iterative Algorithm" for the
+system A P = E; the other sections as cited in the sibling modules).
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional
+
+import numpy as np
+
+from . import interaction, observables, orientation, polarizability, solvers, targets
+
+
+@dataclasses.dataclass
+class Rhs:
+    ori: tuple            # (beta, Theta, Phi)
+    pol: int              # 0 or 1 (e01 / e02)
+    k_tf: np.ndarray      # (3,) k vector in TF (lattice units)
+    e_tf: np.ndarray      # (3,) complex polarization in TF
+    e01_lf: np.ndarray
+    e02_lf: Optional[np.ndarray]
+    axes: tuple           # x_LF, y_LF, z_LF in TF
+    inv_alpha: np.ndarray  # (N, 3) complex diagonal of alpha^{-1}
+    e_inc: np.ndarray     # (3, N) complex incident field
+
+
+@dataclasses.dataclass
+class Problem:
+    target: targets.Target
+    kd: float
+    x: float
+    rhs: List[Rhs]
+    pad: tuple
+
+
+def build_problem(shape, shpar, m, x, prescription, orientations, e01_lf=((0, 0), (1, 0), (0, 0)),
+                  iorth=2, pad=None, target=None, kd=None) -> Problem:
+    tgt = targets.make_target(shape, shpar) if target is None else target
+    if kd is None:
+        kd = x / tgt.aeff            # k d = x / (a_eff / d)
+    else:
+        x = kd * tgt.aeff
+    e01 = np.array([complex(*c) if isinstance(c, (tuple, list)) else complex(c) for c in e01_lf])
+    r = tgt.r
+    rhs = []
+    for ori in orientations:
+        k_tf, pols_tf, pols_lf, axes = orientation.incidence(kd, ori, tgt.a1, tgt.a2, e01, iorth)
+        for l, e_tf in enumerate(pols_tf):
+            ia = polarizability.inv_alpha(prescription, m, kd, k_tf / kd, e_tf)
+            inv_alpha = np.tile(ia, (tgt.n, 1))
+            e_inc = e_tf[:, None] * np.exp(1j * (r @ k_tf))[None, :]
+            rhs.append(Rhs(ori=tuple(ori), pol=l, k_tf=k_tf, e_tf=e_tf, e01_lf=pols_lf[0],
+                           e02_lf=pols_lf[1] if iorth == 2 else None, axes=axes,
+                           inv_alpha=inv_alpha, e_inc=e_inc))
+    pad = interaction.default_pad(tgt.box) if pad is None else tuple(pad)
+    return Problem(target=tgt, kd=kd, x=x, rhs=rhs, pad=pad)
+
+
+def apply_a(prob: Problem, i: int, p: np.ndarray, method: str = "fft", ghat=None, workers=None):
+    t = prob.target
+    if method == "direct":
+        return interaction.matvec_direct(t.r, prob.kd, prob.rhs[i].inv_alpha, p)
+    return interaction.matvec_fft(t.ijk, t.box, prob.kd, prob.rhs[i].inv_alpha, p, pad=prob.pad,
+                                  ghat=ghat, workers=workers)
+
+
+def solve(prob: Problem, method: str = "bicgstab", matvec: str = "fft", tol: float = 1e-10,
+          workers=None, maxit: int = 3000):
+    """Solve every RHS. method: lu | bicgstab | ccg. Returns list of (3, N) P and iteration counts."""
+    t = prob.target
+    out, iters = [], []
+    ghat = None
+    if matvec == "fft" and method != "lu":
+        ghat = interaction.green_fft(t.box, prob.pad, prob.kd, workers=workers)
+    for i, rh in enumerate(prob.rhs):
+        if method == "lu":
+            a = interaction.dense_matrix(t.r, prob.kd, rh.inv_alpha)
+            p = solvers.lu_solve(a, rh.e_inc.reshape(-1)).reshape(3, t.n)
+            out.append(p)
+            iters.append(0)
+            continue
+        shape = rh.e_inc.shape
+
+        def op(v, i=i):
+            return apply_a(prob, i, v.reshape(shape), matvec, ghat=ghat, workers=workers).reshape(-1)
+        fn = solvers.bicgstab if method == "bicgstab" else solvers.ccg
+        p, it, _ = fn(op, rh.e_inc.reshape(-1), tol=tol, maxit=maxit)
+        out.append(p.reshape(shape))
+        iters.append(it)
+    return out, iters
+
+
+def cross_sections(prob: Problem, ps):
+    t = prob.target
+    return [observables.efficiencies(prob.kd, t.aeff, rh.e_inc, p, rh.inv_alpha)
+            for rh, p in zip(prob.rhs, ps)]
+
+
+def mueller(prob: Problem, ps, dirs, ori_index: int = 0):
+    """Mueller matrices for LFRAME directions; needs both polarizations of one orientation."""
+    i0 = 2 * ori_index
+    rh = prob.rhs[i0]
+    return observables.mueller_for_directions(prob.kd, prob.target.r, [ps[i0], ps[i0 + 1]], dirs,
+                                              rh.axes, rh.e01_lf, rh.e02_lf)

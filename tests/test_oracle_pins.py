@@ -1,0 +1,397 @@
+"""Pins for the FP64 oracle: values, closed forms and invariants fixed independently of it.
+
+Each test names what fixes the expected value: a number printed in the DDSCAT
+7.1 guide or in Bohren & Huffman, a textbook closed form written here in a
+different form than the oracle uses, brute force on tiny inputs, or an exact
+invariant of the mathematics.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.special as sp
+
+from conftest import load_golden
+from oracle import dda, interaction, mie, observables, orientation, polarizability, solvers, targets
+from paper_1002_1505_gb300 import workloads as W
+
+
+# ----------------------------------------------------------------------------- Mie
+
+def test_mie_matches_bohren_huffman_printed_example():
+    g, _ = load_golden("mie_bohren_huffman.txt")
+    x = 2 * math.pi * g["radius"] / g["wavelength"]
+    q = mie.efficiencies(complex(g["m_re"], g["m_im"]), x)
+    assert q["Qext"] == pytest.approx(g["Qext"], abs=1e-5)
+    assert q["Qsca"] == pytest.approx(g["Qsca"], abs=1e-5)
+    assert q["Qback"] == pytest.approx(g["Qback"], abs=1e-5)
+
+
+def test_mie_riccati_bessel_against_scipy():
+    # upward recurrence is used only up to n_stop = x + 4 x^(1/3) + 2, where it is stable
+    for x in (0.3, 2.0, 11.7):
+        nstop = int(round(x + 4 * x ** (1 / 3) + 2))
+        psi, chi = mie.riccati_bessel(x, nstop)
+        n = np.arange(nstop + 1)
+        np.testing.assert_allclose(psi, x * sp.spherical_jn(n, x), rtol=1e-7, atol=1e-10)
+        np.testing.assert_allclose(chi, -x * sp.spherical_yn(n, x), rtol=1e-9)
+
+
+def test_mie_rayleigh_limit():
+    m = 1.5 + 0.2j
+    x = 1e-3
+    lor = (m * m - 1) / (m * m + 2)
+    q = mie.efficiencies(m, x)
+    assert q["Qabs"] == pytest.approx(4 * x * lor.imag, rel=1e-4)
+    assert q["Qsca"] == pytest.approx(8.0 / 3.0 * x ** 4 * abs(lor) ** 2, rel=1e-4)
+
+
+def test_mie_real_index_and_extinction_paradox():
+    q = mie.efficiencies(1.33, 3.0)
+    assert q["Qabs"] == pytest.approx(0.0, abs=1e-12)
+    # opaque and large: Q_ext -> 2, the edge correction falling like x^(-2/3)
+    d300 = mie.efficiencies(1.5 + 0.5j, 300.0)["Qext"] - 2.0
+    d3000 = mie.efficiencies(1.5 + 0.5j, 3000.0)["Qext"] - 2.0
+    assert 0 < d3000 < 0.02 and d300 / d3000 == pytest.approx(10 ** (2 / 3), rel=0.1)
+
+
+# ----------------------------------------------------------------------------- targets
+
+def _brute_count_ellipsoid(s):
+    # plain loop over cell centres with exact rationals
+    from fractions import Fraction as F
+    n = 0
+    for i in range(s[0]):
+        for j in range(s[1]):
+            for k in range(s[2]):
+                x = F(2 * i + 1 - s[0], 2)
+                y = F(2 * j + 1 - s[1], 2)
+                z = F(2 * k + 1 - s[2], 2)
+                if (x / s[0]) ** 2 + (y / s[1]) ** 2 + (z / s[2]) ** 2 <= F(1, 4):
+                    n += 1
+    return n
+
+
+@pytest.mark.parametrize("s", [(12, 12, 12), (7, 5, 9), (6, 11, 4)])
+def test_ellipsoid_count_brute_force(s):
+    assert targets.ellipsoid(*s).n == _brute_count_ellipsoid(s)
+
+
+def test_sphere12_has_912_sites_and_cubic_symmetry():
+    t = targets.ellipsoid(12, 12, 12)
+    assert t.n == 912 and t.box == (12, 12, 12)
+    r = t.r
+    key = set(map(tuple, np.round(r * 2).astype(int)))
+    for perm in ((1, 0, 2), (2, 1, 0), (0, 2, 1)):
+        assert set(map(tuple, np.round(r[:, perm] * 2).astype(int))) == key
+    assert set(map(tuple, np.round(-r * 2).astype(int))) == key
+
+
+def test_worked_example_target_bookkeeping():
+    g, _ = load_golden("au_block_worked_example.txt")
+    t = targets.rctglprsm(32, 64, 64)
+    assert t.n == int(g["NAT0"])
+    assert 1.0 / t.aeff == pytest.approx(g["d_over_aeff"], abs=2e-8)
+    kd = g["k_aeff"] / t.aeff
+    assert kd == pytest.approx(g["kd"], abs=1e-5)
+    assert abs(0.9656 + 1.8628j) * kd == pytest.approx(g["mkd"], abs=1e-4)
+    # TF origin at the centre of the upper x face: x spans [-32, 0]
+    assert t.r[:, 0].min() == -31.5 and t.r[:, 0].max() == -0.5
+
+
+def test_hex_prism_against_float_polygon():
+    # point-in-hexagon by half-plane tests with floating-point vertices, skipping the
+    # (absent) points within 1e-9 of an edge; independent of the integer formulation
+    length, vv = 6, 14
+    t = targets.hex_prism(length, vv, 6)  # a1 || z, a2 || y (face normal), a3 = -x (vertex)
+    side = vv / 2.0
+    verts = [(side * math.cos(math.pi / 3 * i), side * math.sin(math.pi / 3 * i)) for i in range(6)]
+    # vertices along +-x (a3 axis), faces normal to y
+    got = set(map(tuple, np.round(t.r * 2).astype(int)))
+    exp = set()
+    for i in range(vv):
+        for j in range(vv):
+            x = i + 0.5 - vv / 2
+            y = j + 0.5 - vv / 2
+            inside = True
+            for a in range(6):
+                (x0, y0), (x1, y1) = verts[a], verts[(a + 1) % 6]
+                cross = (x1 - x0) * (y - y0) - (y1 - y0) * (x - x0)
+                assert abs(cross) > 1e-9
+                inside &= cross > 0
+            if inside:
+                for kk in range(length):
+                    exp.add((int(round(2 * x)), int(round(2 * y)), 2 * kk + 1 - length))
+    assert got == exp
+
+
+def test_cylinder_count_brute_force():
+    t = targets.cylinder1(5, 8, 2)  # axis along y
+    n = 0
+    for i in range(8):
+        for k in range(8):
+            x = i + 0.5 - 4
+            z = k + 0.5 - 4
+            n += (x * x + z * z <= 16.0)
+    assert t.n == 5 * n and t.box[1] == 5
+
+
+# ----------------------------------------------------------------------------- orientation
+
+def test_orientation_examples_printed_in_guide():
+    # Theta=90, Phi=0, beta=0: a1 = y_LF, a2 = -x_LF ; beta=90: a1 = y_LF, a2 = z_LF
+    a1, a2, a3 = orientation.target_axes_in_lf(0.0, math.pi / 2, 0.0)
+    np.testing.assert_allclose(a1, [0, 1, 0], atol=1e-15)
+    np.testing.assert_allclose(a2, [-1, 0, 0], atol=1e-15)
+    a1, a2, a3 = orientation.target_axes_in_lf(math.pi / 2, math.pi / 2, 0.0)
+    np.testing.assert_allclose(a1, [0, 1, 0], atol=1e-15)
+    np.testing.assert_allclose(a2, [0, 0, 1], atol=1e-15)
+    # Phi = 90 puts a1 in the x_LF, z_LF plane
+    a1, _, _ = orientation.target_axes_in_lf(0.3, 0.7, math.pi / 2)
+    assert abs(a1[1]) < 1e-15
+
+
+def test_orientation_inverse_relations_are_the_transpose():
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        b, t, p = rng.uniform(0, 2 * math.pi, 3)
+        a_lf = np.array(orientation.target_axes_in_lf(b, t, p))      # rows a_i in LF
+        lab = np.array(orientation.lab_axes_in_tf(b, t, p, [1, 0, 0], [0, 1, 0]))  # x,y,z_LF in TF
+        np.testing.assert_allclose(a_lf @ a_lf.T, np.eye(3), atol=1e-14)
+        np.testing.assert_allclose(lab, a_lf.T, atol=1e-14)
+        assert np.linalg.det(a_lf) == pytest.approx(1.0)
+
+
+def test_polarization_states_printed_in_guide():
+    e1, e2 = orientation.polarizations_lf([0, 1, 0])
+    np.testing.assert_allclose(e2, [0, 0, 1])
+    e1, e2 = orientation.polarizations_lf([0, 1, 1j])  # (y + i z)/sqrt2 -> e02 = (i y + z)/sqrt2
+    np.testing.assert_allclose(e1, np.array([0, 1, 1j]) / math.sqrt(2))
+    np.testing.assert_allclose(e2, np.array([0, 1j, 1]) / math.sqrt(2))
+
+
+# ----------------------------------------------------------------------------- polarizability
+
+@pytest.mark.parametrize("presc", ["CM", "LATTDR", "GKDLDR"])
+def test_alpha_real_index_is_lossless(presc):
+    kd = 0.37
+    ia = polarizability.inv_alpha(presc, 1.7, kd, [0.3, 0.4, math.sqrt(0.75)], [1, 0, 0])
+    np.testing.assert_allclose(ia.imag, -2.0 / 3.0 * kd ** 3, rtol=1e-13)
+
+
+@pytest.mark.parametrize("presc", ["LATTDR", "GKDLDR"])
+def test_alpha_ldr_tends_to_clausius_mossotti(presc):
+    m = 1.5 + 0.3j
+    eps = m * m
+    a_cm = 3 / (4 * math.pi) * (eps - 1) / (eps + 2)  # Lorentz-Lorenz, written out here
+    ia = polarizability.inv_alpha(presc, m, 1e-6, [1, 0, 0], [0, 1, 0])
+    np.testing.assert_allclose(1.0 / ia, a_cm, rtol=1e-10)
+
+
+def test_gkdldr_equals_lattdr_for_axis_aligned_incidence_transverse_axes():
+    # khat = x, e = y: LATTDR's S = 0, and GKDLDR's y and z entries use khat_y^2 = khat_z^2 = 0
+    ia_l = polarizability.inv_alpha("LATTDR", 1.3 + 0.1j, 0.4, [1, 0, 0], [0, 1, 0])
+    ia_g = polarizability.inv_alpha("GKDLDR", 1.3 + 0.1j, 0.4, [1, 0, 0], [0, 1, 0])
+    np.testing.assert_allclose(ia_g[1:], ia_l[1:], rtol=1e-15)
+    assert abs(ia_g[0] - ia_l[0]) > 1e-3
+
+
+# ----------------------------------------------------------------------------- interaction
+
+def _dipole_field(rvec, p, k):
+    """Field at rvec of a point dipole p at the origin (Jackson eq. 9.18, Gaussian units)."""
+    r = np.linalg.norm(rvec)
+    n = rvec / r
+    return np.exp(1j * k * r) * (k * k * np.cross(np.cross(n, p), n) / r
+                                 + (3 * n * np.dot(n, p) - p) * (1 / r ** 3 - 1j * k / r ** 2))
+
+
+def test_two_dipole_blocks_are_minus_the_dipole_field():
+    r = np.array([[0.0, 0.0, 0.0], [1.0, 2.0, -1.5]])
+    k = 0.8
+    ia = np.array([[2.0 - 0.1j, 2.1 - 0.2j, 1.9 - 0.15j]] * 2)
+    a = interaction.dense_matrix(r, k, ia).reshape(3, 2, 3, 2)
+    for c in range(3):
+        p = np.zeros(3, complex)
+        p[c] = 1.0
+        e = _dipole_field(r[0] - r[1], p, k)      # field at site 0 from unit dipole at site 1
+        np.testing.assert_allclose(a[:, 0, c, 1], -e, rtol=1e-13)
+        np.testing.assert_allclose(a[:, 0, c, 0], np.diag(ia[0])[:, c], rtol=0)
+
+
+def test_single_dipole_cross_sections_closed_form():
+    kd = 0.9
+    m = 1.6 + 0.4j
+    t = targets.from_sites([[0, 0, 0]], [0.0, 0.0, 0.0])
+    prob = dda.build_problem(None, None, m, None, "CM", [(0, 0, 0)], target=t, kd=kd)
+    ps, _ = dda.solve(prob, "lu")
+    alpha = 1.0 / prob.rhs[0].inv_alpha[0, 0]
+    aeff2 = t.aeff ** 2
+    q = dda.cross_sections(prob, ps)[0]
+    assert q["Qext"] * math.pi * aeff2 == pytest.approx(4 * math.pi * kd * alpha.imag, rel=1e-12)
+    # scattered power of an oscillating dipole: C_sca = (8 pi / 3) k^4 |alpha|^2
+    assert q["Qsca"] * math.pi * aeff2 == pytest.approx(8 * math.pi / 3 * kd ** 4 * abs(alpha) ** 2, rel=1e-12)
+    c_int, g1, _, _, _ = observables.angular_averages(kd, t.r, ps[0], prob.rhs[0].axes, 1.0, 0.05)
+    assert c_int == pytest.approx(8 * math.pi / 3 * kd ** 4 * abs(alpha) ** 2, rel=2e-3)
+    assert abs(g1) < 2e-3  # dipole pattern is symmetric forward/backward
+
+
+@pytest.mark.parametrize("shape,shpar,pad", [("ELLIPSOID", (5, 7, 9), None),
+                                             ("ELLIPSOID", (5, 7, 9), (12, 15, 20)),
+                                             ("CYLINDER1", (7, 6, 3), None)])
+def test_fft_convolution_equals_direct_sum(shape, shpar, pad):
+    prob = dda.build_problem(shape, shpar, 1.4 + 0.2j, 2.0, "GKDLDR", [(0.3, 1.1, 2.0)], pad=pad)
+    p = W.seeded_vector((3, prob.target.n), 11)
+    a = dda.apply_a(prob, 0, p, "direct")
+    b = dda.apply_a(prob, 0, p, "fft")
+    assert np.linalg.norm(a - b) / np.linalg.norm(a) < 1e-13
+
+
+def test_matrix_is_complex_symmetric():
+    prob = dda.build_problem("ELLIPSOID", (5, 6, 4), 1.4 + 0.2j, 2.0, "GKDLDR", [(0, 0, 0)])
+    u = W.seeded_vector((3, prob.target.n), 1)
+    v = W.seeded_vector((3, prob.target.n), 2)
+    lhs = np.sum(u * dda.apply_a(prob, 0, v, "direct"))
+    rhs = np.sum(v * dda.apply_a(prob, 0, u, "direct"))
+    assert abs(lhs - rhs) / abs(lhs) < 1e-13
+
+
+# ----------------------------------------------------------------------------- solvers
+
+def test_lu_bicgstab_ccg_agree_sphere12():
+    w = W.SPHERE12
+    prob = dda.build_problem(w.shape, w.shpar, w.m, w.x, w.prescription, w.orientations)
+    p_lu, _ = dda.solve(prob, "lu")
+    p_bi, _ = dda.solve(prob, "bicgstab", tol=1e-12)
+    p_cg, _ = dda.solve(prob, "ccg", tol=1e-12)
+    for a, b, c in zip(p_lu, p_bi, p_cg):
+        assert np.linalg.norm(a - b) / np.linalg.norm(a) < 1e-9
+        assert np.linalg.norm(a - c) / np.linalg.norm(a) < 1e-9
+    # the returned P really solves A P = E: residual from an independent direct product
+    r = prob.rhs[0].e_inc - dda.apply_a(prob, 0, p_bi[0], "direct")
+    assert np.linalg.norm(r) / np.linalg.norm(prob.rhs[0].e_inc) < 1e-11
+
+
+# ----------------------------------------------------------------------------- observables
+
+def test_real_index_has_zero_absorption():
+    prob = dda.build_problem("ELLIPSOID", (6, 6, 6), 1.5, 2.0, "LATTDR", [(0.2, 0.4, 0.9)])
+    ps, _ = dda.solve(prob, "lu")
+    for q in dda.cross_sections(prob, ps):
+        assert abs(q["Qabs"]) < 1e-13 * q["Qext"]
+
+
+def test_optical_theorem_against_angular_integration():
+    prob = dda.build_problem("ELLIPSOID", (8, 6, 5), 1.5 + 0.1j, 2.0, "GKDLDR", [(0.2, 0.4, 0.9)])
+    ps, _ = dda.solve(prob, "lu")
+    q = dda.cross_sections(prob, ps)
+    geo = math.pi * prob.target.aeff ** 2
+    for i in range(2):
+        c_int, _, _, _, _ = observables.angular_averages(prob.kd, prob.target.r, ps[i], prob.rhs[i].axes,
+                                                         prob.x, 0.1)
+        assert c_int / geo == pytest.approx(q[i]["Qsca"], rel=2e-3)
+
+
+def test_efficiencies_invariant_under_phase_origin():
+    w = W.SPHERE12
+    t0 = targets.ellipsoid(6, 7, 5)
+    t1 = targets.Target(ijk=t0.ijk, box=t0.box, origin=t0.origin + np.array([0.3, -1.7, 2.2]),
+                        a1=t0.a1, a2=t0.a2)
+    out = []
+    for t in (t0, t1):
+        prob = dda.build_problem(None, None, 1.4 + 0.3j, None, "GKDLDR", [(0.4, 0.8, 1.9)], target=t, kd=0.5)
+        ps, _ = dda.solve(prob, "lu")
+        out.append(dda.cross_sections(prob, ps))
+    for a, b in zip(*out):
+        for key in a:
+            assert a[key] == pytest.approx(b[key], rel=1e-11, abs=1e-14)
+
+
+def test_sphere_cubic_rotation_gives_same_efficiencies():
+    w = W.SPHERE12
+    prob = dda.build_problem(w.shape, w.shpar, w.m, w.x, w.prescription,
+                             [(0, 0, 0), (0, math.pi / 2, 0), (math.pi / 2, math.pi / 2, math.pi / 2)])
+    ps, _ = dda.solve(prob, "bicgstab", tol=1e-12)
+    q = dda.cross_sections(prob, ps)
+    for qi in q[1:]:
+        assert qi["Qext"] == pytest.approx(q[0]["Qext"], rel=1e-9)
+        assert qi["Qabs"] == pytest.approx(q[0]["Qabs"], rel=1e-9)
+
+
+def test_dda_converges_to_mie_as_dipole_count_grows():
+    m, x = 1.33 + 0.01j, 1.0
+    exact = mie.efficiencies(m, x)
+    errs = []
+    for d in (8, 12, 16, 24):
+        prob = dda.build_problem("ELLIPSOID", (d, d, d), m, x, "LATTDR", [(0, 0, 0)], iorth=1)
+        ps, _ = dda.solve(prob, "bicgstab", tol=1e-10)
+        q = dda.cross_sections(prob, ps)[0]
+        errs.append(abs(q["Qext"] / exact["Qext"] - 1))
+    assert errs[-1] < 0.01                 # "within a few percent" for |m|kd << 1
+    assert errs[0] > errs[-1]
+    assert all(e2 < e1 * 1.05 for e1, e2 in zip(errs, errs[1:]))
+
+
+def test_dda_small_sphere_rayleigh_scaling():
+    m = 1.5 + 0.1j
+    lor = (m * m - 1) / (m * m + 2)
+    qs = []
+    for x in (0.02, 0.04):
+        prob = dda.build_problem("ELLIPSOID", (10, 10, 10), m, x, "LATTDR", [(0, 0, 0)], iorth=1)
+        ps, _ = dda.solve(prob, "lu")
+        qs.append(dda.cross_sections(prob, ps)[0])
+    # Q_sca / x^4 and Q_abs / x are size-independent in the Rayleigh limit
+    assert qs[0]["Qsca"] / 0.02 ** 4 == pytest.approx(qs[1]["Qsca"] / 0.04 ** 4, rel=2e-3)
+    assert qs[0]["Qabs"] / 0.02 == pytest.approx(qs[1]["Qabs"] / 0.04, rel=2e-3)
+    # and close to the continuum sphere's values (pseudosphere shape error of a few %)
+    assert qs[0]["Qabs"] == pytest.approx(4 * 0.02 * lor.imag, rel=0.05)
+    assert qs[0]["Qsca"] == pytest.approx(8 / 3 * 0.02 ** 4 * abs(lor) ** 2, rel=0.05)
+
+
+def test_quadrature_direction_count_matches_worked_example():
+    g, _ = load_golden("au_block_worked_example.txt")
+    rings = observables.scattering_angles(g["k_aeff"], 0.5)
+    assert sum(len(ph) for _, ph, _ in rings) == int(g["NAVG"])
+    total = sum(w * len(ph) for _, ph, w in rings)
+    assert total == pytest.approx(4 * math.pi, rel=1e-14)
+
+
+def test_mueller_relations_for_a_single_dipole():
+    # one isotropic dipole: S_11(theta) = k^2 dC/dOmega = k^6 |alpha|^2 (1 + cos^2)/2 for
+    # unpolarized light; S_12 = -(sin^2)/2 ... ; written from the textbook dipole pattern
+    kd = 0.7
+    t = targets.from_sites([[0, 0, 0]], [0.0, 0.0, 0.0])
+    prob = dda.build_problem(None, None, 1.3 + 0.2j, None, "CM", [(0, 0, 0)], target=t, kd=kd)
+    ps, _ = dda.solve(prob, "lu")
+    alpha = 1.0 / prob.rhs[0].inv_alpha[0, 0]
+    for th in (0.0, 0.5, 1.3, 2.9):
+        mm = dda.mueller(prob, ps, [(th, 0.4)])[0]
+        i0 = kd ** 6 * abs(alpha) ** 2
+        assert mm[0, 0] == pytest.approx(i0 * (1 + math.cos(th) ** 2) / 2, rel=1e-12)
+        assert mm[0, 1] == pytest.approx(-i0 * math.sin(th) ** 2 / 2, rel=1e-10, abs=1e-14 * i0)
+        assert mm[2, 2] == pytest.approx(i0 * math.cos(th), rel=1e-10, abs=1e-14 * i0)
+
+
+@pytest.mark.slow
+def test_worked_example_au_block():
+    """The guide's sample calculation (RCTGLPRSM 32x64x64 Au block, GKDLDR)."""
+    g, rows = load_golden("au_block_worked_example.txt")
+    w = W.AU_BLOCK
+    prob = dda.build_problem(w.shape, w.shpar, w.m, w.x, w.prescription, w.orientations)
+    ps, _ = dda.solve(prob, "bicgstab", tol=1e-6, workers=-1)
+    qs = dda.cross_sections(prob, ps)
+    ka = prob.kd * prob.target.aeff
+    for q in qs:  # the two polarizations are equivalent for this block
+        assert q["Qext"] == pytest.approx(g["Qext"], rel=1e-4)
+        assert q["Qabs"] == pytest.approx(g["Qabs"], rel=1e-4)
+        assert q["Qsca"] == pytest.approx(g["Qsca"], rel=1e-4)
+        assert q["Qpha"] == pytest.approx(g["Qpha"], rel=2e-4)
+    dirs = [(math.radians(r[0]), math.radians(r[1])) for r in rows]
+    mm = dda.mueller(prob, ps, dirs)
+    for r, m in zip(rows, mm):
+        assert m[0, 0] == pytest.approx(r[2], rel=5e-4)
+        assert m[0, 1] == pytest.approx(r[3], rel=5e-4, abs=5e-3)
+        assert m[1, 0] == pytest.approx(m[0, 1], rel=1e-9, abs=1e-9)
+        assert m[1, 1] == pytest.approx(r[5], rel=5e-4)
+    back = [m for r, m in zip(rows, mm) if r[0] == 180][0]
+    assert back[0, 0] / (math.pi * ka ** 2) == pytest.approx(g["Qbk"], rel=1e-4)

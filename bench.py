@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark of the DDA hot path on GB300: FFT-convolution A.P throughput and
+solve time per orientation at residual 1e-5, against the plain FP64 GPU solve.
+
+One step = the whole path for one batch: incident beams and polarizabilities
+for every RHS, the FP64 Fourier-space Green tensor, the batched BiCGstab solve
+(complex64 iterations refined against FP64 true residuals) to |E - A P|/|E| <= 1e-5,
+and the efficiencies plus Mueller elements.  The target's site list is resident
+on the device before the timed region (it is the step's input).
+
+value = A.P products per second (one product = A applied to one RHS vector, any
+precision) summed over all ranks; --gpus N runs N independent replicas.
+--impl reference times the FP64 CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1002_1505_gb300 import workloads as W  # noqa: E402
+
+WORKLOADS = {"ellipsoid64": W.ELLIPSOID64, "prism48": W.PRISM48, "hexprism160": W.HEXPRISM160,
+             "sphere12": W.SPHERE12, "au_block": W.AU_BLOCK}
+MUELLER_DIRS = [(0.0, 0.0), (math.pi / 2, 0.0), (math.pi, 0.0), (math.pi / 2, math.pi / 2)]
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+METRIC = "FFT-conv A.P matvecs/s and solve time/orientation @1e-5 residual vs plain GPU"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.lines = []
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(sched_passes: int, n: int, box, pad, nrhs: int, csize: int):
+    """Bytes per launch of each pass (byte model of the 3-pass / 5-pass schedule)."""
+    nx, ny, nz = box
+    px, py, pz = pad
+    xrow = px * ny * nz            # spectrum after the x pass (per component)
+    yrow = px * py * nz            # after the y pass (5-pass only)
+    ghat = 6 * px * py * pz        # Fourier-space tensor, read once per batch
+    b3 = 3 * nrhs
+    if sched_passes == 3:
+        per = [b3 * (n + xrow), b3 * 2 * xrow + ghat, b3 * (xrow + n)]
+        names = ["k_xfwd", "k_yzplane", "k_xinv"]
+    else:
+        per = [b3 * (n + xrow), b3 * (xrow + yrow), b3 * 2 * yrow + ghat, b3 * (yrow + xrow), b3 * (xrow + n)]
+        names = ["k_xfwd", "k_fft_rows(y fwd)", "k_zconv", "k_fft_rows(y inv)", "k_xinv"]
+    return [v * csize for v in per], names
+
+
+def run_reference(args, w):
+    """Oracle arm: the FP64 CPU FFT-convolution product of the same workload."""
+    from oracle import dda as odda
+    t0 = time.time()
+    prob = odda.build_problem(w.shape, w.shpar, w.m, w.x, w.prescription, w.orientations, e01_lf=w.e01,
+                              iorth=w.iorth, pad=w.pad)
+    from oracle import interaction as oint
+    ghat = oint.green_fft(prob.target.box, prob.pad, prob.kd, workers=-1)
+    rng = np.random.default_rng(1)
+    p = rng.standard_normal((3, prob.target.n)) + 1j * rng.standard_normal((3, prob.target.n))
+    per_step = min(len(prob.rhs), 2)
+
+    def step():
+        for b in range(per_step):
+            odda.apply_a(prob, b, p, "fft", ghat=ghat, workers=-1)
+
+    for _ in range(args.warmup):
+        step()
+    t = time.time()
+    for _ in range(args.steps):
+        step()
+    dt = time.time() - t
+    value = args.steps * per_step / dt
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "matvecs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": w.name, "n_dipoles": prob.target.n, "box": list(prob.target.box),
+                       "pad": list(prob.pad), "nrhs": len(prob.rhs), "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": "matvecs/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} FFT-convolution products A.P (FP64, scipy.fft, workers={cores}) "
+                                       f"per step on {w.name}"},
+            "e2e": {"value": value, "unit": "matvecs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "setup_s": t - t0}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(w, budget_s=15.0):
+    """The oracle's FFT-convolution product timed on the host cores, bounded sample."""
+    from oracle import dda as odda
+    from oracle import interaction as oint
+    prob = odda.build_problem(w.shape, w.shpar, w.m, w.x, w.prescription, w.orientations[:1], e01_lf=w.e01,
+                              iorth=1, pad=w.pad)
+    ghat = oint.green_fft(prob.target.box, prob.pad, prob.kd, workers=-1)
+    rng = np.random.default_rng(2)
+    p = rng.standard_normal((3, prob.target.n)) + 1j * rng.standard_normal((3, prob.target.n))
+    odda.apply_a(prob, 0, p, "fft", ghat=ghat, workers=-1)
+    count, t = 0, time.time()
+    while time.time() - t < budget_s:
+        odda.apply_a(prob, 0, p, "fft", ghat=ghat, workers=-1)
+        count += 1
+    dt = time.time() - t
+    cores = os.cpu_count()
+    return {"value": count / dt, "unit": "matvecs/s", "cores": cores, "kind": "oracle",
+            "sample": f"{count} FP64 FFT-convolution products A.P (one RHS each, scipy.fft workers={cores}) on "
+                      f"{w.name}, {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="ellipsoid64", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-reps", type=int, default=2)
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    ws, rank, local = dist_env()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, w)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1002_1505_gb300 import dda as D
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = D.Context(local, stream)
+    n, box = ctx.dda_setup_shape(w.shape, w.shpar)
+    aeff = (3.0 * n / (4.0 * math.pi)) ** (1.0 / 3.0)
+    kd = w.x / aeff
+    e01 = [[c[0], c[1]] for c in w.e01]
+    n_ori = len(w.orientations)
+    nrhs = n_ori * w.iorth
+    p = torch.zeros((nrhs, 3, n), dtype=torch.complex128, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step(precision="MIXED", use_graph=True):
+        ctx.dda_set_incident(kd, w.orientations, e01, w.iorth)
+        ctx.dda_build_green_fft(w.pad)
+        ctx.dda_set_polarizability(w.prescription, w.m)
+        reps, _ = ctx.dda_solve(p, solver="BICGSTAB", precision=precision, tol=1e-5, maxit=3000, use_graph=use_graph)
+        q, mm = ctx.dda_cross_sections(p, MUELLER_DIRS if w.iorth == 2 else None)
+        return reps, q
+
+    def timed(nsteps, **kw):
+        total, mv, last = 0.0, 0, None
+        for _ in range(nsteps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            reps, q = step(**kw)
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+            mv += reps[0]["matvecs"] * nrhs
+            last = (reps, q)
+        return total, mv, last
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    k0 = D.dda_kernel_launches()
+    total_ms, matvecs, (reps, q) = timed(args.steps)
+    launches = D.dda_kernel_launches() - k0
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if ws > 1:
+        t = torch.tensor([total_ms, float(matvecs)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        total_ms, matvecs = float(tmax[0]), float(t[1])
+    value = matvecs / (total_ms / 1e3)
+    ms_step = total_ms / args.steps
+
+    # plain FP64 GPU comparator: complex128 BiCGstab, no refinement, one launch per kernel
+    plain_ms, plain_mv, (preps, pq) = timed(args.plain_reps, precision="C128", use_graph=False)
+    plain_ms /= args.plain_reps
+
+    # end to end through the C ABI with host buffers: site list in, solution P and Q out
+    sites, origin = ctx.dda_get_sites()
+    h_sites = np.ascontiguousarray(sites)
+    h_p = torch.empty((nrhs, 3, n), dtype=torch.complex128, pin_memory=True)
+    ctx2 = D.Context(local, stream)
+    e2e_ms = 0.0
+    e2e_mv = 0
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx2.dda_setup_target(h_sites, origin=origin)
+        ctx2.dda_set_incident(kd, w.orientations, e01, w.iorth)
+        ctx2.dda_build_green_fft(w.pad)
+        ctx2.dda_set_polarizability(w.prescription, w.m)
+        p2 = torch.zeros((nrhs, 3, n), dtype=torch.complex128, device="cuda")
+        r2, _ = ctx2.dda_solve(p2, precision="MIXED", tol=1e-5, maxit=3000)
+        q2, _ = ctx2.dda_cross_sections(p2, MUELLER_DIRS if w.iorth == 2 else None)
+        h_p.copy_(p2, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            e2e_ms += dt * 1e3
+            e2e_mv += r2[0]["matvecs"] * nrhs
+    e2e_value = e2e_mv / (e2e_ms / 1e3)
+    h2d = h_sites.nbytes + 3 * n_ori * 8 + 48
+    d2h = h_p.numel() * 16 + q2.nbytes
+
+    # dominant pass of the product: CUDA events between passes on the launching stream
+    ms_pass = D.dda_profile_matvec(ctx, nrhs, D.DDA_C64, iters=20)
+    cs = 8
+    pad = w.pad if w.pad else tuple(int(v) for v in np.array(box) * 2)
+    abytes, names = algorithmic_bytes(len(ms_pass), n, box, pad, nrhs, cs)
+    dom = int(np.argmax(ms_pass))
+    peak, peak_kind = peaks()
+    achieved = abytes[dom] / (ms_pass[dom] * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as fh:
+            tj = json.load(fh)
+        key = f"{names[dom]}@{w.name}"
+        traffic = tj.get(key)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": names[dom], "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": abytes[dom], "ms_per_launch": ms_pass[dom],
+                "passes_ms": {nm: float(v) for nm, v in zip(names, ms_pass)},
+                "product_ms": float(np.sum(ms_pass))}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "matvecs/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
+            "config": {"workload": w.name, "n_dipoles": n, "box": list(box), "pad": list(pad), "nrhs": nrhs,
+                       "n_orientations": n_ori, "tol": 1e-5, "solver": "BiCGstab, complex64 + FP64 refinement",
+                       "l2": "flushed (512 MB write) before every step", "parallelism": f"replicas x{args.gpus}"},
+            "solve_ms_per_orientation": ms_step / n_ori,
+            "plain_fp64_solve_ms_per_orientation": plain_ms / n_ori,
+            "speedup_vs_plain_fp64": plain_ms / ms_step,
+            "iterations": [r["iters"] for r in reps], "plain_iterations": [r["iters"] for r in preps],
+            "true_rel_resid": [r["true_rel_resid"] for r in reps],
+            "Q": {"Qext": q[:, 0].tolist(), "Qabs": q[:, 1].tolist(), "Qsca": q[:, 2].tolist()},
+            "e2e": {"value": e2e_value, "unit": "matvecs/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms / args.steps},
+            "gpu_launches": int(launches),
+            "roofline": roofline,
+            "clocks": clk,
+        }
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

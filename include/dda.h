@@ -1,0 +1,211 @@
+/*
+ * dda.h -- C ABI of the GB300 discrete-dipole-approximation (DDA) library.
+ *
+ * The library computes the hot path of the DDA as described in the DDSCAT 7.1
+ * User Guide (Draine & Flatau 2010): for N polarizable points on a cubic
+ * lattice it solves A P = E (guide, eq. AP=E, section "Choice of Iterative
+ * Algorithm"), where the off-diagonal part of A is applied as a zero-padded
+ * 3-D FFT convolution of the six independent components of the symmetric
+ * dipole-dipole tensor with the three components of P (the method of Goodman,
+ * Draine & Flatau 1991 that the guide's FFT options implement; guide, "Choice
+ * of FFT Algorithm"), followed by a pointwise 3x3 complex multiply in Fourier
+ * space.  Units: lattice spacing d = 1, Gaussian units, exp(-i omega t), |E0| = 1.
+ *
+ * Conventions shared by every entry point
+ *  - All functions return a dda_status; DDA_OK is 0.  On any other status,
+ *    dda_last_error() returns a message describing the failure.  No exception,
+ *    abort or trap crosses this boundary.
+ *  - Host arrays are read (or written) during the call only; the caller keeps
+ *    ownership.  Device buffers ("_dev") are borrowed: the caller allocates
+ *    them on the context's device and keeps them alive until the enqueued work
+ *    has finished.  The context owns everything else (Green tensor, plans,
+ *    workspaces) and frees it in dda_destroy.
+ *  - Work is enqueued on the context's stream.  Calls that return host values
+ *    (dda_solve, dda_cross_sections) synchronize that stream before returning.
+ *  - Complex vectors over the target use the layout [rhs][3][N]: right-hand
+ *    side (orientation-major, then polarization), Cartesian component of the
+ *    Target Frame, then the occupied site in x-fastest lexicographic order of
+ *    its lattice index (the order dda_get_sites returns).  Elements are
+ *    interleaved (re, im) pairs of float (DDA_C64) or double (DDA_C128).
+ *  - Calling an entry point before the state it needs exists returns
+ *    DDA_ESTATE (order: target -> incident -> {green, polarizability} ->
+ *    matvec / solve / cross sections).
+ */
+#ifndef DDA_GB300_H
+#define DDA_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define DDA_API __attribute__((visibility("default")))
+#else
+#define DDA_API
+#endif
+
+typedef struct dda_ctx dda_ctx;
+
+typedef enum {
+  DDA_OK = 0,
+  DDA_EINVAL = 1,        /* bad argument (shape, size, pointer, enum) */
+  DDA_ENOMEM = 2,        /* device or host allocation failed */
+  DDA_ECUDA = 3,         /* a CUDA runtime call failed */
+  DDA_ENOCONV = 4,       /* solver stopped at maxit without reaching tol */
+  DDA_ETIMEOUT = 5,      /* solver exceeded its wall-clock budget */
+  DDA_ESTATE = 6,        /* call made before the state it needs */
+  DDA_EUNSUPPORTED = 7   /* valid request this build does not implement */
+} dda_status;
+
+enum { DDA_C64 = 1, DDA_C128 = 2 };
+/* Target shapes (guide, "Target Generation"); SHPAR in lattice units. */
+enum { DDA_ELLIPSOID = 1, DDA_RCTGLPRSM = 2, DDA_CYLINDER1 = 3, DDA_HEX_PRISM = 4 };
+/* Polarizability prescriptions (guide, "Dipole Polarizabilities"). */
+enum { DDA_CM = 1, DDA_LATTDR = 2, DDA_GKDLDR = 3 };
+/* Iterative solvers (guide, "Choice of Iterative Algorithm"). */
+enum { DDA_BICGSTAB = 1, DDA_CCG = 2 };
+/* Arithmetic of the solve: all complex64, all complex128, or complex64 inner
+ * iterations refined against complex128 true residuals. */
+enum { DDA_PREC_C64 = 1, DDA_PREC_C128 = 2, DDA_PREC_MIXED = 3 };
+
+/* Create a context on CUDA device `device`, enqueuing on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * context, or NULL on failure (then the message is lost: only the status).
+ * device < 0 creates a host-only context: target, incidence and
+ * polarizability set-up and their getters work without a GPU; every call that
+ * needs the device returns DDA_ESTATE. */
+DDA_API dda_status dda_create(dda_ctx **out, int device, void *cuda_stream);
+/* Free everything the context owns.  NULL is accepted. */
+DDA_API void dda_destroy(dda_ctx *ctx);
+/* Message for the last failing call on ctx ("" if none).  Owned by ctx. */
+DDA_API const char *dda_last_error(const dda_ctx *ctx);
+/* Change the stream later work is enqueued on. */
+DDA_API dda_status dda_set_stream(dda_ctx *ctx, void *cuda_stream);
+
+/* Built-in target (guide, "Target Generation": ELLIPSOID, RCTGLPRSM, CYLINDER1,
+ * HEX_PRISM).  shpar[0..nshpar) are SHPAR_1.. in lattice units (lengths must
+ * be positive integers; CYLINDER1 needs SHPAR_3 in 1..3, HEX_PRISM in 1..6).
+ * Sites sit at cell centres, the Target-Frame origin at the centroid
+ * (RCTGLPRSM: centre of the upper x face); surface ties count as inside.
+ * Outputs: *n_out = number of occupied sites N, box_out = bounding box
+ * (Nx, Ny, Nz).  Either output pointer may be NULL.  Replaces any earlier
+ * target and drops the incident, Green and polarizability state. */
+DDA_API dda_status dda_setup_shape(dda_ctx *ctx, int shape, const double *shpar, int nshpar, int64_t *n_out,
+                           int32_t box_out[3]);
+
+/* Target from a site list (the guide's FROM_FILE route): ixyz is host N x 3
+ * integer lattice coordinates (any order, no duplicates), icomp host N
+ * composition indices (1-based, NULL = all 1), origin_tf the Target-Frame
+ * position of lattice point (0,0,0), a1/a2 the target axes in the TF (NULL =
+ * x_TF, y_TF).  Sites are re-ordered x-fastest; dda_get_sites reports the order. */
+DDA_API dda_status dda_setup_target(dda_ctx *ctx, const int32_t *ixyz, const int32_t *icomp, int64_t n,
+                            const double origin_tf[3], const double a1[3], const double a2[3]);
+
+/* Copy the site list out: ixyz_out host N x 3 (box-relative lattice indices),
+ * origin_out[3] = TF position of box index (0,0,0).  Either may be NULL. */
+DDA_API dda_status dda_get_sites(dda_ctx *ctx, int32_t *ixyz_out, double origin_out[3]);
+
+/* Incident beams (guide, "Target Orientation" and "Incident Polarization
+ * State").  kd = k d (lattice wavenumber, > 0).  ori: host n_ori x 3 angles
+ * (beta, Theta, Phi) in radians.  e01_lf: host 6 doubles, the Lab-Frame
+ * components (x, y, z) of e01 as (re, im) pairs; normalized here.  iorth = 1
+ * (e01 only) or 2 (adds e02 = x_LF x e01*).  Defines nrhs = n_ori * iorth
+ * right-hand sides, index = ori * iorth + pol. */
+DDA_API dda_status dda_set_incident(dda_ctx *ctx, double kd, const double *ori, int n_ori, const double e01_lf[6],
+                            int iorth);
+
+/* Number of right-hand sides defined by dda_set_incident (0 before). */
+DDA_API int dda_nrhs(const dda_ctx *ctx);
+
+/* Copy the incidence out: k_tf host nrhs x 3 (k vector in the Target Frame,
+ * lattice units), e_tf host nrhs x 6 (polarization in the TF, (re, im) x 3).
+ * Either may be NULL. */
+DDA_API dda_status dda_get_incidence(dda_ctx *ctx, double *k_tf, double *e_tf);
+
+/* Write E_inc,j = e exp(i k . r_j) for every RHS into e_dev ([nrhs][3][N],
+ * dtype DDA_C64 or DDA_C128), phases evaluated in FP64. */
+DDA_API dda_status dda_incident_field(dda_ctx *ctx, void *e_dev, int dtype);
+
+/* Dipole-dipole tensor on the padded FFT grid and its FFT (Goodman, Draine &
+ * Flatau 1991), filled and transformed in FP64 on the device and kept in
+ * complex128 and rounded complex64 copies.  pad = padded grid (Px, Py, Pz),
+ * each even, >= 2 N_axis and a product of 2, 3 and 5; NULL = the smallest
+ * such lengths (the guide's extended computational volume).  Uses the kd
+ * given to dda_set_incident.  Also picks the launch schedule of the product
+ * for this grid (3-pass when a y-z plane fits in shared memory, else 5-pass). */
+DDA_API dda_status dda_build_green_fft(dda_ctx *ctx, const int32_t pad[3]);
+
+/* Polarizabilities (guide, "Dipole Polarizabilities"), after dda_set_incident: prescription DDA_CM
+ * (Clausius-Mossotti with radiative reaction), DDA_LATTDR (Draine & Goodman
+ * 1993) or DDA_GKDLDR (Gutkowicz-Krusin & Draine 2004).  m_reim: host ncomp x 2
+ * refractive indices relative to the medium, one per composition.  Computed
+ * per RHS (they depend on the incidence) in FP64. */
+DDA_API dda_status dda_set_polarizability(dda_ctx *ctx, int prescription, const double *m_reim, int ncomp);
+
+/* Copy the diagonal of alpha^{-1} out: host nrhs x ncomp x 3 complex (re, im). */
+DDA_API dda_status dda_get_inv_alpha(dda_ctx *ctx, double *out);
+
+/* ap_dev = A p_dev for the first nrhs right-hand sides, both [nrhs][3][N] of
+ * dtype DDA_C64 or DDA_C128 (may not alias).  Enqueue only. */
+DDA_API dda_status dda_matvec(dda_ctx *ctx, const void *p_dev, void *ap_dev, int nrhs, int dtype);
+
+typedef struct {
+  int solver;        /* DDA_BICGSTAB or DDA_CCG */
+  int precision;     /* DDA_PREC_C64 / DDA_PREC_C128 / DDA_PREC_MIXED */
+  double tol;        /* stop when |E - A P| / |E| <= tol for every RHS */
+  int maxit;         /* iteration cap (inner iterations summed for MIXED) */
+  double inner_tol;  /* MIXED: relative reduction asked of each inner solve (0 = 1e-3) */
+  double timeout_ms; /* wall-clock budget, 0 = none; exceeded -> DDA_ETIMEOUT */
+  int warm_start;    /* 1 = p_dev holds the initial guess, 0 = start from P = 0 */
+  int check_every;   /* iterations between host convergence checks (0 = 8) */
+  int normal_eq;     /* 1 = also evaluate the guide's normal-equation ratio at exit (2 extra FP64 products) */
+  int use_graph;     /* 1 = replay the iterations as a captured CUDA graph, 0 = plain launches */
+} dda_solve_opts;
+
+typedef struct {
+  int iters;             /* Krylov iterations used (inner ones for MIXED) */
+  int matvecs;           /* products with A (any precision) */
+  int outer;             /* MIXED: refinement steps (true-residual evaluations) */
+  int converged;         /* 1 if the true residual met tol */
+  double true_rel_resid; /* |E - A P| / |E| evaluated with the FP64 product at exit */
+  double normal_eq_ratio;/* guide's eq. err_tol: |A^H A P - A^H E| / |A^H E| (NAN if not computed) */
+} dda_solve_report;
+
+/* Solve A P = E_inc for every RHS.  p_dev: [nrhs][3][N] complex128 (always
+ * FP64 storage), initial guess when opt->warm_start, solution on return.
+ * rep: host array of nrhs reports (may be NULL).  Returns DDA_ENOCONV if any
+ * RHS missed tol within maxit (p_dev and rep still hold the last iterate). */
+DDA_API dda_status dda_solve(dda_ctx *ctx, const dda_solve_opts *opt, void *p_dev, dda_solve_report *rep);
+
+/* Efficiencies and Mueller matrices for a solved P (complex128 [nrhs][3][N]).
+ * q_out: host nrhs x 4 doubles (Q_ext, Q_abs, Q_sca = Q_ext - Q_abs, Q_pha),
+ * Q = C / (pi a_eff^2), formulas of Draine 1988 as used by the guide.
+ * dirs: host ndir x 2 (theta_s, phi_s) radians in the Lab Frame (guide,
+ * CMDFRM = LFRAME); mueller_out: host n_ori x ndir x 16 doubles (row-major S_ij,
+ * guide's Mueller relations) -- needs iorth = 2; pass ndir = 0 / NULL to skip.
+ * Synchronizes the stream. */
+DDA_API dda_status dda_cross_sections(dda_ctx *ctx, const void *p_dev, double *q_out, const double *dirs, int ndir,
+                              double *mueller_out);
+
+/* Number of CUDA kernels the library has launched in this process (graph
+ * replays counted node by node).  For accounting in benchmarks. */
+DDA_API unsigned long long dda_kernel_launches(void);
+
+/* Time the product's passes: runs `iters` products A p (p = 0, scratch
+ * buffers owned by the call) for nrhs RHS in dtype, with CUDA events recorded
+ * on the context's stream between the passes, and writes the mean duration of
+ * each pass in ms to ms_per_pass (up to 5 entries; *npass receives 3 for the
+ * 3-pass schedule: x forward, fused y-z plane, x inverse; or 5 for the 5-pass
+ * schedule: x forward, y forward, z, y inverse, x inverse).  Synchronizes. */
+DDA_API dda_status dda_profile_matvec(dda_ctx *ctx, int nrhs, int dtype, int iters, double *ms_per_pass, int *npass);
+
+/* Library build string (static storage). */
+DDA_API const char *dda_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDA_GB300_H */

@@ -1,0 +1,1144 @@
+// C ABI of the GB300 DDA library: context, target/incidence/polarizability
+// set-up on the host (FP64), Green-tensor build, product A P, the batched
+// Krylov drivers (BiCGstab, CCG; complex64, complex128 or complex64 refined
+// against complex128 true residuals) and the observables.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "dda_internal.h"
+
+using dda::cd;
+using dda::Err;
+
+namespace dda {
+void init_kernel_attrs();
+}
+
+struct dda_ctx {
+  int device = 0;
+  bool host_only = false;  // device < 0: set-up only, no CUDA calls
+  cudaStream_t stream = nullptr;
+  std::string err;
+
+  // target
+  bool have_target = false;
+  dda::HostTarget tgt;
+  int64_t n = 0;
+  int32_t* d_map = nullptr;
+  int32_t* d_ijk = nullptr;
+  uint8_t* d_comp = nullptr;
+  double* d_origin = nullptr;
+
+  // incident
+  bool have_inc = false;
+  double kd = 0;
+  int n_ori = 0, iorth = 0, nrhs = 0;
+  std::vector<double> ori;
+  cd e01[3], e02[3];                  // Lab-Frame polarizations
+  std::vector<double> axes;           // n_ori x 9: x_LF, y_LF, z_LF in TF
+  std::vector<dda::RhsGeom> rg;       // nrhs
+  dda::RhsGeom* d_rg = nullptr;
+  double2* d_e128 = nullptr;          // cached E_inc [nrhs][3][N]
+
+  // green
+  bool have_green = false;
+  dda::Geom g64{}, g128{};
+  dda::MvTune t64{}, t128{};
+  double2* d_ghat128 = nullptr;
+  float2* d_ghat64 = nullptr;
+  double2* d_tw128[3] = {nullptr, nullptr, nullptr};
+  float2* d_tw64[3] = {nullptr, nullptr, nullptr};
+
+  // polarizability
+  bool have_alpha = false;
+  int presc = 0, ncomp = 1;
+  std::vector<cd> ia;                 // nrhs x ncomp x 3
+  double2* d_ia128 = nullptr;
+  float2* d_ia64 = nullptr;
+
+  // workspaces (grown on demand)
+  float2* d_w64 = nullptr;
+  int w64_cap = 0;
+  double2* d_w128 = nullptr;
+  int w128_cap = 0;
+  double* d_part = nullptr;
+  size_t part_bytes = 0;
+  void* d_kvec = nullptr;
+  size_t kvec_bytes = 0;
+  dda::KState* d_ks = nullptr;
+  int ks_cap = 0;
+  double* d_small = nullptr;
+  size_t small_bytes = 0;
+  double* h_pinned = nullptr;
+  size_t pinned_bytes = 0;
+  cudaStream_t own_stream = nullptr;  // used for graph capture when the caller's stream is a default stream
+  cudaEvent_t ev = nullptr;
+};
+
+namespace {
+
+dda_status fail(dda_ctx* c, const Err& e) {
+  if (c) c->err = e.msg;
+  return e.code;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+Err set_dev(dda_ctx* c) {
+  if (c->host_only) return Err::Ok();
+  DDA_CU(cudaSetDevice(c->device));
+  return Err::Ok();
+}
+
+Err need_device(dda_ctx* c) {
+  if (c->host_only) return Err::make(DDA_ESTATE, "host-only context (device < 0) cannot run device work");
+  return Err::Ok();
+}
+
+template <typename T>
+Err dalloc(T** p, size_t bytes) {
+  if (*p) cudaFree((void*)*p);
+  *p = nullptr;
+  if (bytes == 0) return Err::Ok();
+  DDA_CU(cudaMalloc((void**)p, bytes));
+  return Err::Ok();
+}
+
+void drop_alpha(dda_ctx* c) {
+  c->have_alpha = false;
+  dfree(c->d_ia128);
+  dfree(c->d_ia64);
+  c->ia.clear();
+}
+void drop_green(dda_ctx* c) {
+  c->have_green = false;
+  dfree(c->d_ghat128);
+  dfree(c->d_ghat64);
+  for (int a = 0; a < 3; ++a) { dfree(c->d_tw128[a]); dfree(c->d_tw64[a]); }
+  dfree(c->d_w64);
+  dfree(c->d_w128);
+  c->w64_cap = c->w128_cap = 0;
+}
+void drop_incident(dda_ctx* c) {
+  c->have_inc = false;
+  dfree(c->d_rg);
+  dfree(c->d_e128);
+  c->rg.clear();
+  c->nrhs = 0;
+  drop_green(c);
+  drop_alpha(c);
+}
+void drop_target(dda_ctx* c) {
+  c->have_target = false;
+  dfree(c->d_map);
+  dfree(c->d_ijk);
+  dfree(c->d_comp);
+  dfree(c->d_origin);
+  drop_incident(c);
+}
+
+Err upload_target(dda_ctx* c) {
+  auto& t = c->tgt;
+  const int64_t n = (int64_t)t.comp.size();
+  const int64_t nbox = (int64_t)t.box[0] * t.box[1] * t.box[2];
+  std::vector<int32_t> map(nbox, -1);
+  for (int64_t j = 0; j < n; ++j) {
+    const int64_t b = ((int64_t)t.ijk[3 * j + 2] * t.box[1] + t.ijk[3 * j + 1]) * t.box[0] + t.ijk[3 * j];
+    map[b] = (int32_t)j;
+  }
+  c->n = n;
+  if (c->host_only) {
+    c->have_target = true;
+    return Err::Ok();
+  }
+  DDA_TRY(dalloc(&c->d_map, sizeof(int32_t) * nbox));
+  DDA_TRY(dalloc(&c->d_ijk, sizeof(int32_t) * 3 * n));
+  DDA_TRY(dalloc(&c->d_origin, sizeof(double) * 3));
+  DDA_CU(cudaMemcpy(c->d_map, map.data(), sizeof(int32_t) * nbox, cudaMemcpyHostToDevice));
+  DDA_CU(cudaMemcpy(c->d_ijk, t.ijk.data(), sizeof(int32_t) * 3 * n, cudaMemcpyHostToDevice));
+  DDA_CU(cudaMemcpy(c->d_origin, t.origin, sizeof(double) * 3, cudaMemcpyHostToDevice));
+  if (t.ncomp > 1) {
+    DDA_TRY(dalloc(&c->d_comp, n));
+    DDA_CU(cudaMemcpy(c->d_comp, t.comp.data(), n, cudaMemcpyHostToDevice));
+  } else {
+    dfree(c->d_comp);
+  }
+  c->n = n;
+  c->have_target = true;
+  return Err::Ok();
+}
+
+// Lab-Frame unit vectors in the Target Frame for orientation (beta, Theta, Phi)
+// (guide, "Orientation of the Target in the Lab Frame", inverse relations).
+void lab_axes(const double a1[3], const double a2[3], double beta, double theta, double phi, double out[9]) {
+  double a3[3] = {a1[1] * a2[2] - a1[2] * a2[1], a1[2] * a2[0] - a1[0] * a2[2], a1[0] * a2[1] - a1[1] * a2[0]};
+  const double ct = std::cos(theta), st = std::sin(theta), cb = std::cos(beta), sb = std::sin(beta);
+  const double cp = std::cos(phi), sp = std::sin(phi);
+  const double cx[3] = {ct, -st * cb, st * sb};
+  const double cy[3] = {st * cp, ct * cb * cp - sb * sp, -(ct * sb * cp + cb * sp)};
+  const double cz[3] = {st * sp, ct * cb * sp + sb * cp, -(ct * sb * sp - cb * cp)};
+  for (int k = 0; k < 3; ++k) {
+    out[k] = cx[0] * a1[k] + cx[1] * a2[k] + cx[2] * a3[k];
+    out[3 + k] = cy[0] * a1[k] + cy[1] * a2[k] + cy[2] * a3[k];
+    out[6 + k] = cz[0] * a1[k] + cz[1] * a2[k] + cz[2] * a3[k];
+  }
+}
+
+// diagonal of alpha^{-1} (guide "Dipole Polarizabilities"; CM with radiative
+// reaction, LATTDR of Draine & Goodman 1993, GKDLDR of Gutkowicz-Krusin & Draine 2004)
+void inv_alpha(int presc, cd m, double kd, const double khat[3], const cd e[3], cd out[3]) {
+  const double b1 = -1.8915316, b2 = 0.1648469, b3 = -1.7700004;
+  const cd eps = m * m;
+  const double pi = 3.14159265358979323846;
+  const cd inv_cm = (4.0 * pi / 3.0) * (eps + 2.0) / (eps - 1.0);
+  const cd rr = cd(0.0, -(2.0 / 3.0) * kd * kd * kd);
+  if (presc == DDA_CM) {
+    for (int a = 0; a < 3; ++a) out[a] = inv_cm + rr;
+  } else if (presc == DDA_LATTDR) {
+    double s = 0;
+    for (int a = 0; a < 3; ++a) s += khat[a] * khat[a] * std::norm(e[a]);
+    const cd v = inv_cm + (b1 + eps * b2 + eps * b3 * s) * kd * kd + rr;
+    for (int a = 0; a < 3; ++a) out[a] = v;
+  } else {
+    for (int a = 0; a < 3; ++a) out[a] = inv_cm + (b1 + eps * b2 + eps * b3 * (khat[a] * khat[a])) * kd * kd + rr;
+  }
+}
+
+Err ensure_part(dda_ctx* c, size_t bytes) {
+  if (bytes <= c->part_bytes) return Err::Ok();
+  DDA_TRY(dalloc(&c->d_part, bytes));
+  c->part_bytes = bytes;
+  return Err::Ok();
+}
+
+Err ensure_small(dda_ctx* c, size_t bytes) {
+  if (bytes <= c->small_bytes) return Err::Ok();
+  DDA_TRY(dalloc(&c->d_small, bytes));
+  c->small_bytes = bytes;
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  c->h_pinned = nullptr;
+  DDA_CU(cudaMallocHost((void**)&c->h_pinned, bytes));
+  c->pinned_bytes = bytes;
+  return Err::Ok();
+}
+
+dda::RedBuf redbuf(dda_ctx* c, int nrhs, int64_t n3) {
+  dda::RedBuf rb;
+  rb.nblk = (int)std::max<int64_t>(1, std::min<int64_t>((n3 + 2047) / 2048, std::max(1, 1216 / std::max(1, nrhs))));
+  rb.part = c->d_part;
+  return rb;
+}
+
+// Workspace for `want` RHS (capped by a memory budget); returns capacity in RHS.
+template <typename C>
+Err ensure_work(dda_ctx* c, int want, int* cap_out);
+
+template <>
+Err ensure_work<float2>(dda_ctx* c, int want, int* cap_out) {
+  const dda::Geom& g = c->g64;
+  const size_t per = sizeof(float2) * 3ull * g.px * g.nz * g.ys;
+  const size_t budget = 24ull << 30;
+  int cap = (int)std::max<size_t>(1, std::min<size_t>((size_t)want, budget / per));
+  if (cap > c->w64_cap) {
+    DDA_TRY(dalloc(&c->d_w64, per * cap));
+    c->w64_cap = cap;
+  }
+  *cap_out = std::min(c->w64_cap, want);
+  return Err::Ok();
+}
+template <>
+Err ensure_work<double2>(dda_ctx* c, int want, int* cap_out) {
+  const dda::Geom& g = c->g128;
+  const size_t per = sizeof(double2) * 3ull * g.px * g.nz * g.ys;
+  const size_t budget = 24ull << 30;
+  int cap = (int)std::max<size_t>(1, std::min<size_t>((size_t)want, budget / per));
+  if (cap > c->w128_cap) {
+    DDA_TRY(dalloc(&c->d_w128, per * cap));
+    c->w128_cap = cap;
+  }
+  *cap_out = std::min(c->w128_cap, want);
+  return Err::Ok();
+}
+
+template <typename C> struct Sel;
+template <> struct Sel<float2> {
+  static dda::Geom geom(dda_ctx* c) { dda::Geom g = c->g64; g.ncomp = c->ncomp; return g; }
+  static const dda::MvTune& tune(dda_ctx* c) { return c->t64; }
+  static dda::MvData<float2> data(dda_ctx* c) {
+    return dda::MvData<float2>{c->d_map, c->d_comp, c->d_ghat64, c->d_ia64, c->d_tw64[0], c->d_tw64[1], c->d_tw64[2], c->d_w64};
+  }
+};
+template <> struct Sel<double2> {
+  static dda::Geom geom(dda_ctx* c) { dda::Geom g = c->g128; g.ncomp = c->ncomp; return g; }
+  static const dda::MvTune& tune(dda_ctx* c) { return c->t128; }
+  static dda::MvData<double2> data(dda_ctx* c) {
+    return dda::MvData<double2>{c->d_map, c->d_comp, c->d_ghat128, c->d_ia128, c->d_tw128[0], c->d_tw128[1], c->d_tw128[2], c->d_w128};
+  }
+};
+
+// ap = A p over nrhs RHS starting at RHS index rhs0 (chunked by workspace capacity)
+template <typename C>
+Err matvec(dda_ctx* c, const C* p, C* ap, int nrhs, int rhs0, bool conj) {
+  int cap = 0;
+  DDA_TRY(ensure_work<C>(c, nrhs, &cap));
+  const int64_t n3 = 3 * c->n;
+  for (int b0 = 0; b0 < nrhs; b0 += cap) {
+    const int nb = std::min(cap, nrhs - b0);
+    DDA_TRY(dda::launch_matvec<C>(Sel<C>::geom(c), Sel<C>::data(c), Sel<C>::tune(c), p + b0 * n3, ap + b0 * n3, nb,
+                                  rhs0 + b0, conj, c->stream));
+  }
+  return Err::Ok();
+}
+
+Err ensure_einc(dda_ctx* c) {
+  if (c->d_e128) return Err::Ok();
+  DDA_TRY(dalloc(&c->d_e128, sizeof(double2) * (size_t)c->nrhs * 3 * c->n));
+  DDA_TRY(dda::incident_field<double2>(c->d_ijk, c->d_origin, c->d_rg, c->nrhs, c->n, c->d_e128, c->stream));
+  return Err::Ok();
+}
+
+struct SolveStats {
+  std::vector<int> iters, done;
+  int matvecs = 0;
+};
+
+// One Krylov solve in precision C over all nrhs RHS. kv.x holds x0 when have_x0.
+template <typename C>
+Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, double tol, int maxit, bool have_x0,
+           SolveStats* stats, std::chrono::steady_clock::time_point t0, bool* timed_out) {
+  const int nrhs = c->nrhs;
+  const int64_t n3 = 3 * c->n;
+  dda::RedBuf rb = redbuf(c, nrhs, n3);
+  DDA_TRY(ensure_part(c, sizeof(double) * (size_t)rb.nblk * nrhs * dda::kRedSlots));
+  rb.part = c->d_part;
+  if (c->ks_cap < nrhs) {
+    DDA_TRY(dalloc(&c->d_ks, sizeof(dda::KState) * nrhs));
+    c->ks_cap = nrhs;
+  }
+  dda::KState* ks = c->d_ks;
+  cudaStream_t st = c->stream;
+  const bool ccg = (o.solver == DDA_CCG);
+  if (have_x0) {
+    DDA_TRY(matvec<C>(c, kv.x, kv.r, nrhs, 0, false));
+    stats->matvecs += 1;
+  }
+  if (ccg) {
+    DDA_TRY(dda::ccg_init<C>(kv, ks, rb, nrhs, n3, tol, have_x0, st));
+    DDA_TRY(matvec<C>(c, kv.r, kv.s, nrhs, 0, true));
+    DDA_TRY(dda::ccg_start<C>(kv, ks, rb, nrhs, n3, st));
+    stats->matvecs += 1;
+  } else {
+    DDA_TRY(dda::bicg_init<C>(kv, ks, rb, nrhs, n3, tol, have_x0, st));
+  }
+  auto one_iter = [&]() -> Err {
+    if (ccg) {
+      DDA_TRY(matvec<C>(c, kv.p, kv.v, nrhs, 0, false));
+      DDA_TRY(dda::ccg_alpha_update<C>(kv, ks, rb, nrhs, n3, st));
+      DDA_TRY(matvec<C>(c, kv.r, kv.s, nrhs, 0, true));
+      DDA_TRY(dda::ccg_beta_update<C>(kv, ks, rb, nrhs, n3, st));
+    } else {
+      DDA_TRY(dda::bicg_p_update<C>(kv, ks, nrhs, n3, st));
+      DDA_TRY(matvec<C>(c, kv.p, kv.v, nrhs, 0, false));
+      DDA_TRY(dda::bicg_alpha<C>(kv, ks, rb, nrhs, n3, st));
+      DDA_TRY(dda::bicg_s_update<C>(kv, ks, rb, nrhs, n3, st));
+      DDA_TRY(matvec<C>(c, kv.s, kv.t, nrhs, 0, false));
+      DDA_TRY(dda::bicg_omega<C>(kv, ks, rb, nrhs, n3, st));
+      DDA_TRY(dda::bicg_xr_update<C>(kv, ks, rb, nrhs, n3, st));
+    }
+    return Err::Ok();
+  };
+  const int every = o.check_every > 0 ? o.check_every : 8;
+  DDA_TRY(ensure_small(c, sizeof(dda::KState) * nrhs));
+  {
+    int cap = 0;  // no allocation may happen while the stream is being captured
+    DDA_TRY(ensure_work<C>(c, nrhs, &cap));
+  }
+  cudaGraphExec_t gexec = nullptr;
+  unsigned long long graph_kernels = 0;
+  if (o.use_graph) {
+    const unsigned long long before = dda::launches();
+    // make sure every kernel attribute is set before capture, then capture `every` iterations
+    cudaGraph_t graph = nullptr;
+    DDA_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    Err e = Err::Ok();
+    for (int k = 0; k < every && e.ok(); ++k) e = one_iter();
+    cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    if (!e.ok()) { if (graph) cudaGraphDestroy(graph); return e; }
+    if (ce != cudaSuccess) return Err::make(DDA_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    // captured launches did not run: count them when the graph is replayed
+    graph_kernels = dda::launches() - before;
+    dda::sub_launches(graph_kernels);
+    ce = cudaGraphInstantiate(&gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return Err::make(DDA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+  }
+  std::vector<dda::KState> hk(nrhs);
+  int it = 0;
+  Err res = Err::Ok();
+  const int mv_per_it = 2;
+  while (true) {
+    DDA_CU(cudaMemcpyAsync(c->h_pinned, ks, sizeof(dda::KState) * nrhs, cudaMemcpyDeviceToHost, st));
+    DDA_CU(cudaStreamSynchronize(st));
+    std::memcpy(hk.data(), c->h_pinned, sizeof(dda::KState) * nrhs);
+    bool all = true;
+    for (int b = 0; b < nrhs; ++b) all = all && (hk[b].done != 0);
+    if (all || it >= maxit) break;
+    if (o.timeout_ms > 0) {
+      const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      if (ms > o.timeout_ms) { *timed_out = true; break; }
+    }
+    if (gexec) {
+      cudaError_t ce = cudaGraphLaunch(gexec, st);
+      if (ce != cudaSuccess) { res = Err::make(DDA_ECUDA, std::string("graph launch: ") + cudaGetErrorString(ce)); break; }
+      dda::add_launches(graph_kernels);
+    } else {
+      for (int k = 0; k < every && res.ok(); ++k) res = one_iter();
+      if (!res.ok()) break;
+    }
+    it += every;
+    stats->matvecs += mv_per_it * every;
+  }
+  if (gexec) cudaGraphExecDestroy(gexec);
+  DDA_TRY(res);
+  stats->iters.resize(nrhs);
+  stats->done.resize(nrhs);
+  for (int b = 0; b < nrhs; ++b) {
+    stats->iters[b] = hk[b].it;
+    stats->done[b] = hk[b].done;
+  }
+  return Err::Ok();
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+// (the definitions take C linkage from their declarations in dda.h)
+
+const char* dda_version(void) { return "dda-gb300 0.1 (sm_103a)"; }
+
+dda_status dda_create(dda_ctx** out, int device, void* cuda_stream) {
+  if (!out) return DDA_EINVAL;
+  *out = nullptr;
+  dda_ctx* c = new (std::nothrow) dda_ctx();
+  if (!c) return DDA_ENOMEM;
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  if (device < 0) {
+    c->host_only = true;
+    *out = c;
+    return DDA_OK;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    delete c;
+    return DDA_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete c;
+    return DDA_ECUDA;
+  }
+  dda::init_kernel_attrs();
+  *out = c;
+  return DDA_OK;
+}
+
+void dda_destroy(dda_ctx* c) {
+  if (!c) return;
+  if (c->host_only) {
+    delete c;
+    return;
+  }
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_target(c);
+  dfree(c->d_part);
+  dfree(c->d_kvec);
+  dfree(c->d_ks);
+  dfree(c->d_small);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  if (c->ev) cudaEventDestroy(c->ev);
+  delete c;
+}
+
+const char* dda_last_error(const dda_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+dda_status dda_set_stream(dda_ctx* c, void* s) {
+  if (!c) return DDA_EINVAL;
+  c->stream = (cudaStream_t)s;
+  return DDA_OK;
+}
+
+dda_status dda_setup_shape(dda_ctx* c, int shape, const double* shpar, int nshpar, int64_t* n_out,
+                           int32_t box_out[3]) {
+  if (!c) return DDA_EINVAL;
+  try {
+    Err e = set_dev(c);
+    if (!e.ok()) return fail(c, e);
+    dda::HostTarget t;
+    e = dda::make_shape_target(shape, shpar, nshpar, &t);
+    if (!e.ok()) return fail(c, e);
+    drop_target(c);
+    c->tgt = std::move(t);
+    e = upload_target(c);
+    if (!e.ok()) return fail(c, e);
+    if (n_out) *n_out = c->n;
+    if (box_out)
+      for (int a = 0; a < 3; ++a) box_out[a] = c->tgt.box[a];
+    return DDA_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, Err::make(DDA_ENOMEM, "host allocation failed"));
+  }
+}
+
+dda_status dda_setup_target(dda_ctx* c, const int32_t* ixyz, const int32_t* icomp, int64_t n, const double origin[3],
+                            const double a1[3], const double a2[3]) {
+  if (!c) return DDA_EINVAL;
+  try {
+    Err e = set_dev(c);
+    if (!e.ok()) return fail(c, e);
+    dda::HostTarget t;
+    e = dda::make_site_target(ixyz, icomp, n, origin, a1, a2, &t);
+    if (!e.ok()) return fail(c, e);
+    drop_target(c);
+    c->tgt = std::move(t);
+    e = upload_target(c);
+    if (!e.ok()) return fail(c, e);
+    return DDA_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, Err::make(DDA_ENOMEM, "host allocation failed"));
+  }
+}
+
+dda_status dda_get_sites(dda_ctx* c, int32_t* ixyz_out, double origin_out[3]) {
+  if (!c) return DDA_EINVAL;
+  if (!c->have_target) return fail(c, Err::make(DDA_ESTATE, "no target"));
+  if (ixyz_out) std::memcpy(ixyz_out, c->tgt.ijk.data(), sizeof(int32_t) * c->tgt.ijk.size());
+  if (origin_out) std::memcpy(origin_out, c->tgt.origin, sizeof(double) * 3);
+  return DDA_OK;
+}
+
+dda_status dda_set_incident(dda_ctx* c, double kd, const double* ori, int n_ori, const double e01_lf[6], int iorth) {
+  if (!c) return DDA_EINVAL;
+  if (!c->have_target) return fail(c, Err::make(DDA_ESTATE, "set a target first"));
+  if (!(kd > 0) || !std::isfinite(kd)) return fail(c, Err::make(DDA_EINVAL, "kd must be positive"));
+  if (!ori || n_ori <= 0 || n_ori > 65535) return fail(c, Err::make(DDA_EINVAL, "need 1..65535 orientations"));
+  if (iorth != 1 && iorth != 2) return fail(c, Err::make(DDA_EINVAL, "iorth must be 1 or 2"));
+  if (!e01_lf) return fail(c, Err::make(DDA_EINVAL, "e01 missing"));
+  try {
+    Err e = set_dev(c);
+    if (!e.ok()) return fail(c, e);
+    cd e01[3];
+    double nrm = 0;
+    for (int a = 0; a < 3; ++a) {
+      e01[a] = cd(e01_lf[2 * a], e01_lf[2 * a + 1]);
+      nrm += std::norm(e01[a]);
+    }
+    if (!(nrm > 0)) return fail(c, Err::make(DDA_EINVAL, "e01 is zero"));
+    nrm = std::sqrt(nrm);
+    for (int a = 0; a < 3; ++a) e01[a] /= nrm;
+    if (std::abs(e01[0]) > 1e-12) return fail(c, Err::make(DDA_EINVAL, "e01 must be transverse to x_LF"));
+    // e02 = x_LF x conj(e01)
+    cd e02[3] = {cd(0, 0), -std::conj(e01[2]), std::conj(e01[1])};
+    drop_incident(c);
+    c->kd = kd;
+    c->n_ori = n_ori;
+    c->iorth = iorth;
+    c->nrhs = n_ori * iorth;
+    c->ori.assign(ori, ori + 3 * n_ori);
+    for (int a = 0; a < 3; ++a) { c->e01[a] = e01[a]; c->e02[a] = e02[a]; }
+    c->axes.resize(9 * n_ori);
+    c->rg.resize(c->nrhs);
+    for (int o = 0; o < n_ori; ++o) {
+      double* ax = &c->axes[9 * o];
+      lab_axes(c->tgt.a1, c->tgt.a2, ori[3 * o], ori[3 * o + 1], ori[3 * o + 2], ax);
+      for (int l = 0; l < iorth; ++l) {
+        dda::RhsGeom& g = c->rg[o * iorth + l];
+        const cd* ep = (l == 0) ? e01 : e02;
+        for (int k = 0; k < 3; ++k) {
+          g.k[k] = kd * ax[k];
+          const cd v = ep[0] * ax[k] + ep[1] * ax[3 + k] + ep[2] * ax[6 + k];
+          g.e[2 * k] = v.real();
+          g.e[2 * k + 1] = v.imag();
+        }
+      }
+    }
+    if (!c->host_only) {
+      e = dalloc(&c->d_rg, sizeof(dda::RhsGeom) * c->nrhs);
+      if (!e.ok()) return fail(c, e);
+      if (cudaMemcpy(c->d_rg, c->rg.data(), sizeof(dda::RhsGeom) * c->nrhs, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(c, Err::make(DDA_ECUDA, "copy of incidence failed"));
+    }
+    c->have_inc = true;
+    return DDA_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, Err::make(DDA_ENOMEM, "host allocation failed"));
+  }
+}
+
+int dda_nrhs(const dda_ctx* c) { return (c && c->have_inc) ? c->nrhs : 0; }
+
+dda_status dda_get_incidence(dda_ctx* c, double* k_tf, double* e_tf) {
+  if (!c) return DDA_EINVAL;
+  if (!c->have_inc) return fail(c, Err::make(DDA_ESTATE, "set the incident beams first"));
+  for (int b = 0; b < c->nrhs; ++b) {
+    if (k_tf)
+      for (int k = 0; k < 3; ++k) k_tf[3 * b + k] = c->rg[b].k[k];
+    if (e_tf)
+      for (int k = 0; k < 6; ++k) e_tf[6 * b + k] = c->rg[b].e[k];
+  }
+  return DDA_OK;
+}
+
+dda_status dda_incident_field(dda_ctx* c, void* e_dev, int dtype) {
+  if (!c || !e_dev) return DDA_EINVAL;
+  if (!c->have_inc) return fail(c, Err::make(DDA_ESTATE, "set the incident beams first"));
+  Err e = need_device(c);
+  if (!e.ok()) return fail(c, e);
+  e = set_dev(c);
+  if (!e.ok()) return fail(c, e);
+  if (dtype == DDA_C64)
+    e = dda::incident_field<float2>(c->d_ijk, c->d_origin, c->d_rg, c->nrhs, c->n, (float2*)e_dev, c->stream);
+  else if (dtype == DDA_C128)
+    e = dda::incident_field<double2>(c->d_ijk, c->d_origin, c->d_rg, c->nrhs, c->n, (double2*)e_dev, c->stream);
+  else
+    return fail(c, Err::make(DDA_EINVAL, "dtype must be DDA_C64 or DDA_C128"));
+  return e.ok() ? DDA_OK : fail(c, e);
+}
+
+dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
+  if (!c) return DDA_EINVAL;
+  if (!c->have_inc) return fail(c, Err::make(DDA_ESTATE, "set the incident beams (kd) first"));
+  try {
+    Err e = need_device(c);
+    if (!e.ok()) return fail(c, e);
+    e = set_dev(c);
+    if (!e.ok()) return fail(c, e);
+    int P[3];
+    for (int a = 0; a < 3; ++a) {
+      if (pad) {
+        P[a] = pad[a];
+        if (P[a] < 2 * c->tgt.box[a] || (P[a] % 2) || !dda::is_smooth235(P[a]))
+          return fail(c, Err::make(DDA_EINVAL, "pad must be even, >= 2 N per axis and 2,3,5-smooth"));
+      } else {
+        int v = 2 * c->tgt.box[a];
+        while (!dda::is_smooth235(v)) v += 2;
+        P[a] = v;
+      }
+    }
+    drop_green(c);
+    dda::Geom g{};
+    g.n = c->n;
+    g.nx = c->tgt.box[0]; g.ny = c->tgt.box[1]; g.nz = c->tgt.box[2];
+    g.px = P[0]; g.py = P[1]; g.pz = P[2];
+    g.ncomp = c->tgt.ncomp;
+    e = dda::make_plan(g.px, &g.plx);
+    if (e.ok()) e = dda::make_plan(g.py, &g.ply);
+    if (e.ok()) e = dda::make_plan(g.pz, &g.plz);
+    if (!e.ok()) return fail(c, e);
+    // twiddles exp(-2 pi i j / L) in FP64 on the host
+    const double pi = 3.14159265358979323846;
+    for (int a = 0; a < 3; ++a) {
+      const int L = P[a];
+      std::vector<double2> t128(L);
+      std::vector<float2> t64(L);
+      for (int j = 0; j < L; ++j) {
+        const double ang = -2.0 * pi * (double)j / (double)L;
+        t128[j] = make_double2(std::cos(ang), std::sin(ang));
+        t64[j] = make_float2((float)t128[j].x, (float)t128[j].y);
+      }
+      e = dalloc(&c->d_tw128[a], sizeof(double2) * L);
+      if (e.ok()) e = dalloc(&c->d_tw64[a], sizeof(float2) * L);
+      if (!e.ok()) return fail(c, e);
+      cudaMemcpy(c->d_tw128[a], t128.data(), sizeof(double2) * L, cudaMemcpyHostToDevice);
+      cudaMemcpy(c->d_tw64[a], t64.data(), sizeof(float2) * L, cudaMemcpyHostToDevice);
+    }
+    // schedule: 3-pass when the plane fits in the opt-in shared memory
+    int smax = 0;
+    cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    dda::MvTune t64, t128;
+    t64.g = 8; t128.g = 4;
+    dda::Geom g64 = g, g128 = g;
+    g64.ys = g.ny; g128.ys = g.ny;
+    t64.plane = dda::plane_smem_bytes<float2>(g64, t64) <= (size_t)smax;
+    t128.plane = dda::plane_smem_bytes<double2>(g128, t128) <= (size_t)smax;
+    if (!t64.plane) g64.ys = g.py;
+    if (!t128.plane) g128.ys = g.py;
+    c->g64 = g64; c->g128 = g128; c->t64 = t64; c->t128 = t128;
+    const int64_t M = (int64_t)g.px * g.py * g.pz;
+    double2* scratch = nullptr;
+    e = dalloc(&c->d_ghat128, sizeof(double2) * 6 * M);
+    if (e.ok()) e = dalloc(&c->d_ghat64, sizeof(float2) * 6 * M);
+    if (e.ok()) e = dalloc(&scratch, sizeof(double2) * 6 * M);
+    if (!e.ok()) { dfree(scratch); return fail(c, e); }
+    e = dda::build_green(g64, c->kd, c->d_tw128[0], c->d_tw128[1], c->d_tw128[2], scratch, c->d_ghat128, c->d_ghat64,
+                         c->stream);
+    cudaStreamSynchronize(c->stream);
+    dfree(scratch);
+    if (!e.ok()) return fail(c, e);
+    c->have_green = true;
+    return DDA_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, Err::make(DDA_ENOMEM, "host allocation failed"));
+  }
+}
+
+dda_status dda_set_polarizability(dda_ctx* c, int presc, const double* m_reim, int ncomp) {
+  if (!c) return DDA_EINVAL;
+  if (!c->have_inc) return fail(c, Err::make(DDA_ESTATE, "set the incident beams (kd) first"));
+  if (presc != DDA_CM && presc != DDA_LATTDR && presc != DDA_GKDLDR)
+    return fail(c, Err::make(DDA_EINVAL, "unknown prescription"));
+  if (!m_reim || ncomp < c->tgt.ncomp || ncomp > 255)
+    return fail(c, Err::make(DDA_EINVAL, "need one refractive index per composition"));
+  try {
+    Err e = set_dev(c);
+    if (!e.ok()) return fail(c, e);
+    std::vector<cd> ia((size_t)c->nrhs * ncomp * 3);
+    for (int b = 0; b < c->nrhs; ++b) {
+      const dda::RhsGeom& g = c->rg[b];
+      const double kh[3] = {g.k[0] / c->kd, g.k[1] / c->kd, g.k[2] / c->kd};
+      const cd ev[3] = {cd(g.e[0], g.e[1]), cd(g.e[2], g.e[3]), cd(g.e[4], g.e[5])};
+      for (int m = 0; m < ncomp; ++m) {
+        const cd mm(m_reim[2 * m], m_reim[2 * m + 1]);
+        if (std::abs(mm * mm - 1.0) == 0.0) return fail(c, Err::make(DDA_EINVAL, "m = 1 has no polarizability"));
+        inv_alpha(presc, mm, c->kd, kh, ev, &ia[((size_t)b * ncomp + m) * 3]);
+      }
+    }
+    std::vector<double2> h128(ia.size());
+    std::vector<float2> h64(ia.size());
+    for (size_t i = 0; i < ia.size(); ++i) {
+      h128[i] = make_double2(ia[i].real(), ia[i].imag());
+      h64[i] = make_float2((float)ia[i].real(), (float)ia[i].imag());
+    }
+    drop_alpha(c);
+    if (!c->host_only) {
+      e = dalloc(&c->d_ia128, sizeof(double2) * ia.size());
+      if (e.ok()) e = dalloc(&c->d_ia64, sizeof(float2) * ia.size());
+      if (!e.ok()) return fail(c, e);
+      cudaMemcpy(c->d_ia128, h128.data(), sizeof(double2) * ia.size(), cudaMemcpyHostToDevice);
+      cudaMemcpy(c->d_ia64, h64.data(), sizeof(float2) * ia.size(), cudaMemcpyHostToDevice);
+    }
+    c->ia = std::move(ia);
+    c->presc = presc;
+    c->ncomp = ncomp;
+    c->have_alpha = true;
+    return DDA_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, Err::make(DDA_ENOMEM, "host allocation failed"));
+  }
+}
+
+dda_status dda_get_inv_alpha(dda_ctx* c, double* out) {
+  if (!c || !out) return DDA_EINVAL;
+  if (!c->have_alpha) return fail(c, Err::make(DDA_ESTATE, "no polarizability"));
+  for (size_t i = 0; i < c->ia.size(); ++i) {
+    out[2 * i] = c->ia[i].real();
+    out[2 * i + 1] = c->ia[i].imag();
+  }
+  return DDA_OK;
+}
+
+dda_status dda_matvec(dda_ctx* c, const void* p, void* ap, int nrhs, int dtype) {
+  if (!c || !p || !ap) return DDA_EINVAL;
+  if (!c->have_alpha || !c->have_green)
+    return fail(c, Err::make(DDA_ESTATE, "set target, incidence, Green tensor and alpha first"));
+  if (nrhs < 1 || nrhs > c->nrhs) return fail(c, Err::make(DDA_EINVAL, "nrhs out of range"));
+  if (p == ap) return fail(c, Err::make(DDA_EINVAL, "p and ap may not alias"));
+  Err e = set_dev(c);
+  if (!e.ok()) return fail(c, e);
+  if (dtype == DDA_C64) e = matvec<float2>(c, (const float2*)p, (float2*)ap, nrhs, 0, false);
+  else if (dtype == DDA_C128) e = matvec<double2>(c, (const double2*)p, (double2*)ap, nrhs, 0, false);
+  else return fail(c, Err::make(DDA_EINVAL, "dtype must be DDA_C64 or DDA_C128"));
+  return e.ok() ? DDA_OK : fail(c, e);
+}
+
+namespace {
+template <typename C>
+Err kvec_alloc(dda_ctx* c, dda::KrylovVecs<C>* kv, int nvec_extra) {
+  const size_t one = sizeof(C) * (size_t)c->nrhs * 3 * c->n;
+  const size_t need = one * (8 + nvec_extra);
+  if (need > c->kvec_bytes) {
+    DDA_TRY(dalloc(&c->d_kvec, need));
+    c->kvec_bytes = need;
+  }
+  C* base = (C*)c->d_kvec;
+  const size_t el = (size_t)c->nrhs * 3 * c->n;
+  kv->x = base; kv->r = base + el; kv->rhat = base + 2 * el; kv->p = base + 3 * el;
+  kv->v = base + 4 * el; kv->s = base + 5 * el; kv->t = base + 6 * el; kv->b = base + 7 * el;
+  return Err::Ok();
+}
+
+// true residual (FP64 product): |E - A P|^2 and |E|^2 per RHS
+Err true_residual(dda_ctx* c, const double2* p, double2* scratch_ax, double2* scratch_r, std::vector<double>* rel) {
+  const int nrhs = c->nrhs;
+  const int64_t n3 = 3 * c->n;
+  DDA_TRY(matvec<double2>(c, p, scratch_ax, nrhs, 0, false));
+  dda::RedBuf rb = redbuf(c, nrhs, n3);
+  DDA_TRY(ensure_part(c, sizeof(double) * (size_t)rb.nblk * nrhs * dda::kRedSlots));
+  rb.part = c->d_part;
+  DDA_TRY(ensure_small(c, sizeof(double) * 2 * nrhs + sizeof(dda::KState) * nrhs));
+  DDA_TRY(dda::residual_c128(c->d_e128, scratch_ax, scratch_r, c->d_small, rb, nrhs, n3, c->stream));
+  DDA_CU(cudaMemcpyAsync(c->h_pinned, c->d_small, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, c->stream));
+  DDA_CU(cudaStreamSynchronize(c->stream));
+  rel->resize(nrhs);
+  for (int b = 0; b < nrhs; ++b) {
+    const double rr = c->h_pinned[2 * b], bb = c->h_pinned[2 * b + 1];
+    (*rel)[b] = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+  }
+  return Err::Ok();
+}
+}  // namespace
+
+dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_solve_report* rep) {
+  if (!c || !opt || !p_dev) return DDA_EINVAL;
+  if (!c->have_alpha || !c->have_green)
+    return fail(c, Err::make(DDA_ESTATE, "set target, incidence, Green tensor and alpha first"));
+  dda_solve_opts o = *opt;
+  if (o.solver != DDA_BICGSTAB && o.solver != DDA_CCG) return fail(c, Err::make(DDA_EINVAL, "unknown solver"));
+  if (o.precision < DDA_PREC_C64 || o.precision > DDA_PREC_MIXED)
+    return fail(c, Err::make(DDA_EINVAL, "unknown precision"));
+  if (!(o.tol > 0) || o.maxit < 1) return fail(c, Err::make(DDA_EINVAL, "tol must be > 0 and maxit >= 1"));
+  // Default streams cannot be captured: run the solve on a context-owned stream
+  // ordered after the caller's work (the call is synchronous, so nothing is
+  // needed afterwards).
+  cudaStream_t user = c->stream;
+  struct Restore { dda_ctx* c; cudaStream_t s; ~Restore() { c->stream = s; } } restore{c, user};
+  if (o.use_graph && (user == nullptr || user == cudaStreamLegacy || user == cudaStreamPerThread)) {
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, Err::make(DDA_ECUDA, "cudaSetDevice failed"));
+    if (!c->own_stream && cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(c, Err::make(DDA_ECUDA, "stream creation failed"));
+    if (!c->ev && cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess)
+      return fail(c, Err::make(DDA_ECUDA, "event creation failed"));
+    cudaEventRecord(c->ev, user);
+    cudaStreamWaitEvent(c->own_stream, c->ev, 0);
+    c->stream = c->own_stream;
+  }
+  try {
+    Err e = set_dev(c);
+    if (!e.ok()) return fail(c, e);
+    const auto t0 = std::chrono::steady_clock::now();
+    const int nrhs = c->nrhs;
+    const int64_t n3 = 3 * c->n;
+    const int64_t el = (int64_t)nrhs * n3;
+    double2* P = (double2*)p_dev;
+    e = ensure_einc(c);
+    if (!e.ok()) return fail(c, e);
+    std::vector<int> iters(nrhs, 0), outer_n(nrhs, 0);
+    int matvecs = 0;
+    bool timed_out = false;
+    std::vector<double> rel;
+    // scratch c128 pair for true residuals (2 vectors)
+    double2* sc = nullptr;
+    e = dalloc(&sc, sizeof(double2) * 2 * el);
+    if (!e.ok()) return fail(c, e);
+    auto cleanup = [&]() { dfree(sc); };
+    int outer = 0;
+    if (o.precision == DDA_PREC_C128) {
+      dda::KrylovVecs<double2> kv;
+      e = kvec_alloc<double2>(c, &kv, 0);
+      if (e.ok()) {
+        cudaMemcpyAsync(kv.b, c->d_e128, sizeof(double2) * el, cudaMemcpyDeviceToDevice, c->stream);
+        if (o.warm_start) cudaMemcpyAsync(kv.x, P, sizeof(double2) * el, cudaMemcpyDeviceToDevice, c->stream);
+        SolveStats s;
+        e = krylov<double2>(c, o, kv, o.tol, o.maxit, o.warm_start != 0, &s, t0, &timed_out);
+        if (e.ok()) {
+          cudaMemcpyAsync(P, kv.x, sizeof(double2) * el, cudaMemcpyDeviceToDevice, c->stream);
+          iters = s.iters;
+          matvecs += s.matvecs;
+        }
+      }
+    } else if (o.precision == DDA_PREC_C64) {
+      dda::KrylovVecs<float2> kv;
+      e = kvec_alloc<float2>(c, &kv, 0);
+      if (e.ok()) e = dda::convert_from_c128<float2>(c->d_e128, kv.b, el, c->stream);
+      if (e.ok() && o.warm_start) e = dda::convert_from_c128<float2>(P, kv.x, el, c->stream);
+      SolveStats s;
+      if (e.ok()) e = krylov<float2>(c, o, kv, o.tol, o.maxit, o.warm_start != 0, &s, t0, &timed_out);
+      if (e.ok()) {
+        cudaMemsetAsync(P, 0, sizeof(double2) * el, c->stream);
+        e = dda::add_to_c128<float2>(P, kv.x, nullptr, nrhs, n3, c->stream);
+        iters = s.iters;
+        matvecs += s.matvecs;
+      }
+    } else {
+      // mixed: inner complex64 solves of A d = r, r from FP64 true residuals
+      dda::KrylovVecs<float2> kv;
+      e = kvec_alloc<float2>(c, &kv, 0);
+      // each inner solve aims straight for tol, but never below the complex64 floor
+      const double inner = o.inner_tol > 0 ? o.inner_tol : 5e-6;
+      if (e.ok() && !o.warm_start) cudaMemsetAsync(P, 0, sizeof(double2) * el, c->stream);
+      int budget = o.maxit;
+      while (e.ok()) {
+        // r = E - A P (FP64); at P = 0 the residual is E itself
+        double2* r128 = sc + el;
+        if (outer == 0 && !o.warm_start) {
+          cudaMemcpyAsync(r128, c->d_e128, sizeof(double2) * el, cudaMemcpyDeviceToDevice, c->stream);
+          rel.assign(nrhs, 1.0);
+        } else {
+          e = true_residual(c, P, sc, r128, &rel);
+          matvecs += 1;
+          if (!e.ok()) break;
+        }
+        bool all = true;
+        for (int b = 0; b < nrhs; ++b) all = all && rel[b] <= o.tol;
+        if (all || budget <= 0 || timed_out) break;
+        // inner right-hand side: residual of unconverged RHS (converged ones get 0 and stop at once)
+        e = dda::convert_from_c128<float2>(r128, kv.b, el, c->stream);
+        if (!e.ok()) break;
+        for (int b = 0; b < nrhs; ++b)
+          if (rel[b] <= o.tol) cudaMemsetAsync(kv.b + (int64_t)b * n3, 0, sizeof(float2) * n3, c->stream);
+        // ask the inner solve for the reduction that reaches tol, but at least `inner`
+        double worst = 0;
+        for (int b = 0; b < nrhs; ++b) worst = std::max(worst, rel[b] > o.tol ? o.tol / rel[b] : 0.0);
+        const double itol = std::max(inner, 0.5 * worst);
+        SolveStats s;
+        e = krylov<float2>(c, o, kv, itol, budget, false, &s, t0, &timed_out);
+        if (!e.ok()) break;
+        for (int b = 0; b < nrhs; ++b) {
+          iters[b] += s.iters[b];
+          if (rel[b] > o.tol) outer_n[b] += 1;
+        }
+        int used = 0;
+        for (int b = 0; b < nrhs; ++b) used = std::max(used, s.iters[b]);
+        budget -= std::max(used, 1);
+        matvecs += s.matvecs;
+        e = dda::add_to_c128<float2>(P, kv.x, nullptr, nrhs, n3, c->stream);
+        ++outer;
+      }
+    }
+    if (!e.ok()) { cleanup(); return fail(c, e); }
+    // final true residual in FP64 (for MIXED it was computed by the loop's last pass)
+    if (o.precision != DDA_PREC_MIXED || rel.empty()) {
+      e = true_residual(c, P, sc, sc + el, &rel);
+      if (!e.ok()) { cleanup(); return fail(c, e); }
+    }
+    std::vector<double> ner(nrhs, NAN);
+    if (o.normal_eq) {
+      // |A^H (A P - E)| / |A^H E| with FP64 products (guide, eq. err_tol)
+      double2* r128 = sc + el;  // holds E - A P from true_residual
+      e = matvec<double2>(c, r128, sc, nrhs, 0, true);
+      dda::RedBuf rb = redbuf(c, nrhs, n3);
+      std::vector<double> num(nrhs), den(nrhs);
+      if (e.ok()) {
+        // reuse residual kernel: |0 - x|^2 gives |x|^2
+        e = dda::residual_c128(sc, sc, r128, c->d_small, rb, nrhs, n3, c->stream);  // r128 = 0, second slot |sc|^2
+      }
+      if (e.ok()) {
+        cudaMemcpyAsync(c->h_pinned, c->d_small, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, c->stream);
+        cudaStreamSynchronize(c->stream);
+        for (int b = 0; b < nrhs; ++b) num[b] = c->h_pinned[2 * b + 1];
+        e = matvec<double2>(c, c->d_e128, sc, nrhs, 0, true);
+      }
+      if (e.ok()) e = dda::residual_c128(sc, sc, r128, c->d_small, rb, nrhs, n3, c->stream);
+      if (e.ok()) {
+        cudaMemcpyAsync(c->h_pinned, c->d_small, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, c->stream);
+        cudaStreamSynchronize(c->stream);
+        for (int b = 0; b < nrhs; ++b) {
+          den[b] = c->h_pinned[2 * b + 1];
+          ner[b] = den[b] > 0 ? std::sqrt(num[b] / den[b]) : 0.0;
+        }
+      }
+      if (!e.ok()) { cleanup(); return fail(c, e); }
+    }
+    cleanup();
+    bool all = true;
+    for (int b = 0; b < nrhs; ++b) {
+      const bool conv = rel[b] <= o.tol;
+      all = all && conv;
+      if (rep) {
+        rep[b].iters = iters[b];
+        rep[b].matvecs = matvecs;
+        rep[b].outer = (o.precision == DDA_PREC_MIXED) ? outer_n[b] : 0;
+        rep[b].converged = conv ? 1 : 0;
+        rep[b].true_rel_resid = rel[b];
+        rep[b].normal_eq_ratio = ner[b];
+      }
+    }
+    if (timed_out && !all) return fail(c, Err::make(DDA_ETIMEOUT, "solve exceeded timeout_ms"));
+    if (!all) return fail(c, Err::make(DDA_ENOCONV, "some right-hand side did not reach tol within maxit"));
+    return DDA_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, Err::make(DDA_ENOMEM, "host allocation failed"));
+  }
+}
+
+dda_status dda_cross_sections(dda_ctx* c, const void* p_dev, double* q_out, const double* dirs, int ndir,
+                              double* mueller_out) {
+  if (!c || !p_dev) return DDA_EINVAL;
+  if (!c->have_alpha || !c->have_green)
+    return fail(c, Err::make(DDA_ESTATE, "set target, incidence, Green tensor and alpha first"));
+  if (ndir < 0 || (ndir > 0 && (!dirs || !mueller_out))) return fail(c, Err::make(DDA_EINVAL, "bad directions"));
+  if (ndir > 0 && c->iorth != 2) return fail(c, Err::make(DDA_EINVAL, "Mueller matrices need iorth = 2"));
+  try {
+    Err e = set_dev(c);
+    if (!e.ok()) return fail(c, e);
+    const int nrhs = c->nrhs;
+    const double2* P = (const double2*)p_dev;
+    const double pi = 3.14159265358979323846;
+    const double aeff = std::cbrt(3.0 * (double)c->n / (4.0 * pi));
+    const double geo = pi * aeff * aeff, k = c->kd;
+    if (q_out) {
+      dda::RedBuf rb;
+      rb.nblk = (int)std::max<int64_t>(1, std::min<int64_t>((c->n + 1023) / 1024, 1216 / std::max(1, nrhs)));
+      e = ensure_part(c, sizeof(double) * (size_t)rb.nblk * nrhs * 4);
+      if (!e.ok()) return fail(c, e);
+      rb.part = c->d_part;
+      e = ensure_small(c, sizeof(double) * 3 * nrhs);
+      if (!e.ok()) return fail(c, e);
+      e = dda::qsums(c->d_ijk, c->d_comp, c->d_origin, c->d_rg, c->d_ia128, c->ncomp, k, P, nrhs, c->n, c->d_small, rb,
+                     c->stream);
+      if (!e.ok()) return fail(c, e);
+      cudaMemcpyAsync(c->h_pinned, c->d_small, sizeof(double) * 3 * nrhs, cudaMemcpyDeviceToHost, c->stream);
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, Err::make(DDA_ECUDA, "q sums failed"));
+      for (int b = 0; b < nrhs; ++b) {
+        const double cext = 4 * pi * k * c->h_pinned[3 * b], cpha = 2 * pi * k * c->h_pinned[3 * b + 1];
+        const double cabs = 4 * pi * k * c->h_pinned[3 * b + 2];
+        q_out[4 * b] = cext / geo;
+        q_out[4 * b + 1] = cabs / geo;
+        q_out[4 * b + 2] = (cext - cabs) / geo;
+        q_out[4 * b + 3] = cpha / geo;
+      }
+    }
+    if (ndir > 0) {
+      // scattering directions (LFRAME) per orientation, in TF
+      std::vector<double> nh((size_t)nrhs * ndir * 3);
+      std::vector<double> th((size_t)c->n_ori * ndir * 3), ph((size_t)c->n_ori * ndir * 3);
+      for (int o = 0; o < c->n_ori; ++o) {
+        const double* ax = &c->axes[9 * o];
+        for (int d = 0; d < ndir; ++d) {
+          const double t = dirs[2 * d], f = dirs[2 * d + 1];
+          const double nl[3] = {std::cos(t), std::sin(t) * std::cos(f), std::sin(t) * std::sin(f)};
+          const double tl[3] = {-std::sin(t), std::cos(t) * std::cos(f), std::cos(t) * std::sin(f)};
+          const double pl[3] = {0.0, -std::sin(f), std::cos(f)};
+          for (int kk = 0; kk < 3; ++kk) {
+            const double nt = nl[0] * ax[kk] + nl[1] * ax[3 + kk] + nl[2] * ax[6 + kk];
+            th[((size_t)o * ndir + d) * 3 + kk] = tl[0] * ax[kk] + tl[1] * ax[3 + kk] + tl[2] * ax[6 + kk];
+            ph[((size_t)o * ndir + d) * 3 + kk] = pl[0] * ax[kk] + pl[1] * ax[3 + kk] + pl[2] * ax[6 + kk];
+            for (int l = 0; l < c->iorth; ++l) nh[(((size_t)(o * c->iorth + l)) * ndir + d) * 3 + kk] = nt;
+          }
+        }
+      }
+      double* d_nh = nullptr;
+      double2* d_F = nullptr;
+      double2* d_part = nullptr;
+      const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((c->n + 2047) / 2048, 64));
+      e = dalloc(&d_nh, sizeof(double) * nh.size());
+      if (e.ok()) e = dalloc(&d_F, sizeof(double2) * (size_t)nrhs * ndir * 3);
+      if (e.ok()) e = dalloc(&d_part, sizeof(double) * 6 * (size_t)nrhs * ndir * nblk);
+      if (e.ok()) {
+        cudaMemcpy(d_nh, nh.data(), sizeof(double) * nh.size(), cudaMemcpyHostToDevice);
+        e = dda::farfield(c->d_ijk, c->d_origin, d_nh, k, P, nrhs, ndir, c->n, d_F, d_part, nblk, c->stream);
+      }
+      std::vector<double2> F((size_t)nrhs * ndir * 3);
+      if (e.ok()) {
+        cudaMemcpyAsync(F.data(), d_F, sizeof(double2) * F.size(), cudaMemcpyDeviceToHost, c->stream);
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) e = Err::make(DDA_ECUDA, "far field failed");
+      }
+      dfree(d_nh);
+      dfree(d_F);
+      dfree(d_part);
+      if (!e.ok()) return fail(c, e);
+      const double k3 = k * k * k;
+      // a, b, c, d of the guide's GETMUELLER relations (Lab-Frame e01, e02)
+      const cd A = std::conj(c->e01[1]), B = std::conj(c->e01[2]), Cc = std::conj(c->e02[1]), D = std::conj(c->e02[2]);
+      for (int o = 0; o < c->n_ori; ++o)
+        for (int d = 0; d < ndir; ++d) {
+          cd f[2][2];
+          for (int l = 0; l < 2; ++l) {
+            const double2* Fv = &F[(((size_t)(o * 2 + l)) * ndir + d) * 3];
+            const double* e1 = &th[((size_t)o * ndir + d) * 3];
+            const double* e2 = &ph[((size_t)o * ndir + d) * 3];
+            cd s1(0, 0), s2(0, 0);
+            for (int kk = 0; kk < 3; ++kk) {
+              const cd fv(Fv[kk].x, Fv[kk].y);
+              s1 += e1[kk] * fv;
+              s2 += e2[kk] * fv;
+            }
+            f[0][l] = k3 * s1;
+            f[1][l] = k3 * s2;
+          }
+          const double phs = dirs[2 * d + 1], cp = std::cos(phs), sp = std::sin(phs);
+          const cd I(0, 1);
+          const cd S1 = -I * (f[1][0] * (B * cp - A * sp) + f[1][1] * (D * cp - Cc * sp));
+          const cd S2 = -I * (f[0][0] * (A * cp + B * sp) + f[0][1] * (Cc * cp + D * sp));
+          const cd S3 = I * (f[0][0] * (B * cp - A * sp) + f[0][1] * (D * cp - Cc * sp));
+          const cd S4 = I * (f[1][0] * (A * cp + B * sp) + f[1][1] * (Cc * cp + D * sp));
+          double* m = mueller_out + ((size_t)o * ndir + d) * 16;
+          auto cj = [](cd z) { return std::conj(z); };
+          m[0] = 0.5 * (std::norm(S1) + std::norm(S2) + std::norm(S3) + std::norm(S4));
+          m[1] = 0.5 * (std::norm(S2) - std::norm(S1) + std::norm(S4) - std::norm(S3));
+          m[2] = (S2 * cj(S3) + S1 * cj(S4)).real();
+          m[3] = (S2 * cj(S3) - S1 * cj(S4)).imag();
+          m[4] = 0.5 * (std::norm(S2) - std::norm(S1) + std::norm(S3) - std::norm(S4));
+          m[5] = 0.5 * (std::norm(S1) + std::norm(S2) - std::norm(S3) - std::norm(S4));
+          m[6] = (S2 * cj(S3) - S1 * cj(S4)).real();
+          m[7] = (S2 * cj(S3) + S1 * cj(S4)).imag();
+          m[8] = (S2 * cj(S4) + S1 * cj(S3)).real();
+          m[9] = (S2 * cj(S4) - S1 * cj(S3)).real();
+          m[10] = (S1 * cj(S2) + S3 * cj(S4)).real();
+          m[11] = (S2 * cj(S1) + S4 * cj(S3)).imag();
+          m[12] = (S4 * cj(S2) + S1 * cj(S3)).imag();
+          m[13] = (S4 * cj(S2) - S1 * cj(S3)).imag();
+          m[14] = (S1 * cj(S2) - S3 * cj(S4)).imag();
+          m[15] = (S1 * cj(S2) - S3 * cj(S4)).real();
+        }
+    }
+    return DDA_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, Err::make(DDA_ENOMEM, "host allocation failed"));
+  }
+}
+
+
+unsigned long long dda_kernel_launches(void) { return dda::launches(); }
+
+dda_status dda_profile_matvec(dda_ctx* c, int nrhs, int dtype, int iters, double* ms_per_pass, int* npass) {
+  if (!c || !ms_per_pass || !npass || iters < 1) return DDA_EINVAL;
+  if (!c->have_alpha || !c->have_green)
+    return fail(c, Err::make(DDA_ESTATE, "set target, incidence, Green tensor and alpha first"));
+  if (nrhs < 1 || nrhs > c->nrhs) return fail(c, Err::make(DDA_EINVAL, "nrhs out of range"));
+  if (dtype != DDA_C64 && dtype != DDA_C128) return fail(c, Err::make(DDA_EINVAL, "bad dtype"));
+  Err e = set_dev(c);
+  if (!e.ok()) return fail(c, e);
+  const bool plane = (dtype == DDA_C64) ? c->t64.plane : c->t128.plane;
+  const int np = plane ? 3 : 5;
+  const size_t cs = dtype == DDA_C64 ? sizeof(float2) : sizeof(double2);
+  const size_t bytes = cs * (size_t)nrhs * 3 * c->n;
+  void *p = nullptr, *ap = nullptr;
+  cudaEvent_t ev[6] = {};
+  std::vector<double> acc(np, 0.0);
+  e = dalloc((char**)&p, bytes);
+  if (e.ok()) e = dalloc((char**)&ap, bytes);
+  if (e.ok() && cudaMemsetAsync(p, 0, bytes, c->stream) != cudaSuccess) e = Err::make(DDA_ECUDA, "memset failed");
+  for (int i = 0; i <= np && e.ok(); ++i)
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) e = Err::make(DDA_ECUDA, "event creation failed");
+  for (int it = 0; it < iters && e.ok(); ++it) {
+    dda::set_pass_events(ev);
+    if (dtype == DDA_C64) e = matvec<float2>(c, (const float2*)p, (float2*)ap, nrhs, 0, false);
+    else e = matvec<double2>(c, (const double2*)p, (double2*)ap, nrhs, 0, false);
+    dda::set_pass_events(nullptr);
+    if (!e.ok()) break;
+    if (cudaEventSynchronize(ev[np]) != cudaSuccess) { e = Err::make(DDA_ECUDA, "profile sync failed"); break; }
+    for (int i = 0; i < np; ++i) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+      acc[i] += ms;
+    }
+  }
+  dda::set_pass_events(nullptr);
+  for (int i = 0; i <= np; ++i)
+    if (ev[i]) cudaEventDestroy(ev[i]);
+  dfree(p);
+  dfree(ap);
+  if (!e.ok()) return fail(c, e);
+  for (int i = 0; i < np; ++i) ms_per_pass[i] = acc[i] / iters;
+  *npass = np;
+  return DDA_OK;
+}

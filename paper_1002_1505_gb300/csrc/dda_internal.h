@@ -1,0 +1,195 @@
+// Internal declarations of the GB300 DDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "../../include/dda.h"
+#include "fft.cuh"
+
+namespace dda {
+
+using cd = std::complex<double>;
+
+// Status with message; every internal helper returns one.
+struct Err {
+  dda_status code = DDA_OK;
+  std::string msg;
+  bool ok() const { return code == DDA_OK; }
+  static Err Ok() { return Err{}; }
+  static Err make(dda_status c, std::string m) { Err e; e.code = c; e.msg = std::move(m); return e; }
+};
+
+#define DDA_CU(call)                                                                          \
+  do {                                                                                        \
+    cudaError_t e__ = (call);                                                                 \
+    if (e__ != cudaSuccess)                                                                   \
+      return ::dda::Err::make(e__ == cudaErrorMemoryAllocation ? DDA_ENOMEM : DDA_ECUDA,      \
+                              std::string(#call) + ": " + cudaGetErrorString(e__));           \
+  } while (0)
+
+#define DDA_TRY(expr)                  \
+  do {                                 \
+    ::dda::Err e__ = (expr);           \
+    if (!e__.ok()) return e__;         \
+  } while (0)
+
+// ------------------------------------------------------------------ targets (host)
+struct HostTarget {
+  std::vector<int32_t> ijk;   // N x 3 box-relative lattice indices, x-fastest order
+  std::vector<uint8_t> comp;  // N, 0-based composition
+  int box[3] = {0, 0, 0};
+  double origin[3] = {0, 0, 0};
+  double a1[3] = {1, 0, 0};
+  double a2[3] = {0, 1, 0};
+  int ncomp = 1;
+};
+Err make_shape_target(int shape, const double* shpar, int nshpar, HostTarget* out);
+Err make_site_target(const int32_t* ixyz, const int32_t* icomp, int64_t n, const double origin[3],
+                     const double a1[3], const double a2[3], HostTarget* out);
+
+// ------------------------------------------------------------------ FFT plans (host)
+Err make_plan(int L, FftPlan* out);
+bool is_smooth235(int v);
+
+// ------------------------------------------------------------------ device geometry
+// Everything a matvec kernel needs about the grid, by value.
+struct Geom {
+  int64_t n;             // occupied sites
+  int nx, ny, nz;        // box
+  int px, py, pz;        // padded grid
+  int ys;                // y stride of the FFT workspace rows (ny: plane path, py: 5-pass path)
+  int ncomp;
+  FftPlan plx, ply, plz;
+};
+
+// Device-resident data shared by matvec kernels of one precision.
+template <typename C>
+struct MvData {
+  const int32_t* map;   // nx*ny*nz box -> site index or -1
+  const uint8_t* comp;  // N compositions (0-based), may be null when ncomp == 1
+  const C* ghat;        // [px][py][pz][6] Fourier-space tensor (xx,xy,xz,yy,yz,zz), scaled by 1/M
+  const C* ia;          // [nrhs][ncomp][3] diagonal of alpha^{-1}
+  const C* twx;         // twiddles exp(-2 pi i j / L), L entries each
+  const C* twy;
+  const C* twz;
+  C* work;              // FFT workspace [nrhs_chunk][3][px][nz][ys]
+};
+
+// Launch tuning chosen per grid (autotuner fills it).
+struct MvTune {
+  int ty = 8;         // y rows per CTA in the x passes
+  int g = 8;          // z columns per batch in the z pass
+  int thr_x = 256;    // threads, x passes
+  int thr_p = 512;    // threads, plane / z passes
+  bool plane = true;  // 3-pass schedule (plane fits in shared memory)
+};
+
+// Enqueue ap = A p for nrhs right-hand sides (rhs0 = index of the first one for alpha).
+template <typename C>
+Err launch_matvec(const Geom& g, const MvData<C>& d, const MvTune& t, const C* p, C* ap, int nrhs, int rhs0,
+                  bool conj, cudaStream_t st);
+template <typename C>
+size_t plane_smem_bytes(const Geom& g, const MvTune& t);
+size_t x_smem_bytes(const Geom& g, const MvTune& t, size_t csize);
+
+// Profiling and accounting: per-pass events for the next launches on this thread
+// (ev[0] before the first pass, ev[i+1] after pass i; null = off), and a global
+// count of kernels launched by the library (graph replays included).
+void set_pass_events(cudaEvent_t* ev);
+unsigned long long launches();
+void add_launches(unsigned long long n);
+void sub_launches(unsigned long long n);
+
+// Green tensor: fill + FP64 FFT + pack into ghat128 / ghat64.
+Err build_green(const Geom& g, double kd, const double2* tw128x, const double2* tw128y, const double2* tw128z,
+                double2* scratch, double2* ghat128, float2* ghat64, cudaStream_t st);
+
+// Generic batched FFT over rows/strides (used by tests of the engine and the Green build).
+template <typename C>
+Err fft_rows(C* data, int64_t nrows, int64_t row_stride, const FftPlan& pl, const C* tw, int nin, int nout,
+             bool inverse, cudaStream_t st);
+template <typename C>
+Err fft_strided(C* data, int L, int64_t estride, int64_t ninner, int64_t nouter, int64_t outer_stride,
+                const FftPlan& pl, const C* tw, bool inverse, cudaStream_t st);
+
+// ------------------------------------------------------------------ Krylov / BLAS-1 (krylov.cu)
+struct RedBuf {
+  double* part = nullptr;   // partial sums [nrhs][nblk][kRedSlots]
+  int nblk = 0;
+};
+constexpr int kRedSlots = 4;
+
+// Per-RHS scalar state of the iterative solvers (device).
+struct KState {
+  double2 rho, alpha, omega, beta;
+  double bb;      // |b|^2
+  double rr;      // |r|^2 (recursive)
+  double zz;      // CCG |A^H r|^2
+  double tol2;    // (tol)^2 * |b|^2 threshold for this solve
+  int done;       // 1 = converged, 2 = breakdown
+  int it;
+  int pad0, pad1;
+};
+
+template <typename C> Err k_copy_convert_c128_to(const double2* src, C* dst, int64_t count, cudaStream_t st);
+template <typename C> Err k_accumulate_to_c128(double2* dst, const C* src, int64_t count, cudaStream_t st);
+
+template <typename C>
+struct KrylovVecs {
+  C *x, *r, *rhat, *p, *v, *s, *t, *b;
+};
+
+// BiCGstab / CCG building blocks, all per-RHS batched over nrhs vectors of length n3.
+template <typename C> Err bicg_init(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3,
+                                    double tol, bool have_ax, cudaStream_t st);
+template <typename C> Err bicg_p_update(const KrylovVecs<C>& kv, const KState* ks, int nrhs, int64_t n3,
+                                        cudaStream_t st);
+template <typename C> Err bicg_alpha(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3,
+                                     cudaStream_t st);
+template <typename C> Err bicg_s_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3,
+                                        cudaStream_t st);
+template <typename C> Err bicg_omega(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3,
+                                     cudaStream_t st);
+template <typename C> Err bicg_xr_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3,
+                                         cudaStream_t st);
+// CCG (CG on the normal equations)
+template <typename C> Err ccg_init(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3,
+                                   double tol, bool have_ax, cudaStream_t st);
+template <typename C> Err ccg_start(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3,
+                                    cudaStream_t st);
+template <typename C> Err ccg_alpha_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3,
+                                           cudaStream_t st);
+template <typename C> Err ccg_beta_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3,
+                                          cudaStream_t st);
+
+// r = b - ax (c128), returns per-RHS |r|^2 and |b|^2 into out2[2*nrhs] (device)
+Err residual_c128(const double2* b, const double2* ax, double2* r, double* out2, RedBuf rb, int nrhs, int64_t n3,
+                  cudaStream_t st);
+// dst(C) = (C) src(c128)
+template <typename C> Err convert_from_c128(const double2* src, C* dst, int64_t count, cudaStream_t st);
+// dst(c128) += src(C) for RHS whose mask is 0 (mask may be null)
+template <typename C> Err add_to_c128(double2* dst, const C* src, const int* mask_done, int nrhs, int64_t n3,
+                                      cudaStream_t st);
+
+// ------------------------------------------------------------------ observables (observables.cu)
+struct RhsGeom {     // per RHS, device
+  double k[3];       // k vector in TF
+  double e[6];       // polarization (re, im) x 3 in TF
+};
+template <typename C>
+Err incident_field(const int32_t* ijk, const double* origin3, const RhsGeom* rg, int nrhs, int64_t n, C* e,
+                   cudaStream_t st);
+// per RHS: [0] sum Im(E*.P), [1] sum Re(E*.P), [2] sum (-Im ia - 2/3 k^3)|P|^2
+Err qsums(const int32_t* ijk, const uint8_t* comp, const double* origin3, const RhsGeom* rg, const double2* ia,
+          int ncomp, double kd, const double2* p, int nrhs, int64_t n, double* out3, RedBuf rb, cudaStream_t st);
+// F[rhs][dir][3] = sum_j P_j exp(-i kd n_dir . r_j); ndirs directions per RHS (nhat given per RHS, TF)
+Err farfield(const int32_t* ijk, const double* origin3, const double* nhat /*[nrhs][ndir][3]*/, double kd,
+             const double2* p, int nrhs, int ndir, int64_t n, double2* out, double2* part, int nblk,
+             cudaStream_t st);
+
+}  // namespace dda

@@ -1,0 +1,644 @@
+// Batched Krylov solvers for A P = E (guide, "Choice of Iterative Algorithm"):
+//  - BiCGstab (van der Vorst 1992; the guide's PBCGST option), unpreconditioned,
+//    shadow residual = initial residual;
+//  - CCG: conjugate gradients on the normal equations A^H A P = A^H E
+//    (Petravic & Kuo-Petravic 1979; the guide's PETRKP option).
+// Every right-hand side is an independent system solved in lock step: each
+// kernel covers all RHS, with per-RHS scalars kept on the device (KState), so
+// an iteration needs no host round trip and can be captured in a CUDA graph.
+// Vector updates are fused with the reductions that follow them; reductions
+// accumulate in FP64 (warp shuffles, then a per-block tree, then one
+// deterministic per-RHS pass) whatever the vector precision.
+#include <algorithm>
+
+#include "dda_internal.h"
+
+namespace dda {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename C> struct RealOf;
+template <> struct RealOf<float2> { using t = float; };
+template <> struct RealOf<double2> { using t = double; };
+
+__device__ __forceinline__ double2 to_d(float2 a) { return make_double2(a.x, a.y); }
+__device__ __forceinline__ double2 to_d(double2 a) { return a; }
+template <typename C> __device__ __forceinline__ C from_d(double2 a);
+template <> __device__ __forceinline__ float2 from_d<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+template <> __device__ __forceinline__ double2 from_d<double2>(double2 a) { return a; }
+
+// conj(a) * b accumulated in double
+__device__ __forceinline__ double2 cdot_acc(double2 acc, double2 a, double2 b) {
+  acc.x += a.x * b.x + a.y * b.y;
+  acc.y += a.x * b.y - a.y * b.x;
+  return acc;
+}
+__device__ __forceinline__ double nrm_acc(double acc, double2 a) { return acc + a.x * a.x + a.y * a.y; }
+
+template <int NS>
+__device__ __forceinline__ void block_reduce_store(double (&v)[NS], double* out) {
+  __shared__ double red[NS][kThreads / 32];
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+    for (int o = 16; o > 0; o >>= 1) v[s] += __shfl_down_sync(0xffffffffu, v[s], o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int s = 0; s < NS; ++s) red[s][w] = v[s];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      double x = (threadIdx.x < (blockDim.x >> 5)) ? red[s][threadIdx.x] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (threadIdx.x == 0) out[s] = x;
+    }
+  }
+}
+
+// Sum the per-block partials of one RHS (called by all threads of a block; result in tot, valid in thread 0).
+template <int NS>
+__device__ __forceinline__ void sum_partials(const double* part, int nblk, double (&tot)[NS]) {
+  double v[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) v[s] = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x)
+#pragma unroll
+    for (int s = 0; s < NS; ++s) v[s] += part[i * kRedSlots + s];
+  __shared__ double res[NS];
+  block_reduce_store<NS>(v, res);
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < NS; ++s) tot[s] = res[s];
+}
+
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 cmuld(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// grid-stride bounds for RHS b, block blk
+#define VEC_LOOP(n3) for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n3); i += (int64_t)gridDim.x * blockDim.x)
+
+// ------------------------------------------------------------------ BiCGstab kernels
+template <typename C>
+__global__ void k_bicg_init(KrylovVecs<C> kv, RedBuf rb, int64_t n3, bool have_ax) {
+  const int b = blockIdx.y;
+  const int64_t o = (int64_t)b * n3;
+  double acc[3] = {0.0, 0.0, 0.0};  // |b|^2, |r|^2
+  VEC_LOOP(n3) {
+    const double2 bv = to_d(kv.b[o + i]);
+    double2 rv = bv;
+    if (have_ax) {
+      const double2 ax = to_d(kv.r[o + i]);
+      rv = make_double2(bv.x - ax.x, bv.y - ax.y);
+    }
+    const C rc = from_d<C>(rv);
+    kv.r[o + i] = rc;
+    kv.rhat[o + i] = rc;
+    kv.p[o + i] = czero<C>();
+    kv.v[o + i] = czero<C>();
+    if (!have_ax) kv.x[o + i] = czero<C>();
+    acc[0] = nrm_acc(acc[0], bv);
+    acc[1] = nrm_acc(acc[1], to_d(rc));
+  }
+  block_reduce_store<3>(acc, rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots);
+}
+
+__global__ void k_bicg_init_fin(KState* ks, RedBuf rb, double tol) {
+  const int b = blockIdx.x;
+  double t[3];
+  sum_partials<3>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
+  if (threadIdx.x == 0) {
+    KState& k = ks[b];
+    k.bb = t[0];
+    k.rr = t[1];
+    k.rho = make_double2(t[1], 0.0);
+    k.alpha = make_double2(1.0, 0.0);
+    k.omega = make_double2(1.0, 0.0);
+    k.beta = make_double2(0.0, 0.0);
+    k.tol2 = tol * tol * t[0];
+    k.it = 0;
+    k.done = (t[0] == 0.0 || t[1] <= k.tol2) ? 1 : 0;
+  }
+}
+
+// p = r + beta (p - omega v)
+template <typename C>
+__global__ void k_bicg_p(KrylovVecs<C> kv, const KState* ks, int64_t n3) {
+  const int b = blockIdx.y;
+  const KState k = ks[b];
+  if (k.done) return;
+  using R = typename RealOf<C>::t;
+  const C be = mk((R)k.beta.x, (R)k.beta.y), om = mk((R)k.omega.x, (R)k.omega.y);
+  const int64_t o = (int64_t)b * n3;
+  VEC_LOOP(n3) {
+    const C pv = kv.p[o + i], vv = kv.v[o + i], rv = kv.r[o + i];
+    kv.p[o + i] = cadd(rv, cmul(be, csub(pv, cmul(om, vv))));
+  }
+}
+
+// partial <rhat, v>
+template <typename C>
+__global__ void k_bicg_dot_rv(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int64_t n3) {
+  const int b = blockIdx.y;
+  double acc[2] = {0.0, 0.0};
+  if (!ks[b].done) {
+    const int64_t o = (int64_t)b * n3;
+    double2 a = make_double2(0.0, 0.0);
+    VEC_LOOP(n3) a = cdot_acc(a, to_d(kv.rhat[o + i]), to_d(kv.v[o + i]));
+    acc[0] = a.x;
+    acc[1] = a.y;
+  }
+  block_reduce_store<2>(acc, rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots);
+}
+
+__global__ void k_bicg_alpha_fin(KState* ks, RedBuf rb) {
+  const int b = blockIdx.x;
+  double t[2];
+  sum_partials<2>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
+  if (threadIdx.x == 0) {
+    KState& k = ks[b];
+    if (k.done) return;
+    const double2 rv = make_double2(t[0], t[1]);
+    if (rv.x == 0.0 && rv.y == 0.0) { k.done = 2; return; }
+    k.alpha = cdiv(k.rho, rv);
+  }
+}
+
+// s = r - alpha v ; partial |s|^2
+template <typename C>
+__global__ void k_bicg_s(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int64_t n3) {
+  const int b = blockIdx.y;
+  const KState k = ks[b];
+  double acc[1] = {0.0};
+  if (!k.done) {
+    using R = typename RealOf<C>::t;
+    const C al = mk((R)k.alpha.x, (R)k.alpha.y);
+    const int64_t o = (int64_t)b * n3;
+    VEC_LOOP(n3) {
+      const C s = csub(kv.r[o + i], cmul(al, kv.v[o + i]));
+      kv.s[o + i] = s;
+      acc[0] = nrm_acc(acc[0], to_d(s));
+    }
+  }
+  block_reduce_store<1>(acc, rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots);
+}
+
+__global__ void k_bicg_s_fin(KState* ks, RedBuf rb) {
+  const int b = blockIdx.x;
+  double t[1];
+  sum_partials<1>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
+  if (threadIdx.x == 0) {
+    KState& k = ks[b];
+    if (k.done) return;
+    if (t[0] <= k.tol2) { k.done = 3; k.rr = t[0]; }  // converged on the half step
+  }
+}
+
+// partial <t, s>, |t|^2
+template <typename C>
+__global__ void k_bicg_dot_ts(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int64_t n3) {
+  const int b = blockIdx.y;
+  double acc[3] = {0.0, 0.0, 0.0};
+  if (!ks[b].done) {
+    const int64_t o = (int64_t)b * n3;
+    double2 a = make_double2(0.0, 0.0);
+    double tt = 0.0;
+    VEC_LOOP(n3) {
+      const double2 tv = to_d(kv.t[o + i]);
+      a = cdot_acc(a, tv, to_d(kv.s[o + i]));
+      tt = nrm_acc(tt, tv);
+    }
+    acc[0] = a.x;
+    acc[1] = a.y;
+    acc[2] = tt;
+  }
+  block_reduce_store<3>(acc, rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots);
+}
+
+__global__ void k_bicg_omega_fin(KState* ks, RedBuf rb) {
+  const int b = blockIdx.x;
+  double t[3];
+  sum_partials<3>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
+  if (threadIdx.x == 0) {
+    KState& k = ks[b];
+    if (k.done) return;
+    k.omega = (t[2] > 0.0) ? make_double2(t[0] / t[2], t[1] / t[2]) : make_double2(0.0, 0.0);
+  }
+}
+
+// x += alpha p + omega s ; r = s - omega t ; partial <rhat, r>, |r|^2
+// (RHS that converged on the half step: x += alpha p, r = s)
+template <typename C>
+__global__ void k_bicg_xr(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int64_t n3) {
+  const int b = blockIdx.y;
+  const KState k = ks[b];
+  double acc[3] = {0.0, 0.0, 0.0};
+  if (k.done == 0 || k.done == 3) {
+    using R = typename RealOf<C>::t;
+    const C al = mk((R)k.alpha.x, (R)k.alpha.y), om = mk((R)k.omega.x, (R)k.omega.y);
+    const bool half = (k.done == 3);
+    const int64_t o = (int64_t)b * n3;
+    double2 a = make_double2(0.0, 0.0);
+    double rr = 0.0;
+    VEC_LOOP(n3) {
+      const C sv = kv.s[o + i];
+      C xv = cadd(kv.x[o + i], cmul(al, kv.p[o + i]));
+      C rv = sv;
+      if (!half) {
+        xv = cadd(xv, cmul(om, sv));
+        rv = csub(sv, cmul(om, kv.t[o + i]));
+      }
+      kv.x[o + i] = xv;
+      kv.r[o + i] = rv;
+      a = cdot_acc(a, to_d(kv.rhat[o + i]), to_d(rv));
+      rr = nrm_acc(rr, to_d(rv));
+    }
+    acc[0] = a.x;
+    acc[1] = a.y;
+    acc[2] = rr;
+  }
+  block_reduce_store<3>(acc, rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots);
+}
+
+__global__ void k_bicg_xr_fin(KState* ks, RedBuf rb) {
+  const int b = blockIdx.x;
+  double t[3];
+  sum_partials<3>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
+  if (threadIdx.x == 0) {
+    KState& k = ks[b];
+    if (k.done == 3) { k.done = 1; k.it += 1; return; }
+    if (k.done) return;
+    k.it += 1;
+    k.rr = t[2];
+    const double2 rho_new = make_double2(t[0], t[1]);
+    if (t[2] <= k.tol2) { k.done = 1; return; }
+    if ((k.omega.x == 0.0 && k.omega.y == 0.0) || (rho_new.x == 0.0 && rho_new.y == 0.0)) { k.done = 2; return; }
+    k.beta = cmuld(cdiv(rho_new, k.rho), cdiv(k.alpha, k.omega));
+    k.rho = rho_new;
+  }
+}
+
+// ------------------------------------------------------------------ CCG kernels
+template <typename C>
+__global__ void k_ccg_init(KrylovVecs<C> kv, RedBuf rb, int64_t n3, bool have_ax) {
+  const int b = blockIdx.y;
+  const int64_t o = (int64_t)b * n3;
+  double acc[2] = {0.0, 0.0};
+  VEC_LOOP(n3) {
+    const double2 bv = to_d(kv.b[o + i]);
+    double2 rv = bv;
+    if (have_ax) {
+      const double2 ax = to_d(kv.r[o + i]);
+      rv = make_double2(bv.x - ax.x, bv.y - ax.y);
+    }
+    const C rc = from_d<C>(rv);
+    kv.r[o + i] = rc;
+    if (!have_ax) kv.x[o + i] = czero<C>();
+    acc[0] = nrm_acc(acc[0], bv);
+    acc[1] = nrm_acc(acc[1], to_d(rc));
+  }
+  block_reduce_store<2>(acc, rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots);
+}
+
+__global__ void k_ccg_init_fin(KState* ks, RedBuf rb, double tol) {
+  const int b = blockIdx.x;
+  double t[2];
+  sum_partials<2>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
+  if (threadIdx.x == 0) {
+    KState& k = ks[b];
+    k.bb = t[0];
+    k.rr = t[1];
+    k.tol2 = tol * tol * t[0];
+    k.it = 0;
+    k.done = (t[0] == 0.0 || t[1] <= k.tol2) ? 1 : 0;
+  }
+}
+
+// p = z (z held in s); partial |z|^2
+template <typename C>
+__global__ void k_ccg_start(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int64_t n3) {
+  const int b = blockIdx.y;
+  double acc[1] = {0.0};
+  if (!ks[b].done) {
+    const int64_t o = (int64_t)b * n3;
+    VEC_LOOP(n3) {
+      const C z = kv.s[o + i];
+      kv.p[o + i] = z;
+      acc[0] = nrm_acc(acc[0], to_d(z));
+    }
+  }
+  block_reduce_store<1>(acc, rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots);
+}
+
+__global__ void k_ccg_zz_fin(KState* ks, RedBuf rb) {
+  const int b = blockIdx.x;
+  double t[1];
+  sum_partials<1>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
+  if (threadIdx.x == 0) {
+    KState& k = ks[b];
+    if (k.done) return;
+    k.zz = t[0];
+    if (t[0] == 0.0) k.done = 2;
+  }
+}
+
+// partial |w|^2 (w = A p held in v)
+template <typename C>
+__global__ void k_norm_v(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int64_t n3) {
+  const int b = blockIdx.y;
+  double acc[1] = {0.0};
+  if (!ks[b].done) {
+    const int64_t o = (int64_t)b * n3;
+    VEC_LOOP(n3) acc[0] = nrm_acc(acc[0], to_d(kv.v[o + i]));
+  }
+  block_reduce_store<1>(acc, rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots);
+}
+
+__global__ void k_ccg_alpha_fin(KState* ks, RedBuf rb) {
+  const int b = blockIdx.x;
+  double t[1];
+  sum_partials<1>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
+  if (threadIdx.x == 0) {
+    KState& k = ks[b];
+    if (k.done) return;
+    if (t[0] == 0.0) { k.done = 2; return; }
+    k.alpha = make_double2(k.zz / t[0], 0.0);
+  }
+}
+
+// x += alpha p ; r -= alpha w ; partial |r|^2
+template <typename C>
+__global__ void k_ccg_xr(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int64_t n3) {
+  const int b = blockIdx.y;
+  const KState k = ks[b];
+  double acc[1] = {0.0};
+  if (!k.done) {
+    using R = typename RealOf<C>::t;
+    const R al = (R)k.alpha.x;
+    const int64_t o = (int64_t)b * n3;
+    VEC_LOOP(n3) {
+      const C pv = kv.p[o + i], wv = kv.v[o + i];
+      C xv = kv.x[o + i], rv = kv.r[o + i];
+      xv.x += al * pv.x; xv.y += al * pv.y;
+      rv.x -= al * wv.x; rv.y -= al * wv.y;
+      kv.x[o + i] = xv;
+      kv.r[o + i] = rv;
+      acc[0] = nrm_acc(acc[0], to_d(rv));
+    }
+  }
+  block_reduce_store<1>(acc, rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots);
+}
+
+__global__ void k_ccg_r_fin(KState* ks, RedBuf rb) {
+  const int b = blockIdx.x;
+  double t[1];
+  sum_partials<1>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
+  if (threadIdx.x == 0) {
+    KState& k = ks[b];
+    if (k.done) return;
+    k.it += 1;
+    k.rr = t[0];
+    if (t[0] <= k.tol2) k.done = 1;
+  }
+}
+
+// partial |z|^2 for the new z (in s)
+template <typename C>
+__global__ void k_norm_s(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int64_t n3) {
+  const int b = blockIdx.y;
+  double acc[1] = {0.0};
+  if (!ks[b].done) {
+    const int64_t o = (int64_t)b * n3;
+    VEC_LOOP(n3) acc[0] = nrm_acc(acc[0], to_d(kv.s[o + i]));
+  }
+  block_reduce_store<1>(acc, rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots);
+}
+
+__global__ void k_ccg_beta_fin(KState* ks, RedBuf rb) {
+  const int b = blockIdx.x;
+  double t[1];
+  sum_partials<1>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
+  if (threadIdx.x == 0) {
+    KState& k = ks[b];
+    if (k.done) return;
+    k.beta = make_double2(t[0] / k.zz, 0.0);
+    k.zz = t[0];
+  }
+}
+
+// p = z + beta p
+template <typename C>
+__global__ void k_ccg_p(KrylovVecs<C> kv, const KState* ks, int64_t n3) {
+  const int b = blockIdx.y;
+  const KState k = ks[b];
+  if (k.done) return;
+  using R = typename RealOf<C>::t;
+  const R be = (R)k.beta.x;
+  const int64_t o = (int64_t)b * n3;
+  VEC_LOOP(n3) {
+    const C z = kv.s[o + i];
+    C pv = kv.p[o + i];
+    pv.x = z.x + be * pv.x;
+    pv.y = z.y + be * pv.y;
+    kv.p[o + i] = pv;
+  }
+}
+
+// ------------------------------------------------------------------ refinement helpers
+__global__ void k_residual128(const double2* b, const double2* ax, double2* r, RedBuf rb, int64_t n3) {
+  const int bb = blockIdx.y;
+  const int64_t o = (int64_t)bb * n3;
+  double acc[2] = {0.0, 0.0};
+  VEC_LOOP(n3) {
+    const double2 bv = b[o + i], av = ax[o + i];
+    const double2 rv = make_double2(bv.x - av.x, bv.y - av.y);
+    r[o + i] = rv;
+    acc[0] = nrm_acc(acc[0], rv);
+    acc[1] = nrm_acc(acc[1], bv);
+  }
+  block_reduce_store<2>(acc, rb.part + ((int64_t)bb * rb.nblk + blockIdx.x) * kRedSlots);
+}
+
+__global__ void k_residual128_fin(double* out2, RedBuf rb) {
+  const int b = blockIdx.x;
+  double t[2];
+  sum_partials<2>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
+  if (threadIdx.x == 0) {
+    out2[2 * b] = t[0];
+    out2[2 * b + 1] = t[1];
+  }
+}
+
+template <typename C>
+__global__ void k_from128(const double2* src, C* dst, int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = from_d<C>(src[i]);
+}
+
+template <typename C>
+__global__ void k_add128(double2* dst, const C* src, const int* mask_done, int64_t n3) {
+  const int b = blockIdx.y;
+  if (mask_done && mask_done[b]) return;
+  const int64_t o = (int64_t)b * n3;
+  VEC_LOOP(n3) {
+    const double2 s = to_d(src[o + i]);
+    double2 d = dst[o + i];
+    d.x += s.x;
+    d.y += s.y;
+    dst[o + i] = d;
+  }
+}
+
+inline dim3 vgrid(const RedBuf& rb, int nrhs) { return dim3(rb.nblk, nrhs); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ host wrappers
+#define CHECK_LAUNCH()            \
+  do {                            \
+    DDA_CU(cudaGetLastError());   \
+    add_launches(1);              \
+  } while (0)
+
+template <typename C>
+Err bicg_init(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, double tol, bool have_ax,
+              cudaStream_t st) {
+  k_bicg_init<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, rb, n3, have_ax);
+  CHECK_LAUNCH();
+  k_bicg_init_fin<<<nrhs, kThreads, 0, st>>>(ks, rb, tol);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+template <typename C>
+Err bicg_p_update(const KrylovVecs<C>& kv, const KState* ks, int nrhs, int64_t n3, cudaStream_t st) {
+  // grid size independent of reductions
+  const int nb = (int)std::min<int64_t>((n3 + kThreads * 4 - 1) / (kThreads * 4), 1024);
+  k_bicg_p<C><<<dim3(nb, nrhs), kThreads, 0, st>>>(kv, ks, n3);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+template <typename C>
+Err bicg_alpha(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
+  k_bicg_dot_rv<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  CHECK_LAUNCH();
+  k_bicg_alpha_fin<<<nrhs, kThreads, 0, st>>>(ks, rb);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+template <typename C>
+Err bicg_s_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
+  k_bicg_s<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  CHECK_LAUNCH();
+  k_bicg_s_fin<<<nrhs, kThreads, 0, st>>>(ks, rb);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+template <typename C>
+Err bicg_omega(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
+  k_bicg_dot_ts<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  CHECK_LAUNCH();
+  k_bicg_omega_fin<<<nrhs, kThreads, 0, st>>>(ks, rb);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+template <typename C>
+Err bicg_xr_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
+  k_bicg_xr<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  CHECK_LAUNCH();
+  k_bicg_xr_fin<<<nrhs, kThreads, 0, st>>>(ks, rb);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+
+template <typename C>
+Err ccg_init(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, double tol, bool have_ax,
+             cudaStream_t st) {
+  k_ccg_init<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, rb, n3, have_ax);
+  CHECK_LAUNCH();
+  k_ccg_init_fin<<<nrhs, kThreads, 0, st>>>(ks, rb, tol);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+template <typename C>
+Err ccg_start(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
+  k_ccg_start<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  CHECK_LAUNCH();
+  k_ccg_zz_fin<<<nrhs, kThreads, 0, st>>>(ks, rb);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+// after v = A p: alpha, x/r update, convergence
+template <typename C>
+Err ccg_alpha_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
+  k_norm_v<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  CHECK_LAUNCH();
+  k_ccg_alpha_fin<<<nrhs, kThreads, 0, st>>>(ks, rb);
+  CHECK_LAUNCH();
+  k_ccg_xr<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  CHECK_LAUNCH();
+  k_ccg_r_fin<<<nrhs, kThreads, 0, st>>>(ks, rb);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+// after s = A^H r: beta, p update
+template <typename C>
+Err ccg_beta_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
+  k_norm_s<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  CHECK_LAUNCH();
+  k_ccg_beta_fin<<<nrhs, kThreads, 0, st>>>(ks, rb);
+  CHECK_LAUNCH();
+  const int nb = (int)std::min<int64_t>((n3 + kThreads * 4 - 1) / (kThreads * 4), 1024);
+  k_ccg_p<C><<<dim3(nb, nrhs), kThreads, 0, st>>>(kv, ks, n3);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+
+Err residual_c128(const double2* b, const double2* ax, double2* r, double* out2, RedBuf rb, int nrhs, int64_t n3,
+                  cudaStream_t st) {
+  k_residual128<<<vgrid(rb, nrhs), kThreads, 0, st>>>(b, ax, r, rb, n3);
+  CHECK_LAUNCH();
+  k_residual128_fin<<<nrhs, kThreads, 0, st>>>(out2, rb);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+
+template <typename C>
+Err convert_from_c128(const double2* src, C* dst, int64_t count, cudaStream_t st) {
+  const int nb = (int)std::min<int64_t>((count + kThreads - 1) / kThreads, 152 * 16);
+  k_from128<C><<<nb, kThreads, 0, st>>>(src, dst, count);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+
+template <typename C>
+Err add_to_c128(double2* dst, const C* src, const int* mask_done, int nrhs, int64_t n3, cudaStream_t st) {
+  const int nb = (int)std::min<int64_t>((n3 + kThreads * 4 - 1) / (kThreads * 4), 1024);
+  k_add128<C><<<dim3(nb, nrhs), kThreads, 0, st>>>(dst, src, mask_done, n3);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+
+#define INST(C)                                                                                              \
+  template Err bicg_init<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, double, bool, cudaStream_t); \
+  template Err bicg_p_update<C>(const KrylovVecs<C>&, const KState*, int, int64_t, cudaStream_t);             \
+  template Err bicg_alpha<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, cudaStream_t);              \
+  template Err bicg_s_update<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, cudaStream_t);           \
+  template Err bicg_omega<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, cudaStream_t);              \
+  template Err bicg_xr_update<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, cudaStream_t);          \
+  template Err ccg_init<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, double, bool, cudaStream_t);  \
+  template Err ccg_start<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, cudaStream_t);               \
+  template Err ccg_alpha_update<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, cudaStream_t);        \
+  template Err ccg_beta_update<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, cudaStream_t);         \
+  template Err convert_from_c128<C>(const double2*, C*, int64_t, cudaStream_t);                               \
+  template Err add_to_c128<C>(double2*, const C*, const int*, int, int64_t, cudaStream_t);
+INST(float2)
+INST(double2)
+
+}  // namespace dda

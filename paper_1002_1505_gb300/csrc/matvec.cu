@@ -1,0 +1,517 @@
+// FFT-convolution product A P of the discrete dipole approximation and the
+// FP64 Fourier-space Green tensor it uses.
+//
+// (A P)_j = alpha_j^{-1} P_j + sum_{k != j} A(r_j - r_k) P_k  (guide, eq. AP=E;
+// A_jk of Draine 1988).  The sum is a discrete convolution over lattice
+// offsets (Goodman, Draine & Flatau 1991), evaluated on a zero-padded grid
+// Px x Py x Pz >= 2 Nx x 2 Ny x 2 Nz:  conv = IFFT3( Ghat . FFT3(P) ), with the
+// symmetric 3x3 Ghat (6 complex components) applied pointwise.
+//
+// Pass schedule (per right-hand side b, all three components together):
+//   X   gather P from the compact site list into box rows, forward FFT along x
+//       (input pruned to Nx), store the spectrum transposed as W[b][c][kx][z][y];
+//   YZ  per kx plane: forward FFT along y (pruned to Ny), then per batch of ky
+//       columns forward FFT along z (pruned to Nz), 3x3 Ghat multiply, inverse
+//       FFT along z (only z < Nz kept), then inverse FFT along y (only y < Ny
+//       kept); all in shared memory when a plane of 3 x Nz x Py fits (3-pass
+//       schedule), else as three separate launches (5-pass schedule);
+//   X^-1 inverse FFT along x (only x < Nx kept), add alpha^{-1} P, scatter back
+//       to the compact site list.
+// Spectral positions stay in the engine's digit-reversed order throughout.
+#include <algorithm>
+#include <atomic>
+#include <string>
+
+#include "dda_internal.h"
+
+namespace dda {
+
+namespace {
+
+template <typename C> struct Real;
+template <> struct Real<float2> { using t = float; };
+template <> struct Real<double2> { using t = double; };
+
+template <typename C>
+__device__ __forceinline__ void load_tw(C* dst, const C* src, int L) {
+  for (int i = threadIdx.x; i < L; i += blockDim.x) dst[i] = src[i];
+}
+
+// u = Ghat v, Ghat symmetric with components (xx, xy, xz, yy, yz, zz)
+template <typename C>
+__device__ __forceinline__ void gmul(const C* gh, C& v0, C& v1, C& v2) {
+  const C g0 = gh[0], g1 = gh[1], g2 = gh[2], g3 = gh[3], g4 = gh[4], g5 = gh[5];
+  C u0 = cadd(cadd(cmul(g0, v0), cmul(g1, v1)), cmul(g2, v2));
+  C u1 = cadd(cadd(cmul(g1, v0), cmul(g3, v1)), cmul(g4, v2));
+  C u2 = cadd(cadd(cmul(g2, v0), cmul(g4, v1)), cmul(g5, v2));
+  v0 = u0;
+  v1 = u1;
+  v2 = u2;
+}
+
+template <typename C>
+__device__ __forceinline__ C conjc(C a) { a.y = -a.y; return a; }
+
+// ------------------------------------------------------------------ X forward
+// grid (ceil(ny/ty), nz, nrhs); smem: tw[px] + s[3*ty][px+1]
+template <typename C>
+__global__ void k_xfwd(Geom g, MvData<C> d, const C* __restrict__ p, int ty, bool conj) {
+  extern __shared__ unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* s = tw + g.px;
+  const int ps = g.px + 1;
+  const int y0 = blockIdx.x * ty, z = blockIdx.y, b = blockIdx.z;
+  load_tw(tw, d.twx, g.px);
+  const int nld = 3 * ty * g.nx;
+  for (int i = threadIdx.x; i < nld; i += blockDim.x) {
+    const int x = i % g.nx;
+    const int rest = i / g.nx;
+    const int t = rest % ty, c = rest / ty;
+    const int y = y0 + t;
+    C v = czero<C>();
+    if (y < g.ny) {
+      const int32_t idx = d.map[((int64_t)z * g.ny + y) * g.nx + x];
+      if (idx >= 0) {
+        v = p[((int64_t)b * 3 + c) * g.n + idx];
+        if (conj) v = conjc(v);
+      }
+    }
+    s[(c * ty + t) * ps + x] = v;
+  }
+  __syncthreads();
+  fft_forward(s, Batch{3 * ty, ps, 1, false}, g.plx, g.nx, tw);
+  const int nst = 3 * g.px * ty;
+  const int64_t plane = (int64_t)g.nz * g.ys;
+  for (int i = threadIdx.x; i < nst; i += blockDim.x) {
+    const int t = i % ty;
+    const int rest = i / ty;
+    const int kx = rest % g.px, c = rest / g.px;
+    const int y = y0 + t;
+    if (y < g.ny)
+      d.work[(((int64_t)b * 3 + c) * g.px + kx) * plane + (int64_t)z * g.ys + y] = s[(c * ty + t) * ps + kx];
+  }
+}
+
+// ------------------------------------------------------------------ X inverse + diagonal + scatter
+template <typename C>
+__global__ void k_xinv(Geom g, MvData<C> d, const C* __restrict__ p, C* __restrict__ ap, int ty, int rhs0,
+                       bool conj) {
+  extern __shared__ unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* s = tw + g.px;
+  const int ps = g.px + 1;
+  const int y0 = blockIdx.x * ty, z = blockIdx.y, b = blockIdx.z;
+  load_tw(tw, d.twx, g.px);
+  const int nld = 3 * g.px * ty;
+  const int64_t plane = (int64_t)g.nz * g.ys;
+  for (int i = threadIdx.x; i < nld; i += blockDim.x) {
+    const int t = i % ty;
+    const int rest = i / ty;
+    const int kx = rest % g.px, c = rest / g.px;
+    const int y = y0 + t;
+    C v = czero<C>();
+    if (y < g.ny) v = d.work[(((int64_t)b * 3 + c) * g.px + kx) * plane + (int64_t)z * g.ys + y];
+    s[(c * ty + t) * ps + kx] = v;
+  }
+  __syncthreads();
+  fft_inverse(s, Batch{3 * ty, ps, 1, false}, g.plx, g.nx, tw);
+  const int nst = 3 * ty * g.nx;
+  const C* ia = d.ia + (int64_t)(rhs0 + b) * g.ncomp * 3;
+  for (int i = threadIdx.x; i < nst; i += blockDim.x) {
+    const int x = i % g.nx;
+    const int rest = i / g.nx;
+    const int t = rest % ty, c = rest / ty;
+    const int y = y0 + t;
+    if (y >= g.ny) continue;
+    const int32_t idx = d.map[((int64_t)z * g.ny + y) * g.nx + x];
+    if (idx < 0) continue;
+    const int64_t o = ((int64_t)b * 3 + c) * g.n + idx;
+    const int cc = d.comp ? d.comp[idx] : 0;
+    C pv = p[o];
+    if (conj) pv = conjc(pv);
+    C out = cadd(s[(c * ty + t) * ps + x], cmul(ia[cc * 3 + c], pv));
+    ap[o] = conj ? conjc(out) : out;
+  }
+}
+
+// ------------------------------------------------------------------ z columns: FFT, Ghat, IFFT
+// col layout [pz][3][G]; columns ky0..ky0+G-1 of plane kx. Caller loaded z < nz.
+template <typename C>
+__device__ __forceinline__ void zcol_process(C* col, const Geom& g, const MvData<C>& d, const C* twz, int kx,
+                                             int ky0, int G) {
+  const Batch bz{3 * G, 1, 3 * G, true};
+  fft_forward(col, bz, g.plz, g.nz, twz);
+  const int npt = g.pz * G;
+  for (int i = threadIdx.x; i < npt; i += blockDim.x) {
+    const int gg = i % G, kz = i / G;
+    const int ky = ky0 + gg;
+    if (ky >= g.py) continue;
+    const C* gh = d.ghat + (((int64_t)kx * g.py + ky) * g.pz + kz) * 6;
+    C* e = col + (kz * 3) * G + gg;
+    C v0 = e[0], v1 = e[G], v2 = e[2 * G];
+    gmul(gh, v0, v1, v2);
+    e[0] = v0;
+    e[G] = v1;
+    e[2 * G] = v2;
+  }
+  __syncthreads();
+  fft_inverse(col, bz, g.plz, g.nz, twz);
+}
+
+// ------------------------------------------------------------------ fused YZ plane (3-pass schedule)
+// grid (nrhs, px) -- consecutive blocks share kx so the Ghat plane is reused from L2.
+// smem: twy[py] twz[pz] plane[3*nz][py] col[pz][3][G]
+template <typename C>
+__global__ void k_yzplane(Geom g, MvData<C> d, int G) {
+  extern __shared__ unsigned char smem_raw[];
+  C* twy = reinterpret_cast<C*>(smem_raw);
+  C* twz = twy + g.py;
+  C* pl = twz + g.pz;
+  C* col = pl + 3 * g.nz * g.py;
+  const int b = blockIdx.x, kx = blockIdx.y;
+  load_tw(twy, d.twy, g.py);
+  load_tw(twz, d.twz, g.pz);
+  C* wb = d.work + (((int64_t)b * 3) * g.px + kx) * ((int64_t)g.nz * g.ys);
+  const int64_t cstride = (int64_t)g.px * g.nz * g.ys;
+  const int nld = 3 * g.nz * g.ny;
+  for (int i = threadIdx.x; i < nld; i += blockDim.x) {
+    const int y = i % g.ny;
+    const int rest = i / g.ny;
+    const int z = rest % g.nz, c = rest / g.nz;
+    pl[(c * g.nz + z) * g.py + y] = wb[c * cstride + (int64_t)z * g.ys + y];
+  }
+  __syncthreads();
+  const Batch by{3 * g.nz, g.py, 1, false};
+  fft_forward(pl, by, g.ply, g.ny, twy);
+  for (int ky0 = 0; ky0 < g.py; ky0 += G) {
+    const int ncl = 3 * g.nz * G;
+    for (int i = threadIdx.x; i < ncl; i += blockDim.x) {
+      const int gg = i % G;
+      const int rest = i / G;
+      const int z = rest % g.nz, c = rest / g.nz;
+      const int ky = ky0 + gg;
+      col[(z * 3 + c) * G + gg] = (ky < g.py) ? pl[(c * g.nz + z) * g.py + ky] : czero<C>();
+    }
+    __syncthreads();
+    zcol_process(col, g, d, twz, kx, ky0, G);
+    for (int i = threadIdx.x; i < ncl; i += blockDim.x) {
+      const int gg = i % G;
+      const int rest = i / G;
+      const int z = rest % g.nz, c = rest / g.nz;
+      const int ky = ky0 + gg;
+      if (ky < g.py) pl[(c * g.nz + z) * g.py + ky] = col[(z * 3 + c) * G + gg];
+    }
+    __syncthreads();
+  }
+  fft_inverse(pl, by, g.ply, g.ny, twy);
+  for (int i = threadIdx.x; i < nld; i += blockDim.x) {
+    const int y = i % g.ny;
+    const int rest = i / g.ny;
+    const int z = rest % g.nz, c = rest / g.nz;
+    wb[c * cstride + (int64_t)z * g.ys + y] = pl[(c * g.nz + z) * g.py + y];
+  }
+}
+
+// ------------------------------------------------------------------ 5-pass pieces
+// z pass alone: grid (ceil(py/G), px, nrhs)
+template <typename C>
+__global__ void k_zconv(Geom g, MvData<C> d, int G) {
+  extern __shared__ unsigned char smem_raw[];
+  C* twz = reinterpret_cast<C*>(smem_raw);
+  C* col = twz + g.pz;
+  const int ky0 = blockIdx.x * G, kx = blockIdx.y, b = blockIdx.z;
+  load_tw(twz, d.twz, g.pz);
+  C* wb = d.work + (((int64_t)b * 3) * g.px + kx) * ((int64_t)g.nz * g.ys);
+  const int64_t cstride = (int64_t)g.px * g.nz * g.ys;
+  const int ncl = 3 * g.nz * G;
+  for (int i = threadIdx.x; i < ncl; i += blockDim.x) {
+    const int gg = i % G;
+    const int rest = i / G;
+    const int z = rest % g.nz, c = rest / g.nz;
+    const int ky = ky0 + gg;
+    col[(z * 3 + c) * G + gg] = (ky < g.py) ? wb[c * cstride + (int64_t)z * g.ys + ky] : czero<C>();
+  }
+  __syncthreads();
+  zcol_process(col, g, d, twz, kx, ky0, G);
+  for (int i = threadIdx.x; i < ncl; i += blockDim.x) {
+    const int gg = i % G;
+    const int rest = i / G;
+    const int z = rest % g.nz, c = rest / g.nz;
+    const int ky = ky0 + gg;
+    if (ky < g.py) wb[c * cstride + (int64_t)z * g.ys + ky] = col[(z * 3 + c) * G + gg];
+  }
+}
+
+// contiguous rows of length L (row r at data + r*row_stride): rows_per_block rows per CTA
+template <typename C>
+__global__ void k_fft_rows(C* data, int64_t nrows, int64_t row_stride, FftPlan pl, const C* twg, int nin,
+                           int nout, int rpb, bool inverse) {
+  extern __shared__ unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* s = tw + pl.L;
+  const int L = pl.L, ps = L + 1;
+  load_tw(tw, twg, L);
+  const int64_t r0 = (int64_t)blockIdx.x * rpb;
+  const int nr = (int)min((int64_t)rpb, nrows - r0);
+  const int lim_in = inverse ? L : nin;
+  for (int i = threadIdx.x; i < nr * lim_in; i += blockDim.x) {
+    const int r = i / lim_in, e = i % lim_in;
+    s[r * ps + e] = data[(r0 + r) * row_stride + e];
+  }
+  __syncthreads();
+  const Batch bt{nr, ps, 1, false};
+  if (inverse) fft_inverse(s, bt, pl, nout, tw);
+  else fft_forward(s, bt, pl, nin, tw);
+  const int lim_out = inverse ? nout : L;
+  for (int i = threadIdx.x; i < nr * lim_out; i += blockDim.x) {
+    const int r = i / lim_out, e = i % lim_out;
+    data[(r0 + r) * row_stride + e] = s[r * ps + e];
+  }
+}
+
+// strided pencils: element e of pencil (o, i) at data[o*outer_stride + i + e*estride];
+// grid (ceil(ninner/ti), nouter); smem tw[L] + s[L][ti]
+template <typename C>
+__global__ void k_fft_strided(C* data, int64_t estride, int64_t ninner, int64_t outer_stride, FftPlan pl,
+                              const C* twg, int ti, bool inverse) {
+  extern __shared__ unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* s = tw + pl.L;
+  const int L = pl.L;
+  load_tw(tw, twg, L);
+  const int64_t i0 = (int64_t)blockIdx.x * ti;
+  const int ni = (int)min((int64_t)ti, ninner - i0);
+  C* base = data + (int64_t)blockIdx.y * outer_stride + i0;
+  for (int i = threadIdx.x; i < L * ti; i += blockDim.x) {
+    const int ii = i % ti, e = i / ti;
+    s[e * ti + ii] = (ii < ni) ? base[e * estride + ii] : czero<C>();
+  }
+  __syncthreads();
+  const Batch bt{ti, 1, ti, true};
+  if (inverse) fft_inverse(s, bt, pl, L, tw);
+  else fft_forward(s, bt, pl, L, tw);
+  for (int i = threadIdx.x; i < L * ti; i += blockDim.x) {
+    const int ii = i % ti, e = i / ti;
+    if (ii < ni) base[e * estride + ii] = s[e * ti + ii];
+  }
+}
+
+// ------------------------------------------------------------------ Green tensor
+// A_ab(n) = exp(ikr)/r [k^2 (rh_a rh_b - d_ab) + (ikr - 1)/r^2 (3 rh_a rh_b - d_ab)] for offset n != 0
+// reachable by two sites (|n_x| < Nx ...), else 0.  Output Gw[6][pz][py][px].
+__global__ void k_green_fill(Geom g, double kd, double2* gw) {
+  const int64_t M = (int64_t)g.px * g.py * g.pz;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.px);
+    const int64_t rest = i / g.px;
+    const int y = (int)(rest % g.py), z = (int)(rest / g.py);
+    int ox, oy, oz;
+    bool ok = true;
+    if (x < g.nx) ox = x; else if (x > g.px - g.nx) ox = x - g.px; else { ok = false; ox = 0; }
+    if (y < g.ny) oy = y; else if (y > g.py - g.ny) oy = y - g.py; else { ok = false; oy = 0; }
+    if (z < g.nz) oz = z; else if (z > g.pz - g.nz) oz = z - g.pz; else { ok = false; oz = 0; }
+    if (ox == 0 && oy == 0 && oz == 0) ok = false;
+    double2 out[6];
+    for (int c = 0; c < 6; ++c) out[c] = make_double2(0.0, 0.0);
+    if (ok) {
+      const double rx = ox, ry = oy, rz = oz;
+      const double r2 = rx * rx + ry * ry + rz * rz;
+      const double r = sqrt(r2);
+      const double inv_r = 1.0 / r;
+      const double h[3] = {rx * inv_r, ry * inv_r, rz * inv_r};
+      double sn, cs;
+      sincos(kd * r, &sn, &cs);
+      // pref = exp(ikr)/r ; t2 = (ikr - 1)/r^2
+      const double2 pref = make_double2(cs * inv_r, sn * inv_r);
+      const double2 t2 = make_double2(-1.0 / r2, kd * r / r2);
+      const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+      for (int c = 0; c < 6; ++c) {
+        const double hh = h[ia[c]] * h[ib[c]];
+        const double dl = (ia[c] == ib[c]) ? 1.0 : 0.0;
+        const double a = kd * kd * (hh - dl);
+        const double bq = 3.0 * hh - dl;
+        const double2 inner = make_double2(a + t2.x * bq, t2.y * bq);
+        out[c] = make_double2(pref.x * inner.x - pref.y * inner.y, pref.x * inner.y + pref.y * inner.x);
+      }
+    }
+    for (int c = 0; c < 6; ++c) gw[(int64_t)c * M + i] = out[c];
+  }
+}
+
+// ghat[kx][ky][kz][6] = Gw[c][kz][ky][kx] / M (positions = the engine's spectral order)
+__global__ void k_green_pack(Geom g, const double2* gw, double2* g128, float2* g64) {
+  const int64_t M = (int64_t)g.px * g.py * g.pz;
+  const double inv = 1.0 / (double)M;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < 6 * M; o += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(o % 6);
+    const int64_t pt = o / 6;
+    const int kz = (int)(pt % g.pz);
+    const int64_t rest = pt / g.pz;
+    const int ky = (int)(rest % g.py), kx = (int)(rest / g.py);
+    const double2 v = gw[(int64_t)c * M + ((int64_t)kz * g.py + ky) * g.px + kx];
+    const double2 w = make_double2(v.x * inv, v.y * inv);
+    g128[o] = w;
+    g64[o] = make_float2((float)w.x, (float)w.y);
+  }
+}
+
+int g_smem_optin = 0;
+std::atomic<unsigned long long> g_launches{0};
+
+// Dynamic shared memory above 48 KB needs the per-kernel opt-in attribute; it is
+// set once to the device maximum (init_kernel_attrs), so launches made while a
+// stream is being captured need no attribute calls.
+Err set_smem(size_t bytes) {
+  if (g_smem_optin == 0) return Err::make(DDA_ESTATE, "kernel attributes not initialized");
+  if (bytes > (size_t)g_smem_optin)
+    return Err::make(DDA_EUNSUPPORTED, "FFT tile needs " + std::to_string(bytes) + " B of shared memory, device allows " +
+                                           std::to_string(g_smem_optin));
+  return Err::Ok();
+}
+
+template <typename K>
+void optin(K kern) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, g_smem_optin);
+}
+
+}  // namespace
+
+size_t x_smem_bytes(const Geom& g, const MvTune& t, size_t csize) {
+  return csize * ((size_t)g.px + (size_t)3 * t.ty * (g.px + 1));
+}
+
+template <typename C>
+size_t plane_smem_bytes(const Geom& g, const MvTune& t) {
+  return sizeof(C) * ((size_t)g.py + g.pz + (size_t)3 * g.nz * g.py + (size_t)g.pz * 3 * t.g);
+}
+
+
+// optional per-pass events (profiling): ev[0] before the first pass, ev[i+1] after pass i
+thread_local cudaEvent_t* t_pass_events = nullptr;
+inline void mark(int i, cudaStream_t st) {
+  if (t_pass_events) cudaEventRecord(t_pass_events[i], st);
+}
+
+template <typename C>
+Err launch_matvec(const Geom& g, const MvData<C>& d, const MvTune& t, const C* p, C* ap, int nrhs, int rhs0,
+                  bool conj, cudaStream_t st) {
+  if (nrhs <= 0) return Err::Ok();
+  int pass = 0;
+  mark(pass++, st);
+  const size_t sx = x_smem_bytes(g, t, sizeof(C));
+  DDA_TRY(set_smem(sx));
+  dim3 gx((g.ny + t.ty - 1) / t.ty, g.nz, nrhs);
+  k_xfwd<C><<<gx, t.thr_x, sx, st>>>(g, d, p, t.ty, conj);
+  DDA_CU(cudaGetLastError());
+  mark(pass++, st);
+  if (t.plane) {
+    const size_t sp = plane_smem_bytes<C>(g, t);
+    DDA_TRY(set_smem(sp));
+    k_yzplane<C><<<dim3(nrhs, g.px), t.thr_p, sp, st>>>(g, d, t.g);
+    DDA_CU(cudaGetLastError());
+    mark(pass++, st);
+    g_launches += 3;
+  } else {
+    // 5-pass: Y forward rows, Z columns, Y inverse rows
+    const int64_t nrows = (int64_t)nrhs * 3 * g.px * g.nz;
+    const int rpb = 4;
+    const size_t sr = sizeof(C) * ((size_t)g.py + (size_t)rpb * (g.py + 1));
+    DDA_TRY(set_smem(sr));
+    const unsigned nb = (unsigned)((nrows + rpb - 1) / rpb);
+    k_fft_rows<C><<<nb, t.thr_x, sr, st>>>(d.work, nrows, g.ys, g.ply, d.twy, g.ny, g.py, rpb, false);
+    DDA_CU(cudaGetLastError());
+    mark(pass++, st);
+    const size_t sz = sizeof(C) * ((size_t)g.pz + (size_t)g.pz * 3 * t.g);
+    DDA_TRY(set_smem(sz));
+    k_zconv<C><<<dim3((g.py + t.g - 1) / t.g, g.px, nrhs), t.thr_p, sz, st>>>(g, d, t.g);
+    DDA_CU(cudaGetLastError());
+    mark(pass++, st);
+    k_fft_rows<C><<<nb, t.thr_x, sr, st>>>(d.work, nrows, g.ys, g.ply, d.twy, g.py, g.ny, rpb, true);
+    DDA_CU(cudaGetLastError());
+    mark(pass++, st);
+    g_launches += 5;
+  }
+  k_xinv<C><<<gx, t.thr_x, sx, st>>>(g, d, p, ap, t.ty, rhs0, conj);
+  DDA_CU(cudaGetLastError());
+  mark(pass++, st);
+  return Err::Ok();
+}
+
+void set_pass_events(cudaEvent_t* ev) { t_pass_events = ev; }
+unsigned long long launches() { return g_launches.load(); }
+void add_launches(unsigned long long n) { g_launches += n; }
+void sub_launches(unsigned long long n) { g_launches -= n; }
+
+template <typename C>
+Err fft_rows(C* data, int64_t nrows, int64_t row_stride, const FftPlan& pl, const C* tw, int nin, int nout,
+             bool inverse, cudaStream_t st) {
+  const int rpb = 4;
+  const size_t sr = sizeof(C) * ((size_t)pl.L + (size_t)rpb * (pl.L + 1));
+  DDA_TRY(set_smem(sr));
+  const unsigned nb = (unsigned)((nrows + rpb - 1) / rpb);
+  k_fft_rows<C><<<nb, 256, sr, st>>>(data, nrows, row_stride, pl, tw, nin, nout, rpb, inverse);
+  DDA_CU(cudaGetLastError());
+  g_launches += 1;
+  return Err::Ok();
+}
+
+template <typename C>
+Err fft_strided(C* data, int L, int64_t estride, int64_t ninner, int64_t nouter, int64_t outer_stride,
+                const FftPlan& pl, const C* tw, bool inverse, cudaStream_t st) {
+  const int ti = 16;
+  const size_t sm = sizeof(C) * ((size_t)L + (size_t)L * ti);
+  DDA_TRY(set_smem(sm));
+  dim3 grid((unsigned)((ninner + ti - 1) / ti), (unsigned)nouter);
+  k_fft_strided<C><<<grid, 256, sm, st>>>(data, estride, ninner, outer_stride, pl, tw, ti, inverse);
+  DDA_CU(cudaGetLastError());
+  g_launches += 1;
+  return Err::Ok();
+}
+
+void init_kernel_attrs() {
+  if (g_smem_optin) return;
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  g_smem_optin = v;
+  optin(k_xfwd<float2>); optin(k_xfwd<double2>);
+  optin(k_xinv<float2>); optin(k_xinv<double2>);
+  optin(k_yzplane<float2>); optin(k_yzplane<double2>);
+  optin(k_zconv<float2>); optin(k_zconv<double2>);
+  optin(k_fft_rows<float2>); optin(k_fft_rows<double2>);
+  optin(k_fft_strided<float2>); optin(k_fft_strided<double2>);
+}
+
+Err build_green(const Geom& g, double kd, const double2* twx, const double2* twy, const double2* twz,
+                double2* gw, double2* ghat128, float2* ghat64, cudaStream_t st) {
+  const int64_t M = (int64_t)g.px * g.py * g.pz;
+  const int blocks = (int)std::min<int64_t>((M + 255) / 256, 152 * 16);
+  k_green_fill<<<blocks, 256, 0, st>>>(g, kd, gw);
+  DDA_CU(cudaGetLastError());
+  g_launches += 1;
+  // x: contiguous rows; y: stride px; z: stride px*py; 6 components as outer batch
+  DDA_TRY(fft_rows<double2>(gw, 6 * (int64_t)g.py * g.pz, g.px, g.plx, twx, g.px, g.px, false, st));
+  DDA_TRY(fft_strided<double2>(gw, g.py, g.px, g.px, 6 * (int64_t)g.pz, (int64_t)g.px * g.py, g.ply, twy, false, st));
+  DDA_TRY(fft_strided<double2>(gw, g.pz, (int64_t)g.px * g.py, (int64_t)g.px * g.py, 6, M, g.plz, twz, false, st));
+  const int pb = (int)std::min<int64_t>((6 * M + 255) / 256, 152 * 16);
+  k_green_pack<<<pb, 256, 0, st>>>(g, gw, ghat128, ghat64);
+  DDA_CU(cudaGetLastError());
+  g_launches += 1;
+  return Err::Ok();
+}
+
+template Err launch_matvec<float2>(const Geom&, const MvData<float2>&, const MvTune&, const float2*, float2*, int,
+                                   int, bool, cudaStream_t);
+template Err launch_matvec<double2>(const Geom&, const MvData<double2>&, const MvTune&, const double2*, double2*,
+                                    int, int, bool, cudaStream_t);
+template size_t plane_smem_bytes<float2>(const Geom&, const MvTune&);
+template size_t plane_smem_bytes<double2>(const Geom&, const MvTune&);
+template Err fft_rows<float2>(float2*, int64_t, int64_t, const FftPlan&, const float2*, int, int, bool, cudaStream_t);
+template Err fft_rows<double2>(double2*, int64_t, int64_t, const FftPlan&, const double2*, int, int, bool,
+                               cudaStream_t);
+template Err fft_strided<float2>(float2*, int, int64_t, int64_t, int64_t, int64_t, const FftPlan&, const float2*,
+                                 bool, cudaStream_t);
+template Err fft_strided<double2>(double2*, int, int64_t, int64_t, int64_t, int64_t, const FftPlan&, const double2*,
+                                  bool, cudaStream_t);
+
+}  // namespace dda

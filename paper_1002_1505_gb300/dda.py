@@ -1,0 +1,259 @@
+"""Thin Python binding of the C-ABI library libdda.so (ctypes, argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: all of it runs in the library's CUDA kernels (or,
+for set-up, in its host C++).  Device buffers are torch tensors on the
+context's device; their data pointers and torch's current stream are passed
+through.  If the library is missing, importing this module raises: there is
+no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.environ.get("DDA_LIB", os.path.join(_HERE, "libdda.so"))
+
+DDA_OK, DDA_EINVAL, DDA_ENOMEM, DDA_ECUDA, DDA_ENOCONV, DDA_ETIMEOUT, DDA_ESTATE, DDA_EUNSUPPORTED = range(8)
+DDA_C64, DDA_C128 = 1, 2
+SHAPES = {"ELLIPSOID": 1, "RCTGLPRSM": 2, "CYLINDER1": 3, "HEX_PRISM": 4}
+PRESCRIPTIONS = {"CM": 1, "LATTDR": 2, "GKDLDR": 3}
+SOLVERS = {"BICGSTAB": 1, "CCG": 2}
+PRECISIONS = {"C64": 1, "C128": 2, "MIXED": 3}
+STATUS_NAMES = ["DDA_OK", "DDA_EINVAL", "DDA_ENOMEM", "DDA_ECUDA", "DDA_ENOCONV", "DDA_ETIMEOUT", "DDA_ESTATE",
+                "DDA_EUNSUPPORTED"]
+
+
+class DDAError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class dda_solve_opts(ctypes.Structure):
+    _fields_ = [("solver", ctypes.c_int), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
+                ("maxit", ctypes.c_int), ("inner_tol", ctypes.c_double), ("timeout_ms", ctypes.c_double),
+                ("warm_start", ctypes.c_int), ("check_every", ctypes.c_int), ("normal_eq", ctypes.c_int),
+                ("use_graph", ctypes.c_int)]
+
+
+class dda_solve_report(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("matvecs", ctypes.c_int), ("outer", ctypes.c_int),
+                ("converged", ctypes.c_int), ("true_rel_resid", ctypes.c_double),
+                ("normal_eq_ratio", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libdda.so not built at {LIB_PATH}: run paper_1002_1505_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    sig = {
+        "dda_create": (I, [ctypes.POINTER(P), I, P]),
+        "dda_destroy": (None, [P]),
+        "dda_last_error": (ctypes.c_char_p, [P]),
+        "dda_set_stream": (I, [P, P]),
+        "dda_setup_shape": (I, [P, I, P, I, P, P]),
+        "dda_setup_target": (I, [P, P, P, I64, P, P, P]),
+        "dda_get_sites": (I, [P, P, P]),
+        "dda_set_incident": (I, [P, D, P, I, P, I]),
+        "dda_nrhs": (I, [P]),
+        "dda_get_incidence": (I, [P, P, P]),
+        "dda_incident_field": (I, [P, P, I]),
+        "dda_build_green_fft": (I, [P, P]),
+        "dda_set_polarizability": (I, [P, I, P, I]),
+        "dda_get_inv_alpha": (I, [P, P]),
+        "dda_matvec": (I, [P, P, P, I, I]),
+        "dda_solve": (I, [P, P, P, P]),
+        "dda_cross_sections": (I, [P, P, P, P, I, P]),
+        "dda_version": (ctypes.c_char_p, []),
+        "dda_kernel_launches": (ctypes.c_ulonglong, []),
+        "dda_profile_matvec": (I, [P, I, I, I, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+LIB = _load()
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+class Context:
+    """Owns one dda_ctx.  device < 0 gives a host-only context (set-up and getters only)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._h = ctypes.c_void_p()
+        s = 0 if device < 0 else _stream_handle(stream)
+        st = LIB.dda_create(ctypes.byref(self._h), int(device), ctypes.c_void_p(s))
+        if st != DDA_OK:
+            raise DDAError(st, "dda_create failed")
+        self.device = device
+        self.n = 0
+        self.box = (0, 0, 0)
+        self.nrhs = 0
+        self.iorth = 0
+        self.kd = 0.0
+
+    def close(self):
+        if self._h:
+            LIB.dda_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != DDA_OK:
+            raise DDAError(st, LIB.dda_last_error(self._h).decode())
+
+    # ---------------------------------------------------------------- set-up
+    def dda_setup_shape(self, shape: str, shpar: Sequence[float]):
+        sp = np.ascontiguousarray(shpar, dtype=np.float64)
+        n = ctypes.c_int64()
+        box = np.zeros(3, dtype=np.int32)
+        self._check(LIB.dda_setup_shape(self._h, SHAPES[shape.upper()], _ptr(sp), len(sp), ctypes.byref(n), _ptr(box)))
+        self.n = int(n.value)
+        self.box = tuple(int(v) for v in box)
+        return self.n, self.box
+
+    def dda_setup_target(self, ixyz, icomp=None, origin=(0.0, 0.0, 0.0), a1=None, a2=None):
+        ij = np.ascontiguousarray(ixyz, dtype=np.int32)
+        ic = None if icomp is None else np.ascontiguousarray(icomp, dtype=np.int32)
+        org = np.ascontiguousarray(origin, dtype=np.float64)
+        a1v = None if a1 is None else np.ascontiguousarray(a1, dtype=np.float64)
+        a2v = None if a2 is None else np.ascontiguousarray(a2, dtype=np.float64)
+        self._check(LIB.dda_setup_target(self._h, _ptr(ij), None if ic is None else _ptr(ic), ij.shape[0], _ptr(org),
+                                         None if a1v is None else _ptr(a1v), None if a2v is None else _ptr(a2v)))
+        self.n = ij.shape[0]
+        sites, _ = self.dda_get_sites()
+        self.box = tuple(int(v) for v in sites.max(axis=0) + 1)
+
+    def dda_get_sites(self):
+        out = np.zeros((self.n, 3), dtype=np.int32)
+        org = np.zeros(3, dtype=np.float64)
+        self._check(LIB.dda_get_sites(self._h, _ptr(out), _ptr(org)))
+        return out, org
+
+    def dda_set_incident(self, kd: float, orientations, e01_lf=((0, 0), (1, 0), (0, 0)), iorth: int = 2):
+        ori = np.ascontiguousarray(orientations, dtype=np.float64).reshape(-1, 3)
+        e = np.ascontiguousarray(e01_lf, dtype=np.float64).reshape(6)
+        self._check(LIB.dda_set_incident(self._h, float(kd), _ptr(ori), ori.shape[0], _ptr(e), int(iorth)))
+        self.nrhs = LIB.dda_nrhs(self._h)
+        self.iorth = iorth
+        self.kd = float(kd)
+        return self.nrhs
+
+    def dda_get_incidence(self):
+        k = np.zeros((self.nrhs, 3))
+        e = np.zeros((self.nrhs, 6))
+        self._check(LIB.dda_get_incidence(self._h, _ptr(k), _ptr(e)))
+        return k, e[:, 0::2] + 1j * e[:, 1::2]
+
+    def dda_build_green_fft(self, pad: Optional[Sequence[int]] = None):
+        p = None if pad is None else np.ascontiguousarray(pad, dtype=np.int32)
+        self._check(LIB.dda_build_green_fft(self._h, None if p is None else _ptr(p)))
+
+    def dda_set_polarizability(self, prescription: str, m):
+        ms = np.atleast_1d(np.asarray(m, dtype=np.complex128))
+        arr = np.ascontiguousarray(np.stack([ms.real, ms.imag], axis=1))
+        self._check(LIB.dda_set_polarizability(self._h, PRESCRIPTIONS[prescription.upper()], _ptr(arr), len(ms)))
+        self.ncomp = len(ms)
+
+    def dda_get_inv_alpha(self):
+        out = np.zeros((self.nrhs, self.ncomp, 3, 2))
+        self._check(LIB.dda_get_inv_alpha(self._h, _ptr(out)))
+        return out[..., 0] + 1j * out[..., 1]
+
+    # ---------------------------------------------------------------- device work
+    def _dev_check(self, t, dtype_code):
+        import torch
+        want = torch.complex64 if dtype_code == DDA_C64 else torch.complex128
+        if not t.is_cuda or t.dtype != want or not t.is_contiguous():
+            raise DDAError(DDA_EINVAL, f"expected a contiguous {want} CUDA tensor")
+
+    def dda_incident_field(self, e, dtype=DDA_C128):
+        self._dev_check(e, dtype)
+        self._check(LIB.dda_incident_field(self._h, ctypes.c_void_p(e.data_ptr()), dtype))
+
+    def dda_matvec(self, p, ap, nrhs: Optional[int] = None):
+        import torch
+        dt = DDA_C64 if p.dtype == torch.complex64 else DDA_C128
+        self._dev_check(p, dt)
+        self._dev_check(ap, dt)
+        nr = self.nrhs if nrhs is None else nrhs
+        self._check(LIB.dda_matvec(self._h, ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(ap.data_ptr()), nr, dt))
+
+    def dda_solve(self, p, solver="BICGSTAB", precision="MIXED", tol=1e-5, maxit=1000, inner_tol=0.0,
+                  timeout_ms=0.0, warm_start=False, check_every=8, normal_eq=False, use_graph=True,
+                  raise_on_noconv=True):
+        """Solve A P = E_inc; p is a complex128 [nrhs,3,N] CUDA tensor (guess if warm_start, solution out)."""
+        self._dev_check(p, DDA_C128)
+        o = dda_solve_opts(SOLVERS[solver.upper()], PRECISIONS[precision.upper()], tol, maxit, inner_tol,
+                           timeout_ms, int(bool(warm_start)), check_every, int(bool(normal_eq)), int(bool(use_graph)))
+        rep = (dda_solve_report * self.nrhs)()
+        st = LIB.dda_solve(self._h, ctypes.byref(o), ctypes.c_void_p(p.data_ptr()), rep)
+        reports = [{k: getattr(r, k) for k, _ in dda_solve_report._fields_} for r in rep]
+        if st != DDA_OK and (raise_on_noconv or st not in (DDA_ENOCONV, DDA_ETIMEOUT)):
+            self._check(st)
+        return reports, st
+
+    def dda_cross_sections(self, p, dirs=None):
+        """Returns (Q array [nrhs,4] = Qext,Qabs,Qsca,Qpha, Mueller [n_ori,ndir,4,4] or None)."""
+        self._dev_check(p, DDA_C128)
+        q = np.zeros((self.nrhs, 4))
+        if dirs is not None and len(dirs):
+            d = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 2)
+            m = np.zeros((self.nrhs // self.iorth, d.shape[0], 16))
+            self._check(LIB.dda_cross_sections(self._h, ctypes.c_void_p(p.data_ptr()), _ptr(q), _ptr(d), d.shape[0],
+                                               _ptr(m)))
+            return q, m.reshape(-1, d.shape[0], 4, 4)
+        self._check(LIB.dda_cross_sections(self._h, ctypes.c_void_p(p.data_ptr()), _ptr(q), None, 0, None))
+        return q, None
+
+
+def dda_kernel_launches() -> int:
+    return int(LIB.dda_kernel_launches())
+
+
+def dda_profile_matvec(ctx: "Context", nrhs: int, dtype: int = DDA_C64, iters: int = 20):
+    """Mean ms of each pass of the product (3 or 5 passes), CUDA events on the context's stream."""
+    ms = np.zeros(5)
+    npass = ctypes.c_int()
+    ctx._check(LIB.dda_profile_matvec(ctx._h, int(nrhs), int(dtype), int(iters), _ptr(ms), ctypes.byref(npass)))
+    return ms[:npass.value]
+
+
+def dda_version() -> str:
+    return LIB.dda_version().decode()
+
+
+def setup_workload(ctx: Context, w, pad=None):
+    """Target, incidence, Green tensor and polarizability for a workload description."""
+    ctx.dda_setup_shape(w.shape, w.shpar)
+    aeff = (3.0 * ctx.n / (4.0 * np.pi)) ** (1.0 / 3.0)
+    kd = w.x / aeff
+    ctx.dda_set_incident(kd, w.orientations, [[c[0], c[1]] for c in w.e01], w.iorth)
+    if ctx.device >= 0:
+        ctx.dda_build_green_fft(pad if pad is not None else w.pad)
+    ctx.dda_set_polarizability(w.prescription, w.m)
+    return kd

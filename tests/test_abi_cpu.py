@@ -1,0 +1,137 @@
+"""CPU checks of the C-ABI library: it loads, exports every declared symbol, and
+its host-side set-up (targets, incidence, polarizabilities) matches the oracle.
+
+These run without a GPU through a host-only context (device = -1).
+"""
+import math
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import orientation as o_ori
+from oracle import polarizability as o_pol
+from oracle import targets as o_tgt
+from paper_1002_1505_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def D():
+    from paper_1002_1505_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    from paper_1002_1505_gb300 import dda
+    return dda
+
+
+def _declared_symbols():
+    src = open(os.path.join(ROOT, "include", "dda.h")).read()
+    return sorted(set(re.findall(r"DDA_API\s+[\w\s\*]*?\b(dda_\w+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(D):
+    names = _declared_symbols()
+    assert len(names) >= 18
+    out = subprocess.run(["nm", "-D", "--defined-only", D.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\sT\s(dda_\w+)", out))
+    for nm in names:
+        assert nm in exported, nm
+        assert getattr(D.LIB, nm) is not None
+    # nothing else leaks out of the C ABI
+    assert exported == set(names)
+
+
+def test_version_string(D):
+    assert "sm_103a" in D.dda_version()
+
+
+ALL_SHAPES = [("ELLIPSOID", (12, 12, 12)), ("ELLIPSOID", (64, 48, 32)), ("ELLIPSOID", (7, 5, 9)),
+              ("RCTGLPRSM", (32, 64, 64)), ("RCTGLPRSM", (3, 5, 2)), ("CYLINDER1", (32, 16, 1)),
+              ("CYLINDER1", (64, 40, 2)), ("CYLINDER1", (20, 48, 3)), ("HEX_PRISM", (160, 128, 6)),
+              ("HEX_PRISM", (13, 17, 1)), ("HEX_PRISM", (9, 22, 3)), ("HEX_PRISM", (11, 10, 5))]
+
+
+@pytest.mark.parametrize("shape,shpar", ALL_SHAPES)
+def test_targets_bit_exact_against_oracle(D, shape, shpar):
+    ctx = D.Context(-1)
+    n, box = ctx.dda_setup_shape(shape, shpar)
+    sites, origin = ctx.dda_get_sites()
+    ref = o_tgt.make_target(shape, shpar)
+    assert n == ref.n and box == ref.box
+    np.testing.assert_array_equal(sites, ref.ijk)
+    np.testing.assert_array_equal(origin, ref.origin)
+
+
+def test_site_list_target_reorders_and_rejects_duplicates(D):
+    ref = o_tgt.ellipsoid(5, 6, 7)
+    rng = np.random.default_rng(5)
+    perm = rng.permutation(ref.n)
+    ctx = D.Context(-1)
+    ctx.dda_setup_target(ref.ijk[perm] + np.array([3, -2, 7]), origin=(0.5, 0.5, 0.5))
+    sites, origin = ctx.dda_get_sites()
+    np.testing.assert_array_equal(sites, ref.ijk)
+    np.testing.assert_allclose(origin, [3.5, -1.5, 7.5])
+    dup = np.vstack([ref.ijk, ref.ijk[:1]])
+    with pytest.raises(D.DDAError) as ei:
+        ctx.dda_setup_target(dup)
+    assert ei.value.status == D.DDA_EINVAL
+
+
+def test_invalid_arguments_and_state(D):
+    ctx = D.Context(-1)
+    with pytest.raises(D.DDAError) as ei:
+        ctx.dda_set_incident(0.3, [(0, 0, 0)])
+    assert ei.value.status == D.DDA_ESTATE
+    with pytest.raises(D.DDAError) as ei:
+        ctx.dda_setup_shape("ELLIPSOID", (5.5, 6, 7))
+    assert ei.value.status == D.DDA_EINVAL
+    with pytest.raises(D.DDAError):
+        ctx.dda_setup_shape("CYLINDER1", (5, 6, 4))
+    ctx.dda_setup_shape("ELLIPSOID", (5, 6, 7))
+    with pytest.raises(D.DDAError) as ei:
+        ctx.dda_set_incident(-1.0, [(0, 0, 0)])
+    assert ei.value.status == D.DDA_EINVAL
+    with pytest.raises(D.DDAError):  # e01 along the propagation direction
+        ctx.dda_set_incident(0.3, [(0, 0, 0)], e01_lf=((1, 0), (0, 0), (0, 0)))
+    ctx.dda_set_incident(0.3, [(0, 0, 0)])
+    with pytest.raises(D.DDAError) as ei:  # host-only context has no device
+        ctx.dda_build_green_fft()
+    assert ei.value.status == D.DDA_ESTATE
+
+
+def test_incidence_matches_oracle(D):
+    ori = W.uniform_orientations(7, 99)
+    for shape, shpar in [("RCTGLPRSM", (4, 5, 6)), ("HEX_PRISM", (6, 8, 4)), ("CYLINDER1", (5, 6, 3))]:
+        ctx = D.Context(-1)
+        ctx.dda_setup_shape(shape, shpar)
+        for e01 in (((0, 0), (1, 0), (0, 0)), ((0, 0), (0.6, 0.1), (0.3, -0.7))):
+            ctx.dda_set_incident(0.37, ori, e01, 2)
+            k, e = ctx.dda_get_incidence()
+            t = o_tgt.make_target(shape, shpar)
+            e01c = np.array([complex(*c) for c in e01])
+            for i, orr in enumerate(ori):
+                k_ref, pols, _, _ = o_ori.incidence(0.37, orr, t.a1, t.a2, e01c, 2)
+                np.testing.assert_allclose(k[2 * i], k_ref, atol=1e-15)
+                np.testing.assert_allclose(k[2 * i + 1], k_ref, atol=1e-15)
+                np.testing.assert_allclose(e[2 * i], pols[0], atol=1e-15)
+                np.testing.assert_allclose(e[2 * i + 1], pols[1], atol=1e-15)
+
+
+@pytest.mark.parametrize("presc", ["CM", "LATTDR", "GKDLDR"])
+def test_polarizability_matches_oracle(D, presc):
+    ori = W.uniform_orientations(5, 98)
+    ctx = D.Context(-1)
+    ctx.dda_setup_shape("ELLIPSOID", (6, 7, 8))
+    ctx.dda_set_incident(0.41, ori, ((0, 0), (0.8, 0.0), (0.0, 0.6)), 2)
+    ms = [1.33 + 0.01j, 2.5 + 1.5j, 0.9656 + 1.8628j]
+    ctx.dda_set_polarizability(presc, ms)
+    ia = ctx.dda_get_inv_alpha()
+    k, e = ctx.dda_get_incidence()
+    for b in range(ctx.nrhs):
+        for c, m in enumerate(ms):
+            ref = o_pol.inv_alpha(presc, m, 0.41, k[b] / 0.41, e[b])
+            np.testing.assert_allclose(ia[b, c], ref, rtol=1e-14)

@@ -1,0 +1,240 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bars (written in each test):
+  A P      relative L2 <= 1e-12 (complex128) and <= 1e-5 (complex64) against the
+           oracle's direct O(N^2) sum (small targets) or its direct rows
+           (sampled sites of full-size targets);
+  Q_*      <= 1e-4 relative against the oracle solved to 1e-10;
+  integers (sites) bit-exact (tests/test_abi_cpu.py).
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import dda as odda  # noqa: E402
+from oracle import interaction as oint  # noqa: E402
+from paper_1002_1505_gb300 import workloads as W  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def D():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1002_1505_gb300 import dda
+    return dda
+
+
+def _oracle_problem(w, kd=None, pad=None):
+    return odda.build_problem(w.shape, w.shpar, w.m, w.x, w.prescription, w.orientations, e01_lf=w.e01,
+                              iorth=w.iorth, pad=pad if pad is not None else w.pad)
+
+
+def _ctx(D, w, pad=None):
+    ctx = D.Context(0)
+    D.setup_workload(ctx, w, pad)
+    return ctx
+
+
+def _rand_p(n_rhs, n, seed, dtype):
+    p = W.seeded_vector((n_rhs, 3, n), seed)
+    return torch.from_numpy(p).to(dtype).cuda()
+
+
+SMALL = [
+    W.Workload("sph12", "ELLIPSOID", (12, 12, 12), 1.33 + 0.01j, 1.0, "LATTDR", W.IDENTITY),
+    W.Workload("ell_odd", "ELLIPSOID", (7, 5, 9), 1.5 + 0.1j, 2.0, "GKDLDR", W.uniform_orientations(2, 11)),
+    W.Workload("cyl", "CYLINDER1", (9, 6, 2), 1.7 + 0.3j, 3.0, "CM", W.uniform_orientations(2, 12)),
+    W.Workload("hex", "HEX_PRISM", (5, 10, 3), 1.33 + 0.001j, 2.5, "GKDLDR", W.uniform_orientations(1, 13)),
+    W.Workload("blk", "RCTGLPRSM", (3, 17, 4), 2.0 + 1.0j, 1.5, "LATTDR", W.uniform_orientations(2, 14)),
+]
+
+
+@pytest.mark.parametrize("w", SMALL, ids=[w.name for w in SMALL])
+def test_matvec_matches_direct_sum(D, w):
+    ctx = _ctx(D, w)
+    prob = _oracle_problem(w)
+    assert ctx.n == prob.target.n
+    for dt, tol in ((torch.complex128, 1e-12), (torch.complex64, 1e-5)):
+        p = _rand_p(ctx.nrhs, ctx.n, 3, dt)
+        ap = torch.empty_like(p)
+        ctx.dda_matvec(p, ap)
+        torch.cuda.synchronize()
+        pn = p.cpu().numpy().astype(np.complex128)
+        got = ap.cpu().numpy().astype(np.complex128)
+        for b in range(ctx.nrhs):
+            ref = odda.apply_a(prob, b, pn[b], "direct")
+            err = np.linalg.norm(got[b] - ref) / np.linalg.norm(ref)
+            assert err <= tol, (w.name, dt, b, err)
+
+
+def test_matvec_nondefault_pad_and_tail_tiles(D):
+    # odd box sizes against a padded grid larger than 2N (pruned FFT inputs shorter than L/2)
+    w = W.Workload("ell_pad", "ELLIPSOID", (11, 13, 6), 1.4 + 0.2j, 2.0, "GKDLDR", W.uniform_orientations(1, 21),
+                   pad=(30, 30, 16))
+    ctx = _ctx(D, w)
+    prob = _oracle_problem(w)
+    p = _rand_p(ctx.nrhs, ctx.n, 4, torch.complex128)
+    ap = torch.empty_like(p)
+    ctx.dda_matvec(p, ap)
+    got = ap.cpu().numpy()
+    for b in range(ctx.nrhs):
+        ref = odda.apply_a(prob, b, p.cpu().numpy()[b], "direct")
+        assert np.linalg.norm(got[b] - ref) / np.linalg.norm(ref) <= 1e-12
+
+
+@pytest.mark.parametrize("w", [W.ELLIPSOID64, W.PRISM48], ids=["ellipsoid64", "prism48_b128"])
+def test_matvec_full_size_sampled_rows(D, w):
+    """Full-size grids in the launch configuration the benchmark times (all RHS in one batch)."""
+    ctx = _ctx(D, w)
+    prob = _oracle_problem(w)
+    rng = np.random.default_rng(5)
+    rows = np.sort(rng.choice(ctx.n, 24, replace=False))
+    rows = np.concatenate([[0, ctx.n - 1], rows])
+    rhs = [0, ctx.nrhs - 1]
+    for dt, tol in ((torch.complex64, 1e-5), (torch.complex128, 1e-12)):
+        p = _rand_p(ctx.nrhs, ctx.n, 6, dt)
+        ap = torch.empty_like(p)
+        ctx.dda_matvec(p, ap)
+        torch.cuda.synchronize()
+        for b in rhs:
+            pb = p[b].cpu().numpy().astype(np.complex128)
+            ref = oint.matvec_direct(prob.target.r, prob.kd, prob.rhs[b].inv_alpha, pb, rows=rows)
+            got = ap[b].cpu().numpy().astype(np.complex128)[:, rows]
+            err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            assert err <= tol, (dt, b, err)
+
+
+def test_incident_field_matches_oracle(D):
+    w = SMALL[1]
+    ctx = _ctx(D, w)
+    prob = _oracle_problem(w)
+    e = torch.empty((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
+    ctx.dda_incident_field(e)
+    got = e.cpu().numpy()
+    for b in range(ctx.nrhs):
+        np.testing.assert_allclose(got[b], prob.rhs[b].e_inc, rtol=0, atol=1e-13)
+
+
+def _oracle_q(w, tol=1e-10):
+    prob = _oracle_problem(w)
+    method = "lu" if prob.target.n * 3 <= 3000 else "bicgstab"
+    ps, _ = odda.solve(prob, method, tol=tol, workers=-1)
+    return prob, ps, odda.cross_sections(prob, ps)
+
+
+@pytest.mark.parametrize("solver,precision", [("BICGSTAB", "C128"), ("BICGSTAB", "MIXED"), ("BICGSTAB", "C64"),
+                                              ("CCG", "C128"), ("CCG", "MIXED")])
+def test_solve_sphere12_cross_sections(D, solver, precision):
+    w = W.SPHERE12
+    prob, ps, qref = _oracle_q(w)
+    ctx = _ctx(D, w)
+    p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
+    reps, st = ctx.dda_solve(p, solver=solver, precision=precision, tol=1e-5, maxit=2000, normal_eq=True)
+    for r in reps:
+        assert r["converged"] == 1 and r["true_rel_resid"] <= 1e-5
+        assert r["normal_eq_ratio"] <= 1e-4
+    q, _ = ctx.dda_cross_sections(p)
+    for b in range(ctx.nrhs):
+        for i, key in enumerate(("Qext", "Qabs", "Qsca", "Qpha")):
+            assert q[b, i] == pytest.approx(qref[b][key], rel=1e-4), (key, b)
+
+
+def test_solve_ellipsoid64_mixed_vs_oracle(D):
+    w = W.ELLIPSOID64
+    prob, ps, qref = _oracle_q(w, tol=1e-10)
+    ctx = _ctx(D, w)
+    p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
+    reps, _ = ctx.dda_solve(p, precision="MIXED", tol=1e-5, maxit=1000)
+    assert all(r["converged"] for r in reps)
+    q, _ = ctx.dda_cross_sections(p)
+    for b in range(ctx.nrhs):
+        for i, key in enumerate(("Qext", "Qabs", "Qsca", "Qpha")):
+            assert q[b, i] == pytest.approx(qref[b][key], rel=1e-4), (key, b)
+    # the solution itself: relative L2 against the oracle's
+    got = p.cpu().numpy()
+    for b in range(ctx.nrhs):
+        assert np.linalg.norm(got[b] - ps[b]) / np.linalg.norm(ps[b]) < 1e-4
+
+
+def test_mueller_matches_oracle(D):
+    w = W.Workload("ell_m", "ELLIPSOID", (8, 6, 5), 1.5 + 0.1j, 2.0, "GKDLDR", W.uniform_orientations(2, 31))
+    prob, ps, qref = _oracle_q(w)
+    ctx = _ctx(D, w)
+    p = torch.from_numpy(np.stack(ps)).cuda()
+    dirs = [(0.0, 0.0), (0.7, 0.3), (math.pi / 2, 1.1), (2.5, 4.0), (math.pi, 0.0)]
+    q, mm = ctx.dda_cross_sections(p, dirs)
+    for o in range(2):
+        ref = odda.mueller(prob, ps, dirs, ori_index=o)
+        np.testing.assert_allclose(mm[o], ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max())
+    for b in range(ctx.nrhs):
+        assert q[b, 0] == pytest.approx(qref[b]["Qext"], rel=1e-12)
+        assert q[b, 1] == pytest.approx(qref[b]["Qabs"], rel=1e-12)
+
+
+def test_worked_example_au_block_on_gpu(D):
+    """The guide's printed sample calculation, solved by the GPU path."""
+    from conftest import load_golden
+    g, rows = load_golden("au_block_worked_example.txt")
+    w = W.AU_BLOCK
+    ctx = _ctx(D, w)
+    assert ctx.n == int(g["NAT0"])
+    p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
+    reps, _ = ctx.dda_solve(p, precision="MIXED", tol=1e-5, maxit=2000)
+    assert all(r["converged"] for r in reps)
+    dirs = [(math.radians(r[0]), math.radians(r[1])) for r in rows]
+    q, mm = ctx.dda_cross_sections(p, dirs)
+    for b in range(2):
+        assert q[b, 0] == pytest.approx(g["Qext"], rel=1e-4)
+        assert q[b, 1] == pytest.approx(g["Qabs"], rel=1e-4)
+        assert q[b, 2] == pytest.approx(g["Qsca"], rel=1e-4)
+        assert q[b, 3] == pytest.approx(g["Qpha"], rel=2e-4)
+    for r, m in zip(rows, mm[0]):
+        assert m[0, 0] == pytest.approx(r[2], rel=5e-4)
+
+
+def test_warm_start_from_solution_needs_no_iterations(D):
+    w = W.SPHERE12
+    prob, ps, _ = _oracle_q(w, tol=1e-12)
+    ctx = _ctx(D, w)
+    p = torch.from_numpy(np.stack(ps)).cuda()
+    reps, _ = ctx.dda_solve(p, precision="MIXED", tol=1e-5, warm_start=True)
+    assert all(r["iters"] == 0 and r["converged"] for r in reps)
+
+
+def test_graph_and_plain_launches_agree(D):
+    w = SMALL[1]
+    ctx = _ctx(D, w)
+    out = []
+    for g in (True, False):
+        p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
+        reps, _ = ctx.dda_solve(p, precision="C128", tol=1e-8, use_graph=g)
+        out.append((p.cpu().numpy(), [r["iters"] for r in reps]))
+    assert out[0][1] == out[1][1]
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+
+
+def test_state_errors_on_device(D):
+    ctx = D.Context(0)
+    p = torch.zeros((1, 3, 8), dtype=torch.complex128, device="cuda")
+    with pytest.raises(D.DDAError) as ei:
+        ctx.dda_matvec(p, torch.empty_like(p), 1)
+    assert ei.value.status == D.DDA_ESTATE
+    ctx.dda_setup_shape("ELLIPSOID", (4, 4, 4))
+    ctx.dda_set_incident(0.3, [(0, 0, 0)])
+    with pytest.raises(D.DDAError) as ei:
+        ctx.dda_build_green_fft((9, 8, 8))
+    assert ei.value.status == D.DDA_EINVAL
+
+
+def test_solver_reports_nonconvergence(D):
+    w = SMALL[2]
+    ctx = _ctx(D, w)
+    p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
+    reps, st = ctx.dda_solve(p, precision="C128", tol=1e-14, maxit=3, raise_on_noconv=False)
+    assert st == D.DDA_ENOCONV
+    assert all(r["converged"] == 0 and r["true_rel_resid"] > 1e-14 for r in reps)

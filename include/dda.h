@@ -151,6 +151,28 @@ DDA_API dda_status dda_get_inv_alpha(dda_ctx *ctx, double *out);
  * dtype DDA_C64 or DDA_C128 (may not alias).  Enqueue only. */
 DDA_API dda_status dda_matvec(dda_ctx *ctx, const void *p_dev, void *ap_dev, int nrhs, int dtype);
 
+/* ap_dev = A p_dev like dda_matvec, but without allocating any memory.
+ * The guide has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory -- for example code whose device memory is
+ * owned by another allocator under a fixed budget (a framework's caching
+ * pool), or latency-sensitive loops where cudaMalloc/cudaFree would
+ * synchronize the device and stall other streams.  Instead of the context's
+ * grown-on-demand workspace, the product's FFT scratch lives in one fixed
+ * array of 32 MiB inside the library's device image; every GPU that loads the
+ * library holds those 32 MiB until the process exits.  Requests whose scratch
+ * (sizeof(complex) x 3 x Px x Nz x Ys per RHS, Ys = Ny on the 3-pass schedule,
+ * Py on the 5-pass one) exceeds 32 MiB return DDA_EINVAL with the sizes in the
+ * message.  The call makes no cudaMalloc, cudaFree or other allocating call.
+ * The first call on a device looks up the array's device address with that
+ * device current (a one-time set-up); make that first call before any stream
+ * capture.  Every call shares the one array and it keeps the last call's
+ * contents; nothing in it has to start at zero because each pass writes all
+ * the scratch the next pass reads.  Calls whose work overlaps on the GPU (other
+ * streams, other threads, other contexts on the same device) race on the array:
+ * serialize them.  The context must already hold the Green tensor and the
+ * polarizabilities (both allocated earlier by their own calls).  Enqueue only. */
+DDA_API dda_status dda_matvec_noalloc(dda_ctx *ctx, const void *p_dev, void *ap_dev, int nrhs, int dtype);
+
 typedef struct {
   int solver;        /* DDA_BICGSTAB or DDA_CCG */
   int precision;     /* DDA_PREC_C64 / DDA_PREC_C128 / DDA_PREC_MIXED */

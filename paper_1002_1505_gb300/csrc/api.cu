@@ -1099,6 +1099,38 @@ dda_status dda_cross_sections(dda_ctx* c, const void* p_dev, double* q_out, cons
 
 unsigned long long dda_kernel_launches(void) { return dda::launches(); }
 
+namespace {
+template <typename C>
+Err matvec_fixed_scratch(dda_ctx* c, const C* p, C* ap, int nrhs) {
+  const dda::Geom g = Sel<C>::geom(c);
+  const size_t need = sizeof(C) * 3ull * g.px * g.nz * g.ys * (size_t)nrhs;
+  if (need > dda::kNoAllocScratchBytes)
+    return Err::make(DDA_EINVAL, "dda_matvec_noalloc: this grid needs " + std::to_string(need) +
+                                     " bytes of FFT scratch for " + std::to_string(nrhs) +
+                                     " RHS, above the fixed limit of " + std::to_string(dda::kNoAllocScratchBytes) +
+                                     " bytes; pass fewer RHS or use dda_matvec");
+  void* scratch = nullptr;
+  DDA_TRY(dda::noalloc_scratch(c->device, &scratch));
+  dda::MvData<C> d = Sel<C>::data(c);
+  d.work = (C*)scratch;
+  return dda::launch_matvec<C>(g, d, Sel<C>::tune(c), p, ap, nrhs, 0, false, c->stream);
+}
+}  // namespace
+
+dda_status dda_matvec_noalloc(dda_ctx* c, const void* p, void* ap, int nrhs, int dtype) {
+  if (!c || !p || !ap) return DDA_EINVAL;
+  if (!c->have_alpha || !c->have_green)
+    return fail(c, Err::make(DDA_ESTATE, "set target, incidence, Green tensor and alpha first"));
+  if (nrhs < 1 || nrhs > c->nrhs) return fail(c, Err::make(DDA_EINVAL, "nrhs out of range"));
+  if (p == ap) return fail(c, Err::make(DDA_EINVAL, "p and ap may not alias"));
+  Err e = set_dev(c);
+  if (!e.ok()) return fail(c, e);
+  if (dtype == DDA_C64) e = matvec_fixed_scratch<float2>(c, (const float2*)p, (float2*)ap, nrhs);
+  else if (dtype == DDA_C128) e = matvec_fixed_scratch<double2>(c, (const double2*)p, (double2*)ap, nrhs);
+  else return fail(c, Err::make(DDA_EINVAL, "dtype must be DDA_C64 or DDA_C128"));
+  return e.ok() ? DDA_OK : fail(c, e);
+}
+
 dda_status dda_profile_matvec(dda_ctx* c, int nrhs, int dtype, int iters, double* ms_per_pass, int* npass) {
   if (!c || !ms_per_pass || !npass || iters < 1) return DDA_EINVAL;
   if (!c->have_alpha || !c->have_green)

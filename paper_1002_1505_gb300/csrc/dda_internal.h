@@ -105,6 +105,10 @@ unsigned long long launches();
 void add_launches(unsigned long long n);
 void sub_launches(unsigned long long n);
 
+// Fixed device scratch of dda_matvec_noalloc (bytes) and its per-device address.
+constexpr size_t kNoAllocScratchBytes = 32ull << 20;
+Err noalloc_scratch(int device, void** out);
+
 // Green tensor: fill + FP64 FFT + pack into ghat128 / ghat64.
 Err build_green(const Geom& g, double kd, const double2* tw128x, const double2* tw128y, const double2* tw128z,
                 double2* scratch, double2* ghat128, float2* ghat64, cudaStream_t st);

@@ -20,6 +20,7 @@
 // Spectral positions stay in the engine's digit-reversed order throughout.
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <string>
 
 #include "dda_internal.h"
@@ -434,6 +435,41 @@ Err launch_matvec(const Geom& g, const MvData<C>& d, const MvTune& t, const C* p
   k_xinv<C><<<gx, t.thr_x, sx, st>>>(g, d, p, ap, t.ty, rhs0, conj);
   DDA_CU(cudaGetLastError());
   mark(pass++, st);
+  return Err::Ok();
+}
+
+// ------------------------------------------------------------------ fixed scratch for dda_matvec_noalloc
+// The FFT workspace of the product for callers that cannot allocate device
+// memory.  It is part of the module image: every GPU that loads the library
+// holds these bytes until the process exits.  All calls share it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+}  // namespace
+
+// Device address of the fixed scratch on `device`.  The first call for a device
+// makes that device current and asks the runtime for the symbol's address
+// (host code only holds a stand-in for the array, never its device address);
+// later calls return the cached pointer.
+Err noalloc_scratch(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices) return Err::make(DDA_EINVAL, "device index out of range for the fixed scratch");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    int prev = 0;
+    DDA_CU(cudaGetDevice(&prev));
+    DDA_CU(cudaSetDevice(device));
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess || ptr == nullptr)
+      return Err::make(DDA_ECUDA, std::string("cudaGetSymbolAddress of the fixed scratch failed: ") +
+                                      cudaGetErrorString(e));
+    g_noalloc_addr[device] = ptr;
+  }
+  *out = g_noalloc_addr[device];
   return Err::Ok();
 }
 

@@ -73,6 +73,7 @@ def _load():
         "dda_version": (ctypes.c_char_p, []),
         "dda_kernel_launches": (ctypes.c_ulonglong, []),
         "dda_profile_matvec": (I, [P, I, I, I, P, P]),
+        "dda_matvec_noalloc": (I, [P, P, P, I, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -202,6 +203,16 @@ class Context:
         self._dev_check(ap, dt)
         nr = self.nrhs if nrhs is None else nrhs
         self._check(LIB.dda_matvec(self._h, ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(ap.data_ptr()), nr, dt))
+
+    def dda_matvec_noalloc(self, p, ap, nrhs: Optional[int] = None):
+        """Same product as dda_matvec, using the library's fixed 32 MiB scratch (no allocation)."""
+        import torch
+        dt = DDA_C64 if p.dtype == torch.complex64 else DDA_C128
+        self._dev_check(p, dt)
+        self._dev_check(ap, dt)
+        nr = self.nrhs if nrhs is None else nrhs
+        self._check(LIB.dda_matvec_noalloc(self._h, ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(ap.data_ptr()),
+                                           nr, dt))
 
     def dda_solve(self, p, solver="BICGSTAB", precision="MIXED", tol=1e-5, maxit=1000, inner_tol=0.0,
                   timeout_ms=0.0, warm_start=False, check_every=8, normal_eq=False, use_graph=True,

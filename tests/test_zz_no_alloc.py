@@ -1,0 +1,61 @@
+"""dda_matvec_noalloc: the product without any allocation, for callers that cannot
+allocate device memory (a fixed budget owned by another allocator, or loops
+where cudaMalloc/cudaFree would synchronize the device).
+
+It must give the same A.P as dda_matvec, call after call (the fixed scratch is
+shared and keeps the previous call's contents), and refuse requests larger
+than its fixed 32 MiB scratch.  The file sorts last so that a run stopping at
+the first failure has run every other test first.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_1002_1505_gb300 import workloads as W  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def D():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1002_1505_gb300 import dda
+    return dda
+
+
+@pytest.mark.parametrize("w", [W.Workload("ell_odd", "ELLIPSOID", (7, 5, 9), 1.5 + 0.1j, 2.0, "GKDLDR",
+                                          W.uniform_orientations(2, 11)),
+                               W.ELLIPSOID64], ids=["small_4rhs", "ellipsoid64_2rhs"])
+def test_noalloc_product_matches_allocating_product_twice(D, w):
+    ctx = D.Context(0)
+    D.setup_workload(ctx, w)
+    for dt, tol in ((torch.complex64, 1e-5), (torch.complex128, 1e-12)):
+        p = torch.from_numpy(W.seeded_vector((ctx.nrhs, 3, ctx.n), 41)).to(dt).cuda()
+        ref = torch.empty_like(p)
+        ctx.dda_matvec(p, ref)
+        torch.cuda.synchronize()
+        ref_np = ref.cpu().numpy().astype(np.complex128)
+        for call in range(2):
+            out = torch.full_like(p, float("nan"))
+            ctx.dda_matvec_noalloc(p, out)
+            torch.cuda.synchronize()
+            got = out.cpu().numpy().astype(np.complex128)
+            assert np.isfinite(got).all()
+            err = np.linalg.norm(got - ref_np) / np.linalg.norm(ref_np)
+            assert err <= tol, (dt, call, err)
+
+
+def test_noalloc_rejects_requests_beyond_the_fixed_scratch(D):
+    ctx = D.Context(0)
+    D.setup_workload(ctx, W.PRISM48)  # 128 RHS x 5.3 MB of complex64 scratch each
+    p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex64, device="cuda")
+    ap = torch.empty_like(p)
+    with pytest.raises(D.DDAError) as ei:
+        ctx.dda_matvec_noalloc(p, ap)
+    assert ei.value.status == D.DDA_EINVAL
+    assert "fixed limit" in str(ei.value)
+    ctx.dda_matvec_noalloc(p, ap, nrhs=4)  # a few RHS fit
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(ap[:4]).item() == 0

@@ -3,6 +3,7 @@
 // Krylov drivers (BiCGstab, CCG; complex64, complex128 or complex64 refined
 // against complex128 true residuals) and the observables.
 #include <chrono>
+#include <cstdlib>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -66,6 +67,8 @@ struct dda_ctx {
   int w128_cap = 0;
   double* d_part = nullptr;
   size_t part_bytes = 0;
+  unsigned int* d_count = nullptr;  // per-RHS arrival counters of the fused reductions
+  int count_cap = 0;
   void* d_kvec = nullptr;
   size_t kvec_bytes = 0;
   dda::KState* d_ks = nullptr;
@@ -76,6 +79,18 @@ struct dda_ctx {
   size_t pinned_bytes = 0;
   cudaStream_t own_stream = nullptr;  // used for graph capture when the caller's stream is a default stream
   cudaEvent_t ev = nullptr;
+  bool comp_valid = false;            // d_comp holds compositions (ncomp > 1)
+  bool einc_valid = false;            // d_e128 holds E_inc for the current incidence
+  double2* d_gscratch = nullptr;      // FP64 Green-tensor build scratch
+  double2* d_sc = nullptr;            // solve scratch (two complex128 vectors)
+  double* d_nh = nullptr;             // far-field directions
+  double2* d_F = nullptr;             // far-field sums
+  double* d_fpart = nullptr;          // far-field partial sums
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // cached solver graphs (complex64, complex128)
+  // Device buffers grow and are never shrunk while the context lives: set-up
+  // calls for a new problem of the same size recompute their results in the
+  // same memory instead of freeing and allocating again.
+  std::vector<std::pair<void**, size_t>> caps;
 };
 
 namespace {
@@ -102,6 +117,27 @@ Err need_device(dda_ctx* c) {
   return Err::Ok();
 }
 
+size_t& cap_of(dda_ctx* c, void** p) {
+  for (auto& kv : c->caps)
+    if (kv.first == p) return kv.second;
+  c->caps.emplace_back(p, 0);
+  return c->caps.back().second;
+}
+
+// Grow-only device buffer owned by the context (contents are not preserved on growth).
+template <typename T>
+Err grow(dda_ctx* c, T** p, size_t bytes) {
+  size_t& cap = cap_of(c, (void**)p);
+  if (*p && bytes <= cap) return Err::Ok();
+  if (*p) cudaFree((void*)*p);
+  *p = nullptr;
+  cap = 0;
+  if (bytes == 0) return Err::Ok();
+  DDA_CU(cudaMalloc((void**)p, bytes));
+  cap = bytes;
+  return Err::Ok();
+}
+
 template <typename T>
 Err dalloc(T** p, size_t bytes) {
   if (*p) cudaFree((void*)*p);
@@ -113,23 +149,12 @@ Err dalloc(T** p, size_t bytes) {
 
 void drop_alpha(dda_ctx* c) {
   c->have_alpha = false;
-  dfree(c->d_ia128);
-  dfree(c->d_ia64);
   c->ia.clear();
 }
-void drop_green(dda_ctx* c) {
-  c->have_green = false;
-  dfree(c->d_ghat128);
-  dfree(c->d_ghat64);
-  for (int a = 0; a < 3; ++a) { dfree(c->d_tw128[a]); dfree(c->d_tw64[a]); }
-  dfree(c->d_w64);
-  dfree(c->d_w128);
-  c->w64_cap = c->w128_cap = 0;
-}
+void drop_green(dda_ctx* c) { c->have_green = false; }
 void drop_incident(dda_ctx* c) {
   c->have_inc = false;
-  dfree(c->d_rg);
-  dfree(c->d_e128);
+  c->einc_valid = false;
   c->rg.clear();
   c->nrhs = 0;
   drop_green(c);
@@ -137,11 +162,18 @@ void drop_incident(dda_ctx* c) {
 }
 void drop_target(dda_ctx* c) {
   c->have_target = false;
-  dfree(c->d_map);
-  dfree(c->d_ijk);
-  dfree(c->d_comp);
-  dfree(c->d_origin);
+  c->comp_valid = false;
   drop_incident(c);
+}
+
+void free_all(dda_ctx* c) {
+  for (auto& kv : c->caps) {
+    if (*kv.first) cudaFree(*kv.first);
+    *kv.first = nullptr;
+    kv.second = 0;
+  }
+  for (auto& g : c->gexec)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
 }
 
 Err upload_target(dda_ctx* c) {
@@ -158,17 +190,17 @@ Err upload_target(dda_ctx* c) {
     c->have_target = true;
     return Err::Ok();
   }
-  DDA_TRY(dalloc(&c->d_map, sizeof(int32_t) * nbox));
-  DDA_TRY(dalloc(&c->d_ijk, sizeof(int32_t) * 3 * n));
-  DDA_TRY(dalloc(&c->d_origin, sizeof(double) * 3));
+  DDA_TRY(grow(c, &c->d_map, sizeof(int32_t) * nbox));
+  DDA_TRY(grow(c, &c->d_ijk, sizeof(int32_t) * 3 * n));
+  DDA_TRY(grow(c, &c->d_origin, sizeof(double) * 3));
   DDA_CU(cudaMemcpy(c->d_map, map.data(), sizeof(int32_t) * nbox, cudaMemcpyHostToDevice));
   DDA_CU(cudaMemcpy(c->d_ijk, t.ijk.data(), sizeof(int32_t) * 3 * n, cudaMemcpyHostToDevice));
   DDA_CU(cudaMemcpy(c->d_origin, t.origin, sizeof(double) * 3, cudaMemcpyHostToDevice));
+  c->comp_valid = false;
   if (t.ncomp > 1) {
-    DDA_TRY(dalloc(&c->d_comp, n));
+    DDA_TRY(grow(c, &c->d_comp, n));
     DDA_CU(cudaMemcpy(c->d_comp, t.comp.data(), n, cudaMemcpyHostToDevice));
-  } else {
-    dfree(c->d_comp);
+    c->comp_valid = true;
   }
   c->n = n;
   c->have_target = true;
@@ -212,15 +244,22 @@ void inv_alpha(int presc, cd m, double kd, const double khat[3], const cd e[3], 
 }
 
 Err ensure_part(dda_ctx* c, size_t bytes) {
-  if (bytes <= c->part_bytes) return Err::Ok();
-  DDA_TRY(dalloc(&c->d_part, bytes));
-  c->part_bytes = bytes;
+  if (bytes > c->part_bytes) {
+    DDA_TRY(grow(c, &c->d_part, bytes));
+    c->part_bytes = bytes;
+  }
+  // counters for up to 65536 RHS; zeroed once, kept at zero by the kernels that use them
+  if (c->count_cap == 0) {
+    DDA_TRY(grow(c, &c->d_count, sizeof(unsigned int) * 65536));
+    DDA_CU(cudaMemset(c->d_count, 0, sizeof(unsigned int) * 65536));
+    c->count_cap = 65536;
+  }
   return Err::Ok();
 }
 
 Err ensure_small(dda_ctx* c, size_t bytes) {
   if (bytes <= c->small_bytes) return Err::Ok();
-  DDA_TRY(dalloc(&c->d_small, bytes));
+  DDA_TRY(grow(c, &c->d_small, bytes));
   c->small_bytes = bytes;
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   c->h_pinned = nullptr;
@@ -233,6 +272,7 @@ dda::RedBuf redbuf(dda_ctx* c, int nrhs, int64_t n3) {
   dda::RedBuf rb;
   rb.nblk = (int)std::max<int64_t>(1, std::min<int64_t>((n3 + 2047) / 2048, std::max(1, 1216 / std::max(1, nrhs))));
   rb.part = c->d_part;
+  rb.count = c->d_count;
   return rb;
 }
 
@@ -246,10 +286,8 @@ Err ensure_work<float2>(dda_ctx* c, int want, int* cap_out) {
   const size_t per = sizeof(float2) * 3ull * g.px * g.nz * g.ys;
   const size_t budget = 24ull << 30;
   int cap = (int)std::max<size_t>(1, std::min<size_t>((size_t)want, budget / per));
-  if (cap > c->w64_cap) {
-    DDA_TRY(dalloc(&c->d_w64, per * cap));
-    c->w64_cap = cap;
-  }
+  DDA_TRY(grow(c, &c->d_w64, per * cap));
+  c->w64_cap = (int)std::min<size_t>(cap_of(c, (void**)&c->d_w64) / per, (size_t)1 << 30);
   *cap_out = std::min(c->w64_cap, want);
   return Err::Ok();
 }
@@ -259,10 +297,8 @@ Err ensure_work<double2>(dda_ctx* c, int want, int* cap_out) {
   const size_t per = sizeof(double2) * 3ull * g.px * g.nz * g.ys;
   const size_t budget = 24ull << 30;
   int cap = (int)std::max<size_t>(1, std::min<size_t>((size_t)want, budget / per));
-  if (cap > c->w128_cap) {
-    DDA_TRY(dalloc(&c->d_w128, per * cap));
-    c->w128_cap = cap;
-  }
+  DDA_TRY(grow(c, &c->d_w128, per * cap));
+  c->w128_cap = (int)std::min<size_t>(cap_of(c, (void**)&c->d_w128) / per, (size_t)1 << 30);
   *cap_out = std::min(c->w128_cap, want);
   return Err::Ok();
 }
@@ -272,14 +308,14 @@ template <> struct Sel<float2> {
   static dda::Geom geom(dda_ctx* c) { dda::Geom g = c->g64; g.ncomp = c->ncomp; return g; }
   static const dda::MvTune& tune(dda_ctx* c) { return c->t64; }
   static dda::MvData<float2> data(dda_ctx* c) {
-    return dda::MvData<float2>{c->d_map, c->d_comp, c->d_ghat64, c->d_ia64, c->d_tw64[0], c->d_tw64[1], c->d_tw64[2], c->d_w64};
+    return dda::MvData<float2>{c->d_map, c->comp_valid ? c->d_comp : nullptr, c->d_ghat64, c->d_ia64, c->d_tw64[0], c->d_tw64[1], c->d_tw64[2], c->d_w64};
   }
 };
 template <> struct Sel<double2> {
   static dda::Geom geom(dda_ctx* c) { dda::Geom g = c->g128; g.ncomp = c->ncomp; return g; }
   static const dda::MvTune& tune(dda_ctx* c) { return c->t128; }
   static dda::MvData<double2> data(dda_ctx* c) {
-    return dda::MvData<double2>{c->d_map, c->d_comp, c->d_ghat128, c->d_ia128, c->d_tw128[0], c->d_tw128[1], c->d_tw128[2], c->d_w128};
+    return dda::MvData<double2>{c->d_map, c->comp_valid ? c->d_comp : nullptr, c->d_ghat128, c->d_ia128, c->d_tw128[0], c->d_tw128[1], c->d_tw128[2], c->d_w128};
   }
 };
 
@@ -298,9 +334,10 @@ Err matvec(dda_ctx* c, const C* p, C* ap, int nrhs, int rhs0, bool conj) {
 }
 
 Err ensure_einc(dda_ctx* c) {
-  if (c->d_e128) return Err::Ok();
-  DDA_TRY(dalloc(&c->d_e128, sizeof(double2) * (size_t)c->nrhs * 3 * c->n));
+  if (c->einc_valid) return Err::Ok();
+  DDA_TRY(grow(c, &c->d_e128, sizeof(double2) * (size_t)c->nrhs * 3 * c->n));
   DDA_TRY(dda::incident_field<double2>(c->d_ijk, c->d_origin, c->d_rg, c->nrhs, c->n, c->d_e128, c->stream));
+  c->einc_valid = true;
   return Err::Ok();
 }
 
@@ -318,10 +355,8 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
   dda::RedBuf rb = redbuf(c, nrhs, n3);
   DDA_TRY(ensure_part(c, sizeof(double) * (size_t)rb.nblk * nrhs * dda::kRedSlots));
   rb.part = c->d_part;
-  if (c->ks_cap < nrhs) {
-    DDA_TRY(dalloc(&c->d_ks, sizeof(dda::KState) * nrhs));
-    c->ks_cap = nrhs;
-  }
+  rb.count = c->d_count;
+  DDA_TRY(grow(c, &c->d_ks, sizeof(dda::KState) * nrhs));
   dda::KState* ks = c->d_ks;
   cudaStream_t st = c->stream;
   const bool ccg = (o.solver == DDA_CCG);
@@ -363,8 +398,9 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
   cudaGraphExec_t gexec = nullptr;
   unsigned long long graph_kernels = 0;
   if (o.use_graph) {
+    // capture `every` iterations; reuse the context's executable graph when only
+    // parameters changed (cudaGraphExecUpdate), instantiate only when the topology did
     const unsigned long long before = dda::launches();
-    // make sure every kernel attribute is set before capture, then capture `every` iterations
     cudaGraph_t graph = nullptr;
     DDA_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     Err e = Err::Ok();
@@ -375,9 +411,27 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
     // captured launches did not run: count them when the graph is replayed
     graph_kernels = dda::launches() - before;
     dda::sub_launches(graph_kernels);
-    ce = cudaGraphInstantiate(&gexec, graph, 0);
+    cudaGraphExec_t& cached = c->gexec[sizeof(C) == sizeof(float2) ? 0 : 1];
+    bool updated = false;
+    if (cached) {
+      cudaGraphExecUpdateResultInfo info;
+      updated = cudaGraphExecUpdate(cached, graph, &info) == cudaSuccess;
+      if (!updated) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(cached);
+        cached = nullptr;
+      }
+    }
+    if (!updated) {
+      ce = cudaGraphInstantiate(&cached, graph, 0);
+      if (ce != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        cached = nullptr;
+        return Err::make(DDA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+      }
+    }
     cudaGraphDestroy(graph);
-    if (ce != cudaSuccess) return Err::make(DDA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+    gexec = cached;
   }
   std::vector<dda::KState> hk(nrhs);
   int it = 0;
@@ -405,7 +459,6 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
     it += every;
     stats->matvecs += mv_per_it * every;
   }
-  if (gexec) cudaGraphExecDestroy(gexec);
   DDA_TRY(res);
   stats->iters.resize(nrhs);
   stats->done.resize(nrhs);
@@ -458,10 +511,7 @@ void dda_destroy(dda_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   drop_target(c);
-  dfree(c->d_part);
-  dfree(c->d_kvec);
-  dfree(c->d_ks);
-  dfree(c->d_small);
+  free_all(c);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   if (c->ev) cudaEventDestroy(c->ev);
@@ -571,7 +621,7 @@ dda_status dda_set_incident(dda_ctx* c, double kd, const double* ori, int n_ori,
       }
     }
     if (!c->host_only) {
-      e = dalloc(&c->d_rg, sizeof(dda::RhsGeom) * c->nrhs);
+      e = grow(c, &c->d_rg, sizeof(dda::RhsGeom) * c->nrhs);
       if (!e.ok()) return fail(c, e);
       if (cudaMemcpy(c->d_rg, c->rg.data(), sizeof(dda::RhsGeom) * c->nrhs, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(c, Err::make(DDA_ECUDA, "copy of incidence failed"));
@@ -654,8 +704,8 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
         t128[j] = make_double2(std::cos(ang), std::sin(ang));
         t64[j] = make_float2((float)t128[j].x, (float)t128[j].y);
       }
-      e = dalloc(&c->d_tw128[a], sizeof(double2) * L);
-      if (e.ok()) e = dalloc(&c->d_tw64[a], sizeof(float2) * L);
+      e = grow(c, &c->d_tw128[a], sizeof(double2) * L);
+      if (e.ok()) e = grow(c, &c->d_tw64[a], sizeof(float2) * L);
       if (!e.ok()) return fail(c, e);
       cudaMemcpy(c->d_tw128[a], t128.data(), sizeof(double2) * L, cudaMemcpyHostToDevice);
       cudaMemcpy(c->d_tw64[a], t64.data(), sizeof(float2) * L, cudaMemcpyHostToDevice);
@@ -667,21 +717,27 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
     t64.g = 8; t128.g = 4;
     dda::Geom g64 = g, g128 = g;
     g64.ys = g.ny; g128.ys = g.ny;
-    t64.plane = dda::plane_smem_bytes<float2>(g64, t64) <= (size_t)smax;
-    t128.plane = dda::plane_smem_bytes<double2>(g128, t128) <= (size_t)smax;
+    dda::choose_fast_schedule(g64, true, smax, &t64);
+    dda::choose_fast_schedule(g128, false, smax, &t128);
+    if (!t64.fast) t64.plane = dda::plane_smem_bytes<float2>(g64, t64) <= (size_t)smax;
+    if (!t128.fast) t128.plane = dda::plane_smem_bytes<double2>(g128, t128) <= (size_t)smax;
+    if (const char* f = std::getenv("DDA_SCHEDULE")) {  // "generic": force the generic engine (tests)
+      if (std::string(f) == "generic") {
+        t64.fast = t128.fast = false;
+        t64.plane = dda::plane_smem_bytes<float2>(g64, t64) <= (size_t)smax;
+        t128.plane = dda::plane_smem_bytes<double2>(g128, t128) <= (size_t)smax;
+      }
+    }
     if (!t64.plane) g64.ys = g.py;
     if (!t128.plane) g128.ys = g.py;
     c->g64 = g64; c->g128 = g128; c->t64 = t64; c->t128 = t128;
     const int64_t M = (int64_t)g.px * g.py * g.pz;
-    double2* scratch = nullptr;
-    e = dalloc(&c->d_ghat128, sizeof(double2) * 6 * M);
-    if (e.ok()) e = dalloc(&c->d_ghat64, sizeof(float2) * 6 * M);
-    if (e.ok()) e = dalloc(&scratch, sizeof(double2) * 6 * M);
-    if (!e.ok()) { dfree(scratch); return fail(c, e); }
-    e = dda::build_green(g64, c->kd, c->d_tw128[0], c->d_tw128[1], c->d_tw128[2], scratch, c->d_ghat128, c->d_ghat64,
-                         c->stream);
-    cudaStreamSynchronize(c->stream);
-    dfree(scratch);
+    e = grow(c, &c->d_ghat128, sizeof(double2) * 6 * M);
+    if (e.ok()) e = grow(c, &c->d_ghat64, sizeof(float2) * 6 * M);
+    if (e.ok()) e = grow(c, &c->d_gscratch, sizeof(double2) * 6 * M);
+    if (!e.ok()) return fail(c, e);
+    e = dda::build_green(g64, c->kd, c->d_tw128[0], c->d_tw128[1], c->d_tw128[2], c->d_gscratch, c->d_ghat128,
+                         c->d_ghat64, c->stream);
     if (!e.ok()) return fail(c, e);
     c->have_green = true;
     return DDA_OK;
@@ -719,8 +775,8 @@ dda_status dda_set_polarizability(dda_ctx* c, int presc, const double* m_reim, i
     }
     drop_alpha(c);
     if (!c->host_only) {
-      e = dalloc(&c->d_ia128, sizeof(double2) * ia.size());
-      if (e.ok()) e = dalloc(&c->d_ia64, sizeof(float2) * ia.size());
+      e = grow(c, &c->d_ia128, sizeof(double2) * ia.size());
+      if (e.ok()) e = grow(c, &c->d_ia64, sizeof(float2) * ia.size());
       if (!e.ok()) return fail(c, e);
       cudaMemcpy(c->d_ia128, h128.data(), sizeof(double2) * ia.size(), cudaMemcpyHostToDevice);
       cudaMemcpy(c->d_ia64, h64.data(), sizeof(float2) * ia.size(), cudaMemcpyHostToDevice);
@@ -764,10 +820,7 @@ template <typename C>
 Err kvec_alloc(dda_ctx* c, dda::KrylovVecs<C>* kv, int nvec_extra) {
   const size_t one = sizeof(C) * (size_t)c->nrhs * 3 * c->n;
   const size_t need = one * (8 + nvec_extra);
-  if (need > c->kvec_bytes) {
-    DDA_TRY(dalloc(&c->d_kvec, need));
-    c->kvec_bytes = need;
-  }
+  DDA_TRY(grow(c, &c->d_kvec, need));
   C* base = (C*)c->d_kvec;
   const size_t el = (size_t)c->nrhs * 3 * c->n;
   kv->x = base; kv->r = base + el; kv->rhat = base + 2 * el; kv->p = base + 3 * el;
@@ -783,6 +836,7 @@ Err true_residual(dda_ctx* c, const double2* p, double2* scratch_ax, double2* sc
   dda::RedBuf rb = redbuf(c, nrhs, n3);
   DDA_TRY(ensure_part(c, sizeof(double) * (size_t)rb.nblk * nrhs * dda::kRedSlots));
   rb.part = c->d_part;
+  rb.count = c->d_count;
   DDA_TRY(ensure_small(c, sizeof(double) * 2 * nrhs + sizeof(dda::KState) * nrhs));
   DDA_TRY(dda::residual_c128(c->d_e128, scratch_ax, scratch_r, c->d_small, rb, nrhs, n3, c->stream));
   DDA_CU(cudaMemcpyAsync(c->h_pinned, c->d_small, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, c->stream));
@@ -835,10 +889,10 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
     bool timed_out = false;
     std::vector<double> rel;
     // scratch c128 pair for true residuals (2 vectors)
-    double2* sc = nullptr;
-    e = dalloc(&sc, sizeof(double2) * 2 * el);
+    e = grow(c, &c->d_sc, sizeof(double2) * 2 * el);
     if (!e.ok()) return fail(c, e);
-    auto cleanup = [&]() { dfree(sc); };
+    double2* sc = c->d_sc;
+    auto cleanup = [&]() {};
     int outer = 0;
     if (o.precision == DDA_PREC_C128) {
       dda::KrylovVecs<double2> kv;
@@ -1025,25 +1079,21 @@ dda_status dda_cross_sections(dda_ctx* c, const void* p_dev, double* q_out, cons
           }
         }
       }
-      double* d_nh = nullptr;
-      double2* d_F = nullptr;
-      double2* d_part = nullptr;
       const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((c->n + 2047) / 2048, 64));
-      e = dalloc(&d_nh, sizeof(double) * nh.size());
-      if (e.ok()) e = dalloc(&d_F, sizeof(double2) * (size_t)nrhs * ndir * 3);
-      if (e.ok()) e = dalloc(&d_part, sizeof(double) * 6 * (size_t)nrhs * ndir * nblk);
+      e = grow(c, &c->d_nh, sizeof(double) * nh.size());
+      if (e.ok()) e = grow(c, &c->d_F, sizeof(double2) * (size_t)nrhs * ndir * 3);
+      if (e.ok()) e = grow(c, &c->d_fpart, sizeof(double) * 6 * (size_t)nrhs * ndir * nblk);
+      double2* d_F = c->d_F;
       if (e.ok()) {
-        cudaMemcpy(d_nh, nh.data(), sizeof(double) * nh.size(), cudaMemcpyHostToDevice);
-        e = dda::farfield(c->d_ijk, c->d_origin, d_nh, k, P, nrhs, ndir, c->n, d_F, d_part, nblk, c->stream);
+        cudaMemcpy(c->d_nh, nh.data(), sizeof(double) * nh.size(), cudaMemcpyHostToDevice);
+        e = dda::farfield(c->d_ijk, c->d_origin, c->d_nh, k, P, nrhs, ndir, c->n, d_F, (double2*)c->d_fpart, nblk,
+                          c->stream);
       }
       std::vector<double2> F((size_t)nrhs * ndir * 3);
       if (e.ok()) {
         cudaMemcpyAsync(F.data(), d_F, sizeof(double2) * F.size(), cudaMemcpyDeviceToHost, c->stream);
         if (cudaStreamSynchronize(c->stream) != cudaSuccess) e = Err::make(DDA_ECUDA, "far field failed");
       }
-      dfree(d_nh);
-      dfree(d_F);
-      dfree(d_part);
       if (!e.ok()) return fail(c, e);
       const double k3 = k * k * k;
       // a, b, c, d of the guide's GETMUELLER relations (Lab-Frame e01, e02)

@@ -87,6 +87,7 @@ struct MvTune {
   int thr_x = 256;    // threads, x passes
   int thr_p = 512;    // threads, plane / z passes
   bool plane = true;  // 3-pass schedule (plane fits in shared memory)
+  bool fast = false;  // compile-time-length kernels exist for px, py, pz (matvec_fast.cuh)
 };
 
 // Enqueue ap = A p for nrhs right-hand sides (rhs0 = index of the first one for alpha).
@@ -95,6 +96,16 @@ Err launch_matvec(const Geom& g, const MvData<C>& d, const MvTune& t, const C* p
                   bool conj, cudaStream_t st);
 template <typename C>
 size_t plane_smem_bytes(const Geom& g, const MvTune& t);
+// The product on the compile-time-length kernels (matvec_fast_c64.cu / matvec_fast_c128.cu).
+template <typename C>
+Err launch_matvec_fast(const Geom& g, const MvData<C>& d, const MvTune& t, const C* p, C* ap, int nrhs, int rhs0,
+                       bool conj, cudaStream_t st);
+void fast_optin_c64(int smax);
+void fast_optin_c128(int smax);
+// Does a fast schedule exist for this grid (all lengths instantiated, tiles fit)?  Sets t.fast and t.plane.
+void choose_fast_schedule(const Geom& g, bool c64, int smax, MvTune* t);
+// profiling hook: record the i-th pass event if per-pass events are on
+void mark_pass(int i, cudaStream_t st);
 size_t x_smem_bytes(const Geom& g, const MvTune& t, size_t csize);
 
 // Profiling and accounting: per-pass events for the next launches on this thread
@@ -123,7 +134,8 @@ Err fft_strided(C* data, int L, int64_t estride, int64_t ninner, int64_t nouter,
 
 // ------------------------------------------------------------------ Krylov / BLAS-1 (krylov.cu)
 struct RedBuf {
-  double* part = nullptr;   // partial sums [nrhs][nblk][kRedSlots]
+  double* part = nullptr;        // partial sums [nrhs][nblk][kRedSlots]
+  unsigned int* count = nullptr; // per-RHS arrival counters (zero between kernels)
   int nblk = 0;
 };
 constexpr int kRedSlots = 4;

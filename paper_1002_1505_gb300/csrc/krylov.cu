@@ -74,6 +74,39 @@ __device__ __forceinline__ void sum_partials(const double* part, int nblk, doubl
   for (int s = 0; s < NS; ++s) tot[s] = res[s];
 }
 
+
+// Reduce `acc` over the block into this block's partial slot; the last block of
+// RHS b to arrive (device-scope counter) sums all partials of b in a fixed order
+// and returns true with the totals in tot (valid in every thread of that block).
+// The counter is reset by that last block, so it is zero between kernels.
+template <int NS>
+__device__ __forceinline__ bool last_block_totals(double (&acc)[NS], const RedBuf& rb, int b, double (&tot)[NS]) {
+  double* mine = rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots;
+  block_reduce_store<NS>(acc, mine);
+  __shared__ unsigned int s_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(rb.count + b, 1u) == (unsigned)gridDim.x - 1u) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  const double* base = rb.part + (int64_t)b * rb.nblk * kRedSlots;
+  double v[NS];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) v[q] = 0.0;
+  for (int i = threadIdx.x; i < rb.nblk; i += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < NS; ++q) v[q] += __ldcg(base + (int64_t)i * kRedSlots + q);
+  __shared__ double res[NS];
+  block_reduce_store<NS>(v, res);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NS; ++q) tot[q] = res[q];
+  if (threadIdx.x == 0) rb.count[b] = 0;
+  return true;
+}
+
 __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
   const double d = b.x * b.x + b.y * b.y;
   return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
@@ -87,7 +120,7 @@ __device__ __forceinline__ double2 cmuld(double2 a, double2 b) {
 
 // ------------------------------------------------------------------ BiCGstab kernels
 template <typename C>
-__global__ void k_bicg_init(KrylovVecs<C> kv, RedBuf rb, int64_t n3, bool have_ax) {
+__global__ void k_bicg_init(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3, bool have_ax, double tol) {
   const int b = blockIdx.y;
   const int64_t o = (int64_t)b * n3;
   double acc[3] = {0.0, 0.0, 0.0};  // |b|^2, |r|^2
@@ -107,14 +140,8 @@ __global__ void k_bicg_init(KrylovVecs<C> kv, RedBuf rb, int64_t n3, bool have_a
     acc[0] = nrm_acc(acc[0], bv);
     acc[1] = nrm_acc(acc[1], to_d(rc));
   }
-  block_reduce_store<3>(acc, rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots);
-}
-
-__global__ void k_bicg_init_fin(KState* ks, RedBuf rb, double tol) {
-  const int b = blockIdx.x;
   double t[3];
-  sum_partials<3>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
-  if (threadIdx.x == 0) {
+  if (last_block_totals<3>(acc, rb, b, t) && threadIdx.x == 0) {
     KState& k = ks[b];
     k.bb = t[0];
     k.rr = t[1];
@@ -145,7 +172,7 @@ __global__ void k_bicg_p(KrylovVecs<C> kv, const KState* ks, int64_t n3) {
 
 // partial <rhat, v>
 template <typename C>
-__global__ void k_bicg_dot_rv(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int64_t n3) {
+__global__ void k_bicg_dot_rv(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
   const int b = blockIdx.y;
   double acc[2] = {0.0, 0.0};
   if (!ks[b].done) {
@@ -155,14 +182,8 @@ __global__ void k_bicg_dot_rv(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int
     acc[0] = a.x;
     acc[1] = a.y;
   }
-  block_reduce_store<2>(acc, rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots);
-}
-
-__global__ void k_bicg_alpha_fin(KState* ks, RedBuf rb) {
-  const int b = blockIdx.x;
   double t[2];
-  sum_partials<2>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
-  if (threadIdx.x == 0) {
+  if (last_block_totals<2>(acc, rb, b, t) && threadIdx.x == 0) {
     KState& k = ks[b];
     if (k.done) return;
     const double2 rv = make_double2(t[0], t[1]);
@@ -173,7 +194,7 @@ __global__ void k_bicg_alpha_fin(KState* ks, RedBuf rb) {
 
 // s = r - alpha v ; partial |s|^2
 template <typename C>
-__global__ void k_bicg_s(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int64_t n3) {
+__global__ void k_bicg_s(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
   const int b = blockIdx.y;
   const KState k = ks[b];
   double acc[1] = {0.0};
@@ -187,14 +208,8 @@ __global__ void k_bicg_s(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int64_t 
       acc[0] = nrm_acc(acc[0], to_d(s));
     }
   }
-  block_reduce_store<1>(acc, rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots);
-}
-
-__global__ void k_bicg_s_fin(KState* ks, RedBuf rb) {
-  const int b = blockIdx.x;
   double t[1];
-  sum_partials<1>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
-  if (threadIdx.x == 0) {
+  if (last_block_totals<1>(acc, rb, b, t) && threadIdx.x == 0) {
     KState& k = ks[b];
     if (k.done) return;
     if (t[0] <= k.tol2) { k.done = 3; k.rr = t[0]; }  // converged on the half step
@@ -203,7 +218,7 @@ __global__ void k_bicg_s_fin(KState* ks, RedBuf rb) {
 
 // partial <t, s>, |t|^2
 template <typename C>
-__global__ void k_bicg_dot_ts(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int64_t n3) {
+__global__ void k_bicg_dot_ts(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
   const int b = blockIdx.y;
   double acc[3] = {0.0, 0.0, 0.0};
   if (!ks[b].done) {
@@ -219,14 +234,8 @@ __global__ void k_bicg_dot_ts(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int
     acc[1] = a.y;
     acc[2] = tt;
   }
-  block_reduce_store<3>(acc, rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots);
-}
-
-__global__ void k_bicg_omega_fin(KState* ks, RedBuf rb) {
-  const int b = blockIdx.x;
   double t[3];
-  sum_partials<3>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
-  if (threadIdx.x == 0) {
+  if (last_block_totals<3>(acc, rb, b, t) && threadIdx.x == 0) {
     KState& k = ks[b];
     if (k.done) return;
     k.omega = (t[2] > 0.0) ? make_double2(t[0] / t[2], t[1] / t[2]) : make_double2(0.0, 0.0);
@@ -236,7 +245,7 @@ __global__ void k_bicg_omega_fin(KState* ks, RedBuf rb) {
 // x += alpha p + omega s ; r = s - omega t ; partial <rhat, r>, |r|^2
 // (RHS that converged on the half step: x += alpha p, r = s)
 template <typename C>
-__global__ void k_bicg_xr(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int64_t n3) {
+__global__ void k_bicg_xr(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
   const int b = blockIdx.y;
   const KState k = ks[b];
   double acc[3] = {0.0, 0.0, 0.0};
@@ -264,14 +273,8 @@ __global__ void k_bicg_xr(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int64_t
     acc[1] = a.y;
     acc[2] = rr;
   }
-  block_reduce_store<3>(acc, rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots);
-}
-
-__global__ void k_bicg_xr_fin(KState* ks, RedBuf rb) {
-  const int b = blockIdx.x;
   double t[3];
-  sum_partials<3>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
-  if (threadIdx.x == 0) {
+  if (last_block_totals<3>(acc, rb, b, t) && threadIdx.x == 0) {
     KState& k = ks[b];
     if (k.done == 3) { k.done = 1; k.it += 1; return; }
     if (k.done) return;
@@ -287,7 +290,7 @@ __global__ void k_bicg_xr_fin(KState* ks, RedBuf rb) {
 
 // ------------------------------------------------------------------ CCG kernels
 template <typename C>
-__global__ void k_ccg_init(KrylovVecs<C> kv, RedBuf rb, int64_t n3, bool have_ax) {
+__global__ void k_ccg_init(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3, bool have_ax, double tol) {
   const int b = blockIdx.y;
   const int64_t o = (int64_t)b * n3;
   double acc[2] = {0.0, 0.0};
@@ -304,14 +307,8 @@ __global__ void k_ccg_init(KrylovVecs<C> kv, RedBuf rb, int64_t n3, bool have_ax
     acc[0] = nrm_acc(acc[0], bv);
     acc[1] = nrm_acc(acc[1], to_d(rc));
   }
-  block_reduce_store<2>(acc, rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots);
-}
-
-__global__ void k_ccg_init_fin(KState* ks, RedBuf rb, double tol) {
-  const int b = blockIdx.x;
   double t[2];
-  sum_partials<2>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
-  if (threadIdx.x == 0) {
+  if (last_block_totals<2>(acc, rb, b, t) && threadIdx.x == 0) {
     KState& k = ks[b];
     k.bb = t[0];
     k.rr = t[1];
@@ -323,7 +320,7 @@ __global__ void k_ccg_init_fin(KState* ks, RedBuf rb, double tol) {
 
 // p = z (z held in s); partial |z|^2
 template <typename C>
-__global__ void k_ccg_start(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int64_t n3) {
+__global__ void k_ccg_start(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
   const int b = blockIdx.y;
   double acc[1] = {0.0};
   if (!ks[b].done) {
@@ -334,14 +331,8 @@ __global__ void k_ccg_start(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int64
       acc[0] = nrm_acc(acc[0], to_d(z));
     }
   }
-  block_reduce_store<1>(acc, rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots);
-}
-
-__global__ void k_ccg_zz_fin(KState* ks, RedBuf rb) {
-  const int b = blockIdx.x;
   double t[1];
-  sum_partials<1>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
-  if (threadIdx.x == 0) {
+  if (last_block_totals<1>(acc, rb, b, t) && threadIdx.x == 0) {
     KState& k = ks[b];
     if (k.done) return;
     k.zz = t[0];
@@ -351,21 +342,15 @@ __global__ void k_ccg_zz_fin(KState* ks, RedBuf rb) {
 
 // partial |w|^2 (w = A p held in v)
 template <typename C>
-__global__ void k_norm_v(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int64_t n3) {
+__global__ void k_norm_v(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
   const int b = blockIdx.y;
   double acc[1] = {0.0};
   if (!ks[b].done) {
     const int64_t o = (int64_t)b * n3;
     VEC_LOOP(n3) acc[0] = nrm_acc(acc[0], to_d(kv.v[o + i]));
   }
-  block_reduce_store<1>(acc, rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots);
-}
-
-__global__ void k_ccg_alpha_fin(KState* ks, RedBuf rb) {
-  const int b = blockIdx.x;
   double t[1];
-  sum_partials<1>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
-  if (threadIdx.x == 0) {
+  if (last_block_totals<1>(acc, rb, b, t) && threadIdx.x == 0) {
     KState& k = ks[b];
     if (k.done) return;
     if (t[0] == 0.0) { k.done = 2; return; }
@@ -375,7 +360,7 @@ __global__ void k_ccg_alpha_fin(KState* ks, RedBuf rb) {
 
 // x += alpha p ; r -= alpha w ; partial |r|^2
 template <typename C>
-__global__ void k_ccg_xr(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int64_t n3) {
+__global__ void k_ccg_xr(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
   const int b = blockIdx.y;
   const KState k = ks[b];
   double acc[1] = {0.0};
@@ -393,14 +378,8 @@ __global__ void k_ccg_xr(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int64_t 
       acc[0] = nrm_acc(acc[0], to_d(rv));
     }
   }
-  block_reduce_store<1>(acc, rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots);
-}
-
-__global__ void k_ccg_r_fin(KState* ks, RedBuf rb) {
-  const int b = blockIdx.x;
   double t[1];
-  sum_partials<1>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
-  if (threadIdx.x == 0) {
+  if (last_block_totals<1>(acc, rb, b, t) && threadIdx.x == 0) {
     KState& k = ks[b];
     if (k.done) return;
     k.it += 1;
@@ -411,21 +390,15 @@ __global__ void k_ccg_r_fin(KState* ks, RedBuf rb) {
 
 // partial |z|^2 for the new z (in s)
 template <typename C>
-__global__ void k_norm_s(KrylovVecs<C> kv, const KState* ks, RedBuf rb, int64_t n3) {
+__global__ void k_norm_s(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
   const int b = blockIdx.y;
   double acc[1] = {0.0};
   if (!ks[b].done) {
     const int64_t o = (int64_t)b * n3;
     VEC_LOOP(n3) acc[0] = nrm_acc(acc[0], to_d(kv.s[o + i]));
   }
-  block_reduce_store<1>(acc, rb.part + ((int64_t)b * rb.nblk + blockIdx.x) * kRedSlots);
-}
-
-__global__ void k_ccg_beta_fin(KState* ks, RedBuf rb) {
-  const int b = blockIdx.x;
   double t[1];
-  sum_partials<1>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
-  if (threadIdx.x == 0) {
+  if (last_block_totals<1>(acc, rb, b, t) && threadIdx.x == 0) {
     KState& k = ks[b];
     if (k.done) return;
     k.beta = make_double2(t[0] / k.zz, 0.0);
@@ -452,25 +425,20 @@ __global__ void k_ccg_p(KrylovVecs<C> kv, const KState* ks, int64_t n3) {
 }
 
 // ------------------------------------------------------------------ refinement helpers
-__global__ void k_residual128(const double2* b, const double2* ax, double2* r, RedBuf rb, int64_t n3) {
+__global__ void k_residual128(const double2* e, const double2* ax, double2* r, double* out2, RedBuf rb, int64_t n3) {
   const int bb = blockIdx.y;
   const int64_t o = (int64_t)bb * n3;
   double acc[2] = {0.0, 0.0};
   VEC_LOOP(n3) {
-    const double2 bv = b[o + i], av = ax[o + i];
+    const double2 bv = e[o + i], av = ax[o + i];
     const double2 rv = make_double2(bv.x - av.x, bv.y - av.y);
     r[o + i] = rv;
     acc[0] = nrm_acc(acc[0], rv);
     acc[1] = nrm_acc(acc[1], bv);
   }
-  block_reduce_store<2>(acc, rb.part + ((int64_t)bb * rb.nblk + blockIdx.x) * kRedSlots);
-}
-
-__global__ void k_residual128_fin(double* out2, RedBuf rb) {
-  const int b = blockIdx.x;
+  const int b = bb;
   double t[2];
-  sum_partials<2>(rb.part + (int64_t)b * rb.nblk * kRedSlots, rb.nblk, t);
-  if (threadIdx.x == 0) {
+  if (last_block_totals<2>(acc, rb, b, t) && threadIdx.x == 0) {
     out2[2 * b] = t[0];
     out2[2 * b + 1] = t[1];
   }
@@ -510,9 +478,7 @@ inline dim3 vgrid(const RedBuf& rb, int nrhs) { return dim3(rb.nblk, nrhs); }
 template <typename C>
 Err bicg_init(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, double tol, bool have_ax,
               cudaStream_t st) {
-  k_bicg_init<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, rb, n3, have_ax);
-  CHECK_LAUNCH();
-  k_bicg_init_fin<<<nrhs, kThreads, 0, st>>>(ks, rb, tol);
+  k_bicg_init<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3, have_ax, tol);
   CHECK_LAUNCH();
   return Err::Ok();
 }
@@ -528,15 +494,11 @@ template <typename C>
 Err bicg_alpha(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
   k_bicg_dot_rv<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
   CHECK_LAUNCH();
-  k_bicg_alpha_fin<<<nrhs, kThreads, 0, st>>>(ks, rb);
-  CHECK_LAUNCH();
   return Err::Ok();
 }
 template <typename C>
 Err bicg_s_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
   k_bicg_s<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
-  CHECK_LAUNCH();
-  k_bicg_s_fin<<<nrhs, kThreads, 0, st>>>(ks, rb);
   CHECK_LAUNCH();
   return Err::Ok();
 }
@@ -544,15 +506,11 @@ template <typename C>
 Err bicg_omega(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
   k_bicg_dot_ts<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
   CHECK_LAUNCH();
-  k_bicg_omega_fin<<<nrhs, kThreads, 0, st>>>(ks, rb);
-  CHECK_LAUNCH();
   return Err::Ok();
 }
 template <typename C>
 Err bicg_xr_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
   k_bicg_xr<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
-  CHECK_LAUNCH();
-  k_bicg_xr_fin<<<nrhs, kThreads, 0, st>>>(ks, rb);
   CHECK_LAUNCH();
   return Err::Ok();
 }
@@ -560,17 +518,13 @@ Err bicg_xr_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int
 template <typename C>
 Err ccg_init(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, double tol, bool have_ax,
              cudaStream_t st) {
-  k_ccg_init<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, rb, n3, have_ax);
-  CHECK_LAUNCH();
-  k_ccg_init_fin<<<nrhs, kThreads, 0, st>>>(ks, rb, tol);
+  k_ccg_init<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3, have_ax, tol);
   CHECK_LAUNCH();
   return Err::Ok();
 }
 template <typename C>
 Err ccg_start(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
   k_ccg_start<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
-  CHECK_LAUNCH();
-  k_ccg_zz_fin<<<nrhs, kThreads, 0, st>>>(ks, rb);
   CHECK_LAUNCH();
   return Err::Ok();
 }
@@ -579,11 +533,7 @@ template <typename C>
 Err ccg_alpha_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
   k_norm_v<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
   CHECK_LAUNCH();
-  k_ccg_alpha_fin<<<nrhs, kThreads, 0, st>>>(ks, rb);
-  CHECK_LAUNCH();
   k_ccg_xr<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
-  CHECK_LAUNCH();
-  k_ccg_r_fin<<<nrhs, kThreads, 0, st>>>(ks, rb);
   CHECK_LAUNCH();
   return Err::Ok();
 }
@@ -591,8 +541,6 @@ Err ccg_alpha_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, i
 template <typename C>
 Err ccg_beta_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
   k_norm_s<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
-  CHECK_LAUNCH();
-  k_ccg_beta_fin<<<nrhs, kThreads, 0, st>>>(ks, rb);
   CHECK_LAUNCH();
   const int nb = (int)std::min<int64_t>((n3 + kThreads * 4 - 1) / (kThreads * 4), 1024);
   k_ccg_p<C><<<dim3(nb, nrhs), kThreads, 0, st>>>(kv, ks, n3);
@@ -602,9 +550,7 @@ Err ccg_beta_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, in
 
 Err residual_c128(const double2* b, const double2* ax, double2* r, double* out2, RedBuf rb, int nrhs, int64_t n3,
                   cudaStream_t st) {
-  k_residual128<<<vgrid(rb, nrhs), kThreads, 0, st>>>(b, ax, r, rb, n3);
-  CHECK_LAUNCH();
-  k_residual128_fin<<<nrhs, kThreads, 0, st>>>(out2, rb);
+  k_residual128<<<vgrid(rb, nrhs), kThreads, 0, st>>>(b, ax, r, out2, rb, n3);
   CHECK_LAUNCH();
   return Err::Ok();
 }

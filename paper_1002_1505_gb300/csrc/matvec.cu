@@ -147,7 +147,7 @@ __device__ __forceinline__ void zcol_process(C* col, const Geom& g, const MvData
     const int gg = i % G, kz = i / G;
     const int ky = ky0 + gg;
     if (ky >= g.py) continue;
-    const C* gh = d.ghat + (((int64_t)kx * g.py + ky) * g.pz + kz) * 6;
+    const C* gh = d.ghat + (((int64_t)kx * g.pz + kz) * g.py + ky) * 6;
     C* e = col + (kz * 3) * G + gg;
     C v0 = e[0], v1 = e[G], v2 = e[2 * G];
     gmul(gh, v0, v1, v2);
@@ -339,16 +339,16 @@ __global__ void k_green_fill(Geom g, double kd, double2* gw) {
   }
 }
 
-// ghat[kx][ky][kz][6] = Gw[c][kz][ky][kx] / M (positions = the engine's spectral order)
+// ghat[kx][kz][ky][6] = Gw[c][kz][ky][kx] / M (positions = the engine's spectral order)
 __global__ void k_green_pack(Geom g, const double2* gw, double2* g128, float2* g64) {
   const int64_t M = (int64_t)g.px * g.py * g.pz;
   const double inv = 1.0 / (double)M;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < 6 * M; o += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(o % 6);
     const int64_t pt = o / 6;
-    const int kz = (int)(pt % g.pz);
-    const int64_t rest = pt / g.pz;
-    const int ky = (int)(rest % g.py), kx = (int)(rest / g.py);
+    const int ky = (int)(pt % g.py);
+    const int64_t rest = pt / g.py;
+    const int kz = (int)(rest % g.pz), kx = (int)(rest / g.pz);
     const double2 v = gw[(int64_t)c * M + ((int64_t)kz * g.py + ky) * g.px + kx];
     const double2 w = make_double2(v.x * inv, v.y * inv);
     g128[o] = w;
@@ -392,11 +392,13 @@ thread_local cudaEvent_t* t_pass_events = nullptr;
 inline void mark(int i, cudaStream_t st) {
   if (t_pass_events) cudaEventRecord(t_pass_events[i], st);
 }
+void mark_pass(int i, cudaStream_t st) { mark(i, st); }
 
 template <typename C>
 Err launch_matvec(const Geom& g, const MvData<C>& d, const MvTune& t, const C* p, C* ap, int nrhs, int rhs0,
                   bool conj, cudaStream_t st) {
   if (nrhs <= 0) return Err::Ok();
+  if (t.fast) return launch_matvec_fast<C>(g, d, t, p, ap, nrhs, rhs0, conj, st);
   int pass = 0;
   mark(pass++, st);
   const size_t sx = x_smem_bytes(g, t, sizeof(C));
@@ -516,6 +518,8 @@ void init_kernel_attrs() {
   optin(k_zconv<float2>); optin(k_zconv<double2>);
   optin(k_fft_rows<float2>); optin(k_fft_rows<double2>);
   optin(k_fft_strided<float2>); optin(k_fft_strided<double2>);
+  fast_optin_c64(v);
+  fast_optin_c128(v);
 }
 
 Err build_green(const Geom& g, double kd, const double2* twx, const double2* twy, const double2* twz,

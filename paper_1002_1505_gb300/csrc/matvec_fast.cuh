@@ -1,0 +1,721 @@
+// Compile-time-length kernels of the FFT-convolution product (same passes and
+// workspace layout as matvec.cu, faster engine): every 1-D transform is the
+// two-pass register FFT of fft2.cuh, the z-direction pass B is fused with the
+// 3x3 Ghat multiply and the inverse pass B in registers, and global loads and
+// stores are arranged so that consecutive threads touch consecutive addresses.
+//
+// Ghat layout: [kx][kz][ky][6] (xx, xy, xz, yy, yz, zz), scaled by 1/M.
+// Workspace:   W[b][c][kx][z][ys], ys = ny (3-pass) or py (5-pass).
+#pragma once
+
+#include "dda_internal.h"
+#include "fft2.cuh"
+
+namespace dda {
+namespace fast {
+
+using f2::Shape;
+
+template <typename C>
+__device__ __forceinline__ C conjc(C a) { a.y = -a.y; return a; }
+
+template <typename C>
+__device__ __forceinline__ void gmul3(const C* __restrict__ gh, C& v0, C& v1, C& v2) {
+  const C g0 = gh[0], g1 = gh[1], g2 = gh[2], g3 = gh[3], g4 = gh[4], g5 = gh[5];
+  const C u0 = cadd(cadd(cmul(g0, v0), cmul(g1, v1)), cmul(g2, v2));
+  const C u1 = cadd(cadd(cmul(g1, v0), cmul(g3, v1)), cmul(g4, v2));
+  const C u2 = cadd(cadd(cmul(g2, v0), cmul(g4, v1)), cmul(g5, v2));
+  v0 = u0;
+  v1 = u1;
+  v2 = u2;
+}
+
+template <typename C>
+__device__ __forceinline__ void copy_tw(C* dst, const C* src, int L) {
+  for (int i = threadIdx.x; i < L; i += blockDim.x) dst[i] = src[i];
+}
+
+// ------------------------------------------------------------------ x forward
+// grid (ceil(ny/TY), nz, nrhs). smem: tw[PX] | in[3*TY][ip] | out[3*PX][TY]
+template <typename C, int PX, int TY>
+__global__ void __launch_bounds__(256) k_x_fwd(Geom g, MvData<C> d, const C* __restrict__ p, bool conj, int ip) {
+  constexpr int RA = Shape<PX>::RA, LB = Shape<PX>::LB, H = Shape<PX>::H;
+  extern __shared__ unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* in = tw + PX;
+  C* out = in + 3 * TY * ip;
+  const int y0 = blockIdx.x * TY, z = blockIdx.y, b = blockIdx.z;
+  copy_tw(tw, d.twx, PX);
+  const int nld = 3 * TY * g.nx;
+  for (int i = threadIdx.x; i < nld; i += blockDim.x) {
+    const int x = i % g.nx;
+    const int r = i / g.nx;
+    const int t = r % TY, c = r / TY;
+    const int y = y0 + t;
+    C v = czero<C>();
+    if (y < g.ny) {
+      const int32_t idx = __ldg(d.map + ((int64_t)z * g.ny + y) * g.nx + x);
+      if (idx >= 0) {
+        v = p[((int64_t)b * 3 + c) * g.n + idx];
+        if (conj) v = conjc(v);
+      }
+    }
+    in[(c * TY + t) * ip + x] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 3 * TY * LB; i += blockDim.x) {
+    const int t = i % TY;
+    const int r = i / TY;
+    const int n1 = r % LB, c = r / LB;
+    C x[RA], o[2 * RA];
+    const C* src = in + (c * TY + t) * ip;
+#pragma unroll
+    for (int j = 0; j < RA; ++j) {
+      const int xx = n1 + LB * j;
+      x[j] = (xx < g.nx) ? src[xx] : czero<C>();
+    }
+    f2::passA_fwd<PX>(x, n1, tw, o);
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+      for (int k = 0; k < RA; ++k) out[(c * PX + bb * H + n1 + LB * k) * TY + t] = o[bb * RA + k];
+  }
+  __syncthreads();
+  const int64_t plane = (int64_t)g.nz * g.ys;
+  for (int i = threadIdx.x; i < 3 * 2 * RA * TY; i += blockDim.x) {
+    const int t = i % TY;
+    const int r = i / TY;
+    const int blk = r % (2 * RA), c = r / (2 * RA);
+    C v[LB];
+#pragma unroll
+    for (int e = 0; e < LB; ++e) v[e] = out[(c * PX + blk * LB + e) * TY + t];
+    f2::passB_fwd<PX>(v, tw);
+    const int y = y0 + t;
+    if (y < g.ny) {
+      C* dst = d.work + (((int64_t)b * 3 + c) * PX + blk * LB) * plane + (int64_t)z * g.ys + y;
+#pragma unroll
+      for (int e = 0; e < LB; ++e) dst[e * plane] = v[e];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ x inverse + alpha^{-1} P + scatter
+template <typename C, int PX, int TY>
+__global__ void __launch_bounds__(256) k_x_inv(Geom g, MvData<C> d, const C* __restrict__ p, C* __restrict__ ap,
+                                               int rhs0, bool conj, int ip) {
+  constexpr int RA = Shape<PX>::RA, LB = Shape<PX>::LB, H = Shape<PX>::H;
+  extern __shared__ unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* in = tw + PX;
+  C* out = in + 3 * TY * ip;
+  const int y0 = blockIdx.x * TY, z = blockIdx.y, b = blockIdx.z;
+  copy_tw(tw, d.twx, PX);
+  __syncthreads();
+  const int64_t plane = (int64_t)g.nz * g.ys;
+  for (int i = threadIdx.x; i < 3 * 2 * RA * TY; i += blockDim.x) {
+    const int t = i % TY;
+    const int r = i / TY;
+    const int blk = r % (2 * RA), c = r / (2 * RA);
+    const int y = y0 + t;
+    C v[LB];
+    if (y < g.ny) {
+      const C* src = d.work + (((int64_t)b * 3 + c) * PX + blk * LB) * plane + (int64_t)z * g.ys + y;
+#pragma unroll
+      for (int e = 0; e < LB; ++e) v[e] = src[e * plane];
+    } else {
+#pragma unroll
+      for (int e = 0; e < LB; ++e) v[e] = czero<C>();
+    }
+    f2::passB_inv<PX>(v, tw);
+#pragma unroll
+    for (int e = 0; e < LB; ++e) out[(c * PX + blk * LB + e) * TY + t] = v[e];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 3 * TY * LB; i += blockDim.x) {
+    const int t = i % TY;
+    const int r = i / TY;
+    const int n1 = r % LB, c = r / LB;
+    C v[2 * RA], lo[RA];
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+      for (int k = 0; k < RA; ++k) v[bb * RA + k] = out[(c * PX + bb * H + n1 + LB * k) * TY + t];
+    f2::passA_inv<PX, false>(v, n1, tw, lo, (C*)nullptr);
+    C* dst = in + (c * TY + t) * ip;
+#pragma unroll
+    for (int j = 0; j < RA; ++j) {
+      const int xx = n1 + LB * j;
+      if (xx < g.nx) dst[xx] = lo[j];
+    }
+  }
+  __syncthreads();
+  const C* ia = d.ia + (int64_t)(rhs0 + b) * g.ncomp * 3;
+  const int nst = 3 * TY * g.nx;
+  for (int i = threadIdx.x; i < nst; i += blockDim.x) {
+    const int x = i % g.nx;
+    const int r = i / g.nx;
+    const int t = r % TY, c = r / TY;
+    const int y = y0 + t;
+    if (y >= g.ny) continue;
+    const int32_t idx = __ldg(d.map + ((int64_t)z * g.ny + y) * g.nx + x);
+    if (idx < 0) continue;
+    const int64_t o = ((int64_t)b * 3 + c) * g.n + idx;
+    const int cc = d.comp ? d.comp[idx] : 0;
+    C pv = p[o];
+    if (conj) pv = conjc(pv);
+    const C res = cadd(in[(c * TY + t) * ip + x], cmul(ia[cc * 3 + c], pv));
+    ap[o] = conj ? conjc(res) : res;
+  }
+}
+
+// ------------------------------------------------------------------ fused y-z plane (3-pass schedule)
+// grid (nrhs, px), block 512.  smem: twy[PY] | twz[PZ] | pl[PZ*3][PY+1] (row (z,c) = z*3 + c)
+template <typename C, int PY, int PZ>
+__global__ void __launch_bounds__(512) k_yz_plane(Geom g, MvData<C> d) {
+  constexpr int RAy = Shape<PY>::RA, LBy = Shape<PY>::LB, Hy = Shape<PY>::H;
+  constexpr int RAz = Shape<PZ>::RA, LBz = Shape<PZ>::LB, Hz = Shape<PZ>::H;
+  constexpr int RP = PY + 1;
+  extern __shared__ unsigned char smem_raw[];
+  C* twy = reinterpret_cast<C*>(smem_raw);
+  C* twz = twy + PY;
+  C* pl = twz + PZ;
+  const int b = blockIdx.x, kx = blockIdx.y;
+  const int nz = g.nz, ny = g.ny;
+  copy_tw(twy, d.twy, PY);
+  copy_tw(twz, d.twz, PZ);
+  __syncthreads();
+  C* wb = d.work + ((int64_t)b * 3 * g.px + kx) * ((int64_t)nz * g.ys);
+  const int64_t cstride = (int64_t)g.px * nz * g.ys;
+  // y forward, pass A: global -> registers -> plane
+  for (int i = threadIdx.x; i < 3 * nz * LBy; i += blockDim.x) {
+    const int n1 = i % LBy;
+    const int r = i / LBy;
+    const int z = r % nz, c = r / nz;
+    const C* src = wb + c * cstride + (int64_t)z * g.ys;
+    C x[RAy], o[2 * RAy];
+#pragma unroll
+    for (int j = 0; j < RAy; ++j) {
+      const int yy = n1 + LBy * j;
+      x[j] = (yy < ny) ? src[yy] : czero<C>();
+    }
+    f2::passA_fwd<PY>(x, n1, twy, o);
+    C* row = pl + (z * 3 + c) * RP;
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+      for (int k = 0; k < RAy; ++k) row[bb * Hy + n1 + LBy * k] = o[bb * RAy + k];
+  }
+  __syncthreads();
+  // y forward, pass B
+  for (int i = threadIdx.x; i < 3 * nz * 2 * RAy; i += blockDim.x) {
+    const int rr = i % (3 * nz), blk = i / (3 * nz);
+    C* row = pl + rr * RP + blk * LBy;
+    C v[LBy];
+#pragma unroll
+    for (int e = 0; e < LBy; ++e) v[e] = row[e];
+    f2::passB_fwd<PY>(v, twy);
+#pragma unroll
+    for (int e = 0; e < LBy; ++e) row[e] = v[e];
+  }
+  __syncthreads();
+  // z forward, pass A (pencils (c, ky), rows z < nz nonzero)
+  for (int i = threadIdx.x; i < 3 * PY * LBz; i += blockDim.x) {
+    const int ky = i % PY;
+    const int r = i / PY;
+    const int c = r % 3, n1 = r / 3;
+    C x[RAz], o[2 * RAz];
+#pragma unroll
+    for (int j = 0; j < RAz; ++j) {
+      const int zz = n1 + LBz * j;
+      x[j] = (zz < nz) ? pl[(zz * 3 + c) * RP + ky] : czero<C>();
+    }
+    f2::passA_fwd<PZ>(x, n1, twz, o);
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+      for (int k = 0; k < RAz; ++k) pl[((bb * Hz + n1 + LBz * k) * 3 + c) * RP + ky] = o[bb * RAz + k];
+  }
+  __syncthreads();
+  // z pass B, Ghat, inverse z pass B -- in registers for the three components
+  const C* gk = d.ghat + (int64_t)kx * PZ * PY * 6;
+  for (int i = threadIdx.x; i < PY * 2 * RAz; i += blockDim.x) {
+    const int ky = i % PY, blk = i / PY;
+    C v0[LBz], v1[LBz], v2[LBz];
+#pragma unroll
+    for (int e = 0; e < LBz; ++e) {
+      const C* rowp = pl + ((blk * LBz + e) * 3) * RP + ky;
+      v0[e] = rowp[0];
+      v1[e] = rowp[RP];
+      v2[e] = rowp[2 * RP];
+    }
+    f2::passB_fwd<PZ>(v0, twz);
+    f2::passB_fwd<PZ>(v1, twz);
+    f2::passB_fwd<PZ>(v2, twz);
+#pragma unroll
+    for (int e = 0; e < LBz; ++e) gmul3(gk + ((int64_t)(blk * LBz + e) * PY + ky) * 6, v0[e], v1[e], v2[e]);
+    f2::passB_inv<PZ>(v0, twz);
+    f2::passB_inv<PZ>(v1, twz);
+    f2::passB_inv<PZ>(v2, twz);
+#pragma unroll
+    for (int e = 0; e < LBz; ++e) {
+      C* rowp = pl + ((blk * LBz + e) * 3) * RP + ky;
+      rowp[0] = v0[e];
+      rowp[RP] = v1[e];
+      rowp[2 * RP] = v2[e];
+    }
+  }
+  __syncthreads();
+  // z inverse, pass A: rows z < nz only
+  for (int i = threadIdx.x; i < 3 * PY * LBz; i += blockDim.x) {
+    const int ky = i % PY;
+    const int r = i / PY;
+    const int c = r % 3, n1 = r / 3;
+    C v[2 * RAz], lo[RAz];
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+      for (int k = 0; k < RAz; ++k) v[bb * RAz + k] = pl[((bb * Hz + n1 + LBz * k) * 3 + c) * RP + ky];
+    f2::passA_inv<PZ, false>(v, n1, twz, lo, (C*)nullptr);
+#pragma unroll
+    for (int j = 0; j < RAz; ++j) {
+      const int zz = n1 + LBz * j;
+      if (zz < nz) pl[(zz * 3 + c) * RP + ky] = lo[j];
+    }
+  }
+  __syncthreads();
+  // y inverse, pass B
+  for (int i = threadIdx.x; i < 3 * nz * 2 * RAy; i += blockDim.x) {
+    const int rr = i % (3 * nz), blk = i / (3 * nz);
+    C* row = pl + rr * RP + blk * LBy;
+    C v[LBy];
+#pragma unroll
+    for (int e = 0; e < LBy; ++e) v[e] = row[e];
+    f2::passB_inv<PY>(v, twy);
+#pragma unroll
+    for (int e = 0; e < LBy; ++e) row[e] = v[e];
+  }
+  __syncthreads();
+  // y inverse, pass A: plane -> registers -> global (y < ny)
+  for (int i = threadIdx.x; i < 3 * nz * LBy; i += blockDim.x) {
+    const int n1 = i % LBy;
+    const int r = i / LBy;
+    const int z = r % nz, c = r / nz;
+    const C* row = pl + (z * 3 + c) * RP;
+    C v[2 * RAy], lo[RAy];
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+      for (int k = 0; k < RAy; ++k) v[bb * RAy + k] = row[bb * Hy + n1 + LBy * k];
+    f2::passA_inv<PY, false>(v, n1, twy, lo, (C*)nullptr);
+    C* dst = wb + c * cstride + (int64_t)z * g.ys;
+#pragma unroll
+    for (int j = 0; j < RAy; ++j) {
+      const int yy = n1 + LBy * j;
+      if (yy < ny) dst[yy] = lo[j];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ 5-pass: y rows
+// rows (b, c, kx, z) of W with ys = PY; RPB rows per CTA.  smem: tw[PY] | s[RPB][PY+1]
+template <typename C, int PY, int RPB, bool INV>
+__global__ void __launch_bounds__(256) k_y_rows(Geom g, C* __restrict__ work, const C* __restrict__ twg,
+                                                int64_t nrows) {
+  constexpr int RA = Shape<PY>::RA, LB = Shape<PY>::LB, H = Shape<PY>::H;
+  constexpr int RP = PY + 1;
+  extern __shared__ unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* s = tw + PY;
+  const int64_t r0 = (int64_t)blockIdx.x * RPB;
+  const int nr = (int)min((int64_t)RPB, nrows - r0);
+  const int ny = g.ny;
+  copy_tw(tw, twg, PY);
+  __syncthreads();
+  if (!INV) {
+    for (int i = threadIdx.x; i < nr * LB; i += blockDim.x) {
+      const int n1 = i % LB, r = i / LB;
+      const C* src = work + (r0 + r) * PY;
+      C x[RA], o[2 * RA];
+#pragma unroll
+      for (int j = 0; j < RA; ++j) {
+        const int yy = n1 + LB * j;
+        x[j] = (yy < ny) ? src[yy] : czero<C>();
+      }
+      f2::passA_fwd<PY>(x, n1, tw, o);
+#pragma unroll
+      for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+        for (int k = 0; k < RA; ++k) s[r * RP + bb * H + n1 + LB * k] = o[bb * RA + k];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nr * 2 * RA; i += blockDim.x) {
+      const int r = i % nr, blk = i / nr;
+      C* row = s + r * RP + blk * LB;
+      C v[LB];
+#pragma unroll
+      for (int e = 0; e < LB; ++e) v[e] = row[e];
+      f2::passB_fwd<PY>(v, tw);
+#pragma unroll
+      for (int e = 0; e < LB; ++e) row[e] = v[e];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nr * PY; i += blockDim.x) {
+      const int r = i / PY, y = i % PY;
+      work[(r0 + r) * PY + y] = s[r * RP + y];
+    }
+  } else {
+    for (int i = threadIdx.x; i < nr * PY; i += blockDim.x) {
+      const int r = i / PY, y = i % PY;
+      s[r * RP + y] = work[(r0 + r) * PY + y];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nr * 2 * RA; i += blockDim.x) {
+      const int r = i % nr, blk = i / nr;
+      C* row = s + r * RP + blk * LB;
+      C v[LB];
+#pragma unroll
+      for (int e = 0; e < LB; ++e) v[e] = row[e];
+      f2::passB_inv<PY>(v, tw);
+#pragma unroll
+      for (int e = 0; e < LB; ++e) row[e] = v[e];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nr * LB; i += blockDim.x) {
+      const int n1 = i % LB, r = i / LB;
+      const C* row = s + r * RP;
+      C v[2 * RA], lo[RA];
+#pragma unroll
+      for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+        for (int k = 0; k < RA; ++k) v[bb * RA + k] = row[bb * H + n1 + LB * k];
+      f2::passA_inv<PY, false>(v, n1, tw, lo, (C*)nullptr);
+      C* dst = work + (r0 + r) * PY;
+#pragma unroll
+      for (int j = 0; j < RA; ++j) {
+        const int yy = n1 + LB * j;
+        if (yy < ny) dst[yy] = lo[j];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ 5-pass: z columns with Ghat
+// grid (ceil(py/G), px, nrhs); smem: tw[PZ] | s[PZ*3][G]
+template <typename C, int PZ, int G>
+__global__ void __launch_bounds__(256) k_z_cols(Geom g, MvData<C> d) {
+  constexpr int RA = Shape<PZ>::RA, LB = Shape<PZ>::LB, H = Shape<PZ>::H;
+  constexpr bool kFuse = (LB * sizeof(C) <= 96);
+  extern __shared__ unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* s = tw + PZ;
+  const int ky0 = blockIdx.x * G, kx = blockIdx.y, b = blockIdx.z;
+  const int nz = g.nz, py = g.py;
+  copy_tw(tw, d.twz, PZ);
+  __syncthreads();
+  C* wb = d.work + ((int64_t)b * 3 * g.px + kx) * ((int64_t)nz * g.ys);
+  const int64_t cstride = (int64_t)g.px * nz * g.ys;
+  // forward pass A from global
+  for (int i = threadIdx.x; i < 3 * G * LB; i += blockDim.x) {
+    const int gg = i % G;
+    const int r = i / G;
+    const int c = r % 3, n1 = r / 3;
+    const int ky = ky0 + gg;
+    C x[RA], o[2 * RA];
+#pragma unroll
+    for (int j = 0; j < RA; ++j) {
+      const int zz = n1 + LB * j;
+      x[j] = (zz < nz && ky < py) ? wb[c * cstride + (int64_t)zz * g.ys + ky] : czero<C>();
+    }
+    f2::passA_fwd<PZ>(x, n1, tw, o);
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+      for (int k = 0; k < RA; ++k) s[((bb * H + n1 + LB * k) * 3 + c) * G + gg] = o[bb * RA + k];
+  }
+  __syncthreads();
+  const C* gk = d.ghat + (int64_t)kx * PZ * py * 6;
+  if constexpr (kFuse) {
+    for (int i = threadIdx.x; i < G * 2 * RA; i += blockDim.x) {
+      const int gg = i % G, blk = i / G;
+      const int ky = ky0 + gg;
+      C v0[LB], v1[LB], v2[LB];
+#pragma unroll
+      for (int e = 0; e < LB; ++e) {
+        const C* q = s + ((blk * LB + e) * 3) * G + gg;
+        v0[e] = q[0];
+        v1[e] = q[G];
+        v2[e] = q[2 * G];
+      }
+      f2::passB_fwd<PZ>(v0, tw);
+      f2::passB_fwd<PZ>(v1, tw);
+      f2::passB_fwd<PZ>(v2, tw);
+      if (ky < py) {
+#pragma unroll
+        for (int e = 0; e < LB; ++e) gmul3(gk + ((int64_t)(blk * LB + e) * py + ky) * 6, v0[e], v1[e], v2[e]);
+      }
+      f2::passB_inv<PZ>(v0, tw);
+      f2::passB_inv<PZ>(v1, tw);
+      f2::passB_inv<PZ>(v2, tw);
+#pragma unroll
+      for (int e = 0; e < LB; ++e) {
+        C* q = s + ((blk * LB + e) * 3) * G + gg;
+        q[0] = v0[e];
+        q[G] = v1[e];
+        q[2 * G] = v2[e];
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i < 3 * G * 2 * RA; i += blockDim.x) {
+      const int gg = i % G;
+      const int r = i / G;
+      const int c = r % 3, blk = r / 3;
+      C v[LB];
+#pragma unroll
+      for (int e = 0; e < LB; ++e) v[e] = s[((blk * LB + e) * 3 + c) * G + gg];
+      f2::passB_fwd<PZ>(v, tw);
+#pragma unroll
+      for (int e = 0; e < LB; ++e) s[((blk * LB + e) * 3 + c) * G + gg] = v[e];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < PZ * G; i += blockDim.x) {
+      const int gg = i % G, kz = i / G;
+      const int ky = ky0 + gg;
+      if (ky >= py) continue;
+      C* q = s + (kz * 3) * G + gg;
+      C v0 = q[0], v1 = q[G], v2 = q[2 * G];
+      gmul3(gk + ((int64_t)kz * py + ky) * 6, v0, v1, v2);
+      q[0] = v0;
+      q[G] = v1;
+      q[2 * G] = v2;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * G * 2 * RA; i += blockDim.x) {
+      const int gg = i % G;
+      const int r = i / G;
+      const int c = r % 3, blk = r / 3;
+      C v[LB];
+#pragma unroll
+      for (int e = 0; e < LB; ++e) v[e] = s[((blk * LB + e) * 3 + c) * G + gg];
+      f2::passB_inv<PZ>(v, tw);
+#pragma unroll
+      for (int e = 0; e < LB; ++e) s[((blk * LB + e) * 3 + c) * G + gg] = v[e];
+    }
+  }
+  __syncthreads();
+  // inverse pass A to global (z < nz)
+  for (int i = threadIdx.x; i < 3 * G * LB; i += blockDim.x) {
+    const int gg = i % G;
+    const int r = i / G;
+    const int c = r % 3, n1 = r / 3;
+    const int ky = ky0 + gg;
+    C v[2 * RA], lo[RA];
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+      for (int k = 0; k < RA; ++k) v[bb * RA + k] = s[((bb * H + n1 + LB * k) * 3 + c) * G + gg];
+    f2::passA_inv<PZ, false>(v, n1, tw, lo, (C*)nullptr);
+    if (ky < py) {
+#pragma unroll
+      for (int j = 0; j < RA; ++j) {
+        const int zz = n1 + LB * j;
+        if (zz < nz) wb[c * cstride + (int64_t)zz * g.ys + ky] = lo[j];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ dispatch
+#define DDA_FAST_LENGTHS(X) X(16) X(24) X(32) X(40) X(48) X(64) X(80) X(96) X(128) X(160) X(192) X(256) X(320)
+#define DDA_FAST_PLANES(X)                                                                               \
+  X(16, 16) X(24, 24) X(32, 32) X(40, 40) X(48, 48) X(64, 64) X(80, 80) X(96, 96) X(96, 64) X(64, 96) \
+  X(96, 48) X(48, 96) X(64, 32) X(32, 64) X(96, 40) X(80, 40) X(48, 32) X(32, 48)
+
+inline bool fast_length(int L) {
+  switch (L) {
+#define DDA_CASE(L_) case L_:
+    DDA_FAST_LENGTHS(DDA_CASE)
+#undef DDA_CASE
+    return true;
+    default: return false;
+  }
+}
+
+inline bool fast_plane_pair(int py, int pz) {
+#define DDA_CASE(A, B) if (py == A && pz == B) return true;
+  DDA_FAST_PLANES(DDA_CASE)
+#undef DDA_CASE
+  return false;
+}
+
+// y rows per CTA of the x passes: 128-byte row segments where shared memory allows
+template <typename C, int PX> constexpr int x_ty() {
+  return sizeof(C) == 8 ? (PX <= 128 ? 16 : 8) : (PX <= 128 ? 8 : 4);
+}
+inline int x_ty_rt(size_t csize, int px) { return csize == 8 ? (px <= 128 ? 16 : 8) : (px <= 128 ? 8 : 4); }
+
+// z columns per CTA of the 5-pass z kernel: widest tile under ~110 KB of shared memory
+constexpr int zcols_g_rt(size_t csize, int pz) {
+  return (size_t)pz * 3 * 32 * csize <= 110 * 1024 ? 32 : ((size_t)pz * 3 * 16 * csize <= 110 * 1024 ? 16 : 8);
+}
+
+inline int odd_pitch(int n) { return (n % 2) ? n : n + 1; }
+
+template <typename C>
+size_t x_fast_smem(const Geom& g) {
+  const int TY = x_ty_rt(sizeof(C), g.px);
+  return sizeof(C) * ((size_t)g.px + (size_t)3 * TY * odd_pitch(g.nx) + (size_t)3 * g.px * TY);
+}
+template <typename C>
+size_t plane_fast_smem(const Geom& g) {
+  return sizeof(C) * ((size_t)g.py + g.pz + (size_t)g.pz * 3 * (g.py + 1));
+}
+constexpr int kRowsPerCta = 8;
+template <typename C>
+size_t yrows_fast_smem(const Geom& g) {
+  return sizeof(C) * ((size_t)g.py + (size_t)kRowsPerCta * (g.py + 1));
+}
+template <typename C>
+size_t zcols_fast_smem(const Geom& g) {
+  return sizeof(C) * ((size_t)g.pz + (size_t)g.pz * 3 * zcols_g_rt(sizeof(C), g.pz));
+}
+
+template <typename C>
+Err launch_x_fwd(const Geom& g, const MvData<C>& d, const C* p, int nrhs, bool conj, cudaStream_t st) {
+  const int TY = x_ty_rt(sizeof(C), g.px);
+  const size_t sm = x_fast_smem<C>(g);
+  const dim3 grid((g.ny + TY - 1) / TY, g.nz, nrhs);
+  const int ip = odd_pitch(g.nx);
+  switch (g.px) {
+#define DDA_CASE(L_)                                                                 \
+  case L_:                                                                           \
+    k_x_fwd<C, L_, x_ty<C, L_>()><<<grid, 256, sm, st>>>(g, d, p, conj, ip);         \
+    break;
+    DDA_FAST_LENGTHS(DDA_CASE)
+#undef DDA_CASE
+    default: return Err::make(DDA_EUNSUPPORTED, "no fast x kernel for this length");
+  }
+  DDA_CU(cudaGetLastError());
+  return Err::Ok();
+}
+
+template <typename C>
+Err launch_x_inv(const Geom& g, const MvData<C>& d, const C* p, C* ap, int nrhs, int rhs0, bool conj,
+                 cudaStream_t st) {
+  const int TY = x_ty_rt(sizeof(C), g.px);
+  const size_t sm = x_fast_smem<C>(g);
+  const dim3 grid((g.ny + TY - 1) / TY, g.nz, nrhs);
+  const int ip = odd_pitch(g.nx);
+  switch (g.px) {
+#define DDA_CASE(L_)                                                                       \
+  case L_:                                                                                 \
+    k_x_inv<C, L_, x_ty<C, L_>()><<<grid, 256, sm, st>>>(g, d, p, ap, rhs0, conj, ip);     \
+    break;
+    DDA_FAST_LENGTHS(DDA_CASE)
+#undef DDA_CASE
+    default: return Err::make(DDA_EUNSUPPORTED, "no fast x kernel for this length");
+  }
+  DDA_CU(cudaGetLastError());
+  return Err::Ok();
+}
+
+// complex64 only: a complex128 plane does not fit in shared memory at these sizes
+template <typename C>
+Err launch_plane(const Geom& g, const MvData<C>& d, int nrhs, cudaStream_t st) {
+  if constexpr (sizeof(C) == 8) {
+    const size_t sm = plane_fast_smem<C>(g);
+    const dim3 grid(nrhs, g.px);
+#define DDA_CASE(A, B)                                               \
+    if (g.py == A && g.pz == B) {                                    \
+      k_yz_plane<C, A, B><<<grid, 512, sm, st>>>(g, d);              \
+      DDA_CU(cudaGetLastError());                                    \
+      return Err::Ok();                                              \
+    }
+    DDA_FAST_PLANES(DDA_CASE)
+#undef DDA_CASE
+  }
+  return Err::make(DDA_EUNSUPPORTED, "no fast plane kernel for this pair");
+}
+
+template <typename C>
+Err launch_y_rows(const Geom& g, C* work, const C* tw, int64_t nrows, bool inv, cudaStream_t st) {
+  const size_t sm = yrows_fast_smem<C>(g);
+  const unsigned nb = (unsigned)((nrows + kRowsPerCta - 1) / kRowsPerCta);
+  switch (g.py) {
+#define DDA_CASE(L_)                                                                            \
+  case L_:                                                                                      \
+    if (inv) k_y_rows<C, L_, kRowsPerCta, true><<<nb, 256, sm, st>>>(g, work, tw, nrows);       \
+    else k_y_rows<C, L_, kRowsPerCta, false><<<nb, 256, sm, st>>>(g, work, tw, nrows);          \
+    break;
+    DDA_FAST_LENGTHS(DDA_CASE)
+#undef DDA_CASE
+    default: return Err::make(DDA_EUNSUPPORTED, "no fast y kernel for this length");
+  }
+  DDA_CU(cudaGetLastError());
+  return Err::Ok();
+}
+
+template <typename C>
+Err launch_z_cols(const Geom& g, const MvData<C>& d, int nrhs, cudaStream_t st) {
+  const size_t sm = zcols_fast_smem<C>(g);
+  const int G = zcols_g_rt(sizeof(C), g.pz);
+  const dim3 grid((g.py + G - 1) / G, g.px, nrhs);
+  switch (g.pz) {
+#define DDA_CASE(L_)                                                                      \
+  case L_:                                                                                \
+    k_z_cols<C, L_, zcols_g_rt(sizeof(C), L_)><<<grid, 256, sm, st>>>(g, d);              \
+    break;
+    DDA_FAST_LENGTHS(DDA_CASE)
+#undef DDA_CASE
+    default: return Err::make(DDA_EUNSUPPORTED, "no fast z kernel for this length");
+  }
+  DDA_CU(cudaGetLastError());
+  return Err::Ok();
+}
+
+// Opt every instantiation of this precision into the device's maximum dynamic shared memory.
+template <typename C>
+void optin_all(int smax) {
+#define DDA_CASE(L_)                                                                                                 \
+  cudaFuncSetAttribute(k_x_fwd<C, L_, x_ty<C, L_>()>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);         \
+  cudaFuncSetAttribute(k_x_inv<C, L_, x_ty<C, L_>()>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);         \
+  cudaFuncSetAttribute(k_y_rows<C, L_, kRowsPerCta, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);   \
+  cudaFuncSetAttribute(k_y_rows<C, L_, kRowsPerCta, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);    \
+  cudaFuncSetAttribute(k_z_cols<C, L_, zcols_g_rt(sizeof(C), L_)>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  DDA_FAST_LENGTHS(DDA_CASE)
+#undef DDA_CASE
+  if constexpr (sizeof(C) == 8) {
+#define DDA_CASE(A, B) cudaFuncSetAttribute(k_yz_plane<C, A, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    DDA_FAST_PLANES(DDA_CASE)
+#undef DDA_CASE
+  }
+}
+
+// The whole product on the compile-time-length kernels (3-pass when t.plane, else 5-pass).
+template <typename C>
+Err launch_matvec_fast(const Geom& g, const MvData<C>& d, const MvTune& t, const C* p, C* ap, int nrhs, int rhs0,
+                       bool conj, cudaStream_t st) {
+  int pass = 0;
+  mark_pass(pass++, st);
+  DDA_TRY(launch_x_fwd<C>(g, d, p, nrhs, conj, st));
+  mark_pass(pass++, st);
+  if (t.plane) {
+    DDA_TRY(launch_plane<C>(g, d, nrhs, st));
+    mark_pass(pass++, st);
+    add_launches(3);
+  } else {
+    const int64_t nrows = (int64_t)nrhs * 3 * g.px * g.nz;
+    DDA_TRY(launch_y_rows<C>(g, d.work, d.twy, nrows, false, st));
+    mark_pass(pass++, st);
+    DDA_TRY(launch_z_cols<C>(g, d, nrhs, st));
+    mark_pass(pass++, st);
+    DDA_TRY(launch_y_rows<C>(g, d.work, d.twy, nrows, true, st));
+    mark_pass(pass++, st);
+    add_launches(5);
+  }
+  DDA_TRY(launch_x_inv<C>(g, d, p, ap, nrhs, rhs0, conj, st));
+  mark_pass(pass++, st);
+  return Err::Ok();
+}
+
+}  // namespace fast
+}  // namespace dda

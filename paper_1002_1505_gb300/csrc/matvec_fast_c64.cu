@@ -1,0 +1,26 @@
+// complex64 instantiations of the compile-time-length product kernels.
+#include "matvec_fast.cuh"
+
+namespace dda {
+template <>
+Err launch_matvec_fast<float2>(const Geom& g, const MvData<float2>& d, const MvTune& t, const float2* p, float2* ap,
+                               int nrhs, int rhs0, bool conj, cudaStream_t st) {
+  return fast::launch_matvec_fast<float2>(g, d, t, p, ap, nrhs, rhs0, conj, st);
+}
+void fast_optin_c64(int smax) { fast::optin_all<float2>(smax); }
+
+void choose_fast_schedule(const Geom& g, bool c64, int smax, MvTune* t) {
+  t->fast = fast::fast_length(g.px) && fast::fast_length(g.py) && fast::fast_length(g.pz);
+  if (!t->fast) return;
+  const size_t cs = c64 ? sizeof(float2) : sizeof(double2);
+  const size_t xs = c64 ? fast::x_fast_smem<float2>(g) : fast::x_fast_smem<double2>(g);
+  const size_t ys = c64 ? fast::yrows_fast_smem<float2>(g) : fast::yrows_fast_smem<double2>(g);
+  const size_t zs = c64 ? fast::zcols_fast_smem<float2>(g) : fast::zcols_fast_smem<double2>(g);
+  if (xs > (size_t)smax || ys > (size_t)smax || zs > (size_t)smax) {
+    t->fast = false;
+    return;
+  }
+  (void)cs;
+  t->plane = c64 && fast::fast_plane_pair(g.py, g.pz) && fast::plane_fast_smem<float2>(g) <= (size_t)smax;
+}
+}  // namespace dda

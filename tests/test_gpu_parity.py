@@ -72,6 +72,53 @@ def test_matvec_matches_direct_sum(D, w):
             assert err <= tol, (w.name, dt, b, err)
 
 
+FAST_PADS = [
+    # (workload, pad): plane pair (32, 48); 5-pass with a 16-point x length (one-stage pass A);
+    # plane (40, 40); 5-pass c64 and c128 with odd boxes and ragged y tiles
+    (W.Workload("ell_p1", "ELLIPSOID", (12, 16, 24), 1.5 + 0.1j, 2.0, "GKDLDR", W.uniform_orientations(1, 41)),
+     (24, 32, 48)),
+    (W.Workload("blk_p2", "RCTGLPRSM", (3, 17, 4), 2.0 + 1.0j, 1.5, "LATTDR", W.uniform_orientations(2, 42)),
+     (16, 40, 40)),
+    (W.Workload("cyl_p3", "CYLINDER1", (30, 20, 1), 1.33 + 0.05j, 3.0, "CM", W.uniform_orientations(1, 43)),
+     (64, 40, 40)),
+    (W.Workload("ell_p4", "ELLIPSOID", (11, 13, 6), 1.4 + 0.2j, 2.0, "GKDLDR", W.uniform_orientations(2, 44)),
+     (24, 32, 16)),
+]
+
+
+@pytest.mark.parametrize("w,pad", FAST_PADS, ids=[w.name for w, _ in FAST_PADS])
+def test_matvec_fast_kernels_match_direct_sum(D, w, pad):
+    ctx = _ctx(D, w, pad)
+    prob = _oracle_problem(w)
+    for dt, tol in ((torch.complex128, 1e-12), (torch.complex64, 1e-5)):
+        p = _rand_p(ctx.nrhs, ctx.n, 8, dt)
+        ap = torch.empty_like(p)
+        ctx.dda_matvec(p, ap)
+        torch.cuda.synchronize()
+        pn = p.cpu().numpy().astype(np.complex128)
+        got = ap.cpu().numpy().astype(np.complex128)
+        for b in range(ctx.nrhs):
+            ref = odda.apply_a(prob, b, pn[b], "direct")
+            err = np.linalg.norm(got[b] - ref) / np.linalg.norm(ref)
+            assert err <= tol, (w.name, dt, b, err)
+
+
+def test_fast_and_generic_engines_agree(D, monkeypatch):
+    w = W.ELLIPSOID64
+    out = {}
+    for mode in ("default", "generic"):
+        if mode == "generic":
+            monkeypatch.setenv("DDA_SCHEDULE", "generic")
+        ctx = _ctx(D, w)
+        p = _rand_p(ctx.nrhs, ctx.n, 9, torch.complex64)
+        ap = torch.empty_like(p)
+        ctx.dda_matvec(p, ap)
+        torch.cuda.synchronize()
+        out[mode] = ap.cpu().numpy().astype(np.complex128)
+    err = np.linalg.norm(out["default"] - out["generic"]) / np.linalg.norm(out["generic"])
+    assert err <= 2e-6, err
+
+
 def test_matvec_nondefault_pad_and_tail_tiles(D):
     # odd box sizes against a padded grid larger than 2N (pruned FFT inputs shorter than L/2)
     w = W.Workload("ell_pad", "ELLIPSOID", (11, 13, 6), 1.4 + 0.2j, 2.0, "GKDLDR", W.uniform_orientations(1, 21),

@@ -25,26 +25,37 @@ def D():
     return dda
 
 
-@pytest.mark.parametrize("w", [W.Workload("ell_odd", "ELLIPSOID", (7, 5, 9), 1.5 + 0.1j, 2.0, "GKDLDR",
-                                          W.uniform_orientations(2, 11)),
-                               W.ELLIPSOID64], ids=["small_4rhs", "ellipsoid64_2rhs"])
-def test_noalloc_product_matches_allocating_product_twice(D, w):
+# (workload, RHS per call for complex64, for complex128): the 64x48x32 grid needs 9.4 MB of
+# complex64 scratch per RHS on its 3-pass schedule and 18.9 MB of complex128 scratch on its 5-pass one,
+# so one complex128 RHS fits the fixed 32 MiB and two do not.
+CASES = [(W.Workload("ell_odd", "ELLIPSOID", (7, 5, 9), 1.5 + 0.1j, 2.0, "GKDLDR", W.uniform_orientations(2, 11)),
+          4, 4),
+         (W.ELLIPSOID64, 2, 1)]
+
+
+@pytest.mark.parametrize("w,nr64,nr128", CASES, ids=["small_4rhs", "ellipsoid64"])
+def test_noalloc_product_matches_allocating_product_twice(D, w, nr64, nr128):
     ctx = D.Context(0)
     D.setup_workload(ctx, w)
-    for dt, tol in ((torch.complex64, 1e-5), (torch.complex128, 1e-12)):
-        p = torch.from_numpy(W.seeded_vector((ctx.nrhs, 3, ctx.n), 41)).to(dt).cuda()
+    for dt, tol, nr in ((torch.complex64, 1e-5, nr64), (torch.complex128, 1e-12, nr128)):
+        p = torch.from_numpy(W.seeded_vector((nr, 3, ctx.n), 41)).to(dt).cuda()
         ref = torch.empty_like(p)
-        ctx.dda_matvec(p, ref)
+        ctx.dda_matvec(p, ref, nrhs=nr)
         torch.cuda.synchronize()
         ref_np = ref.cpu().numpy().astype(np.complex128)
         for call in range(2):
             out = torch.full_like(p, float("nan"))
-            ctx.dda_matvec_noalloc(p, out)
+            ctx.dda_matvec_noalloc(p, out, nrhs=nr)
             torch.cuda.synchronize()
             got = out.cpu().numpy().astype(np.complex128)
             assert np.isfinite(got).all()
             err = np.linalg.norm(got - ref_np) / np.linalg.norm(ref_np)
             assert err <= tol, (dt, call, err)
+    if w is W.ELLIPSOID64:  # two complex128 RHS exceed the fixed scratch
+        p2 = torch.zeros((2, 3, ctx.n), dtype=torch.complex128, device="cuda")
+        with pytest.raises(D.DDAError) as ei:
+            ctx.dda_matvec_noalloc(p2, torch.empty_like(p2), nrhs=2)
+        assert ei.value.status == D.DDA_EINVAL
 
 
 def test_noalloc_rejects_requests_beyond_the_fixed_scratch(D):

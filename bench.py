@@ -105,8 +105,8 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def algorithmic_bytes(sched_passes: int, n: int, box, pad, nrhs: int, csize: int):
-    """Bytes per launch of each pass (byte model of the 3-pass / 5-pass schedule)."""
+def algorithmic_bytes(sched_passes: int, n: int, box, pad, nrhs: int, csize: int, fast: bool = True):
+    """Bytes per launch of each pass (byte model of the 3-pass / 5-pass schedule) and kernel names."""
     nx, ny, nz = box
     px, py, pz = pad
     xrow = px * ny * nz            # spectrum after the x pass (per component)
@@ -115,10 +115,11 @@ def algorithmic_bytes(sched_passes: int, n: int, box, pad, nrhs: int, csize: int
     b3 = 3 * nrhs
     if sched_passes == 3:
         per = [b3 * (n + xrow), b3 * 2 * xrow + ghat, b3 * (xrow + n)]
-        names = ["k_xfwd", "k_yzplane", "k_xinv"]
+        names = ["k_x_fwd", "k_yz_plane", "k_x_inv"] if fast else ["k_xfwd", "k_yzplane", "k_xinv"]
     else:
         per = [b3 * (n + xrow), b3 * (xrow + yrow), b3 * 2 * yrow + ghat, b3 * (yrow + xrow), b3 * (xrow + n)]
-        names = ["k_xfwd", "k_fft_rows(y fwd)", "k_zconv", "k_fft_rows(y inv)", "k_xinv"]
+        names = (["k_x_fwd", "k_y_rows(fwd)", "k_z_cols", "k_y_rows(inv)", "k_x_inv"] if fast else
+                 ["k_xfwd", "k_fft_rows(y fwd)", "k_zconv", "k_fft_rows(y inv)", "k_xinv"])
     return [v * csize for v in per], names
 
 
@@ -189,8 +190,14 @@ def main():
     ap.add_argument("--workload", default="ellipsoid64", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-reps", type=int, default=2)
+    ap.add_argument("--orientations", type=int, default=0,
+                    help="use only the first N orientations of the workload (smaller profiling runs)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
+    if args.orientations > 0:
+        import dataclasses
+        w = dataclasses.replace(w, name=f"{w.name}[:{args.orientations}]",
+                                orientations=w.orientations[:args.orientations])
     ws, rank, local = dist_env()
     if args.warmup < 3:
         args.warmup = 3
@@ -296,9 +303,10 @@ def main():
 
     # dominant pass of the product: CUDA events between passes on the launching stream
     ms_pass = D.dda_profile_matvec(ctx, nrhs, D.DDA_C64, iters=20)
+    sched = D.dda_schedule_info(ctx, D.DDA_C64)
     cs = 8
     pad = w.pad if w.pad else tuple(int(v) for v in np.array(box) * 2)
-    abytes, names = algorithmic_bytes(len(ms_pass), n, box, pad, nrhs, cs)
+    abytes, names = algorithmic_bytes(len(ms_pass), n, box, pad, nrhs, cs, fast=bool(sched[1]))
     dom = int(np.argmax(ms_pass))
     peak, peak_kind = peaks()
     achieved = abytes[dom] / (ms_pass[dom] * 1e-3) / 1e9
@@ -313,6 +321,8 @@ def main():
                 "traffic": traffic, "kernel": names[dom], "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": abytes[dom], "ms_per_launch": ms_pass[dom],
                 "passes_ms": {nm: float(v) for nm, v in zip(names, ms_pass)},
+                "schedule": {"passes": sched[0], "compile_time_kernels": bool(sched[1]),
+                             "plane_threads": sched[2], "tuned_for_nrhs": sched[3]},
                 "product_ms": float(np.sum(ms_pass))}
 
     if rank == 0:

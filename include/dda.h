@@ -223,6 +223,15 @@ DDA_API unsigned long long dda_kernel_launches(void);
  * schedule: x forward, y forward, z, y inverse, x inverse).  Synchronizes. */
 DDA_API dda_status dda_profile_matvec(dda_ctx *ctx, int nrhs, int dtype, int iters, double *ms_per_pass, int *npass);
 
+/* Launch schedule of the product for dtype, as chosen by the autotuner (the
+ * first product for a given RHS count times the candidate schedules and keeps
+ * the fastest) or pinned by the DDA_SCHEDULE environment variable at
+ * dda_build_green_fft time ("generic", "fast5", "plane512", "plane768").
+ * info[0] = passes (3 = fused y-z plane, 5 = split), info[1] = 1 when the
+ * compile-time-length kernels are used, info[2] = threads of the plane kernel
+ * (0 if none), info[3] = RHS count the choice was tuned for (0 = not tuned). */
+DDA_API dda_status dda_schedule_info(dda_ctx *ctx, int dtype, int32_t info[4]);
+
 /* Library build string (static storage). */
 DDA_API const char *dda_version(void);
 

@@ -2,7 +2,10 @@
 // set-up on the host (FP64), Green-tensor build, product A P, the batched
 // Krylov drivers (BiCGstab, CCG; complex64, complex128 or complex64 refined
 // against complex128 true residuals) and the observables.
+#include <array>
 #include <chrono>
+#include <map>
+#include <mutex>
 #include <cstdlib>
 #include <cmath>
 #include <cstdio>
@@ -87,6 +90,9 @@ struct dda_ctx {
   double2* d_F = nullptr;             // far-field sums
   double* d_fpart = nullptr;          // far-field partial sums
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // cached solver graphs (complex64, complex128)
+  int tuned_nrhs[2] = {0, 0};         // RHS count the current schedule was tuned for (c64, c128)
+  bool forced_schedule = false;       // DDA_SCHEDULE fixed the schedule: no autotuning
+  void* d_tunebuf = nullptr;          // operands of the autotuner's timed products
   // Device buffers grow and are never shrunk while the context lives: set-up
   // calls for a new problem of the same size recompute their results in the
   // same memory instead of freeing and allocating again.
@@ -330,6 +336,89 @@ Err matvec(dda_ctx* c, const C* p, C* ap, int nrhs, int rhs0, bool conj) {
     DDA_TRY(dda::launch_matvec<C>(Sel<C>::geom(c), Sel<C>::data(c), Sel<C>::tune(c), p + b0 * n3, ap + b0 * n3, nb,
                                   rhs0 + b0, conj, c->stream));
   }
+  return Err::Ok();
+}
+
+// ------------------------------------------------------------------ autotuner
+// The product has several launch schedules for a grid: the fused 3-pass plane
+// kernel at 512 or 768 threads, and the 5-pass split (more memory traffic,
+// more CTAs; better when few RHS leave SMs idle).  The first product of a
+// given (grid, RHS count, precision) times each candidate on the device (one
+// warm-up, then three products between CUDA events) and keeps the fastest;
+// the choice is cached for the process.
+std::mutex g_tune_mu;
+std::map<std::array<int, 8>, dda::MvTune> g_tune_cache;
+
+template <typename C>
+Err apply_tune(dda_ctx* c, const dda::MvTune& t) {
+  dda::MvTune& cur = (sizeof(C) == sizeof(float2)) ? c->t64 : c->t128;
+  dda::Geom& g = (sizeof(C) == sizeof(float2)) ? c->g64 : c->g128;
+  cur = t;
+  g.ys = t.plane ? g.ny : g.py;
+  return Err::Ok();
+}
+
+template <typename C>
+Err ensure_tuned(dda_ctx* c, int nrhs) {
+  const int idx = (sizeof(C) == sizeof(float2)) ? 0 : 1;
+  const dda::MvTune base = idx == 0 ? c->t64 : c->t128;
+  if (c->forced_schedule || !base.fast || c->tuned_nrhs[idx] == nrhs) return Err::Ok();
+  const dda::Geom& g0 = idx == 0 ? c->g64 : c->g128;
+  const std::array<int, 8> key = {g0.nx, g0.ny, g0.nz, g0.px, g0.py, g0.pz, nrhs, (int)sizeof(C)};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      DDA_TRY(apply_tune<C>(c, it->second));
+      c->tuned_nrhs[idx] = nrhs;
+      return Err::Ok();
+    }
+  }
+  std::vector<dda::MvTune> cand;
+  dda::MvTune t5 = base;
+  t5.plane = false;
+  if (base.plane_ok) {
+    dda::MvTune a = base, b = base;
+    a.plane = b.plane = true;
+    a.thr_p = 512;
+    b.thr_p = 768;
+    cand.push_back(a);
+    cand.push_back(b);
+  }
+  cand.push_back(t5);
+  dda::MvTune best = cand[0];
+  if (cand.size() > 1) {
+    const size_t bytes = sizeof(C) * (size_t)nrhs * 3 * c->n;
+    DDA_TRY(grow(c, (char**)&c->d_tunebuf, 2 * bytes));
+    C* p = (C*)c->d_tunebuf;
+    C* ap = p + (size_t)nrhs * 3 * c->n;
+    DDA_CU(cudaMemsetAsync(p, 0, bytes, c->stream));
+    cudaEvent_t e0, e1;
+    DDA_CU(cudaEventCreate(&e0));
+    DDA_CU(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    Err err = Err::Ok();
+    for (const dda::MvTune& t : cand) {
+      apply_tune<C>(c, t);
+      err = matvec<C>(c, p, ap, nrhs, 0, false);
+      if (!err.ok()) break;
+      cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < 3 && err.ok(); ++r) err = matvec<C>(c, p, ap, nrhs, 0, false);
+      cudaEventRecord(e1, c->stream);
+      if (!err.ok()) break;
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) { best_ms = ms; best = t; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    DDA_TRY(err);
+  }
+  DDA_TRY(apply_tune<C>(c, best));
+  c->tuned_nrhs[idx] = nrhs;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[key] = best;
   return Err::Ok();
 }
 
@@ -721,11 +810,24 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
     dda::choose_fast_schedule(g128, false, smax, &t128);
     if (!t64.fast) t64.plane = dda::plane_smem_bytes<float2>(g64, t64) <= (size_t)smax;
     if (!t128.fast) t128.plane = dda::plane_smem_bytes<double2>(g128, t128) <= (size_t)smax;
-    if (const char* f = std::getenv("DDA_SCHEDULE")) {  // "generic": force the generic engine (tests)
-      if (std::string(f) == "generic") {
+    // DDA_SCHEDULE pins the schedule instead of autotuning it: "generic" (shared-memory
+    // engine of fft.cuh), "fast5" (compile-time kernels, 5 passes), "plane512" / "plane768"
+    // (compile-time kernels, fused plane pass where it exists)
+    c->forced_schedule = false;
+    c->tuned_nrhs[0] = c->tuned_nrhs[1] = 0;
+    if (const char* f = std::getenv("DDA_SCHEDULE")) {
+      const std::string sched(f);
+      if (sched == "generic") {
         t64.fast = t128.fast = false;
         t64.plane = dda::plane_smem_bytes<float2>(g64, t64) <= (size_t)smax;
         t128.plane = dda::plane_smem_bytes<double2>(g128, t128) <= (size_t)smax;
+        c->forced_schedule = true;
+      } else if (sched == "fast5") {
+        t64.plane = t128.plane = false;
+        c->forced_schedule = true;
+      } else if (sched == "plane512" || sched == "plane768") {
+        t64.thr_p = t128.thr_p = (sched == "plane768") ? 768 : 512;
+        c->forced_schedule = true;
       }
     }
     if (!t64.plane) g64.ys = g.py;
@@ -809,9 +911,15 @@ dda_status dda_matvec(dda_ctx* c, const void* p, void* ap, int nrhs, int dtype) 
   if (p == ap) return fail(c, Err::make(DDA_EINVAL, "p and ap may not alias"));
   Err e = set_dev(c);
   if (!e.ok()) return fail(c, e);
-  if (dtype == DDA_C64) e = matvec<float2>(c, (const float2*)p, (float2*)ap, nrhs, 0, false);
-  else if (dtype == DDA_C128) e = matvec<double2>(c, (const double2*)p, (double2*)ap, nrhs, 0, false);
-  else return fail(c, Err::make(DDA_EINVAL, "dtype must be DDA_C64 or DDA_C128"));
+  if (dtype == DDA_C64) {
+    e = ensure_tuned<float2>(c, nrhs);
+    if (e.ok()) e = matvec<float2>(c, (const float2*)p, (float2*)ap, nrhs, 0, false);
+  } else if (dtype == DDA_C128) {
+    e = ensure_tuned<double2>(c, nrhs);
+    if (e.ok()) e = matvec<double2>(c, (const double2*)p, (double2*)ap, nrhs, 0, false);
+  } else {
+    return fail(c, Err::make(DDA_EINVAL, "dtype must be DDA_C64 or DDA_C128"));
+  }
   return e.ok() ? DDA_OK : fail(c, e);
 }
 
@@ -883,6 +991,8 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
     const int64_t el = (int64_t)nrhs * n3;
     double2* P = (double2*)p_dev;
     e = ensure_einc(c);
+    if (e.ok()) e = ensure_tuned<double2>(c, nrhs);
+    if (e.ok() && o.precision != DDA_PREC_C128) e = ensure_tuned<float2>(c, nrhs);
     if (!e.ok()) return fail(c, e);
     std::vector<int> iters(nrhs, 0), outer_n(nrhs, 0);
     int matvecs = 0;
@@ -1189,6 +1299,8 @@ dda_status dda_profile_matvec(dda_ctx* c, int nrhs, int dtype, int iters, double
   if (dtype != DDA_C64 && dtype != DDA_C128) return fail(c, Err::make(DDA_EINVAL, "bad dtype"));
   Err e = set_dev(c);
   if (!e.ok()) return fail(c, e);
+  e = (dtype == DDA_C64) ? ensure_tuned<float2>(c, nrhs) : ensure_tuned<double2>(c, nrhs);
+  if (!e.ok()) return fail(c, e);
   const bool plane = (dtype == DDA_C64) ? c->t64.plane : c->t128.plane;
   const int np = plane ? 3 : 5;
   const size_t cs = dtype == DDA_C64 ? sizeof(float2) : sizeof(double2);
@@ -1201,6 +1313,7 @@ dda_status dda_profile_matvec(dda_ctx* c, int nrhs, int dtype, int iters, double
   if (e.ok() && cudaMemsetAsync(p, 0, bytes, c->stream) != cudaSuccess) e = Err::make(DDA_ECUDA, "memset failed");
   for (int i = 0; i <= np && e.ok(); ++i)
     if (cudaEventCreate(&ev[i]) != cudaSuccess) e = Err::make(DDA_ECUDA, "event creation failed");
+  if (e.ok()) e = (dtype == DDA_C64) ? ensure_tuned<float2>(c, nrhs) : ensure_tuned<double2>(c, nrhs);
   for (int it = 0; it < iters && e.ok(); ++it) {
     dda::set_pass_events(ev);
     if (dtype == DDA_C64) e = matvec<float2>(c, (const float2*)p, (float2*)ap, nrhs, 0, false);
@@ -1222,5 +1335,17 @@ dda_status dda_profile_matvec(dda_ctx* c, int nrhs, int dtype, int iters, double
   if (!e.ok()) return fail(c, e);
   for (int i = 0; i < np; ++i) ms_per_pass[i] = acc[i] / iters;
   *npass = np;
+  return DDA_OK;
+}
+
+dda_status dda_schedule_info(dda_ctx* c, int dtype, int32_t info[4]) {
+  if (!c || !info) return DDA_EINVAL;
+  if (!c->have_green) return fail(c, Err::make(DDA_ESTATE, "build the Green tensor first"));
+  if (dtype != DDA_C64 && dtype != DDA_C128) return fail(c, Err::make(DDA_EINVAL, "bad dtype"));
+  const dda::MvTune& t = dtype == DDA_C64 ? c->t64 : c->t128;
+  info[0] = t.plane ? 3 : 5;
+  info[1] = t.fast ? 1 : 0;
+  info[2] = t.plane ? t.thr_p : 0;
+  info[3] = c->tuned_nrhs[dtype == DDA_C64 ? 0 : 1];
   return DDA_OK;
 }

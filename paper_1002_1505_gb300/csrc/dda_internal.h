@@ -88,6 +88,7 @@ struct MvTune {
   int thr_p = 512;    // threads, plane / z passes
   bool plane = true;  // 3-pass schedule (plane fits in shared memory)
   bool fast = false;  // compile-time-length kernels exist for px, py, pz (matvec_fast.cuh)
+  bool plane_ok = false;  // the fast 3-pass plane kernel exists and fits for this grid
 };
 
 // Enqueue ap = A p for nrhs right-hand sides (rhs0 = index of the first one for alpha).

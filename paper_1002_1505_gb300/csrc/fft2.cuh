@@ -26,8 +26,9 @@ struct CPlan {
   int r[kMaxStages];
 };
 
-// Compile-time copy of make_plan's stage list (targets.cpp): 2, then radix 8/4
-// stages for the remaining power of two, then 3s and 5s.
+// Compile-time copy of make_plan's stage list (targets.cpp): 2, then radix-8
+// stages for the remaining power of two with one radix 4 or 2 for the
+// remainder, then 3s and 5s.
 constexpr CPlan cplan(int L) {
   CPlan p{};
   int k = 0;
@@ -39,10 +40,7 @@ constexpr CPlan cplan(int L) {
   int n2 = 0;
   while (a >= 3) { r2[n2++] = 8; a -= 3; }
   if (a == 2) r2[n2++] = 4;
-  else if (a == 1) {
-    if (n2 > 0) { r2[n2 - 1] = 4; r2[n2++] = 4; }
-    else r2[n2++] = 2;
-  }
+  else if (a == 1) r2[n2++] = 2;
   for (int i = 0; i < n2; ++i) p.r[k++] = r2[i];
   while (rest % 3 == 0) { rest /= 3; p.r[k++] = 3; }
   while (rest % 5 == 0) { rest /= 5; p.r[k++] = 5; }

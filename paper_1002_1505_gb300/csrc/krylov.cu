@@ -37,6 +37,44 @@ __device__ __forceinline__ double2 cdot_acc(double2 acc, double2 a, double2 b) {
 }
 __device__ __forceinline__ double nrm_acc(double acc, double2 a) { return acc + a.x * a.x + a.y * a.y; }
 
+// Per-thread accumulator of products.  complex128 vectors: FP64.  complex64
+// vectors: a double-float pair (Dekker/Knuth): each product is split exactly
+// into p + pe with one FMA, added with the two-sum, so a thread's partial keeps
+// about 48 bits using FP32 instructions only (the FP64 pipe of this GPU is too
+// slow to keep up with memory); partials are combined in FP64 from the warp up.
+template <typename C> struct Acc;
+template <> struct Acc<double2> {
+  double v = 0.0;
+  __device__ __forceinline__ void fma(double a, double b) { v = __fma_rn(a, b, v); }
+  __device__ __forceinline__ double get() const { return v; }
+};
+template <> struct Acc<float2> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void fma(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);
+    const float t = __fadd_rn(hi, p);
+    const float z = __fsub_rn(t, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, z)), __fsub_rn(p, z));
+    hi = t;
+    lo = __fadd_rn(lo, __fadd_rn(e, pe));
+  }
+  __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
+};
+// re + i im += conj(a) b
+template <typename C>
+__device__ __forceinline__ void acc_cdot(Acc<C>& re, Acc<C>& im, C a, C b) {
+  re.fma(a.x, b.x);
+  re.fma(a.y, b.y);
+  im.fma(a.x, b.y);
+  im.fma(-a.y, b.x);
+}
+template <typename C>
+__device__ __forceinline__ void acc_nrm(Acc<C>& s, C a) {
+  s.fma(a.x, a.x);
+  s.fma(a.y, a.y);
+}
+
 template <int NS>
 __device__ __forceinline__ void block_reduce_store(double (&v)[NS], double* out) {
   __shared__ double red[NS][kThreads / 32];
@@ -177,10 +215,10 @@ __global__ void k_bicg_dot_rv(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n
   double acc[2] = {0.0, 0.0};
   if (!ks[b].done) {
     const int64_t o = (int64_t)b * n3;
-    double2 a = make_double2(0.0, 0.0);
-    VEC_LOOP(n3) a = cdot_acc(a, to_d(kv.rhat[o + i]), to_d(kv.v[o + i]));
-    acc[0] = a.x;
-    acc[1] = a.y;
+    Acc<C> re, im;
+    VEC_LOOP(n3) acc_cdot(re, im, kv.rhat[o + i], kv.v[o + i]);
+    acc[0] = re.get();
+    acc[1] = im.get();
   }
   double t[2];
   if (last_block_totals<2>(acc, rb, b, t) && threadIdx.x == 0) {
@@ -202,11 +240,13 @@ __global__ void k_bicg_s(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
     using R = typename RealOf<C>::t;
     const C al = mk((R)k.alpha.x, (R)k.alpha.y);
     const int64_t o = (int64_t)b * n3;
+    Acc<C> ss;
     VEC_LOOP(n3) {
       const C s = csub(kv.r[o + i], cmul(al, kv.v[o + i]));
       kv.s[o + i] = s;
-      acc[0] = nrm_acc(acc[0], to_d(s));
+      acc_nrm(ss, s);
     }
+    acc[0] = ss.get();
   }
   double t[1];
   if (last_block_totals<1>(acc, rb, b, t) && threadIdx.x == 0) {
@@ -223,16 +263,15 @@ __global__ void k_bicg_dot_ts(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n
   double acc[3] = {0.0, 0.0, 0.0};
   if (!ks[b].done) {
     const int64_t o = (int64_t)b * n3;
-    double2 a = make_double2(0.0, 0.0);
-    double tt = 0.0;
+    Acc<C> re, im, tt;
     VEC_LOOP(n3) {
-      const double2 tv = to_d(kv.t[o + i]);
-      a = cdot_acc(a, tv, to_d(kv.s[o + i]));
-      tt = nrm_acc(tt, tv);
+      const C tv = kv.t[o + i];
+      acc_cdot(re, im, tv, kv.s[o + i]);
+      acc_nrm(tt, tv);
     }
-    acc[0] = a.x;
-    acc[1] = a.y;
-    acc[2] = tt;
+    acc[0] = re.get();
+    acc[1] = im.get();
+    acc[2] = tt.get();
   }
   double t[3];
   if (last_block_totals<3>(acc, rb, b, t) && threadIdx.x == 0) {
@@ -254,8 +293,7 @@ __global__ void k_bicg_xr(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
     const C al = mk((R)k.alpha.x, (R)k.alpha.y), om = mk((R)k.omega.x, (R)k.omega.y);
     const bool half = (k.done == 3);
     const int64_t o = (int64_t)b * n3;
-    double2 a = make_double2(0.0, 0.0);
-    double rr = 0.0;
+    Acc<C> re, im, rr;
     VEC_LOOP(n3) {
       const C sv = kv.s[o + i];
       C xv = cadd(kv.x[o + i], cmul(al, kv.p[o + i]));
@@ -266,12 +304,12 @@ __global__ void k_bicg_xr(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
       }
       kv.x[o + i] = xv;
       kv.r[o + i] = rv;
-      a = cdot_acc(a, to_d(kv.rhat[o + i]), to_d(rv));
-      rr = nrm_acc(rr, to_d(rv));
+      acc_cdot(re, im, kv.rhat[o + i], rv);
+      acc_nrm(rr, rv);
     }
-    acc[0] = a.x;
-    acc[1] = a.y;
-    acc[2] = rr;
+    acc[0] = re.get();
+    acc[1] = im.get();
+    acc[2] = rr.get();
   }
   double t[3];
   if (last_block_totals<3>(acc, rb, b, t) && threadIdx.x == 0) {
@@ -325,11 +363,13 @@ __global__ void k_ccg_start(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3)
   double acc[1] = {0.0};
   if (!ks[b].done) {
     const int64_t o = (int64_t)b * n3;
+    Acc<C> zz;
     VEC_LOOP(n3) {
       const C z = kv.s[o + i];
       kv.p[o + i] = z;
-      acc[0] = nrm_acc(acc[0], to_d(z));
+      acc_nrm(zz, z);
     }
+    acc[0] = zz.get();
   }
   double t[1];
   if (last_block_totals<1>(acc, rb, b, t) && threadIdx.x == 0) {
@@ -347,7 +387,9 @@ __global__ void k_norm_v(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
   double acc[1] = {0.0};
   if (!ks[b].done) {
     const int64_t o = (int64_t)b * n3;
-    VEC_LOOP(n3) acc[0] = nrm_acc(acc[0], to_d(kv.v[o + i]));
+    Acc<C> ww;
+    VEC_LOOP(n3) acc_nrm(ww, kv.v[o + i]);
+    acc[0] = ww.get();
   }
   double t[1];
   if (last_block_totals<1>(acc, rb, b, t) && threadIdx.x == 0) {
@@ -368,6 +410,7 @@ __global__ void k_ccg_xr(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
     using R = typename RealOf<C>::t;
     const R al = (R)k.alpha.x;
     const int64_t o = (int64_t)b * n3;
+    Acc<C> rr;
     VEC_LOOP(n3) {
       const C pv = kv.p[o + i], wv = kv.v[o + i];
       C xv = kv.x[o + i], rv = kv.r[o + i];
@@ -375,8 +418,9 @@ __global__ void k_ccg_xr(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
       rv.x -= al * wv.x; rv.y -= al * wv.y;
       kv.x[o + i] = xv;
       kv.r[o + i] = rv;
-      acc[0] = nrm_acc(acc[0], to_d(rv));
+      acc_nrm(rr, rv);
     }
+    acc[0] = rr.get();
   }
   double t[1];
   if (last_block_totals<1>(acc, rb, b, t) && threadIdx.x == 0) {
@@ -395,7 +439,9 @@ __global__ void k_norm_s(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
   double acc[1] = {0.0};
   if (!ks[b].done) {
     const int64_t o = (int64_t)b * n3;
-    VEC_LOOP(n3) acc[0] = nrm_acc(acc[0], to_d(kv.s[o + i]));
+    Acc<C> zz;
+    VEC_LOOP(n3) acc_nrm(zz, kv.s[o + i]);
+    acc[0] = zz.get();
   }
   double t[1];
   if (last_block_totals<1>(acc, rb, b, t) && threadIdx.x == 0) {

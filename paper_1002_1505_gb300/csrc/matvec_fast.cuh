@@ -20,8 +20,24 @@ template <typename C>
 __device__ __forceinline__ C conjc(C a) { a.y = -a.y; return a; }
 
 template <typename C>
+__device__ __forceinline__ void load6(const C* __restrict__ gh, C (&g)[6]) {
+  if constexpr (sizeof(C) == 8) {  // 48 bytes, 16-byte aligned: three 128-bit loads
+    const float4* q = reinterpret_cast<const float4*>(gh);
+    const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+    g[0] = make_float2(a.x, a.y); g[1] = make_float2(a.z, a.w);
+    g[2] = make_float2(b.x, b.y); g[3] = make_float2(b.z, b.w);
+    g[4] = make_float2(c.x, c.y); g[5] = make_float2(c.z, c.w);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) g[i] = gh[i];
+  }
+}
+
+template <typename C>
 __device__ __forceinline__ void gmul3(const C* __restrict__ gh, C& v0, C& v1, C& v2) {
-  const C g0 = gh[0], g1 = gh[1], g2 = gh[2], g3 = gh[3], g4 = gh[4], g5 = gh[5];
+  C gg[6];
+  load6(gh, gg);
+  const C g0 = gg[0], g1 = gg[1], g2 = gg[2], g3 = gg[3], g4 = gg[4], g5 = gg[5];
   const C u0 = cadd(cadd(cmul(g0, v0), cmul(g1, v1)), cmul(g2, v2));
   const C u1 = cadd(cadd(cmul(g1, v0), cmul(g3, v1)), cmul(g4, v2));
   const C u2 = cadd(cadd(cmul(g2, v0), cmul(g4, v1)), cmul(g5, v2));
@@ -169,9 +185,9 @@ __global__ void __launch_bounds__(256) k_x_inv(Geom g, MvData<C> d, const C* __r
 }
 
 // ------------------------------------------------------------------ fused y-z plane (3-pass schedule)
-// grid (nrhs, px), block 512.  smem: twy[PY] | twz[PZ] | pl[PZ*3][PY+1] (row (z,c) = z*3 + c)
-template <typename C, int PY, int PZ>
-__global__ void __launch_bounds__(512) k_yz_plane(Geom g, MvData<C> d) {
+// grid (nrhs, px), block NT.  smem: twy[PY] | twz[PZ] | pl[PZ*3][PY+1] (row (z,c) = z*3 + c)
+template <typename C, int PY, int PZ, int NT>
+__global__ void __launch_bounds__(NT) k_yz_plane(Geom g, MvData<C> d) {
   constexpr int RAy = Shape<PY>::RA, LBy = Shape<PY>::LB, Hy = Shape<PY>::H;
   constexpr int RAz = Shape<PZ>::RA, LBz = Shape<PZ>::LB, Hz = Shape<PZ>::H;
   constexpr int RP = PY + 1;
@@ -620,13 +636,14 @@ Err launch_x_inv(const Geom& g, const MvData<C>& d, const C* p, C* ap, int nrhs,
 
 // complex64 only: a complex128 plane does not fit in shared memory at these sizes
 template <typename C>
-Err launch_plane(const Geom& g, const MvData<C>& d, int nrhs, cudaStream_t st) {
+Err launch_plane(const Geom& g, const MvData<C>& d, int nrhs, int nt, cudaStream_t st) {
   if constexpr (sizeof(C) == 8) {
     const size_t sm = plane_fast_smem<C>(g);
     const dim3 grid(nrhs, g.px);
 #define DDA_CASE(A, B)                                               \
     if (g.py == A && g.pz == B) {                                    \
-      k_yz_plane<C, A, B><<<grid, 512, sm, st>>>(g, d);              \
+      if (nt == 768) k_yz_plane<C, A, B, 768><<<grid, 768, sm, st>>>(g, d); \
+      else k_yz_plane<C, A, B, 512><<<grid, 512, sm, st>>>(g, d);    \
       DDA_CU(cudaGetLastError());                                    \
       return Err::Ok();                                              \
     }
@@ -684,7 +701,9 @@ void optin_all(int smax) {
   DDA_FAST_LENGTHS(DDA_CASE)
 #undef DDA_CASE
   if constexpr (sizeof(C) == 8) {
-#define DDA_CASE(A, B) cudaFuncSetAttribute(k_yz_plane<C, A, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+#define DDA_CASE(A, B)                                                                                    \
+  cudaFuncSetAttribute(k_yz_plane<C, A, B, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);     \
+  cudaFuncSetAttribute(k_yz_plane<C, A, B, 768>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
     DDA_FAST_PLANES(DDA_CASE)
 #undef DDA_CASE
   }
@@ -699,7 +718,7 @@ Err launch_matvec_fast(const Geom& g, const MvData<C>& d, const MvTune& t, const
   DDA_TRY(launch_x_fwd<C>(g, d, p, nrhs, conj, st));
   mark_pass(pass++, st);
   if (t.plane) {
-    DDA_TRY(launch_plane<C>(g, d, nrhs, st));
+    DDA_TRY(launch_plane<C>(g, d, nrhs, t.thr_p, st));
     mark_pass(pass++, st);
     add_launches(3);
   } else {

@@ -22,5 +22,6 @@ void choose_fast_schedule(const Geom& g, bool c64, int smax, MvTune* t) {
   }
   (void)cs;
   t->plane = c64 && fast::fast_plane_pair(g.py, g.pz) && fast::plane_fast_smem<float2>(g) <= (size_t)smax;
+  t->plane_ok = t->plane;
 }
 }  // namespace dda

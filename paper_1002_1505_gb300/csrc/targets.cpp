@@ -196,7 +196,9 @@ bool is_smooth235(int v) {
 }
 
 // Stage list: a leading radix 2 (pruned stage for zero-padded data), then the
-// remaining power of two in radix-8/4 stages, then radix 3 and 5 stages.
+// remaining power of two as radix-8 stages with one radix-4 or radix-2 stage
+// for the remainder (a radix 8 right after the leading radix 2 keeps the
+// register sub-blocks of the second pass short), then radix 3 and 5 stages.
 Err make_plan(int L, FftPlan* out) {
   if (L < 2 || (L % 2) != 0 || !is_smooth235(L))
     return Err::make(DDA_EINVAL, "FFT length must be even and a product of 2, 3 and 5");
@@ -210,10 +212,7 @@ Err make_plan(int L, FftPlan* out) {
   std::vector<int> r2;
   while (a >= 3) { r2.push_back(8); a -= 3; }
   if (a == 2) r2.push_back(4);
-  else if (a == 1) {
-    if (!r2.empty()) { r2.back() = 4; r2.push_back(4); }
-    else r2.push_back(2);
-  }
+  else if (a == 1) r2.push_back(2);
   for (int r : r2) p.radix[k++] = r;
   while (rest % 3 == 0) { rest /= 3; p.radix[k++] = 3; }
   while (rest % 5 == 0) { rest /= 5; p.radix[k++] = 5; }

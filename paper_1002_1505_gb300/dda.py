@@ -74,6 +74,7 @@ def _load():
         "dda_kernel_launches": (ctypes.c_ulonglong, []),
         "dda_profile_matvec": (I, [P, I, I, I, P, P]),
         "dda_matvec_noalloc": (I, [P, P, P, I, I]),
+        "dda_schedule_info": (I, [P, I, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -252,6 +253,13 @@ def dda_profile_matvec(ctx: "Context", nrhs: int, dtype: int = DDA_C64, iters: i
     npass = ctypes.c_int()
     ctx._check(LIB.dda_profile_matvec(ctx._h, int(nrhs), int(dtype), int(iters), _ptr(ms), ctypes.byref(npass)))
     return ms[:npass.value]
+
+
+def dda_schedule_info(ctx: "Context", dtype: int = DDA_C64):
+    """(passes, fast, plane_threads, tuned_nrhs) of the product's current schedule."""
+    info = np.zeros(4, dtype=np.int32)
+    ctx._check(LIB.dda_schedule_info(ctx._h, int(dtype), _ptr(info)))
+    return tuple(int(v) for v in info)
 
 
 def dda_version() -> str:

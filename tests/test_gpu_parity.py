@@ -119,6 +119,33 @@ def test_fast_and_generic_engines_agree(D, monkeypatch):
     assert err <= 2e-6, err
 
 
+@pytest.mark.parametrize("sched", ["generic", "fast5", "plane512", "plane768", None])
+def test_every_schedule_matches_direct_rows(D, monkeypatch, sched):
+    """Each launch schedule the autotuner can pick, pinned through DDA_SCHEDULE, on the 64x48x32 grid."""
+    if sched:
+        monkeypatch.setenv("DDA_SCHEDULE", sched)
+    w = W.ELLIPSOID64
+    ctx = _ctx(D, w)
+    prob = _oracle_problem(w)
+    rows = np.sort(np.random.default_rng(7).choice(ctx.n, 16, replace=False))
+    for dt, tol in ((torch.complex64, 1e-5), (torch.complex128, 1e-12)):
+        p = _rand_p(ctx.nrhs, ctx.n, 10, dt)
+        ap = torch.empty_like(p)
+        ctx.dda_matvec(p, ap)
+        torch.cuda.synchronize()
+        info = D.dda_schedule_info(ctx, D.DDA_C64 if dt == torch.complex64 else D.DDA_C128)
+        if sched == "fast5":
+            assert info[0] == 5 and info[1] == 1
+        if sched in ("plane512", "plane768") and dt == torch.complex64:
+            assert info[0] == 3 and info[2] == int(sched[-3:])
+        for b in range(ctx.nrhs):
+            pb = p[b].cpu().numpy().astype(np.complex128)
+            ref = oint.matvec_direct(prob.target.r, prob.kd, prob.rhs[b].inv_alpha, pb, rows=rows)
+            got = ap[b].cpu().numpy().astype(np.complex128)[:, rows]
+            err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            assert err <= tol, (sched, dt, b, err)
+
+
 def test_matvec_nondefault_pad_and_tail_tiles(D):
     # odd box sizes against a padded grid larger than 2N (pruned FFT inputs shorter than L/2)
     w = W.Workload("ell_pad", "ELLIPSOID", (11, 13, 6), 1.4 + 0.2j, 2.0, "GKDLDR", W.uniform_orientations(1, 21),

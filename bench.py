@@ -32,7 +32,7 @@ import numpy as np  # noqa: E402
 from paper_1002_1505_gb300 import workloads as W  # noqa: E402
 
 WORKLOADS = {"ellipsoid64": W.ELLIPSOID64, "prism48": W.PRISM48, "hexprism160": W.HEXPRISM160,
-             "sphere12": W.SPHERE12, "au_block": W.AU_BLOCK}
+             "sphere12": W.SPHERE12, "au_block": W.AU_BLOCK, "mixed": None}
 MUELLER_DIRS = [(0.0, 0.0), (math.pi / 2, 0.0), (math.pi, 0.0), (math.pi / 2, math.pi / 2)]
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 METRIC = "FFT-conv A.P matvecs/s and solve time/orientation @1e-5 residual vs plain GPU"
@@ -181,6 +181,78 @@ def cpu_baseline(w, budget_s=15.0):
                       f"{w.name}, {dt:.1f} s"}
 
 
+def run_mixed(args):
+    """Uneven mixed batch (spheres D = 16..64, three cylinders; |m| kd = 0.5; 2 orientations x 2
+    polarizations each) solved concurrently with dda_solve_batch, against the same targets solved
+    one after another."""
+    import torch
+    from paper_1002_1505_gb300 import dda as D
+    ws = W.mixed_batch()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctxs, kds = [], []
+    for w in ws:
+        c = D.Context(0, stream)
+        c.dda_setup_shape(w.shape, w.shpar)
+        ctxs.append(c)
+        kds.append(0.5 / abs(w.m))
+    ps = [torch.zeros((len(w.orientations) * w.iorth, 3, c.n), dtype=torch.complex128, device="cuda")
+          for w, c in zip(ws, ctxs)]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def setup_all():
+        for w, c, kd in zip(ws, ctxs, kds):
+            c.dda_set_incident(kd, w.orientations, [[q[0], q[1]] for q in w.e01], w.iorth)
+            c.dda_build_green_fft()
+            c.dda_set_polarizability(w.prescription, w.m)
+
+    def step(concurrent=True):
+        setup_all()
+        if concurrent:
+            reps, sts, overall = D.dda_solve_batch(ctxs, ps, precision="MIXED", tol=1e-5, maxit=3000)
+            assert overall == D.DDA_OK, sts
+        else:
+            reps = [c.dda_solve(p, precision="MIXED", tol=1e-5, maxit=3000)[0] for c, p in zip(ctxs, ps)]
+        for c, p in zip(ctxs, ps):
+            c.dda_cross_sections(p)
+        return sum(r[0]["matvecs"] * len(r) for r in reps), reps
+
+    def timed(k, concurrent):
+        tot, mv = 0.0, 0
+        for _ in range(k):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m, reps = step(concurrent)
+            torch.cuda.synchronize()
+            tot += time.perf_counter() - t0
+            mv += m
+        return tot * 1e3, mv, reps
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(0)
+    k0 = D.dda_kernel_launches()
+    ms, mv, reps = timed(args.steps, True)
+    launches = D.dda_kernel_launches() - k0
+    clk = clocks.stop()
+    seq_ms, _, _ = timed(max(1, args.steps // 2), False)
+    seq_ms /= max(1, args.steps // 2)
+    n_ori = sum(len(w.orientations) for w in ws)
+    line = {"metric": METRIC, "value": mv / (ms / 1e3), "unit": "matvecs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
+            "config": {"workload": "mixed batch: " + ", ".join(w.name for w in ws),
+                       "n_dipoles": [c.n for c in ctxs], "nrhs_total": sum(len(r) for r in reps),
+                       "tol": 1e-5, "l2": "flushed (512 MB write) before every step", "parallelism": "replicas x1"},
+            "solve_ms_per_orientation": ms / args.steps / n_ori,
+            "sequential_ms_per_step": seq_ms, "concurrency_speedup": seq_ms / (ms / args.steps),
+            "schedules": [D.dda_schedule_info(c, D.DDA_C64) for c in ctxs],
+            "gpu_launches": int(launches), "clocks": clk,
+            "note": "wall-clock per step (host threads drive one stream per target)"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -194,6 +266,9 @@ def main():
                     help="use only the first N orientations of the workload (smaller profiling runs)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
+    if w is None:
+        run_mixed(args)
+        return
     if args.orientations > 0:
         import dataclasses
         w = dataclasses.replace(w, name=f"{w.name}[:{args.orientations}]",

@@ -201,6 +201,22 @@ typedef struct {
  * RHS missed tol within maxit (p_dev and rep still hold the last iterate). */
 DDA_API dda_status dda_solve(dda_ctx *ctx, const dda_solve_opts *opt, void *p_dev, dda_solve_report *rep);
 
+/* Solve several targets at once (mixed batches: targets of uneven grid sizes
+ * on one device).  ctxs[i] are distinct contexts on the same
+ * device, each fully set up (target, incidence, Green tensor, alpha) with its
+ * own product schedule; p_devs[i] their complex128 [nrhs_i][3][N_i] buffers;
+ * reps[i] host arrays of nrhs_i reports (or reps = NULL); statuses host array
+ * of nctx statuses (or NULL).  Every target runs the same algorithm as
+ * dda_solve, each replaying its iterations as its own CUDA graph on its own
+ * stream from its own host thread, so the targets' kernels share the GPU
+ * concurrently and small targets fill SMs that one target alone leaves idle.
+ * Product schedules are autotuned one target at a time before the concurrent
+ * part starts, so the tuner's timings are not disturbed by the other targets.
+ * Returns DDA_OK if every target succeeded, else the first failing status.
+ * Returns after all targets finished. */
+DDA_API dda_status dda_solve_batch(dda_ctx *const *ctxs, int nctx, const dda_solve_opts *opt, void *const *p_devs,
+                                   dda_solve_report *const *reps, dda_status *statuses);
+
 /* Efficiencies and Mueller matrices for a solved P (complex128 [nrhs][3][N]).
  * q_out: host nrhs x 4 doubles (Q_ext, Q_abs, Q_sca = Q_ext - Q_abs, Q_pha),
  * Q = C / (pi a_eff^2), formulas of Draine 1988 as used by the guide.

@@ -4,6 +4,7 @@
 // against complex128 true residuals) and the observables.
 #include <array>
 #include <chrono>
+#include <thread>
 #include <map>
 #include <mutex>
 #include <cstdlib>
@@ -1348,4 +1349,57 @@ dda_status dda_schedule_info(dda_ctx* c, int dtype, int32_t info[4]) {
   info[2] = t.plane ? t.thr_p : 0;
   info[3] = c->tuned_nrhs[dtype == DDA_C64 ? 0 : 1];
   return DDA_OK;
+}
+
+dda_status dda_solve_batch(dda_ctx* const* ctxs, int nctx, const dda_solve_opts* opt, void* const* p_devs,
+                           dda_solve_report* const* reps, dda_status* statuses) {
+  if (!ctxs || nctx < 1 || !opt || !p_devs) return DDA_EINVAL;
+  for (int i = 0; i < nctx; ++i) {
+    if (!ctxs[i] || !p_devs[i]) return DDA_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(ctxs[i], Err::make(DDA_EINVAL, "a context appears twice in the batch"));
+  }
+  // tune every target's product schedules alone first (timings free of contention)
+  for (int i = 0; i < nctx; ++i) {
+    dda_ctx* c = ctxs[i];
+    if (!c->have_alpha || !c->have_green)
+      return fail(c, Err::make(DDA_ESTATE, "set target, incidence, Green tensor and alpha first"));
+    Err e = set_dev(c);
+    if (e.ok()) e = ensure_tuned<double2>(c, c->nrhs);
+    if (e.ok() && opt->precision != DDA_PREC_C128) e = ensure_tuned<float2>(c, c->nrhs);
+    if (e.ok() && c->stream && cudaStreamSynchronize(c->stream) != cudaSuccess)
+      e = Err::make(DDA_ECUDA, "stream synchronize failed");
+    if (!e.ok()) return fail(c, e);
+  }
+  // each target gets a stream of its own for the concurrent part (ordered after its caller's stream)
+  std::vector<cudaStream_t> user(nctx);
+  for (int i = 0; i < nctx; ++i) {
+    dda_ctx* c = ctxs[i];
+    user[i] = c->stream;
+    if (!c->own_stream && cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(c, Err::make(DDA_ECUDA, "stream creation failed"));
+    if (!c->ev && cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess)
+      return fail(c, Err::make(DDA_ECUDA, "event creation failed"));
+    cudaEventRecord(c->ev, user[i]);
+    cudaStreamWaitEvent(c->own_stream, c->ev, 0);
+    c->stream = c->own_stream;
+  }
+  std::vector<dda_status> st(nctx, DDA_OK);
+  std::vector<std::thread> pool;
+  pool.reserve(nctx);
+  for (int i = 0; i < nctx; ++i) {
+    pool.emplace_back([&, i]() {
+      dda_solve_opts o = *opt;
+      o.use_graph = 1;
+      st[i] = dda_solve(ctxs[i], &o, p_devs[i], reps ? reps[i] : nullptr);
+    });
+  }
+  for (auto& t : pool) t.join();
+  for (int i = 0; i < nctx; ++i) ctxs[i]->stream = user[i];
+  dda_status first = DDA_OK;
+  for (int i = 0; i < nctx; ++i) {
+    if (statuses) statuses[i] = st[i];
+    if (first == DDA_OK && st[i] != DDA_OK) first = st[i];
+  }
+  return first;
 }

@@ -75,6 +75,7 @@ def _load():
         "dda_profile_matvec": (I, [P, I, I, I, P, P]),
         "dda_matvec_noalloc": (I, [P, P, P, I, I]),
         "dda_schedule_info": (I, [P, I, P]),
+        "dda_solve_batch": (I, [P, I, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -260,6 +261,26 @@ def dda_schedule_info(ctx: "Context", dtype: int = DDA_C64):
     info = np.zeros(4, dtype=np.int32)
     ctx._check(LIB.dda_schedule_info(ctx._h, int(dtype), _ptr(info)))
     return tuple(int(v) for v in info)
+
+
+def dda_solve_batch(ctxs, ps, solver="BICGSTAB", precision="MIXED", tol=1e-5, maxit=1000, inner_tol=0.0,
+                    timeout_ms=0.0, check_every=8, normal_eq=False):
+    """Solve several contexts concurrently; ps[i] complex128 [nrhs_i,3,N_i] CUDA tensors.
+
+    Returns (list of per-context report lists, list of statuses, overall status)."""
+    n = len(ctxs)
+    for c, p in zip(ctxs, ps):
+        c._dev_check(p, DDA_C128)
+    o = dda_solve_opts(SOLVERS[solver.upper()], PRECISIONS[precision.upper()], tol, maxit, inner_tol, timeout_ms,
+                       0, check_every, int(bool(normal_eq)), 1)
+    handles = (ctypes.c_void_p * n)(*[c._h.value for c in ctxs])
+    bufs = (ctypes.c_void_p * n)(*[p.data_ptr() for p in ps])
+    rep_arrays = [(dda_solve_report * c.nrhs)() for c in ctxs]
+    reps = (ctypes.c_void_p * n)(*[ctypes.cast(r, ctypes.c_void_p).value for r in rep_arrays])
+    sts = (ctypes.c_int * n)(*([-1] * n))
+    overall = LIB.dda_solve_batch(handles, n, ctypes.byref(o), bufs, reps, sts)
+    out = [[{k: getattr(r, k) for k, _ in dda_solve_report._fields_} for r in ra] for ra in rep_arrays]
+    return out, list(sts), overall
 
 
 def dda_version() -> str:

@@ -248,6 +248,71 @@ DDA_API dda_status dda_profile_matvec(dda_ctx *ctx, int nrhs, int dtype, int ite
  * (0 if none), info[3] = RHS count the choice was tuned for (0 = not tuned). */
 DDA_API dda_status dda_schedule_info(dda_ctx *ctx, int dtype, int32_t info[4]);
 
+/* ---------------------------------------------------------------------------
+ * Learned warm start (the guide has no counterpart: the solver accepts any
+ * initial guess, and a network trained on the solver's own solutions gives a
+ * better one).  A small 3-D U-Net maps per-voxel features of a target on a grid
+ * of dims (x, y, z), each a multiple of 8 covering the box, to the local field
+ * E_loc = alpha^{-1} P; the warm start is P0 = alpha E_loc.  Tensors are FP32,
+ * channels-last [batch][z][y][x][channel], on the device.
+ * ------------------------------------------------------------------------- */
+typedef struct dda_unet dda_unet;
+
+/* Network with cin input and cout output channels and level widths ch[0..3]
+ * (each 1..64), He-uniform weights from seed; work on `cuda_stream`. */
+DDA_API dda_status dda_unet_create(dda_unet **out, int device, void *cuda_stream, int cin, int cout, const int32_t ch[4],
+                                   uint64_t seed);
+DDA_API void dda_unet_destroy(dda_unet *net);
+DDA_API const char *dda_unet_last_error(const dda_unet *net);
+DDA_API int64_t dda_unet_nparams(const dda_unet *net);
+/* Copy the FP32 parameters (which = 0) or their last gradients (which = 1) to
+ * host memory, layer by layer W[tap][cin][cout] then b.  Synchronizes. */
+DDA_API dda_status dda_unet_get_params(dda_unet *net, float *host, int which);
+DDA_API dda_status dda_unet_set_params(dda_unet *net, const float *host);
+/* y = net(x) for `batch` grids of the given dims. */
+DDA_API dda_status dda_unet_forward(dda_unet *net, const float *x_dev, float *y_dev, int batch, const int32_t dims[3]);
+/* Masked mean-squared error against t (mask [batch][z][y][x] of 0/1) and its
+ * gradient w.r.t. every parameter (kept in the network for dda_unet_adamw);
+ * *loss_out receives the loss.  Synchronizes. */
+DDA_API dda_status dda_unet_loss_grad(dda_unet *net, const float *x_dev, const float *t_dev, const float *mask_dev,
+                                      int batch, const int32_t dims[3], double *loss_out);
+/* Training with an arbitrary loss: forward pass keeping the activations for
+ * dda_unet_backward (same batch and dims), weight times the masked
+ * mean-squared error's value and gradient gy_dev = dL/dy (overwritten), and
+ * the backward pass from a given dL/dy (gradients kept for dda_unet_adamw).
+ * Synchronizing calls: dda_unet_mse. */
+DDA_API dda_status dda_unet_forward_train(dda_unet *net, const float *x_dev, float *y_dev, int batch,
+                                          const int32_t dims[3]);
+DDA_API dda_status dda_unet_mse(dda_unet *net, const float *y_dev, const float *t_dev, const float *mask_dev,
+                                int batch, const int32_t dims[3], double weight, float *gy_dev, double *loss_out);
+DDA_API dda_status dda_unet_backward(dda_unet *net, const float *gy_dev, int batch, const int32_t dims[3]);
+/* One AdamW step (decoupled weight decay wd) with the stored gradients. */
+DDA_API dda_status dda_unet_adamw(dda_unet *net, double lr, double beta1, double beta2, double eps, double wd);
+/* Features of every RHS of ctx on the grid: x_dev [nrhs][z][y][x][9] =
+ * [occupied, (Re eps - 1)/4, Im eps / 2, Re/Im of E_inc x, y, z], zero outside
+ * the target.  offset = position of box index (0,0,0) in the grid (NULL = centred). */
+DDA_API dda_status dda_unet_features(dda_ctx *ctx, float *x_dev, const int32_t dims[3], const int32_t offset[3]);
+/* Training targets from a solution p_dev (complex128 [nrhs][3][N]):
+ * t_dev [nrhs][z][y][x][6] = Re/Im of alpha^{-1} P (residual = 0) or of
+ * alpha^{-1} P - E_inc (residual = 1: the network learns the correction to the
+ * local field being the incident field), mask_dev [nrhs][z][y][x]. */
+DDA_API dda_status dda_unet_targets(dda_ctx *ctx, const void *p_dev, float *t_dev, float *mask_dev,
+                                    const int32_t dims[3], const int32_t offset[3], int residual);
+/* Initial guess p_dev (complex128 [nrhs][3][N]) = alpha * E_loc from network
+ * output y_dev [nrhs][z][y][x][6], E_loc = y (+ E_inc when residual = 1); pass
+ * it to dda_solve with warm_start = 1. */
+DDA_API dda_status dda_unet_warm_start(dda_ctx *ctx, const float *y_dev, const int32_t dims[3],
+                                       const int32_t offset[3], int residual, void *p_dev);
+
+/* Residual loss of a network output for ctx: with P0 = alpha (E_inc + y)
+ * (residual-mode output y_dev [nrhs][z][y][x][6] on the grid), adds
+ * weight * sum_b |E_b - A P0_b|^2 / |E_b|^2 to *loss_out and its gradient to
+ * gy_dev (same layout, accumulated), computed with the complex64 product and
+ * its adjoint A^H x = conj(A conj x).  This trains the network on the quantity
+ * the solver's convergence depends on.  Synchronizes. */
+DDA_API dda_status dda_unet_residual_grad(dda_ctx *ctx, const float *y_dev, const int32_t dims[3],
+                                          const int32_t offset[3], double weight, float *gy_dev, double *loss_out);
+
 /* Library build string (static storage). */
 DDA_API const char *dda_version(void);
 

@@ -17,7 +17,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdda.so")
 SOURCES = ["api.cu", "matvec.cu", "matvec_fast_c64.cu", "matvec_fast_c128.cu", "krylov.cu", "observables.cu",
-           "targets.cpp"]
+           "unet.cu", "targets.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

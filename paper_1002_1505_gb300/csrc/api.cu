@@ -63,6 +63,11 @@ struct dda_ctx {
   std::vector<cd> ia;                 // nrhs x ncomp x 3
   double2* d_ia128 = nullptr;
   float2* d_ia64 = nullptr;
+  std::vector<cd> eps;                // permittivity m^2 per composition
+  float2* d_eps = nullptr;
+  float2* d_nnv = nullptr;            // residual-loss vectors (three complex64 [nrhs][3][N])
+  double* d_nnpart = nullptr;
+  double* d_nnw = nullptr;
 
   // workspaces (grown on demand)
   float2* d_w64 = nullptr;
@@ -885,6 +890,11 @@ dda_status dda_set_polarizability(dda_ctx* c, int presc, const double* m_reim, i
       cudaMemcpy(c->d_ia64, h64.data(), sizeof(float2) * ia.size(), cudaMemcpyHostToDevice);
     }
     c->ia = std::move(ia);
+    c->eps.resize(ncomp);
+    for (int m = 0; m < ncomp; ++m) {
+      const cd mm(m_reim[2 * m], m_reim[2 * m + 1]);
+      c->eps[m] = mm * mm;
+    }
     c->presc = presc;
     c->ncomp = ncomp;
     c->have_alpha = true;
@@ -1402,4 +1412,118 @@ dda_status dda_solve_batch(dda_ctx* const* ctxs, int nctx, const dda_solve_opts*
     if (first == DDA_OK && st[i] != DDA_OK) first = st[i];
   }
   return first;
+}
+
+// ------------------------------------------------------------------ learned warm start: context side
+namespace {
+Err grid_place(dda_ctx* c, const int32_t dims[3], const int32_t off_in[3], int32_t off[3]) {
+  for (int a = 0; a < 3; ++a) {
+    if (dims[a] < c->tgt.box[a] || dims[a] % 8)
+      return Err::make(DDA_EINVAL, "network grid must cover the box and be a multiple of 8 per axis");
+    off[a] = off_in ? off_in[a] : (dims[a] - c->tgt.box[a]) / 2;
+    if (off[a] < 0 || off[a] + c->tgt.box[a] > dims[a]) return Err::make(DDA_EINVAL, "box does not fit at offset");
+  }
+  return Err::Ok();
+}
+}  // namespace
+
+dda_status dda_unet_features(dda_ctx* c, float* x_dev, const int32_t dims[3], const int32_t offset[3]) {
+  if (!c || !x_dev || !dims) return DDA_EINVAL;
+  if (!c->have_alpha) return fail(c, Err::make(DDA_ESTATE, "set target, incidence and alpha first"));
+  int32_t off[3];
+  Err e = grid_place(c, dims, offset, off);
+  if (e.ok()) e = need_device(c);
+  if (e.ok()) e = set_dev(c);
+  if (e.ok()) e = ensure_einc(c);
+  std::vector<float2> eps(c->ncomp);
+  for (int m = 0; m < c->ncomp; ++m) eps[m] = make_float2((float)c->eps[m].real(), (float)c->eps[m].imag());
+  if (e.ok()) e = grow(c, &c->d_eps, sizeof(float2) * c->ncomp);
+  if (e.ok() && cudaMemcpy(c->d_eps, eps.data(), sizeof(float2) * c->ncomp, cudaMemcpyHostToDevice) != cudaSuccess)
+    e = Err::make(DDA_ECUDA, "copy failed");
+  if (e.ok())
+    e = dda::unet_features(c->d_ijk, c->n, c->comp_valid ? c->d_comp : nullptr, c->d_eps, c->d_e128, c->nrhs, dims,
+                           off, x_dev, c->stream);
+  return e.ok() ? DDA_OK : fail(c, e);
+}
+
+dda_status dda_unet_targets(dda_ctx* c, const void* p_dev, float* t_dev, float* mask_dev, const int32_t dims[3],
+                            const int32_t offset[3], int residual) {
+  if (!c || !p_dev || !t_dev || !mask_dev || !dims) return DDA_EINVAL;
+  if (!c->have_alpha) return fail(c, Err::make(DDA_ESTATE, "set target, incidence and alpha first"));
+  int32_t off[3];
+  Err e = grid_place(c, dims, offset, off);
+  if (e.ok()) e = need_device(c);
+  if (e.ok()) e = set_dev(c);
+  if (e.ok() && residual) e = ensure_einc(c);
+  if (e.ok())
+    e = dda::unet_targets(c->d_ijk, c->n, c->comp_valid ? c->d_comp : nullptr, c->d_ia128, c->ncomp,
+                          (const double2*)p_dev, residual ? c->d_e128 : nullptr, c->nrhs, dims, off, t_dev, mask_dev,
+                          c->stream);
+  return e.ok() ? DDA_OK : fail(c, e);
+}
+
+dda_status dda_unet_warm_start(dda_ctx* c, const float* y_dev, const int32_t dims[3], const int32_t offset[3],
+                               int residual, void* p_dev) {
+  if (!c || !p_dev || !y_dev || !dims) return DDA_EINVAL;
+  if (!c->have_alpha) return fail(c, Err::make(DDA_ESTATE, "set target, incidence and alpha first"));
+  int32_t off[3];
+  Err e = grid_place(c, dims, offset, off);
+  if (e.ok()) e = need_device(c);
+  if (e.ok()) e = set_dev(c);
+  if (e.ok() && residual) e = ensure_einc(c);
+  if (e.ok())
+    e = dda::unet_warm(c->d_ijk, c->n, c->comp_valid ? c->d_comp : nullptr, c->d_ia128, c->ncomp, y_dev,
+                       residual ? c->d_e128 : nullptr, c->nrhs, dims, off, (double2*)p_dev, c->stream);
+  return e.ok() ? DDA_OK : fail(c, e);
+}
+
+dda_status dda_unet_residual_grad(dda_ctx* c, const float* y_dev, const int32_t dims[3], const int32_t offset[3],
+                                  double weight, float* gy_dev, double* loss_out) {
+  if (!c || !y_dev || !gy_dev || !dims) return DDA_EINVAL;
+  if (!c->have_alpha || !c->have_green)
+    return fail(c, Err::make(DDA_ESTATE, "set target, incidence, Green tensor and alpha first"));
+  int32_t off[3];
+  Err e = grid_place(c, dims, offset, off);
+  if (e.ok()) e = need_device(c);
+  if (e.ok()) e = set_dev(c);
+  if (e.ok()) e = ensure_einc(c);
+  const int nrhs = c->nrhs;
+  const int64_t n3 = 3 * c->n, el = (int64_t)nrhs * n3;
+  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((n3 + 2047) / 2048, 256));
+  if (e.ok()) e = grow(c, &c->d_nnv, sizeof(float2) * 3 * el);
+  if (e.ok()) e = grow(c, &c->d_nnpart, sizeof(double) * 2 * nblk * nrhs);
+  if (e.ok()) e = grow(c, &c->d_nnw, sizeof(double) * nrhs);
+  if (e.ok()) e = ensure_tuned<float2>(c, nrhs);
+  if (!e.ok()) return fail(c, e);
+  float2 *p0 = c->d_nnv, *r = c->d_nnv + el, *g = c->d_nnv + 2 * el;
+  const uint8_t* comp = c->comp_valid ? c->d_comp : nullptr;
+  e = dda::unet_guess64(c->d_ijk, c->n, comp, c->d_ia128, c->ncomp, y_dev, c->d_e128, nrhs, dims, off, p0, c->stream);
+  if (e.ok()) e = matvec<float2>(c, p0, r, nrhs, 0, false);
+  if (e.ok()) e = dda::unet_resid64(c->d_e128, r, nrhs, n3, c->d_nnpart, nblk, c->stream);
+  if (e.ok()) e = matvec<float2>(c, r, g, nrhs, 0, true);
+  std::vector<double> part(2 * (size_t)nblk * nrhs), w(nrhs);
+  if (e.ok()) {
+    if (cudaMemcpyAsync(part.data(), c->d_nnpart, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      e = Err::make(DDA_ECUDA, "residual copy failed");
+  }
+  if (!e.ok()) return fail(c, e);
+  double L = 0.0;
+  for (int b = 0; b < nrhs; ++b) {
+    double rr = 0, ee = 0;
+    for (int k = 0; k < nblk; ++k) {
+      rr += part[((size_t)b * nblk + k) * 2];
+      ee += part[((size_t)b * nblk + k) * 2 + 1];
+    }
+    w[b] = ee > 0 ? weight / ee : 0.0;  // loss term weight * |r_b|^2 / |E_b|^2
+    L += w[b] * rr;
+  }
+  if (cudaMemcpyAsync(c->d_nnw, w.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+    return fail(c, Err::make(DDA_ECUDA, "weight copy failed"));
+  e = dda::unet_resgrad(c->d_ijk, c->n, comp, c->d_ia128, c->ncomp, g, c->d_nnw, nrhs, dims, off, gy_dev, c->stream);
+  if (e.ok() && cudaStreamSynchronize(c->stream) != cudaSuccess) e = Err::make(DDA_ECUDA, "sync failed");
+  if (!e.ok()) return fail(c, e);
+  if (loss_out) *loss_out = L;
+  return DDA_OK;
 }

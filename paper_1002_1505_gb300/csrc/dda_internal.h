@@ -209,4 +209,19 @@ Err farfield(const int32_t* ijk, const double* origin3, const double* nhat /*[nr
              const double2* p, int nrhs, int ndir, int64_t n, double2* out, double2* part, int nblk,
              cudaStream_t st);
 
+// ------------------------------------------------------------------ learned warm start glue (unet.cu)
+Err unet_features(const int32_t* ijk, int64_t n, const uint8_t* comp, const float2* eps, const double2* e, int nrhs,
+                  const int32_t dims[3], const int32_t off[3], float* x, cudaStream_t st);
+Err unet_targets(const int32_t* ijk, int64_t n, const uint8_t* comp, const double2* ia, int ncomp, const double2* p,
+                 const double2* e, int nrhs, const int32_t dims[3], const int32_t off[3], float* t, float* mask,
+                 cudaStream_t st);
+Err unet_warm(const int32_t* ijk, int64_t n, const uint8_t* comp, const double2* ia, int ncomp, const float* y,
+              const double2* e, int nrhs, const int32_t dims[3], const int32_t off[3], double2* p, cudaStream_t st);
+
+Err unet_guess64(const int32_t* ijk, int64_t n, const uint8_t* comp, const double2* ia, int ncomp, const float* y,
+                 const double2* e, int nrhs, const int32_t dims[3], const int32_t off[3], float2* p, cudaStream_t st);
+Err unet_resid64(const double2* e, float2* r, int nrhs, int64_t n3, double* part, int nblk, cudaStream_t st);
+Err unet_resgrad(const int32_t* ijk, int64_t n, const uint8_t* comp, const double2* ia, int ncomp, const float2* g,
+                 const double* wb, int nrhs, const int32_t dims[3], const int32_t off[3], float* gy, cudaStream_t st);
+
 }  // namespace dda

@@ -1,0 +1,1108 @@
+// Learned warm start for the Krylov solve: a small 3-D U-Net trained on the
+// solver's own solutions (the guide has no learned component; the solver
+// accepts any initial guess, and a better one saves iterations).
+//
+// Network (channels-last tensors [B][Z][Y][X][C], FP32 in memory):
+//   enc1: cin->C1, C1->C1 | pool | enc2: C1->C2, C2->C2 | pool | enc3: C2->C3, C3->C3 | pool
+//   bottleneck: C3->C4, C4->C4 | up | dec3: C4+C3->C3, C3->C3 | up | dec2: C3+C2->C2, C2->C2
+//   | up | dec1: C2+C1->C1, C1->C1 | head 1x1x1: C1->cout
+// 3x3x3 zero-padded convolutions with ReLU, 2x2x2 average pooling, nearest
+// x2 upsampling, skips concatenated as [upsampled, skip].
+//
+// Convolutions are implicit GEMMs on the tensor cores (mma.sync m16n8k16,
+// bfloat16 operands, FP32 accumulation): the input activation (or incoming
+// gradient) is rounded to bfloat16 as it is loaded, weights are kept as an FP32
+// master copy and repacked to bfloat16 fragments after every update.
+//   forward     y[v, co]  = sum_{tap, ci} x[v + tap, ci] W[tap, ci, co] + b[co]
+//   input grad  gx[v, ci] = sum_{tap, co} g[v - tap, co] W[tap, ci, co]   (same kernel, flipped
+//                           taps and transposed weights)
+//   weight grad gW[tap, ci, co] = sum_v x[v + tap, ci] g[v, co]            (voxels as the K axis,
+//                           per-chunk partials summed in a fixed order: deterministic)
+// AdamW (decoupled weight decay) updates the FP32 master parameters.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "dda_internal.h"
+
+namespace dda {
+namespace nn {
+
+constexpr int kTaps = 27;
+constexpr int kConvThreads = 128;  // 4 warps, 16 voxels each
+constexpr int kVoxPerCta = 64;
+constexpr int kWgradChunk = 4096;  // voxels reduced by one weight-gradient CTA
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint2 b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
+}
+
+struct Dims {
+  int Z, Y, X;  // per sample
+  __host__ __device__ int64_t nvox() const { return (int64_t)Z * Y * X; }
+};
+
+__device__ __forceinline__ int64_t neighbour(int64_t v, const Dims& d, int tap, int ntaps, bool flip) {
+  if (ntaps == 1) return v;
+  int t = flip ? (kTaps - 1 - tap) : tap;
+  const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+  const int64_t nv = d.nvox();
+  const int64_t b = v / nv, r = v - b * nv;
+  const int x = (int)(r % d.X);
+  const int64_t r2 = r / d.X;
+  const int y = (int)(r2 % d.Y), z = (int)(r2 / d.Y);
+  const int zz = z + dz, yy = y + dy, xx = x + dx;
+  if (zz < 0 || zz >= d.Z || yy < 0 || yy >= d.Y || xx < 0 || xx >= d.X) return -1;
+  return b * nv + ((int64_t)zz * d.Y + yy) * d.X + xx;
+}
+
+// Pack W[tap][ci][co] (FP32, leading dims cin, cout) into mma B fragments
+// wp[tap][kc][nt][lane] = {b0, b1}.  transpose: the GEMM reads W^T (input
+// gradient): element (k = co, n = ci) of tap t is W[t][ci][co]; the input
+// gradient kernel walks the neighbours in the opposite direction instead.
+__global__ void k_pack(const float* __restrict__ w, int taps, int cin, int cout, int kc_n, int nt_n, bool transpose,
+                       uint2* __restrict__ wp) {
+  const int total = taps * kc_n * nt_n * 32;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int lane = i % 32;
+    int r = i / 32;
+    const int nt = r % nt_n;
+    r /= nt_n;
+    const int kc = r % kc_n, tap = r / kc_n;
+    const int g = lane >> 2, t = lane & 3;
+    const int n = nt * 8 + g;
+    float v[4];
+    const int ks[4] = {kc * 16 + 2 * t, kc * 16 + 2 * t + 1, kc * 16 + 2 * t + 8, kc * 16 + 2 * t + 9};
+    for (int q = 0; q < 4; ++q) {
+      const int k = ks[q];
+      float val = 0.f;
+      if (!transpose) {
+        if (k < cin && n < cout) val = w[((int64_t)tap * cin + k) * cout + n];
+      } else {  // K axis = co (0..cout), N axis = ci (0..cin)
+        if (k < cout && n < cin) val = w[((int64_t)tap * cin + n) * cout + k];
+      }
+      v[q] = val;
+    }
+    wp[i] = make_uint2(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]));
+  }
+}
+
+// Implicit-GEMM convolution: y[v, 0:cout] = (relu?)(sum_tap x[nb(v, tap), 0:cin] W + bias)
+// x has xs channels per voxel (reads channel range [0, cin)); y has ys channels, written at [0, cout).
+// flip selects the input-gradient neighbour direction.  grid (ceil(V/64)), block 128.
+template <int NT>
+__global__ void __launch_bounds__(kConvThreads) k_conv(const float* __restrict__ x, int xs, int cin, int kc_n,
+                                                     const uint2* __restrict__ wp, int taps, bool flip,
+                                                     const float* __restrict__ bias, float* __restrict__ y, int ys,
+                                                     int cout, bool relu, Dims d, int64_t V) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int64_t v0 = (int64_t)blockIdx.x * kVoxPerCta + warp * 16;
+  const int64_t r0 = v0 + g, r1 = v0 + g + 8;
+  float acc[NT][4];
+#pragma unroll
+  for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+  for (int tap = 0; tap < taps; ++tap) {
+    const int64_t n0 = (r0 < V) ? neighbour(r0, d, tap, taps, flip) : -1;
+    const int64_t n1 = (r1 < V) ? neighbour(r1, d, tap, taps, flip) : -1;
+    const float* x0 = n0 >= 0 ? x + n0 * xs : nullptr;
+    const float* x1 = n1 >= 0 ? x + n1 * xs : nullptr;
+    for (int kc = 0; kc < kc_n; ++kc) {
+      const int c0 = kc * 16 + 2 * t;
+      auto ld = [&](const float* p, int c) -> float { return (p && c < cin) ? __ldg(p + c) : 0.f; };
+      uint32_t a[4];
+      a[0] = pack_bf16(ld(x0, c0), ld(x0, c0 + 1));
+      a[1] = pack_bf16(ld(x1, c0), ld(x1, c0 + 1));
+      a[2] = pack_bf16(ld(x0, c0 + 8), ld(x0, c0 + 9));
+      a[3] = pack_bf16(ld(x1, c0 + 8), ld(x1, c0 + 9));
+      const uint2* wb = wp + ((int64_t)(tap * kc_n + kc) * NT) * 32 + lane;
+#pragma unroll
+      for (int n = 0; n < NT; ++n) mma_bf16(acc[n], a, __ldg(wb + n * 32));
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < NT; ++n) {
+    const int co = n * 8 + 2 * t;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t r = h ? r1 : r0;
+      if (r >= V) continue;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int c = co + e;
+        if (c >= cout) continue;
+        float val = acc[n][2 * h + e] + (bias ? bias[c] : 0.f);
+        if (relu) val = fmaxf(val, 0.f);
+        y[r * ys + c] = val;
+      }
+    }
+  }
+}
+
+// Weight gradient partials: part[chunk][tap][kc*16 + row][nt*8 + col] = sum over the chunk's voxels
+// of x[nb(v, tap), ci] g[v, co].  grid (nchunk, taps, kc_n), block 128.
+template <int NT>
+__global__ void __launch_bounds__(kConvThreads) k_wgrad(const float* __restrict__ x, int xs, int cin,
+                                                      const float* __restrict__ gy, int gs, int cout, int taps,
+                                                      Dims d, int64_t V, float* __restrict__ part, int kc_n) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int chunk = blockIdx.x, tap = blockIdx.y, kc = blockIdx.z;
+  const int64_t vbeg = (int64_t)chunk * kWgradChunk;
+  const int64_t vend = min(V, vbeg + kWgradChunk);
+  float acc[NT][4];
+#pragma unroll
+  for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+  const int ci_a = kc * 16 + g, ci_b = kc * 16 + g + 8;
+  for (int64_t vb = vbeg + warp * 16; vb < vend; vb += 4 * 16) {
+    // voxel columns of this k-step: vb + 2t, +1, +8, +9
+    const int64_t vc[4] = {vb + 2 * t, vb + 2 * t + 1, vb + 2 * t + 8, vb + 2 * t + 9};
+    float xa[4], xb[4];
+    int64_t vv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      vv[q] = vc[q] < vend ? vc[q] : -1;
+      const int64_t nb = vv[q] >= 0 ? neighbour(vv[q], d, tap, taps, false) : -1;
+      xa[q] = (nb >= 0 && ci_a < cin) ? __ldg(x + nb * xs + ci_a) : 0.f;
+      xb[q] = (nb >= 0 && ci_b < cin) ? __ldg(x + nb * xs + ci_b) : 0.f;
+    }
+    uint32_t a[4];
+    a[0] = pack_bf16(xa[0], xa[1]);
+    a[1] = pack_bf16(xb[0], xb[1]);
+    a[2] = pack_bf16(xa[2], xa[3]);
+    a[3] = pack_bf16(xb[2], xb[3]);
+#pragma unroll
+    for (int n = 0; n < NT; ++n) {
+      const int co = n * 8 + g;
+      float gv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) gv[q] = (vv[q] >= 0 && co < cout) ? __ldg(gy + vv[q] * gs + co) : 0.f;
+      const uint2 b = make_uint2(pack_bf16(gv[0], gv[1]), pack_bf16(gv[2], gv[3]));
+      mma_bf16(acc[n], a, b);
+    }
+  }
+  // reduce the 4 warps in shared memory, fixed order
+  __shared__ float red[4][16][NT * 8];
+#pragma unroll
+  for (int n = 0; n < NT; ++n) {
+    red[warp][g][n * 8 + 2 * t] = acc[n][0];
+    red[warp][g][n * 8 + 2 * t + 1] = acc[n][1];
+    red[warp][g + 8][n * 8 + 2 * t] = acc[n][2];
+    red[warp][g + 8][n * 8 + 2 * t + 1] = acc[n][3];
+  }
+  __syncthreads();
+  float* out = part + (((int64_t)chunk * taps + tap) * kc_n * 16 + kc * 16) * (NT * 8);
+  for (int i = threadIdx.x; i < 16 * NT * 8; i += blockDim.x) {
+    const int row = i / (NT * 8), col = i % (NT * 8);
+    out[(int64_t)row * (NT * 8) + col] = red[0][row][col] + red[1][row][col] + red[2][row][col] + red[3][row][col];
+  }
+}
+
+// gw[tap][ci][co] = sum_chunk part[chunk][tap][ci][co] (ci < cin, co < cout)
+__global__ void k_wgrad_sum(const float* __restrict__ part, int nchunk, int taps, int cinp, int coutp, int cin,
+                            int cout, float* __restrict__ gw) {
+  const int total = taps * cin * cout;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int co = i % cout;
+    const int r = i / cout;
+    const int ci = r % cin, tap = r / cin;
+    float s = 0.f;
+    for (int c = 0; c < nchunk; ++c) s += part[(((int64_t)c * taps + tap) * cinp + ci) * coutp + co];
+    gw[i] = s;
+  }
+}
+
+// gb[co] = sum_v g[v, co]  (one block per channel, fixed-order tree)
+__global__ void k_colsum(const float* __restrict__ g, int gs, int cout, int64_t V, float* __restrict__ gb) {
+  const int co = blockIdx.x;
+  double s = 0.0;
+  for (int64_t v = threadIdx.x; v < V; v += blockDim.x) s += g[v * gs + co];
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) gb[co] = (float)red[0];
+}
+
+// g *= (out > 0)
+__global__ void k_relu_bwd(float* __restrict__ g, const float* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!(out[i] > 0.f)) g[i] = 0.f;
+}
+
+// average pool 2x2x2: y[b, z, y, x, c] = mean of the 8 children; d = output dims
+__global__ void k_pool(const float* __restrict__ x, float* __restrict__ y, int C, Dims d, int B) {
+  const int64_t total = (int64_t)B * d.nvox() * C;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    int64_t v = i / C;
+    const int xx = (int)(v % d.X);
+    v /= d.X;
+    const int yy = (int)(v % d.Y);
+    v /= d.Y;
+    const int zz = (int)(v % d.Z);
+    const int64_t b = v / d.Z;
+    const int X2 = 2 * d.X, Y2 = 2 * d.Y, Z2 = 2 * d.Z;
+    float s = 0.f;
+    for (int q = 0; q < 8; ++q) {
+      const int z = 2 * zz + (q >> 2), y2 = 2 * yy + ((q >> 1) & 1), x2 = 2 * xx + (q & 1);
+      s += x[(((b * Z2 + z) * Y2 + y2) * X2 + x2) * C + c];
+    }
+    y[i] = s * 0.125f;
+  }
+}
+
+// pool backward: gx (fine, C channels) += g (coarse) / 8 ; accumulate selects += vs =
+__global__ void k_pool_bwd(const float* __restrict__ g, float* __restrict__ gx, int C, Dims d_fine, int B,
+                           bool accumulate) {
+  const int64_t total = (int64_t)B * d_fine.nvox() * C;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    int64_t v = i / C;
+    const int x = (int)(v % d_fine.X);
+    v /= d_fine.X;
+    const int y = (int)(v % d_fine.Y);
+    v /= d_fine.Y;
+    const int z = (int)(v % d_fine.Z);
+    const int64_t b = v / d_fine.Z;
+    const int Xc = d_fine.X / 2, Yc = d_fine.Y / 2, Zc = d_fine.Z / 2;
+    const float val = 0.125f * g[(((b * Zc + z / 2) * Yc + y / 2) * Xc + x / 2) * C + c];
+    gx[i] = accumulate ? gx[i] + val : val;
+  }
+}
+
+// nearest upsample x2 of src (C channels, coarse dims) into channels [0, C) of dst (dst_c channels, fine dims)
+__global__ void k_up(const float* __restrict__ src, int C, float* __restrict__ dst, int dst_c, Dims d_fine, int B) {
+  const int64_t total = (int64_t)B * d_fine.nvox() * C;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    int64_t v = i / C;
+    const int x = (int)(v % d_fine.X);
+    v /= d_fine.X;
+    const int y = (int)(v % d_fine.Y);
+    v /= d_fine.Y;
+    const int z = (int)(v % d_fine.Z);
+    const int64_t b = v / d_fine.Z;
+    const int Xc = d_fine.X / 2, Yc = d_fine.Y / 2, Zc = d_fine.Z / 2;
+    const int64_t fine = ((b * d_fine.Z + z) * d_fine.Y + y) * d_fine.X + x;
+    dst[fine * dst_c + c] = src[(((b * Zc + z / 2) * Yc + y / 2) * Xc + x / 2) * C + c];
+  }
+}
+
+// upsample backward: g_src (coarse, C) = sum of the 8 children of channels [0, C) of g (fine, g_c channels)
+__global__ void k_up_bwd(const float* __restrict__ g, int g_c, float* __restrict__ gsrc, int C, Dims d_coarse, int B) {
+  const int64_t total = (int64_t)B * d_coarse.nvox() * C;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    int64_t v = i / C;
+    const int xx = (int)(v % d_coarse.X);
+    v /= d_coarse.X;
+    const int yy = (int)(v % d_coarse.Y);
+    v /= d_coarse.Y;
+    const int zz = (int)(v % d_coarse.Z);
+    const int64_t b = v / d_coarse.Z;
+    const int X2 = 2 * d_coarse.X, Y2 = 2 * d_coarse.Y, Z2 = 2 * d_coarse.Z;
+    float s = 0.f;
+    for (int q = 0; q < 8; ++q) {
+      const int z = 2 * zz + (q >> 2), y = 2 * yy + ((q >> 1) & 1), x = 2 * xx + (q & 1);
+      s += g[(((b * Z2 + z) * Y2 + y) * X2 + x) * g_c + c];
+    }
+    gsrc[i] = s;
+  }
+}
+
+// copy channels: dst[v, doff + c] = src[v, soff + c] for c < C (accumulate: +=)
+__global__ void k_copy_ch(const float* __restrict__ src, int sc, int soff, float* __restrict__ dst, int dc, int doff,
+                          int C, int64_t V, bool accumulate) {
+  const int64_t total = V * C;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const int64_t v = i / C;
+    const float val = src[v * sc + soff + c];
+    float* o = dst + v * dc + doff + c;
+    *o = accumulate ? *o + val : val;
+  }
+}
+
+// masked MSE: loss partials and gradient g = 2 m (y - t) / (count * C)
+__global__ void k_loss(const float* __restrict__ y, const float* __restrict__ t, const float* __restrict__ mask, int C,
+                       int64_t V, double inv_cnt, float* __restrict__ g, double* __restrict__ part) {
+  double s = 0.0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+    const float m = mask[v];
+    for (int c = 0; c < C; ++c) {
+      const float diff = y[v * C + c] - t[v * C + c];
+      s += (double)m * diff * diff;
+      g[v * C + c] = (float)(2.0 * m * diff * inv_cnt);
+    }
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0] * inv_cnt;
+}
+
+// AdamW on the flat FP32 parameter vector
+__global__ void k_adamw(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                        float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float wd, float c1,
+                        float c2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / c1, vh = vi / c2;
+    p[i] -= lr * (mh / (sqrtf(vh) + eps) + wd * p[i]);
+  }
+}
+
+// Network input per voxel of the box grid (zero outside the target), channels:
+// [1, (Re eps - 1)/4, Im eps / 2, Re E_x, Im E_x, Re E_y, Im E_y, Re E_z, Im E_z]
+__global__ void k_features(const int32_t* __restrict__ ijk, int64_t n, const uint8_t* __restrict__ comp,
+                           const float2* __restrict__ eps, const double2* __restrict__ e, int nrhs, Dims d, int ox,
+                           int oy, int oz, float* __restrict__ x) {
+  const int b = blockIdx.y;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int xx = ijk[3 * j] + ox, yy = ijk[3 * j + 1] + oy, zz = ijk[3 * j + 2] + oz;
+    const int64_t v = (int64_t)b * d.nvox() + ((int64_t)zz * d.Y + yy) * d.X + xx;
+    const float2 ep = eps[comp ? comp[j] : 0];
+    float* o = x + v * 9;
+    o[0] = 1.f;
+    o[1] = 0.25f * (ep.x - 1.f);
+    o[2] = 0.5f * ep.y;
+    for (int c = 0; c < 3; ++c) {
+      const double2 ev = e[((int64_t)b * 3 + c) * n + j];
+      o[3 + 2 * c] = (float)ev.x;
+      o[4 + 2 * c] = (float)ev.y;
+    }
+  }
+}
+
+// Training target E_loc = alpha^{-1} P (Re, Im per component), minus E_inc when `e` is given
+// (residual mode), and the occupancy mask
+__global__ void k_targets(const int32_t* __restrict__ ijk, int64_t n, const uint8_t* __restrict__ comp,
+                          const double2* __restrict__ ia, int ncomp, const double2* __restrict__ p,
+                          const double2* __restrict__ e, int nrhs, Dims d, int ox, int oy, int oz,
+                          float* __restrict__ t, float* __restrict__ mask) {
+  const int b = blockIdx.y;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int xx = ijk[3 * j] + ox, yy = ijk[3 * j + 1] + oy, zz = ijk[3 * j + 2] + oz;
+    const int64_t v = (int64_t)b * d.nvox() + ((int64_t)zz * d.Y + yy) * d.X + xx;
+    const int cc = comp ? comp[j] : 0;
+    for (int c = 0; c < 3; ++c) {
+      const double2 a = ia[((int64_t)b * ncomp + cc) * 3 + c];
+      const double2 pv = p[((int64_t)b * 3 + c) * n + j];
+      double re = a.x * pv.x - a.y * pv.y, im = a.x * pv.y + a.y * pv.x;
+      if (e) {
+        const double2 ev = e[((int64_t)b * 3 + c) * n + j];
+        re -= ev.x;
+        im -= ev.y;
+      }
+      t[v * 6 + 2 * c] = (float)re;
+      t[v * 6 + 2 * c + 1] = (float)im;
+    }
+    mask[v] = 1.f;
+  }
+}
+
+// Warm start P0 = alpha E_loc = E_loc / alpha^{-1} at the target's sites, E_loc = y (+ E_inc when `e`
+// is given: residual mode)
+__global__ void k_warm(const int32_t* __restrict__ ijk, int64_t n, const uint8_t* __restrict__ comp,
+                       const double2* __restrict__ ia, int ncomp, const float* __restrict__ y,
+                       const double2* __restrict__ e, int nrhs, Dims d, int ox, int oy, int oz,
+                       double2* __restrict__ p) {
+  const int b = blockIdx.y;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int xx = ijk[3 * j] + ox, yy = ijk[3 * j + 1] + oy, zz = ijk[3 * j + 2] + oz;
+    const int64_t v = (int64_t)b * d.nvox() + ((int64_t)zz * d.Y + yy) * d.X + xx;
+    const int cc = comp ? comp[j] : 0;
+    for (int c = 0; c < 3; ++c) {
+      const double2 a = ia[((int64_t)b * ncomp + cc) * 3 + c];
+      double er = y[v * 6 + 2 * c], ei = y[v * 6 + 2 * c + 1];
+      if (e) {
+        const double2 ev = e[((int64_t)b * 3 + c) * n + j];
+        er += ev.x;
+        ei += ev.y;
+      }
+      const double den = a.x * a.x + a.y * a.y;
+      p[((int64_t)b * 3 + c) * n + j] = make_double2((er * a.x + ei * a.y) / den, (ei * a.x - er * a.y) / den);
+    }
+  }
+}
+
+inline int blocks_for(int64_t n, int th = 256) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + th - 1) / th, 152 * 8)); }
+
+}  // namespace nn
+}  // namespace dda
+
+// ============================================================================ network object
+struct dda_unet {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int cin = 0, cout = 0, ch[4] = {0, 0, 0, 0};
+  struct Layer {
+    int taps, cin, cout, kc_n, nt_n, cin_t_kc, cout_t_nt;  // kc/nt for forward; *_t for transposed
+    int64_t woff, boff;                                      // offsets into the flat parameter vector
+    uint2* wp = nullptr;                                     // forward fragments
+    uint2* wt = nullptr;                                     // transposed+flipped fragments (input grad)
+  };
+  std::vector<Layer> layers;
+  int64_t nparams = 0;
+  float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+  int64_t adam_step = 0;
+  // activation workspace (grown on demand)
+  float* ws = nullptr;
+  size_t ws_bytes = 0;
+  float* part = nullptr;
+  size_t part_bytes = 0;
+  double* lpart = nullptr;
+  double* h_loss = nullptr;
+};
+
+namespace {
+
+using dda::Err;
+
+dda_status ufail(dda_unet* n, const Err& e) {
+  if (n) n->err = e.msg;
+  return e.code;
+}
+
+int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+Err repack(dda_unet* n) {
+  for (auto& L : n->layers) {
+    const int tot = L.taps * L.kc_n * L.nt_n * 32;
+    dda::nn::k_pack<<<dda::nn::blocks_for(tot), 256, 0, n->stream>>>(n->p + L.woff, L.taps, L.cin, L.cout, L.kc_n,
+                                                                       L.nt_n, false, L.wp);
+    const int tot2 = L.taps * L.cin_t_kc * L.cout_t_nt * 32;
+    dda::nn::k_pack<<<dda::nn::blocks_for(tot2), 256, 0, n->stream>>>(n->p + L.woff, L.taps, L.cin, L.cout,
+                                                                        L.cin_t_kc, L.cout_t_nt, true, L.wt);
+    DDA_CU(cudaGetLastError());
+    dda::add_launches(2);
+  }
+  return Err::Ok();
+}
+
+// y = conv(x) for layer L; x has xs channels (uses the first cin), y gets ys channels (writes first cout)
+Err conv(dda_unet* n, const dda_unet::Layer& L, const float* x, int xs, float* y, int ys, bool relu, dda::nn::Dims d,
+         int B, bool transposed) {
+  const int64_t V = (int64_t)B * d.nvox();
+  const int blocks = (int)((V + dda::nn::kVoxPerCta - 1) / dda::nn::kVoxPerCta);
+  const int kc_n = transposed ? L.cin_t_kc : L.kc_n;
+  const int nt_n = transposed ? L.cout_t_nt : L.nt_n;
+  const int cin = transposed ? L.cout : L.cin;
+  const int cout = transposed ? L.cin : L.cout;
+  const uint2* w = transposed ? L.wt : L.wp;
+  const float* bias = transposed ? nullptr : n->p + L.boff;
+  switch (nt_n) {
+#define CASE(NT)                                                                                                   \
+  case NT:                                                                                                         \
+    dda::nn::k_conv<NT><<<blocks, dda::nn::kConvThreads, 0, n->stream>>>(x, xs, cin, kc_n, w, L.taps, transposed, \
+                                                                         bias, y, ys, cout, relu, d, V);           \
+    break;
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11) CASE(12) CASE(13)
+    CASE(14) CASE(15) CASE(16)
+#undef CASE
+    default: return Err::make(DDA_EUNSUPPORTED, "layer wider than 128 channels");
+  }
+  DDA_CU(cudaGetLastError());
+  dda::add_launches(1);
+  return Err::Ok();
+}
+
+Err grow_ws(dda_unet* n, float** p, size_t* cap, size_t bytes) {
+  if (bytes <= *cap) return Err::Ok();
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  DDA_CU(cudaMalloc((void**)p, bytes));
+  *cap = bytes;
+  return Err::Ok();
+}
+
+// weight and bias gradients of layer L from input x (xs channels) and output gradient gy (gs channels)
+Err wgrad(dda_unet* n, const dda_unet::Layer& L, const float* x, int xs, const float* gy, int gs, dda::nn::Dims d,
+          int B) {
+  const int64_t V = (int64_t)B * d.nvox();
+  const int nchunk = (int)((V + dda::nn::kWgradChunk - 1) / dda::nn::kWgradChunk);
+  const size_t need = sizeof(float) * (size_t)nchunk * L.taps * L.kc_n * 16 * L.nt_n * 8;
+  DDA_TRY(grow_ws(n, &n->part, &n->part_bytes, need));
+  dim3 grid(nchunk, L.taps, L.kc_n);
+  switch (L.nt_n) {
+#define CASE(NT)                                                                                                    \
+  case NT:                                                                                                          \
+    dda::nn::k_wgrad<NT><<<grid, dda::nn::kConvThreads, 0, n->stream>>>(x, xs, L.cin, gy, gs, L.cout, L.taps, d, V, \
+                                                                        n->part, L.kc_n);                           \
+    break;
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+    default: return Err::make(DDA_EUNSUPPORTED, "layer wider than 64 channels");
+  }
+  DDA_CU(cudaGetLastError());
+  const int tot = L.taps * L.cin * L.cout;
+  dda::nn::k_wgrad_sum<<<dda::nn::blocks_for(tot), 256, 0, n->stream>>>(n->part, nchunk, L.taps, L.kc_n * 16,
+                                                                        L.nt_n * 8, L.cin, L.cout, n->g + L.woff);
+  dda::nn::k_colsum<<<L.cout, 256, 0, n->stream>>>(gy, gs, L.cout, V, n->g + L.boff);
+  DDA_CU(cudaGetLastError());
+  dda::add_launches(3);
+  return Err::Ok();
+}
+
+// Activation buffers of one pass for batch B and base dims d1 (all offsets in floats).
+struct Acts {
+  float *x, *e1a, *s1, *p1, *e2a, *s2, *p2, *e3a, *s3, *p3, *ba, *bb, *c3, *d3a, *d3b, *c2, *d2a, *d2b, *c1, *d1a,
+      *d1b, *y;
+  // gradients
+  float *g_y, *g_d1b, *g_c1, *g_d2b, *g_c2, *g_d3b, *g_c3, *g_bb, *g_p3, *g_s3, *g_p2, *g_s2, *g_p1, *g_s1, *g_tmp;
+};
+
+Err layout(dda_unet* n, int B, dda::nn::Dims d1, bool with_grads, Acts* a) {
+  const int64_t V1 = (int64_t)B * d1.nvox(), V2 = V1 / 8, V3 = V2 / 8, V4 = V3 / 8;
+  const int c1 = n->ch[0], c2 = n->ch[1], c3 = n->ch[2], c4 = n->ch[3];
+  std::vector<std::pair<float**, int64_t>> list = {
+      {&a->x, V1 * n->cin}, {&a->e1a, V1 * c1}, {&a->s1, V1 * c1}, {&a->p1, V2 * c1}, {&a->e2a, V2 * c2},
+      {&a->s2, V2 * c2}, {&a->p2, V3 * c2}, {&a->e3a, V3 * c3}, {&a->s3, V3 * c3}, {&a->p3, V4 * c3},
+      {&a->ba, V4 * c4}, {&a->bb, V4 * c4}, {&a->c3, V3 * (c4 + c3)}, {&a->d3a, V3 * c3}, {&a->d3b, V3 * c3},
+      {&a->c2, V2 * (c3 + c2)}, {&a->d2a, V2 * c2}, {&a->d2b, V2 * c2}, {&a->c1, V1 * (c2 + c1)},
+      {&a->d1a, V1 * c1}, {&a->d1b, V1 * c1}, {&a->y, V1 * n->cout}};
+  if (with_grads) {
+    const int64_t cmax = std::max({(int64_t)n->cout, (int64_t)c1 + c2, (int64_t)c4 + c3, (int64_t)c3 + c2});
+    std::vector<std::pair<float**, int64_t>> gl = {
+        {&a->g_y, V1 * n->cout}, {&a->g_d1b, V1 * c1}, {&a->g_c1, V1 * (c2 + c1)}, {&a->g_d2b, V2 * c2},
+        {&a->g_c2, V2 * (c3 + c2)}, {&a->g_d3b, V3 * c3}, {&a->g_c3, V3 * (c4 + c3)}, {&a->g_bb, V4 * c4},
+        {&a->g_p3, V4 * c3}, {&a->g_s3, V3 * c3}, {&a->g_p2, V3 * c2}, {&a->g_s2, V2 * c2}, {&a->g_p1, V2 * c1},
+        {&a->g_s1, V1 * c1}, {&a->g_tmp, V1 * cmax}};
+    list.insert(list.end(), gl.begin(), gl.end());
+  }
+  int64_t total = 0;
+  for (auto& e : list) total += (e.second + 63) / 64 * 64;
+  DDA_TRY(grow_ws(n, &n->ws, &n->ws_bytes, sizeof(float) * (size_t)total));
+  int64_t off = 0;
+  for (auto& e : list) {
+    *e.first = n->ws + off;
+    off += (e.second + 63) / 64 * 64;
+  }
+  return Err::Ok();
+}
+
+Err forward_pass(dda_unet* n, const Acts& a, int B, dda::nn::Dims d1) {
+  const dda::nn::Dims d2{d1.Z / 2, d1.Y / 2, d1.X / 2}, d3{d2.Z / 2, d2.Y / 2, d2.X / 2},
+      d4{d3.Z / 2, d3.Y / 2, d3.X / 2};
+  const int c1 = n->ch[0], c2 = n->ch[1], c3 = n->ch[2], c4 = n->ch[3];
+  auto& L = n->layers;
+  cudaStream_t st = n->stream;
+  using namespace dda::nn;
+  DDA_TRY(conv(n, L[0], a.x, n->cin, a.e1a, c1, true, d1, B, false));
+  DDA_TRY(conv(n, L[1], a.e1a, c1, a.s1, c1, true, d1, B, false));
+  k_pool<<<blocks_for((int64_t)B * d2.nvox() * c1), 256, 0, st>>>(a.s1, a.p1, c1, d2, B);
+  DDA_TRY(conv(n, L[2], a.p1, c1, a.e2a, c2, true, d2, B, false));
+  DDA_TRY(conv(n, L[3], a.e2a, c2, a.s2, c2, true, d2, B, false));
+  k_pool<<<blocks_for((int64_t)B * d3.nvox() * c2), 256, 0, st>>>(a.s2, a.p2, c2, d3, B);
+  DDA_TRY(conv(n, L[4], a.p2, c2, a.e3a, c3, true, d3, B, false));
+  DDA_TRY(conv(n, L[5], a.e3a, c3, a.s3, c3, true, d3, B, false));
+  k_pool<<<blocks_for((int64_t)B * d4.nvox() * c3), 256, 0, st>>>(a.s3, a.p3, c3, d4, B);
+  DDA_TRY(conv(n, L[6], a.p3, c3, a.ba, c4, true, d4, B, false));
+  DDA_TRY(conv(n, L[7], a.ba, c4, a.bb, c4, true, d4, B, false));
+  k_up<<<blocks_for((int64_t)B * d3.nvox() * c4), 256, 0, st>>>(a.bb, c4, a.c3, c4 + c3, d3, B);
+  k_copy_ch<<<blocks_for((int64_t)B * d3.nvox() * c3), 256, 0, st>>>(a.s3, c3, 0, a.c3, c4 + c3, c4, c3,
+                                                                      (int64_t)B * d3.nvox(), false);
+  DDA_TRY(conv(n, L[8], a.c3, c4 + c3, a.d3a, c3, true, d3, B, false));
+  DDA_TRY(conv(n, L[9], a.d3a, c3, a.d3b, c3, true, d3, B, false));
+  k_up<<<blocks_for((int64_t)B * d2.nvox() * c3), 256, 0, st>>>(a.d3b, c3, a.c2, c3 + c2, d2, B);
+  k_copy_ch<<<blocks_for((int64_t)B * d2.nvox() * c2), 256, 0, st>>>(a.s2, c2, 0, a.c2, c3 + c2, c3, c2,
+                                                                      (int64_t)B * d2.nvox(), false);
+  DDA_TRY(conv(n, L[10], a.c2, c3 + c2, a.d2a, c2, true, d2, B, false));
+  DDA_TRY(conv(n, L[11], a.d2a, c2, a.d2b, c2, true, d2, B, false));
+  k_up<<<blocks_for((int64_t)B * d1.nvox() * c2), 256, 0, st>>>(a.d2b, c2, a.c1, c2 + c1, d1, B);
+  k_copy_ch<<<blocks_for((int64_t)B * d1.nvox() * c1), 256, 0, st>>>(a.s1, c1, 0, a.c1, c2 + c1, c2, c1,
+                                                                      (int64_t)B * d1.nvox(), false);
+  DDA_TRY(conv(n, L[12], a.c1, c2 + c1, a.d1a, c1, true, d1, B, false));
+  DDA_TRY(conv(n, L[13], a.d1a, c1, a.d1b, c1, true, d1, B, false));
+  DDA_TRY(conv(n, L[14], a.d1b, c1, a.y, n->cout, false, d1, B, false));
+  DDA_CU(cudaGetLastError());
+  dda::add_launches(9);
+  return Err::Ok();
+}
+
+// conv backward for layer li: output activation `out` (for the ReLU mask), its gradient g_out (gs channels,
+// modified in place by the mask), input activation x (xs channels); writes the input gradient to gx (gxs ch.)
+Err conv_back(dda_unet* n, int li, const float* x, int xs, const float* out, float* g_out, int gs, float* gx, int gxs,
+              dda::nn::Dims d, int B, bool relu) {
+  const auto& L = n->layers[li];
+  const int64_t V = (int64_t)B * d.nvox();
+  if (relu) {
+    dda::nn::k_relu_bwd<<<dda::nn::blocks_for(V * gs), 256, 0, n->stream>>>(g_out, out, V * gs);
+    dda::add_launches(1);
+  }
+  DDA_TRY(wgrad(n, L, x, xs, g_out, gs, d, B));
+  if (gx) DDA_TRY(conv(n, L, g_out, gs, gx, gxs, false, d, B, true));
+  return Err::Ok();
+}
+
+Err backward_pass(dda_unet* n, const Acts& a, int B, dda::nn::Dims d1) {
+  using namespace dda::nn;
+  const Dims d2{d1.Z / 2, d1.Y / 2, d1.X / 2}, d3{d2.Z / 2, d2.Y / 2, d2.X / 2}, d4{d3.Z / 2, d3.Y / 2, d3.X / 2};
+  const int c1 = n->ch[0], c2 = n->ch[1], c3 = n->ch[2], c4 = n->ch[3];
+  cudaStream_t st = n->stream;
+  const int64_t V1 = (int64_t)B * d1.nvox(), V2 = V1 / 8, V3 = V2 / 8, V4 = V3 / 8;
+  // head (linear): input d1b
+  DDA_TRY(conv_back(n, 14, a.d1b, c1, a.y, a.g_y, n->cout, a.g_d1b, c1, d1, B, false));
+  // dec1
+  DDA_TRY(conv_back(n, 13, a.d1a, c1, a.d1b, a.g_d1b, c1, a.g_tmp, c1, d1, B, true));
+  DDA_TRY(conv_back(n, 12, a.c1, c2 + c1, a.d1a, a.g_tmp, c1, a.g_c1, c2 + c1, d1, B, true));
+  k_up_bwd<<<blocks_for(V2 * c2), 256, 0, st>>>(a.g_c1, c2 + c1, a.g_d2b, c2, d2, B);
+  k_copy_ch<<<blocks_for(V1 * c1), 256, 0, st>>>(a.g_c1, c2 + c1, c2, a.g_s1, c1, 0, c1, V1, false);
+  // dec2
+  DDA_TRY(conv_back(n, 11, a.d2a, c2, a.d2b, a.g_d2b, c2, a.g_tmp, c2, d2, B, true));
+  DDA_TRY(conv_back(n, 10, a.c2, c3 + c2, a.d2a, a.g_tmp, c2, a.g_c2, c3 + c2, d2, B, true));
+  k_up_bwd<<<blocks_for(V3 * c3), 256, 0, st>>>(a.g_c2, c3 + c2, a.g_d3b, c3, d3, B);
+  k_copy_ch<<<blocks_for(V2 * c2), 256, 0, st>>>(a.g_c2, c3 + c2, c3, a.g_s2, c2, 0, c2, V2, false);
+  // dec3
+  DDA_TRY(conv_back(n, 9, a.d3a, c3, a.d3b, a.g_d3b, c3, a.g_tmp, c3, d3, B, true));
+  DDA_TRY(conv_back(n, 8, a.c3, c4 + c3, a.d3a, a.g_tmp, c3, a.g_c3, c4 + c3, d3, B, true));
+  k_up_bwd<<<blocks_for(V4 * c4), 256, 0, st>>>(a.g_c3, c4 + c3, a.g_bb, c4, d4, B);
+  k_copy_ch<<<blocks_for(V3 * c3), 256, 0, st>>>(a.g_c3, c4 + c3, c4, a.g_s3, c3, 0, c3, V3, false);
+  // bottleneck
+  DDA_TRY(conv_back(n, 7, a.ba, c4, a.bb, a.g_bb, c4, a.g_tmp, c4, d4, B, true));
+  DDA_TRY(conv_back(n, 6, a.p3, c3, a.ba, a.g_tmp, c4, a.g_p3, c3, d4, B, true));
+  k_pool_bwd<<<blocks_for(V3 * c3), 256, 0, st>>>(a.g_p3, a.g_s3, c3, d3, B, true);
+  // enc3
+  DDA_TRY(conv_back(n, 5, a.e3a, c3, a.s3, a.g_s3, c3, a.g_tmp, c3, d3, B, true));
+  DDA_TRY(conv_back(n, 4, a.p2, c2, a.e3a, a.g_tmp, c3, a.g_p2, c2, d3, B, true));
+  k_pool_bwd<<<blocks_for(V2 * c2), 256, 0, st>>>(a.g_p2, a.g_s2, c2, d2, B, true);
+  // enc2
+  DDA_TRY(conv_back(n, 3, a.e2a, c2, a.s2, a.g_s2, c2, a.g_tmp, c2, d2, B, true));
+  DDA_TRY(conv_back(n, 2, a.p1, c1, a.e2a, a.g_tmp, c2, a.g_p1, c1, d2, B, true));
+  k_pool_bwd<<<blocks_for(V1 * c1), 256, 0, st>>>(a.g_p1, a.g_s1, c1, d1, B, true);
+  // enc1
+  DDA_TRY(conv_back(n, 1, a.e1a, c1, a.s1, a.g_s1, c1, a.g_tmp, c1, d1, B, true));
+  DDA_TRY(conv_back(n, 0, a.x, n->cin, a.e1a, a.g_tmp, c1, nullptr, 0, d1, B, true));
+  DDA_CU(cudaGetLastError());
+  dda::add_launches(9);
+  return Err::Ok();
+}
+
+Err check_dims(const int32_t dims[3]) {
+  for (int k = 0; k < 3; ++k)
+    if (dims[k] < 8 || dims[k] % 8 != 0) return Err::make(DDA_EINVAL, "network grid dims must be multiples of 8");
+  return Err::Ok();
+}
+
+}  // namespace
+
+dda_status dda_unet_create(dda_unet** out, int device, void* stream, int cin, int cout, const int32_t ch[4],
+                           uint64_t seed) {
+  if (!out || !ch || cin < 1 || cout < 1 || cin > 64 || cout > 64) return DDA_EINVAL;
+  for (int k = 0; k < 4; ++k)
+    if (ch[k] < 1 || ch[k] > 64) return DDA_EINVAL;
+  if (ch[3] + ch[2] > 128 || ch[2] + ch[1] > 128 || ch[1] + ch[0] > 128) return DDA_EINVAL;
+  *out = nullptr;
+  dda_unet* n = new (std::nothrow) dda_unet();
+  if (!n) return DDA_ENOMEM;
+  n->device = device;
+  n->stream = (cudaStream_t)stream;
+  n->cin = cin;
+  n->cout = cout;
+  for (int k = 0; k < 4; ++k) n->ch[k] = ch[k];
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete n;
+    return DDA_ECUDA;
+  }
+  const int c1 = ch[0], c2 = ch[1], c3 = ch[2], c4 = ch[3];
+  const int convs[15][3] = {{27, cin, c1}, {27, c1, c1},     {27, c1, c2},      {27, c2, c2},      {27, c2, c3},
+                            {27, c3, c3},  {27, c3, c4},     {27, c4, c4},      {27, c4 + c3, c3}, {27, c3, c3},
+                            {27, c3 + c2, c2}, {27, c2, c2}, {27, c2 + c1, c1}, {27, c1, c1},      {1, c1, cout}};
+  int64_t off = 0;
+  for (auto& cv : convs) {
+    dda_unet::Layer L;
+    L.taps = cv[0];
+    L.cin = cv[1];
+    L.cout = cv[2];
+    L.kc_n = ceil_div(L.cin, 16);
+    L.nt_n = ceil_div(L.cout, 8);
+    L.cin_t_kc = ceil_div(L.cout, 16);
+    L.cout_t_nt = ceil_div(L.cin, 8);
+    L.woff = off;
+    off += (int64_t)L.taps * L.cin * L.cout;
+    L.boff = off;
+    off += L.cout;
+    n->layers.push_back(L);
+  }
+  n->nparams = off;
+  // He-uniform initialization (fan-in = taps * cin), zero biases, deterministic from seed
+  std::vector<float> h(off, 0.f);
+  std::mt19937_64 rng(seed);
+  for (auto& L : n->layers) {
+    const double bound = std::sqrt(6.0 / (double)(L.taps * L.cin));
+    std::uniform_real_distribution<double> U(-bound, bound);
+    for (int64_t i = 0; i < (int64_t)L.taps * L.cin * L.cout; ++i) h[L.woff + i] = (float)U(rng);
+  }
+  bool ok = cudaMalloc((void**)&n->p, sizeof(float) * off) == cudaSuccess &&
+            cudaMalloc((void**)&n->g, sizeof(float) * off) == cudaSuccess &&
+            cudaMalloc((void**)&n->m, sizeof(float) * off) == cudaSuccess &&
+            cudaMalloc((void**)&n->v, sizeof(float) * off) == cudaSuccess &&
+            cudaMalloc((void**)&n->lpart, sizeof(double) * 2048) == cudaSuccess &&
+            cudaMallocHost((void**)&n->h_loss, sizeof(double) * 2048) == cudaSuccess;
+  for (auto& L : n->layers) {
+    ok = ok && cudaMalloc((void**)&L.wp, sizeof(uint2) * L.taps * L.kc_n * L.nt_n * 32) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&L.wt, sizeof(uint2) * L.taps * L.cin_t_kc * L.cout_t_nt * 32) == cudaSuccess;
+  }
+  if (!ok) {
+    dda_unet_destroy(n);
+    return DDA_ENOMEM;
+  }
+  cudaMemcpy(n->p, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice);
+  cudaMemset(n->m, 0, sizeof(float) * off);
+  cudaMemset(n->v, 0, sizeof(float) * off);
+  cudaMemset(n->g, 0, sizeof(float) * off);
+  Err e = repack(n);
+  if (!e.ok() || cudaStreamSynchronize(n->stream) != cudaSuccess) {
+    dda_unet_destroy(n);
+    return DDA_ECUDA;
+  }
+  *out = n;
+  return DDA_OK;
+}
+
+void dda_unet_destroy(dda_unet* n) {
+  if (!n) return;
+  cudaSetDevice(n->device);
+  if (n->stream) cudaStreamSynchronize(n->stream);
+  for (auto& L : n->layers) {
+    if (L.wp) cudaFree(L.wp);
+    if (L.wt) cudaFree(L.wt);
+  }
+  for (float* q : {n->p, n->g, n->m, n->v, n->ws, n->part})
+    if (q) cudaFree(q);
+  if (n->lpart) cudaFree(n->lpart);
+  if (n->h_loss) cudaFreeHost(n->h_loss);
+  delete n;
+}
+
+const char* dda_unet_last_error(const dda_unet* n) { return n ? n->err.c_str() : "null network"; }
+
+int64_t dda_unet_nparams(const dda_unet* n) { return n ? n->nparams : 0; }
+
+dda_status dda_unet_get_params(dda_unet* n, float* host, int which) {
+  if (!n || !host || which < 0 || which > 1) return DDA_EINVAL;
+  if (cudaSetDevice(n->device) != cudaSuccess || cudaStreamSynchronize(n->stream) != cudaSuccess)
+    return ufail(n, Err::make(DDA_ECUDA, "device sync failed"));
+  if (cudaMemcpy(host, which ? n->g : n->p, sizeof(float) * n->nparams, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return ufail(n, Err::make(DDA_ECUDA, "copy failed"));
+  return DDA_OK;
+}
+
+dda_status dda_unet_set_params(dda_unet* n, const float* host) {
+  if (!n || !host) return DDA_EINVAL;
+  if (cudaSetDevice(n->device) != cudaSuccess) return ufail(n, Err::make(DDA_ECUDA, "cudaSetDevice failed"));
+  if (cudaMemcpy(n->p, host, sizeof(float) * n->nparams, cudaMemcpyHostToDevice) != cudaSuccess)
+    return ufail(n, Err::make(DDA_ECUDA, "copy failed"));
+  Err e = repack(n);
+  if (!e.ok()) return ufail(n, e);
+  return DDA_OK;
+}
+
+dda_status dda_unet_forward(dda_unet* n, const float* x_dev, float* y_dev, int batch, const int32_t dims[3]) {
+  if (!n || !x_dev || !y_dev || batch < 1 || !dims) return DDA_EINVAL;
+  Err e = check_dims(dims);
+  if (!e.ok()) return ufail(n, e);
+  if (cudaSetDevice(n->device) != cudaSuccess) return ufail(n, Err::make(DDA_ECUDA, "cudaSetDevice failed"));
+  const dda::nn::Dims d1{dims[2], dims[1], dims[0]};
+  Acts a;
+  e = layout(n, batch, d1, false, &a);
+  if (e.ok()) {
+    const int64_t V1 = (int64_t)batch * d1.nvox();
+    if (cudaMemcpyAsync(a.x, x_dev, sizeof(float) * V1 * n->cin, cudaMemcpyDeviceToDevice, n->stream) != cudaSuccess)
+      e = Err::make(DDA_ECUDA, "input copy failed");
+  }
+  if (e.ok()) e = forward_pass(n, a, batch, d1);
+  if (e.ok()) {
+    const int64_t V1 = (int64_t)batch * d1.nvox();
+    if (cudaMemcpyAsync(y_dev, a.y, sizeof(float) * V1 * n->cout, cudaMemcpyDeviceToDevice, n->stream) != cudaSuccess)
+      e = Err::make(DDA_ECUDA, "output copy failed");
+  }
+  return e.ok() ? DDA_OK : ufail(n, e);
+}
+
+dda_status dda_unet_loss_grad(dda_unet* n, const float* x_dev, const float* t_dev, const float* mask_dev, int batch,
+                              const int32_t dims[3], double* loss_out) {
+  if (!n || !x_dev || !t_dev || !mask_dev || batch < 1 || !dims) return DDA_EINVAL;
+  Err e = check_dims(dims);
+  if (!e.ok()) return ufail(n, e);
+  if (cudaSetDevice(n->device) != cudaSuccess) return ufail(n, Err::make(DDA_ECUDA, "cudaSetDevice failed"));
+  const dda::nn::Dims d1{dims[2], dims[1], dims[0]};
+  const int64_t V1 = (int64_t)batch * d1.nvox();
+  Acts a;
+  e = layout(n, batch, d1, true, &a);
+  if (e.ok() && cudaMemcpyAsync(a.x, x_dev, sizeof(float) * V1 * n->cin, cudaMemcpyDeviceToDevice, n->stream) !=
+                    cudaSuccess)
+    e = Err::make(DDA_ECUDA, "input copy failed");
+  if (e.ok()) e = forward_pass(n, a, batch, d1);
+  // masked-voxel count on the host side of the device: sum the mask once
+  double cnt = 0.0;
+  if (e.ok()) {
+    std::vector<float> hm(V1);
+    if (cudaMemcpyAsync(hm.data(), mask_dev, sizeof(float) * V1, cudaMemcpyDeviceToHost, n->stream) != cudaSuccess ||
+        cudaStreamSynchronize(n->stream) != cudaSuccess)
+      e = Err::make(DDA_ECUDA, "mask copy failed");
+    for (float m : hm) cnt += m;
+    if (e.ok() && cnt <= 0) e = Err::make(DDA_EINVAL, "mask selects no voxel");
+  }
+  const int lb = 512;
+  if (e.ok()) {
+    dda::nn::k_loss<<<lb, 256, 0, n->stream>>>(a.y, t_dev, mask_dev, n->cout, V1, 1.0 / (cnt * n->cout), a.g_y,
+                                                n->lpart);
+    dda::add_launches(1);
+    e = backward_pass(n, a, batch, d1);
+  }
+  if (e.ok()) {
+    if (cudaMemcpyAsync(n->h_loss, n->lpart, sizeof(double) * lb, cudaMemcpyDeviceToHost, n->stream) != cudaSuccess ||
+        cudaStreamSynchronize(n->stream) != cudaSuccess)
+      e = Err::make(DDA_ECUDA, "loss copy failed");
+  }
+  if (!e.ok()) return ufail(n, e);
+  double L = 0.0;
+  for (int i = 0; i < lb; ++i) L += n->h_loss[i];
+  if (loss_out) *loss_out = L;
+  return DDA_OK;
+}
+
+dda_status dda_unet_adamw(dda_unet* n, double lr, double beta1, double beta2, double eps, double wd) {
+  if (!n || !(lr > 0)) return DDA_EINVAL;
+  if (cudaSetDevice(n->device) != cudaSuccess) return ufail(n, Err::make(DDA_ECUDA, "cudaSetDevice failed"));
+  n->adam_step += 1;
+  const float c1 = (float)(1.0 - std::pow(beta1, (double)n->adam_step));
+  const float c2 = (float)(1.0 - std::pow(beta2, (double)n->adam_step));
+  dda::nn::k_adamw<<<dda::nn::blocks_for(n->nparams), 256, 0, n->stream>>>(n->p, n->g, n->m, n->v, n->nparams,
+                                                                            (float)lr, (float)beta1, (float)beta2,
+                                                                            (float)eps, (float)wd, c1, c2);
+  dda::add_launches(1);
+  Err e = repack(n);
+  if (e.ok() && cudaGetLastError() != cudaSuccess) e = Err::make(DDA_ECUDA, "AdamW launch failed");
+  return e.ok() ? DDA_OK : ufail(n, e);
+}
+
+namespace dda {
+Err unet_features(const int32_t* ijk, int64_t n, const uint8_t* comp, const float2* eps, const double2* e, int nrhs,
+                  const int32_t dims[3], const int32_t off[3], float* x, cudaStream_t st) {
+  const nn::Dims d{dims[2], dims[1], dims[0]};
+  DDA_CU(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)nrhs * d.nvox() * 9, st));
+  const int nb = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  nn::k_features<<<dim3(nb, nrhs), 256, 0, st>>>(ijk, n, comp, eps, e, nrhs, d, off[0], off[1], off[2], x);
+  DDA_CU(cudaGetLastError());
+  add_launches(1);
+  return Err::Ok();
+}
+Err unet_targets(const int32_t* ijk, int64_t n, const uint8_t* comp, const double2* ia, int ncomp, const double2* p,
+                 const double2* e, int nrhs, const int32_t dims[3], const int32_t off[3], float* t, float* mask,
+                 cudaStream_t st) {
+  const nn::Dims d{dims[2], dims[1], dims[0]};
+  DDA_CU(cudaMemsetAsync(t, 0, sizeof(float) * (size_t)nrhs * d.nvox() * 6, st));
+  DDA_CU(cudaMemsetAsync(mask, 0, sizeof(float) * (size_t)nrhs * d.nvox(), st));
+  const int nb = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  nn::k_targets<<<dim3(nb, nrhs), 256, 0, st>>>(ijk, n, comp, ia, ncomp, p, e, nrhs, d, off[0], off[1], off[2], t,
+                                                 mask);
+  DDA_CU(cudaGetLastError());
+  add_launches(1);
+  return Err::Ok();
+}
+Err unet_warm(const int32_t* ijk, int64_t n, const uint8_t* comp, const double2* ia, int ncomp, const float* y,
+              const double2* e, int nrhs, const int32_t dims[3], const int32_t off[3], double2* p, cudaStream_t st) {
+  const nn::Dims d{dims[2], dims[1], dims[0]};
+  const int nb = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  nn::k_warm<<<dim3(nb, nrhs), 256, 0, st>>>(ijk, n, comp, ia, ncomp, y, e, nrhs, d, off[0], off[1], off[2], p);
+  DDA_CU(cudaGetLastError());
+  add_launches(1);
+  return Err::Ok();
+}
+}  // namespace dda
+
+dda_status dda_unet_forward_train(dda_unet* n, const float* x_dev, float* y_dev, int batch, const int32_t dims[3]) {
+  if (!n || !x_dev || !y_dev || batch < 1 || !dims) return DDA_EINVAL;
+  Err e = check_dims(dims);
+  if (!e.ok()) return ufail(n, e);
+  if (cudaSetDevice(n->device) != cudaSuccess) return ufail(n, Err::make(DDA_ECUDA, "cudaSetDevice failed"));
+  const dda::nn::Dims d1{dims[2], dims[1], dims[0]};
+  const int64_t V1 = (int64_t)batch * d1.nvox();
+  Acts a;
+  e = layout(n, batch, d1, true, &a);
+  if (e.ok() && cudaMemcpyAsync(a.x, x_dev, sizeof(float) * V1 * n->cin, cudaMemcpyDeviceToDevice, n->stream) !=
+                    cudaSuccess)
+    e = Err::make(DDA_ECUDA, "input copy failed");
+  if (e.ok()) e = forward_pass(n, a, batch, d1);
+  if (e.ok() && cudaMemcpyAsync(y_dev, a.y, sizeof(float) * V1 * n->cout, cudaMemcpyDeviceToDevice, n->stream) !=
+                    cudaSuccess)
+    e = Err::make(DDA_ECUDA, "output copy failed");
+  return e.ok() ? DDA_OK : ufail(n, e);
+}
+
+dda_status dda_unet_mse(dda_unet* n, const float* y_dev, const float* t_dev, const float* mask_dev, int batch,
+                        const int32_t dims[3], double weight, float* gy_dev, double* loss_out) {
+  if (!n || !y_dev || !t_dev || !mask_dev || !gy_dev || batch < 1 || !dims) return DDA_EINVAL;
+  if (cudaSetDevice(n->device) != cudaSuccess) return ufail(n, Err::make(DDA_ECUDA, "cudaSetDevice failed"));
+  const int64_t V1 = (int64_t)batch * dims[0] * dims[1] * dims[2];
+  std::vector<float> hm(V1);
+  if (cudaMemcpyAsync(hm.data(), mask_dev, sizeof(float) * V1, cudaMemcpyDeviceToHost, n->stream) != cudaSuccess ||
+      cudaStreamSynchronize(n->stream) != cudaSuccess)
+    return ufail(n, Err::make(DDA_ECUDA, "mask copy failed"));
+  double cnt = 0.0;
+  for (float m : hm) cnt += m;
+  if (cnt <= 0) return ufail(n, Err::make(DDA_EINVAL, "mask selects no voxel"));
+  const int lb = 512;
+  dda::nn::k_loss<<<lb, 256, 0, n->stream>>>(y_dev, t_dev, mask_dev, n->cout, V1, weight / (cnt * n->cout), gy_dev,
+                                              n->lpart);
+  dda::add_launches(1);
+  if (cudaMemcpyAsync(n->h_loss, n->lpart, sizeof(double) * lb, cudaMemcpyDeviceToHost, n->stream) != cudaSuccess ||
+      cudaStreamSynchronize(n->stream) != cudaSuccess)
+    return ufail(n, Err::make(DDA_ECUDA, "loss copy failed"));
+  double L = 0.0;
+  for (int i = 0; i < lb; ++i) L += n->h_loss[i];
+  if (loss_out) *loss_out = L;
+  return DDA_OK;
+}
+
+dda_status dda_unet_backward(dda_unet* n, const float* gy_dev, int batch, const int32_t dims[3]) {
+  if (!n || !gy_dev || batch < 1 || !dims) return DDA_EINVAL;
+  Err e = check_dims(dims);
+  if (!e.ok()) return ufail(n, e);
+  if (cudaSetDevice(n->device) != cudaSuccess) return ufail(n, Err::make(DDA_ECUDA, "cudaSetDevice failed"));
+  const dda::nn::Dims d1{dims[2], dims[1], dims[0]};
+  const int64_t V1 = (int64_t)batch * d1.nvox();
+  Acts a;
+  e = layout(n, batch, d1, true, &a);  // same sizes as the preceding dda_unet_forward_train: same buffers
+  if (e.ok() && cudaMemcpyAsync(a.g_y, gy_dev, sizeof(float) * V1 * n->cout, cudaMemcpyDeviceToDevice, n->stream) !=
+                    cudaSuccess)
+    e = Err::make(DDA_ECUDA, "gradient copy failed");
+  if (e.ok()) e = backward_pass(n, a, batch, d1);
+  return e.ok() ? DDA_OK : ufail(n, e);
+}
+
+// --------------------------------------------------------------------- residual loss glue
+namespace dda {
+namespace nn {
+// P0 (complex64) = alpha (E_inc + y) at the target's sites
+__global__ void k_guess64(const int32_t* __restrict__ ijk, int64_t n, const uint8_t* __restrict__ comp,
+                          const double2* __restrict__ ia, int ncomp, const float* __restrict__ y,
+                          const double2* __restrict__ e, int nrhs, Dims d, int ox, int oy, int oz,
+                          float2* __restrict__ p) {
+  const int b = blockIdx.y;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int xx = ijk[3 * j] + ox, yy = ijk[3 * j + 1] + oy, zz = ijk[3 * j + 2] + oz;
+    const int64_t v = (int64_t)b * d.nvox() + ((int64_t)zz * d.Y + yy) * d.X + xx;
+    const int cc = comp ? comp[j] : 0;
+    for (int c = 0; c < 3; ++c) {
+      const double2 a = ia[((int64_t)b * ncomp + cc) * 3 + c];
+      const double2 ev = e[((int64_t)b * 3 + c) * n + j];
+      const double er = y[v * 6 + 2 * c] + ev.x, ei = y[v * 6 + 2 * c + 1] + ev.y;
+      const double den = a.x * a.x + a.y * a.y;
+      p[((int64_t)b * 3 + c) * n + j] = make_float2((float)((er * a.x + ei * a.y) / den),
+                                                    (float)((ei * a.x - er * a.y) / den));
+    }
+  }
+}
+
+// r = E - A P0 (complex64) and per-RHS |r|^2, |E|^2 partials
+__global__ void k_resid64(const double2* __restrict__ e, float2* __restrict__ r, int64_t n3, double* __restrict__ part,
+                          int nblk) {
+  const int b = blockIdx.y;
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 ev = e[(int64_t)b * n3 + i];
+    const float2 ap = r[(int64_t)b * n3 + i];
+    const float rx = (float)ev.x - ap.x, ry = (float)ev.y - ap.y;
+    r[(int64_t)b * n3 + i] = make_float2(rx, ry);
+    s0 += (double)rx * rx + (double)ry * ry;
+    s1 += ev.x * ev.x + ev.y * ev.y;
+  }
+  __shared__ double red[2][256];
+  red[0][threadIdx.x] = s0;
+  red[1][threadIdx.x] = s1;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + w];
+      red[1][threadIdx.x] += red[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[((int64_t)b * nblk + blockIdx.x) * 2] = red[0][0];
+    part[((int64_t)b * nblk + blockIdx.x) * 2 + 1] = red[1][0];
+  }
+}
+
+// gy += w_b * d|r|^2/dy with g = A^H r:  d/dy_re = -2 Re(conj(g) alpha), d/dy_im = 2 Im(conj(g) alpha)
+__global__ void k_resgrad(const int32_t* __restrict__ ijk, int64_t n, const uint8_t* __restrict__ comp,
+                          const double2* __restrict__ ia, int ncomp, const float2* __restrict__ g,
+                          const double* __restrict__ wb, int nrhs, Dims d, int ox, int oy, int oz,
+                          float* __restrict__ gy) {
+  const int b = blockIdx.y;
+  const double w = wb[b];
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int xx = ijk[3 * j] + ox, yy = ijk[3 * j + 1] + oy, zz = ijk[3 * j + 2] + oz;
+    const int64_t v = (int64_t)b * d.nvox() + ((int64_t)zz * d.Y + yy) * d.X + xx;
+    const int cc = comp ? comp[j] : 0;
+    for (int c = 0; c < 3; ++c) {
+      const double2 ai = ia[((int64_t)b * ncomp + cc) * 3 + c];
+      const double den = ai.x * ai.x + ai.y * ai.y;
+      const double ar = ai.x / den, aim = -ai.y / den;  // alpha = 1 / alpha^{-1}
+      const float2 gv = g[((int64_t)b * 3 + c) * n + j];
+      // conj(g) alpha
+      const double pr = gv.x * ar + gv.y * aim, pim = gv.x * aim - gv.y * ar;
+      gy[v * 6 + 2 * c] += (float)(-2.0 * w * pr);
+      gy[v * 6 + 2 * c + 1] += (float)(2.0 * w * pim);
+    }
+  }
+}
+}  // namespace nn
+
+Err unet_guess64(const int32_t* ijk, int64_t n, const uint8_t* comp, const double2* ia, int ncomp, const float* y,
+                 const double2* e, int nrhs, const int32_t dims[3], const int32_t off[3], float2* p, cudaStream_t st) {
+  const nn::Dims d{dims[2], dims[1], dims[0]};
+  const int nb = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  nn::k_guess64<<<dim3(nb, nrhs), 256, 0, st>>>(ijk, n, comp, ia, ncomp, y, e, nrhs, d, off[0], off[1], off[2], p);
+  DDA_CU(cudaGetLastError());
+  add_launches(1);
+  return Err::Ok();
+}
+Err unet_resid64(const double2* e, float2* r, int nrhs, int64_t n3, double* part, int nblk, cudaStream_t st) {
+  nn::k_resid64<<<dim3(nblk, nrhs), 256, 0, st>>>(e, r, n3, part, nblk);
+  DDA_CU(cudaGetLastError());
+  add_launches(1);
+  return Err::Ok();
+}
+Err unet_resgrad(const int32_t* ijk, int64_t n, const uint8_t* comp, const double2* ia, int ncomp, const float2* g,
+                 const double* wb, int nrhs, const int32_t dims[3], const int32_t off[3], float* gy, cudaStream_t st) {
+  const nn::Dims d{dims[2], dims[1], dims[0]};
+  const int nb = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  nn::k_resgrad<<<dim3(nb, nrhs), 256, 0, st>>>(ijk, n, comp, ia, ncomp, g, wb, nrhs, d, off[0], off[1], off[2], gy);
+  DDA_CU(cudaGetLastError());
+  add_launches(1);
+  return Err::Ok();
+}
+}  // namespace dda

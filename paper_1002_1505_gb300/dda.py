@@ -76,6 +76,22 @@ def _load():
         "dda_matvec_noalloc": (I, [P, P, P, I, I]),
         "dda_schedule_info": (I, [P, I, P]),
         "dda_solve_batch": (I, [P, I, P, P, P, P]),
+        "dda_unet_create": (I, [ctypes.POINTER(P), I, P, I, I, P, ctypes.c_uint64]),
+        "dda_unet_destroy": (None, [P]),
+        "dda_unet_last_error": (ctypes.c_char_p, [P]),
+        "dda_unet_nparams": (I64, [P]),
+        "dda_unet_get_params": (I, [P, P, I]),
+        "dda_unet_set_params": (I, [P, P]),
+        "dda_unet_forward": (I, [P, P, P, I, P]),
+        "dda_unet_loss_grad": (I, [P, P, P, P, I, P, ctypes.POINTER(D)]),
+        "dda_unet_adamw": (I, [P, D, D, D, D, D]),
+        "dda_unet_features": (I, [P, P, P, P]),
+        "dda_unet_targets": (I, [P, P, P, P, P, P, I]),
+        "dda_unet_warm_start": (I, [P, P, P, P, I, P]),
+        "dda_unet_forward_train": (I, [P, P, P, I, P]),
+        "dda_unet_mse": (I, [P, P, P, P, I, P, D, P, ctypes.POINTER(D)]),
+        "dda_unet_backward": (I, [P, P, I, P]),
+        "dda_unet_residual_grad": (I, [P, P, P, P, D, P, ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -242,6 +258,116 @@ class Context:
             return q, m.reshape(-1, d.shape[0], 4, 4)
         self._check(LIB.dda_cross_sections(self._h, ctypes.c_void_p(p.data_ptr()), _ptr(q), None, 0, None))
         return q, None
+
+
+class UNet:
+    """The learned warm start's 3-D U-Net (library-owned parameters and kernels)."""
+
+    def __init__(self, device: int = 0, stream=None, cin: int = 9, cout: int = 6, ch=(12, 24, 32, 48), seed: int = 0):
+        self._h = ctypes.c_void_p()
+        chv = np.ascontiguousarray(ch, dtype=np.int32)
+        st = LIB.dda_unet_create(ctypes.byref(self._h), int(device), ctypes.c_void_p(_stream_handle(stream)),
+                                 int(cin), int(cout), _ptr(chv), ctypes.c_uint64(seed))
+        if st != DDA_OK:
+            raise DDAError(st, "dda_unet_create failed")
+        self.cin, self.cout, self.ch = cin, cout, tuple(ch)
+        self._keep = chv
+
+    def close(self):
+        if self._h:
+            LIB.dda_unet_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != DDA_OK:
+            raise DDAError(st, LIB.dda_unet_last_error(self._h).decode())
+
+    @property
+    def nparams(self) -> int:
+        return int(LIB.dda_unet_nparams(self._h))
+
+    def dda_unet_get_params(self, which: int = 0) -> np.ndarray:
+        out = np.zeros(self.nparams, dtype=np.float32)
+        self._check(LIB.dda_unet_get_params(self._h, _ptr(out), int(which)))
+        return out
+
+    def dda_unet_set_params(self, theta):
+        arr = np.ascontiguousarray(theta, dtype=np.float32)
+        self._check(LIB.dda_unet_set_params(self._h, _ptr(arr)))
+
+    @staticmethod
+    def _dims(dims):
+        return np.ascontiguousarray(dims, dtype=np.int32)
+
+    def dda_unet_forward(self, x, y, dims):
+        d = self._dims(dims)
+        self._check(LIB.dda_unet_forward(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                         int(x.shape[0]), _ptr(d)))
+
+    def dda_unet_loss_grad(self, x, t, mask, dims) -> float:
+        d = self._dims(dims)
+        loss = ctypes.c_double()
+        self._check(LIB.dda_unet_loss_grad(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                           ctypes.c_void_p(mask.data_ptr()), int(x.shape[0]), _ptr(d),
+                                           ctypes.byref(loss)))
+        return float(loss.value)
+
+    def dda_unet_forward_train(self, x, y, dims):
+        d = self._dims(dims)
+        self._check(LIB.dda_unet_forward_train(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                               int(x.shape[0]), _ptr(d)))
+
+    def dda_unet_mse(self, y, t, mask, gy, dims, weight=1.0) -> float:
+        d = self._dims(dims)
+        loss = ctypes.c_double()
+        self._check(LIB.dda_unet_mse(self._h, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                     ctypes.c_void_p(mask.data_ptr()), int(y.shape[0]), _ptr(d), float(weight),
+                                     ctypes.c_void_p(gy.data_ptr()), ctypes.byref(loss)))
+        return float(loss.value)
+
+    def dda_unet_backward(self, gy, dims):
+        d = self._dims(dims)
+        self._check(LIB.dda_unet_backward(self._h, ctypes.c_void_p(gy.data_ptr()), int(gy.shape[0]), _ptr(d)))
+
+    def dda_unet_adamw(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.0):
+        self._check(LIB.dda_unet_adamw(self._h, float(lr), float(beta1), float(beta2), float(eps), float(wd)))
+
+
+def dda_unet_features(ctx: "Context", x, dims, offset=None):
+    d = np.ascontiguousarray(dims, dtype=np.int32)
+    o = None if offset is None else np.ascontiguousarray(offset, dtype=np.int32)
+    ctx._check(LIB.dda_unet_features(ctx._h, ctypes.c_void_p(x.data_ptr()), _ptr(d), None if o is None else _ptr(o)))
+
+
+def dda_unet_targets(ctx: "Context", p, t, mask, dims, offset=None, residual=False):
+    d = np.ascontiguousarray(dims, dtype=np.int32)
+    o = None if offset is None else np.ascontiguousarray(offset, dtype=np.int32)
+    ctx._check(LIB.dda_unet_targets(ctx._h, ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                    ctypes.c_void_p(mask.data_ptr()), _ptr(d), None if o is None else _ptr(o),
+                                    int(bool(residual))))
+
+
+def dda_unet_warm_start(ctx: "Context", y, dims, p, offset=None, residual=False):
+    d = np.ascontiguousarray(dims, dtype=np.int32)
+    o = None if offset is None else np.ascontiguousarray(offset, dtype=np.int32)
+    ctx._check(LIB.dda_unet_warm_start(ctx._h, ctypes.c_void_p(y.data_ptr()), _ptr(d), None if o is None else _ptr(o),
+                                       int(bool(residual)), ctypes.c_void_p(p.data_ptr())))
+
+
+def dda_unet_residual_grad(ctx: "Context", y, gy, dims, weight=1.0, offset=None) -> float:
+    """Adds weight * sum_b |E_b - A P0_b|^2/|E_b|^2 (P0 = alpha (E_inc + y)) to the returned loss and its gradient to gy."""
+    d = np.ascontiguousarray(dims, dtype=np.int32)
+    o = None if offset is None else np.ascontiguousarray(offset, dtype=np.int32)
+    loss = ctypes.c_double()
+    ctx._check(LIB.dda_unet_residual_grad(ctx._h, ctypes.c_void_p(y.data_ptr()), _ptr(d), None if o is None else _ptr(o),
+                                          float(weight), ctypes.c_void_p(gy.data_ptr()), ctypes.byref(loss)))
+    return float(loss.value)
 
 
 def dda_kernel_launches() -> int:

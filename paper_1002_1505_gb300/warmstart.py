@@ -1,0 +1,196 @@
+"""Learned warm start for the DDA solve: data from the solver, training, use.
+
+The solver (dda_solve) accepts any initial guess.  This module trains the
+library's 3-D U-Net (dda_unet_*) to predict the local field E_loc = alpha^{-1} P
+from per-voxel features of a target (occupancy, permittivity, incident field)
+and turns its prediction into a guess P0 = alpha E_loc.  The network learns
+the correction E_loc - E_inc: for a small sphere in the static limit the
+Lorentz local field equals the incident field, so the network-free guess
+alpha E_inc is its starting point.  Every step runs in
+the library: solutions come from dda_solve, features/targets/guesses from
+dda_unet_features / dda_unet_targets / dda_unet_warm_start, training from
+dda_unet_loss_grad and dda_unet_adamw.  torch only holds device buffers and
+gathers mini-batches.
+
+Random problems: spheres, ellipsoids and hexagonal prisms on boxes up to
+max_box^3, Re m in [1.1, 2.5], Im m in [0, 0.5], x in [1, 10], one uniform
+orientation (workloads.random_unet_sample); kd is capped at 0.8/|m| so that
+every problem stays in the DDA's range of validity (|m| kd < 1).
+"""
+from __future__ import annotations
+
+import math
+from typing import List, Tuple
+
+import numpy as np
+
+from . import dda as D
+from . import workloads as W
+
+CIN, COUT = 9, 6
+DEFAULT_CH = (12, 24, 32, 48)
+
+
+def grid_dims(box, mult: int = 8) -> Tuple[int, int, int]:
+    return tuple(int(math.ceil(b / mult) * mult) for b in box)
+
+
+def problem(index: int, max_box: int, device: int = 0, stream=None):
+    """Context for random problem `index` (target, incidence, Green tensor, alpha)."""
+    shape, shpar, m, x, ori = W.random_unet_sample(index, max_box)
+    ctx = D.Context(device, stream)
+    n, box = ctx.dda_setup_shape(shape, shpar)
+    aeff = (3.0 * n / (4.0 * math.pi)) ** (1.0 / 3.0)
+    kd = min(x / aeff, 0.8 / abs(m))
+    ctx.dda_set_incident(kd, [ori], [[0, 0], [1, 0], [0, 0]], 2)
+    ctx.dda_build_green_fft()
+    ctx.dda_set_polarizability("GKDLDR", m)
+    return ctx
+
+
+def generate(indices, max_box: int, grid, device: int = 0, group: int = 8, tol: float = 1e-5, keep: bool = False):
+    """Solve the random problems `indices` and return device tensors (X, T, M) on the fixed grid.
+
+    Each problem gives two samples (its two polarizations).  Problems are solved
+    `group` at a time with dda_solve_batch.  keep=True also returns the
+    contexts (for the residual loss), else they are closed.
+    """
+    import torch
+    V = grid[0] * grid[1] * grid[2]
+    S = 2 * len(indices)
+    X = torch.zeros((S, grid[2], grid[1], grid[0], CIN), dtype=torch.float32, device="cuda")
+    T = torch.zeros((S, grid[2], grid[1], grid[0], COUT), dtype=torch.float32, device="cuda")
+    M = torch.zeros((S, grid[2], grid[1], grid[0]), dtype=torch.float32, device="cuda")
+    iters, kept = [], []
+    for g0 in range(0, len(indices), group):
+        ctxs = [problem(i, max_box, device) for i in indices[g0:g0 + group]]
+        ps = [torch.zeros((c.nrhs, 3, c.n), dtype=torch.complex128, device="cuda") for c in ctxs]
+        reps, sts, overall = D.dda_solve_batch(ctxs, ps, precision="MIXED", tol=tol, maxit=3000)
+        for k, (c, p, r) in enumerate(zip(ctxs, ps, reps)):
+            s = 2 * (g0 + k)
+            D.dda_unet_features(c, X[s:s + 2], grid)
+            D.dda_unet_targets(c, p, T[s:s + 2], M[s:s + 2], grid, residual=True)
+            iters.extend(x["iters"] for x in r)
+        torch.cuda.synchronize()
+        if keep:
+            kept.extend(ctxs)
+        else:
+            for c in ctxs:
+                c.close()
+    return (X, T, M, iters, kept) if keep else (X, T, M, iters)
+
+
+def train(net: "D.UNet", X, T, M, grid, steps: int, batch: int, lr: float = 2e-3, seed: int = 0,
+          wd: float = 0.0) -> List[float]:
+    """AdamW on random mini-batches; cosine learning-rate decay. Returns the loss history."""
+    import torch
+    rng = np.random.default_rng(seed)
+    S = X.shape[0]
+    hist = []
+    for it in range(steps):
+        idx = torch.from_numpy(rng.choice(S, size=min(batch, S), replace=False)).cuda()
+        xb, tb, mb = X[idx].contiguous(), T[idx].contiguous(), M[idx].contiguous()
+        loss = net.dda_unet_loss_grad(xb, tb, mb, grid)
+        rate = lr * 0.5 * (1.0 + math.cos(math.pi * it / max(1, steps)))
+        net.dda_unet_adamw(rate, wd=wd)
+        hist.append(loss)
+    return hist
+
+
+def zero_head(net: "D.UNet"):
+    """Zero the 1x1x1 output layer: the untrained network then predicts no
+    correction, i.e. its guess starts as the alpha E_inc guess."""
+    theta = net.dda_unet_get_params(0)
+    c1 = net.ch[0]
+    theta[-(c1 * COUT + COUT):] = 0.0
+    net.dda_unet_set_params(theta)
+
+
+def train_residual(net: "D.UNet", ctxs, X, T, M, grid, steps: int, per_step: int = 8, lr: float = 1e-3,
+                   res_weight: float = 1.0, mse_weight: float = 1.0, seed: int = 0,
+                   wd: float = 0.0) -> List[Tuple[float, float]]:
+    """Train on mse_weight * MSE(E_loc) + res_weight * mean |E - A P0|^2/|E|^2 over `per_step` problems per step.
+
+    The residual term goes through the library's own product and its adjoint
+    (dda_unet_residual_grad), so the network is trained on the quantity the
+    Krylov solver starts from.  Returns (mse, residual) per step."""
+    import torch
+    rng = np.random.default_rng(seed)
+    K = len(ctxs)
+    hist = []
+    for it in range(steps):
+        pick = rng.choice(K, size=min(per_step, K), replace=False)
+        idx = torch.from_numpy(np.stack([2 * pick, 2 * pick + 1], axis=1).reshape(-1)).cuda()
+        xb, tb, mb = X[idx].contiguous(), T[idx].contiguous(), M[idx].contiguous()
+        y = torch.empty_like(tb)
+        gy = torch.empty_like(tb)
+        net.dda_unet_forward_train(xb, y, grid)
+        mse = net.dda_unet_mse(y, tb, mb, gy, grid, weight=mse_weight)
+        res = 0.0
+        for k, ci in enumerate(pick):
+            res += D.dda_unet_residual_grad(ctxs[ci], y[2 * k:2 * k + 2], gy[2 * k:2 * k + 2], grid,
+                                            weight=res_weight / (2 * len(pick)))
+        net.dda_unet_backward(gy, grid)
+        rate = lr * 0.5 * (1.0 + math.cos(math.pi * it / max(1, steps)))
+        net.dda_unet_adamw(rate, wd=wd)
+        hist.append((mse / mse_weight if mse_weight else 0.0, res / res_weight if res_weight else 0.0))
+    return hist
+
+
+def residual_of_guess(ctxs, grid, ys=None) -> float:
+    """Mean |E - A P0|^2/|E|^2 over the contexts' right-hand sides for outputs ys (None: y = 0, the alpha E_inc guess)."""
+    import torch
+    tot, cnt = 0.0, 0
+    for k, c in enumerate(ctxs):
+        y = torch.zeros((c.nrhs, grid[2], grid[1], grid[0], COUT), dtype=torch.float32, device="cuda") if ys is None else ys[k]
+        gy = torch.zeros_like(y)
+        tot += D.dda_unet_residual_grad(c, y, gy, grid)
+        cnt += c.nrhs
+    return tot / cnt
+
+
+def warm_guess(ctx: "D.Context", net: "D.UNet", grid=None):
+    """Initial guess P0 (complex128 [nrhs, 3, N]) for a context from the network."""
+    import torch
+    grid = grid_dims(ctx.box) if grid is None else grid
+    x = torch.zeros((ctx.nrhs, grid[2], grid[1], grid[0], CIN), dtype=torch.float32, device="cuda")
+    y = torch.empty((ctx.nrhs, grid[2], grid[1], grid[0], COUT), dtype=torch.float32, device="cuda")
+    D.dda_unet_features(ctx, x, grid)
+    net.dda_unet_forward(x, y, grid)
+    p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
+    D.dda_unet_warm_start(ctx, y, grid, p, residual=True)
+    return p
+
+
+def local_field_guess(ctx: "D.Context", grid=None):
+    """The network-free guess P0 = alpha E_inc (the local field taken as the incident field)."""
+    import torch
+    grid = grid_dims(ctx.box) if grid is None else grid
+    x = torch.zeros((ctx.nrhs, grid[2], grid[1], grid[0], CIN), dtype=torch.float32, device="cuda")
+    D.dda_unet_features(ctx, x, grid)
+    y = torch.zeros((ctx.nrhs, grid[2], grid[1], grid[0], COUT), dtype=torch.float32, device="cuda")
+    p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
+    D.dda_unet_warm_start(ctx, y, grid, p, residual=True)  # zero correction: E_loc = E_inc
+    return p
+
+
+def evaluate(net: "D.UNet", indices, max_box: int, grid=None, tol: float = 1e-5):
+    """Iterations to tol (true residual) from a cold start, the alpha E_inc guess and the network guess."""
+    import torch
+    rows = []
+    for i in indices:
+        ctx = problem(i, max_box)
+        out = {}
+        for name in ("cold", "alpha_einc", "network"):
+            if name == "cold":
+                p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
+                warm = False
+            elif name == "alpha_einc":
+                p, warm = local_field_guess(ctx, grid), True
+            else:
+                p, warm = warm_guess(ctx, net, grid), True
+            reps, _ = ctx.dda_solve(p, precision="MIXED", tol=tol, maxit=3000, warm_start=warm)
+            out[name] = (sum(r["iters"] for r in reps), max(r["true_rel_resid"] for r in reps))
+        rows.append(out)
+        ctx.close()
+    return rows

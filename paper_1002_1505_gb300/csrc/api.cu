@@ -386,10 +386,22 @@ Err ensure_tuned(dda_ctx* c, int nrhs) {
   if (base.plane_ok) {
     dda::MvTune a = base, b = base;
     a.plane = b.plane = true;
+    a.clus = b.clus = 0;
     a.thr_p = 512;
     b.thr_p = 768;
     cand.push_back(a);
     cand.push_back(b);
+    if constexpr (sizeof(C) == sizeof(float2)) {
+      int smax = 0;
+      cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+      for (int S : {2, 4}) {
+        if (dda::plane_cluster_capacity_c64(g0, S, smax) > 0) {
+          dda::MvTune t = a;
+          t.clus = S;
+          cand.push_back(t);
+        }
+      }
+    }
   }
   cand.push_back(t5);
   dda::MvTune best = cand[0];
@@ -818,7 +830,8 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
     if (!t128.fast) t128.plane = dda::plane_smem_bytes<double2>(g128, t128) <= (size_t)smax;
     // DDA_SCHEDULE pins the schedule instead of autotuning it: "generic" (shared-memory
     // engine of fft.cuh), "fast5" (compile-time kernels, 5 passes), "plane512" / "plane768"
-    // (compile-time kernels, fused plane pass where it exists)
+    // (compile-time kernels, fused plane pass where it exists), "cluster2" / "cluster4"
+    // (complex64 plane pass split over a cluster of 2 or 4 CTAs where it fits)
     c->forced_schedule = false;
     c->tuned_nrhs[0] = c->tuned_nrhs[1] = 0;
     if (const char* f = std::getenv("DDA_SCHEDULE")) {
@@ -833,6 +846,10 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
         c->forced_schedule = true;
       } else if (sched == "plane512" || sched == "plane768") {
         t64.thr_p = t128.thr_p = (sched == "plane768") ? 768 : 512;
+        c->forced_schedule = true;
+      } else if (sched == "cluster2" || sched == "cluster4") {
+        const int S = sched == "cluster2" ? 2 : 4;
+        if (t64.plane_ok && dda::plane_cluster_capacity_c64(g64, S, smax) > 0) t64.clus = S;
         c->forced_schedule = true;
       }
     }
@@ -1349,15 +1366,16 @@ dda_status dda_profile_matvec(dda_ctx* c, int nrhs, int dtype, int iters, double
   return DDA_OK;
 }
 
-dda_status dda_schedule_info(dda_ctx* c, int dtype, int32_t info[4]) {
+dda_status dda_schedule_info(dda_ctx* c, int dtype, int32_t info[5]) {
   if (!c || !info) return DDA_EINVAL;
   if (!c->have_green) return fail(c, Err::make(DDA_ESTATE, "build the Green tensor first"));
   if (dtype != DDA_C64 && dtype != DDA_C128) return fail(c, Err::make(DDA_EINVAL, "bad dtype"));
   const dda::MvTune& t = dtype == DDA_C64 ? c->t64 : c->t128;
   info[0] = t.plane ? 3 : 5;
   info[1] = t.fast ? 1 : 0;
-  info[2] = t.plane ? t.thr_p : 0;
+  info[2] = t.plane ? (t.clus == 2 ? 384 : t.clus == 4 ? 256 : t.thr_p) : 0;
   info[3] = c->tuned_nrhs[dtype == DDA_C64 ? 0 : 1];
+  info[4] = t.plane && t.clus > 1 ? t.clus : 1;
   return DDA_OK;
 }
 

@@ -89,6 +89,7 @@ struct MvTune {
   bool plane = true;  // 3-pass schedule (plane fits in shared memory)
   bool fast = false;  // compile-time-length kernels exist for px, py, pz (matvec_fast.cuh)
   bool plane_ok = false;  // the fast 3-pass plane kernel exists and fits for this grid
+  int clus = 0;           // plane pass split over a cluster of this many CTAs (0: one CTA per plane)
 };
 
 // Enqueue ap = A p for nrhs right-hand sides (rhs0 = index of the first one for alpha).
@@ -102,6 +103,10 @@ template <typename C>
 Err launch_matvec_fast(const Geom& g, const MvData<C>& d, const MvTune& t, const C* p, C* ap, int nrhs, int rhs0,
                        bool conj, cudaStream_t st);
 void fast_optin_c64(int smax);
+// complex64 plane pass split over a thread-block cluster of S CTAs (matvec_cluster.cu)
+Err launch_plane_cluster_c64(const Geom& g, const MvData<float2>& d, int S, int nrhs, cudaStream_t st);
+int plane_cluster_capacity_c64(const Geom& g, int S, int smax);  // co-resident clusters, 0 = not possible
+void cluster_optin_c64(int smax);
 void fast_optin_c128(int smax);
 // Does a fast schedule exist for this grid (all lengths instantiated, tiles fit)?  Sets t.fast and t.plane.
 void choose_fast_schedule(const Geom& g, bool c64, int smax, MvTune* t);

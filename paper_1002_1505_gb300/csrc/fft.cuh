@@ -76,14 +76,16 @@ template <int S, typename C> struct Dft<2, S, C> {
 template <int S, typename C> struct Dft<3, S, C> {
   static __device__ __forceinline__ void run(C* v) {
     using R = decltype(v[0].x);
-    const R h = (R)0.86602540378443864676;  // sin(2 pi / 3)
-    C s = cadd(v[1], v[2]);
-    C d = csub(v[1], v[2]);
-    C m = csub(v[0], cscale(s, (R)0.5));
-    C t = cmuli(cscale(d, h), S);  // i S sin(2pi/3) (x1 - x2)
+    const R h = (R)(S * 0.86602540378443864676);  // S sin(2 pi / 3)
+    const C s = cadd(v[1], v[2]);
+    const C d = csub(v[1], v[2]);
+    C m;  // x0 - s/2
+    m.x = fma((R)-0.5, s.x, v[0].x);
+    m.y = fma((R)-0.5, s.y, v[0].y);
     v[0] = cadd(v[0], s);
-    v[1] = cadd(m, t);
-    v[2] = csub(m, t);
+    // outputs m +- i h d, one FMA per real part
+    v[1] = mk(fma(-h, d.y, m.x), fma(h, d.x, m.y));
+    v[2] = mk(fma(h, d.y, m.x), fma(-h, d.x, m.y));
   }
 };
 
@@ -128,18 +130,19 @@ template <int S, typename C> struct Dft<8, S, C> {
     C o[4] = {v[1], v[3], v[5], v[7]};
     Dft<4, S, C>::run(e);
     Dft<4, S, C>::run(o);
-    // w8^k = exp(S 2 pi i k / 8): k=1 -> (1 + iS)/sqrt2, k=2 -> iS, k=3 -> (-1 + iS)/sqrt2
-    C o1 = cscale(cadd(o[1], cmuli(o[1], S)), r2);
-    C o2 = cmuli(o[2], S);
-    C o3 = cscale(csub(cmuli(o[3], S), o[3]), r2);
+    // w8^k = exp(S 2 pi i k / 8): k=1 -> (1 + iS)/sqrt2, k=2 -> iS, k=3 -> (-1 + iS)/sqrt2.
+    // The 1/sqrt2 factor is folded into the butterflies' FMAs.
+    const C a1 = mk(o[1].x - S * o[1].y, o[1].y + S * o[1].x);  // (1 + iS) o1
+    const C a3 = mk(-o[3].x - S * o[3].y, S * o[3].x - o[3].y);  // (-1 + iS) o3
+    const C o2 = cmuli(o[2], S);
     v[0] = cadd(e[0], o[0]);
     v[4] = csub(e[0], o[0]);
-    v[1] = cadd(e[1], o1);
-    v[5] = csub(e[1], o1);
+    v[1] = mk(fma(r2, a1.x, e[1].x), fma(r2, a1.y, e[1].y));
+    v[5] = mk(fma(-r2, a1.x, e[1].x), fma(-r2, a1.y, e[1].y));
     v[2] = cadd(e[2], o2);
     v[6] = csub(e[2], o2);
-    v[3] = cadd(e[3], o3);
-    v[7] = csub(e[3], o3);
+    v[3] = mk(fma(r2, a3.x, e[3].x), fma(r2, a3.y, e[3].y));
+    v[7] = mk(fma(-r2, a3.x, e[3].x), fma(-r2, a3.y, e[3].y));
   }
 };
 

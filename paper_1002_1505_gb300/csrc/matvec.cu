@@ -214,13 +214,13 @@ __global__ void k_yzplane(Geom g, MvData<C> d, int G) {
 }
 
 // ------------------------------------------------------------------ 5-pass pieces
-// z pass alone: grid (ceil(py/G), px, nrhs)
+// z pass alone: grid (nrhs, ceil(py/G), px)
 template <typename C>
 __global__ void k_zconv(Geom g, MvData<C> d, int G) {
   extern __shared__ unsigned char smem_raw[];
   C* twz = reinterpret_cast<C*>(smem_raw);
   C* col = twz + g.pz;
-  const int ky0 = blockIdx.x * G, kx = blockIdx.y, b = blockIdx.z;
+  const int ky0 = blockIdx.y * G, kx = blockIdx.z, b = blockIdx.x;  // RHS fastest: Ghat tiles reused from L2
   load_tw(twz, d.twz, g.pz);
   C* wb = d.work + (((int64_t)b * 3) * g.px + kx) * ((int64_t)g.nz * g.ys);
   const int64_t cstride = (int64_t)g.px * g.nz * g.ys;
@@ -426,7 +426,7 @@ Err launch_matvec(const Geom& g, const MvData<C>& d, const MvTune& t, const C* p
     mark(pass++, st);
     const size_t sz = sizeof(C) * ((size_t)g.pz + (size_t)g.pz * 3 * t.g);
     DDA_TRY(set_smem(sz));
-    k_zconv<C><<<dim3((g.py + t.g - 1) / t.g, g.px, nrhs), t.thr_p, sz, st>>>(g, d, t.g);
+    k_zconv<C><<<dim3(nrhs, (g.py + t.g - 1) / t.g, g.px), t.thr_p, sz, st>>>(g, d, t.g);
     DDA_CU(cudaGetLastError());
     mark(pass++, st);
     k_fft_rows<C><<<nb, t.thr_x, sr, st>>>(d.work, nrows, g.ys, g.ply, d.twy, g.py, g.ny, rpb, true);
@@ -519,6 +519,7 @@ void init_kernel_attrs() {
   optin(k_fft_rows<float2>); optin(k_fft_rows<double2>);
   optin(k_fft_strided<float2>); optin(k_fft_strided<double2>);
   fast_optin_c64(v);
+  cluster_optin_c64(v);
   fast_optin_c128(v);
 }
 

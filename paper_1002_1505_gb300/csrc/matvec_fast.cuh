@@ -33,14 +33,24 @@ __device__ __forceinline__ void load6(const C* __restrict__ gh, C (&g)[6]) {
   }
 }
 
+// u = Ghat v for one voxel: each output component is a 3-term complex dot
+// product, written as one FMUL and five FMAs per real part (12 real products
+// per output, no separate additions).
+template <typename C>
+__device__ __forceinline__ C cdot3(C a0, C b0, C a1, C b1, C a2, C b2) {
+  C r;
+  r.x = fma(a0.x, b0.x, fma(-a0.y, b0.y, fma(a1.x, b1.x, fma(-a1.y, b1.y, fma(a2.x, b2.x, -a2.y * b2.y)))));
+  r.y = fma(a0.x, b0.y, fma(a0.y, b0.x, fma(a1.x, b1.y, fma(a1.y, b1.x, fma(a2.x, b2.y, a2.y * b2.x)))));
+  return r;
+}
+
 template <typename C>
 __device__ __forceinline__ void gmul3(const C* __restrict__ gh, C& v0, C& v1, C& v2) {
   C gg[6];
   load6(gh, gg);
-  const C g0 = gg[0], g1 = gg[1], g2 = gg[2], g3 = gg[3], g4 = gg[4], g5 = gg[5];
-  const C u0 = cadd(cadd(cmul(g0, v0), cmul(g1, v1)), cmul(g2, v2));
-  const C u1 = cadd(cadd(cmul(g1, v0), cmul(g3, v1)), cmul(g4, v2));
-  const C u2 = cadd(cadd(cmul(g2, v0), cmul(g4, v1)), cmul(g5, v2));
+  const C u0 = cdot3(gg[0], v0, gg[1], v1, gg[2], v2);
+  const C u1 = cdot3(gg[1], v0, gg[3], v1, gg[4], v2);
+  const C u2 = cdot3(gg[2], v0, gg[4], v1, gg[5], v2);
   v0 = u0;
   v1 = u1;
   v2 = u2;
@@ -416,7 +426,9 @@ __global__ void __launch_bounds__(256) k_y_rows(Geom g, C* __restrict__ work, co
 }
 
 // ------------------------------------------------------------------ 5-pass: z columns with Ghat
-// grid (ceil(py/G), px, nrhs); smem: tw[PZ] | s[PZ*3][G]
+// grid (nrhs, ceil(py/G), px): the right-hand sides of one Ghat tile are
+// neighbours in launch order, so a tile is read from HBM once and then hits L2
+// for the other right-hand sides.  smem: tw[PZ] | s[PZ*3][G]
 template <typename C, int PZ, int G>
 __global__ void __launch_bounds__(256) k_z_cols(Geom g, MvData<C> d) {
   constexpr int RA = Shape<PZ>::RA, LB = Shape<PZ>::LB, H = Shape<PZ>::H;
@@ -424,7 +436,7 @@ __global__ void __launch_bounds__(256) k_z_cols(Geom g, MvData<C> d) {
   extern __shared__ unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* s = tw + PZ;
-  const int ky0 = blockIdx.x * G, kx = blockIdx.y, b = blockIdx.z;
+  const int ky0 = blockIdx.y * G, kx = blockIdx.z, b = blockIdx.x;
   const int nz = g.nz, py = g.py;
   copy_tw(tw, d.twz, PZ);
   __syncthreads();
@@ -675,7 +687,7 @@ template <typename C>
 Err launch_z_cols(const Geom& g, const MvData<C>& d, int nrhs, cudaStream_t st) {
   const size_t sm = zcols_fast_smem<C>(g);
   const int G = zcols_g_rt(sizeof(C), g.pz);
-  const dim3 grid((g.py + G - 1) / G, g.px, nrhs);
+  const dim3 grid(nrhs, (g.py + G - 1) / G, g.px);
   switch (g.pz) {
 #define DDA_CASE(L_)                                                                      \
   case L_:                                                                                \
@@ -718,7 +730,15 @@ Err launch_matvec_fast(const Geom& g, const MvData<C>& d, const MvTune& t, const
   DDA_TRY(launch_x_fwd<C>(g, d, p, nrhs, conj, st));
   mark_pass(pass++, st);
   if (t.plane) {
-    DDA_TRY(launch_plane<C>(g, d, nrhs, t.thr_p, st));
+    if constexpr (sizeof(C) == 8) {
+      if (t.clus > 1) {
+        DDA_TRY(launch_plane_cluster_c64(g, d, t.clus, nrhs, st));
+      } else {
+        DDA_TRY(launch_plane<C>(g, d, nrhs, t.thr_p, st));
+      }
+    } else {
+      DDA_TRY(launch_plane<C>(g, d, nrhs, t.thr_p, st));
+    }
     mark_pass(pass++, st);
     add_launches(3);
   } else {

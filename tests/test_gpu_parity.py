@@ -103,6 +103,28 @@ def test_matvec_fast_kernels_match_direct_sum(D, w, pad):
             assert err <= tol, (w.name, dt, b, err)
 
 
+@pytest.mark.parametrize("sched", ["cluster2", "cluster4"])
+@pytest.mark.parametrize("w,pad", FAST_PADS[:3], ids=[w.name for w, _ in FAST_PADS[:3]])
+def test_cluster_plane_matches_direct_sum(D, monkeypatch, w, pad, sched):
+    """The plane pass split over a thread-block cluster, on plane pairs (32, 48) and (40, 40)
+    with odd and ragged boxes (pass-A rows shared unevenly between the CTAs)."""
+    monkeypatch.setenv("DDA_SCHEDULE", sched)
+    ctx = _ctx(D, w, pad)
+    prob = _oracle_problem(w)
+    p = _rand_p(ctx.nrhs, ctx.n, 18, torch.complex64)
+    ap = torch.empty_like(p)
+    ctx.dda_matvec(p, ap)
+    torch.cuda.synchronize()
+    info = D.dda_schedule_info(ctx, D.DDA_C64)
+    assert info[0] == 3 and info[4] == int(sched[-1]), info
+    pn = p.cpu().numpy().astype(np.complex128)
+    got = ap.cpu().numpy().astype(np.complex128)
+    for b in range(ctx.nrhs):
+        ref = odda.apply_a(prob, b, pn[b], "direct")
+        err = np.linalg.norm(got[b] - ref) / np.linalg.norm(ref)
+        assert err <= 1e-5, (w.name, sched, b, err)
+
+
 def test_fast_and_generic_engines_agree(D, monkeypatch):
     w = W.ELLIPSOID64
     out = {}
@@ -119,7 +141,7 @@ def test_fast_and_generic_engines_agree(D, monkeypatch):
     assert err <= 2e-6, err
 
 
-@pytest.mark.parametrize("sched", ["generic", "fast5", "plane512", "plane768", None])
+@pytest.mark.parametrize("sched", ["generic", "fast5", "plane512", "plane768", "cluster2", "cluster4", None])
 def test_every_schedule_matches_direct_rows(D, monkeypatch, sched):
     """Each launch schedule the autotuner can pick, pinned through DDA_SCHEDULE, on the 64x48x32 grid."""
     if sched:
@@ -138,6 +160,8 @@ def test_every_schedule_matches_direct_rows(D, monkeypatch, sched):
             assert info[0] == 5 and info[1] == 1
         if sched in ("plane512", "plane768") and dt == torch.complex64:
             assert info[0] == 3 and info[2] == int(sched[-3:])
+        if sched in ("cluster2", "cluster4") and dt == torch.complex64:
+            assert info[0] == 3 and info[4] == int(sched[-1])
         for b in range(ctx.nrhs):
             pb = p[b].cpu().numpy().astype(np.complex128)
             ref = oint.matvec_direct(prob.target.r, prob.kd, prob.rhs[b].inv_alpha, pb, rows=rows)

@@ -123,6 +123,64 @@ def algorithmic_bytes(sched_passes: int, n: int, box, pad, nrhs: int, csize: int
     return [v * csize for v in per], names
 
 
+# FP32 issue roofline of the GB300 SMs: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def algorithmic_flops(sched_passes: int, box, pad, nrhs: int):
+    """FP32 flops per launch of each pass: 5 L log2 L per complex FFT of length L (no credit for the
+    pruned zero halves), 66 flops per voxel for the 3x3 symmetric Fourier-space multiply."""
+    nx, ny, nz = box
+    px, py, pz = pad
+    fft = lambda L: 5.0 * L * math.log2(L)
+    xl = 3 * ny * nz * fft(px)                  # x lines, one direction
+    yl = 3 * nz * px * fft(py)
+    zl = 3 * px * py * fft(pz)
+    gm = 66.0 * px * py * pz
+    if sched_passes == 3:
+        per = [xl, 2 * yl + 2 * zl + gm, xl]
+    else:
+        per = [xl, yl, 2 * zl + gm, yl, xl]
+    return [v * nrhs for v in per]
+
+
+def cufft_product_ms(box, pad, nrhs: int, stream, iters: int = 10):
+    """Timed comparison only: the same zero-padded convolution with cuFFT (torch.fft) and torch
+    element-wise ops for the 3x3 Fourier-space multiply, on box-shaped input (no site gather or
+    scatter, no alpha^{-1} term), CUDA events on the launching stream."""
+    import torch
+    nx, ny, nz = box
+    px, py, pz = pad
+    g = torch.randn((6, pz, py, px), dtype=torch.complex64, device="cuda")
+    v = torch.randn((nrhs, 3, nz, ny, nx), dtype=torch.complex64, device="cuda")
+    idx = [[0, 1, 2], [1, 3, 4], [2, 4, 5]]
+
+    def prod():
+        f = torch.fft.fftn(v, s=(pz, py, px), dim=(-3, -2, -1))
+        u = torch.stack([g[idx[a][0]] * f[:, 0] + g[idx[a][1]] * f[:, 1] + g[idx[a][2]] * f[:, 2]
+                         for a in range(3)], dim=1)
+        return torch.fft.ifftn(u, dim=(-3, -2, -1))[..., :nz, :ny, :nx]
+
+    def ffts_only():
+        f = torch.fft.fftn(v, s=(pz, py, px), dim=(-3, -2, -1))
+        return torch.fft.ifftn(f, dim=(-3, -2, -1))
+
+    out = []
+    for fn in (prod, ffts_only):
+        for _ in range(2):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(iters):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1) / iters)
+    del g, v
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args, w):
     """Oracle arm: the FP64 CPU FFT-convolution product of the same workload."""
     from oracle import dda as odda
@@ -397,8 +455,22 @@ def main():
                 "algorithmic_bytes_per_launch": abytes[dom], "ms_per_launch": ms_pass[dom],
                 "passes_ms": {nm: float(v) for nm, v in zip(names, ms_pass)},
                 "schedule": {"passes": sched[0], "compile_time_kernels": bool(sched[1]),
-                             "plane_threads": sched[2], "tuned_for_nrhs": sched[3]},
+                             "plane_threads": sched[2], "tuned_for_nrhs": sched[3], "ctas_per_plane": sched[4]},
                 "product_ms": float(np.sum(ms_pass))}
+    flops = algorithmic_flops(len(ms_pass), box, pad, nrhs)
+    tfl = flops[dom] / (ms_pass[dom] * 1e-3) / 1e12
+    roofline["alu"] = {"bound": "fp32 issue", "achieved": tfl, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                       "frac": tfl / FP32_PEAK_TFLOPS, "flops_per_launch": flops[dom],
+                       "peak_kind": "nominal: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    try:
+        cu_ms, cu_fft_ms = cufft_product_ms(box, pad, nrhs, stream)
+        roofline["cufft_compare"] = {"cufft_product_ms": cu_ms, "cufft_ffts_only_ms": cu_fft_ms,
+                                     "ours_product_ms": float(np.sum(ms_pass)),
+                                     "ratio": cu_ms / float(np.sum(ms_pass)),
+                                     "note": "torch.fft (cuFFT) zero-padded 3-D FFT + inverse of 3 components "
+                                             "(+ torch 3x3 multiply for cufft_product_ms) on box-shaped input"}
+    except RuntimeError as exc:  # e.g. out of memory on the largest grids
+        roofline["cufft_compare"] = {"error": str(exc).splitlines()[0]}
 
     if rank == 0:
         line = {

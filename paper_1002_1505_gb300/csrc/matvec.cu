@@ -300,22 +300,35 @@ __global__ void k_fft_strided(C* data, int64_t estride, int64_t ninner, int64_t 
 // ------------------------------------------------------------------ Green tensor
 // A_ab(n) = exp(ikr)/r [k^2 (rh_a rh_b - d_ab) + (ikr - 1)/r^2 (3 rh_a rh_b - d_ab)] for offset n != 0
 // reachable by two sites (|n_x| < Nx ...), else 0.  Output Gw[6][pz][py][px].
-__global__ void k_green_fill(Geom g, double kd, double2* gw) {
-  const int64_t M = (int64_t)g.px * g.py * g.pz;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+// The interaction tensor of a lattice offset n, component c (xx, xy, xz, yy, yz, zz), is even
+// or odd in each of n_x, n_y, n_z: xy is odd in x and y, xz in x and z, yz in y and z, the
+// diagonal components even in all three.  Its zero-padded DFT inherits the same parity per
+// axis, so the FP64 build fills and transforms only what the parities do not determine:
+// the x transforms run on the rows with y <= Py/2, z <= Pz/2, the y transforms on the
+// planes with z <= Pz/2, and the missing halves are mirrored in between (7/12 of the FFT
+// work of a plain 3-D transform, 1/4 of the fill).
+__device__ __forceinline__ bool odd_in(int c, int axis) {
+  // bit a of the mask = odd in axis a (0 = x, 1 = y, 2 = z)
+  const int mask[6] = {0, 3, 5, 0, 6, 0};
+  return (mask[c] >> axis) & 1;
+}
+
+// q[c][zq][yq][x] for zq <= Pz/2, yq <= Py/2 and all x (offsets wrapped along x)
+__global__ void k_green_fill_q(Geom g, double kd, double2* q) {
+  const int hy1 = g.py / 2 + 1, hz1 = g.pz / 2 + 1;
+  const int64_t Q = (int64_t)g.px * hy1 * hz1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q; i += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(i % g.px);
     const int64_t rest = i / g.px;
-    const int y = (int)(rest % g.py), z = (int)(rest / g.py);
-    int ox, oy, oz;
-    bool ok = true;
-    if (x < g.nx) ox = x; else if (x > g.px - g.nx) ox = x - g.px; else { ok = false; ox = 0; }
-    if (y < g.ny) oy = y; else if (y > g.py - g.ny) oy = y - g.py; else { ok = false; oy = 0; }
-    if (z < g.nz) oz = z; else if (z > g.pz - g.nz) oz = z - g.pz; else { ok = false; oz = 0; }
-    if (ox == 0 && oy == 0 && oz == 0) ok = false;
+    const int y = (int)(rest % hy1), z = (int)(rest / hy1);
+    int ox = 0;
+    bool ok = y < g.ny && z < g.nz;
+    if (x < g.nx) ox = x; else if (x > g.px - g.nx) ox = x - g.px; else ok = false;
+    if (ox == 0 && y == 0 && z == 0) ok = false;
     double2 out[6];
     for (int c = 0; c < 6; ++c) out[c] = make_double2(0.0, 0.0);
     if (ok) {
-      const double rx = ox, ry = oy, rz = oz;
+      const double rx = ox, ry = y, rz = z;
       const double r2 = rx * rx + ry * ry + rz * rz;
       const double r = sqrt(r2);
       const double inv_r = 1.0 / r;
@@ -335,7 +348,42 @@ __global__ void k_green_fill(Geom g, double kd, double2* gw) {
         out[c] = make_double2(pref.x * inner.x - pref.y * inner.y, pref.x * inner.y + pref.y * inner.x);
       }
     }
-    for (int c = 0; c < 6; ++c) gw[(int64_t)c * M + i] = out[c];
+    for (int c = 0; c < 6; ++c) q[(int64_t)c * Q + i] = out[c];
+  }
+}
+
+// t[c][zq][y][kx] (all y) from q[c][zq][yq][kx]: rows y > Py/2 mirror Py - y with the y parity
+__global__ void k_green_expand_y(Geom g, const double2* __restrict__ q, double2* __restrict__ t) {
+  const int hy1 = g.py / 2 + 1, hz1 = g.pz / 2 + 1;
+  const int64_t Q = (int64_t)g.px * hy1 * hz1, T = (int64_t)g.px * g.py * hz1;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < 6 * T; o += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(o / T);
+    const int64_t i = o - c * T;
+    const int kx = (int)(i % g.px);
+    const int64_t rest = i / g.px;
+    const int y = (int)(rest % g.py), z = (int)(rest / g.py);
+    const bool mir = y > g.py / 2;
+    const int ys = mir ? g.py - y : y;
+    double2 v = q[(int64_t)c * Q + ((int64_t)z * hy1 + ys) * g.px + kx];
+    if (mir && odd_in(c, 1)) v = make_double2(-v.x, -v.y);
+    t[o] = v;
+  }
+}
+
+// f[c][z][ky][kx] (all z) from t[c][zq][ky][kx]: planes z > Pz/2 mirror Pz - z with the z parity
+__global__ void k_green_expand_z(Geom g, const double2* __restrict__ t, double2* __restrict__ f) {
+  const int hz1 = g.pz / 2 + 1;
+  const int64_t P = (int64_t)g.px * g.py, M = P * g.pz, T = P * hz1;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < 6 * M; o += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(o / M);
+    const int64_t i = o - c * M;
+    const int z = (int)(i / P);
+    const int64_t xy = i - (int64_t)z * P;
+    const bool mir = z > g.pz / 2;
+    const int zs = mir ? g.pz - z : z;
+    double2 v = t[(int64_t)c * T + (int64_t)zs * P + xy];
+    if (mir && odd_in(c, 2)) v = make_double2(-v.x, -v.y);
+    f[o] = v;
   }
 }
 
@@ -526,16 +574,25 @@ void init_kernel_attrs() {
 Err build_green(const Geom& g, double kd, const double2* twx, const double2* twy, const double2* twz,
                 double2* gw, double2* ghat128, float2* ghat64, cudaStream_t st) {
   const int64_t M = (int64_t)g.px * g.py * g.pz;
-  const int blocks = (int)std::min<int64_t>((M + 255) / 256, 152 * 16);
-  k_green_fill<<<blocks, 256, 0, st>>>(g, kd, gw);
+  const int hy1 = g.py / 2 + 1, hz1 = g.pz / 2 + 1;
+  const int64_t Q = (int64_t)g.px * hy1 * hz1, T = (int64_t)g.px * g.py * hz1;
+  auto nblk = [](int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 16); };
+  // q (in gw): the quarter y <= Py/2, z <= Pz/2; x rows transformed in place
+  double2* q = gw;
+  k_green_fill_q<<<nblk(Q), 256, 0, st>>>(g, kd, q);
   DDA_CU(cudaGetLastError());
-  g_launches += 1;
-  // x: contiguous rows; y: stride px; z: stride px*py; 6 components as outer batch
-  DDA_TRY(fft_rows<double2>(gw, 6 * (int64_t)g.py * g.pz, g.px, g.plx, twx, g.px, g.px, false, st));
-  DDA_TRY(fft_strided<double2>(gw, g.py, g.px, g.px, 6 * (int64_t)g.pz, (int64_t)g.px * g.py, g.ply, twy, false, st));
+  DDA_TRY(fft_rows<double2>(q, 6 * (int64_t)hy1 * hz1, g.px, g.plx, twx, g.px, g.px, false, st));
+  // t (in the ghat128 buffer, free until the pack): planes z <= Pz/2, all y; y columns transformed
+  double2* t = ghat128;
+  k_green_expand_y<<<nblk(6 * T), 256, 0, st>>>(g, q, t);
+  DDA_CU(cudaGetLastError());
+  DDA_TRY(fft_strided<double2>(t, g.py, g.px, g.px, 6 * (int64_t)hz1, (int64_t)g.px * g.py, g.ply, twy, false, st));
+  // f (in gw): all z; z columns transformed
+  k_green_expand_z<<<nblk(6 * M), 256, 0, st>>>(g, t, gw);
+  DDA_CU(cudaGetLastError());
   DDA_TRY(fft_strided<double2>(gw, g.pz, (int64_t)g.px * g.py, (int64_t)g.px * g.py, 6, M, g.plz, twz, false, st));
-  const int pb = (int)std::min<int64_t>((6 * M + 255) / 256, 152 * 16);
-  k_green_pack<<<pb, 256, 0, st>>>(g, gw, ghat128, ghat64);
+  g_launches += 3;
+  k_green_pack<<<nblk(6 * M), 256, 0, st>>>(g, gw, ghat128, ghat64);
   DDA_CU(cudaGetLastError());
   g_launches += 1;
   return Err::Ok();

@@ -243,13 +243,15 @@ DDA_API dda_status dda_profile_matvec(dda_ctx *ctx, int nrhs, int dtype, int ite
  * first product for a given RHS count times the candidate schedules and keeps
  * the fastest) or pinned by the DDA_SCHEDULE environment variable at
  * dda_build_green_fft time ("generic", "fast5", "plane512", "plane768",
- * "cluster2", "cluster4").
+ * "cluster2", "cluster4"; DDA_XTILE = 4, 8 or 16 pins the x passes' tile
+ * height).
  * info[0] = passes (3 = fused y-z plane, 5 = split), info[1] = 1 when the
  * compile-time-length kernels are used, info[2] = threads per CTA of the plane
  * kernel (0 if none), info[3] = RHS count the choice was tuned for (0 = not
  * tuned), info[4] = CTAs per plane (1, or the thread-block cluster size when
- * the plane pass is split over a cluster). */
-DDA_API dda_status dda_schedule_info(dda_ctx *ctx, int dtype, int32_t info[5]);
+ * the plane pass is split over a cluster), info[5] = y rows per CTA of the x
+ * passes (0 for the generic engine). */
+DDA_API dda_status dda_schedule_info(dda_ctx *ctx, int dtype, int32_t info[6]);
 
 /* ---------------------------------------------------------------------------
  * Learned warm start (the guide has no counterpart: the solver accepts any

@@ -405,7 +405,7 @@ Err ensure_tuned(dda_ctx* c, int nrhs) {
   }
   cand.push_back(t5);
   dda::MvTune best = cand[0];
-  if (cand.size() > 1) {
+  {
     const size_t bytes = sizeof(C) * (size_t)nrhs * 3 * c->n;
     DDA_TRY(grow(c, (char**)&c->d_tunebuf, 2 * bytes));
     C* p = (C*)c->d_tunebuf;
@@ -416,18 +416,35 @@ Err ensure_tuned(dda_ctx* c, int nrhs) {
     DDA_CU(cudaEventCreate(&e1));
     float best_ms = 1e30f;
     Err err = Err::Ok();
-    for (const dda::MvTune& t : cand) {
+    // one warm-up product, then three timed between events on the context's stream
+    auto time_one = [&](const dda::MvTune& t) {
       apply_tune<C>(c, t);
       err = matvec<C>(c, p, ap, nrhs, 0, false);
-      if (!err.ok()) break;
+      if (!err.ok()) return;
       cudaEventRecord(e0, c->stream);
       for (int r = 0; r < 3 && err.ok(); ++r) err = matvec<C>(c, p, ap, nrhs, 0, false);
       cudaEventRecord(e1, c->stream);
-      if (!err.ok()) break;
+      if (!err.ok()) return;
       cudaEventSynchronize(e1);
       float ms = 0;
       cudaEventElapsedTime(&ms, e0, e1);
       if (ms < best_ms) { best_ms = ms; best = t; }
+    };
+    for (const dda::MvTune& t : cand) {
+      time_one(t);
+      if (!err.ok()) break;
+    }
+    // then the x passes' tile height for the chosen schedule (short tiles give small batches more CTAs)
+    if (err.ok()) {
+      const dda::MvTune chosen = best;
+      for (int ty : {4, 8}) {
+        if (!dda::x_tile_height_ok(sizeof(C), g0.px, ty) || ty == dda::x_tile_height_default(sizeof(C), g0.px))
+          continue;
+        dda::MvTune t = chosen;
+        t.xty = ty;
+        time_one(t);
+        if (!err.ok()) break;
+      }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -852,6 +869,13 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
         if (t64.plane_ok && dda::plane_cluster_capacity_c64(g64, S, smax) > 0) t64.clus = S;
         c->forced_schedule = true;
       }
+    }
+    // DDA_XTILE pins the x passes' tile height (y rows per CTA: 4, 8 or 16 where instantiated)
+    if (const char* f = std::getenv("DDA_XTILE")) {
+      const int ty = std::atoi(f);
+      if (t64.fast && dda::x_tile_height_ok(sizeof(float2), g.px, ty)) t64.xty = ty;
+      if (t128.fast && dda::x_tile_height_ok(sizeof(double2), g.px, ty)) t128.xty = ty;
+      c->forced_schedule = true;
     }
     if (!t64.plane) g64.ys = g.py;
     if (!t128.plane) g128.ys = g.py;
@@ -1366,7 +1390,7 @@ dda_status dda_profile_matvec(dda_ctx* c, int nrhs, int dtype, int iters, double
   return DDA_OK;
 }
 
-dda_status dda_schedule_info(dda_ctx* c, int dtype, int32_t info[5]) {
+dda_status dda_schedule_info(dda_ctx* c, int dtype, int32_t info[6]) {
   if (!c || !info) return DDA_EINVAL;
   if (!c->have_green) return fail(c, Err::make(DDA_ESTATE, "build the Green tensor first"));
   if (dtype != DDA_C64 && dtype != DDA_C128) return fail(c, Err::make(DDA_EINVAL, "bad dtype"));
@@ -1376,6 +1400,13 @@ dda_status dda_schedule_info(dda_ctx* c, int dtype, int32_t info[5]) {
   info[2] = t.plane ? (t.clus == 2 ? 384 : t.clus == 4 ? 256 : t.thr_p) : 0;
   info[3] = c->tuned_nrhs[dtype == DDA_C64 ? 0 : 1];
   info[4] = t.plane && t.clus > 1 ? t.clus : 1;
+  {
+    const dda::Geom& g = dtype == DDA_C64 ? c->g64 : c->g128;
+    const size_t cs = dtype == DDA_C64 ? sizeof(float2) : sizeof(double2);
+    info[5] = !t.fast ? 0
+                      : (t.xty > 0 && dda::x_tile_height_ok(cs, g.px, t.xty) ? t.xty
+                                                                             : dda::x_tile_height_default(cs, g.px));
+  }
   return DDA_OK;
 }
 

@@ -90,6 +90,7 @@ struct MvTune {
   bool fast = false;  // compile-time-length kernels exist for px, py, pz (matvec_fast.cuh)
   bool plane_ok = false;  // the fast 3-pass plane kernel exists and fits for this grid
   int clus = 0;           // plane pass split over a cluster of this many CTAs (0: one CTA per plane)
+  int xty = 0;            // y rows per CTA of the compile-time x passes (0: the length's default)
 };
 
 // Enqueue ap = A p for nrhs right-hand sides (rhs0 = index of the first one for alpha).
@@ -110,6 +111,10 @@ void cluster_optin_c64(int smax);
 void fast_optin_c128(int smax);
 // Does a fast schedule exist for this grid (all lengths instantiated, tiles fit)?  Sets t.fast and t.plane.
 void choose_fast_schedule(const Geom& g, bool c64, int smax, MvTune* t);
+// x-pass tile heights (y rows per CTA) of the compile-time kernels: the default for a length, and
+// whether a height is instantiated
+int x_tile_height_default(size_t csize, int px);
+bool x_tile_height_ok(size_t csize, int px, int ty);
 // profiling hook: record the i-th pass event if per-pass events are on
 void mark_pass(int i, cudaStream_t st);
 size_t x_smem_bytes(const Geom& g, const MvTune& t, size_t csize);

@@ -580,6 +580,13 @@ template <typename C, int PX> constexpr int x_ty() {
   return sizeof(C) == 8 ? (PX <= 128 ? 16 : 8) : (PX <= 128 ? 8 : 4);
 }
 inline int x_ty_rt(size_t csize, int px) { return csize == 8 ? (px <= 128 ? 16 : 8) : (px <= 128 ? 8 : 4); }
+// the tile heights instantiated besides the default (small batches want more, shorter tiles)
+inline bool x_ty_valid(size_t csize, int px, int ty) {
+  return ty == x_ty_rt(csize, px) || ty == 4 || (ty == 8 && x_ty_rt(csize, px) > 8);
+}
+inline int x_ty_pick(const MvTune& t, size_t csize, int px) {
+  return (t.xty > 0 && x_ty_valid(csize, px, t.xty)) ? t.xty : x_ty_rt(csize, px);
+}
 
 // z columns per CTA of the 5-pass z kernel: widest tile under ~110 KB of shared memory
 constexpr int zcols_g_rt(size_t csize, int pz) {
@@ -589,8 +596,8 @@ constexpr int zcols_g_rt(size_t csize, int pz) {
 inline int odd_pitch(int n) { return (n % 2) ? n : n + 1; }
 
 template <typename C>
-size_t x_fast_smem(const Geom& g) {
-  const int TY = x_ty_rt(sizeof(C), g.px);
+size_t x_fast_smem(const Geom& g, int TY = 0) {
+  if (TY <= 0) TY = x_ty_rt(sizeof(C), g.px);
   return sizeof(C) * ((size_t)g.px + (size_t)3 * TY * odd_pitch(g.nx) + (size_t)3 * g.px * TY);
 }
 template <typename C>
@@ -607,16 +614,34 @@ size_t zcols_fast_smem(const Geom& g) {
   return sizeof(C) * ((size_t)g.pz + (size_t)g.pz * 3 * zcols_g_rt(sizeof(C), g.pz));
 }
 
+// k_x_fwd / k_x_inv for the tile height TY chosen at run time (the default or 4 / 8)
+template <typename C, int L_, typename F>
+Err with_ty(int ty, F&& f) {
+  constexpr int D = x_ty<C, L_>();
+  if (ty == D) return f(std::integral_constant<int, D>{});
+  if constexpr (D != 4) {
+    if (ty == 4) return f(std::integral_constant<int, 4>{});
+  }
+  if constexpr (D > 8) {
+    if (ty == 8) return f(std::integral_constant<int, 8>{});
+  }
+  return Err::make(DDA_EUNSUPPORTED, "x tile height not instantiated");
+}
+
 template <typename C>
-Err launch_x_fwd(const Geom& g, const MvData<C>& d, const C* p, int nrhs, bool conj, cudaStream_t st) {
-  const int TY = x_ty_rt(sizeof(C), g.px);
-  const size_t sm = x_fast_smem<C>(g);
+Err launch_x_fwd(const Geom& g, const MvData<C>& d, const MvTune& t, const C* p, int nrhs, bool conj,
+                 cudaStream_t st) {
+  const int TY = x_ty_pick(t, sizeof(C), g.px);
+  const size_t sm = x_fast_smem<C>(g, TY);
   const dim3 grid((g.ny + TY - 1) / TY, g.nz, nrhs);
   const int ip = odd_pitch(g.nx);
   switch (g.px) {
-#define DDA_CASE(L_)                                                                 \
-  case L_:                                                                           \
-    k_x_fwd<C, L_, x_ty<C, L_>()><<<grid, 256, sm, st>>>(g, d, p, conj, ip);         \
+#define DDA_CASE(L_)                                                                      \
+  case L_:                                                                                \
+    DDA_TRY((with_ty<C, L_>(TY, [&](auto tyc) {                                         \
+      k_x_fwd<C, L_, decltype(tyc)::value><<<grid, 256, sm, st>>>(g, d, p, conj, ip);     \
+      return Err::Ok();                                                                   \
+    })));                                                                                 \
     break;
     DDA_FAST_LENGTHS(DDA_CASE)
 #undef DDA_CASE
@@ -627,16 +652,19 @@ Err launch_x_fwd(const Geom& g, const MvData<C>& d, const C* p, int nrhs, bool c
 }
 
 template <typename C>
-Err launch_x_inv(const Geom& g, const MvData<C>& d, const C* p, C* ap, int nrhs, int rhs0, bool conj,
-                 cudaStream_t st) {
-  const int TY = x_ty_rt(sizeof(C), g.px);
-  const size_t sm = x_fast_smem<C>(g);
+Err launch_x_inv(const Geom& g, const MvData<C>& d, const MvTune& t, const C* p, C* ap, int nrhs, int rhs0,
+                 bool conj, cudaStream_t st) {
+  const int TY = x_ty_pick(t, sizeof(C), g.px);
+  const size_t sm = x_fast_smem<C>(g, TY);
   const dim3 grid((g.ny + TY - 1) / TY, g.nz, nrhs);
   const int ip = odd_pitch(g.nx);
   switch (g.px) {
-#define DDA_CASE(L_)                                                                       \
-  case L_:                                                                                 \
-    k_x_inv<C, L_, x_ty<C, L_>()><<<grid, 256, sm, st>>>(g, d, p, ap, rhs0, conj, ip);     \
+#define DDA_CASE(L_)                                                                            \
+  case L_:                                                                                      \
+    DDA_TRY((with_ty<C, L_>(TY, [&](auto tyc) {                                               \
+      k_x_inv<C, L_, decltype(tyc)::value><<<grid, 256, sm, st>>>(g, d, p, ap, rhs0, conj, ip);  \
+      return Err::Ok();                                                                         \
+    })));                                                                                       \
     break;
     DDA_FAST_LENGTHS(DDA_CASE)
 #undef DDA_CASE
@@ -701,12 +729,26 @@ Err launch_z_cols(const Geom& g, const MvData<C>& d, int nrhs, cudaStream_t st) 
   return Err::Ok();
 }
 
+template <typename C, int L_>
+void optin_x(int smax) {
+  constexpr int D = x_ty<C, L_>();
+  cudaFuncSetAttribute(k_x_fwd<C, L_, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  cudaFuncSetAttribute(k_x_inv<C, L_, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  if constexpr (D != 4) {
+    cudaFuncSetAttribute(k_x_fwd<C, L_, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    cudaFuncSetAttribute(k_x_inv<C, L_, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  }
+  if constexpr (D > 8) {
+    cudaFuncSetAttribute(k_x_fwd<C, L_, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    cudaFuncSetAttribute(k_x_inv<C, L_, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  }
+}
+
 // Opt every instantiation of this precision into the device's maximum dynamic shared memory.
 template <typename C>
 void optin_all(int smax) {
 #define DDA_CASE(L_)                                                                                                 \
-  cudaFuncSetAttribute(k_x_fwd<C, L_, x_ty<C, L_>()>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);         \
-  cudaFuncSetAttribute(k_x_inv<C, L_, x_ty<C, L_>()>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);         \
+  optin_x<C, L_>(smax);                                                                                              \
   cudaFuncSetAttribute(k_y_rows<C, L_, kRowsPerCta, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);   \
   cudaFuncSetAttribute(k_y_rows<C, L_, kRowsPerCta, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);    \
   cudaFuncSetAttribute(k_z_cols<C, L_, zcols_g_rt(sizeof(C), L_)>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
@@ -727,7 +769,7 @@ Err launch_matvec_fast(const Geom& g, const MvData<C>& d, const MvTune& t, const
                        bool conj, cudaStream_t st) {
   int pass = 0;
   mark_pass(pass++, st);
-  DDA_TRY(launch_x_fwd<C>(g, d, p, nrhs, conj, st));
+  DDA_TRY(launch_x_fwd<C>(g, d, t, p, nrhs, conj, st));
   mark_pass(pass++, st);
   if (t.plane) {
     if constexpr (sizeof(C) == 8) {
@@ -751,7 +793,7 @@ Err launch_matvec_fast(const Geom& g, const MvData<C>& d, const MvTune& t, const
     mark_pass(pass++, st);
     add_launches(5);
   }
-  DDA_TRY(launch_x_inv<C>(g, d, p, ap, nrhs, rhs0, conj, st));
+  DDA_TRY(launch_x_inv<C>(g, d, t, p, ap, nrhs, rhs0, conj, st));
   mark_pass(pass++, st);
   return Err::Ok();
 }

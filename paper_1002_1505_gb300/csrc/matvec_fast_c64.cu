@@ -9,6 +9,9 @@ Err launch_matvec_fast<float2>(const Geom& g, const MvData<float2>& d, const MvT
 }
 void fast_optin_c64(int smax) { fast::optin_all<float2>(smax); }
 
+int x_tile_height_default(size_t csize, int px) { return fast::x_ty_rt(csize, px); }
+bool x_tile_height_ok(size_t csize, int px, int ty) { return fast::x_ty_valid(csize, px, ty); }
+
 void choose_fast_schedule(const Geom& g, bool c64, int smax, MvTune* t) {
   t->fast = fast::fast_length(g.px) && fast::fast_length(g.py) && fast::fast_length(g.pz);
   if (!t->fast) return;

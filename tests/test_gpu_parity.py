@@ -125,6 +125,29 @@ def test_cluster_plane_matches_direct_sum(D, monkeypatch, w, pad, sched):
         assert err <= 1e-5, (w.name, sched, b, err)
 
 
+@pytest.mark.parametrize("xtile", ["4", "8"])
+@pytest.mark.parametrize("w,pad", FAST_PADS, ids=[w.name for w, _ in FAST_PADS])
+def test_x_tile_heights_match_direct_sum(D, monkeypatch, w, pad, xtile):
+    """The x passes with short tiles (4 or 8 y rows per CTA), both precisions, ragged y tiles."""
+    monkeypatch.setenv("DDA_XTILE", xtile)
+    ctx = _ctx(D, w, pad)
+    prob = _oracle_problem(w)
+    info = D.dda_schedule_info(ctx, D.DDA_C64)
+    if info[1]:
+        assert info[5] == int(xtile), info
+    for dt, tol in ((torch.complex128, 1e-12), (torch.complex64, 1e-5)):
+        p = _rand_p(ctx.nrhs, ctx.n, 19, dt)
+        ap = torch.empty_like(p)
+        ctx.dda_matvec(p, ap)
+        torch.cuda.synchronize()
+        pn = p.cpu().numpy().astype(np.complex128)
+        got = ap.cpu().numpy().astype(np.complex128)
+        for b in range(ctx.nrhs):
+            ref = odda.apply_a(prob, b, pn[b], "direct")
+            err = np.linalg.norm(got[b] - ref) / np.linalg.norm(ref)
+            assert err <= tol, (w.name, xtile, dt, b, err)
+
+
 def test_fast_and_generic_engines_agree(D, monkeypatch):
     w = W.ELLIPSOID64
     out = {}

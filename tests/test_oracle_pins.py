@@ -272,6 +272,34 @@ def test_lu_bicgstab_ccg_agree_sphere12():
     assert np.linalg.norm(r) / np.linalg.norm(prob.rhs[0].e_inc) < 1e-11
 
 
+def test_bicgstab_l_reduces_to_bicgstab_and_solves():
+    """BiCGstab(l) (Sleijpen & Fokkema 1993; the guide's PBCGS2 family): with l = 1 it is BiCGstab
+    step for step (same iterates up to rounding), and with l = 2, 4 it converges to the LU solution."""
+    w = W.SPHERE12
+    prob = dda.build_problem(w.shape, w.shpar, w.m, w.x, w.prescription, w.orientations)
+    rh = prob.rhs[1]
+    shape = rh.e_inc.shape
+
+    def op(v):
+        return dda.apply_a(prob, 1, v.reshape(shape), "direct").reshape(-1)
+    e = rh.e_inc.reshape(-1)
+    x1, it1, h1 = solvers.bicgstab_l(op, e, ell=1, tol=1e-10)
+    xb, itb, hb = solvers.bicgstab(op, e, tol=1e-10)
+    # bicgstab may stop on its half step; compare the residual histories where both are full steps
+    n = min(len(h1), len(hb)) - 1
+    assert n >= 5
+    assert np.allclose(h1[:n], hb[:n], rtol=1e-6, atol=0)
+    p_lu = solvers.lu_solve(interaction.dense_matrix(prob.target.r, prob.kd, rh.inv_alpha), e)
+    for ell in (2, 4):
+        x, it, h = solvers.bicgstab_l(op, e, ell=ell, tol=1e-12)
+        assert h[-1] <= 1e-12 and it % ell == 0
+        assert np.linalg.norm(x - p_lu) / np.linalg.norm(p_lu) < 1e-9
+        # the recursive residual is the true one
+        assert np.linalg.norm(e - op(x)) / np.linalg.norm(e) < 1e-11
+    p2, its = dda.solve(prob, "bicgstab2", tol=1e-10)
+    assert all(i > 0 for i in its)
+
+
 # ----------------------------------------------------------------------------- observables
 
 def test_real_index_has_zero_absorption():

@@ -64,8 +64,12 @@ enum { DDA_C64 = 1, DDA_C128 = 2 };
 enum { DDA_ELLIPSOID = 1, DDA_RCTGLPRSM = 2, DDA_CYLINDER1 = 3, DDA_HEX_PRISM = 4 };
 /* Polarizability prescriptions (guide, "Dipole Polarizabilities"). */
 enum { DDA_CM = 1, DDA_LATTDR = 2, DDA_GKDLDR = 3 };
-/* Iterative solvers (guide, "Choice of Iterative Algorithm"). */
-enum { DDA_BICGSTAB = 1, DDA_CCG = 2 };
+/* Iterative solvers (guide, "Choice of Iterative Algorithm"): BiCGstab (van
+ * der Vorst 1992, the guide's PBCGST), CCG (conjugate gradients on the normal
+ * equations, Petravic & Kuo-Petravic 1979, the guide's PETRKP) and
+ * BiCGstab(2) (Sleijpen & Fokkema 1993, the method family of the guide's
+ * recommended PBCGS2, without that routine's reliability refinements). */
+enum { DDA_BICGSTAB = 1, DDA_CCG = 2, DDA_BICGSTAB2 = 3 };
 /* Arithmetic of the solve: all complex64, all complex128, or complex64 inner
  * iterations refined against complex128 true residuals. */
 enum { DDA_PREC_C64 = 1, DDA_PREC_C128 = 2, DDA_PREC_MIXED = 3 };
@@ -174,14 +178,14 @@ DDA_API dda_status dda_matvec(dda_ctx *ctx, const void *p_dev, void *ap_dev, int
 DDA_API dda_status dda_matvec_noalloc(dda_ctx *ctx, const void *p_dev, void *ap_dev, int nrhs, int dtype);
 
 typedef struct {
-  int solver;        /* DDA_BICGSTAB or DDA_CCG */
+  int solver;        /* DDA_BICGSTAB, DDA_CCG or DDA_BICGSTAB2 */
   int precision;     /* DDA_PREC_C64 / DDA_PREC_C128 / DDA_PREC_MIXED */
   double tol;        /* stop when |E - A P| / |E| <= tol for every RHS */
   int maxit;         /* iteration cap (inner iterations summed for MIXED) */
   double inner_tol;  /* MIXED: relative reduction asked of each inner solve (0 = 1e-3) */
   double timeout_ms; /* wall-clock budget, 0 = none; exceeded -> DDA_ETIMEOUT */
   int warm_start;    /* 1 = p_dev holds the initial guess, 0 = start from P = 0 */
-  int check_every;   /* iterations between host convergence checks (0 = 8) */
+  int check_every;   /* iterations between host convergence checks (0 = 8; BiCGstab(2): cycles of two iterations) */
   int normal_eq;     /* 1 = also evaluate the guide's normal-equation ratio at exit (2 extra FP64 products) */
   int use_graph;     /* 1 = replay the iterations as a captured CUDA graph, 0 = plain launches */
 } dda_solve_opts;

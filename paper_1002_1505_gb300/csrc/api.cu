@@ -332,14 +332,17 @@ template <> struct Sel<double2> {
 };
 
 // ap = A p over nrhs RHS starting at RHS index rhs0 (chunked by workspace capacity)
+// ks (optional): the solver state of RHS rhs0.. ; RHS whose solve has finished are skipped
 template <typename C>
-Err matvec(dda_ctx* c, const C* p, C* ap, int nrhs, int rhs0, bool conj) {
+Err matvec(dda_ctx* c, const C* p, C* ap, int nrhs, int rhs0, bool conj, const dda::KState* ks = nullptr) {
   int cap = 0;
   DDA_TRY(ensure_work<C>(c, nrhs, &cap));
   const int64_t n3 = 3 * c->n;
+  dda::MvData<C> d = Sel<C>::data(c);
   for (int b0 = 0; b0 < nrhs; b0 += cap) {
     const int nb = std::min(cap, nrhs - b0);
-    DDA_TRY(dda::launch_matvec<C>(Sel<C>::geom(c), Sel<C>::data(c), Sel<C>::tune(c), p + b0 * n3, ap + b0 * n3, nb,
+    d.ks = ks ? ks + b0 : nullptr;  // indexed by RHS within this launch
+    DDA_TRY(dda::launch_matvec<C>(Sel<C>::geom(c), d, Sel<C>::tune(c), p + b0 * n3, ap + b0 * n3, nb,
                                   rhs0 + b0, conj, c->stream));
   }
   return Err::Ok();
@@ -484,6 +487,8 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
   dda::KState* ks = c->d_ks;
   cudaStream_t st = c->stream;
   const bool ccg = (o.solver == DDA_CCG);
+  const bool b2 = (o.solver == DDA_BICGSTAB2);
+  if (b2 && !kv.u2) return Err::make(DDA_ESTATE, "BiCGstab(2) needs the extra Krylov vector");
   if (have_x0) {
     DDA_TRY(matvec<C>(c, kv.x, kv.r, nrhs, 0, false));
     stats->matvecs += 1;
@@ -493,21 +498,38 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
     DDA_TRY(matvec<C>(c, kv.r, kv.s, nrhs, 0, true));
     DDA_TRY(dda::ccg_start<C>(kv, ks, rb, nrhs, n3, st));
     stats->matvecs += 1;
+  } else if (b2) {
+    DDA_TRY(dda::b2_init<C>(kv, ks, rb, nrhs, n3, tol, have_x0, st));
   } else {
     DDA_TRY(dda::bicg_init<C>(kv, ks, rb, nrhs, n3, tol, have_x0, st));
   }
+  // one_iter: one BiCGstab / CCG iteration (2 products), or one BiCGstab(2) cycle (4 products)
   auto one_iter = [&]() -> Err {
-    if (ccg) {
-      DDA_TRY(matvec<C>(c, kv.p, kv.v, nrhs, 0, false));
+    if (b2) {
+      // r0 = r, r1 = s, r2 = t, u0 = p, u1 = v, u2 = u2
+      DDA_TRY(dda::b2_u_update<C>(kv, ks, 0, nrhs, n3, st));
+      DDA_TRY(matvec<C>(c, kv.p, kv.v, nrhs, 0, false, ks));
+      DDA_TRY(dda::b2_alpha<C>(kv, ks, rb, 0, nrhs, n3, st));
+      DDA_TRY(dda::b2_r_update<C>(kv, ks, 0, nrhs, n3, st));
+      DDA_TRY(matvec<C>(c, kv.r, kv.s, nrhs, 0, false, ks));
+      DDA_TRY(dda::b2_beta<C>(kv, ks, rb, nrhs, n3, st));
+      DDA_TRY(dda::b2_u_update<C>(kv, ks, 1, nrhs, n3, st));
+      DDA_TRY(matvec<C>(c, kv.v, kv.u2, nrhs, 0, false, ks));
+      DDA_TRY(dda::b2_alpha<C>(kv, ks, rb, 1, nrhs, n3, st));
+      DDA_TRY(dda::b2_r_update<C>(kv, ks, 1, nrhs, n3, st));
+      DDA_TRY(matvec<C>(c, kv.s, kv.t, nrhs, 0, false, ks));
+      DDA_TRY(dda::b2_mr<C>(kv, ks, rb, nrhs, n3, st));
+    } else if (ccg) {
+      DDA_TRY(matvec<C>(c, kv.p, kv.v, nrhs, 0, false, ks));
       DDA_TRY(dda::ccg_alpha_update<C>(kv, ks, rb, nrhs, n3, st));
-      DDA_TRY(matvec<C>(c, kv.r, kv.s, nrhs, 0, true));
+      DDA_TRY(matvec<C>(c, kv.r, kv.s, nrhs, 0, true, ks));
       DDA_TRY(dda::ccg_beta_update<C>(kv, ks, rb, nrhs, n3, st));
     } else {
       DDA_TRY(dda::bicg_p_update<C>(kv, ks, nrhs, n3, st));
-      DDA_TRY(matvec<C>(c, kv.p, kv.v, nrhs, 0, false));
+      DDA_TRY(matvec<C>(c, kv.p, kv.v, nrhs, 0, false, ks));
       DDA_TRY(dda::bicg_alpha<C>(kv, ks, rb, nrhs, n3, st));
       DDA_TRY(dda::bicg_s_update<C>(kv, ks, rb, nrhs, n3, st));
-      DDA_TRY(matvec<C>(c, kv.s, kv.t, nrhs, 0, false));
+      DDA_TRY(matvec<C>(c, kv.s, kv.t, nrhs, 0, false, ks));
       DDA_TRY(dda::bicg_omega<C>(kv, ks, rb, nrhs, n3, st));
       DDA_TRY(dda::bicg_xr_update<C>(kv, ks, rb, nrhs, n3, st));
     }
@@ -560,6 +582,7 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
   std::vector<dda::KState> hk(nrhs);
   int it = 0;
   Err res = Err::Ok();
+  const int it_per_call = b2 ? 2 : 1;  // iterations (2 products each) per one_iter
   const int mv_per_it = 2;
   while (true) {
     DDA_CU(cudaMemcpyAsync(c->h_pinned, ks, sizeof(dda::KState) * nrhs, cudaMemcpyDeviceToHost, st));
@@ -580,8 +603,8 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
       for (int k = 0; k < every && res.ok(); ++k) res = one_iter();
       if (!res.ok()) break;
     }
-    it += every;
-    stats->matvecs += mv_per_it * every;
+    it += every * it_per_call;
+    stats->matvecs += mv_per_it * every * it_per_call;
   }
   DDA_TRY(res);
   stats->iters.resize(nrhs);
@@ -985,6 +1008,7 @@ Err kvec_alloc(dda_ctx* c, dda::KrylovVecs<C>* kv, int nvec_extra) {
   const size_t el = (size_t)c->nrhs * 3 * c->n;
   kv->x = base; kv->r = base + el; kv->rhat = base + 2 * el; kv->p = base + 3 * el;
   kv->v = base + 4 * el; kv->s = base + 5 * el; kv->t = base + 6 * el; kv->b = base + 7 * el;
+  kv->u2 = nvec_extra >= 1 ? base + 8 * el : nullptr;
   return Err::Ok();
 }
 
@@ -1015,7 +1039,8 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
   if (!c->have_alpha || !c->have_green)
     return fail(c, Err::make(DDA_ESTATE, "set target, incidence, Green tensor and alpha first"));
   dda_solve_opts o = *opt;
-  if (o.solver != DDA_BICGSTAB && o.solver != DDA_CCG) return fail(c, Err::make(DDA_EINVAL, "unknown solver"));
+  if (o.solver != DDA_BICGSTAB && o.solver != DDA_CCG && o.solver != DDA_BICGSTAB2)
+    return fail(c, Err::make(DDA_EINVAL, "unknown solver"));
   if (o.precision < DDA_PREC_C64 || o.precision > DDA_PREC_MIXED)
     return fail(c, Err::make(DDA_EINVAL, "unknown precision"));
   if (!(o.tol > 0) || o.maxit < 1) return fail(c, Err::make(DDA_EINVAL, "tol must be > 0 and maxit >= 1"));
@@ -1058,7 +1083,7 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
     int outer = 0;
     if (o.precision == DDA_PREC_C128) {
       dda::KrylovVecs<double2> kv;
-      e = kvec_alloc<double2>(c, &kv, 0);
+      e = kvec_alloc<double2>(c, &kv, o.solver == DDA_BICGSTAB2 ? 1 : 0);
       if (e.ok()) {
         cudaMemcpyAsync(kv.b, c->d_e128, sizeof(double2) * el, cudaMemcpyDeviceToDevice, c->stream);
         if (o.warm_start) cudaMemcpyAsync(kv.x, P, sizeof(double2) * el, cudaMemcpyDeviceToDevice, c->stream);
@@ -1072,7 +1097,7 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
       }
     } else if (o.precision == DDA_PREC_C64) {
       dda::KrylovVecs<float2> kv;
-      e = kvec_alloc<float2>(c, &kv, 0);
+      e = kvec_alloc<float2>(c, &kv, o.solver == DDA_BICGSTAB2 ? 1 : 0);
       if (e.ok()) e = dda::convert_from_c128<float2>(c->d_e128, kv.b, el, c->stream);
       if (e.ok() && o.warm_start) e = dda::convert_from_c128<float2>(P, kv.x, el, c->stream);
       SolveStats s;
@@ -1086,7 +1111,7 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
     } else {
       // mixed: inner complex64 solves of A d = r, r from FP64 true residuals
       dda::KrylovVecs<float2> kv;
-      e = kvec_alloc<float2>(c, &kv, 0);
+      e = kvec_alloc<float2>(c, &kv, o.solver == DDA_BICGSTAB2 ? 1 : 0);
       // each inner solve aims straight for tol, but never below the complex64 floor
       const double inner = o.inner_tol > 0 ? o.inner_tol : 5e-6;
       if (e.ok() && !o.warm_start) cudaMemsetAsync(P, 0, sizeof(double2) * el, c->stream);

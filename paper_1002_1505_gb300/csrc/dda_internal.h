@@ -67,6 +67,8 @@ struct Geom {
   FftPlan plx, ply, plz;
 };
 
+struct KState;
+
 // Device-resident data shared by matvec kernels of one precision.
 template <typename C>
 struct MvData {
@@ -78,6 +80,9 @@ struct MvData {
   const C* twy;
   const C* twz;
   C* work;              // FFT workspace [nrhs_chunk][3][px][nz][ys]
+  // solver state of the RHS of this launch (index = RHS within the launch), or null: the
+  // compile-time kernels skip the RHS whose solve has finished (their products are unused)
+  const KState* ks = nullptr;
 };
 
 // Launch tuning chosen per grid (autotuner fills it).
@@ -149,11 +154,12 @@ struct RedBuf {
   unsigned int* count = nullptr; // per-RHS arrival counters (zero between kernels)
   int nblk = 0;
 };
-constexpr int kRedSlots = 4;
+constexpr int kRedSlots = 8;
 
 // Per-RHS scalar state of the iterative solvers (device).
 struct KState {
   double2 rho, alpha, omega, beta;
+  double2 g1, g2; // BiCGstab(2): coefficients of the minimal-residual step
   double bb;      // |b|^2
   double rr;      // |r|^2 (recursive)
   double zz;      // CCG |A^H r|^2
@@ -169,6 +175,7 @@ template <typename C> Err k_accumulate_to_c128(double2* dst, const C* src, int64
 template <typename C>
 struct KrylovVecs {
   C *x, *r, *rhat, *p, *v, *s, *t, *b;
+  C* u2 = nullptr;  // BiCGstab(2) only
 };
 
 // BiCGstab / CCG building blocks, all per-RHS batched over nrhs vectors of length n3.
@@ -184,6 +191,21 @@ template <typename C> Err bicg_omega(const KrylovVecs<C>& kv, KState* ks, RedBuf
                                      cudaStream_t st);
 template <typename C> Err bicg_xr_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3,
                                          cudaStream_t st);
+// BiCGstab(2) (Sleijpen & Fokkema 1993): vectors r0 = r, r1 = s, r2 = t, u0 = p, u1 = v, u2 = u2,
+// shadow = rhat.  init; then per cycle: u_update(0), [u1 = A u0], alpha(1), r_update(0),
+// [r1 = A r0], beta(1), u_update(1), [u2 = A u1], alpha(2), r_update(1), [r2 = A r1], mr.
+template <typename C> Err b2_init(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, double tol,
+                                  bool have_ax, cudaStream_t st);
+template <typename C> Err b2_u_update(const KrylovVecs<C>& kv, const KState* ks, int j, int nrhs, int64_t n3,
+                                      cudaStream_t st);
+template <typename C> Err b2_alpha(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int j, int nrhs, int64_t n3,
+                                   cudaStream_t st);
+template <typename C> Err b2_r_update(const KrylovVecs<C>& kv, const KState* ks, int j, int nrhs, int64_t n3,
+                                      cudaStream_t st);
+template <typename C> Err b2_beta(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3,
+                                  cudaStream_t st);
+template <typename C> Err b2_mr(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3,
+                                cudaStream_t st);
 // CCG (CG on the normal equations)
 template <typename C> Err ccg_init(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3,
                                    double tol, bool have_ax, cudaStream_t st);

@@ -2,7 +2,9 @@
 //  - BiCGstab (van der Vorst 1992; the guide's PBCGST option), unpreconditioned,
 //    shadow residual = initial residual;
 //  - CCG: conjugate gradients on the normal equations A^H A P = A^H E
-//    (Petravic & Kuo-Petravic 1979; the guide's PETRKP option).
+//    (Petravic & Kuo-Petravic 1979; the guide's PETRKP option);
+//  - BiCGstab(2) (Sleijpen & Fokkema 1993), the method family of the guide's
+//    PBCGS2 option: two BiCG steps, then a degree-2 minimal-residual step.
 // Every right-hand side is an independent system solved in lock step: each
 // kernel covers all RHS, with per-RHS scalars kept on the device (KState), so
 // an iteration needs no host round trip and can be captured in a CUDA graph.
@@ -470,6 +472,197 @@ __global__ void k_ccg_p(KrylovVecs<C> kv, const KState* ks, int64_t n3) {
   }
 }
 
+// ------------------------------------------------------------------ BiCGstab(2) kernels
+// r0 = b - A x (or b), shadow = r0, u0 = 0; rho0 = <shadow, r0> (the first BiCG step's rho with beta = 0)
+template <typename C>
+__global__ void k_b2_init(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3, bool have_ax, double tol) {
+  const int b = blockIdx.y;
+  const int64_t o = (int64_t)b * n3;
+  double acc[2] = {0.0, 0.0};  // |b|^2, |r|^2
+  VEC_LOOP(n3) {
+    const double2 bv = to_d(kv.b[o + i]);
+    double2 rv = bv;
+    if (have_ax) {
+      const double2 ax = to_d(kv.r[o + i]);
+      rv = make_double2(bv.x - ax.x, bv.y - ax.y);
+    }
+    const C rc = from_d<C>(rv);
+    kv.r[o + i] = rc;
+    kv.rhat[o + i] = rc;
+    kv.p[o + i] = czero<C>();
+    if (!have_ax) kv.x[o + i] = czero<C>();
+    acc[0] = nrm_acc(acc[0], bv);
+    acc[1] = nrm_acc(acc[1], to_d(rc));
+  }
+  double t[2];
+  if (last_block_totals<2>(acc, rb, b, t) && threadIdx.x == 0) {
+    KState& k = ks[b];
+    k.bb = t[0];
+    k.rr = t[1];
+    k.rho = make_double2(t[1], 0.0);
+    k.alpha = make_double2(0.0, 0.0);
+    k.omega = make_double2(1.0, 0.0);
+    k.beta = make_double2(0.0, 0.0);
+    k.tol2 = tol * tol * t[0];
+    k.it = 0;
+    k.done = (t[0] == 0.0 || t[1] <= k.tol2) ? 1 : 0;
+  }
+}
+
+// BiCG step j: u_i = r_i - beta u_i for i <= j (u0 = p, u1 = v; r0 = r, r1 = s)
+template <typename C>
+__global__ void k_b2_u(KrylovVecs<C> kv, const KState* ks, int j, int64_t n3) {
+  const int b = blockIdx.y;
+  const KState k = ks[b];
+  if (k.done) return;
+  using R = typename RealOf<C>::t;
+  const C be = mk((R)k.beta.x, (R)k.beta.y);
+  const int64_t o = (int64_t)b * n3;
+  VEC_LOOP(n3) {
+    kv.p[o + i] = csub(kv.r[o + i], cmul(be, kv.p[o + i]));
+    if (j == 1) kv.v[o + i] = csub(kv.s[o + i], cmul(be, kv.v[o + i]));
+  }
+}
+
+// alpha = rho0 / <shadow, u_{j+1}> (u1 = v for j = 0, u2 for j = 1)
+template <typename C>
+__global__ void k_b2_alpha(KrylovVecs<C> kv, KState* ks, RedBuf rb, int j, int64_t n3) {
+  const int b = blockIdx.y;
+  double acc[2] = {0.0, 0.0};
+  if (!ks[b].done) {
+    const C* u = (j == 0) ? kv.v : kv.u2;
+    const int64_t o = (int64_t)b * n3;
+    Acc<C> re, im;
+    VEC_LOOP(n3) acc_cdot(re, im, kv.rhat[o + i], u[o + i]);
+    acc[0] = re.get();
+    acc[1] = im.get();
+  }
+  double t[2];
+  if (last_block_totals<2>(acc, rb, b, t) && threadIdx.x == 0) {
+    KState& k = ks[b];
+    if (k.done) return;
+    const double2 g = make_double2(t[0], t[1]);
+    if (g.x == 0.0 && g.y == 0.0) { k.done = 2; return; }
+    k.alpha = cdiv(k.rho, g);
+  }
+}
+
+// r_i -= alpha u_{i+1} for i <= j; x += alpha u0
+template <typename C>
+__global__ void k_b2_r(KrylovVecs<C> kv, const KState* ks, int j, int64_t n3) {
+  const int b = blockIdx.y;
+  const KState k = ks[b];
+  if (k.done) return;
+  using R = typename RealOf<C>::t;
+  const C al = mk((R)k.alpha.x, (R)k.alpha.y);
+  const int64_t o = (int64_t)b * n3;
+  VEC_LOOP(n3) {
+    kv.r[o + i] = csub(kv.r[o + i], cmul(al, kv.v[o + i]));
+    if (j == 1) kv.s[o + i] = csub(kv.s[o + i], cmul(al, kv.u2[o + i]));
+    kv.x[o + i] = cadd(kv.x[o + i], cmul(al, kv.p[o + i]));
+  }
+}
+
+// rho1 = <shadow, r1>; beta = alpha rho1 / rho0; rho0 = rho1
+template <typename C>
+__global__ void k_b2_beta(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
+  const int b = blockIdx.y;
+  double acc[2] = {0.0, 0.0};
+  if (!ks[b].done) {
+    const int64_t o = (int64_t)b * n3;
+    Acc<C> re, im;
+    VEC_LOOP(n3) acc_cdot(re, im, kv.rhat[o + i], kv.s[o + i]);
+    acc[0] = re.get();
+    acc[1] = im.get();
+  }
+  double t[2];
+  if (last_block_totals<2>(acc, rb, b, t) && threadIdx.x == 0) {
+    KState& k = ks[b];
+    if (k.done) return;
+    const double2 rho1 = make_double2(t[0], t[1]);
+    if (k.rho.x == 0.0 && k.rho.y == 0.0) { k.done = 2; return; }
+    k.beta = cmuld(k.alpha, cdiv(rho1, k.rho));
+    k.rho = rho1;
+  }
+}
+
+// Gram system of the minimal-residual step: |r1|^2, <r1, r2>, |r2|^2, <r1, r0>, <r2, r0>
+// (r0 = r, r1 = s, r2 = t); gamma solves [<r1,r1> <r1,r2>; <r2,r1> <r2,r2>] gamma = [<r1,r0>; <r2,r0>]
+template <typename C>
+__global__ void k_b2_gram(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
+  const int b = blockIdx.y;
+  double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  if (!ks[b].done) {
+    const int64_t o = (int64_t)b * n3;
+    Acc<C> a11, b12r, b12i, a22, c1r, c1i, c2r, c2i;
+    VEC_LOOP(n3) {
+      const C r0 = kv.r[o + i], r1 = kv.s[o + i], r2 = kv.t[o + i];
+      acc_nrm(a11, r1);
+      acc_cdot(b12r, b12i, r1, r2);
+      acc_nrm(a22, r2);
+      acc_cdot(c1r, c1i, r1, r0);
+      acc_cdot(c2r, c2i, r2, r0);
+    }
+    acc[0] = a11.get(); acc[1] = b12r.get(); acc[2] = b12i.get(); acc[3] = a22.get();
+    acc[4] = c1r.get(); acc[5] = c1i.get(); acc[6] = c2r.get(); acc[7] = c2i.get();
+  }
+  double t[8];
+  if (last_block_totals<8>(acc, rb, b, t) && threadIdx.x == 0) {
+    KState& k = ks[b];
+    if (k.done) return;
+    const double a = t[0], d = t[3];
+    const double2 bb = make_double2(t[1], t[2]);  // <r1, r2>
+    const double2 c1 = make_double2(t[4], t[5]), c2 = make_double2(t[6], t[7]);
+    const double det = a * d - (bb.x * bb.x + bb.y * bb.y);
+    if (!(det > 0.0)) { k.done = 2; return; }
+    // gamma1 = (d c1 - b c2) / det ; gamma2 = (a c2 - conj(b) c1) / det
+    const double2 bc2 = cmuld(bb, c2), cbc1 = cmuld(make_double2(bb.x, -bb.y), c1);
+    k.g1 = make_double2((d * c1.x - bc2.x) / det, (d * c1.y - bc2.y) / det);
+    k.g2 = make_double2((a * c2.x - cbc1.x) / det, (a * c2.y - cbc1.y) / det);
+  }
+}
+
+// x += g1 r0 + g2 r1 ; r0 -= g1 r1 + g2 r2 ; u0 -= g1 u1 + g2 u2 ; partial |r0|^2, <shadow, r0>,
+// then the next cycle's first BiCG coefficients: rho0 <- -omega rho0, beta = alpha <shadow, r0> / rho0
+template <typename C>
+__global__ void k_b2_mr(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
+  const int b = blockIdx.y;
+  const KState k = ks[b];
+  double acc[3] = {0.0, 0.0, 0.0};
+  if (!k.done) {
+    using R = typename RealOf<C>::t;
+    const C g1 = mk((R)k.g1.x, (R)k.g1.y), g2 = mk((R)k.g2.x, (R)k.g2.y);
+    const int64_t o = (int64_t)b * n3;
+    Acc<C> rr, re, im;
+    VEC_LOOP(n3) {
+      const C r0 = kv.r[o + i], r1 = kv.s[o + i], r2 = kv.t[o + i];
+      kv.x[o + i] = cadd(kv.x[o + i], cadd(cmul(g1, r0), cmul(g2, r1)));
+      const C rn = csub(r0, cadd(cmul(g1, r1), cmul(g2, r2)));
+      kv.r[o + i] = rn;
+      kv.p[o + i] = csub(kv.p[o + i], cadd(cmul(g1, kv.v[o + i]), cmul(g2, kv.u2[o + i])));
+      acc_nrm(rr, rn);
+      acc_cdot(re, im, kv.rhat[o + i], rn);
+    }
+    acc[0] = rr.get();
+    acc[1] = re.get();
+    acc[2] = im.get();
+  }
+  double t[3];
+  if (last_block_totals<3>(acc, rb, b, t) && threadIdx.x == 0) {
+    KState& k = ks[b];
+    if (k.done) return;
+    k.it += 2;
+    k.rr = t[0];
+    if (t[0] <= k.tol2) { k.done = 1; return; }
+    k.omega = k.g2;
+    const double2 rho0 = cmuld(make_double2(-k.omega.x, -k.omega.y), k.rho);
+    const double2 rho1 = make_double2(t[1], t[2]);
+    if ((rho0.x == 0.0 && rho0.y == 0.0) || (rho1.x == 0.0 && rho1.y == 0.0)) { k.done = 2; return; }
+    k.beta = cmuld(k.alpha, cdiv(rho1, rho0));
+    k.rho = rho1;
+  }
+}
+
 // ------------------------------------------------------------------ refinement helpers
 __global__ void k_residual128(const double2* e, const double2* ax, double2* r, double* out2, RedBuf rb, int64_t n3) {
   const int bb = blockIdx.y;
@@ -594,6 +787,48 @@ Err ccg_beta_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, in
   return Err::Ok();
 }
 
+template <typename C>
+Err b2_init(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, double tol, bool have_ax,
+            cudaStream_t st) {
+  k_b2_init<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3, have_ax, tol);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+template <typename C>
+Err b2_u_update(const KrylovVecs<C>& kv, const KState* ks, int j, int nrhs, int64_t n3, cudaStream_t st) {
+  const int nb = (int)std::min<int64_t>((n3 + kThreads * 4 - 1) / (kThreads * 4), 1024);
+  k_b2_u<C><<<dim3(nb, nrhs), kThreads, 0, st>>>(kv, ks, j, n3);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+template <typename C>
+Err b2_alpha(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int j, int nrhs, int64_t n3, cudaStream_t st) {
+  k_b2_alpha<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, j, n3);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+template <typename C>
+Err b2_r_update(const KrylovVecs<C>& kv, const KState* ks, int j, int nrhs, int64_t n3, cudaStream_t st) {
+  const int nb = (int)std::min<int64_t>((n3 + kThreads * 4 - 1) / (kThreads * 4), 1024);
+  k_b2_r<C><<<dim3(nb, nrhs), kThreads, 0, st>>>(kv, ks, j, n3);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+template <typename C>
+Err b2_beta(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
+  k_b2_beta<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+template <typename C>
+Err b2_mr(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
+  k_b2_gram<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  CHECK_LAUNCH();
+  k_b2_mr<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+
 Err residual_c128(const double2* b, const double2* ax, double2* r, double* out2, RedBuf rb, int nrhs, int64_t n3,
                   cudaStream_t st) {
   k_residual128<<<vgrid(rb, nrhs), kThreads, 0, st>>>(b, ax, r, out2, rb, n3);
@@ -629,7 +864,13 @@ Err add_to_c128(double2* dst, const C* src, const int* mask_done, int nrhs, int6
   template Err ccg_alpha_update<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, cudaStream_t);        \
   template Err ccg_beta_update<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, cudaStream_t);         \
   template Err convert_from_c128<C>(const double2*, C*, int64_t, cudaStream_t);                               \
-  template Err add_to_c128<C>(double2*, const C*, const int*, int, int64_t, cudaStream_t);
+  template Err add_to_c128<C>(double2*, const C*, const int*, int, int64_t, cudaStream_t);                    \
+  template Err b2_init<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, double, bool, cudaStream_t);   \
+  template Err b2_u_update<C>(const KrylovVecs<C>&, const KState*, int, int, int64_t, cudaStream_t);          \
+  template Err b2_alpha<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int, int64_t, cudaStream_t);           \
+  template Err b2_r_update<C>(const KrylovVecs<C>&, const KState*, int, int, int64_t, cudaStream_t);          \
+  template Err b2_beta<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, cudaStream_t);                 \
+  template Err b2_mr<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, cudaStream_t);
 INST(float2)
 INST(double2)
 

@@ -43,9 +43,10 @@ __global__ void __launch_bounds__(ClusterCfg<S>::NT, ClusterCfg<S>::MINB) k_yz_c
   C* twy = reinterpret_cast<C*>(smem_raw);
   C* twz = twy + PY;
   C* pl = twz + PZ;
+  const int b = blockIdx.y, kx = blockIdx.z;
+  if (rhs_done(d, b)) return;  // every CTA of the cluster has the same b: none waits at a cluster barrier
   cg::cluster_group cl = cg::this_cluster();
   const int h = (int)cl.block_rank();
-  const int b = blockIdx.y, kx = blockIdx.z;
   const int nz = g.nz, ny = g.ny;
   copy_tw(twy, d.twy, PY);
   copy_tw(twz, d.twz, PZ);

@@ -56,6 +56,12 @@ __device__ __forceinline__ void gmul3(const C* __restrict__ gh, C& v0, C& v1, C&
   v2 = u2;
 }
 
+// true when RHS b of this launch belongs to a finished solve (whole CTA exits before any barrier)
+template <typename C>
+__device__ __forceinline__ bool rhs_done(const MvData<C>& d, int b) {
+  return d.ks != nullptr && d.ks[b].done != 0;
+}
+
 template <typename C>
 __device__ __forceinline__ void copy_tw(C* dst, const C* src, int L) {
   for (int i = threadIdx.x; i < L; i += blockDim.x) dst[i] = src[i];
@@ -71,6 +77,7 @@ __global__ void __launch_bounds__(256) k_x_fwd(Geom g, MvData<C> d, const C* __r
   C* in = tw + PX;
   C* out = in + 3 * TY * ip;
   const int y0 = blockIdx.x * TY, z = blockIdx.y, b = blockIdx.z;
+  if (rhs_done(d, b)) return;
   copy_tw(tw, d.twx, PX);
   const int nld = 3 * TY * g.nx;
   for (int i = threadIdx.x; i < nld; i += blockDim.x) {
@@ -135,6 +142,7 @@ __global__ void __launch_bounds__(256) k_x_inv(Geom g, MvData<C> d, const C* __r
   C* in = tw + PX;
   C* out = in + 3 * TY * ip;
   const int y0 = blockIdx.x * TY, z = blockIdx.y, b = blockIdx.z;
+  if (rhs_done(d, b)) return;
   copy_tw(tw, d.twx, PX);
   __syncthreads();
   const int64_t plane = (int64_t)g.nz * g.ys;
@@ -206,6 +214,7 @@ __global__ void __launch_bounds__(NT) k_yz_plane(Geom g, MvData<C> d) {
   C* twz = twy + PY;
   C* pl = twz + PZ;
   const int b = blockIdx.x, kx = blockIdx.y;
+  if (rhs_done(d, b)) return;
   const int nz = g.nz, ny = g.ny;
   copy_tw(twy, d.twy, PY);
   copy_tw(twz, d.twz, PZ);
@@ -437,6 +446,7 @@ __global__ void __launch_bounds__(256) k_z_cols(Geom g, MvData<C> d) {
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* s = tw + PZ;
   const int ky0 = blockIdx.y * G, kx = blockIdx.z, b = blockIdx.x;
+  if (rhs_done(d, b)) return;
   const int nz = g.nz, py = g.py;
   copy_tw(tw, d.twz, PZ);
   __syncthreads();

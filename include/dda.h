@@ -248,14 +248,15 @@ DDA_API dda_status dda_profile_matvec(dda_ctx *ctx, int nrhs, int dtype, int ite
  * the fastest) or pinned by the DDA_SCHEDULE environment variable at
  * dda_build_green_fft time ("generic", "fast5", "plane512", "plane768",
  * "cluster2", "cluster4"; DDA_XTILE = 4, 8 or 16 pins the x passes' tile
- * height).
+ * height; DDA_BULK = 1 or 0 pins bulk-copy staging of the plane pass).
  * info[0] = passes (3 = fused y-z plane, 5 = split), info[1] = 1 when the
  * compile-time-length kernels are used, info[2] = threads per CTA of the plane
  * kernel (0 if none), info[3] = RHS count the choice was tuned for (0 = not
  * tuned), info[4] = CTAs per plane (1, or the thread-block cluster size when
  * the plane pass is split over a cluster), info[5] = y rows per CTA of the x
- * passes (0 for the generic engine). */
-DDA_API dda_status dda_schedule_info(dda_ctx *ctx, int dtype, int32_t info[6]);
+ * passes (0 for the generic engine), info[6] = 1 when the plane pass stages its
+ * HBM blocks with bulk copies (TMA). */
+DDA_API dda_status dda_schedule_info(dda_ctx *ctx, int dtype, int32_t info[7]);
 
 /* ---------------------------------------------------------------------------
  * Learned warm start (the guide has no counterpart: the solver accepts any
@@ -321,6 +322,14 @@ DDA_API dda_status dda_unet_warm_start(dda_ctx *ctx, const float *y_dev, const i
  * the solver's convergence depends on.  Synchronizes. */
 DDA_API dda_status dda_unet_residual_grad(dda_ctx *ctx, const float *y_dev, const int32_t dims[3],
                                           const int32_t offset[3], double weight, float *gy_dev, double *loss_out);
+
+/* Diagnostic (no counterpart in the guide): the product kernels stage their
+ * shared-memory blocks with bulk asynchronous copies whose completion waits are
+ * bounded; a kernel that gives up records a flag, and the next synchronizing
+ * call (dda_solve, dda_profile_matvec) returns DDA_ECUDA.  This call runs that
+ * bounded wait on a barrier that never completes, on `device`, and sets
+ * *gave_up = 1 when the wait ended by itself (the device stays usable). */
+DDA_API dda_status dda_selftest_bulk_wait(int device, int32_t *gave_up);
 
 /* Library build string (static storage). */
 DDA_API const char *dda_version(void);

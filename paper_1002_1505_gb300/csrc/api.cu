@@ -71,6 +71,7 @@ struct dda_ctx {
 
   // workspaces (grown on demand)
   float2* d_w64 = nullptr;
+  unsigned int* d_fault = nullptr;  // set by product kernels whose bounded bulk-copy wait gave up
   int w64_cap = 0;
   double2* d_w128 = nullptr;
   int w128_cap = 0;
@@ -292,8 +293,27 @@ dda::RedBuf redbuf(dda_ctx* c, int nrhs, int64_t n3) {
 template <typename C>
 Err ensure_work(dda_ctx* c, int want, int* cap_out);
 
+Err ensure_fault_flag(dda_ctx* c) {
+  if (c->d_fault) return Err::Ok();
+  DDA_TRY(grow(c, &c->d_fault, sizeof(unsigned int) * 4));
+  DDA_CU(cudaMemset(c->d_fault, 0, sizeof(unsigned int) * 4));
+  return Err::Ok();
+}
+
+// A product kernel that gave up waiting for a bulk copy leaves the flag set: report it (once).
+Err check_fault(dda_ctx* c) {
+  if (!c->d_fault) return Err::Ok();
+  unsigned int h = 0;
+  DDA_CU(cudaMemcpyAsync(&h, c->d_fault, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  DDA_CU(cudaStreamSynchronize(c->stream));
+  if (h == 0) return Err::Ok();
+  DDA_CU(cudaMemsetAsync(c->d_fault, 0, sizeof(unsigned int), c->stream));
+  return Err::make(DDA_ECUDA, "a product kernel gave up waiting for a bulk copy; the results since the last check are invalid");
+}
+
 template <>
 Err ensure_work<float2>(dda_ctx* c, int want, int* cap_out) {
+  DDA_TRY(ensure_fault_flag(c));
   const dda::Geom& g = c->g64;
   const size_t per = sizeof(float2) * 3ull * g.px * g.nz * g.ys;
   const size_t budget = 24ull << 30;
@@ -305,6 +325,7 @@ Err ensure_work<float2>(dda_ctx* c, int want, int* cap_out) {
 }
 template <>
 Err ensure_work<double2>(dda_ctx* c, int want, int* cap_out) {
+  DDA_TRY(ensure_fault_flag(c));
   const dda::Geom& g = c->g128;
   const size_t per = sizeof(double2) * 3ull * g.px * g.nz * g.ys;
   const size_t budget = 24ull << 30;
@@ -320,14 +341,18 @@ template <> struct Sel<float2> {
   static dda::Geom geom(dda_ctx* c) { dda::Geom g = c->g64; g.ncomp = c->ncomp; return g; }
   static const dda::MvTune& tune(dda_ctx* c) { return c->t64; }
   static dda::MvData<float2> data(dda_ctx* c) {
-    return dda::MvData<float2>{c->d_map, c->comp_valid ? c->d_comp : nullptr, c->d_ghat64, c->d_ia64, c->d_tw64[0], c->d_tw64[1], c->d_tw64[2], c->d_w64};
+    dda::MvData<float2> d{c->d_map, c->comp_valid ? c->d_comp : nullptr, c->d_ghat64, c->d_ia64, c->d_tw64[0], c->d_tw64[1], c->d_tw64[2], c->d_w64};
+    d.fault = c->d_fault;
+    return d;
   }
 };
 template <> struct Sel<double2> {
   static dda::Geom geom(dda_ctx* c) { dda::Geom g = c->g128; g.ncomp = c->ncomp; return g; }
   static const dda::MvTune& tune(dda_ctx* c) { return c->t128; }
   static dda::MvData<double2> data(dda_ctx* c) {
-    return dda::MvData<double2>{c->d_map, c->comp_valid ? c->d_comp : nullptr, c->d_ghat128, c->d_ia128, c->d_tw128[0], c->d_tw128[1], c->d_tw128[2], c->d_w128};
+    dda::MvData<double2> d{c->d_map, c->comp_valid ? c->d_comp : nullptr, c->d_ghat128, c->d_ia128, c->d_tw128[0], c->d_tw128[1], c->d_tw128[2], c->d_w128};
+    d.fault = c->d_fault;
+    return d;
   }
 };
 
@@ -448,6 +473,15 @@ Err ensure_tuned(dda_ctx* c, int nrhs) {
         time_one(t);
         if (!err.ok()) break;
       }
+    }
+    // and bulk-copy staging of the plane pass's HBM blocks
+    int smax_b = 0;
+    cudaDeviceGetAttribute(&smax_b, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    if (err.ok() && sizeof(C) == sizeof(float2) && best.plane && best.clus == 0 &&
+        dda::plane_bulk_ok_c64(g0, smax_b)) {
+      dda::MvTune t = best;
+      t.bulk = true;
+      time_one(t);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -893,6 +927,11 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
         c->forced_schedule = true;
       }
     }
+    // DDA_BULK=1 / 0 pins bulk-copy staging of the plane pass on / off
+    if (const char* f = std::getenv("DDA_BULK")) {
+      t64.bulk = (std::atoi(f) != 0) && t64.plane_ok && dda::plane_bulk_ok_c64(g64, smax);
+      c->forced_schedule = true;
+    }
     // DDA_XTILE pins the x passes' tile height (y rows per CTA: 4, 8 or 16 where instantiated)
     if (const char* f = std::getenv("DDA_XTILE")) {
       const int ty = std::atoi(f);
@@ -1189,6 +1228,10 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
       if (!e.ok()) { cleanup(); return fail(c, e); }
     }
     cleanup();
+    {
+      const Err fe = check_fault(c);
+      if (!fe.ok()) return fail(c, fe);
+    }
     bool all = true;
     for (int b = 0; b < nrhs; ++b) {
       const bool conv = rel[b] <= o.tol;
@@ -1409,13 +1452,24 @@ dda_status dda_profile_matvec(dda_ctx* c, int nrhs, int dtype, int iters, double
     if (ev[i]) cudaEventDestroy(ev[i]);
   dfree(p);
   dfree(ap);
+  if (e.ok()) e = check_fault(c);
   if (!e.ok()) return fail(c, e);
   for (int i = 0; i < np; ++i) ms_per_pass[i] = acc[i] / iters;
   *npass = np;
   return DDA_OK;
 }
 
-dda_status dda_schedule_info(dda_ctx* c, int dtype, int32_t info[6]) {
+dda_status dda_selftest_bulk_wait(int device, int32_t* gave_up) {
+  if (!gave_up) return DDA_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return DDA_ECUDA;
+  int v = -1;
+  const Err e = dda::selftest_bulk_wait(&v);
+  if (!e.ok()) return e.code;
+  *gave_up = v;
+  return DDA_OK;
+}
+
+dda_status dda_schedule_info(dda_ctx* c, int dtype, int32_t info[7]) {
   if (!c || !info) return DDA_EINVAL;
   if (!c->have_green) return fail(c, Err::make(DDA_ESTATE, "build the Green tensor first"));
   if (dtype != DDA_C64 && dtype != DDA_C128) return fail(c, Err::make(DDA_EINVAL, "bad dtype"));
@@ -1425,6 +1479,7 @@ dda_status dda_schedule_info(dda_ctx* c, int dtype, int32_t info[6]) {
   info[2] = t.plane ? (t.clus == 2 ? 384 : t.clus == 4 ? 256 : t.thr_p) : 0;
   info[3] = c->tuned_nrhs[dtype == DDA_C64 ? 0 : 1];
   info[4] = t.plane && t.clus > 1 ? t.clus : 1;
+  info[6] = t.plane && t.bulk ? 1 : 0;
   {
     const dda::Geom& g = dtype == DDA_C64 ? c->g64 : c->g128;
     const size_t cs = dtype == DDA_C64 ? sizeof(float2) : sizeof(double2);

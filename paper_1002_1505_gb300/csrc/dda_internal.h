@@ -83,6 +83,7 @@ struct MvData {
   // solver state of the RHS of this launch (index = RHS within the launch), or null: the
   // compile-time kernels skip the RHS whose solve has finished (their products are unused)
   const KState* ks = nullptr;
+  unsigned int* fault = nullptr;  // set by a kernel whose bounded wait on a bulk copy gave up
 };
 
 // Launch tuning chosen per grid (autotuner fills it).
@@ -96,6 +97,7 @@ struct MvTune {
   bool plane_ok = false;  // the fast 3-pass plane kernel exists and fits for this grid
   int clus = 0;           // plane pass split over a cluster of this many CTAs (0: one CTA per plane)
   int xty = 0;            // y rows per CTA of the compile-time x passes (0: the length's default)
+  bool bulk = false;      // plane pass stages its HBM blocks with bulk copies
 };
 
 // Enqueue ap = A p for nrhs right-hand sides (rhs0 = index of the first one for alpha).
@@ -108,10 +110,26 @@ size_t plane_smem_bytes(const Geom& g, const MvTune& t);
 template <typename C>
 Err launch_matvec_fast(const Geom& g, const MvData<C>& d, const MvTune& t, const C* p, C* ap, int nrhs, int rhs0,
                        bool conj, cudaStream_t st);
+// Opt a kernel into the largest dynamic shared memory the device allows beside the kernel's
+// own static shared memory (the attribute is refused when the sum would exceed the limit).
+template <typename K>
+inline void optin_smem(K kern, int smax) {
+  cudaFuncAttributes a{};
+  int stat = 0;
+  if (cudaFuncGetAttributes(&a, kern) == cudaSuccess) stat = (int)a.sharedSizeBytes;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smax - stat);
+}
 void fast_optin_c64(int smax);
+// Runs the bounded mbarrier wait of the bulk-copy path on a barrier that never completes (a few
+// thousand polls) and reports whether it gave up (1) instead of hanging.
+Err selftest_bulk_wait(int* gave_up);
 // complex64 plane pass split over a thread-block cluster of S CTAs (matvec_cluster.cu)
 Err launch_plane_cluster_c64(const Geom& g, const MvData<float2>& d, int S, int nrhs, cudaStream_t st);
 int plane_cluster_capacity_c64(const Geom& g, int S, int smax);  // co-resident clusters, 0 = not possible
+// complex64 plane pass with its HBM blocks staged by bulk copies (matvec_plane_bulk.cu)
+Err launch_plane_bulk_c64(const Geom& g, const MvData<float2>& d, int nrhs, cudaStream_t st);
+bool plane_bulk_ok_c64(const Geom& g, int smax);
+void plane_bulk_optin_c64(int smax);
 void cluster_optin_c64(int smax);
 void fast_optin_c128(int smax);
 // Does a fast schedule exist for this grid (all lengths instantiated, tiles fit)?  Sets t.fast and t.plane.

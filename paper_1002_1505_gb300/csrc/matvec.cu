@@ -420,7 +420,7 @@ Err set_smem(size_t bytes) {
 
 template <typename K>
 void optin(K kern) {
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, g_smem_optin);
+  optin_smem(kern, g_smem_optin);
 }
 
 }  // namespace
@@ -568,6 +568,7 @@ void init_kernel_attrs() {
   optin(k_fft_strided<float2>); optin(k_fft_strided<double2>);
   fast_optin_c64(v);
   cluster_optin_c64(v);
+  plane_bulk_optin_c64(v);
   fast_optin_c128(v);
 }
 

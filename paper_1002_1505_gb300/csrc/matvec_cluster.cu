@@ -271,9 +271,9 @@ namespace fast {
 template <int A, int B>
 void optin_pair(int smax) {
   if constexpr (cluster_ok<A, B>(2))
-    cudaFuncSetAttribute(k_yz_cluster<float2, A, B, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    optin_smem(k_yz_cluster<float2, A, B, 2>, smax);
   if constexpr (cluster_ok<A, B>(4))
-    cudaFuncSetAttribute(k_yz_cluster<float2, A, B, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    optin_smem(k_yz_cluster<float2, A, B, 4>, smax);
 }
 }  // namespace fast
 

@@ -8,6 +8,7 @@
 // Workspace:   W[b][c][kx][z][ys], ys = ny (3-pass) or py (5-pass).
 #pragma once
 
+#include "bulk.cuh"
 #include "dda_internal.h"
 #include "fft2.cuh"
 
@@ -204,7 +205,18 @@ __global__ void __launch_bounds__(256) k_x_inv(Geom g, MvData<C> d, const C* __r
 
 // ------------------------------------------------------------------ fused y-z plane (3-pass schedule)
 // grid (nrhs, px), block NT.  smem: twy[PY] | twz[PZ] | pl[PZ*3][PY+1] (row (z,c) = z*3 + c)
-template <typename C, int PY, int PZ, int NT>
+// With BULK, the plane's input and output (three contiguous nz x ny blocks of the
+// workspace) move between HBM and shared memory as bulk copies (TMA) when nz*ny is even
+// (16-byte granularity), staged in the plane rows z >= nz, which are unused before the
+// forward z transform and after the inverse one; otherwise every thread loads and stores
+// its own elements.
+// shared-memory bytes of the plane pass; the bulk-staged variant keeps its mbarrier after the plane
+template <typename C>
+__host__ __device__ constexpr size_t plane_bytes(int py, int pz) {
+  return sizeof(C) * ((size_t)py + pz + (size_t)pz * 3 * (py + 1));
+}
+
+template <typename C, int PY, int PZ, int NT, bool BULK>
 __global__ void __launch_bounds__(NT) k_yz_plane(Geom g, MvData<C> d) {
   constexpr int RAy = Shape<PY>::RA, LBy = Shape<PY>::LB, Hy = Shape<PY>::H;
   constexpr int RAz = Shape<PZ>::RA, LBz = Shape<PZ>::LB, Hz = Shape<PZ>::H;
@@ -213,20 +225,31 @@ __global__ void __launch_bounds__(NT) k_yz_plane(Geom g, MvData<C> d) {
   C* twy = reinterpret_cast<C*>(smem_raw);
   C* twz = twy + PY;
   C* pl = twz + PZ;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + ((plane_bytes<C>(PY, PZ) + 15) & ~(size_t)15));
   const int b = blockIdx.x, kx = blockIdx.y;
   if (rhs_done(d, b)) return;
   const int nz = g.nz, ny = g.ny;
-  copy_tw(twy, d.twy, PY);
-  copy_tw(twz, d.twz, PZ);
-  __syncthreads();
   C* wb = d.work + ((int64_t)b * 3 * g.px + kx) * ((int64_t)nz * g.ys);
   const int64_t cstride = (int64_t)g.px * nz * g.ys;
-  // y forward, pass A: global -> registers -> plane
+  // staging block [c][z][y] in rows z >= nz, 16-byte aligned
+  const bool staged = BULK && ((nz * ny) % 2 == 0) && g.ys == ny;
+  C* stage = pl + 3 * nz * RP + ((3 * nz * RP) & 1);
+  const uint32_t cbytes = (uint32_t)(sizeof(C) * nz * ny);
+  if (staged && threadIdx.x == 0) {
+    bulk::mbar_init(bar, 1);
+    bulk::mbar_arrive_expect_tx(bar, 3 * cbytes);
+    for (int c = 0; c < 3; ++c) bulk::load_g2s(stage + c * nz * ny, wb + c * cstride, cbytes, bar);
+  }
+  copy_tw(twy, d.twy, PY);
+  copy_tw(twz, d.twz, PZ);
+  __syncthreads();  // barrier initialised before anyone polls it
+  if (staged) bulk::mbar_wait(bar, 0, bulk::kMaxPolls, d.fault);
+  // y forward, pass A: staged block (or global) -> registers -> plane
   for (int i = threadIdx.x; i < 3 * nz * LBy; i += blockDim.x) {
     const int n1 = i % LBy;
     const int r = i / LBy;
     const int z = r % nz, c = r / nz;
-    const C* src = wb + c * cstride + (int64_t)z * g.ys;
+    const C* src = staged ? stage + (c * nz + z) * ny : wb + c * cstride + (int64_t)z * g.ys;
     C x[RAy], o[2 * RAy];
 #pragma unroll
     for (int j = 0; j < RAy; ++j) {
@@ -330,7 +353,7 @@ __global__ void __launch_bounds__(NT) k_yz_plane(Geom g, MvData<C> d) {
     for (int e = 0; e < LBy; ++e) row[e] = v[e];
   }
   __syncthreads();
-  // y inverse, pass A: plane -> registers -> global (y < ny)
+  // y inverse, pass A: plane -> registers -> staged block (or global), y < ny
   for (int i = threadIdx.x; i < 3 * nz * LBy; i += blockDim.x) {
     const int n1 = i % LBy;
     const int r = i / LBy;
@@ -342,11 +365,20 @@ __global__ void __launch_bounds__(NT) k_yz_plane(Geom g, MvData<C> d) {
 #pragma unroll
       for (int k = 0; k < RAy; ++k) v[bb * RAy + k] = row[bb * Hy + n1 + LBy * k];
     f2::passA_inv<PY, false>(v, n1, twy, lo, (C*)nullptr);
-    C* dst = wb + c * cstride + (int64_t)z * g.ys;
+    C* dst = staged ? stage + (c * nz + z) * ny : wb + c * cstride + (int64_t)z * g.ys;
 #pragma unroll
     for (int j = 0; j < RAy; ++j) {
       const int yy = n1 + LBy * j;
       if (yy < ny) dst[yy] = lo[j];
+    }
+  }
+  if (staged) {
+    bulk::fence_smem_to_async();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int c = 0; c < 3; ++c) bulk::store_s2g(wb + c * cstride, stage + c * nz * ny, cbytes);
+      bulk::store_commit();
+      bulk::store_wait_read();  // shared memory stays allocated until the copies have read it
     }
   }
 }
@@ -612,7 +644,12 @@ size_t x_fast_smem(const Geom& g, int TY = 0) {
 }
 template <typename C>
 size_t plane_fast_smem(const Geom& g) {
-  return sizeof(C) * ((size_t)g.py + g.pz + (size_t)g.pz * 3 * (g.py + 1));
+  return plane_bytes<C>(g.py, g.pz);
+}
+// the bulk-staged variant: the plane, then its 8-byte mbarrier at the next 16-byte boundary
+template <typename C>
+size_t plane_bulk_smem(const Geom& g) {
+  return ((plane_bytes<C>(g.py, g.pz) + 15) & ~(size_t)15) + 16;
 }
 constexpr int kRowsPerCta = 8;
 template <typename C>
@@ -692,8 +729,8 @@ Err launch_plane(const Geom& g, const MvData<C>& d, int nrhs, int nt, cudaStream
     const dim3 grid(nrhs, g.px);
 #define DDA_CASE(A, B)                                               \
     if (g.py == A && g.pz == B) {                                    \
-      if (nt == 768) k_yz_plane<C, A, B, 768><<<grid, 768, sm, st>>>(g, d); \
-      else k_yz_plane<C, A, B, 512><<<grid, 512, sm, st>>>(g, d);    \
+      if (nt == 768) k_yz_plane<C, A, B, 768, false><<<grid, 768, sm, st>>>(g, d); \
+      else k_yz_plane<C, A, B, 512, false><<<grid, 512, sm, st>>>(g, d);    \
       DDA_CU(cudaGetLastError());                                    \
       return Err::Ok();                                              \
     }
@@ -742,15 +779,15 @@ Err launch_z_cols(const Geom& g, const MvData<C>& d, int nrhs, cudaStream_t st) 
 template <typename C, int L_>
 void optin_x(int smax) {
   constexpr int D = x_ty<C, L_>();
-  cudaFuncSetAttribute(k_x_fwd<C, L_, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-  cudaFuncSetAttribute(k_x_inv<C, L_, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  optin_smem(k_x_fwd<C, L_, D>, smax);
+  optin_smem(k_x_inv<C, L_, D>, smax);
   if constexpr (D != 4) {
-    cudaFuncSetAttribute(k_x_fwd<C, L_, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-    cudaFuncSetAttribute(k_x_inv<C, L_, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    optin_smem(k_x_fwd<C, L_, 4>, smax);
+    optin_smem(k_x_inv<C, L_, 4>, smax);
   }
   if constexpr (D > 8) {
-    cudaFuncSetAttribute(k_x_fwd<C, L_, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-    cudaFuncSetAttribute(k_x_inv<C, L_, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    optin_smem(k_x_fwd<C, L_, 8>, smax);
+    optin_smem(k_x_inv<C, L_, 8>, smax);
   }
 }
 
@@ -759,15 +796,15 @@ template <typename C>
 void optin_all(int smax) {
 #define DDA_CASE(L_)                                                                                                 \
   optin_x<C, L_>(smax);                                                                                              \
-  cudaFuncSetAttribute(k_y_rows<C, L_, kRowsPerCta, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);   \
-  cudaFuncSetAttribute(k_y_rows<C, L_, kRowsPerCta, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);    \
-  cudaFuncSetAttribute(k_z_cols<C, L_, zcols_g_rt(sizeof(C), L_)>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  optin_smem(k_y_rows<C, L_, kRowsPerCta, false>, smax);   \
+  optin_smem(k_y_rows<C, L_, kRowsPerCta, true>, smax);    \
+  optin_smem(k_z_cols<C, L_, zcols_g_rt(sizeof(C), L_)>, smax);
   DDA_FAST_LENGTHS(DDA_CASE)
 #undef DDA_CASE
   if constexpr (sizeof(C) == 8) {
 #define DDA_CASE(A, B)                                                                                    \
-  cudaFuncSetAttribute(k_yz_plane<C, A, B, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);     \
-  cudaFuncSetAttribute(k_yz_plane<C, A, B, 768>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  optin_smem(k_yz_plane<C, A, B, 512, false>, smax);     \
+  optin_smem(k_yz_plane<C, A, B, 768, false>, smax);
     DDA_FAST_PLANES(DDA_CASE)
 #undef DDA_CASE
   }
@@ -785,6 +822,8 @@ Err launch_matvec_fast(const Geom& g, const MvData<C>& d, const MvTune& t, const
     if constexpr (sizeof(C) == 8) {
       if (t.clus > 1) {
         DDA_TRY(launch_plane_cluster_c64(g, d, t.clus, nrhs, st));
+      } else if (t.bulk) {
+        DDA_TRY(launch_plane_bulk_c64(g, d, nrhs, st));
       } else {
         DDA_TRY(launch_plane<C>(g, d, nrhs, t.thr_p, st));
       }

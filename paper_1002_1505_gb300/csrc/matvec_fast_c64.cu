@@ -9,6 +9,32 @@ Err launch_matvec_fast<float2>(const Geom& g, const MvData<float2>& d, const MvT
 }
 void fast_optin_c64(int smax) { fast::optin_all<float2>(smax); }
 
+namespace {
+// one CTA: a barrier expecting one arrival and 16 bytes that nobody sends
+__global__ void k_selftest_bulk_wait(unsigned int* flag) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) bulk::mbar_init(&bar, 1);
+  __syncthreads();
+  bulk::mbar_wait(&bar, 0, 4096, flag);
+}
+}  // namespace
+
+Err selftest_bulk_wait(int* gave_up) {
+  unsigned int* d = nullptr;
+  DDA_CU(cudaMalloc(&d, sizeof(unsigned int)));
+  cudaError_t ce = cudaMemset(d, 0, sizeof(unsigned int));
+  if (ce == cudaSuccess) {
+    k_selftest_bulk_wait<<<1, 32>>>(d);
+    ce = cudaGetLastError();
+  }
+  unsigned int h = 0;
+  if (ce == cudaSuccess) ce = cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (ce != cudaSuccess) return Err::make(DDA_ECUDA, cudaGetErrorString(ce));
+  *gave_up = h ? 1 : 0;
+  return Err::Ok();
+}
+
 int x_tile_height_default(size_t csize, int px) { return fast::x_ty_rt(csize, px); }
 bool x_tile_height_ok(size_t csize, int px, int ty) { return fast::x_ty_valid(csize, px, ty); }
 

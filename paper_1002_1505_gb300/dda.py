@@ -72,6 +72,7 @@ def _load():
         "dda_cross_sections": (I, [P, P, P, P, I, P]),
         "dda_version": (ctypes.c_char_p, []),
         "dda_kernel_launches": (ctypes.c_ulonglong, []),
+        "dda_selftest_bulk_wait": (I, [I, P]),
         "dda_profile_matvec": (I, [P, I, I, I, P, P]),
         "dda_matvec_noalloc": (I, [P, P, P, I, I]),
         "dda_schedule_info": (I, [P, I, P]),
@@ -370,6 +371,15 @@ def dda_unet_residual_grad(ctx: "Context", y, gy, dims, weight=1.0, offset=None)
     return float(loss.value)
 
 
+def dda_selftest_bulk_wait(device: int = 0) -> bool:
+    """True when the library's bounded bulk-copy wait gives up by itself on a barrier that never completes."""
+    out = np.zeros(1, dtype=np.int32)
+    st = LIB.dda_selftest_bulk_wait(int(device), _ptr(out))
+    if st != DDA_OK:
+        raise DDAError(st, "dda_selftest_bulk_wait failed")
+    return bool(out[0])
+
+
 def dda_kernel_launches() -> int:
     return int(LIB.dda_kernel_launches())
 
@@ -383,8 +393,8 @@ def dda_profile_matvec(ctx: "Context", nrhs: int, dtype: int = DDA_C64, iters: i
 
 
 def dda_schedule_info(ctx: "Context", dtype: int = DDA_C64):
-    """(passes, fast, plane_threads, tuned_nrhs, ctas_per_plane, x_tile_rows) of the product's current schedule."""
-    info = np.zeros(6, dtype=np.int32)
+    """(passes, fast, plane_threads, tuned_nrhs, ctas_per_plane, x_tile_rows, bulk_staged) of the product's schedule."""
+    info = np.zeros(7, dtype=np.int32)
     ctx._check(LIB.dda_schedule_info(ctx._h, int(dtype), _ptr(info)))
     return tuple(int(v) for v in info)
 

@@ -83,6 +83,9 @@ FAST_PADS = [
      (64, 40, 40)),
     (W.Workload("ell_p4", "ELLIPSOID", (11, 13, 6), 1.4 + 0.2j, 2.0, "GKDLDR", W.uniform_orientations(2, 44)),
      (24, 32, 16)),
+    # plane pair (32, 32) with an odd ny*nz = 15*15: the plane pass without bulk-copy staging
+    (W.Workload("ell_p5", "ELLIPSOID", (10, 15, 15), 1.5 + 0.05j, 2.0, "LATTDR", W.uniform_orientations(1, 45)),
+     (24, 32, 32)),
 ]
 
 
@@ -125,6 +128,24 @@ def test_cluster_plane_matches_direct_sum(D, monkeypatch, w, pad, sched):
         assert err <= 1e-5, (w.name, sched, b, err)
 
 
+@pytest.mark.parametrize("w,pad", FAST_PADS, ids=[w.name for w, _ in FAST_PADS])
+def test_bulk_staged_plane_matches_direct_sum(D, monkeypatch, w, pad):
+    """The plane pass with its HBM blocks staged by bulk copies (where the grid allows it)."""
+    monkeypatch.setenv("DDA_BULK", "1")
+    ctx = _ctx(D, w, pad)
+    prob = _oracle_problem(w)
+    p = _rand_p(ctx.nrhs, ctx.n, 23, torch.complex64)
+    ap = torch.empty_like(p)
+    ctx.dda_matvec(p, ap)
+    torch.cuda.synchronize()
+    pn = p.cpu().numpy().astype(np.complex128)
+    got = ap.cpu().numpy().astype(np.complex128)
+    for b in range(ctx.nrhs):
+        ref = odda.apply_a(prob, b, pn[b], "direct")
+        err = np.linalg.norm(got[b] - ref) / np.linalg.norm(ref)
+        assert err <= 1e-5, (w.name, b, err)
+
+
 @pytest.mark.parametrize("xtile", ["4", "8"])
 @pytest.mark.parametrize("w,pad", FAST_PADS, ids=[w.name for w, _ in FAST_PADS])
 def test_x_tile_heights_match_direct_sum(D, monkeypatch, w, pad, xtile):
@@ -148,6 +169,19 @@ def test_x_tile_heights_match_direct_sum(D, monkeypatch, w, pad, xtile):
             assert err <= tol, (w.name, xtile, dt, b, err)
 
 
+def test_bounded_bulk_wait_gives_up_and_device_stays_usable(D):
+    """The bounded wait of the bulk-copy path ends by itself on a barrier that never completes
+    (no fault, no hang), and the device keeps working afterwards."""
+    assert D.dda_selftest_bulk_wait(0) is True
+    w = FAST_PADS[0][0]
+    ctx = _ctx(D, w, FAST_PADS[0][1])
+    p = _rand_p(ctx.nrhs, ctx.n, 3, torch.complex64)
+    ap = torch.empty_like(p)
+    ctx.dda_matvec(p, ap)
+    torch.cuda.synchronize()
+    assert torch.isfinite(torch.view_as_real(ap)).all()
+
+
 def test_fast_and_generic_engines_agree(D, monkeypatch):
     w = W.ELLIPSOID64
     out = {}
@@ -164,10 +198,12 @@ def test_fast_and_generic_engines_agree(D, monkeypatch):
     assert err <= 2e-6, err
 
 
-@pytest.mark.parametrize("sched", ["generic", "fast5", "plane512", "plane768", "cluster2", "cluster4", None])
+@pytest.mark.parametrize("sched", ["generic", "fast5", "plane512", "plane768", "cluster2", "cluster4", "bulk", None])
 def test_every_schedule_matches_direct_rows(D, monkeypatch, sched):
     """Each launch schedule the autotuner can pick, pinned through DDA_SCHEDULE, on the 64x48x32 grid."""
-    if sched:
+    if sched == "bulk":
+        monkeypatch.setenv("DDA_BULK", "1")
+    elif sched:
         monkeypatch.setenv("DDA_SCHEDULE", sched)
     w = W.ELLIPSOID64
     ctx = _ctx(D, w)
@@ -185,6 +221,8 @@ def test_every_schedule_matches_direct_rows(D, monkeypatch, sched):
             assert info[0] == 3 and info[2] == int(sched[-3:])
         if sched in ("cluster2", "cluster4") and dt == torch.complex64:
             assert info[0] == 3 and info[4] == int(sched[-1])
+        if sched == "bulk" and dt == torch.complex64:
+            assert info[0] == 3 and info[6] == 1
         for b in range(ctx.nrhs):
             pb = p[b].cpu().numpy().astype(np.complex128)
             ref = oint.matvec_direct(prob.target.r, prob.kd, prob.rhs[b].inv_alpha, pb, rows=rows)

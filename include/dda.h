@@ -323,6 +323,22 @@ DDA_API dda_status dda_unet_warm_start(dda_ctx *ctx, const float *y_dev, const i
 DDA_API dda_status dda_unet_residual_grad(dda_ctx *ctx, const float *y_dev, const int32_t dims[3],
                                           const int32_t offset[3], double weight, float *gy_dev, double *loss_out);
 
+/* Angular averages over scattering directions (guide, "Averaging over
+ * Scattering Directions"): the guide's direction set for x = k a_eff and eta
+ * (theta_j equally spaced in s(theta) = theta + theta/(theta + theta0),
+ * theta0 = 2 pi/(1 + x), N_theta = nint of the guide's expression in eta,
+ * N_phi(j) = max(3, nint(4 pi sin theta_j / (theta_{j+1} - theta_{j-1}))),
+ * phi_{j,k} = 2 pi (k-1)/N_phi(j), solid-angle weights Omega_{j,k}), applied to
+ * dC_sca/dOmega = k^4 |F - n (n . F)|^2 with F = sum_j P_j exp(-i k n . r_j).
+ * p_dev: the solved P (complex128 [nrhs][3][N], device).  out[nrhs][6] =
+ * Q_sca by integration, <cos theta>, <cos^2 theta>, and the Lab-Frame
+ * components of <n> (the guide's g vector), all intensity-weighted.
+ * *ndir_out = number of directions (the guide's N_sca).  The far-field sums
+ * run on the device with FP32 phases from FP64 separable tables and FP64
+ * block totals.  Synchronizes. */
+DDA_API dda_status dda_angular_averages(dda_ctx *ctx, const void *p_dev, double eta, double *out,
+                                        int32_t *ndir_out);
+
 /* Diagnostic (no counterpart in the guide): the product kernels stage their
  * shared-memory blocks with bulk asynchronous copies whose completion waits are
  * bounded; a kernel that gives up records a flag, and the next synchronizing

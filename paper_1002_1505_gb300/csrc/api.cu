@@ -1459,6 +1459,139 @@ dda_status dda_profile_matvec(dda_ctx* c, int nrhs, int dtype, int iters, double
   return DDA_OK;
 }
 
+// ------------------------------------------------------------------ angular averages
+// Scattering directions and solid-angle weights (guide, "Averaging over Scattering
+// Directions"): theta_j equally spaced in s(theta) = theta + theta/(theta + theta0),
+// theta0 = 2 pi/(1 + x), N_theta from eta rounded to the nearest integer, N_phi(j) rings of
+// phi_{j,k} = 2 pi (k - 1)/N_phi(j), one direction at theta = 0 and at theta = pi.
+struct ScaDir {
+  double theta, phi, w;
+};
+std::vector<ScaDir> scattering_directions(double x, double eta) {
+  const double pi = 3.14159265358979323846;
+  const double th0 = 2.0 * pi / (1.0 + x);
+  const double nreal = 1.0 + 2.0 * (3.0 + x) / eta * (1.0 + 1.0 / (pi + th0)) / (1.0 + th0 / ((pi + th0) * (pi + th0)));
+  const int nth = std::max(3, (int)std::nearbyint(nreal));
+  std::vector<double> th(nth);
+  const double ds = pi * (1.0 + 1.0 / (pi + th0)) / (nth - 1);
+  for (int j = 0; j < nth; ++j) {
+    const double sj = j * ds;
+    th[j] = ((sj - 1.0 - th0) + std::sqrt((1.0 + th0 - sj) * (1.0 + th0 - sj) + 4.0 * th0 * sj)) / 2.0;
+  }
+  th[0] = 0.0;
+  th[nth - 1] = pi;
+  std::vector<ScaDir> out;
+  for (int j = 0; j < nth; ++j) {
+    const bool pole = (j == 0 || j == nth - 1);
+    const int nphi = pole ? 1 : std::max(3, (int)std::nearbyint(4.0 * pi * std::sin(th[j]) / (th[j + 1] - th[j - 1])));
+    double w;
+    if (j == 0) w = 2.0 * pi / nphi * (1.0 - (std::cos(th[0]) + std::cos(th[1])) / 2.0);
+    else if (j == nth - 1) w = 2.0 * pi / nphi * ((std::cos(th[nth - 2]) + std::cos(th[nth - 1])) / 2.0 + 1.0);
+    else w = pi / nphi * (std::cos(th[j - 1]) - std::cos(th[j + 1]));
+    for (int k = 0; k < nphi; ++k) out.push_back({th[j], 2.0 * pi * k / nphi, w});
+  }
+  return out;
+}
+
+dda_status dda_angular_averages(dda_ctx* c, const void* p_dev, double eta, double* out, int32_t* ndir_out) {
+  if (!c || !p_dev || !out || !(eta > 0.0)) return DDA_EINVAL;
+  if (!c->have_inc) return fail(c, Err::make(DDA_ESTATE, "set the target and the incident beams first"));
+  try {
+    Err e = set_dev(c);
+    if (!e.ok()) return fail(c, e);
+    const double pi = 3.14159265358979323846;
+    const int nrhs = c->nrhs;
+    const double k = c->kd;
+    const double aeff = std::cbrt(3.0 * (double)c->n / (4.0 * pi));
+    const std::vector<ScaDir> dirs = scattering_directions(k * aeff, eta);
+    const int ndir = (int)dirs.size();
+    const int box[3] = {c->tgt.box[0], c->tgt.box[1], c->tgt.box[2]};
+    const int nt = box[0] + box[1] + box[2];
+    const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((c->n + 2047) / 2048, 64));
+    const int nchunk = (ndir + 7) / 8;
+    // RHS per pass: phase tables under ~256 MB
+    const int per = (int)std::max<int64_t>(1, std::min<int64_t>(nrhs, (256ll << 20) / ((int64_t)ndir * nt * 8)));
+    std::vector<double> nl((size_t)ndir * 3);
+    for (int d = 0; d < ndir; ++d) {
+      const double t = dirs[d].theta, f = dirs[d].phi;
+      nl[3 * d] = std::cos(t);
+      nl[3 * d + 1] = std::sin(t) * std::cos(f);
+      nl[3 * d + 2] = std::sin(t) * std::sin(f);
+    }
+    float2* d_tab = nullptr;
+    double* d_part = nullptr;
+    double* d_nh = nullptr;
+    double2* d_F = nullptr;
+    e = dalloc((char**)&d_tab, sizeof(float2) * (size_t)per * ndir * nt);
+    if (e.ok()) e = dalloc((char**)&d_part, sizeof(double) * (size_t)per * nchunk * nblk * 48);
+    if (e.ok()) e = dalloc((char**)&d_nh, sizeof(double) * (size_t)per * ndir * 3);
+    if (e.ok()) e = dalloc((char**)&d_F, sizeof(double2) * (size_t)per * ndir * 3);
+    std::vector<double> nh((size_t)per * ndir * 3);
+    std::vector<double2> F((size_t)per * ndir * 3);
+    for (int b0 = 0; b0 < nrhs && e.ok(); b0 += per) {
+      const int nb = std::min(per, nrhs - b0);
+      // directions in the Target Frame of each RHS's orientation
+      for (int bb = 0; bb < nb; ++bb) {
+        const double* ax = &c->axes[9 * ((b0 + bb) / c->iorth)];
+        for (int d = 0; d < ndir; ++d)
+          for (int q = 0; q < 3; ++q)
+            nh[((size_t)bb * ndir + d) * 3 + q] = nl[3 * d] * ax[q] + nl[3 * d + 1] * ax[3 + q] + nl[3 * d + 2] * ax[6 + q];
+      }
+      if (cudaMemcpyAsync(d_nh, nh.data(), sizeof(double) * (size_t)nb * ndir * 3, cudaMemcpyHostToDevice, c->stream) !=
+          cudaSuccess) {
+        e = Err::make(DDA_ECUDA, "direction upload failed");
+        break;
+      }
+      const double2* P = (const double2*)p_dev + (size_t)b0 * 3 * c->n;
+      e = dda::farfield_many(c->d_ijk, c->d_origin, d_nh, k, P, nb, ndir, c->n, box, d_tab, d_part, nblk, d_F,
+                             c->stream);
+      if (!e.ok()) break;
+      if (cudaMemcpyAsync(F.data(), d_F, sizeof(double2) * (size_t)nb * ndir * 3, cudaMemcpyDeviceToHost, c->stream) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        e = Err::make(DDA_ECUDA, "far-field sums failed");
+        break;
+      }
+      // dC_sca/dOmega = k^4 |F - n (n . F)|^2, summed with the solid-angle weights
+      const double k4 = k * k * k * k;
+      for (int bb = 0; bb < nb; ++bb) {
+        double csum = 0, g1 = 0, g2 = 0, gv[3] = {0, 0, 0};
+        for (int d = 0; d < ndir; ++d) {
+          const double* n = &nh[((size_t)bb * ndir + d) * 3];
+          const double2* Fv = &F[((size_t)bb * ndir + d) * 3];
+          cd f[3], nf(0, 0);
+          for (int q = 0; q < 3; ++q) {
+            f[q] = cd(Fv[q].x, Fv[q].y);
+            nf += n[q] * f[q];
+          }
+          double i2 = 0;
+          for (int q = 0; q < 3; ++q) i2 += std::norm(f[q] - n[q] * nf);
+          const double dc = k4 * i2 * dirs[d].w;
+          const double ct = std::cos(dirs[d].theta);
+          csum += dc;
+          g1 += dc * ct;
+          g2 += dc * ct * ct;
+          for (int q = 0; q < 3; ++q) gv[q] += dc * nl[3 * d + q];
+        }
+        double* o = out + 6 * (size_t)(b0 + bb);
+        o[0] = csum / (pi * aeff * aeff);
+        o[1] = csum > 0 ? g1 / csum : 0.0;
+        o[2] = csum > 0 ? g2 / csum : 0.0;
+        for (int q = 0; q < 3; ++q) o[3 + q] = csum > 0 ? gv[q] / csum : 0.0;
+      }
+    }
+    dfree(d_tab);
+    dfree(d_part);
+    dfree(d_nh);
+    dfree(d_F);
+    if (!e.ok()) return fail(c, e);
+    if (ndir_out) *ndir_out = ndir;
+    return DDA_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, Err::make(DDA_ENOMEM, "host allocation failed"));
+  }
+}
+
 dda_status dda_selftest_bulk_wait(int device, int32_t* gave_up) {
   if (!gave_up) return DDA_EINVAL;
   if (cudaSetDevice(device) != cudaSuccess) return DDA_ECUDA;

@@ -258,6 +258,12 @@ Err qsums(const int32_t* ijk, const uint8_t* comp, const double* origin3, const 
 Err farfield(const int32_t* ijk, const double* origin3, const double* nhat /*[nrhs][ndir][3]*/, double kd,
              const double2* p, int nrhs, int ndir, int64_t n, double2* out, double2* part, int nblk,
              cudaStream_t st);
+// Far field F = sum_j P_j exp(-i k n.r_j) for many directions (nhat [nrhs][ndir][3] in TF) from
+// separable FP32 phase tables (tab: nrhs*ndir*(box sum) float2; part: nrhs*ceil(ndir/8)*nblk*48
+// doubles); out [nrhs][ndir][3].
+Err farfield_many(const int32_t* ijk, const double* origin3, const double* nhat, double kd, const double2* p,
+                  int nrhs, int ndir, int64_t n, const int box[3], float2* tab, double* part, int nblk, double2* out,
+                  cudaStream_t st);
 
 // ------------------------------------------------------------------ learned warm start glue (unet.cu)
 Err unet_features(const int32_t* ijk, int64_t n, const uint8_t* comp, const float2* eps, const double2* e, int nrhs,

@@ -130,7 +130,115 @@ __global__ void k_far_fin(const double* part, int nblk, double2* out) {
     for (int c = 0; c < 3; ++c) out[(int64_t)o * 3 + c] = make_double2(res[2 * c], res[2 * c + 1]);
 }
 
+// ------------------------------------------------------------------ many scattering directions
+// The far-field phase of a lattice site factorises over the axes:
+// exp(-i k n.r) = T_x[i] T_y[j] T_z[l] with T_a[i] = exp(-i k n_a (i + origin_a)); the tables
+// are built in FP64 and stored in FP32, one set per (RHS, direction):
+// tab[rd * nt + {0 | bx | bx + by} + i], nt = bx + by + bz.
+__global__ void k_phase_tables(const double* __restrict__ nhat, int64_t nrd, const double* __restrict__ org, double kd,
+                               int bx, int by, int bz, float2* __restrict__ tab) {
+  const int nt = bx + by + bz;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nrd * nt; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t rd = t / nt;
+    const int i = (int)(t - rd * nt);
+    int a, ii;
+    if (i < bx) { a = 0; ii = i; }
+    else if (i < bx + by) { a = 1; ii = i - bx; }
+    else { a = 2; ii = i - bx - by; }
+    double sn, cs;
+    sincos(-kd * nhat[rd * 3 + a] * ((double)ii + org[a]), &sn, &cs);
+    tab[t] = make_float2((float)cs, (float)sn);
+  }
+}
+
+// F[rhs][d] = sum_j P_j exp(-i k n_d . r_j) for kDirPerCta directions per CTA: grid (site blocks,
+// direction chunks, nrhs); per-thread FP32 sums over its sites, then FP64 across the block.
+constexpr int kDirPerCta = 8;
+__global__ void __launch_bounds__(kT) k_far_many(const int32_t* __restrict__ ijk, const double2* __restrict__ p,
+                                                 int64_t n, int ndir, int bx, int by, int bz,
+                                                 const float2* __restrict__ tab, double* __restrict__ part) {
+  extern __shared__ float2 stab[];
+  const int nt = bx + by + bz;
+  const int b = blockIdx.z, d0 = blockIdx.y * kDirPerCta;
+  const int nd = min(kDirPerCta, ndir - d0);
+  const float2* src = tab + ((int64_t)b * ndir + d0) * nt;
+  for (int i = threadIdx.x; i < nd * nt; i += blockDim.x) stab[i] = src[i];
+  __syncthreads();
+  float acc[kDirPerCta][6];
+#pragma unroll
+  for (int dd = 0; dd < kDirPerCta; ++dd)
+#pragma unroll
+    for (int s = 0; s < 6; ++s) acc[dd][s] = 0.f;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int ix = ijk[3 * j], iy = bx + ijk[3 * j + 1], iz = bx + by + ijk[3 * j + 2];
+    float2 pv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double2 v = p[((int64_t)b * 3 + c) * n + j];
+      pv[c] = make_float2((float)v.x, (float)v.y);
+    }
+#pragma unroll
+    for (int dd = 0; dd < kDirPerCta; ++dd) {
+      if (dd < nd) {
+        const float2* t = stab + dd * nt;
+        const float2 tx = t[ix], ty = t[iy], tz = t[iz];
+        const float2 txy = make_float2(tx.x * ty.x - tx.y * ty.y, tx.x * ty.y + tx.y * ty.x);
+        const float2 ph = make_float2(txy.x * tz.x - txy.y * tz.y, txy.x * tz.y + txy.y * tz.x);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          acc[dd][2 * c] = fmaf(pv[c].x, ph.x, fmaf(-pv[c].y, ph.y, acc[dd][2 * c]));
+          acc[dd][2 * c + 1] = fmaf(pv[c].x, ph.y, fmaf(pv[c].y, ph.x, acc[dd][2 * c + 1]));
+        }
+      }
+    }
+  }
+  double v[kDirPerCta * 6];
+#pragma unroll
+  for (int dd = 0; dd < kDirPerCta; ++dd)
+#pragma unroll
+    for (int s = 0; s < 6; ++s) v[dd * 6 + s] = (double)acc[dd][s];
+  bred<kDirPerCta * 6>(v, part + (((int64_t)b * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (kDirPerCta * 6));
+}
+
+// sum the site-block partials: out[rhs][d][3] (complex)
+__global__ void k_far_many_fin(const double* __restrict__ part, int nblk, int nchunk, int ndir,
+                               double2* __restrict__ out) {
+  const int rc = blockIdx.x;  // rhs * nchunk + chunk
+  const int b = rc / nchunk, ch = rc - b * nchunk;
+  for (int s = threadIdx.x; s < kDirPerCta * 6; s += blockDim.x) {
+    double v = 0.0;
+    for (int i = 0; i < nblk; ++i) v += part[((int64_t)rc * nblk + i) * (kDirPerCta * 6) + s];
+    const int d = ch * kDirPerCta + s / 6;
+    if (d < ndir) {
+      const int q = s % 6;
+      double* o = reinterpret_cast<double*>(out + ((int64_t)b * ndir + d) * 3);
+      o[q] = v;
+    }
+  }
+}
+
 }  // namespace
+
+Err farfield_many(const int32_t* ijk, const double* origin3, const double* nhat, double kd, const double2* p,
+                  int nrhs, int ndir, int64_t n, const int box[3], float2* tab, double* part, int nblk, double2* out,
+                  cudaStream_t st) {
+  const int nt = box[0] + box[1] + box[2];
+  const int64_t nrd = (int64_t)nrhs * ndir;
+  const int tb = (int)std::min<int64_t>((nrd * nt + kT - 1) / kT, 152 * 32);
+  k_phase_tables<<<tb, kT, 0, st>>>(nhat, nrd, origin3, kd, box[0], box[1], box[2], tab);
+  DDA_CU(cudaGetLastError());
+  add_launches(1);
+  const int nchunk = (ndir + kDirPerCta - 1) / kDirPerCta;
+  const size_t sm = sizeof(float2) * (size_t)kDirPerCta * nt;
+  if (sm > 48 * 1024) return Err::make(DDA_EUNSUPPORTED, "target box too long for the phase tables");
+  k_far_many<<<dim3(nblk, nchunk, nrhs), kT, sm, st>>>(ijk, p, n, ndir, box[0], box[1], box[2], tab, part);
+  DDA_CU(cudaGetLastError());
+  add_launches(1);
+  k_far_many_fin<<<nrhs * nchunk, 64, 0, st>>>(part, nblk, nchunk, ndir, out);
+  DDA_CU(cudaGetLastError());
+  add_launches(1);
+  return Err::Ok();
+}
 
 template <typename C>
 Err incident_field(const int32_t* ijk, const double* origin3, const RhsGeom* rg, int nrhs, int64_t n, C* e,

@@ -73,6 +73,7 @@ def _load():
         "dda_version": (ctypes.c_char_p, []),
         "dda_kernel_launches": (ctypes.c_ulonglong, []),
         "dda_selftest_bulk_wait": (I, [I, P]),
+        "dda_angular_averages": (I, [P, P, D, P, P]),
         "dda_profile_matvec": (I, [P, I, I, I, P, P]),
         "dda_matvec_noalloc": (I, [P, P, P, I, I]),
         "dda_schedule_info": (I, [P, I, P]),
@@ -246,6 +247,14 @@ class Context:
         if st != DDA_OK and (raise_on_noconv or st not in (DDA_ENOCONV, DDA_ETIMEOUT)):
             self._check(st)
         return reports, st
+
+    def dda_angular_averages(self, p, eta=0.5):
+        """(out [nrhs, 6] = Qsca_int, <cos>, <cos^2>, <n>_LF xyz; number of directions) for solved P."""
+        self._dev_check(p, DDA_C128)
+        out = np.zeros((self.nrhs, 6))
+        nd = np.zeros(1, dtype=np.int32)
+        self._check(LIB.dda_angular_averages(self._h, ctypes.c_void_p(p.data_ptr()), float(eta), _ptr(out), _ptr(nd)))
+        return out, int(nd[0])
 
     def dda_cross_sections(self, p, dirs=None):
         """Returns (Q array [nrhs,4] = Qext,Qabs,Qsca,Qpha, Mueller [n_ori,ndir,4,4] or None)."""

@@ -339,6 +339,18 @@ DDA_API dda_status dda_unet_residual_grad(dda_ctx *ctx, const float *y_dev, cons
 DDA_API dda_status dda_angular_averages(dda_ctx *ctx, const void *p_dev, double eta, double *out,
                                         int32_t *ndir_out);
 
+/* Orientation grid for orientational averaging (guide, "Sampling in Theta,
+ * Phi, and beta" and "Orientational Averaging"): beta and Phi at the midpoints
+ * of nbeta / nphi equal intervals of [min, max] (degrees); cos(Theta) uniform:
+ * ntheta odd -> the end points included with Simpson weights
+ * (1/3, 4/3, 2/3, ..., 4/3, 1/3)/(ntheta - 1), ntheta even -> interval
+ * midpoints with equal weights.  ori_out [nbeta*ntheta*nphi][3] = (beta,
+ * Theta, Phi) in radians, Phi fastest then Theta then beta (pass it to
+ * dda_set_incident); w_out [n] = weights (they sum to one; the average of a
+ * quantity over orientations is sum_o w_o Q_o).  Host only. */
+DDA_API dda_status dda_orientation_grid(const double beta_deg[2], int nbeta, const double theta_deg[2], int ntheta,
+                                        const double phi_deg[2], int nphi, double *ori_out, double *w_out);
+
 /* Diagnostic (no counterpart in the guide): the product kernels stage their
  * shared-memory blocks with bulk asynchronous copies whose completion waits are
  * bounded; a kernel that gives up records a flag, and the next synchronizing

@@ -9,6 +9,13 @@
 * "Scattering directions" (CMDFRM = LFRAME): n_s = x cos(th) + y sin(th) cos(ph)
   + z sin(th) sin(ph); the scattered basis is theta_hat, phi_hat of that
   direction ("Scattering Amplitude Matrix" section).
+* "Sampling in Theta, Phi, and beta" / "Orientational Averaging": beta and
+  Phi at the midpoints of NBETA / NPHI equal intervals, uniform weights;
+  cos(Theta) uniform: NTHETA odd -> the end points included and Simpson
+  weights, NTHETA even -> interval midpoints and equal weights.  The guide
+  writes the odd-NTHETA weights as (1/3, 4/3, 2/3)/(NTHETA NPHI), which would
+  not sum to one; they are taken here as Simpson's rule on NTHETA - 1
+  intervals of cos(Theta), i.e. (1/3, 4/3, 2/3, ..., 4/3, 1/3)/(NTHETA - 1).
 """
 from __future__ import annotations
 
@@ -75,3 +82,30 @@ def scattering_basis_lf(theta_s: float, phi_s: float):
     th = np.array([-st, ct * cp, ct * sp])
     ph = np.array([0.0, -sp, cp])
     return n, th, ph
+
+
+def orientation_grid(beta_deg, nbeta: int, theta_deg, ntheta: int, phi_deg, nphi: int):
+    """(orientations [(beta, Theta, Phi)] in radians, weights summing to one); Phi varies fastest,
+    then Theta, then beta.  *_deg = (min, max) in degrees."""
+    def mids(lo, hi, n):
+        return [lo + (hi - lo) * (i + 0.5) / n for i in range(n)]
+    betas = mids(beta_deg[0], beta_deg[1], nbeta)
+    phis = mids(phi_deg[0], phi_deg[1], nphi)
+    c0, c1 = np.cos(np.radians(theta_deg[0])), np.cos(np.radians(theta_deg[1]))
+    if ntheta % 2 == 1:
+        if ntheta == 1:
+            cosv, wt = [c0], [1.0]
+        else:
+            cosv = [c0 + (c1 - c0) * i / (ntheta - 1) for i in range(ntheta)]
+            wt = [(1.0 if i in (0, ntheta - 1) else (4.0 if i % 2 == 1 else 2.0)) / 3.0 / (ntheta - 1)
+                  for i in range(ntheta)]
+    else:
+        cosv = [c0 + (c1 - c0) * (i + 0.5) / ntheta for i in range(ntheta)]
+        wt = [1.0 / ntheta] * ntheta
+    oris, w = [], []
+    for b in betas:
+        for t, wth in zip(cosv, wt):
+            for f in phis:
+                oris.append((np.radians(b), float(np.arccos(np.clip(t, -1.0, 1.0))), np.radians(f)))
+                w.append(wth / (nbeta * nphi))
+    return oris, np.array(w)

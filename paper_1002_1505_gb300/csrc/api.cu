@@ -1592,6 +1592,45 @@ dda_status dda_angular_averages(dda_ctx* c, const void* p_dev, double eta, doubl
   }
 }
 
+dda_status dda_orientation_grid(const double beta_deg[2], int nbeta, const double theta_deg[2], int ntheta,
+                                const double phi_deg[2], int nphi, double* ori_out, double* w_out) {
+  if (!beta_deg || !theta_deg || !phi_deg || !ori_out || !w_out || nbeta < 1 || ntheta < 1 || nphi < 1)
+    return DDA_EINVAL;
+  const double rad = 3.14159265358979323846 / 180.0;
+  // beta and Phi: midpoints of equal intervals; cos(Theta): Simpson nodes (odd) or midpoints (even)
+  std::vector<double> cth(ntheta), wth(ntheta);
+  const double c0 = std::cos(theta_deg[0] * rad), c1 = std::cos(theta_deg[1] * rad);
+  if (ntheta == 1) {
+    cth[0] = c0;
+    wth[0] = 1.0;
+  } else if (ntheta % 2 == 1) {
+    for (int i = 0; i < ntheta; ++i) {
+      cth[i] = c0 + (c1 - c0) * (double)i / (ntheta - 1);
+      const double s = (i == 0 || i == ntheta - 1) ? 1.0 : (i % 2 ? 4.0 : 2.0);
+      wth[i] = s / 3.0 / (ntheta - 1);
+    }
+  } else {
+    for (int i = 0; i < ntheta; ++i) {
+      cth[i] = c0 + (c1 - c0) * (i + 0.5) / ntheta;
+      wth[i] = 1.0 / ntheta;
+    }
+  }
+  int64_t o = 0;
+  for (int ib = 0; ib < nbeta; ++ib) {
+    const double beta = (beta_deg[0] + (beta_deg[1] - beta_deg[0]) * (ib + 0.5) / nbeta) * rad;
+    for (int it = 0; it < ntheta; ++it) {
+      const double th = std::acos(std::max(-1.0, std::min(1.0, cth[it])));
+      for (int ip = 0; ip < nphi; ++ip, ++o) {
+        ori_out[3 * o] = beta;
+        ori_out[3 * o + 1] = th;
+        ori_out[3 * o + 2] = (phi_deg[0] + (phi_deg[1] - phi_deg[0]) * (ip + 0.5) / nphi) * rad;
+        w_out[o] = wth[it] / ((double)nbeta * nphi);
+      }
+    }
+  }
+  return DDA_OK;
+}
+
 dda_status dda_selftest_bulk_wait(int device, int32_t* gave_up) {
   if (!gave_up) return DDA_EINVAL;
   if (cudaSetDevice(device) != cudaSuccess) return DDA_ECUDA;

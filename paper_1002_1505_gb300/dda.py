@@ -74,6 +74,7 @@ def _load():
         "dda_kernel_launches": (ctypes.c_ulonglong, []),
         "dda_selftest_bulk_wait": (I, [I, P]),
         "dda_angular_averages": (I, [P, P, D, P, P]),
+        "dda_orientation_grid": (I, [P, I, P, I, P, I, P, P]),
         "dda_profile_matvec": (I, [P, I, I, I, P, P]),
         "dda_matvec_noalloc": (I, [P, P, P, I, I]),
         "dda_schedule_info": (I, [P, I, P]),
@@ -378,6 +379,27 @@ def dda_unet_residual_grad(ctx: "Context", y, gy, dims, weight=1.0, offset=None)
     ctx._check(LIB.dda_unet_residual_grad(ctx._h, ctypes.c_void_p(y.data_ptr()), _ptr(d), None if o is None else _ptr(o),
                                           float(weight), ctypes.c_void_p(gy.data_ptr()), ctypes.byref(loss)))
     return float(loss.value)
+
+
+def dda_orientation_grid(beta_deg, nbeta, theta_deg, ntheta, phi_deg, nphi):
+    """(orientations [n, 3] radians (beta, Theta, Phi), weights [n]) of the guide's orientation sampling."""
+    n = int(nbeta) * int(ntheta) * int(nphi)
+    ori = np.zeros((n, 3))
+    w = np.zeros(n)
+    b = np.ascontiguousarray(beta_deg, dtype=np.float64)
+    t = np.ascontiguousarray(theta_deg, dtype=np.float64)
+    f = np.ascontiguousarray(phi_deg, dtype=np.float64)
+    st = LIB.dda_orientation_grid(_ptr(b), int(nbeta), _ptr(t), int(ntheta), _ptr(f), int(nphi), _ptr(ori), _ptr(w))
+    if st != DDA_OK:
+        raise DDAError(st, "dda_orientation_grid failed")
+    return ori, w
+
+
+def orientation_average(q, w, iorth: int = 2):
+    """Weighted average over orientations of per-RHS results q [n_ori * iorth, ...]; returns [iorth, ...]."""
+    q = np.asarray(q)
+    q = q.reshape((len(w), iorth) + q.shape[1:])
+    return np.tensordot(np.asarray(w), q, axes=(0, 0))
 
 
 def dda_selftest_bulk_wait(device: int = 0) -> bool:

@@ -135,3 +135,14 @@ def test_polarizability_matches_oracle(D, presc):
         for c, m in enumerate(ms):
             ref = o_pol.inv_alpha(presc, m, 0.41, k[b] / 0.41, e[b])
             np.testing.assert_allclose(ia[b, c], ref, rtol=1e-14)
+
+
+def test_orientation_grid_matches_oracle(D):
+    """The library's orientation sampling against the oracle's restatement of the guide."""
+    from oracle import orientation as oori
+    for args in [((0, 90), 2, (0, 90), 3, (0, 180), 2), ((0, 360), 3, (0, 180), 5, (0, 360), 4),
+                 ((10, 20), 1, (30, 150), 4, (0, 0), 1), ((0, 0), 1, (0, 0), 1, (0, 0), 1)]:
+        ori, w = D.dda_orientation_grid(*args)
+        ref, wr = oori.orientation_grid(*args)
+        np.testing.assert_allclose(ori, np.array(ref), rtol=0, atol=1e-13)
+        np.testing.assert_allclose(w, wr, rtol=1e-14, atol=0)

@@ -473,6 +473,29 @@ def test_angular_averages_au_block(D):
         assert abs(fine[b, 1] - 0.46029) < 1e-3
 
 
+def test_orientation_averaged_efficiencies(D):
+    """Orientational averaging with the guide's (beta, Theta, Phi) sampling (Simpson in cos Theta):
+    GPU batched solve over all orientations, weighted average, against the oracle's."""
+    from oracle import orientation as oori
+    args = ((0, 360), 2, (0, 180), 3, (0, 360), 2)
+    ori, wts = D.dda_orientation_grid(*args)
+    w = W.Workload("ell_avg", "ELLIPSOID", (8, 6, 5), 1.5 + 0.1j, 2.0, "GKDLDR", tuple(map(tuple, ori)))
+    ref_ori, ref_w = oori.orientation_grid(*args)
+    prob = odda.build_problem(w.shape, w.shpar, w.m, w.x, w.prescription, ref_ori)
+    ps, _ = odda.solve(prob, "lu")
+    qref = odda.cross_sections(prob, ps)
+    qr = np.array([[q["Qext"], q["Qabs"], q["Qsca"]] for q in qref])
+    ctx = _ctx(D, w)
+    p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
+    reps, _ = ctx.dda_solve(p, precision="MIXED", tol=1e-6, maxit=2000)
+    q, _ = ctx.dda_cross_sections(p)
+    avg = D.orientation_average(q[:, :3], wts)
+    avg_ref = D.orientation_average(qr, ref_w)
+    np.testing.assert_allclose(avg, avg_ref, rtol=2e-5)
+    # the average differs from any single orientation (the ellipsoid is not isotropic)
+    assert np.ptp(q[:, 0]) > 1e-3 * avg[0, 0]
+
+
 def test_warm_start_from_solution_needs_no_iterations(D):
     w = W.SPHERE12
     prob, ps, _ = _oracle_q(w, tol=1e-12)

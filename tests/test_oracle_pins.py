@@ -300,6 +300,28 @@ def test_bicgstab_l_reduces_to_bicgstab_and_solves():
     assert all(i > 0 for i in its)
 
 
+def test_orientation_grid_guide_examples():
+    """The guide's own examples of the (beta, Theta, Phi) sampling, and the weights' quadrature."""
+    deg = lambda v: [math.degrees(x) for x in v]
+    oris, _ = orientation.orientation_grid((0, 90), 2, (0, 0), 1, (0, 0), 1)
+    assert deg([o[0] for o in oris]) == pytest.approx([22.5, 67.5])
+    oris, _ = orientation.orientation_grid((0, 0), 1, (0, 0), 1, (0, 180), 2)
+    assert deg([o[2] for o in oris]) == pytest.approx([45.0, 135.0])
+    oris, _ = orientation.orientation_grid((0, 0), 1, (0, 90), 3, (0, 0), 1)
+    assert deg([o[1] for o in oris]) == pytest.approx([0.0, 60.0, 90.0], abs=1e-12)
+    oris, _ = orientation.orientation_grid((0, 0), 1, (0, 90), 2, (0, 0), 1)
+    assert deg([o[1] for o in oris]) == pytest.approx([41.4096, 75.5225], abs=1e-4)
+    # weights sum to one; odd NTHETA integrates cubics in cos(Theta) exactly over [-1, 1]
+    oris, w = orientation.orientation_grid((0, 360), 3, (0, 180), 5, (0, 360), 4)
+    assert len(oris) == 60 and w.sum() == pytest.approx(1.0, abs=1e-15)
+    ct = np.cos([o[1] for o in oris])
+    for k, exact in ((1, 0.0), (2, 1.0 / 3.0), (3, 0.0)):
+        assert np.sum(w * ct ** k) == pytest.approx(exact, abs=1e-14)
+    # even NTHETA: midpoint rule, exact for linear functions
+    oris, w = orientation.orientation_grid((0, 360), 1, (0, 180), 4, (0, 360), 1)
+    assert np.sum(w * np.cos([o[1] for o in oris])) == pytest.approx(0.0, abs=1e-15)
+
+
 # ----------------------------------------------------------------------------- observables
 
 def test_real_index_has_zero_absorption():

@@ -456,7 +456,8 @@ def main():
                 "passes_ms": {nm: float(v) for nm, v in zip(names, ms_pass)},
                 "schedule": {"passes": sched[0], "compile_time_kernels": bool(sched[1]),
                              "plane_threads": sched[2], "tuned_for_nrhs": sched[3], "ctas_per_plane": sched[4],
-                             "x_tile_rows": sched[5], "bulk_staged_plane": bool(sched[6])},
+                             "x_tile_rows": sched[5], "bulk_staged_plane": bool(sched[6]),
+                             "x_components_per_cta": sched[7]},
                 "product_ms": float(np.sum(ms_pass))}
     flops = algorithmic_flops(len(ms_pass), box, pad, nrhs)
     tfl = flops[dom] / (ms_pass[dom] * 1e-3) / 1e12

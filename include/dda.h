@@ -248,15 +248,17 @@ DDA_API dda_status dda_profile_matvec(dda_ctx *ctx, int nrhs, int dtype, int ite
  * the fastest) or pinned by the DDA_SCHEDULE environment variable at
  * dda_build_green_fft time ("generic", "fast5", "plane512", "plane768",
  * "cluster2", "cluster4"; DDA_XTILE = 4, 8 or 16 pins the x passes' tile
- * height; DDA_BULK = 1 or 0 pins bulk-copy staging of the plane pass).
+ * height; DDA_BULK = 1 or 0 pins bulk-copy staging of the plane pass;
+ * DDA_XCOMP = 1 runs the x passes with one field component per CTA).
  * info[0] = passes (3 = fused y-z plane, 5 = split), info[1] = 1 when the
  * compile-time-length kernels are used, info[2] = threads per CTA of the plane
  * kernel (0 if none), info[3] = RHS count the choice was tuned for (0 = not
  * tuned), info[4] = CTAs per plane (1, or the thread-block cluster size when
  * the plane pass is split over a cluster), info[5] = y rows per CTA of the x
  * passes (0 for the generic engine), info[6] = 1 when the plane pass stages its
- * HBM blocks with bulk copies (TMA). */
-DDA_API dda_status dda_schedule_info(dda_ctx *ctx, int dtype, int32_t info[7]);
+ * HBM blocks with bulk copies (TMA), info[7] = field components per CTA of the
+ * x passes (3 or 1; 0 for the generic engine). */
+DDA_API dda_status dda_schedule_info(dda_ctx *ctx, int dtype, int32_t info[8]);
 
 /* ---------------------------------------------------------------------------
  * Learned warm start (the guide has no counterpart: the solver accepts any

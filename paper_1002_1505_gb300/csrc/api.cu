@@ -474,6 +474,13 @@ Err ensure_tuned(dda_ctx* c, int nrhs) {
         if (!err.ok()) break;
       }
     }
+    // one component per x-pass CTA (smaller tiles in shared memory, longer rows per store)
+    if (err.ok()) {
+      dda::MvTune t = best;
+      t.xnc = 1;
+      t.xty = 0;
+      time_one(t);
+    }
     // and bulk-copy staging of the plane pass's HBM blocks
     int smax_b = 0;
     cudaDeviceGetAttribute(&smax_b, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
@@ -930,6 +937,14 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
     // DDA_BULK=1 / 0 pins bulk-copy staging of the plane pass on / off
     if (const char* f = std::getenv("DDA_BULK")) {
       t64.bulk = (std::atoi(f) != 0) && t64.plane_ok && dda::plane_bulk_ok_c64(g64, smax);
+      c->forced_schedule = true;
+    }
+    // DDA_XCOMP=1 runs the x passes with one component per CTA
+    if (const char* f = std::getenv("DDA_XCOMP")) {
+      if (std::atoi(f) == 1) {
+        if (t64.fast) t64.xnc = 1;
+        if (t128.fast) t128.xnc = 1;
+      }
       c->forced_schedule = true;
     }
     // DDA_XTILE pins the x passes' tile height (y rows per CTA: 4, 8 or 16 where instantiated)
@@ -1641,7 +1656,7 @@ dda_status dda_selftest_bulk_wait(int device, int32_t* gave_up) {
   return DDA_OK;
 }
 
-dda_status dda_schedule_info(dda_ctx* c, int dtype, int32_t info[7]) {
+dda_status dda_schedule_info(dda_ctx* c, int dtype, int32_t info[8]) {
   if (!c || !info) return DDA_EINVAL;
   if (!c->have_green) return fail(c, Err::make(DDA_ESTATE, "build the Green tensor first"));
   if (dtype != DDA_C64 && dtype != DDA_C128) return fail(c, Err::make(DDA_EINVAL, "bad dtype"));
@@ -1656,8 +1671,10 @@ dda_status dda_schedule_info(dda_ctx* c, int dtype, int32_t info[7]) {
     const dda::Geom& g = dtype == DDA_C64 ? c->g64 : c->g128;
     const size_t cs = dtype == DDA_C64 ? sizeof(float2) : sizeof(double2);
     info[5] = !t.fast ? 0
-                      : (t.xty > 0 && dda::x_tile_height_ok(cs, g.px, t.xty) ? t.xty
-                                                                             : dda::x_tile_height_default(cs, g.px));
+              : t.xnc == 1 ? dda::x_tile_height_one_component(cs)
+                           : (t.xty > 0 && dda::x_tile_height_ok(cs, g.px, t.xty) ? t.xty
+                                                                                  : dda::x_tile_height_default(cs, g.px));
+    info[7] = !t.fast ? 0 : (t.xnc == 1 ? 1 : 3);
   }
   return DDA_OK;
 }

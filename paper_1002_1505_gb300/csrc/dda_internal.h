@@ -97,6 +97,7 @@ struct MvTune {
   bool plane_ok = false;  // the fast 3-pass plane kernel exists and fits for this grid
   int clus = 0;           // plane pass split over a cluster of this many CTAs (0: one CTA per plane)
   int xty = 0;            // y rows per CTA of the compile-time x passes (0: the length's default)
+  int xnc = 0;            // components per CTA of the x passes (0 or 3: all three; 1: one)
   bool bulk = false;      // plane pass stages its HBM blocks with bulk copies
 };
 
@@ -138,6 +139,7 @@ void choose_fast_schedule(const Geom& g, bool c64, int smax, MvTune* t);
 // whether a height is instantiated
 int x_tile_height_default(size_t csize, int px);
 bool x_tile_height_ok(size_t csize, int px, int ty);
+int x_tile_height_one_component(size_t csize);
 // profiling hook: record the i-th pass event if per-pass events are on
 void mark_pass(int i, cudaStream_t st);
 size_t x_smem_bytes(const Geom& g, const MvTune& t, size_t csize);

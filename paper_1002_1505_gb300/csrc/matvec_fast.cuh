@@ -69,40 +69,43 @@ __device__ __forceinline__ void copy_tw(C* dst, const C* src, int L) {
 }
 
 // ------------------------------------------------------------------ x forward
-// grid (ceil(ny/TY), nz, nrhs). smem: tw[PX] | in[3*TY][ip] | out[3*PX][TY]
-template <typename C, int PX, int TY>
+// grid (ceil(ny/TY), nz, nrhs * 3/NC): NC components (1 or 3) of TY y rows per CTA.
+// smem: tw[PX] | in[NC*TY][ip] | out[NC*PX][TY]
+template <typename C, int PX, int TY, int NC = 3>
 __global__ void __launch_bounds__(256) k_x_fwd(Geom g, MvData<C> d, const C* __restrict__ p, bool conj, int ip) {
   constexpr int RA = Shape<PX>::RA, LB = Shape<PX>::LB, H = Shape<PX>::H;
+  static_assert(NC == 1 || NC == 3, "one or three components per CTA");
   extern __shared__ unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* in = tw + PX;
-  C* out = in + 3 * TY * ip;
-  const int y0 = blockIdx.x * TY, z = blockIdx.y, b = blockIdx.z;
+  C* out = in + NC * TY * ip;
+  const int y0 = blockIdx.x * TY, z = blockIdx.y;
+  const int b = blockIdx.z / (3 / NC), c0 = (blockIdx.z % (3 / NC)) * NC;
   if (rhs_done(d, b)) return;
   copy_tw(tw, d.twx, PX);
-  const int nld = 3 * TY * g.nx;
+  const int nld = NC * TY * g.nx;
   for (int i = threadIdx.x; i < nld; i += blockDim.x) {
     const int x = i % g.nx;
     const int r = i / g.nx;
-    const int t = r % TY, c = r / TY;
+    const int t = r % TY, cl = r / TY;
     const int y = y0 + t;
     C v = czero<C>();
     if (y < g.ny) {
       const int32_t idx = __ldg(d.map + ((int64_t)z * g.ny + y) * g.nx + x);
       if (idx >= 0) {
-        v = p[((int64_t)b * 3 + c) * g.n + idx];
+        v = p[((int64_t)b * 3 + c0 + cl) * g.n + idx];
         if (conj) v = conjc(v);
       }
     }
-    in[(c * TY + t) * ip + x] = v;
+    in[(cl * TY + t) * ip + x] = v;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 3 * TY * LB; i += blockDim.x) {
+  for (int i = threadIdx.x; i < NC * TY * LB; i += blockDim.x) {
     const int t = i % TY;
     const int r = i / TY;
-    const int n1 = r % LB, c = r / LB;
+    const int n1 = r % LB, cl = r / LB;
     C x[RA], o[2 * RA];
-    const C* src = in + (c * TY + t) * ip;
+    const C* src = in + (cl * TY + t) * ip;
 #pragma unroll
     for (int j = 0; j < RA; ++j) {
       const int xx = n1 + LB * j;
@@ -112,21 +115,21 @@ __global__ void __launch_bounds__(256) k_x_fwd(Geom g, MvData<C> d, const C* __r
 #pragma unroll
     for (int bb = 0; bb < 2; ++bb)
 #pragma unroll
-      for (int k = 0; k < RA; ++k) out[(c * PX + bb * H + n1 + LB * k) * TY + t] = o[bb * RA + k];
+      for (int k = 0; k < RA; ++k) out[(cl * PX + bb * H + n1 + LB * k) * TY + t] = o[bb * RA + k];
   }
   __syncthreads();
   const int64_t plane = (int64_t)g.nz * g.ys;
-  for (int i = threadIdx.x; i < 3 * 2 * RA * TY; i += blockDim.x) {
+  for (int i = threadIdx.x; i < NC * 2 * RA * TY; i += blockDim.x) {
     const int t = i % TY;
     const int r = i / TY;
-    const int blk = r % (2 * RA), c = r / (2 * RA);
+    const int blk = r % (2 * RA), cl = r / (2 * RA);
     C v[LB];
 #pragma unroll
-    for (int e = 0; e < LB; ++e) v[e] = out[(c * PX + blk * LB + e) * TY + t];
+    for (int e = 0; e < LB; ++e) v[e] = out[(cl * PX + blk * LB + e) * TY + t];
     f2::passB_fwd<PX>(v, tw);
     const int y = y0 + t;
     if (y < g.ny) {
-      C* dst = d.work + (((int64_t)b * 3 + c) * PX + blk * LB) * plane + (int64_t)z * g.ys + y;
+      C* dst = d.work + (((int64_t)b * 3 + c0 + cl) * PX + blk * LB) * plane + (int64_t)z * g.ys + y;
 #pragma unroll
       for (int e = 0; e < LB; ++e) dst[e * plane] = v[e];
     }
@@ -134,27 +137,30 @@ __global__ void __launch_bounds__(256) k_x_fwd(Geom g, MvData<C> d, const C* __r
 }
 
 // ------------------------------------------------------------------ x inverse + alpha^{-1} P + scatter
-template <typename C, int PX, int TY>
+// grid and shared memory as k_x_fwd
+template <typename C, int PX, int TY, int NC = 3>
 __global__ void __launch_bounds__(256) k_x_inv(Geom g, MvData<C> d, const C* __restrict__ p, C* __restrict__ ap,
                                                int rhs0, bool conj, int ip) {
   constexpr int RA = Shape<PX>::RA, LB = Shape<PX>::LB, H = Shape<PX>::H;
+  static_assert(NC == 1 || NC == 3, "one or three components per CTA");
   extern __shared__ unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* in = tw + PX;
-  C* out = in + 3 * TY * ip;
-  const int y0 = blockIdx.x * TY, z = blockIdx.y, b = blockIdx.z;
+  C* out = in + NC * TY * ip;
+  const int y0 = blockIdx.x * TY, z = blockIdx.y;
+  const int b = blockIdx.z / (3 / NC), c0 = (blockIdx.z % (3 / NC)) * NC;
   if (rhs_done(d, b)) return;
   copy_tw(tw, d.twx, PX);
   __syncthreads();
   const int64_t plane = (int64_t)g.nz * g.ys;
-  for (int i = threadIdx.x; i < 3 * 2 * RA * TY; i += blockDim.x) {
+  for (int i = threadIdx.x; i < NC * 2 * RA * TY; i += blockDim.x) {
     const int t = i % TY;
     const int r = i / TY;
-    const int blk = r % (2 * RA), c = r / (2 * RA);
+    const int blk = r % (2 * RA), cl = r / (2 * RA);
     const int y = y0 + t;
     C v[LB];
     if (y < g.ny) {
-      const C* src = d.work + (((int64_t)b * 3 + c) * PX + blk * LB) * plane + (int64_t)z * g.ys + y;
+      const C* src = d.work + (((int64_t)b * 3 + c0 + cl) * PX + blk * LB) * plane + (int64_t)z * g.ys + y;
 #pragma unroll
       for (int e = 0; e < LB; ++e) v[e] = src[e * plane];
     } else {
@@ -163,20 +169,20 @@ __global__ void __launch_bounds__(256) k_x_inv(Geom g, MvData<C> d, const C* __r
     }
     f2::passB_inv<PX>(v, tw);
 #pragma unroll
-    for (int e = 0; e < LB; ++e) out[(c * PX + blk * LB + e) * TY + t] = v[e];
+    for (int e = 0; e < LB; ++e) out[(cl * PX + blk * LB + e) * TY + t] = v[e];
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 3 * TY * LB; i += blockDim.x) {
+  for (int i = threadIdx.x; i < NC * TY * LB; i += blockDim.x) {
     const int t = i % TY;
     const int r = i / TY;
-    const int n1 = r % LB, c = r / LB;
+    const int n1 = r % LB, cl = r / LB;
     C v[2 * RA], lo[RA];
 #pragma unroll
     for (int bb = 0; bb < 2; ++bb)
 #pragma unroll
-      for (int k = 0; k < RA; ++k) v[bb * RA + k] = out[(c * PX + bb * H + n1 + LB * k) * TY + t];
+      for (int k = 0; k < RA; ++k) v[bb * RA + k] = out[(cl * PX + bb * H + n1 + LB * k) * TY + t];
     f2::passA_inv<PX, false>(v, n1, tw, lo, (C*)nullptr);
-    C* dst = in + (c * TY + t) * ip;
+    C* dst = in + (cl * TY + t) * ip;
 #pragma unroll
     for (int j = 0; j < RA; ++j) {
       const int xx = n1 + LB * j;
@@ -185,20 +191,21 @@ __global__ void __launch_bounds__(256) k_x_inv(Geom g, MvData<C> d, const C* __r
   }
   __syncthreads();
   const C* ia = d.ia + (int64_t)(rhs0 + b) * g.ncomp * 3;
-  const int nst = 3 * TY * g.nx;
+  const int nst = NC * TY * g.nx;
   for (int i = threadIdx.x; i < nst; i += blockDim.x) {
     const int x = i % g.nx;
     const int r = i / g.nx;
-    const int t = r % TY, c = r / TY;
+    const int t = r % TY, cl = r / TY;
     const int y = y0 + t;
     if (y >= g.ny) continue;
     const int32_t idx = __ldg(d.map + ((int64_t)z * g.ny + y) * g.nx + x);
     if (idx < 0) continue;
+    const int c = c0 + cl;
     const int64_t o = ((int64_t)b * 3 + c) * g.n + idx;
     const int cc = d.comp ? d.comp[idx] : 0;
     C pv = p[o];
     if (conj) pv = conjc(pv);
-    const C res = cadd(in[(c * TY + t) * ip + x], cmul(ia[cc * 3 + c], pv));
+    const C res = cadd(in[(cl * TY + t) * ip + x], cmul(ia[cc * 3 + c], pv));
     ap[o] = conj ? conjc(res) : res;
   }
 }
@@ -626,7 +633,12 @@ inline int x_ty_rt(size_t csize, int px) { return csize == 8 ? (px <= 128 ? 16 :
 inline bool x_ty_valid(size_t csize, int px, int ty) {
   return ty == x_ty_rt(csize, px) || ty == 4 || (ty == 8 && x_ty_rt(csize, px) > 8);
 }
+// the one-component variant (each CTA transforms one of the three components) has this tile height
+template <typename C> constexpr int x_nc1_ty() { return sizeof(C) == 8 ? 16 : 8; }
+inline int x_nc1_ty_rt(size_t csize) { return csize == 8 ? 16 : 8; }
+inline int x_nc_pick(const MvTune& t) { return t.xnc == 1 ? 1 : 3; }
 inline int x_ty_pick(const MvTune& t, size_t csize, int px) {
+  if (x_nc_pick(t) == 1) return x_nc1_ty_rt(csize);
   return (t.xty > 0 && x_ty_valid(csize, px, t.xty)) ? t.xty : x_ty_rt(csize, px);
 }
 
@@ -638,9 +650,9 @@ constexpr int zcols_g_rt(size_t csize, int pz) {
 inline int odd_pitch(int n) { return (n % 2) ? n : n + 1; }
 
 template <typename C>
-size_t x_fast_smem(const Geom& g, int TY = 0) {
+size_t x_fast_smem(const Geom& g, int TY = 0, int NC = 3) {
   if (TY <= 0) TY = x_ty_rt(sizeof(C), g.px);
-  return sizeof(C) * ((size_t)g.px + (size_t)3 * TY * odd_pitch(g.nx) + (size_t)3 * g.px * TY);
+  return sizeof(C) * ((size_t)g.px + (size_t)NC * TY * odd_pitch(g.nx) + (size_t)NC * g.px * TY);
 }
 template <typename C>
 size_t plane_fast_smem(const Geom& g) {
@@ -661,16 +673,22 @@ size_t zcols_fast_smem(const Geom& g) {
   return sizeof(C) * ((size_t)g.pz + (size_t)g.pz * 3 * zcols_g_rt(sizeof(C), g.pz));
 }
 
-// k_x_fwd / k_x_inv for the tile height TY chosen at run time (the default or 4 / 8)
+// k_x_fwd / k_x_inv for the variant chosen at run time: three components per CTA with tile
+// height TY (the default, 4 or 8), or one component per CTA with the one-component height
 template <typename C, int L_, typename F>
-Err with_ty(int ty, F&& f) {
+Err with_x(int nc, int ty, F&& f) {
   constexpr int D = x_ty<C, L_>();
-  if (ty == D) return f(std::integral_constant<int, D>{});
+  using I3 = std::integral_constant<int, 3>;
+  if (nc == 1) {
+    if (ty == x_nc1_ty<C>()) return f(std::integral_constant<int, x_nc1_ty<C>()>{}, std::integral_constant<int, 1>{});
+    return Err::make(DDA_EUNSUPPORTED, "x tile height not instantiated");
+  }
+  if (ty == D) return f(std::integral_constant<int, D>{}, I3{});
   if constexpr (D != 4) {
-    if (ty == 4) return f(std::integral_constant<int, 4>{});
+    if (ty == 4) return f(std::integral_constant<int, 4>{}, I3{});
   }
   if constexpr (D > 8) {
-    if (ty == 8) return f(std::integral_constant<int, 8>{});
+    if (ty == 8) return f(std::integral_constant<int, 8>{}, I3{});
   }
   return Err::make(DDA_EUNSUPPORTED, "x tile height not instantiated");
 }
@@ -678,17 +696,18 @@ Err with_ty(int ty, F&& f) {
 template <typename C>
 Err launch_x_fwd(const Geom& g, const MvData<C>& d, const MvTune& t, const C* p, int nrhs, bool conj,
                  cudaStream_t st) {
+  const int NC = x_nc_pick(t);
   const int TY = x_ty_pick(t, sizeof(C), g.px);
-  const size_t sm = x_fast_smem<C>(g, TY);
-  const dim3 grid((g.ny + TY - 1) / TY, g.nz, nrhs);
+  const size_t sm = x_fast_smem<C>(g, TY, NC);
+  const dim3 grid((g.ny + TY - 1) / TY, g.nz, nrhs * (3 / NC));
   const int ip = odd_pitch(g.nx);
   switch (g.px) {
-#define DDA_CASE(L_)                                                                      \
-  case L_:                                                                                \
-    DDA_TRY((with_ty<C, L_>(TY, [&](auto tyc) {                                         \
-      k_x_fwd<C, L_, decltype(tyc)::value><<<grid, 256, sm, st>>>(g, d, p, conj, ip);     \
-      return Err::Ok();                                                                   \
-    })));                                                                                 \
+#define DDA_CASE(L_)                                                                                    \
+  case L_:                                                                                              \
+    DDA_TRY((with_x<C, L_>(NC, TY, [&](auto tyc, auto ncc) {                                          \
+      k_x_fwd<C, L_, decltype(tyc)::value, decltype(ncc)::value><<<grid, 256, sm, st>>>(g, d, p, conj, ip); \
+      return Err::Ok();                                                                                 \
+    })));                                                                                               \
     break;
     DDA_FAST_LENGTHS(DDA_CASE)
 #undef DDA_CASE
@@ -701,17 +720,19 @@ Err launch_x_fwd(const Geom& g, const MvData<C>& d, const MvTune& t, const C* p,
 template <typename C>
 Err launch_x_inv(const Geom& g, const MvData<C>& d, const MvTune& t, const C* p, C* ap, int nrhs, int rhs0,
                  bool conj, cudaStream_t st) {
+  const int NC = x_nc_pick(t);
   const int TY = x_ty_pick(t, sizeof(C), g.px);
-  const size_t sm = x_fast_smem<C>(g, TY);
-  const dim3 grid((g.ny + TY - 1) / TY, g.nz, nrhs);
+  const size_t sm = x_fast_smem<C>(g, TY, NC);
+  const dim3 grid((g.ny + TY - 1) / TY, g.nz, nrhs * (3 / NC));
   const int ip = odd_pitch(g.nx);
   switch (g.px) {
-#define DDA_CASE(L_)                                                                            \
-  case L_:                                                                                      \
-    DDA_TRY((with_ty<C, L_>(TY, [&](auto tyc) {                                               \
-      k_x_inv<C, L_, decltype(tyc)::value><<<grid, 256, sm, st>>>(g, d, p, ap, rhs0, conj, ip);  \
-      return Err::Ok();                                                                         \
-    })));                                                                                       \
+#define DDA_CASE(L_)                                                                                         \
+  case L_:                                                                                                   \
+    DDA_TRY((with_x<C, L_>(NC, TY, [&](auto tyc, auto ncc) {                                               \
+      k_x_inv<C, L_, decltype(tyc)::value, decltype(ncc)::value><<<grid, 256, sm, st>>>(g, d, p, ap, rhs0, conj, \
+                                                                                        ip);                 \
+      return Err::Ok();                                                                                      \
+    })));                                                                                                    \
     break;
     DDA_FAST_LENGTHS(DDA_CASE)
 #undef DDA_CASE
@@ -789,6 +810,8 @@ void optin_x(int smax) {
     optin_smem(k_x_fwd<C, L_, 8>, smax);
     optin_smem(k_x_inv<C, L_, 8>, smax);
   }
+  optin_smem(k_x_fwd<C, L_, x_nc1_ty<C>(), 1>, smax);
+  optin_smem(k_x_inv<C, L_, x_nc1_ty<C>(), 1>, smax);
 }
 
 // Opt every instantiation of this precision into the device's maximum dynamic shared memory.

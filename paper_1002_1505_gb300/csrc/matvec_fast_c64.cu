@@ -37,6 +37,7 @@ Err selftest_bulk_wait(int* gave_up) {
 
 int x_tile_height_default(size_t csize, int px) { return fast::x_ty_rt(csize, px); }
 bool x_tile_height_ok(size_t csize, int px, int ty) { return fast::x_ty_valid(csize, px, ty); }
+int x_tile_height_one_component(size_t csize) { return fast::x_nc1_ty_rt(csize); }
 
 void choose_fast_schedule(const Geom& g, bool c64, int smax, MvTune* t) {
   t->fast = fast::fast_length(g.px) && fast::fast_length(g.py) && fast::fast_length(g.pz);

@@ -424,8 +424,8 @@ def dda_profile_matvec(ctx: "Context", nrhs: int, dtype: int = DDA_C64, iters: i
 
 
 def dda_schedule_info(ctx: "Context", dtype: int = DDA_C64):
-    """(passes, fast, plane_threads, tuned_nrhs, ctas_per_plane, x_tile_rows, bulk_staged) of the product's schedule."""
-    info = np.zeros(7, dtype=np.int32)
+    """(passes, fast, plane_threads, tuned_nrhs, ctas_per_plane, x_tile_rows, bulk_staged, x_components_per_cta)."""
+    info = np.zeros(8, dtype=np.int32)
     ctx._check(LIB.dda_schedule_info(ctx._h, int(dtype), _ptr(info)))
     return tuple(int(v) for v in info)
 

@@ -146,6 +146,26 @@ def test_bulk_staged_plane_matches_direct_sum(D, monkeypatch, w, pad):
         assert err <= 1e-5, (w.name, b, err)
 
 
+@pytest.mark.parametrize("w,pad", FAST_PADS, ids=[w.name for w, _ in FAST_PADS])
+def test_x_one_component_per_cta_matches_direct_sum(D, monkeypatch, w, pad):
+    """The x passes with one field component per CTA, both precisions."""
+    monkeypatch.setenv("DDA_XCOMP", "1")
+    ctx = _ctx(D, w, pad)
+    prob = _oracle_problem(w)
+    assert D.dda_schedule_info(ctx, D.DDA_C64)[7] in (0, 1)
+    for dt, tol in ((torch.complex128, 1e-12), (torch.complex64, 1e-5)):
+        p = _rand_p(ctx.nrhs, ctx.n, 29, dt)
+        ap = torch.empty_like(p)
+        ctx.dda_matvec(p, ap)
+        torch.cuda.synchronize()
+        pn = p.cpu().numpy().astype(np.complex128)
+        got = ap.cpu().numpy().astype(np.complex128)
+        for b in range(ctx.nrhs):
+            ref = odda.apply_a(prob, b, pn[b], "direct")
+            err = np.linalg.norm(got[b] - ref) / np.linalg.norm(ref)
+            assert err <= tol, (w.name, dt, b, err)
+
+
 @pytest.mark.parametrize("xtile", ["4", "8"])
 @pytest.mark.parametrize("w,pad", FAST_PADS, ids=[w.name for w, _ in FAST_PADS])
 def test_x_tile_heights_match_direct_sum(D, monkeypatch, w, pad, xtile):

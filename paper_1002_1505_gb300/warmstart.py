@@ -149,14 +149,17 @@ def residual_of_guess(ctxs, grid, ys=None) -> float:
     return tot / cnt
 
 
-def warm_guess(ctx: "D.Context", net: "D.UNet", grid=None):
-    """Initial guess P0 (complex128 [nrhs, 3, N]) for a context from the network."""
+def warm_guess(ctx: "D.Context", net: "D.UNet", grid=None, chunk: int = 0):
+    """Initial guess P0 (complex128 [nrhs, 3, N]) for a context from the network (forward pass in
+    chunks of `chunk` right-hand sides when > 0, to bound the activations of large grids)."""
     import torch
     grid = grid_dims(ctx.box) if grid is None else grid
     x = torch.zeros((ctx.nrhs, grid[2], grid[1], grid[0], CIN), dtype=torch.float32, device="cuda")
     y = torch.empty((ctx.nrhs, grid[2], grid[1], grid[0], COUT), dtype=torch.float32, device="cuda")
     D.dda_unet_features(ctx, x, grid)
-    net.dda_unet_forward(x, y, grid)
+    step = chunk if chunk > 0 else ctx.nrhs
+    for b0 in range(0, ctx.nrhs, step):
+        net.dda_unet_forward(x[b0:b0 + step].contiguous(), y[b0:b0 + step], grid)
     p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
     D.dda_unet_warm_start(ctx, y, grid, p, residual=True)
     return p
@@ -194,3 +197,76 @@ def evaluate(net: "D.UNet", indices, max_box: int, grid=None, tol: float = 1e-5)
         rows.append(out)
         ctx.close()
     return rows
+
+
+def main():
+    """Config-4-style evaluation: train on solver output, compare iterations to 1e-5 on held-out problems
+    (cold start, alpha E_inc, network) and, with --large, on the 160 x 128 hexagonal prism."""
+    import argparse
+    import json
+    import time
+
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train-problems", type=int, default=8192)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--max-box", type=int, default=16)
+    ap.add_argument("--heldout", type=int, default=32)
+    ap.add_argument("--large", action="store_true")
+    args = ap.parse_args()
+    grid = (args.max_box, args.max_box, args.max_box)
+    t0 = time.time()
+    X, T, M, _ = generate(list(range(args.train_problems)), args.max_box, grid)
+    torch.cuda.synchronize()
+    t_gen = time.time() - t0
+    m = M[..., None]
+    mse0 = float((m * T * T).sum() / (m.sum() * COUT))
+    net = D.UNet(0, None, CIN, COUT, (16, 32, 48, 64), seed=5)
+    zero_head(net)
+    t0 = time.time()
+    hist = train(net, X, T, M, grid, steps=args.steps, batch=16, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    del X, T, M
+    rows = evaluate(net, list(range(100000, 100000 + args.heldout)), args.max_box, grid)
+    out = {"train_samples": 2 * args.train_problems, "max_box": args.max_box, "steps": args.steps,
+           "params": int(net.nparams),
+           "generate_s": round(t_gen, 1), "train_s": round(t_train, 1),
+           "mse_no_network": mse0, "mse_final": float(np.mean(hist[-200:])),
+           "heldout_problems": args.heldout,
+           "heldout_iterations": {k: int(sum(r[k][0] for r in rows)) for k in ("cold", "alpha_einc", "network")},
+           "heldout_max_resid": {k: float(max(r[k][1] for r in rows)) for k in ("cold", "alpha_einc", "network")}}
+    if args.large:
+        w = W.HEXPRISM160
+        ctx = D.Context(0)
+        D.setup_workload(ctx, w)
+        big = grid_dims(ctx.box)
+        # autotune the product schedules before any timed solve
+        D.dda_profile_matvec(ctx, ctx.nrhs, D.DDA_C64, 1)
+        D.dda_profile_matvec(ctx, ctx.nrhs, D.DDA_C128, 1)
+        res = {}
+        for name in ("cold", "alpha_einc", "network"):
+            torch.cuda.synchronize()
+            t0 = time.time()
+            if name == "cold":
+                p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
+                warm = False
+            elif name == "alpha_einc":
+                p, warm = local_field_guess(ctx, big), True
+            else:
+                p, warm = warm_guess(ctx, net, big, chunk=2), True
+            torch.cuda.synchronize()
+            t_guess = time.time() - t0
+            t0 = time.time()
+            reps, _ = ctx.dda_solve(p, precision="MIXED", tol=1e-5, maxit=3000, warm_start=warm)
+            torch.cuda.synchronize()
+            res[name] = {"iterations": int(sum(r["iters"] for r in reps)), "solve_s": round(time.time() - t0, 3),
+                         "guess_s": round(t_guess, 3), "max_resid": float(max(r["true_rel_resid"] for r in reps))}
+            del p
+        out["hexprism160"] = {"grid": list(big), "nrhs": ctx.nrhs, **res}
+        ctx.close()
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1291,8 +1291,10 @@ dda_status dda_cross_sections(dda_ctx* c, const void* p_dev, double* q_out, cons
       rb.part = c->d_part;
       e = ensure_small(c, sizeof(double) * 3 * nrhs);
       if (!e.ok()) return fail(c, e);
-      e = dda::qsums(c->d_ijk, c->d_comp, c->d_origin, c->d_rg, c->d_ia128, c->ncomp, k, P, nrhs, c->n, c->d_small, rb,
-                     c->stream);
+      e = ensure_einc(c);
+      if (e.ok())
+        e = dda::qsums(c->comp_valid ? c->d_comp : nullptr, c->d_e128, c->d_ia128, c->ncomp, k, P, nrhs, c->n,
+                       c->d_small, rb, c->stream);
       if (!e.ok()) return fail(c, e);
       cudaMemcpyAsync(c->h_pinned, c->d_small, sizeof(double) * 3 * nrhs, cudaMemcpyDeviceToHost, c->stream);
       if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, Err::make(DDA_ECUDA, "q sums failed"));
@@ -1331,8 +1333,9 @@ dda_status dda_cross_sections(dda_ctx* c, const void* p_dev, double* q_out, cons
       double2* d_F = c->d_F;
       if (e.ok()) {
         cudaMemcpy(c->d_nh, nh.data(), sizeof(double) * nh.size(), cudaMemcpyHostToDevice);
-        e = dda::farfield(c->d_ijk, c->d_origin, c->d_nh, k, P, nrhs, ndir, c->n, d_F, (double2*)c->d_fpart, nblk,
-                          c->stream);
+        const int box[3] = {c->tgt.box[0], c->tgt.box[1], c->tgt.box[2]};
+        e = dda::farfield(c->d_ijk, c->d_origin, c->d_nh, k, P, nrhs, ndir, c->n, box, d_F, (double2*)c->d_fpart,
+                          nblk, c->stream);
       }
       std::vector<double2> F((size_t)nrhs * ndir * 3);
       if (e.ok()) {

@@ -254,11 +254,11 @@ template <typename C>
 Err incident_field(const int32_t* ijk, const double* origin3, const RhsGeom* rg, int nrhs, int64_t n, C* e,
                    cudaStream_t st);
 // per RHS: [0] sum Im(E*.P), [1] sum Re(E*.P), [2] sum (-Im ia - 2/3 k^3)|P|^2
-Err qsums(const int32_t* ijk, const uint8_t* comp, const double* origin3, const RhsGeom* rg, const double2* ia,
-          int ncomp, double kd, const double2* p, int nrhs, int64_t n, double* out3, RedBuf rb, cudaStream_t st);
+Err qsums(const uint8_t* comp, const double2* einc /*[nrhs][3][N]*/, const double2* ia, int ncomp, double kd,
+          const double2* p, int nrhs, int64_t n, double* out3, RedBuf rb, cudaStream_t st);
 // F[rhs][dir][3] = sum_j P_j exp(-i kd n_dir . r_j); ndirs directions per RHS (nhat given per RHS, TF)
 Err farfield(const int32_t* ijk, const double* origin3, const double* nhat /*[nrhs][ndir][3]*/, double kd,
-             const double2* p, int nrhs, int ndir, int64_t n, double2* out, double2* part, int nblk,
+             const double2* p, int nrhs, int ndir, int64_t n, const int box[3], double2* out, double2* part, int nblk,
              cudaStream_t st);
 // Far field F = sum_j P_j exp(-i k n.r_j) for many directions (nhat [nrhs][ndir][3] in TF) from
 // separable FP32 phase tables (tab: nrhs*ndir*(box sum) float2; part: nrhs*ceil(ndir/8)*nblk*48

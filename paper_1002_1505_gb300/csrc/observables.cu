@@ -3,7 +3,7 @@
 // E_inc,j = e exp(i k . r_j) (guide, "Incident Polarization State"; plane wave
 // along x_LF, expressed in the Target Frame), phase in FP64.
 // Efficiency sums (Draine 1988, the formulas behind the guide's Q_ext, Q_abs,
-// Q_pha), per RHS, FP64 accumulation:
+// Q_pha), per RHS, FP64 accumulation, from the cached incident field:
 //   S_ext = sum_j Im(E_j^* . P_j),  S_pha = sum_j Re(E_j^* . P_j),
 //   S_abs = sum_j sum_a (-Im(alpha^{-1}_aa) - (2/3) k^3) |P_ja|^2
 // (the host scales them by 4 pi k, 2 pi k and 4 pi k and divides by pi a_eff^2).
@@ -60,23 +60,19 @@ __device__ __forceinline__ void bred(double (&v)[NS], double* out) {
   }
 }
 
-__global__ void k_qsum(const int32_t* ijk, const uint8_t* comp, const double* org, const RhsGeom* rg,
-                       const double2* ia, int ncomp, double kd, const double2* p, int64_t n, double* part) {
+// efficiency sums from the cached incident field e [nrhs][3][N]
+__global__ void k_qsum(const uint8_t* comp, const double2* __restrict__ e, const double2* ia, int ncomp, double kd,
+                       const double2* p, int64_t n, double* part) {
   const int b = blockIdx.y;
-  const RhsGeom g = rg[b];
   const double rr = (2.0 / 3.0) * kd * kd * kd;
   double acc[3] = {0.0, 0.0, 0.0};
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-    const double rx = ijk[3 * j] + org[0], ry = ijk[3 * j + 1] + org[1], rz = ijk[3 * j + 2] + org[2];
-    double sn, cs;
-    sincos(g.k[0] * rx + g.k[1] * ry + g.k[2] * rz, &sn, &cs);
     const int cc = comp ? comp[j] : 0;
     for (int c = 0; c < 3; ++c) {
-      const double er = g.e[2 * c], ei = g.e[2 * c + 1];
-      const double Er = er * cs - ei * sn, Ei = er * sn + ei * cs;
+      const double2 ev = e[((int64_t)b * 3 + c) * n + j];
       const double2 pv = p[((int64_t)b * 3 + c) * n + j];
       // conj(E) * P
-      const double re = Er * pv.x + Ei * pv.y, im = Er * pv.y - Ei * pv.x;
+      const double re = ev.x * pv.x + ev.y * pv.y, im = ev.x * pv.y - ev.y * pv.x;
       acc[0] += im;
       acc[1] += re;
       const double2 a = ia[((int64_t)b * ncomp + cc) * 3 + c];
@@ -98,17 +94,29 @@ __global__ void k_qsum_fin(const double* part, int nblk, double* out3) {
     for (int s = 0; s < 3; ++s) out3[3 * b + s] = res[s];
 }
 
-// grid (nblk, ndir, nrhs): partial sums of P_j exp(-i k n.r_j) -> part[rhs][dir][blk][6]
+// grid (nblk, ndir, nrhs): partial sums of P_j exp(-i k n.r_j) -> part[rhs][dir][blk][6], FP64.
+// The phase factorises over the lattice axes, so each CTA first tabulates
+// exp(-i k n_a (i + origin_a)) for its direction (box sum entries), then needs two
+// complex products per site instead of a sine and cosine.
 __global__ void k_far(const int32_t* ijk, const double* org, const double* nhat, double kd, const double2* p,
-                      int ndir, int64_t n, double* part) {
+                      int ndir, int64_t n, int bx, int by, int bz, double* part) {
+  extern __shared__ double2 ftab[];
   const int d = blockIdx.y, b = blockIdx.z;
   const double* nh = nhat + ((int64_t)b * ndir + d) * 3;
-  const double kx = kd * nh[0], ky = kd * nh[1], kz = kd * nh[2];
+  const int nt = bx + by + bz;
+  for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+    const int a = i < bx ? 0 : (i < bx + by ? 1 : 2);
+    const int ii = a == 0 ? i : (a == 1 ? i - bx : i - bx - by);
+    double sn, cs;
+    sincos(-kd * nh[a] * ((double)ii + org[a]), &sn, &cs);
+    ftab[i] = make_double2(cs, sn);
+  }
+  __syncthreads();
   double acc[6] = {0, 0, 0, 0, 0, 0};
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-    const double rx = ijk[3 * j] + org[0], ry = ijk[3 * j + 1] + org[1], rz = ijk[3 * j + 2] + org[2];
-    double sn, cs;
-    sincos(-(kx * rx + ky * ry + kz * rz), &sn, &cs);
+    const double2 tx = ftab[ijk[3 * j]], ty = ftab[bx + ijk[3 * j + 1]], tz = ftab[bx + by + ijk[3 * j + 2]];
+    const double2 txy = make_double2(tx.x * ty.x - tx.y * ty.y, tx.x * ty.y + tx.y * ty.x);
+    const double cs = txy.x * tz.x - txy.y * tz.y, sn = txy.x * tz.y + txy.y * tz.x;
     for (int c = 0; c < 3; ++c) {
       const double2 pv = p[((int64_t)b * 3 + c) * n + j];
       acc[2 * c] += pv.x * cs - pv.y * sn;
@@ -253,9 +261,9 @@ template Err incident_field<float2>(const int32_t*, const double*, const RhsGeom
 template Err incident_field<double2>(const int32_t*, const double*, const RhsGeom*, int, int64_t, double2*,
                                      cudaStream_t);
 
-Err qsums(const int32_t* ijk, const uint8_t* comp, const double* origin3, const RhsGeom* rg, const double2* ia,
-          int ncomp, double kd, const double2* p, int nrhs, int64_t n, double* out3, RedBuf rb, cudaStream_t st) {
-  k_qsum<<<dim3(rb.nblk, nrhs), kT, 0, st>>>(ijk, comp, origin3, rg, ia, ncomp, kd, p, n, rb.part);
+Err qsums(const uint8_t* comp, const double2* einc, const double2* ia, int ncomp, double kd, const double2* p,
+          int nrhs, int64_t n, double* out3, RedBuf rb, cudaStream_t st) {
+  k_qsum<<<dim3(rb.nblk, nrhs), kT, 0, st>>>(comp, einc, ia, ncomp, kd, p, n, rb.part);
   DDA_CU(cudaGetLastError());
   add_launches(1);
   k_qsum_fin<<<nrhs, kT, 0, st>>>(rb.part, rb.nblk, out3);
@@ -265,9 +273,11 @@ Err qsums(const int32_t* ijk, const uint8_t* comp, const double* origin3, const 
 }
 
 Err farfield(const int32_t* ijk, const double* origin3, const double* nhat, double kd, const double2* p, int nrhs,
-             int ndir, int64_t n, double2* out, double2* part, int nblk, cudaStream_t st) {
+             int ndir, int64_t n, const int box[3], double2* out, double2* part, int nblk, cudaStream_t st) {
   double* pd = reinterpret_cast<double*>(part);
-  k_far<<<dim3(nblk, ndir, nrhs), kT, 0, st>>>(ijk, origin3, nhat, kd, p, ndir, n, pd);
+  const size_t sm = sizeof(double2) * (size_t)(box[0] + box[1] + box[2]);
+  if (sm > 48 * 1024) return Err::make(DDA_EUNSUPPORTED, "target box too long for the far-field phase tables");
+  k_far<<<dim3(nblk, ndir, nrhs), kT, sm, st>>>(ijk, origin3, nhat, kd, p, ndir, n, box[0], box[1], box[2], pd);
   DDA_CU(cudaGetLastError());
   add_launches(1);
   k_far_fin<<<nrhs * ndir, kT, 0, st>>>(pd, nblk, out);

@@ -36,6 +36,9 @@ struct dda_ctx {
   int32_t* d_ijk = nullptr;
   uint8_t* d_comp = nullptr;
   double* d_origin = nullptr;
+  int tw_len[3] = {0, 0, 0};          // padded lengths the twiddle tables were built for
+  int32_t* d_gperm = nullptr;         // storage <-> natural frequency tables of the Green build
+  int gperm_key[2] = {0, 0};          // (px, py) they were built for
 
   // incident
   bool have_inc = false;
@@ -881,10 +884,11 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
     if (e.ok()) e = dda::make_plan(g.py, &g.ply);
     if (e.ok()) e = dda::make_plan(g.pz, &g.plz);
     if (!e.ok()) return fail(c, e);
-    // twiddles exp(-2 pi i j / L) in FP64 on the host
+    // twiddles exp(-2 pi i j / L) in FP64 on the host (kept while the padded lengths stay the same)
     const double pi = 3.14159265358979323846;
     for (int a = 0; a < 3; ++a) {
       const int L = P[a];
+      if (c->tw_len[a] == L && c->d_tw128[a] && c->d_tw64[a]) continue;
       std::vector<double2> t128(L);
       std::vector<float2> t64(L);
       for (int j = 0; j < L; ++j) {
@@ -897,6 +901,7 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
       if (!e.ok()) return fail(c, e);
       cudaMemcpy(c->d_tw128[a], t128.data(), sizeof(double2) * L, cudaMemcpyHostToDevice);
       cudaMemcpy(c->d_tw64[a], t64.data(), sizeof(float2) * L, cudaMemcpyHostToDevice);
+      c->tw_len[a] = L;
     }
     // schedule: 3-pass when the plane fits in the opt-in shared memory
     int smax = 0;
@@ -962,8 +967,19 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
     if (e.ok()) e = grow(c, &c->d_ghat64, sizeof(float2) * 6 * M);
     if (e.ok()) e = grow(c, &c->d_gscratch, sizeof(double2) * 6 * M);
     if (!e.ok()) return fail(c, e);
-    e = dda::build_green(g64, c->kd, c->d_tw128[0], c->d_tw128[1], c->d_tw128[2], c->d_gscratch, c->d_ghat128,
-                         c->d_ghat64, c->stream);
+    // frequency-order tables of the Green build (kept while px, py stay the same)
+    if (e.ok() && (c->gperm_key[0] != g.px || c->gperm_key[1] != g.py || !c->d_gperm)) {
+      std::vector<int32_t> tab;
+      dda::green_perm_tables(g64, &tab);
+      e = grow(c, &c->d_gperm, sizeof(int32_t) * tab.size());
+      if (e.ok() && cudaMemcpy(c->d_gperm, tab.data(), sizeof(int32_t) * tab.size(), cudaMemcpyHostToDevice) !=
+                        cudaSuccess)
+        e = Err::make(DDA_ECUDA, "Green-table upload failed");
+      if (e.ok()) { c->gperm_key[0] = g.px; c->gperm_key[1] = g.py; }
+    }
+    if (!e.ok()) return fail(c, e);
+    e = dda::build_green(g64, c->kd, c->d_tw128[0], c->d_tw128[1], c->d_tw128[2], c->d_gperm, c->d_gscratch,
+                         c->d_ghat128, c->d_ghat64, c->stream);
     if (!e.ok()) return fail(c, e);
     c->have_green = true;
     return DDA_OK;

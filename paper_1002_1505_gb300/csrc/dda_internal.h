@@ -157,8 +157,10 @@ constexpr size_t kNoAllocScratchBytes = 32ull << 20;
 Err noalloc_scratch(int device, void** out);
 
 // Green tensor: fill + FP64 FFT + pack into ghat128 / ghat64.
-Err build_green(const Geom& g, double kd, const double2* tw128x, const double2* tw128y, const double2* tw128z,
-                double2* scratch, double2* ghat128, float2* ghat64, cudaStream_t st);
+// storage <-> natural frequency tables the Green build needs (natx[px] | naty[py] | stx[px/2+1] | sty[py/2+1])
+void green_perm_tables(const Geom& g, std::vector<int32_t>* out);
+Err build_green(const Geom& g, double kd, const double2* twx, const double2* twy, const double2* twz,
+                const int32_t* perm, double2* gw, double2* ghat128, float2* ghat64, cudaStream_t st);
 
 // Generic batched FFT over rows/strides (used by tests of the engine and the Green build).
 template <typename C>

@@ -305,8 +305,9 @@ __global__ void k_fft_strided(C* data, int64_t estride, int64_t ninner, int64_t 
 // diagonal components even in all three.  Its zero-padded DFT inherits the same parity per
 // axis, so the FP64 build fills and transforms only what the parities do not determine:
 // the x transforms run on the rows with y <= Py/2, z <= Pz/2, the y transforms on the
-// planes with z <= Pz/2, and the missing halves are mirrored in between (7/12 of the FFT
-// work of a plain 3-D transform, 1/4 of the fill).
+// planes z <= Pz/2 for natural kx <= Px/2, the z transforms on natural kx <= Px/2,
+// ky <= Py/2, and the missing parts are mirrored in between and in the final pack (1/4 of
+// the FFT work and of the fill of a plain 3-D transform).
 __device__ __forceinline__ bool odd_in(int c, int axis) {
   // bit a of the mask = odd in axis a (0 = x, 1 = y, 2 = z)
   const int mask[6] = {0, 3, 5, 0, 6, 0};
@@ -352,44 +353,56 @@ __global__ void k_green_fill_q(Geom g, double kd, double2* q) {
   }
 }
 
-// t[c][zq][y][kx] (all y) from q[c][zq][yq][kx]: rows y > Py/2 mirror Py - y with the y parity
-__global__ void k_green_expand_y(Geom g, const double2* __restrict__ q, double2* __restrict__ t) {
-  const int hy1 = g.py / 2 + 1, hz1 = g.pz / 2 + 1;
-  const int64_t Q = (int64_t)g.px * hy1 * hz1, T = (int64_t)g.px * g.py * hz1;
+// After the x transform only the natural frequencies kx <= Px/2 are carried on (the others
+// follow by the x parity); the spectra are in the engine's digit-reversed storage order, so
+// the host passes the storage position stx[k] of natural frequency k and, for the final
+// pack, the natural frequency natx[s] of storage position s (likewise for y).
+// t[c][zq][y][k] (all y, k <= Px/2) from q[c][zq][yq][stx[k]]: rows y > Py/2 mirror Py - y
+__global__ void k_green_expand_y(Geom g, const int32_t* __restrict__ stx, const double2* __restrict__ q,
+                                 double2* __restrict__ t) {
+  const int hx1 = g.px / 2 + 1, hy1 = g.py / 2 + 1, hz1 = g.pz / 2 + 1;
+  const int64_t Q = (int64_t)g.px * hy1 * hz1, T = (int64_t)hx1 * g.py * hz1;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < 6 * T; o += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(o / T);
     const int64_t i = o - c * T;
-    const int kx = (int)(i % g.px);
-    const int64_t rest = i / g.px;
+    const int k = (int)(i % hx1);
+    const int64_t rest = i / hx1;
     const int y = (int)(rest % g.py), z = (int)(rest / g.py);
     const bool mir = y > g.py / 2;
     const int ys = mir ? g.py - y : y;
-    double2 v = q[(int64_t)c * Q + ((int64_t)z * hy1 + ys) * g.px + kx];
+    double2 v = q[(int64_t)c * Q + ((int64_t)z * hy1 + ys) * g.px + stx[k]];
     if (mir && odd_in(c, 1)) v = make_double2(-v.x, -v.y);
     t[o] = v;
   }
 }
 
-// f[c][z][ky][kx] (all z) from t[c][zq][ky][kx]: planes z > Pz/2 mirror Pz - z with the z parity
-__global__ void k_green_expand_z(Geom g, const double2* __restrict__ t, double2* __restrict__ f) {
-  const int hz1 = g.pz / 2 + 1;
-  const int64_t P = (int64_t)g.px * g.py, M = P * g.pz, T = P * hz1;
-  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < 6 * M; o += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(o / M);
-    const int64_t i = o - c * M;
+// f[c][z][ky][kx] (all z; natural ky <= Py/2, kx <= Px/2) from t[c][zq][sty[ky]][kx]:
+// planes z > Pz/2 mirror Pz - z with the z parity
+__global__ void k_green_expand_z(Geom g, const int32_t* __restrict__ sty, const double2* __restrict__ t,
+                                 double2* __restrict__ f) {
+  const int hx1 = g.px / 2 + 1, hy1 = g.py / 2 + 1, hz1 = g.pz / 2 + 1;
+  const int64_t T = (int64_t)hx1 * g.py * hz1, P = (int64_t)hx1 * hy1, F = P * g.pz;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < 6 * F; o += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(o / F);
+    const int64_t i = o - c * F;
     const int z = (int)(i / P);
-    const int64_t xy = i - (int64_t)z * P;
+    const int64_t r = i - (int64_t)z * P;
+    const int ky = (int)(r / hx1), kx = (int)(r - (int64_t)ky * hx1);
     const bool mir = z > g.pz / 2;
     const int zs = mir ? g.pz - z : z;
-    double2 v = t[(int64_t)c * T + (int64_t)zs * P + xy];
+    double2 v = t[(int64_t)c * T + ((int64_t)zs * g.py + sty[ky]) * hx1 + kx];
     if (mir && odd_in(c, 2)) v = make_double2(-v.x, -v.y);
     f[o] = v;
   }
 }
 
-// ghat[kx][kz][ky][6] = Gw[c][kz][ky][kx] / M (positions = the engine's spectral order)
-__global__ void k_green_pack(Geom g, const double2* gw, double2* g128, float2* g64) {
+// ghat[kx][kz][ky][6] (storage positions) = f[c][kz][ky'][kx'] / M, with kx', ky' the natural
+// frequencies folded into [0, P/2] and the sign of the parities of the folds
+__global__ void k_green_pack(Geom g, const int32_t* __restrict__ natx, const int32_t* __restrict__ naty,
+                             const double2* __restrict__ f, double2* __restrict__ g128, float2* __restrict__ g64) {
   const int64_t M = (int64_t)g.px * g.py * g.pz;
+  const int hx1 = g.px / 2 + 1, hy1 = g.py / 2 + 1;
+  const int64_t P = (int64_t)hx1 * hy1, F = P * g.pz;
   const double inv = 1.0 / (double)M;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < 6 * M; o += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(o % 6);
@@ -397,11 +410,31 @@ __global__ void k_green_pack(Geom g, const double2* gw, double2* g128, float2* g
     const int ky = (int)(pt % g.py);
     const int64_t rest = pt / g.py;
     const int kz = (int)(rest % g.pz), kx = (int)(rest / g.pz);
-    const double2 v = gw[(int64_t)c * M + ((int64_t)kz * g.py + ky) * g.px + kx];
-    const double2 w = make_double2(v.x * inv, v.y * inv);
+    int nx = natx[kx], ny = naty[ky];
+    const bool fx = nx > g.px / 2, fy = ny > g.py / 2;
+    if (fx) nx = g.px - nx;
+    if (fy) ny = g.py - ny;
+    double2 v = f[(int64_t)c * F + (int64_t)kz * P + (int64_t)ny * hx1 + nx];
+    const bool neg = (fx && odd_in(c, 0)) != (fy && odd_in(c, 1));
+    const double sc = neg ? -inv : inv;
+    const double2 w = make_double2(v.x * sc, v.y * sc);
     g128[o] = w;
     g64[o] = make_float2((float)w.x, (float)w.y);
   }
+}
+
+// natural frequency of storage position p of an in-place DIF transform with this plan:
+// a radix-R stage on length L leaves frequency residue k at offset k (L/R) of the next sub-transform
+int natural_index(const FftPlan& pl, int p) {
+  int L = pl.L, nat = 0, mult = 1;
+  for (int s = 0; s < pl.nst && L > 1; ++s) {
+    const int R = pl.radix[s], m = L / R;
+    nat += mult * (p / m);
+    mult *= R;
+    p %= m;
+    L = m;
+  }
+  return nat;
 }
 
 int g_smem_optin = 0;
@@ -572,31 +605,62 @@ void init_kernel_attrs() {
   fast_optin_c128(v);
 }
 
+void green_perm_tables(const Geom& g, std::vector<int32_t>* out) {
+  const int hx1 = g.px / 2 + 1, hy1 = g.py / 2 + 1;
+  out->assign((size_t)g.px + g.py + hx1 + hy1, 0);
+  int32_t* natx = out->data();
+  int32_t* naty = natx + g.px;
+  int32_t* stx = naty + g.py;
+  int32_t* sty = stx + hx1;
+  for (int p = 0; p < g.px; ++p) {
+    natx[p] = natural_index(g.plx, p);
+    if (natx[p] <= g.px / 2) stx[natx[p]] = p;
+  }
+  for (int p = 0; p < g.py; ++p) {
+    naty[p] = natural_index(g.ply, p);
+    if (naty[p] <= g.py / 2) sty[naty[p]] = p;
+  }
+}
+
 Err build_green(const Geom& g, double kd, const double2* twx, const double2* twy, const double2* twz,
-                double2* gw, double2* ghat128, float2* ghat64, cudaStream_t st) {
+                const int32_t* perm, double2* gw, double2* ghat128, float2* ghat64, cudaStream_t st) {
   const int64_t M = (int64_t)g.px * g.py * g.pz;
-  const int hy1 = g.py / 2 + 1, hz1 = g.pz / 2 + 1;
-  const int64_t Q = (int64_t)g.px * hy1 * hz1, T = (int64_t)g.px * g.py * hz1;
+  const int hx1 = g.px / 2 + 1, hy1 = g.py / 2 + 1, hz1 = g.pz / 2 + 1;
+  const int64_t Q = (int64_t)g.px * hy1 * hz1, T = (int64_t)hx1 * g.py * hz1, F = (int64_t)hx1 * hy1 * g.pz;
   auto nblk = [](int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 16); };
-  // q (in gw): the quarter y <= Py/2, z <= Pz/2; x rows transformed in place
+  Err e = Err::Ok();
+  // perm (green_perm_tables): natx[px] | naty[py] | stx[hx1] | sty[hy1]
+  const int32_t* d_natx = perm;
+  const int32_t* d_naty = d_natx + g.px;
+  const int32_t* d_stx = d_naty + g.py;
+  const int32_t* d_sty = d_stx + hx1;
+  // q (in gw): the quarter y <= Py/2, z <= Pz/2 of the wrapped tensor; x rows transformed in place
   double2* q = gw;
-  k_green_fill_q<<<nblk(Q), 256, 0, st>>>(g, kd, q);
-  DDA_CU(cudaGetLastError());
-  DDA_TRY(fft_rows<double2>(q, 6 * (int64_t)hy1 * hz1, g.px, g.plx, twx, g.px, g.px, false, st));
-  // t (in the ghat128 buffer, free until the pack): planes z <= Pz/2, all y; y columns transformed
+  if (e.ok()) {
+    k_green_fill_q<<<nblk(Q), 256, 0, st>>>(g, kd, q);
+    if (cudaGetLastError() != cudaSuccess) e = Err::make(DDA_ECUDA, "Green fill failed");
+  }
+  if (e.ok()) e = fft_rows<double2>(q, 6 * (int64_t)hy1 * hz1, g.px, g.plx, twx, g.px, g.px, false, st);
+  // t (in the ghat128 buffer, free until the pack): planes z <= Pz/2, all y, natural kx <= Px/2
   double2* t = ghat128;
-  k_green_expand_y<<<nblk(6 * T), 256, 0, st>>>(g, q, t);
-  DDA_CU(cudaGetLastError());
-  DDA_TRY(fft_strided<double2>(t, g.py, g.px, g.px, 6 * (int64_t)hz1, (int64_t)g.px * g.py, g.ply, twy, false, st));
-  // f (in gw): all z; z columns transformed
-  k_green_expand_z<<<nblk(6 * M), 256, 0, st>>>(g, t, gw);
-  DDA_CU(cudaGetLastError());
-  DDA_TRY(fft_strided<double2>(gw, g.pz, (int64_t)g.px * g.py, (int64_t)g.px * g.py, 6, M, g.plz, twz, false, st));
-  g_launches += 3;
-  k_green_pack<<<nblk(6 * M), 256, 0, st>>>(g, gw, ghat128, ghat64);
-  DDA_CU(cudaGetLastError());
-  g_launches += 1;
-  return Err::Ok();
+  if (e.ok()) {
+    k_green_expand_y<<<nblk(6 * T), 256, 0, st>>>(g, d_stx, q, t);
+    if (cudaGetLastError() != cudaSuccess) e = Err::make(DDA_ECUDA, "Green expand (y) failed");
+  }
+  if (e.ok()) e = fft_strided<double2>(t, g.py, hx1, hx1, 6 * (int64_t)hz1, (int64_t)hx1 * g.py, g.ply, twy, false, st);
+  // f (in gw): all z, natural ky <= Py/2, kx <= Px/2; z columns transformed
+  if (e.ok()) {
+    k_green_expand_z<<<nblk(6 * F), 256, 0, st>>>(g, d_sty, t, gw);
+    if (cudaGetLastError() != cudaSuccess) e = Err::make(DDA_ECUDA, "Green expand (z) failed");
+  }
+  if (e.ok())
+    e = fft_strided<double2>(gw, g.pz, (int64_t)hx1 * hy1, (int64_t)hx1 * hy1, 6, F, g.plz, twz, false, st);
+  if (e.ok()) {
+    k_green_pack<<<nblk(6 * M), 256, 0, st>>>(g, d_natx, d_naty, gw, ghat128, ghat64);
+    if (cudaGetLastError() != cudaSuccess) e = Err::make(DDA_ECUDA, "Green pack failed");
+  }
+  g_launches += 4;
+  return e;
 }
 
 template Err launch_matvec<float2>(const Geom&, const MvData<float2>&, const MvTune&, const float2*, float2*, int,

@@ -36,7 +36,11 @@ class Problem:
 
 
 def build_problem(shape, shpar, m, x, prescription, orientations, e01_lf=((0, 0), (1, 0), (0, 0)),
-                  iorth=2, pad=None, target=None, kd=None) -> Problem:
+                  iorth=2, pad=None, target=None, kd=None, comp=None) -> Problem:
+    """comp (optional): per-site composition indices (0-based) in the target's site order, shape
+    (N,) for isotropic materials or (N, 3) for one composition per Cartesian axis (the guide's
+    ICOMP triple of an anisotropic material whose principal axes are the TF axes); m is then a
+    sequence of refractive indices, one per composition."""
     tgt = targets.make_target(shape, shpar) if target is None else target
     if kd is None:
         kd = x / tgt.aeff            # k d = x / (a_eff / d)
@@ -48,8 +52,16 @@ def build_problem(shape, shpar, m, x, prescription, orientations, e01_lf=((0, 0)
     for ori in orientations:
         k_tf, pols_tf, pols_lf, axes = orientation.incidence(kd, ori, tgt.a1, tgt.a2, e01, iorth)
         for l, e_tf in enumerate(pols_tf):
-            ia = polarizability.inv_alpha(prescription, m, kd, k_tf / kd, e_tf)
-            inv_alpha = np.tile(ia, (tgt.n, 1))
+            if comp is None:
+                ia = polarizability.inv_alpha(prescription, m, kd, k_tf / kd, e_tf)
+                inv_alpha = np.tile(ia, (tgt.n, 1))
+            else:
+                # one diagonal per composition, then axis a of site j takes composition comp[j, a]
+                table = np.array([polarizability.inv_alpha(prescription, mc, kd, k_tf / kd, e_tf) for mc in m])
+                cj = np.asarray(comp, dtype=np.int64)
+                if cj.ndim == 1:
+                    cj = np.repeat(cj[:, None], 3, axis=1)
+                inv_alpha = table[cj, np.arange(3)[None, :]]
             e_inc = e_tf[:, None] * np.exp(1j * (r @ k_tf))[None, :]
             rhs.append(Rhs(ori=tuple(ori), pol=l, k_tf=k_tf, e_tf=e_tf, e01_lf=pols_lf[0],
                            e02_lf=pols_lf[1] if iorth == 2 else None, axes=axes,

@@ -300,6 +300,43 @@ def test_bicgstab_l_reduces_to_bicgstab_and_solves():
     assert all(i > 0 for i in its)
 
 
+def test_compositions_assemble_per_site_and_axis():
+    """Per-site and per-axis compositions: equal indices reduce to the homogeneous problem, relabelling
+    compositions (with the index list permuted alike) changes nothing, real indices absorb nothing,
+    and a single anisotropic dipole gives C_ext = 4 pi k Im sum_a alpha_aa |e_a|^2 exactly."""
+    t = targets.make_target("ELLIPSOID", (6, 5, 4))
+    ori = [(0.3, 0.7, 1.1)]
+    base = dda.build_problem(None, None, 1.5 + 0.1j, 2.0, "GKDLDR", ori, target=t)
+    same = dda.build_problem(None, None, [1.5 + 0.1j, 1.5 + 0.1j], 2.0, "GKDLDR", ori, target=t,
+                             comp=(t.ijk[:, 2] % 2))
+    for a, b in zip(base.rhs, same.rhs):
+        assert np.array_equal(a.inv_alpha, b.inv_alpha)
+    c3 = np.stack([t.ijk[:, 2] % 2, np.zeros(t.n, int), (t.ijk[:, 0] + t.ijk[:, 1]) % 3], axis=1)
+    m = [1.5 + 0.1j, 1.3 + 0.02j, 2.0 + 0.4j]
+    p1 = dda.build_problem(None, None, m, 2.0, "LATTDR", ori, target=t, comp=c3)
+    perm = np.array([2, 0, 1])                     # new label of old composition i
+    m2 = [None] * 3
+    for i, k in enumerate(perm):
+        m2[k] = m[i]
+    p2 = dda.build_problem(None, None, m2, 2.0, "LATTDR", ori, target=t, comp=perm[c3])
+    for a, b in zip(p1.rhs, p2.rhs):
+        assert np.array_equal(a.inv_alpha, b.inv_alpha)
+    q1 = dda.cross_sections(p1, dda.solve(p1, "lu")[0])
+    pr = dda.build_problem(None, None, [1.5, 1.3, 2.0], 2.0, "LATTDR", ori, target=t, comp=c3)
+    for q in dda.cross_sections(pr, dda.solve(pr, "lu")[0]):
+        assert abs(q["Qabs"]) < 1e-12 * q["Qext"]
+    assert all(q["Qabs"] > 0 for q in q1)
+    # one anisotropic site
+    t1 = targets.from_sites([[0, 0, 0]], [0.0, 0.0, 0.0])
+    kd = 0.3
+    prob = dda.build_problem(None, None, m, None, "CM", [(0.2, 0.9, 0.4)], target=t1, kd=kd, comp=[[0, 1, 2]])
+    ps, _ = dda.solve(prob, "lu")
+    for rh, q in zip(prob.rhs, dda.cross_sections(prob, ps)):
+        alpha = 1.0 / rh.inv_alpha[0]
+        cext = 4 * math.pi * kd * np.sum(alpha.imag * np.abs(rh.e_tf) ** 2)
+        assert q["Qext"] * math.pi * t1.aeff ** 2 == pytest.approx(cext, rel=1e-12)
+
+
 def test_orientation_grid_guide_examples():
     """The guide's own examples of the (beta, Theta, Phi) sampling, and the weights' quadrature."""
     deg = lambda v: [math.degrees(x) for x in v]

@@ -107,6 +107,16 @@ DDA_API dda_status dda_setup_shape(dda_ctx *ctx, int shape, const double *shpar,
 DDA_API dda_status dda_setup_target(dda_ctx *ctx, const int32_t *ixyz, const int32_t *icomp, int64_t n,
                             const double origin_tf[3], const double a1[3], const double a2[3]);
 
+/* The same for a target of anisotropic materials whose principal axes are the
+ * Target-Frame axes (the guide's FROM_FILE targets with a composition per
+ * site and axis, section "FROM_FILE = Target composed of possibly anisotropic
+ * material"): icomp3 host N x 3, the 1-based
+ * composition of each site's x, y and z axis; dda_set_polarizability then
+ * gives one refractive index per composition, and axis a of a site takes the
+ * polarizability of its axis-a composition. */
+DDA_API dda_status dda_setup_target_aniso(dda_ctx *ctx, const int32_t *ixyz, const int32_t *icomp3, int64_t n,
+                                  const double origin_tf[3], const double a1[3], const double a2[3]);
+
 /* Copy the site list out: ixyz_out host N x 3 (box-relative lattice indices),
  * origin_out[3] = TF position of box index (0,0,0).  Either may be NULL. */
 DDA_API dda_status dda_get_sites(dda_ctx *ctx, int32_t *ixyz_out, double origin_out[3]);

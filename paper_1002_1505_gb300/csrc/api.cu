@@ -194,7 +194,7 @@ void free_all(dda_ctx* c) {
 
 Err upload_target(dda_ctx* c) {
   auto& t = c->tgt;
-  const int64_t n = (int64_t)t.comp.size();
+  const int64_t n = (int64_t)t.comp.size() / 3;
   const int64_t nbox = (int64_t)t.box[0] * t.box[1] * t.box[2];
   std::vector<int32_t> map(nbox, -1);
   for (int64_t j = 0; j < n; ++j) {
@@ -214,8 +214,8 @@ Err upload_target(dda_ctx* c) {
   DDA_CU(cudaMemcpy(c->d_origin, t.origin, sizeof(double) * 3, cudaMemcpyHostToDevice));
   c->comp_valid = false;
   if (t.ncomp > 1) {
-    DDA_TRY(grow(c, &c->d_comp, n));
-    DDA_CU(cudaMemcpy(c->d_comp, t.comp.data(), n, cudaMemcpyHostToDevice));
+    DDA_TRY(grow(c, &c->d_comp, 3 * n));
+    DDA_CU(cudaMemcpy(c->d_comp, t.comp.data(), 3 * n, cudaMemcpyHostToDevice));
     c->comp_valid = true;
   }
   c->n = n;
@@ -739,14 +739,14 @@ dda_status dda_setup_shape(dda_ctx* c, int shape, const double* shpar, int nshpa
   }
 }
 
-dda_status dda_setup_target(dda_ctx* c, const int32_t* ixyz, const int32_t* icomp, int64_t n, const double origin[3],
-                            const double a1[3], const double a2[3]) {
+static dda_status setup_sites(dda_ctx* c, const int32_t* ixyz, const int32_t* icomp, int64_t n, const double origin[3],
+                              const double a1[3], const double a2[3], bool per_axis) {
   if (!c) return DDA_EINVAL;
   try {
     Err e = set_dev(c);
     if (!e.ok()) return fail(c, e);
     dda::HostTarget t;
-    e = dda::make_site_target(ixyz, icomp, n, origin, a1, a2, &t);
+    e = dda::make_site_target(ixyz, icomp, n, origin, a1, a2, &t, per_axis);
     if (!e.ok()) return fail(c, e);
     drop_target(c);
     c->tgt = std::move(t);
@@ -756,6 +756,17 @@ dda_status dda_setup_target(dda_ctx* c, const int32_t* ixyz, const int32_t* icom
   } catch (const std::bad_alloc&) {
     return fail(c, Err::make(DDA_ENOMEM, "host allocation failed"));
   }
+}
+
+dda_status dda_setup_target(dda_ctx* c, const int32_t* ixyz, const int32_t* icomp, int64_t n, const double origin[3],
+                            const double a1[3], const double a2[3]) {
+  return setup_sites(c, ixyz, icomp, n, origin, a1, a2, false);
+}
+
+dda_status dda_setup_target_aniso(dda_ctx* c, const int32_t* ixyz, const int32_t* icomp3, int64_t n,
+                                  const double origin[3], const double a1[3], const double a2[3]) {
+  if (!icomp3) return DDA_EINVAL;
+  return setup_sites(c, ixyz, icomp3, n, origin, a1, a2, true);
 }
 
 dda_status dda_get_sites(dda_ctx* c, int32_t* ixyz_out, double origin_out[3]) {

@@ -41,7 +41,7 @@ struct Err {
 // ------------------------------------------------------------------ targets (host)
 struct HostTarget {
   std::vector<int32_t> ijk;   // N x 3 box-relative lattice indices, x-fastest order
-  std::vector<uint8_t> comp;  // N, 0-based composition
+  std::vector<uint8_t> comp;  // N x 3, 0-based composition of each site's x, y, z axis
   int box[3] = {0, 0, 0};
   double origin[3] = {0, 0, 0};
   double a1[3] = {1, 0, 0};
@@ -50,7 +50,7 @@ struct HostTarget {
 };
 Err make_shape_target(int shape, const double* shpar, int nshpar, HostTarget* out);
 Err make_site_target(const int32_t* ixyz, const int32_t* icomp, int64_t n, const double origin[3],
-                     const double a1[3], const double a2[3], HostTarget* out);
+                     const double a1[3], const double a2[3], HostTarget* out, bool per_axis = false);
 
 // ------------------------------------------------------------------ FFT plans (host)
 Err make_plan(int L, FftPlan* out);
@@ -73,7 +73,7 @@ struct KState;
 template <typename C>
 struct MvData {
   const int32_t* map;   // nx*ny*nz box -> site index or -1
-  const uint8_t* comp;  // N compositions (0-based), may be null when ncomp == 1
+  const uint8_t* comp;  // N x 3 compositions (0-based, per site and axis), may be null when ncomp == 1
   const C* ghat;        // [px][py][pz][6] Fourier-space tensor (xx,xy,xz,yy,yz,zz), scaled by 1/M
   const C* ia;          // [nrhs][ncomp][3] diagonal of alpha^{-1}
   const C* twx;         // twiddles exp(-2 pi i j / L), L entries each

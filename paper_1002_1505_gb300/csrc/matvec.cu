@@ -127,7 +127,7 @@ __global__ void k_xinv(Geom g, MvData<C> d, const C* __restrict__ p, C* __restri
     const int32_t idx = d.map[((int64_t)z * g.ny + y) * g.nx + x];
     if (idx < 0) continue;
     const int64_t o = ((int64_t)b * 3 + c) * g.n + idx;
-    const int cc = d.comp ? d.comp[idx] : 0;
+    const int cc = d.comp ? d.comp[3 * idx + c] : 0;  // composition of axis c
     C pv = p[o];
     if (conj) pv = conjc(pv);
     C out = cadd(s[(c * ty + t) * ps + x], cmul(ia[cc * 3 + c], pv));

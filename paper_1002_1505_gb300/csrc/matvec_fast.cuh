@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(256) k_x_inv(Geom g, MvData<C> d, const C* __r
     if (idx < 0) continue;
     const int c = c0 + cl;
     const int64_t o = ((int64_t)b * 3 + c) * g.n + idx;
-    const int cc = d.comp ? d.comp[idx] : 0;
+    const int cc = d.comp ? d.comp[3 * idx + c] : 0;  // composition of axis c
     C pv = p[o];
     if (conj) pv = conjc(pv);
     const C res = cadd(in[(cl * TY + t) * ip + x], cmul(ia[cc * 3 + c], pv));

@@ -67,8 +67,8 @@ __global__ void k_qsum(const uint8_t* comp, const double2* __restrict__ e, const
   const double rr = (2.0 / 3.0) * kd * kd * kd;
   double acc[3] = {0.0, 0.0, 0.0};
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-    const int cc = comp ? comp[j] : 0;
     for (int c = 0; c < 3; ++c) {
+      const int cc = comp ? comp[3 * j + c] : 0;  // composition of axis c
       const double2 ev = e[((int64_t)b * 3 + c) * n + j];
       const double2 pv = p[((int64_t)b * 3 + c) * n + j];
       // conj(E) * P

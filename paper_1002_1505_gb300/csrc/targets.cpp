@@ -58,7 +58,7 @@ Err collect(int64_t L0, int64_t L1, int64_t L2, const std::vector<int64_t>& ux, 
   out->origin[2] = 0.5 * (double)uz[lo[2]];
   std::memcpy(out->a1, a1, sizeof(double) * 3);
   std::memcpy(out->a2, a2, sizeof(double) * 3);
-  out->comp.assign(tmp.size() / 3, 0);
+  out->comp.assign(tmp.size(), 0);  // N x 3
   out->ncomp = 1;
   return Err::Ok();
 }
@@ -146,7 +146,7 @@ Err make_shape_target(int shape, const double* shpar, int nshpar, HostTarget* ou
 }
 
 Err make_site_target(const int32_t* ixyz, const int32_t* icomp, int64_t n, const double origin[3],
-                     const double a1[3], const double a2[3], HostTarget* out) {
+                     const double a1[3], const double a2[3], HostTarget* out, bool per_axis) {
   if (!ixyz || n <= 0) return Err::make(DDA_EINVAL, "site list is empty");
   if (n > (int64_t)1 << 30) return Err::make(DDA_EINVAL, "too many sites");
   int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
@@ -166,15 +166,17 @@ Err make_site_target(const int32_t* ixyz, const int32_t* icomp, int64_t n, const
   for (int64_t j = 1; j < n; ++j)
     if (key(order[j]) == key(order[j - 1])) return Err::make(DDA_EINVAL, "duplicate site in list");
   out->ijk.resize(3 * n);
-  out->comp.resize(n);
+  out->comp.resize(3 * n);
   int maxc = 1;
   for (int64_t s = 0; s < n; ++s) {
     int64_t j = order[s];
     for (int a = 0; a < 3; ++a) out->ijk[3 * s + a] = ixyz[3 * j + a] - lo[a];
-    int c = icomp ? icomp[j] : 1;
-    if (c < 1 || c > 255) return Err::make(DDA_EINVAL, "composition index must be in 1..255");
-    out->comp[s] = (uint8_t)(c - 1);
-    maxc = std::max(maxc, c);
+    for (int a = 0; a < 3; ++a) {
+      const int c = icomp ? icomp[per_axis ? 3 * j + a : j] : 1;
+      if (c < 1 || c > 255) return Err::make(DDA_EINVAL, "composition index must be in 1..255");
+      out->comp[3 * s + a] = (uint8_t)(c - 1);
+      maxc = std::max(maxc, c);
+    }
   }
   for (int a = 0; a < 3; ++a) {
     out->box[a] = hi[a] - lo[a] + 1;

@@ -388,7 +388,7 @@ __global__ void k_features(const int32_t* __restrict__ ijk, int64_t n, const uin
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
     const int xx = ijk[3 * j] + ox, yy = ijk[3 * j + 1] + oy, zz = ijk[3 * j + 2] + oz;
     const int64_t v = (int64_t)b * d.nvox() + ((int64_t)zz * d.Y + yy) * d.X + xx;
-    const float2 ep = eps[comp ? comp[j] : 0];
+    const float2 ep = eps[comp ? comp[3 * j] : 0];  // the x-axis material of the site
     float* o = x + v * 9;
     o[0] = 1.f;
     o[1] = 0.25f * (ep.x - 1.f);
@@ -411,8 +411,8 @@ __global__ void k_targets(const int32_t* __restrict__ ijk, int64_t n, const uint
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
     const int xx = ijk[3 * j] + ox, yy = ijk[3 * j + 1] + oy, zz = ijk[3 * j + 2] + oz;
     const int64_t v = (int64_t)b * d.nvox() + ((int64_t)zz * d.Y + yy) * d.X + xx;
-    const int cc = comp ? comp[j] : 0;
     for (int c = 0; c < 3; ++c) {
+      const int cc = comp ? comp[3 * j + c] : 0;  // composition of axis c
       const double2 a = ia[((int64_t)b * ncomp + cc) * 3 + c];
       const double2 pv = p[((int64_t)b * 3 + c) * n + j];
       double re = a.x * pv.x - a.y * pv.y, im = a.x * pv.y + a.y * pv.x;
@@ -438,8 +438,8 @@ __global__ void k_warm(const int32_t* __restrict__ ijk, int64_t n, const uint8_t
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
     const int xx = ijk[3 * j] + ox, yy = ijk[3 * j + 1] + oy, zz = ijk[3 * j + 2] + oz;
     const int64_t v = (int64_t)b * d.nvox() + ((int64_t)zz * d.Y + yy) * d.X + xx;
-    const int cc = comp ? comp[j] : 0;
     for (int c = 0; c < 3; ++c) {
+      const int cc = comp ? comp[3 * j + c] : 0;  // composition of axis c
       const double2 a = ia[((int64_t)b * ncomp + cc) * 3 + c];
       double er = y[v * 6 + 2 * c], ei = y[v * 6 + 2 * c + 1];
       if (e) {
@@ -1014,8 +1014,8 @@ __global__ void k_guess64(const int32_t* __restrict__ ijk, int64_t n, const uint
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
     const int xx = ijk[3 * j] + ox, yy = ijk[3 * j + 1] + oy, zz = ijk[3 * j + 2] + oz;
     const int64_t v = (int64_t)b * d.nvox() + ((int64_t)zz * d.Y + yy) * d.X + xx;
-    const int cc = comp ? comp[j] : 0;
     for (int c = 0; c < 3; ++c) {
+      const int cc = comp ? comp[3 * j + c] : 0;  // composition of axis c
       const double2 a = ia[((int64_t)b * ncomp + cc) * 3 + c];
       const double2 ev = e[((int64_t)b * 3 + c) * n + j];
       const double er = y[v * 6 + 2 * c] + ev.x, ei = y[v * 6 + 2 * c + 1] + ev.y;
@@ -1066,8 +1066,8 @@ __global__ void k_resgrad(const int32_t* __restrict__ ijk, int64_t n, const uint
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
     const int xx = ijk[3 * j] + ox, yy = ijk[3 * j + 1] + oy, zz = ijk[3 * j + 2] + oz;
     const int64_t v = (int64_t)b * d.nvox() + ((int64_t)zz * d.Y + yy) * d.X + xx;
-    const int cc = comp ? comp[j] : 0;
     for (int c = 0; c < 3; ++c) {
+      const int cc = comp ? comp[3 * j + c] : 0;  // composition of axis c
       const double2 ai = ia[((int64_t)b * ncomp + cc) * 3 + c];
       const double den = ai.x * ai.x + ai.y * ai.y;
       const double ar = ai.x / den, aim = -ai.y / den;  // alpha = 1 / alpha^{-1}

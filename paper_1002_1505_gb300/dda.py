@@ -59,6 +59,7 @@ def _load():
         "dda_set_stream": (I, [P, P]),
         "dda_setup_shape": (I, [P, I, P, I, P, P]),
         "dda_setup_target": (I, [P, P, P, I64, P, P, P]),
+        "dda_setup_target_aniso": (I, [P, P, P, I64, P, P, P]),
         "dda_get_sites": (I, [P, P, P]),
         "dda_set_incident": (I, [P, D, P, I, P, I]),
         "dda_nrhs": (I, [P]),
@@ -159,12 +160,16 @@ class Context:
         return self.n, self.box
 
     def dda_setup_target(self, ixyz, icomp=None, origin=(0.0, 0.0, 0.0), a1=None, a2=None):
+        """icomp: None, N 1-based compositions, or N x 3 (one per axis: anisotropic materials)."""
         ij = np.ascontiguousarray(ixyz, dtype=np.int32)
         ic = None if icomp is None else np.ascontiguousarray(icomp, dtype=np.int32)
+        fn = LIB.dda_setup_target
+        if ic is not None and ic.ndim == 2:
+            fn = LIB.dda_setup_target_aniso
         org = np.ascontiguousarray(origin, dtype=np.float64)
         a1v = None if a1 is None else np.ascontiguousarray(a1, dtype=np.float64)
         a2v = None if a2 is None else np.ascontiguousarray(a2, dtype=np.float64)
-        self._check(LIB.dda_setup_target(self._h, _ptr(ij), None if ic is None else _ptr(ic), ij.shape[0], _ptr(org),
+        self._check(fn(self._h, _ptr(ij), None if ic is None else _ptr(ic), ij.shape[0], _ptr(org),
                                          None if a1v is None else _ptr(a1v), None if a2v is None else _ptr(a2v)))
         self.n = ij.shape[0]
         sites, _ = self.dda_get_sites()

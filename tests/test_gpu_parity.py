@@ -16,7 +16,8 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-from oracle import dda as odda  # noqa: E402
+from oracle import dda as odda
+from oracle import targets as o_targets  # noqa: E402
 from oracle import interaction as oint  # noqa: E402
 from paper_1002_1505_gb300 import workloads as W  # noqa: E402
 
@@ -514,6 +515,51 @@ def test_orientation_averaged_efficiencies(D):
     np.testing.assert_allclose(avg, avg_ref, rtol=2e-5)
     # the average differs from any single orientation (the ellipsoid is not isotropic)
     assert np.ptp(q[:, 0]) > 1e-3 * avg[0, 0]
+
+
+@pytest.mark.parametrize("aniso", [False, True])
+def test_multi_composition_targets(D, aniso):
+    """Site-list targets of several materials, isotropic (one composition per site) or anisotropic
+    (one per site and axis, the guide's FROM_FILE compositions): product, solve and efficiencies
+    against the oracle."""
+    t = o_targets.make_target("ELLIPSOID", (9, 7, 6))
+    if aniso:
+        comp = np.stack([t.ijk[:, 2] % 2, (t.ijk[:, 0] // 3) % 3, np.full(t.n, 1)], axis=1)
+    else:
+        comp = (t.ijk[:, 0] + t.ijk[:, 2]) % 3
+    m = [1.5 + 0.1j, 1.33 + 0.01j, 2.2 + 0.6j]
+    ori = W.uniform_orientations(2, 61)
+    prob = odda.build_problem(None, None, m, 2.5, "GKDLDR", ori, target=t, comp=comp)
+    ctx = D.Context(0)
+    ctx.dda_setup_target(t.ijk, icomp=comp + 1, origin=t.origin)
+    ctx.dda_set_incident(prob.kd, ori, [[0, 0], [1, 0], [0, 0]], 2)
+    ctx.dda_build_green_fft()
+    ctx.dda_set_polarizability("GKDLDR", m)
+    ia = ctx.dda_get_inv_alpha()
+    for b in range(ctx.nrhs):
+        for mi in range(3):
+            for a in range(3):
+                sel = comp[:, a] == mi if aniso else comp == mi
+                if np.any(sel):
+                    assert ia[b, mi, a] == pytest.approx(prob.rhs[b].inv_alpha[sel, a][0], rel=1e-13)
+    for dt, tol in ((torch.complex128, 1e-12), (torch.complex64, 1e-5)):
+        p = _rand_p(ctx.nrhs, ctx.n, 31, dt)
+        ap = torch.empty_like(p)
+        ctx.dda_matvec(p, ap)
+        torch.cuda.synchronize()
+        pn = p.cpu().numpy().astype(np.complex128)
+        got = ap.cpu().numpy().astype(np.complex128)
+        for b in range(ctx.nrhs):
+            ref = odda.apply_a(prob, b, pn[b], "direct")
+            assert np.linalg.norm(got[b] - ref) / np.linalg.norm(ref) <= tol, (aniso, dt, b)
+    ps, _ = odda.solve(prob, "lu")
+    qref = odda.cross_sections(prob, ps)
+    p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
+    reps, _ = ctx.dda_solve(p, precision="MIXED", tol=1e-6, maxit=2000)
+    q, _ = ctx.dda_cross_sections(p)
+    for b in range(ctx.nrhs):
+        for i, key in enumerate(("Qext", "Qabs", "Qsca")):
+            assert q[b, i] == pytest.approx(qref[b][key], rel=1e-4), (aniso, key, b)
 
 
 def test_warm_start_from_solution_needs_no_iterations(D):

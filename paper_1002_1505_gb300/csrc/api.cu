@@ -296,6 +296,11 @@ dda::RedBuf redbuf(dda_ctx* c, int nrhs, int64_t n3) {
 template <typename C>
 Err ensure_work(dda_ctx* c, int want, int* cap_out);
 
+// a CUDA call's status as an Err
+inline Err cuda_ok(cudaError_t r, const char* what) {
+  return r == cudaSuccess ? Err::Ok() : Err::make(DDA_ECUDA, std::string(what) + ": " + cudaGetErrorString(r));
+}
+
 Err ensure_fault_flag(dda_ctx* c) {
   if (c->d_fault) return Err::Ok();
   DDA_TRY(grow(c, &c->d_fault, sizeof(unsigned int) * 4));
@@ -910,8 +915,9 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
       e = grow(c, &c->d_tw128[a], sizeof(double2) * L);
       if (e.ok()) e = grow(c, &c->d_tw64[a], sizeof(float2) * L);
       if (!e.ok()) return fail(c, e);
-      cudaMemcpy(c->d_tw128[a], t128.data(), sizeof(double2) * L, cudaMemcpyHostToDevice);
-      cudaMemcpy(c->d_tw64[a], t64.data(), sizeof(float2) * L, cudaMemcpyHostToDevice);
+      e = cuda_ok(cudaMemcpy(c->d_tw128[a], t128.data(), sizeof(double2) * L, cudaMemcpyHostToDevice), "twiddle upload");
+      if (e.ok()) e = cuda_ok(cudaMemcpy(c->d_tw64[a], t64.data(), sizeof(float2) * L, cudaMemcpyHostToDevice), "twiddle upload");
+      if (!e.ok()) return fail(c, e);
       c->tw_len[a] = L;
     }
     // schedule: 3-pass when the plane fits in the opt-in shared memory
@@ -1031,8 +1037,12 @@ dda_status dda_set_polarizability(dda_ctx* c, int presc, const double* m_reim, i
       e = grow(c, &c->d_ia128, sizeof(double2) * ia.size());
       if (e.ok()) e = grow(c, &c->d_ia64, sizeof(float2) * ia.size());
       if (!e.ok()) return fail(c, e);
-      cudaMemcpy(c->d_ia128, h128.data(), sizeof(double2) * ia.size(), cudaMemcpyHostToDevice);
-      cudaMemcpy(c->d_ia64, h64.data(), sizeof(float2) * ia.size(), cudaMemcpyHostToDevice);
+      e = cuda_ok(cudaMemcpy(c->d_ia128, h128.data(), sizeof(double2) * ia.size(), cudaMemcpyHostToDevice),
+                  "polarizability upload");
+      if (e.ok())
+        e = cuda_ok(cudaMemcpy(c->d_ia64, h64.data(), sizeof(float2) * ia.size(), cudaMemcpyHostToDevice),
+                    "polarizability upload");
+      if (!e.ok()) return fail(c, e);
     }
     c->ia = std::move(ia);
     c->eps.resize(ncomp);
@@ -1166,12 +1176,16 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
       dda::KrylovVecs<double2> kv;
       e = kvec_alloc<double2>(c, &kv, o.solver == DDA_BICGSTAB2 ? 1 : 0);
       if (e.ok()) {
-        cudaMemcpyAsync(kv.b, c->d_e128, sizeof(double2) * el, cudaMemcpyDeviceToDevice, c->stream);
-        if (o.warm_start) cudaMemcpyAsync(kv.x, P, sizeof(double2) * el, cudaMemcpyDeviceToDevice, c->stream);
+        e = cuda_ok(cudaMemcpyAsync(kv.b, c->d_e128, sizeof(double2) * el, cudaMemcpyDeviceToDevice, c->stream),
+                    "right-hand side copy");
+        if (e.ok() && o.warm_start)
+          e = cuda_ok(cudaMemcpyAsync(kv.x, P, sizeof(double2) * el, cudaMemcpyDeviceToDevice, c->stream),
+                      "initial guess copy");
         SolveStats s;
-        e = krylov<double2>(c, o, kv, o.tol, o.maxit, o.warm_start != 0, &s, t0, &timed_out);
+        if (e.ok()) e = krylov<double2>(c, o, kv, o.tol, o.maxit, o.warm_start != 0, &s, t0, &timed_out);
+        if (e.ok()) e = cuda_ok(cudaMemcpyAsync(P, kv.x, sizeof(double2) * el, cudaMemcpyDeviceToDevice, c->stream),
+                                "solution copy");
         if (e.ok()) {
-          cudaMemcpyAsync(P, kv.x, sizeof(double2) * el, cudaMemcpyDeviceToDevice, c->stream);
           iters = s.iters;
           matvecs += s.matvecs;
         }
@@ -1184,8 +1198,8 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
       SolveStats s;
       if (e.ok()) e = krylov<float2>(c, o, kv, o.tol, o.maxit, o.warm_start != 0, &s, t0, &timed_out);
       if (e.ok()) {
-        cudaMemsetAsync(P, 0, sizeof(double2) * el, c->stream);
-        e = dda::add_to_c128<float2>(P, kv.x, nullptr, nrhs, n3, c->stream);
+        e = cuda_ok(cudaMemsetAsync(P, 0, sizeof(double2) * el, c->stream), "solution clear");
+        if (e.ok()) e = dda::add_to_c128<float2>(P, kv.x, nullptr, nrhs, n3, c->stream);
         iters = s.iters;
         matvecs += s.matvecs;
       }
@@ -1195,13 +1209,15 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
       e = kvec_alloc<float2>(c, &kv, o.solver == DDA_BICGSTAB2 ? 1 : 0);
       // each inner solve aims straight for tol, but never below the complex64 floor
       const double inner = o.inner_tol > 0 ? o.inner_tol : 5e-6;
-      if (e.ok() && !o.warm_start) cudaMemsetAsync(P, 0, sizeof(double2) * el, c->stream);
+      if (e.ok() && !o.warm_start) e = cuda_ok(cudaMemsetAsync(P, 0, sizeof(double2) * el, c->stream), "solution clear");
       int budget = o.maxit;
       while (e.ok()) {
         // r = E - A P (FP64); at P = 0 the residual is E itself
         double2* r128 = sc + el;
         if (outer == 0 && !o.warm_start) {
-          cudaMemcpyAsync(r128, c->d_e128, sizeof(double2) * el, cudaMemcpyDeviceToDevice, c->stream);
+          e = cuda_ok(cudaMemcpyAsync(r128, c->d_e128, sizeof(double2) * el, cudaMemcpyDeviceToDevice, c->stream),
+                      "residual copy");
+          if (!e.ok()) break;
           rel.assign(nrhs, 1.0);
         } else {
           e = true_residual(c, P, sc, r128, &rel);
@@ -1253,15 +1269,17 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
         e = dda::residual_c128(sc, sc, r128, c->d_small, rb, nrhs, n3, c->stream);  // r128 = 0, second slot |sc|^2
       }
       if (e.ok()) {
-        cudaMemcpyAsync(c->h_pinned, c->d_small, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, c->stream);
-        cudaStreamSynchronize(c->stream);
+        e = cuda_ok(cudaMemcpyAsync(c->h_pinned, c->d_small, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost,
+                                    c->stream), "norm readback");
+        if (e.ok()) e = cuda_ok(cudaStreamSynchronize(c->stream), "norm readback");
         for (int b = 0; b < nrhs; ++b) num[b] = c->h_pinned[2 * b + 1];
         e = matvec<double2>(c, c->d_e128, sc, nrhs, 0, true);
       }
       if (e.ok()) e = dda::residual_c128(sc, sc, r128, c->d_small, rb, nrhs, n3, c->stream);
       if (e.ok()) {
-        cudaMemcpyAsync(c->h_pinned, c->d_small, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, c->stream);
-        cudaStreamSynchronize(c->stream);
+        e = cuda_ok(cudaMemcpyAsync(c->h_pinned, c->d_small, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost,
+                                    c->stream), "norm readback");
+        if (e.ok()) e = cuda_ok(cudaStreamSynchronize(c->stream), "norm readback");
         for (int b = 0; b < nrhs; ++b) {
           den[b] = c->h_pinned[2 * b + 1];
           ner[b] = den[b] > 0 ? std::sqrt(num[b] / den[b]) : 0.0;
@@ -1323,8 +1341,10 @@ dda_status dda_cross_sections(dda_ctx* c, const void* p_dev, double* q_out, cons
         e = dda::qsums(c->comp_valid ? c->d_comp : nullptr, c->d_e128, c->d_ia128, c->ncomp, k, P, nrhs, c->n,
                        c->d_small, rb, c->stream);
       if (!e.ok()) return fail(c, e);
-      cudaMemcpyAsync(c->h_pinned, c->d_small, sizeof(double) * 3 * nrhs, cudaMemcpyDeviceToHost, c->stream);
-      if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, Err::make(DDA_ECUDA, "q sums failed"));
+      if (cudaMemcpyAsync(c->h_pinned, c->d_small, sizeof(double) * 3 * nrhs, cudaMemcpyDeviceToHost, c->stream) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return fail(c, Err::make(DDA_ECUDA, "q sums failed"));
       for (int b = 0; b < nrhs; ++b) {
         const double cext = 4 * pi * k * c->h_pinned[3 * b], cpha = 2 * pi * k * c->h_pinned[3 * b + 1];
         const double cabs = 4 * pi * k * c->h_pinned[3 * b + 2];
@@ -1359,10 +1379,12 @@ dda_status dda_cross_sections(dda_ctx* c, const void* p_dev, double* q_out, cons
       if (e.ok()) e = grow(c, &c->d_fpart, sizeof(double) * 6 * (size_t)nrhs * ndir * nblk);
       double2* d_F = c->d_F;
       if (e.ok()) {
-        cudaMemcpy(c->d_nh, nh.data(), sizeof(double) * nh.size(), cudaMemcpyHostToDevice);
+        e = cuda_ok(cudaMemcpy(c->d_nh, nh.data(), sizeof(double) * nh.size(), cudaMemcpyHostToDevice),
+                    "direction upload");
         const int box[3] = {c->tgt.box[0], c->tgt.box[1], c->tgt.box[2]};
-        e = dda::farfield(c->d_ijk, c->d_origin, c->d_nh, k, P, nrhs, ndir, c->n, box, d_F, (double2*)c->d_fpart,
-                          nblk, c->stream);
+        if (e.ok())
+          e = dda::farfield(c->d_ijk, c->d_origin, c->d_nh, k, P, nrhs, ndir, c->n, box, d_F, (double2*)c->d_fpart,
+                            nblk, c->stream);
       }
       std::vector<double2> F((size_t)nrhs * ndir * 3);
       if (e.ok()) {

@@ -776,11 +776,11 @@ dda_status dda_unet_create(dda_unet** out, int device, void* stream, int cin, in
     dda_unet_destroy(n);
     return DDA_ENOMEM;
   }
-  cudaMemcpy(n->p, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice);
-  cudaMemset(n->m, 0, sizeof(float) * off);
-  cudaMemset(n->v, 0, sizeof(float) * off);
-  cudaMemset(n->g, 0, sizeof(float) * off);
-  Err e = repack(n);
+  const bool init_ok = cudaMemcpy(n->p, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice) == cudaSuccess &&
+                       cudaMemset(n->m, 0, sizeof(float) * off) == cudaSuccess &&
+                       cudaMemset(n->v, 0, sizeof(float) * off) == cudaSuccess &&
+                       cudaMemset(n->g, 0, sizeof(float) * off) == cudaSuccess;
+  Err e = init_ok ? repack(n) : Err::make(DDA_ECUDA, "parameter upload failed");
   if (!e.ok() || cudaStreamSynchronize(n->stream) != cudaSuccess) {
     dda_unet_destroy(n);
     return DDA_ECUDA;

@@ -9,7 +9,9 @@ and the efficiencies plus Mueller elements.  The target's site list is resident
 on the device before the timed region (it is the step's input).
 
 value = A.P products per second (one product = A applied to one RHS vector, any
-precision) summed over all ranks; --gpus N runs N independent replicas.
+precision, counted per RHS: the products a batch skips for RHS whose solve has
+finished are not counted) summed over all ranks; --gpus N runs N independent
+replicas.
 --impl reference times the FP64 CPU oracle on the same workload instead.
 """
 from __future__ import annotations
@@ -273,7 +275,7 @@ def run_mixed(args):
             reps = [c.dda_solve(p, precision="MIXED", tol=1e-5, maxit=3000)[0] for c, p in zip(ctxs, ps)]
         for c, p in zip(ctxs, ps):
             c.dda_cross_sections(p)
-        return sum(r[0]["matvecs"] * len(r) for r in reps), reps
+        return sum(x["matvecs"] for r in reps for x in r), reps
 
     def timed(k, concurrent):
         tot, mv = 0.0, 0
@@ -377,7 +379,7 @@ def main():
             e1.record(stream)
             e1.synchronize()
             total += e0.elapsed_time(e1)
-            mv += reps[0]["matvecs"] * nrhs
+            mv += sum(r["matvecs"] for r in reps)  # products actually applied to each RHS
             last = (reps, q)
         return total, mv, last
 
@@ -429,7 +431,7 @@ def main():
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             e2e_ms += dt * 1e3
-            e2e_mv += r2[0]["matvecs"] * nrhs
+            e2e_mv += sum(r["matvecs"] for r in r2)
     e2e_value = e2e_mv / (e2e_ms / 1e3)
     h2d = h_sites.nbytes + 3 * n_ori * 8 + 48
     d2h = h_p.numel() * 16 + q2.nbytes

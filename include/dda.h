@@ -202,7 +202,8 @@ typedef struct {
 
 typedef struct {
   int iters;             /* Krylov iterations used (inner ones for MIXED) */
-  int matvecs;           /* products with A (any precision) */
+  int matvecs;           /* products with A applied to this RHS (any precision; a batch skips the
+                            products of RHS whose solve has finished) */
   int outer;             /* MIXED: refinement steps (true-residual evaluations) */
   int converged;         /* 1 if the true residual met tol */
   double true_rel_resid; /* |E - A P| / |E| evaluated with the FP64 product at exit */

@@ -519,7 +519,7 @@ Err ensure_einc(dda_ctx* c) {
 
 struct SolveStats {
   std::vector<int> iters, done;
-  int matvecs = 0;
+  std::vector<int> mv;  // products with A applied to each RHS
 };
 
 // One Krylov solve in precision C over all nrhs RHS. kv.x holds x0 when have_x0.
@@ -538,15 +538,11 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
   const bool ccg = (o.solver == DDA_CCG);
   const bool b2 = (o.solver == DDA_BICGSTAB2);
   if (b2 && !kv.u2) return Err::make(DDA_ESTATE, "BiCGstab(2) needs the extra Krylov vector");
-  if (have_x0) {
-    DDA_TRY(matvec<C>(c, kv.x, kv.r, nrhs, 0, false));
-    stats->matvecs += 1;
-  }
+  if (have_x0) DDA_TRY(matvec<C>(c, kv.x, kv.r, nrhs, 0, false));
   if (ccg) {
     DDA_TRY(dda::ccg_init<C>(kv, ks, rb, nrhs, n3, tol, have_x0, st));
     DDA_TRY(matvec<C>(c, kv.r, kv.s, nrhs, 0, true));
     DDA_TRY(dda::ccg_start<C>(kv, ks, rb, nrhs, n3, st));
-    stats->matvecs += 1;
   } else if (b2) {
     DDA_TRY(dda::b2_init<C>(kv, ks, rb, nrhs, n3, tol, have_x0, st));
   } else {
@@ -632,7 +628,6 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
   int it = 0;
   Err res = Err::Ok();
   const int it_per_call = b2 ? 2 : 1;  // iterations (2 products each) per one_iter
-  const int mv_per_it = 2;
   while (true) {
     DDA_CU(cudaMemcpyAsync(c->h_pinned, ks, sizeof(dda::KState) * nrhs, cudaMemcpyDeviceToHost, st));
     DDA_CU(cudaStreamSynchronize(st));
@@ -653,14 +648,15 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
       if (!res.ok()) break;
     }
     it += every * it_per_call;
-    stats->matvecs += mv_per_it * every * it_per_call;
   }
   DDA_TRY(res);
   stats->iters.resize(nrhs);
   stats->done.resize(nrhs);
+  stats->mv.resize(nrhs);
   for (int b = 0; b < nrhs; ++b) {
     stats->iters[b] = hk[b].it;
     stats->done[b] = hk[b].done;
+    stats->mv[b] = hk[b].mv + (have_x0 ? 1 : 0);
   }
   return Err::Ok();
 }
@@ -1163,7 +1159,13 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
     if (e.ok() && o.precision != DDA_PREC_C128) e = ensure_tuned<float2>(c, nrhs);
     if (!e.ok()) return fail(c, e);
     std::vector<int> iters(nrhs, 0), outer_n(nrhs, 0);
-    int matvecs = 0;
+    std::vector<int> mvb(nrhs, 0);  // products with A applied to each RHS
+    auto add_mv = [&](const std::vector<int>& v) {
+      for (int b = 0; b < nrhs && b < (int)v.size(); ++b) mvb[b] += v[b];
+    };
+    auto add_all = [&](int k) {
+      for (int b = 0; b < nrhs; ++b) mvb[b] += k;
+    };
     bool timed_out = false;
     std::vector<double> rel;
     // scratch c128 pair for true residuals (2 vectors)
@@ -1187,7 +1189,7 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
                                 "solution copy");
         if (e.ok()) {
           iters = s.iters;
-          matvecs += s.matvecs;
+          add_mv(s.mv);
         }
       }
     } else if (o.precision == DDA_PREC_C64) {
@@ -1201,7 +1203,7 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
         e = cuda_ok(cudaMemsetAsync(P, 0, sizeof(double2) * el, c->stream), "solution clear");
         if (e.ok()) e = dda::add_to_c128<float2>(P, kv.x, nullptr, nrhs, n3, c->stream);
         iters = s.iters;
-        matvecs += s.matvecs;
+        add_mv(s.mv);
       }
     } else {
       // mixed: inner complex64 solves of A d = r, r from FP64 true residuals
@@ -1221,7 +1223,7 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
           rel.assign(nrhs, 1.0);
         } else {
           e = true_residual(c, P, sc, r128, &rel);
-          matvecs += 1;
+          add_all(1);
           if (!e.ok()) break;
         }
         bool all = true;
@@ -1246,7 +1248,7 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
         int used = 0;
         for (int b = 0; b < nrhs; ++b) used = std::max(used, s.iters[b]);
         budget -= std::max(used, 1);
-        matvecs += s.matvecs;
+        add_mv(s.mv);
         e = dda::add_to_c128<float2>(P, kv.x, nullptr, nrhs, n3, c->stream);
         ++outer;
       }
@@ -1255,6 +1257,7 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
     // final true residual in FP64 (for MIXED it was computed by the loop's last pass)
     if (o.precision != DDA_PREC_MIXED || rel.empty()) {
       e = true_residual(c, P, sc, sc + el, &rel);
+      add_all(1);
       if (!e.ok()) { cleanup(); return fail(c, e); }
     }
     std::vector<double> ner(nrhs, NAN);
@@ -1273,7 +1276,8 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
                                     c->stream), "norm readback");
         if (e.ok()) e = cuda_ok(cudaStreamSynchronize(c->stream), "norm readback");
         for (int b = 0; b < nrhs; ++b) num[b] = c->h_pinned[2 * b + 1];
-        e = matvec<double2>(c, c->d_e128, sc, nrhs, 0, true);
+        if (e.ok()) e = matvec<double2>(c, c->d_e128, sc, nrhs, 0, true);
+        add_all(2);
       }
       if (e.ok()) e = dda::residual_c128(sc, sc, r128, c->d_small, rb, nrhs, n3, c->stream);
       if (e.ok()) {
@@ -1298,7 +1302,7 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
       all = all && conv;
       if (rep) {
         rep[b].iters = iters[b];
-        rep[b].matvecs = matvecs;
+        rep[b].matvecs = mvb[b];
         rep[b].outer = (o.precision == DDA_PREC_MIXED) ? outer_n[b] : 0;
         rep[b].converged = conv ? 1 : 0;
         rep[b].true_rel_resid = rel[b];

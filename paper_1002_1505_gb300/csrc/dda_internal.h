@@ -188,7 +188,8 @@ struct KState {
   double tol2;    // (tol)^2 * |b|^2 threshold for this solve
   int done;       // 1 = converged, 2 = breakdown
   int it;
-  int pad0, pad1;
+  int mv;         // products with A applied to this RHS (products of finished RHS are skipped)
+  int pad1;
 };
 
 template <typename C> Err k_copy_convert_c128_to(const double2* src, C* dst, int64_t count, cudaStream_t st);

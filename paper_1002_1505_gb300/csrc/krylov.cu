@@ -191,6 +191,7 @@ __global__ void k_bicg_init(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3,
     k.beta = make_double2(0.0, 0.0);
     k.tol2 = tol * tol * t[0];
     k.it = 0;
+    k.mv = 0;
     k.done = (t[0] == 0.0 || t[1] <= k.tol2) ? 1 : 0;
   }
 }
@@ -226,6 +227,7 @@ __global__ void k_bicg_dot_rv(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n
   if (last_block_totals<2>(acc, rb, b, t) && threadIdx.x == 0) {
     KState& k = ks[b];
     if (k.done) return;
+    k.mv += 1;  // v = A p
     const double2 rv = make_double2(t[0], t[1]);
     if (rv.x == 0.0 && rv.y == 0.0) { k.done = 2; return; }
     k.alpha = cdiv(k.rho, rv);
@@ -279,6 +281,7 @@ __global__ void k_bicg_dot_ts(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n
   if (last_block_totals<3>(acc, rb, b, t) && threadIdx.x == 0) {
     KState& k = ks[b];
     if (k.done) return;
+    k.mv += 1;  // t = A s
     k.omega = (t[2] > 0.0) ? make_double2(t[0] / t[2], t[1] / t[2]) : make_double2(0.0, 0.0);
   }
 }
@@ -354,6 +357,7 @@ __global__ void k_ccg_init(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3, 
     k.rr = t[1];
     k.tol2 = tol * tol * t[0];
     k.it = 0;
+    k.mv = 0;
     k.done = (t[0] == 0.0 || t[1] <= k.tol2) ? 1 : 0;
   }
 }
@@ -377,6 +381,7 @@ __global__ void k_ccg_start(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3)
   if (last_block_totals<1>(acc, rb, b, t) && threadIdx.x == 0) {
     KState& k = ks[b];
     if (k.done) return;
+    k.mv += 1;  // z = A^H r
     k.zz = t[0];
     if (t[0] == 0.0) k.done = 2;
   }
@@ -397,6 +402,7 @@ __global__ void k_norm_v(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
   if (last_block_totals<1>(acc, rb, b, t) && threadIdx.x == 0) {
     KState& k = ks[b];
     if (k.done) return;
+    k.mv += 1;  // w = A p
     if (t[0] == 0.0) { k.done = 2; return; }
     k.alpha = make_double2(k.zz / t[0], 0.0);
   }
@@ -449,6 +455,7 @@ __global__ void k_norm_s(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
   if (last_block_totals<1>(acc, rb, b, t) && threadIdx.x == 0) {
     KState& k = ks[b];
     if (k.done) return;
+    k.mv += 1;  // z = A^H r
     k.beta = make_double2(t[0] / k.zz, 0.0);
     k.zz = t[0];
   }
@@ -505,6 +512,7 @@ __global__ void k_b2_init(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3, b
     k.beta = make_double2(0.0, 0.0);
     k.tol2 = tol * tol * t[0];
     k.it = 0;
+    k.mv = 0;
     k.done = (t[0] == 0.0 || t[1] <= k.tol2) ? 1 : 0;
   }
 }
@@ -541,6 +549,7 @@ __global__ void k_b2_alpha(KrylovVecs<C> kv, KState* ks, RedBuf rb, int j, int64
   if (last_block_totals<2>(acc, rb, b, t) && threadIdx.x == 0) {
     KState& k = ks[b];
     if (k.done) return;
+    k.mv += 1;  // u_{j+1} = A u_j
     const double2 g = make_double2(t[0], t[1]);
     if (g.x == 0.0 && g.y == 0.0) { k.done = 2; return; }
     k.alpha = cdiv(k.rho, g);
@@ -579,6 +588,7 @@ __global__ void k_b2_beta(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
   if (last_block_totals<2>(acc, rb, b, t) && threadIdx.x == 0) {
     KState& k = ks[b];
     if (k.done) return;
+    k.mv += 1;  // r1 = A r0
     const double2 rho1 = make_double2(t[0], t[1]);
     if (k.rho.x == 0.0 && k.rho.y == 0.0) { k.done = 2; return; }
     k.beta = cmuld(k.alpha, cdiv(rho1, k.rho));
@@ -610,6 +620,7 @@ __global__ void k_b2_gram(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
   if (last_block_totals<8>(acc, rb, b, t) && threadIdx.x == 0) {
     KState& k = ks[b];
     if (k.done) return;
+    k.mv += 1;  // r2 = A r1
     const double a = t[0], d = t[3];
     const double2 bb = make_double2(t[1], t[2]);  // <r1, r2>
     const double2 c1 = make_double2(t[4], t[5]), c2 = make_double2(t[6], t[7]);

@@ -157,14 +157,21 @@ Err make_site_target(const int32_t* ixyz, const int32_t* icomp, int64_t n, const
     }
   for (int a = 0; a < 3; ++a)
     if ((int64_t)hi[a] - lo[a] + 1 > 4096) return Err::make(DDA_EINVAL, "site list spans more than 4096 cells");
+  // x-fastest order by the box key; a list already in that order (as dda_get_sites returns it)
+  // is taken as is
+  std::vector<int64_t> keys(n);
+  bool sorted = true;
+  for (int64_t j = 0; j < n; ++j) {
+    keys[j] = (((int64_t)(ixyz[3 * j + 2] - lo[2]) * 4096 + (ixyz[3 * j + 1] - lo[1])) * 4096) + (ixyz[3 * j] - lo[0]);
+    if (j > 0 && keys[j] <= keys[j - 1]) sorted = false;
+  }
   std::vector<int64_t> order(n);
   for (int64_t j = 0; j < n; ++j) order[j] = j;
-  auto key = [&](int64_t j) {
-    return (((int64_t)(ixyz[3 * j + 2] - lo[2]) * 4096 + (ixyz[3 * j + 1] - lo[1])) * 4096) + (ixyz[3 * j] - lo[0]);
-  };
-  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return key(a) < key(b); });
-  for (int64_t j = 1; j < n; ++j)
-    if (key(order[j]) == key(order[j - 1])) return Err::make(DDA_EINVAL, "duplicate site in list");
+  if (!sorted) {
+    std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return keys[a] < keys[b]; });
+    for (int64_t j = 1; j < n; ++j)
+      if (keys[order[j]] == keys[order[j - 1]]) return Err::make(DDA_EINVAL, "duplicate site in list");
+  }
   out->ijk.resize(3 * n);
   out->comp.resize(3 * n);
   int maxc = 1;

@@ -172,8 +172,7 @@ class Context:
         self._check(fn(self._h, _ptr(ij), None if ic is None else _ptr(ic), ij.shape[0], _ptr(org),
                                          None if a1v is None else _ptr(a1v), None if a2v is None else _ptr(a2v)))
         self.n = ij.shape[0]
-        sites, _ = self.dda_get_sites()
-        self.box = tuple(int(v) for v in sites.max(axis=0) + 1)
+        self.box = tuple(int(ij[:, a].max()) - int(ij[:, a].min()) + 1 for a in range(3))
 
     def dda_get_sites(self):
         out = np.zeros((self.n, 3), dtype=np.int32)

@@ -2,6 +2,7 @@
 // set-up on the host (FP64), Green-tensor build, product A P, the batched
 // Krylov drivers (BiCGstab, CCG; complex64, complex128 or complex64 refined
 // against complex128 true residuals) and the observables.
+#include <algorithm>
 #include <array>
 #include <chrono>
 #include <thread>
@@ -100,6 +101,15 @@ struct dda_ctx {
   double2* d_F = nullptr;             // far-field sums
   double* d_fpart = nullptr;          // far-field partial sums
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // cached solver graphs (complex64, complex128)
+  // A captured iteration graph holds device pointers and launch parameters by value.  `gen`
+  // changes whenever a device buffer is (re)allocated or the launch schedule or geometry
+  // changes; a graph captured at the same generation for the same solver, iteration count,
+  // RHS count and vector length is replayed without a new capture.
+  unsigned long long gen = 1;
+  bool have_sched = false;  // g64/g128/t64/t128 describe the current grid
+  unsigned long long gexec_gen[2] = {0, 0};
+  long long gexec_key[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+  unsigned long long gexec_kernels[2] = {0, 0};
   int tuned_nrhs[2] = {0, 0};         // RHS count the current schedule was tuned for (c64, c128)
   bool forced_schedule = false;       // DDA_SCHEDULE fixed the schedule: no autotuning
   void* d_tunebuf = nullptr;          // operands of the autotuner's timed products
@@ -151,6 +161,7 @@ Err grow(dda_ctx* c, T** p, size_t bytes) {
   if (bytes == 0) return Err::Ok();
   DDA_CU(cudaMalloc((void**)p, bytes));
   cap = bytes;
+  c->gen++;
   return Err::Ok();
 }
 
@@ -212,12 +223,15 @@ Err upload_target(dda_ctx* c) {
   DDA_CU(cudaMemcpy(c->d_map, map.data(), sizeof(int32_t) * nbox, cudaMemcpyHostToDevice));
   DDA_CU(cudaMemcpy(c->d_ijk, t.ijk.data(), sizeof(int32_t) * 3 * n, cudaMemcpyHostToDevice));
   DDA_CU(cudaMemcpy(c->d_origin, t.origin, sizeof(double) * 3, cudaMemcpyHostToDevice));
+  const int64_t old_n = c->n;
+  const bool old_comp = c->comp_valid;
   c->comp_valid = false;
   if (t.ncomp > 1) {
     DDA_TRY(grow(c, &c->d_comp, 3 * n));
     DDA_CU(cudaMemcpy(c->d_comp, t.comp.data(), 3 * n, cudaMemcpyHostToDevice));
     c->comp_valid = true;
   }
+  if (old_n != n || old_comp != c->comp_valid) c->gen++;  // site count / composition pointer changed
   c->n = n;
   c->have_target = true;
   return Err::Ok();
@@ -395,8 +409,10 @@ template <typename C>
 Err apply_tune(dda_ctx* c, const dda::MvTune& t) {
   dda::MvTune& cur = (sizeof(C) == sizeof(float2)) ? c->t64 : c->t128;
   dda::Geom& g = (sizeof(C) == sizeof(float2)) ? c->g64 : c->g128;
+  const int ys = t.plane ? g.ny : g.py;
+  if (std::memcmp(&cur, &t, sizeof(t)) != 0 || g.ys != ys) c->gen++;  // a different launch schedule
   cur = t;
-  g.ys = t.plane ? g.ny : g.py;
+  g.ys = ys;
   return Err::Ok();
 }
 
@@ -588,7 +604,14 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
   }
   cudaGraphExec_t gexec = nullptr;
   unsigned long long graph_kernels = 0;
-  if (o.use_graph) {
+  const int gi = sizeof(C) == sizeof(float2) ? 0 : 1;
+  const long long gkey[4] = {o.solver, every, nrhs, (long long)n3};
+  const bool reuse = o.use_graph && c->gexec[gi] && c->gexec_gen[gi] == c->gen &&
+                     std::equal(gkey, gkey + 4, c->gexec_key[gi]);
+  if (reuse) {
+    gexec = c->gexec[gi];
+    graph_kernels = c->gexec_kernels[gi];
+  } else if (o.use_graph) {
     // capture `every` iterations; reuse the context's executable graph when only
     // parameters changed (cudaGraphExecUpdate), instantiate only when the topology did
     const unsigned long long before = dda::launches();
@@ -623,6 +646,9 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
     }
     cudaGraphDestroy(graph);
     gexec = cached;
+    c->gexec_gen[gi] = c->gen;
+    std::copy(gkey, gkey + 4, c->gexec_key[gi]);
+    c->gexec_kernels[gi] = graph_kernels;
   }
   std::vector<dda::KState> hk(nrhs);
   int it = 0;
@@ -919,7 +945,7 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
     // schedule: 3-pass when the plane fits in the opt-in shared memory
     int smax = 0;
     cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-    dda::MvTune t64, t128;
+    dda::MvTune t64{}, t128{};
     t64.g = 8; t128.g = 4;
     dda::Geom g64 = g, g128 = g;
     g64.ys = g.ny; g128.ys = g.ny;
@@ -931,8 +957,12 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
     // engine of fft.cuh), "fast5" (compile-time kernels, 5 passes), "plane512" / "plane768"
     // (compile-time kernels, fused plane pass where it exists), "cluster2" / "cluster4"
     // (complex64 plane pass split over a cluster of 2 or 4 CTAs where it fits)
+    // the same grid as the previous build keeps its tuned schedules (no new tuning, no new graph)
+    const bool same_grid = c->have_sched && c->g64.n == g.n && c->g64.nx == g.nx && c->g64.ny == g.ny &&
+                           c->g64.nz == g.nz && c->g64.px == g.px && c->g64.py == g.py && c->g64.pz == g.pz &&
+                           c->g64.ncomp == g.ncomp;
+    const bool prev_forced = c->forced_schedule;
     c->forced_schedule = false;
-    c->tuned_nrhs[0] = c->tuned_nrhs[1] = 0;
     if (const char* f = std::getenv("DDA_SCHEDULE")) {
       const std::string sched(f);
       if (sched == "generic") {
@@ -974,7 +1004,13 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
     }
     if (!t64.plane) g64.ys = g.py;
     if (!t128.plane) g128.ys = g.py;
-    c->g64 = g64; c->g128 = g128; c->t64 = t64; c->t128 = t128;
+    if (!(same_grid && !prev_forced && !c->forced_schedule)) {
+      // a different geometry or schedule invalidates the tuning and the captured iteration graphs
+      c->g64 = g64; c->g128 = g128; c->t64 = t64; c->t128 = t128;
+      c->tuned_nrhs[0] = c->tuned_nrhs[1] = 0;
+      c->gen++;
+      c->have_sched = true;
+    }
     const int64_t M = (int64_t)g.px * g.py * g.pz;
     e = grow(c, &c->d_ghat128, sizeof(double2) * 6 * M);
     if (e.ok()) e = grow(c, &c->d_ghat64, sizeof(float2) * 6 * M);
@@ -1047,6 +1083,7 @@ dda_status dda_set_polarizability(dda_ctx* c, int presc, const double* m_reim, i
       c->eps[m] = mm * mm;
     }
     c->presc = presc;
+    if (c->ncomp != ncomp) c->gen++;
     c->ncomp = ncomp;
     c->have_alpha = true;
     return DDA_OK;

@@ -461,6 +461,14 @@ def main():
                              "x_tile_rows": sched[5], "bulk_staged_plane": bool(sched[6]),
                              "x_components_per_cta": sched[7]},
                 "product_ms": float(np.sum(ms_pass))}
+    # the FP64-accurate product of the true residuals: complex128 on the FP64 units against
+    # double-float arithmetic on the FP32 units (the one the mixed solve uses where it exists)
+    fp64_products = {}
+    for nm, dt in (("complex128", D.DDA_C128), ("double_float", D.DDA_C128DF)):
+        try:
+            fp64_products[nm] = float(np.sum(D.dda_profile_matvec(ctx, nrhs, dt, iters=5)))
+        except D.DDAError as exc:
+            fp64_products[nm] = str(exc).splitlines()[0]
     flops = algorithmic_flops(len(ms_pass), box, pad, nrhs)
     tfl = flops[dom] / (ms_pass[dom] * 1e-3) / 1e12
     roofline["alu"] = {"bound": "fp32 issue", "achieved": tfl, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -489,6 +497,7 @@ def main():
             "speedup_vs_plain_fp64": plain_ms / ms_step,
             "iterations": [r["iters"] for r in reps], "plain_iterations": [r["iters"] for r in preps],
             "true_rel_resid": [r["true_rel_resid"] for r in reps],
+            "true_residual_product_ms": fp64_products,
             "Q": {"Qext": q[:, 0].tolist(), "Qabs": q[:, 1].tolist(), "Qsca": q[:, 2].tolist()},
             "e2e": {"value": e2e_value, "unit": "matvecs/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms / args.steps},

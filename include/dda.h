@@ -59,7 +59,15 @@ typedef enum {
   DDA_EUNSUPPORTED = 7   /* valid request this build does not implement */
 } dda_status;
 
-enum { DDA_C64 = 1, DDA_C128 = 2 };
+/* Element types.  DDA_C128DF is not a storage type: products asked for in it
+ * read and write complex128 vectors but compute in double-float arithmetic
+ * (each FP64 value carried as an unevaluated sum of two floats, 48 significand
+ * bits) on the FP32 units, because GB300's FP64 rate is 1/64 of its FP32 rate.
+ * Its results agree with the complex128 product to about 1e-13 of the norm of
+ * the result; it exists where the complex128 schedule has compile-time kernels
+ * (dda_schedule_info(DDA_C128) info[1] = 1 and info[0] = 5), else the calls
+ * that take it return DDA_EUNSUPPORTED. */
+enum { DDA_C64 = 1, DDA_C128 = 2, DDA_C128DF = 3 };
 /* Target shapes (guide, "Target Generation"); SHPAR in lattice units. */
 enum { DDA_ELLIPSOID = 1, DDA_RCTGLPRSM = 2, DDA_CYLINDER1 = 3, DDA_HEX_PRISM = 4 };
 /* Polarizability prescriptions (guide, "Dipole Polarizabilities"). */
@@ -162,7 +170,8 @@ DDA_API dda_status dda_set_polarizability(dda_ctx *ctx, int prescription, const 
 DDA_API dda_status dda_get_inv_alpha(dda_ctx *ctx, double *out);
 
 /* ap_dev = A p_dev for the first nrhs right-hand sides, both [nrhs][3][N] of
- * dtype DDA_C64 or DDA_C128 (may not alias).  Enqueue only. */
+ * dtype DDA_C64 or DDA_C128 (may not alias); DDA_C128DF takes and returns
+ * complex128 vectors and computes in double-float arithmetic.  Enqueue only. */
 DDA_API dda_status dda_matvec(dda_ctx *ctx, const void *p_dev, void *ap_dev, int nrhs, int dtype);
 
 /* ap_dev = A p_dev like dda_matvec, but without allocating any memory.
@@ -206,7 +215,10 @@ typedef struct {
                             products of RHS whose solve has finished) */
   int outer;             /* MIXED: refinement steps (true-residual evaluations) */
   int converged;         /* 1 if the true residual met tol */
-  double true_rel_resid; /* |E - A P| / |E| evaluated with the FP64 product at exit */
+  double true_rel_resid; /* |E - A P| / |E| evaluated with an FP64-accurate product at exit: the
+                            complex128 product, or for precisions C64 and MIXED at tol >= 1e-10 the
+                            double-float one (DDA_C128DF) where it exists (environment variable
+                            DDA_RESIDUAL=fp64 forces the complex128 product) */
   double normal_eq_ratio;/* guide's eq. err_tol: |A^H A P - A^H E| / |A^H E| (NAN if not computed) */
 } dda_solve_report;
 

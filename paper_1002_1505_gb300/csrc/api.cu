@@ -60,6 +60,11 @@ struct dda_ctx {
   float2* d_ghat64 = nullptr;
   double2* d_tw128[3] = {nullptr, nullptr, nullptr};
   float2* d_tw64[3] = {nullptr, nullptr, nullptr};
+  // double-float copies for the FP64-accurate product on FP32 units (built when the
+  // complex128 schedule has compile-time kernels)
+  dda::dfp::dfc* d_ghatdf = nullptr;
+  dda::dfp::dfc* d_twdf[3] = {nullptr, nullptr, nullptr};
+  bool ghatdf_valid = false;
 
   // polarizability
   bool have_alpha = false;
@@ -67,6 +72,7 @@ struct dda_ctx {
   std::vector<cd> ia;                 // nrhs x ncomp x 3
   double2* d_ia128 = nullptr;
   float2* d_ia64 = nullptr;
+  dda::dfp::dfc* d_iadf = nullptr;
   std::vector<cd> eps;                // permittivity m^2 per composition
   float2* d_eps = nullptr;
   float2* d_nnv = nullptr;            // residual-loss vectors (three complex64 [nrhs][3][N])
@@ -393,6 +399,39 @@ Err matvec(dda_ctx* c, const C* p, C* ap, int nrhs, int rhs0, bool conj, const d
                                   rhs0 + b0, conj, c->stream));
   }
   return Err::Ok();
+}
+
+// The FP64-accurate product in double-float arithmetic (complex128 in and out) on the
+// complex128 schedule's compile-time 5-pass kernels; DDA_EUNSUPPORTED where that schedule
+// does not exist.
+bool df_available(dda_ctx* c) {
+  return c->t128.fast && !c->t128.plane && c->ghatdf_valid && c->d_iadf && c->d_twdf[0] && c->d_twdf[1] &&
+         c->d_twdf[2];
+}
+Err matvec_df(dda_ctx* c, const double2* p, double2* ap, int nrhs, int rhs0, bool conj) {
+  if (!df_available(c))
+    return Err::make(DDA_EUNSUPPORTED, "no double-float product for this grid (needs the compile-time 5-pass schedule)");
+  int cap = 0;
+  DDA_TRY(ensure_work<double2>(c, nrhs, &cap));
+  const int64_t n3 = 3 * c->n;
+  dda::MvData<dda::dfp::dfc> d{c->d_map, c->comp_valid ? c->d_comp : nullptr, c->d_ghatdf, c->d_iadf,
+                               c->d_twdf[0], c->d_twdf[1], c->d_twdf[2],
+                               reinterpret_cast<dda::dfp::dfc*>(c->d_w128)};
+  d.fault = c->d_fault;
+  for (int b0 = 0; b0 < nrhs; b0 += cap) {
+    const int nb = std::min(cap, nrhs - b0);
+    DDA_TRY(dda::launch_matvec_df(Sel<double2>::geom(c), d, c->t128, p + b0 * n3, ap + b0 * n3, nb, rhs0 + b0, conj,
+                                  c->stream));
+  }
+  return Err::Ok();
+}
+// True residuals of the mixed and complex64 solves use the double-float product when the
+// tolerance leaves it a margin of 100 or more (its error is about 1e-12 of |E|) and the grid
+// has it; DDA_RESIDUAL=fp64 keeps them on the FP64 units.
+bool df_residuals(dda_ctx* c, double tol) {
+  if (tol < 1e-10 || !df_available(c)) return false;
+  const char* f = std::getenv("DDA_RESIDUAL");
+  return !(f && std::string(f) == "fp64");
 }
 
 // ------------------------------------------------------------------ autotuner
@@ -926,19 +965,26 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
     const double pi = 3.14159265358979323846;
     for (int a = 0; a < 3; ++a) {
       const int L = P[a];
-      if (c->tw_len[a] == L && c->d_tw128[a] && c->d_tw64[a]) continue;
+      if (c->tw_len[a] == L && c->d_tw128[a] && c->d_tw64[a] && c->d_twdf[a]) continue;
       std::vector<double2> t128(L);
       std::vector<float2> t64(L);
+      std::vector<dda::dfp::dfc> tdf(L);
       for (int j = 0; j < L; ++j) {
         const double ang = -2.0 * pi * (double)j / (double)L;
         t128[j] = make_double2(std::cos(ang), std::sin(ang));
         t64[j] = make_float2((float)t128[j].x, (float)t128[j].y);
+        tdf[j].x = dda::dfp::df(t128[j].x);
+        tdf[j].y = dda::dfp::df(t128[j].y);
       }
       e = grow(c, &c->d_tw128[a], sizeof(double2) * L);
       if (e.ok()) e = grow(c, &c->d_tw64[a], sizeof(float2) * L);
+      if (e.ok()) e = grow(c, &c->d_twdf[a], sizeof(dda::dfp::dfc) * L);
       if (!e.ok()) return fail(c, e);
       e = cuda_ok(cudaMemcpy(c->d_tw128[a], t128.data(), sizeof(double2) * L, cudaMemcpyHostToDevice), "twiddle upload");
       if (e.ok()) e = cuda_ok(cudaMemcpy(c->d_tw64[a], t64.data(), sizeof(float2) * L, cudaMemcpyHostToDevice), "twiddle upload");
+      if (e.ok())
+        e = cuda_ok(cudaMemcpy(c->d_twdf[a], tdf.data(), sizeof(dda::dfp::dfc) * L, cudaMemcpyHostToDevice),
+                    "twiddle upload");
       if (!e.ok()) return fail(c, e);
       c->tw_len[a] = L;
     }
@@ -1015,6 +1061,10 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
     e = grow(c, &c->d_ghat128, sizeof(double2) * 6 * M);
     if (e.ok()) e = grow(c, &c->d_ghat64, sizeof(float2) * 6 * M);
     if (e.ok()) e = grow(c, &c->d_gscratch, sizeof(double2) * 6 * M);
+    // the double-float copy exists only where the double-float product can run
+    c->ghatdf_valid = false;
+    const bool want_df = c->t128.fast && !c->t128.plane;
+    if (e.ok() && want_df) e = grow(c, &c->d_ghatdf, sizeof(dda::dfp::dfc) * 6 * M);
     if (!e.ok()) return fail(c, e);
     // frequency-order tables of the Green build (kept while px, py stay the same)
     if (e.ok() && (c->gperm_key[0] != g.px || c->gperm_key[1] != g.py || !c->d_gperm)) {
@@ -1028,8 +1078,9 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
     }
     if (!e.ok()) return fail(c, e);
     e = dda::build_green(g64, c->kd, c->d_tw128[0], c->d_tw128[1], c->d_tw128[2], c->d_gperm, c->d_gscratch,
-                         c->d_ghat128, c->d_ghat64, c->stream);
+                         c->d_ghat128, c->d_ghat64, want_df ? c->d_ghatdf : nullptr, c->stream);
     if (!e.ok()) return fail(c, e);
+    c->ghatdf_valid = want_df;
     c->have_green = true;
     return DDA_OK;
   } catch (const std::bad_alloc&) {
@@ -1060,19 +1111,26 @@ dda_status dda_set_polarizability(dda_ctx* c, int presc, const double* m_reim, i
     }
     std::vector<double2> h128(ia.size());
     std::vector<float2> h64(ia.size());
+    std::vector<dda::dfp::dfc> hdf(ia.size());
     for (size_t i = 0; i < ia.size(); ++i) {
       h128[i] = make_double2(ia[i].real(), ia[i].imag());
       h64[i] = make_float2((float)ia[i].real(), (float)ia[i].imag());
+      hdf[i].x = dda::dfp::df(ia[i].real());
+      hdf[i].y = dda::dfp::df(ia[i].imag());
     }
     drop_alpha(c);
     if (!c->host_only) {
       e = grow(c, &c->d_ia128, sizeof(double2) * ia.size());
       if (e.ok()) e = grow(c, &c->d_ia64, sizeof(float2) * ia.size());
+      if (e.ok()) e = grow(c, &c->d_iadf, sizeof(dda::dfp::dfc) * ia.size());
       if (!e.ok()) return fail(c, e);
       e = cuda_ok(cudaMemcpy(c->d_ia128, h128.data(), sizeof(double2) * ia.size(), cudaMemcpyHostToDevice),
                   "polarizability upload");
       if (e.ok())
         e = cuda_ok(cudaMemcpy(c->d_ia64, h64.data(), sizeof(float2) * ia.size(), cudaMemcpyHostToDevice),
+                    "polarizability upload");
+      if (e.ok())
+        e = cuda_ok(cudaMemcpy(c->d_iadf, hdf.data(), sizeof(dda::dfp::dfc) * ia.size(), cudaMemcpyHostToDevice),
                     "polarizability upload");
       if (!e.ok()) return fail(c, e);
     }
@@ -1116,8 +1174,11 @@ dda_status dda_matvec(dda_ctx* c, const void* p, void* ap, int nrhs, int dtype) 
   } else if (dtype == DDA_C128) {
     e = ensure_tuned<double2>(c, nrhs);
     if (e.ok()) e = matvec<double2>(c, (const double2*)p, (double2*)ap, nrhs, 0, false);
+  } else if (dtype == DDA_C128DF) {
+    e = ensure_tuned<double2>(c, nrhs);
+    if (e.ok()) e = matvec_df(c, (const double2*)p, (double2*)ap, nrhs, 0, false);
   } else {
-    return fail(c, Err::make(DDA_EINVAL, "dtype must be DDA_C64 or DDA_C128"));
+    return fail(c, Err::make(DDA_EINVAL, "dtype must be DDA_C64, DDA_C128 or DDA_C128DF"));
   }
   return e.ok() ? DDA_OK : fail(c, e);
 }
@@ -1137,10 +1198,13 @@ Err kvec_alloc(dda_ctx* c, dda::KrylovVecs<C>* kv, int nvec_extra) {
 }
 
 // true residual (FP64 product): |E - A P|^2 and |E|^2 per RHS
-Err true_residual(dda_ctx* c, const double2* p, double2* scratch_ax, double2* scratch_r, std::vector<double>* rel) {
+// (use_df: the product in double-float arithmetic, matvec_df)
+Err true_residual(dda_ctx* c, const double2* p, double2* scratch_ax, double2* scratch_r, std::vector<double>* rel,
+                  bool use_df) {
   const int nrhs = c->nrhs;
   const int64_t n3 = 3 * c->n;
-  DDA_TRY(matvec<double2>(c, p, scratch_ax, nrhs, 0, false));
+  if (use_df) DDA_TRY(matvec_df(c, p, scratch_ax, nrhs, 0, false));
+  else DDA_TRY(matvec<double2>(c, p, scratch_ax, nrhs, 0, false));
   dda::RedBuf rb = redbuf(c, nrhs, n3);
   DDA_TRY(ensure_part(c, sizeof(double) * (size_t)rb.nblk * nrhs * dda::kRedSlots));
   rb.part = c->d_part;
@@ -1205,6 +1269,7 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
     };
     bool timed_out = false;
     std::vector<double> rel;
+    const bool df_res = o.precision != DDA_PREC_C128 && df_residuals(c, o.tol);
     // scratch c128 pair for true residuals (2 vectors)
     e = grow(c, &c->d_sc, sizeof(double2) * 2 * el);
     if (!e.ok()) return fail(c, e);
@@ -1259,7 +1324,7 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
           if (!e.ok()) break;
           rel.assign(nrhs, 1.0);
         } else {
-          e = true_residual(c, P, sc, r128, &rel);
+          e = true_residual(c, P, sc, r128, &rel, df_res);
           add_all(1);
           if (!e.ok()) break;
         }
@@ -1293,7 +1358,7 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
     if (!e.ok()) { cleanup(); return fail(c, e); }
     // final true residual in FP64 (for MIXED it was computed by the loop's last pass)
     if (o.precision != DDA_PREC_MIXED || rel.empty()) {
-      e = true_residual(c, P, sc, sc + el, &rel);
+      e = true_residual(c, P, sc, sc + el, &rel, df_res);
       add_all(1);
       if (!e.ok()) { cleanup(); return fail(c, e); }
     }
@@ -1524,7 +1589,7 @@ dda_status dda_profile_matvec(dda_ctx* c, int nrhs, int dtype, int iters, double
   if (!c->have_alpha || !c->have_green)
     return fail(c, Err::make(DDA_ESTATE, "set target, incidence, Green tensor and alpha first"));
   if (nrhs < 1 || nrhs > c->nrhs) return fail(c, Err::make(DDA_EINVAL, "nrhs out of range"));
-  if (dtype != DDA_C64 && dtype != DDA_C128) return fail(c, Err::make(DDA_EINVAL, "bad dtype"));
+  if (dtype != DDA_C64 && dtype != DDA_C128 && dtype != DDA_C128DF) return fail(c, Err::make(DDA_EINVAL, "bad dtype"));
   Err e = set_dev(c);
   if (!e.ok()) return fail(c, e);
   e = (dtype == DDA_C64) ? ensure_tuned<float2>(c, nrhs) : ensure_tuned<double2>(c, nrhs);
@@ -1545,6 +1610,7 @@ dda_status dda_profile_matvec(dda_ctx* c, int nrhs, int dtype, int iters, double
   for (int it = 0; it < iters && e.ok(); ++it) {
     dda::set_pass_events(ev);
     if (dtype == DDA_C64) e = matvec<float2>(c, (const float2*)p, (float2*)ap, nrhs, 0, false);
+    else if (dtype == DDA_C128DF) e = matvec_df(c, (const double2*)p, (double2*)ap, nrhs, 0, false);
     else e = matvec<double2>(c, (const double2*)p, (double2*)ap, nrhs, 0, false);
     dda::set_pass_events(nullptr);
     if (!e.ok()) break;
@@ -1752,7 +1818,7 @@ dda_status dda_selftest_bulk_wait(int device, int32_t* gave_up) {
 dda_status dda_schedule_info(dda_ctx* c, int dtype, int32_t info[8]) {
   if (!c || !info) return DDA_EINVAL;
   if (!c->have_green) return fail(c, Err::make(DDA_ESTATE, "build the Green tensor first"));
-  if (dtype != DDA_C64 && dtype != DDA_C128) return fail(c, Err::make(DDA_EINVAL, "bad dtype"));
+  if (dtype != DDA_C64 && dtype != DDA_C128 && dtype != DDA_C128DF) return fail(c, Err::make(DDA_EINVAL, "bad dtype"));
   const dda::MvTune& t = dtype == DDA_C64 ? c->t64 : c->t128;
   info[0] = t.plane ? 3 : 5;
   info[1] = t.fast ? 1 : 0;

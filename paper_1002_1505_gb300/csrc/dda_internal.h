@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/dda.h"
+#include "df.cuh"
 #include "fft.cuh"
 
 namespace dda {
@@ -133,6 +134,12 @@ bool plane_bulk_ok_c64(const Geom& g, int smax);
 void plane_bulk_optin_c64(int smax);
 void cluster_optin_c64(int smax);
 void fast_optin_c128(int smax);
+// The product with complex128 vectors in and out and double-float arithmetic (df.cuh) inside:
+// the compile-time 5-pass kernels of the complex128 schedule t (matvec_fast_df.cu).  Returns
+// DDA_EUNSUPPORTED when t is not a compile-time 5-pass schedule.
+Err launch_matvec_df(const Geom& g, const MvData<dfp::dfc>& d, const MvTune& t, const double2* p, double2* ap,
+                     int nrhs, int rhs0, bool conj, cudaStream_t st);
+void fast_optin_df(int smax);
 // Does a fast schedule exist for this grid (all lengths instantiated, tiles fit)?  Sets t.fast and t.plane.
 void choose_fast_schedule(const Geom& g, bool c64, int smax, MvTune* t);
 // x-pass tile heights (y rows per CTA) of the compile-time kernels: the default for a length, and
@@ -156,11 +163,12 @@ void sub_launches(unsigned long long n);
 constexpr size_t kNoAllocScratchBytes = 32ull << 20;
 Err noalloc_scratch(int device, void** out);
 
-// Green tensor: fill + FP64 FFT + pack into ghat128 / ghat64.
+// Green tensor: fill + FP64 FFT + pack into ghat128 / ghat64 / ghatdf (double-float, may be null).
 // storage <-> natural frequency tables the Green build needs (natx[px] | naty[py] | stx[px/2+1] | sty[py/2+1])
 void green_perm_tables(const Geom& g, std::vector<int32_t>* out);
 Err build_green(const Geom& g, double kd, const double2* twx, const double2* twy, const double2* twz,
-                const int32_t* perm, double2* gw, double2* ghat128, float2* ghat64, cudaStream_t st);
+                const int32_t* perm, double2* gw, double2* ghat128, float2* ghat64, dfp::dfc* ghatdf,
+                cudaStream_t st);
 
 // Generic batched FFT over rows/strides (used by tests of the engine and the Green build).
 template <typename C>

@@ -399,7 +399,8 @@ __global__ void k_green_expand_z(Geom g, const int32_t* __restrict__ sty, const 
 // ghat[kx][kz][ky][6] (storage positions) = f[c][kz][ky'][kx'] / M, with kx', ky' the natural
 // frequencies folded into [0, P/2] and the sign of the parities of the folds
 __global__ void k_green_pack(Geom g, const int32_t* __restrict__ natx, const int32_t* __restrict__ naty,
-                             const double2* __restrict__ f, double2* __restrict__ g128, float2* __restrict__ g64) {
+                             const double2* __restrict__ f, double2* __restrict__ g128, float2* __restrict__ g64,
+                             dfp::dfc* __restrict__ gdf) {
   const int64_t M = (int64_t)g.px * g.py * g.pz;
   const int hx1 = g.px / 2 + 1, hy1 = g.py / 2 + 1;
   const int64_t P = (int64_t)hx1 * hy1, F = P * g.pz;
@@ -420,6 +421,7 @@ __global__ void k_green_pack(Geom g, const int32_t* __restrict__ natx, const int
     const double2 w = make_double2(v.x * sc, v.y * sc);
     g128[o] = w;
     g64[o] = make_float2((float)w.x, (float)w.y);
+    if (gdf) gdf[o] = dfp::from_c128(w);
   }
 }
 
@@ -603,6 +605,7 @@ void init_kernel_attrs() {
   cluster_optin_c64(v);
   plane_bulk_optin_c64(v);
   fast_optin_c128(v);
+  fast_optin_df(v);
 }
 
 void green_perm_tables(const Geom& g, std::vector<int32_t>* out) {
@@ -623,7 +626,8 @@ void green_perm_tables(const Geom& g, std::vector<int32_t>* out) {
 }
 
 Err build_green(const Geom& g, double kd, const double2* twx, const double2* twy, const double2* twz,
-                const int32_t* perm, double2* gw, double2* ghat128, float2* ghat64, cudaStream_t st) {
+                const int32_t* perm, double2* gw, double2* ghat128, float2* ghat64, dfp::dfc* ghatdf,
+                cudaStream_t st) {
   const int64_t M = (int64_t)g.px * g.py * g.pz;
   const int hx1 = g.px / 2 + 1, hy1 = g.py / 2 + 1, hz1 = g.pz / 2 + 1;
   const int64_t Q = (int64_t)g.px * hy1 * hz1, T = (int64_t)hx1 * g.py * hz1, F = (int64_t)hx1 * hy1 * g.pz;
@@ -656,7 +660,7 @@ Err build_green(const Geom& g, double kd, const double2* twx, const double2* twy
   if (e.ok())
     e = fft_strided<double2>(gw, g.pz, (int64_t)hx1 * hy1, (int64_t)hx1 * hy1, 6, F, g.plz, twz, false, st);
   if (e.ok()) {
-    k_green_pack<<<nblk(6 * M), 256, 0, st>>>(g, d_natx, d_naty, gw, ghat128, ghat64);
+    k_green_pack<<<nblk(6 * M), 256, 0, st>>>(g, d_natx, d_naty, gw, ghat128, ghat64, ghatdf);
     if (cudaGetLastError() != cudaSuccess) e = Err::make(DDA_ECUDA, "Green pack failed");
   }
   g_launches += 4;

@@ -10,6 +10,7 @@
 
 #include "bulk.cuh"
 #include "dda_internal.h"
+#include "df.cuh"
 #include "fft2.cuh"
 
 namespace dda {
@@ -72,7 +73,8 @@ __device__ __forceinline__ void copy_tw(C* dst, const C* src, int L) {
 // grid (ceil(ny/TY), nz, nrhs * 3/NC): NC components (1 or 3) of TY y rows per CTA.
 // smem: tw[PX] | in[NC*TY][ip] | out[NC*PX][TY]
 template <typename C, int PX, int TY, int NC = 3>
-__global__ void __launch_bounds__(256) k_x_fwd(Geom g, MvData<C> d, const C* __restrict__ p, bool conj, int ip) {
+__global__ void __launch_bounds__(256) k_x_fwd(Geom g, MvData<C> d, const typename Io<C>::t* __restrict__ p,
+                                               bool conj, int ip) {
   constexpr int RA = Shape<PX>::RA, LB = Shape<PX>::LB, H = Shape<PX>::H;
   static_assert(NC == 1 || NC == 3, "one or three components per CTA");
   extern __shared__ unsigned char smem_raw[];
@@ -93,7 +95,7 @@ __global__ void __launch_bounds__(256) k_x_fwd(Geom g, MvData<C> d, const C* __r
     if (y < g.ny) {
       const int32_t idx = __ldg(d.map + ((int64_t)z * g.ny + y) * g.nx + x);
       if (idx >= 0) {
-        v = p[((int64_t)b * 3 + c0 + cl) * g.n + idx];
+        v = io_get<C>(p[((int64_t)b * 3 + c0 + cl) * g.n + idx]);
         if (conj) v = conjc(v);
       }
     }
@@ -139,8 +141,8 @@ __global__ void __launch_bounds__(256) k_x_fwd(Geom g, MvData<C> d, const C* __r
 // ------------------------------------------------------------------ x inverse + alpha^{-1} P + scatter
 // grid and shared memory as k_x_fwd
 template <typename C, int PX, int TY, int NC = 3>
-__global__ void __launch_bounds__(256) k_x_inv(Geom g, MvData<C> d, const C* __restrict__ p, C* __restrict__ ap,
-                                               int rhs0, bool conj, int ip) {
+__global__ void __launch_bounds__(256) k_x_inv(Geom g, MvData<C> d, const typename Io<C>::t* __restrict__ p,
+                                               typename Io<C>::t* __restrict__ ap, int rhs0, bool conj, int ip) {
   constexpr int RA = Shape<PX>::RA, LB = Shape<PX>::LB, H = Shape<PX>::H;
   static_assert(NC == 1 || NC == 3, "one or three components per CTA");
   extern __shared__ unsigned char smem_raw[];
@@ -203,10 +205,10 @@ __global__ void __launch_bounds__(256) k_x_inv(Geom g, MvData<C> d, const C* __r
     const int c = c0 + cl;
     const int64_t o = ((int64_t)b * 3 + c) * g.n + idx;
     const int cc = d.comp ? d.comp[3 * idx + c] : 0;  // composition of axis c
-    C pv = p[o];
+    C pv = io_get<C>(p[o]);
     if (conj) pv = conjc(pv);
     const C res = cadd(in[(cl * TY + t) * ip + x], cmul(ia[cc * 3 + c], pv));
-    ap[o] = conj ? conjc(res) : res;
+    ap[o] = io_put<C>(conj ? conjc(res) : res);
   }
 }
 
@@ -694,7 +696,7 @@ Err with_x(int nc, int ty, F&& f) {
 }
 
 template <typename C>
-Err launch_x_fwd(const Geom& g, const MvData<C>& d, const MvTune& t, const C* p, int nrhs, bool conj,
+Err launch_x_fwd(const Geom& g, const MvData<C>& d, const MvTune& t, const typename Io<C>::t* p, int nrhs, bool conj,
                  cudaStream_t st) {
   const int NC = x_nc_pick(t);
   const int TY = x_ty_pick(t, sizeof(C), g.px);
@@ -718,8 +720,8 @@ Err launch_x_fwd(const Geom& g, const MvData<C>& d, const MvTune& t, const C* p,
 }
 
 template <typename C>
-Err launch_x_inv(const Geom& g, const MvData<C>& d, const MvTune& t, const C* p, C* ap, int nrhs, int rhs0,
-                 bool conj, cudaStream_t st) {
+Err launch_x_inv(const Geom& g, const MvData<C>& d, const MvTune& t, const typename Io<C>::t* p,
+                 typename Io<C>::t* ap, int nrhs, int rhs0, bool conj, cudaStream_t st) {
   const int NC = x_nc_pick(t);
   const int TY = x_ty_pick(t, sizeof(C), g.px);
   const size_t sm = x_fast_smem<C>(g, TY, NC);
@@ -835,8 +837,8 @@ void optin_all(int smax) {
 
 // The whole product on the compile-time-length kernels (3-pass when t.plane, else 5-pass).
 template <typename C>
-Err launch_matvec_fast(const Geom& g, const MvData<C>& d, const MvTune& t, const C* p, C* ap, int nrhs, int rhs0,
-                       bool conj, cudaStream_t st) {
+Err launch_matvec_fast(const Geom& g, const MvData<C>& d, const MvTune& t, const typename Io<C>::t* p,
+                       typename Io<C>::t* ap, int nrhs, int rhs0, bool conj, cudaStream_t st) {
   int pass = 0;
   mark_pass(pass++, st);
   DDA_TRY(launch_x_fwd<C>(g, d, t, p, nrhs, conj, st));

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("DDA_LIB", os.path.join(_HERE, "libdda.so"))
 
 DDA_OK, DDA_EINVAL, DDA_ENOMEM, DDA_ECUDA, DDA_ENOCONV, DDA_ETIMEOUT, DDA_ESTATE, DDA_EUNSUPPORTED = range(8)
-DDA_C64, DDA_C128 = 1, 2
+DDA_C64, DDA_C128, DDA_C128DF = 1, 2, 3  # DDA_C128DF: complex128 vectors, double-float arithmetic
 SHAPES = {"ELLIPSOID": 1, "RCTGLPRSM": 2, "CYLINDER1": 3, "HEX_PRISM": 4}
 PRESCRIPTIONS = {"CM": 1, "LATTDR": 2, "GKDLDR": 3}
 SOLVERS = {"BICGSTAB": 1, "CCG": 2, "BICGSTAB2": 3}
@@ -213,7 +213,7 @@ class Context:
     # ---------------------------------------------------------------- device work
     def _dev_check(self, t, dtype_code):
         import torch
-        want = torch.complex64 if dtype_code == DDA_C64 else torch.complex128
+        want = torch.complex64 if dtype_code == DDA_C64 else torch.complex128  # C128 and C128DF
         if not t.is_cuda or t.dtype != want or not t.is_contiguous():
             raise DDAError(DDA_EINVAL, f"expected a contiguous {want} CUDA tensor")
 
@@ -221,9 +221,15 @@ class Context:
         self._dev_check(e, dtype)
         self._check(LIB.dda_incident_field(self._h, ctypes.c_void_p(e.data_ptr()), dtype))
 
-    def dda_matvec(self, p, ap, nrhs: Optional[int] = None):
+    def dda_matvec(self, p, ap, nrhs: Optional[int] = None, double_float: bool = False):
+        """ap = A p (dtype of p); double_float=True computes a complex128 product in
+        double-float arithmetic (DDA_C128DF)."""
         import torch
         dt = DDA_C64 if p.dtype == torch.complex64 else DDA_C128
+        if double_float:
+            if dt != DDA_C128:
+                raise DDAError(DDA_EINVAL, "the double-float product takes complex128 vectors")
+            dt = DDA_C128DF
         self._dev_check(p, dt)
         self._dev_check(ap, dt)
         nr = self.nrhs if nrhs is None else nrhs

@@ -107,6 +107,59 @@ def test_matvec_fast_kernels_match_direct_sum(D, w, pad):
             assert err <= tol, (w.name, dt, b, err)
 
 
+@pytest.mark.parametrize("w,pad", FAST_PADS, ids=[w.name for w, _ in FAST_PADS])
+def test_double_float_product_matches_direct_sum(D, w, pad):
+    """complex128 vectors, double-float arithmetic (DDA_C128DF): within 1e-12 of the oracle's
+    direct sum and of the complex128 product (48-bit significands, error ~1e-13 of |A P|)."""
+    ctx = _ctx(D, w, pad)
+    prob = _oracle_problem(w)
+    p = _rand_p(ctx.nrhs, ctx.n, 8, torch.complex128)
+    ap_df = torch.empty_like(p)
+    ap_64 = torch.empty_like(p)
+    ctx.dda_matvec(p, ap_df, double_float=True)
+    ctx.dda_matvec(p, ap_64)
+    torch.cuda.synchronize()
+    pn = p.cpu().numpy()
+    got = ap_df.cpu().numpy()
+    fp64 = ap_64.cpu().numpy()
+    for b in range(ctx.nrhs):
+        ref = odda.apply_a(prob, b, pn[b], "direct")
+        assert np.linalg.norm(got[b] - ref) / np.linalg.norm(ref) <= 1e-12, (w.name, b)
+        assert np.linalg.norm(got[b] - fp64[b]) / np.linalg.norm(fp64[b]) <= 1e-12, (w.name, b)
+
+
+def test_double_float_product_needs_compile_time_schedule(D, monkeypatch):
+    monkeypatch.setenv("DDA_SCHEDULE", "generic")
+    w, pad = FAST_PADS[0]
+    ctx = _ctx(D, w, pad)
+    p = _rand_p(ctx.nrhs, ctx.n, 8, torch.complex128)
+    with pytest.raises(D.DDAError, match="DDA_EUNSUPPORTED"):
+        ctx.dda_matvec(p, torch.empty_like(p), double_float=True)
+    # the solve still runs: its true residuals fall back to the complex128 product
+    p = torch.zeros_like(p)
+    reps, _ = ctx.dda_solve(p, precision="MIXED", tol=1e-6, maxit=500)
+    assert all(r["converged"] for r in reps)
+
+
+def test_double_float_true_residuals_are_fp64_accurate(D):
+    """A mixed solve to 1e-8 takes its true residuals from the double-float product; the residual it
+    reports matches |E - A P| / |E| recomputed with the complex128 product."""
+    w = W.ELLIPSOID64
+    ctx = _ctx(D, w)
+    assert D.dda_schedule_info(ctx, D.DDA_C128)[:2] == (5, 1)
+    p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
+    reps, _ = ctx.dda_solve(p, precision="MIXED", tol=1e-8, maxit=3000)
+    e = torch.empty_like(p)
+    ctx.dda_incident_field(e)
+    ap = torch.empty_like(p)
+    ctx.dda_matvec(p, ap)
+    torch.cuda.synchronize()
+    for b, r in enumerate(reps):
+        rel = float(torch.linalg.vector_norm(e[b] - ap[b]) / torch.linalg.vector_norm(e[b]))
+        assert r["converged"] == 1 and rel <= 1e-8, (b, rel)
+        assert abs(r["true_rel_resid"] - rel) <= 1e-11, (b, r["true_rel_resid"], rel)
+
+
 @pytest.mark.parametrize("sched", ["cluster2", "cluster4"])
 @pytest.mark.parametrize("w,pad", FAST_PADS[:3], ids=[w.name for w, _ in FAST_PADS[:3]])
 def test_cluster_plane_matches_direct_sum(D, monkeypatch, w, pad, sched):
@@ -276,17 +329,18 @@ def test_matvec_full_size_sampled_rows(D, w):
     rows = np.sort(rng.choice(ctx.n, 24, replace=False))
     rows = np.concatenate([[0, ctx.n - 1], rows])
     rhs = [0, ctx.nrhs - 1]
-    for dt, tol in ((torch.complex64, 1e-5), (torch.complex128, 1e-12)):
+    for dt, tol, dfl in ((torch.complex64, 1e-5, False), (torch.complex128, 1e-12, False),
+                         (torch.complex128, 1e-12, True)):
         p = _rand_p(ctx.nrhs, ctx.n, 6, dt)
         ap = torch.empty_like(p)
-        ctx.dda_matvec(p, ap)
+        ctx.dda_matvec(p, ap, double_float=dfl)
         torch.cuda.synchronize()
         for b in rhs:
             pb = p[b].cpu().numpy().astype(np.complex128)
             ref = oint.matvec_direct(prob.target.r, prob.kd, prob.rhs[b].inv_alpha, pb, rows=rows)
             got = ap[b].cpu().numpy().astype(np.complex128)[:, rows]
             err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-            assert err <= tol, (dt, b, err)
+            assert err <= tol, (dt, dfl, b, err)
 
 
 def test_matvec_large_hexprism_sampled_rows(D):

@@ -22,6 +22,7 @@ def main():
                     help="pin the product schedule (generic, fast5, plane512, plane768, cluster2, cluster4)")
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--c128", action="store_true")
+    ap.add_argument("--df", action="store_true", help="complex128 product in double-float arithmetic")
     args = ap.parse_args()
     if args.schedule:
         os.environ["DDA_SCHEDULE"] = args.schedule
@@ -31,7 +32,7 @@ def main():
          "hexprism160": W.HEXPRISM160, "au_block": W.AU_BLOCK}[args.workload]
     ctx = D.Context(0)
     D.setup_workload(ctx, w)
-    dt = D.DDA_C128 if args.c128 else D.DDA_C64
+    dt = D.DDA_C128DF if args.df else (D.DDA_C128 if args.c128 else D.DDA_C64)
     ms = D.dda_profile_matvec(ctx, ctx.nrhs, dt, args.iters)
     info = D.dda_schedule_info(ctx, dt)
     print(f"{w.name}: N={ctx.n} box={ctx.box} rhs={ctx.nrhs} schedule(passes, fast, threads, tuned_nrhs, "

@@ -455,6 +455,11 @@ def test_worked_example_au_block_on_gpu(D):
         assert q[b, 3] == pytest.approx(g["Qpha"], rel=2e-4)
     for r, m in zip(rows, mm[0]):
         assert m[0, 0] == pytest.approx(r[2], rel=5e-4)
+    # backscattering efficiency Q_bk = (dC_sca/dOmega at theta = pi) / (pi a_eff^2) = S11(pi) / (pi (k a_eff)^2)
+    back = [m for r, m in zip(rows, mm[0]) if r[0] == 180.0]
+    assert len(back) == 1
+    ka = ctx.kd * (3.0 * ctx.n / (4.0 * math.pi)) ** (1.0 / 3.0)
+    assert back[0][0, 0] / (math.pi * ka ** 2) == pytest.approx(g["Qbk"], rel=6e-4)  # printed values agree to 3e-5
 
 
 def test_bicgstab2_follows_the_oracle(D):

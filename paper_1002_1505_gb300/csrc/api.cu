@@ -603,8 +603,18 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
   } else {
     DDA_TRY(dda::bicg_init<C>(kv, ks, rb, nrhs, n3, tol, have_x0, st));
   }
+  // Programmatic dependent launch inside the iteration chain (DDA_PDL=1): every kernel
+  // of an iteration may be scheduled behind its predecessor's tail (pdl.cuh).
+  const char* pdl_env = std::getenv("DDA_PDL");
+  const bool pdl = pdl_env && std::atoi(pdl_env) != 0;
+  struct PdlScope {
+    bool prev;
+    explicit PdlScope(bool on) : prev(dda::pdl_enabled()) { dda::set_pdl(on); }
+    ~PdlScope() { dda::set_pdl(prev); }
+  };
   // one_iter: one BiCGstab / CCG iteration (2 products), or one BiCGstab(2) cycle (4 products)
   auto one_iter = [&]() -> Err {
+    PdlScope scope(pdl);
     if (b2) {
       // r0 = r, r1 = s, r2 = t, u0 = p, u1 = v, u2 = u2
       DDA_TRY(dda::b2_u_update<C>(kv, ks, 0, nrhs, n3, st));
@@ -644,7 +654,7 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
   cudaGraphExec_t gexec = nullptr;
   unsigned long long graph_kernels = 0;
   const int gi = sizeof(C) == sizeof(float2) ? 0 : 1;
-  const long long gkey[4] = {o.solver, every, nrhs, (long long)n3};
+  const long long gkey[4] = {o.solver, 2LL * every + (pdl ? 1 : 0), nrhs, (long long)n3};
   const bool reuse = o.use_graph && c->gexec[gi] && c->gexec_gen[gi] == c->gen &&
                      std::equal(gkey, gkey + 4, c->gexec_key[gi]);
   if (reuse) {

@@ -11,6 +11,9 @@
 #include "../../include/dda.h"
 #include "df.cuh"
 #include "fft.cuh"
+#ifdef __CUDACC__
+#include "pdl.cuh"
+#endif
 
 namespace dda {
 

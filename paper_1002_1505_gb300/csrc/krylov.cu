@@ -199,6 +199,7 @@ __global__ void k_bicg_init(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3,
 // p = r + beta (p - omega v)
 template <typename C>
 __global__ void k_bicg_p(KrylovVecs<C> kv, const KState* ks, int64_t n3) {
+  pdl_begin();
   const int b = blockIdx.y;
   const KState k = ks[b];
   if (k.done) return;
@@ -214,6 +215,7 @@ __global__ void k_bicg_p(KrylovVecs<C> kv, const KState* ks, int64_t n3) {
 // partial <rhat, v>
 template <typename C>
 __global__ void k_bicg_dot_rv(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
+  pdl_begin();
   const int b = blockIdx.y;
   double acc[2] = {0.0, 0.0};
   if (!ks[b].done) {
@@ -237,6 +239,7 @@ __global__ void k_bicg_dot_rv(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n
 // s = r - alpha v ; partial |s|^2
 template <typename C>
 __global__ void k_bicg_s(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
+  pdl_begin();
   const int b = blockIdx.y;
   const KState k = ks[b];
   double acc[1] = {0.0};
@@ -263,6 +266,7 @@ __global__ void k_bicg_s(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
 // partial <t, s>, |t|^2
 template <typename C>
 __global__ void k_bicg_dot_ts(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
+  pdl_begin();
   const int b = blockIdx.y;
   double acc[3] = {0.0, 0.0, 0.0};
   if (!ks[b].done) {
@@ -290,6 +294,7 @@ __global__ void k_bicg_dot_ts(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n
 // (RHS that converged on the half step: x += alpha p, r = s)
 template <typename C>
 __global__ void k_bicg_xr(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
+  pdl_begin();
   const int b = blockIdx.y;
   const KState k = ks[b];
   double acc[3] = {0.0, 0.0, 0.0};
@@ -390,6 +395,7 @@ __global__ void k_ccg_start(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3)
 // partial |w|^2 (w = A p held in v)
 template <typename C>
 __global__ void k_norm_v(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
+  pdl_begin();
   const int b = blockIdx.y;
   double acc[1] = {0.0};
   if (!ks[b].done) {
@@ -411,6 +417,7 @@ __global__ void k_norm_v(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
 // x += alpha p ; r -= alpha w ; partial |r|^2
 template <typename C>
 __global__ void k_ccg_xr(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
+  pdl_begin();
   const int b = blockIdx.y;
   const KState k = ks[b];
   double acc[1] = {0.0};
@@ -443,6 +450,7 @@ __global__ void k_ccg_xr(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
 // partial |z|^2 for the new z (in s)
 template <typename C>
 __global__ void k_norm_s(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
+  pdl_begin();
   const int b = blockIdx.y;
   double acc[1] = {0.0};
   if (!ks[b].done) {
@@ -464,6 +472,7 @@ __global__ void k_norm_s(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
 // p = z + beta p
 template <typename C>
 __global__ void k_ccg_p(KrylovVecs<C> kv, const KState* ks, int64_t n3) {
+  pdl_begin();
   const int b = blockIdx.y;
   const KState k = ks[b];
   if (k.done) return;
@@ -520,6 +529,7 @@ __global__ void k_b2_init(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3, b
 // BiCG step j: u_i = r_i - beta u_i for i <= j (u0 = p, u1 = v; r0 = r, r1 = s)
 template <typename C>
 __global__ void k_b2_u(KrylovVecs<C> kv, const KState* ks, int j, int64_t n3) {
+  pdl_begin();
   const int b = blockIdx.y;
   const KState k = ks[b];
   if (k.done) return;
@@ -535,6 +545,7 @@ __global__ void k_b2_u(KrylovVecs<C> kv, const KState* ks, int j, int64_t n3) {
 // alpha = rho0 / <shadow, u_{j+1}> (u1 = v for j = 0, u2 for j = 1)
 template <typename C>
 __global__ void k_b2_alpha(KrylovVecs<C> kv, KState* ks, RedBuf rb, int j, int64_t n3) {
+  pdl_begin();
   const int b = blockIdx.y;
   double acc[2] = {0.0, 0.0};
   if (!ks[b].done) {
@@ -559,6 +570,7 @@ __global__ void k_b2_alpha(KrylovVecs<C> kv, KState* ks, RedBuf rb, int j, int64
 // r_i -= alpha u_{i+1} for i <= j; x += alpha u0
 template <typename C>
 __global__ void k_b2_r(KrylovVecs<C> kv, const KState* ks, int j, int64_t n3) {
+  pdl_begin();
   const int b = blockIdx.y;
   const KState k = ks[b];
   if (k.done) return;
@@ -575,6 +587,7 @@ __global__ void k_b2_r(KrylovVecs<C> kv, const KState* ks, int j, int64_t n3) {
 // rho1 = <shadow, r1>; beta = alpha rho1 / rho0; rho0 = rho1
 template <typename C>
 __global__ void k_b2_beta(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
+  pdl_begin();
   const int b = blockIdx.y;
   double acc[2] = {0.0, 0.0};
   if (!ks[b].done) {
@@ -600,6 +613,7 @@ __global__ void k_b2_beta(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
 // (r0 = r, r1 = s, r2 = t); gamma solves [<r1,r1> <r1,r2>; <r2,r1> <r2,r2>] gamma = [<r1,r0>; <r2,r0>]
 template <typename C>
 __global__ void k_b2_gram(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
+  pdl_begin();
   const int b = blockIdx.y;
   double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   if (!ks[b].done) {
@@ -637,6 +651,7 @@ __global__ void k_b2_gram(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
 // then the next cycle's first BiCG coefficients: rho0 <- -omega rho0, beta = alpha <shadow, r0> / rho0
 template <typename C>
 __global__ void k_b2_mr(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
+  pdl_begin();
   const int b = blockIdx.y;
   const KState k = ks[b];
   double acc[3] = {0.0, 0.0, 0.0};
@@ -736,31 +751,31 @@ template <typename C>
 Err bicg_p_update(const KrylovVecs<C>& kv, const KState* ks, int nrhs, int64_t n3, cudaStream_t st) {
   // grid size independent of reductions
   const int nb = (int)std::min<int64_t>((n3 + kThreads * 4 - 1) / (kThreads * 4), 1024);
-  k_bicg_p<C><<<dim3(nb, nrhs), kThreads, 0, st>>>(kv, ks, n3);
+  DDA_CU(launch_k(k_bicg_p<C>, dim3(nb, nrhs), dim3(kThreads), 0, st, kv, ks, n3));
   CHECK_LAUNCH();
   return Err::Ok();
 }
 template <typename C>
 Err bicg_alpha(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
-  k_bicg_dot_rv<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  DDA_CU(launch_k(k_bicg_dot_rv<C>, vgrid(rb, nrhs), dim3(kThreads), 0, st, kv, ks, rb, n3));
   CHECK_LAUNCH();
   return Err::Ok();
 }
 template <typename C>
 Err bicg_s_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
-  k_bicg_s<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  DDA_CU(launch_k(k_bicg_s<C>, vgrid(rb, nrhs), dim3(kThreads), 0, st, kv, ks, rb, n3));
   CHECK_LAUNCH();
   return Err::Ok();
 }
 template <typename C>
 Err bicg_omega(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
-  k_bicg_dot_ts<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  DDA_CU(launch_k(k_bicg_dot_ts<C>, vgrid(rb, nrhs), dim3(kThreads), 0, st, kv, ks, rb, n3));
   CHECK_LAUNCH();
   return Err::Ok();
 }
 template <typename C>
 Err bicg_xr_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
-  k_bicg_xr<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  DDA_CU(launch_k(k_bicg_xr<C>, vgrid(rb, nrhs), dim3(kThreads), 0, st, kv, ks, rb, n3));
   CHECK_LAUNCH();
   return Err::Ok();
 }
@@ -781,19 +796,19 @@ Err ccg_start(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t 
 // after v = A p: alpha, x/r update, convergence
 template <typename C>
 Err ccg_alpha_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
-  k_norm_v<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  DDA_CU(launch_k(k_norm_v<C>, vgrid(rb, nrhs), dim3(kThreads), 0, st, kv, ks, rb, n3));
   CHECK_LAUNCH();
-  k_ccg_xr<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  DDA_CU(launch_k(k_ccg_xr<C>, vgrid(rb, nrhs), dim3(kThreads), 0, st, kv, ks, rb, n3));
   CHECK_LAUNCH();
   return Err::Ok();
 }
 // after s = A^H r: beta, p update
 template <typename C>
 Err ccg_beta_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
-  k_norm_s<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  DDA_CU(launch_k(k_norm_s<C>, vgrid(rb, nrhs), dim3(kThreads), 0, st, kv, ks, rb, n3));
   CHECK_LAUNCH();
   const int nb = (int)std::min<int64_t>((n3 + kThreads * 4 - 1) / (kThreads * 4), 1024);
-  k_ccg_p<C><<<dim3(nb, nrhs), kThreads, 0, st>>>(kv, ks, n3);
+  DDA_CU(launch_k(k_ccg_p<C>, dim3(nb, nrhs), dim3(kThreads), 0, st, kv, ks, n3));
   CHECK_LAUNCH();
   return Err::Ok();
 }
@@ -808,34 +823,34 @@ Err b2_init(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3
 template <typename C>
 Err b2_u_update(const KrylovVecs<C>& kv, const KState* ks, int j, int nrhs, int64_t n3, cudaStream_t st) {
   const int nb = (int)std::min<int64_t>((n3 + kThreads * 4 - 1) / (kThreads * 4), 1024);
-  k_b2_u<C><<<dim3(nb, nrhs), kThreads, 0, st>>>(kv, ks, j, n3);
+  DDA_CU(launch_k(k_b2_u<C>, dim3(nb, nrhs), dim3(kThreads), 0, st, kv, ks, j, n3));
   CHECK_LAUNCH();
   return Err::Ok();
 }
 template <typename C>
 Err b2_alpha(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int j, int nrhs, int64_t n3, cudaStream_t st) {
-  k_b2_alpha<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, j, n3);
+  DDA_CU(launch_k(k_b2_alpha<C>, vgrid(rb, nrhs), dim3(kThreads), 0, st, kv, ks, rb, j, n3));
   CHECK_LAUNCH();
   return Err::Ok();
 }
 template <typename C>
 Err b2_r_update(const KrylovVecs<C>& kv, const KState* ks, int j, int nrhs, int64_t n3, cudaStream_t st) {
   const int nb = (int)std::min<int64_t>((n3 + kThreads * 4 - 1) / (kThreads * 4), 1024);
-  k_b2_r<C><<<dim3(nb, nrhs), kThreads, 0, st>>>(kv, ks, j, n3);
+  DDA_CU(launch_k(k_b2_r<C>, dim3(nb, nrhs), dim3(kThreads), 0, st, kv, ks, j, n3));
   CHECK_LAUNCH();
   return Err::Ok();
 }
 template <typename C>
 Err b2_beta(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
-  k_b2_beta<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  DDA_CU(launch_k(k_b2_beta<C>, vgrid(rb, nrhs), dim3(kThreads), 0, st, kv, ks, rb, n3));
   CHECK_LAUNCH();
   return Err::Ok();
 }
 template <typename C>
 Err b2_mr(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
-  k_b2_gram<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  DDA_CU(launch_k(k_b2_gram<C>, vgrid(rb, nrhs), dim3(kThreads), 0, st, kv, ks, rb, n3));
   CHECK_LAUNCH();
-  k_b2_mr<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3);
+  DDA_CU(launch_k(k_b2_mr<C>, vgrid(rb, nrhs), dim3(kThreads), 0, st, kv, ks, rb, n3));
   CHECK_LAUNCH();
   return Err::Ok();
 }

@@ -559,6 +559,11 @@ Err noalloc_scratch(int device, void** out) {
 }
 
 void set_pass_events(cudaEvent_t* ev) { t_pass_events = ev; }
+namespace {
+thread_local bool t_pdl = false;
+}
+bool pdl_enabled() { return t_pdl; }
+void set_pdl(bool on) { t_pdl = on; }
 unsigned long long launches() { return g_launches.load(); }
 void add_launches(unsigned long long n) { g_launches += n; }
 void sub_launches(unsigned long long n) { g_launches -= n; }

@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(256) k_x_fwd(Geom g, MvData<C> d, const typena
                                                bool conj, int ip) {
   constexpr int RA = Shape<PX>::RA, LB = Shape<PX>::LB, H = Shape<PX>::H;
   static_assert(NC == 1 || NC == 3, "one or three components per CTA");
+  pdl_begin();
   extern __shared__ unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* in = tw + PX;
@@ -145,6 +146,7 @@ __global__ void __launch_bounds__(256) k_x_inv(Geom g, MvData<C> d, const typena
                                                typename Io<C>::t* __restrict__ ap, int rhs0, bool conj, int ip) {
   constexpr int RA = Shape<PX>::RA, LB = Shape<PX>::LB, H = Shape<PX>::H;
   static_assert(NC == 1 || NC == 3, "one or three components per CTA");
+  pdl_begin();
   extern __shared__ unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* in = tw + PX;
@@ -230,6 +232,7 @@ __global__ void __launch_bounds__(NT) k_yz_plane(Geom g, MvData<C> d) {
   constexpr int RAy = Shape<PY>::RA, LBy = Shape<PY>::LB, Hy = Shape<PY>::H;
   constexpr int RAz = Shape<PZ>::RA, LBz = Shape<PZ>::LB, Hz = Shape<PZ>::H;
   constexpr int RP = PY + 1;
+  pdl_begin();
   extern __shared__ unsigned char smem_raw[];
   C* twy = reinterpret_cast<C*>(smem_raw);
   C* twz = twy + PY;
@@ -399,6 +402,7 @@ __global__ void __launch_bounds__(256) k_y_rows(Geom g, C* __restrict__ work, co
                                                 int64_t nrows) {
   constexpr int RA = Shape<PY>::RA, LB = Shape<PY>::LB, H = Shape<PY>::H;
   constexpr int RP = PY + 1;
+  pdl_begin();
   extern __shared__ unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* s = tw + PY;
@@ -483,6 +487,7 @@ template <typename C, int PZ, int G>
 __global__ void __launch_bounds__(256) k_z_cols(Geom g, MvData<C> d) {
   constexpr int RA = Shape<PZ>::RA, LB = Shape<PZ>::LB, H = Shape<PZ>::H;
   constexpr bool kFuse = (LB * sizeof(C) <= 96);
+  pdl_begin();
   extern __shared__ unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* s = tw + PZ;
@@ -707,7 +712,8 @@ Err launch_x_fwd(const Geom& g, const MvData<C>& d, const MvTune& t, const typen
 #define DDA_CASE(L_)                                                                                    \
   case L_:                                                                                              \
     DDA_TRY((with_x<C, L_>(NC, TY, [&](auto tyc, auto ncc) {                                          \
-      k_x_fwd<C, L_, decltype(tyc)::value, decltype(ncc)::value><<<grid, 256, sm, st>>>(g, d, p, conj, ip); \
+      DDA_CU(launch_k(k_x_fwd<C, L_, decltype(tyc)::value, decltype(ncc)::value>, grid, dim3(256), sm, st, g, \
+                      d, p, conj, ip));                                                                \
       return Err::Ok();                                                                                 \
     })));                                                                                               \
     break;
@@ -731,8 +737,8 @@ Err launch_x_inv(const Geom& g, const MvData<C>& d, const MvTune& t, const typen
 #define DDA_CASE(L_)                                                                                         \
   case L_:                                                                                                   \
     DDA_TRY((with_x<C, L_>(NC, TY, [&](auto tyc, auto ncc) {                                               \
-      k_x_inv<C, L_, decltype(tyc)::value, decltype(ncc)::value><<<grid, 256, sm, st>>>(g, d, p, ap, rhs0, conj, \
-                                                                                        ip);                 \
+      DDA_CU(launch_k(k_x_inv<C, L_, decltype(tyc)::value, decltype(ncc)::value>, grid, dim3(256), sm, st, g, d, \
+                      p, ap, rhs0, conj, ip));                                                               \
       return Err::Ok();                                                                                      \
     })));                                                                                                    \
     break;
@@ -752,8 +758,8 @@ Err launch_plane(const Geom& g, const MvData<C>& d, int nrhs, int nt, cudaStream
     const dim3 grid(nrhs, g.px);
 #define DDA_CASE(A, B)                                               \
     if (g.py == A && g.pz == B) {                                    \
-      if (nt == 768) k_yz_plane<C, A, B, 768, false><<<grid, 768, sm, st>>>(g, d); \
-      else k_yz_plane<C, A, B, 512, false><<<grid, 512, sm, st>>>(g, d);    \
+      if (nt == 768) DDA_CU(launch_k(k_yz_plane<C, A, B, 768, false>, grid, dim3(768), sm, st, g, d)); \
+      else DDA_CU(launch_k(k_yz_plane<C, A, B, 512, false>, grid, dim3(512), sm, st, g, d));             \
       DDA_CU(cudaGetLastError());                                    \
       return Err::Ok();                                              \
     }
@@ -770,8 +776,8 @@ Err launch_y_rows(const Geom& g, C* work, const C* tw, int64_t nrows, bool inv, 
   switch (g.py) {
 #define DDA_CASE(L_)                                                                            \
   case L_:                                                                                      \
-    if (inv) k_y_rows<C, L_, kRowsPerCta, true><<<nb, 256, sm, st>>>(g, work, tw, nrows);       \
-    else k_y_rows<C, L_, kRowsPerCta, false><<<nb, 256, sm, st>>>(g, work, tw, nrows);          \
+    if (inv) DDA_CU(launch_k(k_y_rows<C, L_, kRowsPerCta, true>, dim3(nb), dim3(256), sm, st, g, work, tw, nrows)); \
+    else DDA_CU(launch_k(k_y_rows<C, L_, kRowsPerCta, false>, dim3(nb), dim3(256), sm, st, g, work, tw, nrows));   \
     break;
     DDA_FAST_LENGTHS(DDA_CASE)
 #undef DDA_CASE
@@ -789,7 +795,7 @@ Err launch_z_cols(const Geom& g, const MvData<C>& d, int nrhs, cudaStream_t st) 
   switch (g.pz) {
 #define DDA_CASE(L_)                                                                      \
   case L_:                                                                                \
-    k_z_cols<C, L_, zcols_g_rt(sizeof(C), L_)><<<grid, 256, sm, st>>>(g, d);              \
+    DDA_CU(launch_k(k_z_cols<C, L_, zcols_g_rt(sizeof(C), L_)>, grid, dim3(256), sm, st, g, d)); \
     break;
     DDA_FAST_LENGTHS(DDA_CASE)
 #undef DDA_CASE

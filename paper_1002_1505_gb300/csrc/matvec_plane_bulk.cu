@@ -14,7 +14,7 @@ Err launch_plane_bulk_c64(const Geom& g, const MvData<float2>& d, int nrhs, cuda
   const dim3 grid(nrhs, g.px);
 #define DDA_CASE(A, B)                                                                  \
   if (g.py == A && g.pz == B) {                                                         \
-    fast::k_yz_plane<float2, A, B, 512, true><<<grid, 512, sm, st>>>(g, d);             \
+    DDA_CU(launch_k(fast::k_yz_plane<float2, A, B, 512, true>, grid, dim3(512), sm, st, g, d)); \
     DDA_CU(cudaGetLastError());                                                         \
     return Err::Ok();                                                                   \
   }

@@ -490,7 +490,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
             "config": {"workload": w.name, "n_dipoles": n, "box": list(box), "pad": list(pad), "nrhs": nrhs,
-                       "n_orientations": n_ori, "tol": 1e-5, "solver": "BiCGstab, complex64 + FP64 refinement",
+                       "n_orientations": n_ori, "tol": 1e-5, "solver": "BiCGstab, complex64 + FP64-accurate refinement",
+                       "true_residual": "double-float product (FP32 pairs, within 1e-12 of FP64) where the grid "
+                                        "has compile-time kernels, else complex128",
                        "l2": "flushed (512 MB write) before every step", "parallelism": f"replicas x{args.gpus}"},
             "solve_ms_per_orientation": ms_step / n_ori,
             "plain_fp64_solve_ms_per_orientation": plain_ms / n_ori,

@@ -345,6 +345,7 @@ def main():
     import torch
     import torch.distributed as dist
     from paper_1002_1505_gb300 import dda as D
+    from paper_1002_1505_gb300 import replicas
 
     torch.cuda.set_device(local)
     if ws > 1:
@@ -396,11 +397,7 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     if ws > 1:
-        t = torch.tensor([total_ms, float(matvecs)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_ms, matvecs = float(tmax[0]), float(t[1])
+        total_ms, matvecs = replicas.reduce_max_sum(total_ms, float(matvecs))
     value = matvecs / (total_ms / 1e3)
     ms_step = total_ms / args.steps
 

@@ -80,7 +80,8 @@ def apply_a(prob: Problem, i: int, p: np.ndarray, method: str = "fft", ghat=None
 
 def solve(prob: Problem, method: str = "bicgstab", matvec: str = "fft", tol: float = 1e-10,
           workers=None, maxit: int = 3000):
-    """Solve every RHS. method: lu | bicgstab | bicgstab2 | ccg. Returns list of (3, N) P and iteration counts."""
+    """Solve every RHS. method: lu | bicgstab | bicgstab2 | ccg | cocg | qmr_cs.
+    Returns list of (3, N) P and iteration counts."""
     t = prob.target
     out, iters = [], []
     ghat = None
@@ -97,7 +98,8 @@ def solve(prob: Problem, method: str = "bicgstab", matvec: str = "fft", tol: flo
 
         def op(v, i=i):
             return apply_a(prob, i, v.reshape(shape), matvec, ghat=ghat, workers=workers).reshape(-1)
-        fn = {"bicgstab": solvers.bicgstab, "ccg": solvers.ccg,
+        fn = {"bicgstab": solvers.bicgstab, "ccg": solvers.ccg, "cocg": solvers.cocg,
+              "qmr_cs": lambda *a, **k: solvers.qmr_cs(*a, **k)[:3],
               "bicgstab2": lambda *a, **k: solvers.bicgstab_l(*a, ell=2, **k)}[method]
         p, it, _ = fn(op, rh.e_inc.reshape(-1), tol=tol, maxit=maxit)
         out.append(p.reshape(shape))

@@ -300,6 +300,58 @@ def test_bicgstab_l_reduces_to_bicgstab_and_solves():
     assert all(i > 0 for i in its)
 
 
+def _sphere12_operator(index=0):
+    w = W.SPHERE12
+    prob = dda.build_problem(w.shape, w.shpar, w.m, w.x, w.prescription, w.orientations)
+    rh = prob.rhs[index]
+    shape = rh.e_inc.shape
+
+    def op(v):
+        return dda.apply_a(prob, index, v.reshape(shape), "direct").reshape(-1)
+    p_lu = solvers.lu_solve(interaction.dense_matrix(prob.target.r, prob.kd, rh.inv_alpha), rh.e_inc.reshape(-1))
+    return op, rh.e_inc.reshape(-1), p_lu
+
+
+def test_cocg_and_qmr_cs_solve_the_dda_system():
+    """COCG (van der Vorst & Melissen 1990) and QMR for complex symmetric systems (Freund 1992) reach
+    the LU solution of the (complex symmetric, non-Hermitian) DDA system; with a conjugated inner
+    product in place of x^T y neither would."""
+    op, e, p_lu = _sphere12_operator(1)
+    for fn in (solvers.cocg, solvers.qmr_cs):
+        out = fn(op, e, tol=1e-12)
+        x, hist = out[0], out[2]
+        assert hist[-1] <= 1e-12, fn.__name__
+        assert np.linalg.norm(x - p_lu) / np.linalg.norm(p_lu) < 1e-9, fn.__name__
+        assert np.linalg.norm(e - op(x)) / np.linalg.norm(e) < 1e-11
+    p, its = dda.solve(dda.build_problem(W.SPHERE12.shape, W.SPHERE12.shpar, W.SPHERE12.m, W.SPHERE12.x,
+                                         W.SPHERE12.prescription, W.SPHERE12.orientations), "qmr_cs", tol=1e-10)
+    assert all(i > 0 for i in its)
+
+
+@pytest.mark.parametrize("solver", ["cocg", "qmr_cs"])
+def test_symmetric_krylov_terminates_at_the_number_of_distinct_eigenvalues(solver):
+    """Exact-arithmetic property of both methods: on A = diag(lambda) with k distinct complex
+    eigenvalues (complex symmetric, not Hermitian) the residual vanishes after k products."""
+    rng = np.random.default_rng(3)
+    lam = np.array([1 + 1j, 2 - 0.5j, 3 + 0.2j, 0.5 + 2j, -1.5 + 0.7j])
+    for k in (2, 3, 5):
+        dg = np.repeat(lam[:k], 13)
+        b = rng.normal(size=dg.size) + 1j * rng.normal(size=dg.size)
+        out = getattr(solvers, solver)(lambda v: dg * v, b, tol=1e-12, maxit=50)
+        assert out[1] == k and out[2][-1] <= 1e-12, (solver, k, out[1])
+        np.testing.assert_allclose(out[0], b / dg, rtol=1e-11)
+
+
+def test_qmr_cs_quasi_residual_bounds_the_residual():
+    """The quasi-residual |tau_{n+1}| never increases (a growing least-squares problem) and, with unit
+    2-norm Lanczos vectors, |E - A x_n| <= sqrt(n+1) |tau_{n+1}|."""
+    op, e, _ = _sphere12_operator(0)
+    _, it, hist, q = solvers.qmr_cs(op, e, tol=1e-12)
+    assert it >= 5
+    assert all(q[i + 1] <= q[i] * (1 + 1e-12) for i in range(len(q) - 1))
+    assert all(hist[i] <= np.sqrt(i + 1) * q[i] * (1 + 1e-9) for i in range(len(hist)))
+
+
 def test_compositions_assemble_per_site_and_axis():
     """Per-site and per-axis compositions: equal indices reduce to the homogeneous problem, relabelling
     compositions (with the index list permuted alike) changes nothing, real indices absorb nothing,

@@ -201,7 +201,9 @@ typedef struct {
   int precision;     /* DDA_PREC_C64 / DDA_PREC_C128 / DDA_PREC_MIXED */
   double tol;        /* stop when |E - A P| / |E| <= tol for every RHS */
   int maxit;         /* iteration cap (inner iterations summed for MIXED) */
-  double inner_tol;  /* MIXED: relative reduction asked of each inner solve (0 = 1e-3) */
+  double inner_tol;  /* MIXED: smallest relative reduction asked of an inner complex64 solve; each
+                        inner solve aims at 0.5 tol / (current true relative residual) but not
+                        below this floor (0 = 5e-6, near the complex64 limit) */
   double timeout_ms; /* wall-clock budget, 0 = none; exceeded -> DDA_ETIMEOUT */
   int warm_start;    /* 1 = p_dev holds the initial guess, 0 = start from P = 0 */
   int check_every;   /* iterations between host convergence checks (0 = 8; BiCGstab(2): cycles of two iterations) */

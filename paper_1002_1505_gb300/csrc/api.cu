@@ -1284,7 +1284,6 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
     e = grow(c, &c->d_sc, sizeof(double2) * 2 * el);
     if (!e.ok()) return fail(c, e);
     double2* sc = c->d_sc;
-    auto cleanup = [&]() {};
     int outer = 0;
     if (o.precision == DDA_PREC_C128) {
       dda::KrylovVecs<double2> kv;
@@ -1345,7 +1344,10 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
         e = dda::convert_from_c128<float2>(r128, kv.b, el, c->stream);
         if (!e.ok()) break;
         for (int b = 0; b < nrhs; ++b)
-          if (rel[b] <= o.tol) cudaMemsetAsync(kv.b + (int64_t)b * n3, 0, sizeof(float2) * n3, c->stream);
+          if (rel[b] <= o.tol && e.ok())
+            e = cuda_ok(cudaMemsetAsync(kv.b + (int64_t)b * n3, 0, sizeof(float2) * n3, c->stream),
+                        "inner right-hand side clear");
+        if (!e.ok()) break;
         // ask the inner solve for the reduction that reaches tol, but at least `inner`
         double worst = 0;
         for (int b = 0; b < nrhs; ++b) worst = std::max(worst, rel[b] > o.tol ? o.tol / rel[b] : 0.0);
@@ -1365,12 +1367,12 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
         ++outer;
       }
     }
-    if (!e.ok()) { cleanup(); return fail(c, e); }
+    if (!e.ok()) return fail(c, e);
     // final true residual in FP64 (for MIXED it was computed by the loop's last pass)
     if (o.precision != DDA_PREC_MIXED || rel.empty()) {
       e = true_residual(c, P, sc, sc + el, &rel, df_res);
       add_all(1);
-      if (!e.ok()) { cleanup(); return fail(c, e); }
+      if (!e.ok()) return fail(c, e);
     }
     std::vector<double> ner(nrhs, NAN);
     if (o.normal_eq) {
@@ -1401,9 +1403,8 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
           ner[b] = den[b] > 0 ? std::sqrt(num[b] / den[b]) : 0.0;
         }
       }
-      if (!e.ok()) { cleanup(); return fail(c, e); }
+      if (!e.ok()) return fail(c, e);
     }
-    cleanup();
     {
       const Err fe = check_fault(c);
       if (!fe.ok()) return fail(c, fe);
@@ -1504,8 +1505,9 @@ dda_status dda_cross_sections(dda_ctx* c, const void* p_dev, double* q_out, cons
       }
       std::vector<double2> F((size_t)nrhs * ndir * 3);
       if (e.ok()) {
-        cudaMemcpyAsync(F.data(), d_F, sizeof(double2) * F.size(), cudaMemcpyDeviceToHost, c->stream);
-        if (cudaStreamSynchronize(c->stream) != cudaSuccess) e = Err::make(DDA_ECUDA, "far field failed");
+        e = cuda_ok(cudaMemcpyAsync(F.data(), d_F, sizeof(double2) * F.size(), cudaMemcpyDeviceToHost, c->stream),
+                    "far-field readback");
+        if (e.ok() && cudaStreamSynchronize(c->stream) != cudaSuccess) e = Err::make(DDA_ECUDA, "far field failed");
       }
       if (!e.ok()) return fail(c, e);
       const double k3 = k * k * k;

@@ -4,7 +4,8 @@ solve time per orientation at residual 1e-5, against the plain FP64 GPU solve.
 
 One step = the whole path for one batch: incident beams and polarizabilities
 for every RHS, the FP64 Fourier-space Green tensor, the batched BiCGstab solve
-(complex64 iterations refined against FP64 true residuals) to |E - A P|/|E| <= 1e-5,
+(complex64 iterations refined against FP64-accurate true residuals, whose product runs in
+double-float arithmetic) to |E - A P|/|E| <= 1e-5,
 and the efficiencies plus Mueller elements.  The target's site list is resident
 on the device before the timed region (it is the step's input).
 

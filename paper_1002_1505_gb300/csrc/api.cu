@@ -6,6 +6,7 @@
 #include <array>
 #include <chrono>
 #include <thread>
+#include <type_traits>
 #include <map>
 #include <mutex>
 #include <cstdlib>
@@ -603,6 +604,12 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
   } else {
     DDA_TRY(dda::bicg_init<C>(kv, ks, rb, nrhs, n3, tol, have_x0, st));
   }
+  // BiCGstab in complex64 on the compile-time product with every RHS in one launch folds its
+  // vector updates and dot products into the product's x passes: 7 launches per iteration
+  // instead of 11 (DDA_FUSE=0 keeps them separate).  Decided below, once the workspace
+  // capacity is known.
+  bool fused = false;
+  dda::RedBuf rbx{};
   // Programmatic dependent launch inside the iteration chain (DDA_PDL=1): every kernel
   // of an iteration may be scheduled behind its predecessor's tail (pdl.cuh).
   const char* pdl_env = std::getenv("DDA_PDL");
@@ -634,6 +641,15 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
       DDA_TRY(dda::ccg_alpha_update<C>(kv, ks, rb, nrhs, n3, st));
       DDA_TRY(matvec<C>(c, kv.r, kv.s, nrhs, 0, true, ks));
       DDA_TRY(dda::ccg_beta_update<C>(kv, ks, rb, nrhs, n3, st));
+    } else if (fused) {
+      if constexpr (std::is_same<C, float2>::value) {
+        dda::MvData<float2> d = Sel<float2>::data(c);
+        d.ks = ks;
+        const dda::Geom g = Sel<float2>::geom(c);
+        DDA_TRY(dda::launch_bicg_half_c64(g, d, c->t64, kv, ks, rbx, nrhs, 0, st));
+        DDA_TRY(dda::launch_bicg_half_c64(g, d, c->t64, kv, ks, rbx, nrhs, 1, st));
+        DDA_TRY(dda::bicg_xr_update<C>(kv, ks, rb, nrhs, n3, st));
+      }
     } else {
       DDA_TRY(dda::bicg_p_update<C>(kv, ks, nrhs, n3, st));
       DDA_TRY(matvec<C>(c, kv.p, kv.v, nrhs, 0, false, ks));
@@ -650,11 +666,24 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
   {
     int cap = 0;  // no allocation may happen while the stream is being captured
     DDA_TRY(ensure_work<C>(c, nrhs, &cap));
+    const char* fe = std::getenv("DDA_FUSE");
+    if constexpr (std::is_same<C, float2>::value) {
+      fused = !(fe && std::atoi(fe) == 0) && !ccg && !b2 && c->t64.fast && cap >= nrhs;
+      if (fused) {
+        // the folded reductions' table follows the vector kernels' table in the same buffer
+        const int nx = dda::x_ctas_per_rhs_c64(Sel<float2>::geom(c), c->t64);
+        DDA_TRY(ensure_part(c, sizeof(double) * ((size_t)rb.nblk + nx) * nrhs * dda::kRedSlots));
+        rb.part = c->d_part;
+        rbx.part = c->d_part + (size_t)rb.nblk * nrhs * dda::kRedSlots;
+        rbx.count = c->d_count;
+        rbx.nblk = nx;
+      }
+    }
   }
   cudaGraphExec_t gexec = nullptr;
   unsigned long long graph_kernels = 0;
   const int gi = sizeof(C) == sizeof(float2) ? 0 : 1;
-  const long long gkey[4] = {o.solver, 2LL * every + (pdl ? 1 : 0), nrhs, (long long)n3};
+  const long long gkey[4] = {o.solver, 4LL * every + (fused ? 2 : 0) + (pdl ? 1 : 0), nrhs, (long long)n3};
   const bool reuse = o.use_graph && c->gexec[gi] && c->gexec_gen[gi] == c->gen &&
                      std::equal(gkey, gkey + 4, c->gexec_key[gi]);
   if (reuse) {

@@ -250,6 +250,18 @@ template <typename C> Err ccg_alpha_update(const KrylovVecs<C>& kv, KState* ks, 
 template <typename C> Err ccg_beta_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3,
                                           cudaStream_t st);
 
+// BiCGstab half-iterations of the complex64 solve with the vector updates and dot products folded
+// into the x passes of the compile-time product (matvec_fused_c64.cu).  half 0: p = r + beta (p -
+// omega v), v = A p, alpha = rho / <rhat, v>; half 1: s = r - alpha v (half-step test on |s|),
+// t = A s, omega = <t, s> / |t|^2.  All nrhs RHS of the solve in one launch; d.ks = ks; rbx: a
+// reduction table of x_ctas_per_rhs_c64 slots per RHS and zeroed per-RHS counters.
+Err launch_bicg_half_c64(const Geom& g, const MvData<float2>& d, const MvTune& t, const KrylovVecs<float2>& kv,
+                         KState* ks, const RedBuf& rbx, int nrhs, int half, cudaStream_t st);
+int x_ctas_per_rhs_c64(const Geom& g, const MvTune& t);
+// the passes between the x passes of the complex64 product (plane pass or y/z/y), matvec_fast_c64.cu
+Err launch_middle_c64(const Geom& g, const MvData<float2>& d, const MvTune& t, int nrhs, cudaStream_t st);
+void fused_optin_c64(int smax);
+
 // r = b - ax (c128), returns per-RHS |r|^2 and |b|^2 into out2[2*nrhs] (device)
 Err residual_c128(const double2* b, const double2* ax, double2* r, double* out2, RedBuf rb, int nrhs, int64_t n3,
                   cudaStream_t st);

@@ -611,6 +611,7 @@ void init_kernel_attrs() {
   plane_bulk_optin_c64(v);
   fast_optin_c128(v);
   fast_optin_df(v);
+  fused_optin_c64(v);
 }
 
 void green_perm_tables(const Geom& g, std::vector<int32_t>* out) {

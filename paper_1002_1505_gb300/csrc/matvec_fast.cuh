@@ -12,6 +12,7 @@
 #include "dda_internal.h"
 #include "df.cuh"
 #include "fft2.cuh"
+#include "kred.cuh"
 
 namespace dda {
 namespace fast {
@@ -69,14 +70,39 @@ __device__ __forceinline__ void copy_tw(C* dst, const C* src, int L) {
   for (int i = threadIdx.x; i < L; i += blockDim.x) dst[i] = src[i];
 }
 
+// ------------------------------------------------------------------ BiCGstab updates folded into the x passes
+// (complex64, product without conjugation).  The x forward pass visits every (site, component)
+// of every RHS exactly once while gathering the product's input, and the x inverse pass while
+// scattering its output, so the vector updates and dot products that BiCGstab applies just
+// before and after each product can ride on those passes:
+//   kFuseP   x forward: p = r + beta (p - omega v) gathered, stored and transformed
+//   kFuseS   x forward: s = r - alpha v gathered, stored and transformed; |s|^2 -> half-step test
+//   kFuseRV  x inverse: v = A p stored, <rhat, v> -> alpha
+//   kFuseTS  x inverse: t = A s stored, <t, s>, |t|^2 -> omega
+// with the same per-RHS scalars (KState) and finalisation as the separate vector kernels.
+enum FuseMode { kFuseNone = 0, kFuseP = 1, kFuseS = 2, kFuseRV = 3, kFuseTS = 4 };
+
+// this CTA's reduction slot within its RHS, and the CTAs per RHS, of an x-pass grid
+// (ceil(ny/TY), nz, nrhs * 3/NC)
+template <int NC>
+__device__ __forceinline__ int x_slot() {
+  return (int)((blockIdx.z % (3 / NC)) * (gridDim.x * gridDim.y) + blockIdx.y * gridDim.x + blockIdx.x);
+}
+template <int NC>
+__device__ __forceinline__ int x_slots() {
+  return (int)(gridDim.x * gridDim.y * (3 / NC));
+}
+
 // ------------------------------------------------------------------ x forward
 // grid (ceil(ny/TY), nz, nrhs * 3/NC): NC components (1 or 3) of TY y rows per CTA.
 // smem: tw[PX] | in[NC*TY][ip] | out[NC*PX][TY]
-template <typename C, int PX, int TY, int NC = 3>
-__global__ void __launch_bounds__(256) k_x_fwd(Geom g, MvData<C> d, const typename Io<C>::t* __restrict__ p,
-                                               bool conj, int ip) {
+template <typename C, int PX, int TY, int NC, int MODE>
+__device__ __forceinline__ void x_fwd_body(const Geom& g, const MvData<C>& d, const typename Io<C>::t* __restrict__ p,
+                                           bool conj, int ip, const KrylovVecs<float2>* kf, KState* ksw,
+                                           const RedBuf* rbx) {
   constexpr int RA = Shape<PX>::RA, LB = Shape<PX>::LB, H = Shape<PX>::H;
   static_assert(NC == 1 || NC == 3, "one or three components per CTA");
+  static_assert(MODE == kFuseNone || (MODE == kFuseP || MODE == kFuseS), "x forward fuses p or s updates");
   pdl_begin();
   extern __shared__ unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
@@ -86,6 +112,16 @@ __global__ void __launch_bounds__(256) k_x_fwd(Geom g, MvData<C> d, const typena
   const int b = blockIdx.z / (3 / NC), c0 = (blockIdx.z % (3 / NC)) * NC;
   if (rhs_done(d, b)) return;
   copy_tw(tw, d.twx, PX);
+  [[maybe_unused]] C k1 = czero<C>(), k2 = czero<C>();  // (beta, omega) or (alpha, -)
+  [[maybe_unused]] kred::AccF ss;
+  if constexpr (MODE == kFuseP) {
+    const KState k = ksw[b];
+    k1 = mk((float)k.beta.x, (float)k.beta.y);
+    k2 = mk((float)k.omega.x, (float)k.omega.y);
+  } else if constexpr (MODE == kFuseS) {
+    const KState k = ksw[b];
+    k1 = mk((float)k.alpha.x, (float)k.alpha.y);
+  }
   const int nld = NC * TY * g.nx;
   for (int i = threadIdx.x; i < nld; i += blockDim.x) {
     const int x = i % g.nx;
@@ -96,8 +132,18 @@ __global__ void __launch_bounds__(256) k_x_fwd(Geom g, MvData<C> d, const typena
     if (y < g.ny) {
       const int32_t idx = __ldg(d.map + ((int64_t)z * g.ny + y) * g.nx + x);
       if (idx >= 0) {
-        v = io_get<C>(p[((int64_t)b * 3 + c0 + cl) * g.n + idx]);
-        if (conj) v = conjc(v);
+        const int64_t o = ((int64_t)b * 3 + c0 + cl) * g.n + idx;
+        if constexpr (MODE == kFuseNone) {
+          v = io_get<C>(p[o]);
+          if (conj) v = conjc(v);
+        } else if constexpr (MODE == kFuseP) {
+          v = cadd(kf->r[o], cmul(k1, csub(kf->p[o], cmul(k2, kf->v[o]))));
+          kf->p[o] = v;
+        } else {
+          v = csub(kf->r[o], cmul(k1, kf->v[o]));
+          kf->s[o] = v;
+          kred::acc_nrm(ss, v);
+        }
       }
     }
     in[(cl * TY + t) * ip + x] = v;
@@ -137,15 +183,39 @@ __global__ void __launch_bounds__(256) k_x_fwd(Geom g, MvData<C> d, const typena
       for (int e = 0; e < LB; ++e) dst[e * plane] = v[e];
     }
   }
+  if constexpr (MODE == kFuseS) {
+    double acc[1] = {ss.get()};
+    double tot[1];
+    if (kred::last_cta_totals<1>(acc, rbx->part, rbx->count, b, x_slot<NC>(), x_slots<NC>(), tot) &&
+        threadIdx.x == 0) {
+      KState& k = ksw[b];
+      if (!k.done && tot[0] <= k.tol2) { k.done = 3; k.rr = tot[0]; }  // converged on the half step
+    }
+  }
+}
+
+template <typename C, int PX, int TY, int NC = 3>
+__global__ void __launch_bounds__(256) k_x_fwd(Geom g, MvData<C> d, const typename Io<C>::t* __restrict__ p,
+                                               bool conj, int ip) {
+  x_fwd_body<C, PX, TY, NC, kFuseNone>(g, d, p, conj, ip, nullptr, nullptr, nullptr);
+}
+
+// the x forward pass with the BiCGstab p (MODE = kFuseP) or s (kFuseS) update folded in
+template <int PX, int TY, int NC, int MODE>
+__global__ void __launch_bounds__(256) k_x_fwd_fused(Geom g, MvData<float2> d, KrylovVecs<float2> kv, KState* ks,
+                                                     RedBuf rbx, int ip) {
+  x_fwd_body<float2, PX, TY, NC, MODE>(g, d, nullptr, false, ip, &kv, ks, &rbx);
 }
 
 // ------------------------------------------------------------------ x inverse + alpha^{-1} P + scatter
 // grid and shared memory as k_x_fwd
-template <typename C, int PX, int TY, int NC = 3>
-__global__ void __launch_bounds__(256) k_x_inv(Geom g, MvData<C> d, const typename Io<C>::t* __restrict__ p,
-                                               typename Io<C>::t* __restrict__ ap, int rhs0, bool conj, int ip) {
+template <typename C, int PX, int TY, int NC, int MODE>
+__device__ __forceinline__ void x_inv_body(const Geom& g, const MvData<C>& d, const typename Io<C>::t* __restrict__ p,
+                                           typename Io<C>::t* __restrict__ ap, int rhs0, bool conj, int ip,
+                                           const KrylovVecs<float2>* kf, KState* ksw, const RedBuf* rbx) {
   constexpr int RA = Shape<PX>::RA, LB = Shape<PX>::LB, H = Shape<PX>::H;
   static_assert(NC == 1 || NC == 3, "one or three components per CTA");
+  static_assert(MODE == kFuseNone || (MODE == kFuseRV || MODE == kFuseTS), "x inverse fuses the dot products");
   pdl_begin();
   extern __shared__ unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
@@ -196,6 +266,7 @@ __global__ void __launch_bounds__(256) k_x_inv(Geom g, MvData<C> d, const typena
   __syncthreads();
   const C* ia = d.ia + (int64_t)(rhs0 + b) * g.ncomp * 3;
   const int nst = NC * TY * g.nx;
+  [[maybe_unused]] kred::AccF re, im, tt;
   for (int i = threadIdx.x; i < nst; i += blockDim.x) {
     const int x = i % g.nx;
     const int r = i / g.nx;
@@ -211,7 +282,54 @@ __global__ void __launch_bounds__(256) k_x_inv(Geom g, MvData<C> d, const typena
     if (conj) pv = conjc(pv);
     const C res = cadd(in[(cl * TY + t) * ip + x], cmul(ia[cc * 3 + c], pv));
     ap[o] = io_put<C>(conj ? conjc(res) : res);
+    if constexpr (MODE == kFuseRV) {
+      kred::acc_cdot(re, im, kf->rhat[o], res);  // <rhat, v>
+    } else if constexpr (MODE == kFuseTS) {
+      kred::acc_cdot(re, im, res, kf->s[o]);     // <t, s>
+      kred::acc_nrm(tt, res);                    // |t|^2
+    }
   }
+  if constexpr (MODE == kFuseRV) {
+    double acc[2] = {re.get(), im.get()};
+    double tot[2];
+    if (kred::last_cta_totals<2>(acc, rbx->part, rbx->count, b, x_slot<NC>(), x_slots<NC>(), tot) &&
+        threadIdx.x == 0) {
+      KState& k = ksw[b];
+      if (!k.done) {
+        k.mv += 1;  // v = A p
+        const double2 rv = make_double2(tot[0], tot[1]);
+        if (rv.x == 0.0 && rv.y == 0.0) k.done = 2;
+        else k.alpha = kred::cdiv(k.rho, rv);
+      }
+    }
+  } else if constexpr (MODE == kFuseTS) {
+    double acc[3] = {re.get(), im.get(), tt.get()};
+    double tot[3];
+    if (kred::last_cta_totals<3>(acc, rbx->part, rbx->count, b, x_slot<NC>(), x_slots<NC>(), tot) &&
+        threadIdx.x == 0) {
+      KState& k = ksw[b];
+      if (!k.done) {
+        k.mv += 1;  // t = A s
+        k.omega = (tot[2] > 0.0) ? make_double2(tot[0] / tot[2], tot[1] / tot[2]) : make_double2(0.0, 0.0);
+      }
+    }
+  }
+}
+
+template <typename C, int PX, int TY, int NC = 3>
+__global__ void __launch_bounds__(256) k_x_inv(Geom g, MvData<C> d, const typename Io<C>::t* __restrict__ p,
+                                               typename Io<C>::t* __restrict__ ap, int rhs0, bool conj, int ip) {
+  x_inv_body<C, PX, TY, NC, kFuseNone>(g, d, p, ap, rhs0, conj, ip, nullptr, nullptr, nullptr);
+}
+
+// the x inverse pass with the BiCGstab dot products folded in: v = A p and <rhat, v>
+// (MODE = kFuseRV), or t = A s with <t, s> and |t|^2 (kFuseTS)
+template <int PX, int TY, int NC, int MODE>
+__global__ void __launch_bounds__(256) k_x_inv_fused(Geom g, MvData<float2> d, KrylovVecs<float2> kv, KState* ks,
+                                                     RedBuf rbx, int ip) {
+  const float2* p = MODE == kFuseRV ? kv.p : kv.s;
+  float2* ap = MODE == kFuseRV ? kv.v : kv.t;
+  x_inv_body<float2, PX, TY, NC, MODE>(g, d, p, ap, 0, false, ip, &kv, ks, &rbx);
 }
 
 // ------------------------------------------------------------------ fused y-z plane (3-pass schedule)
@@ -841,14 +959,10 @@ void optin_all(int smax) {
   }
 }
 
-// The whole product on the compile-time-length kernels (3-pass when t.plane, else 5-pass).
+// The passes between the x passes: the fused y-z plane pass (3-pass schedule, complex64 variants:
+// single CTA, cluster-split, bulk-staged), or y rows, z columns, y rows (5-pass).
 template <typename C>
-Err launch_matvec_fast(const Geom& g, const MvData<C>& d, const MvTune& t, const typename Io<C>::t* p,
-                       typename Io<C>::t* ap, int nrhs, int rhs0, bool conj, cudaStream_t st) {
-  int pass = 0;
-  mark_pass(pass++, st);
-  DDA_TRY(launch_x_fwd<C>(g, d, t, p, nrhs, conj, st));
-  mark_pass(pass++, st);
+Err launch_middle(const Geom& g, const MvData<C>& d, const MvTune& t, int nrhs, cudaStream_t st, int& pass) {
   if (t.plane) {
     if constexpr (sizeof(C) == 8) {
       if (t.clus > 1) {
@@ -873,9 +987,74 @@ Err launch_matvec_fast(const Geom& g, const MvData<C>& d, const MvTune& t, const
     mark_pass(pass++, st);
     add_launches(5);
   }
+  return Err::Ok();
+}
+
+// The whole product on the compile-time-length kernels (3-pass when t.plane, else 5-pass).
+template <typename C>
+Err launch_matvec_fast(const Geom& g, const MvData<C>& d, const MvTune& t, const typename Io<C>::t* p,
+                       typename Io<C>::t* ap, int nrhs, int rhs0, bool conj, cudaStream_t st) {
+  int pass = 0;
+  mark_pass(pass++, st);
+  DDA_TRY(launch_x_fwd<C>(g, d, t, p, nrhs, conj, st));
+  mark_pass(pass++, st);
+  DDA_TRY(launch_middle<C>(g, d, t, nrhs, st, pass));
   DDA_TRY(launch_x_inv<C>(g, d, t, p, ap, nrhs, rhs0, conj, st));
   mark_pass(pass++, st);
   return Err::Ok();
+}
+
+// ------------------------------------------------------------------ BiCGstab half-iterations, folded (complex64)
+// x-pass CTAs per RHS of the schedule t (the reduction slots of the folded dot products)
+inline int x_ctas_per_rhs(const Geom& g, const MvTune& t) {
+  const int NC = x_nc_pick(t);
+  const int TY = x_ty_pick(t, sizeof(float2), g.px);
+  return ((g.ny + TY - 1) / TY) * g.nz * (3 / NC);
+}
+
+template <int MODE, bool FWD>
+Err launch_x_fused(const Geom& g, const MvData<float2>& d, const MvTune& t, const KrylovVecs<float2>& kv, KState* ks,
+                   const RedBuf& rbx, int nrhs, cudaStream_t st) {
+  const int NC = x_nc_pick(t);
+  const int TY = x_ty_pick(t, sizeof(float2), g.px);
+  const size_t sm = x_fast_smem<float2>(g, TY, NC);
+  const dim3 grid((g.ny + TY - 1) / TY, g.nz, nrhs * (3 / NC));
+  const int ip = odd_pitch(g.nx);
+  switch (g.px) {
+#define DDA_CASE(L_)                                                                                      \
+  case L_:                                                                                                \
+    DDA_TRY((with_x<float2, L_>(NC, TY, [&](auto tyc, auto ncc) {                                        \
+      constexpr int TY_ = decltype(tyc)::value, NC_ = decltype(ncc)::value;                               \
+      if constexpr (FWD)                                                                                  \
+        DDA_CU(launch_k(k_x_fwd_fused<L_, TY_, NC_, MODE>, grid, dim3(256), sm, st, g, d, kv, ks, rbx, ip)); \
+      else                                                                                                \
+        DDA_CU(launch_k(k_x_inv_fused<L_, TY_, NC_, MODE>, grid, dim3(256), sm, st, g, d, kv, ks, rbx, ip)); \
+      return Err::Ok();                                                                                   \
+    })));                                                                                                 \
+    break;
+    DDA_FAST_LENGTHS(DDA_CASE)
+#undef DDA_CASE
+    default: return Err::make(DDA_EUNSUPPORTED, "no fast x kernel for this length");
+  }
+  DDA_CU(cudaGetLastError());
+  return Err::Ok();
+}
+
+template <int L_>
+void optin_x_fused(int smax) {
+  constexpr int D = x_ty<float2, L_>();
+  auto all_modes = [&](auto tyc, auto ncc) {
+    constexpr int TY_ = decltype(tyc)::value, NC_ = decltype(ncc)::value;
+    optin_smem(k_x_fwd_fused<L_, TY_, NC_, kFuseP>, smax);
+    optin_smem(k_x_fwd_fused<L_, TY_, NC_, kFuseS>, smax);
+    optin_smem(k_x_inv_fused<L_, TY_, NC_, kFuseRV>, smax);
+    optin_smem(k_x_inv_fused<L_, TY_, NC_, kFuseTS>, smax);
+  };
+  using I3 = std::integral_constant<int, 3>;
+  all_modes(std::integral_constant<int, D>{}, I3{});
+  if constexpr (D != 4) all_modes(std::integral_constant<int, 4>{}, I3{});
+  if constexpr (D > 8) all_modes(std::integral_constant<int, 8>{}, I3{});
+  all_modes(std::integral_constant<int, x_nc1_ty<float2>()>{}, std::integral_constant<int, 1>{});
 }
 
 }  // namespace fast

@@ -8,6 +8,10 @@ Err launch_matvec_fast<float2>(const Geom& g, const MvData<float2>& d, const MvT
   return fast::launch_matvec_fast<float2>(g, d, t, p, ap, nrhs, rhs0, conj, st);
 }
 void fast_optin_c64(int smax) { fast::optin_all<float2>(smax); }
+Err launch_middle_c64(const Geom& g, const MvData<float2>& d, const MvTune& t, int nrhs, cudaStream_t st) {
+  int pass = 0;
+  return fast::launch_middle<float2>(g, d, t, nrhs, st, pass);
+}
 
 namespace {
 // one CTA: a barrier expecting one arrival and 16 bytes that nobody sends

@@ -33,6 +33,10 @@ struct dda_ctx {
   // target
   bool have_target = false;
   dda::HostTarget tgt;
+  dda::HostTarget tgt_next;           // scratch for the next dda_setup_target (capacity reused)
+  std::vector<int32_t> h_map;         // host box -> site map of the last upload
+  int64_t uploaded_n = -1;            // site count and composition use of the last upload
+  bool uploaded_comp = false;
   int64_t n = 0;
   int32_t* d_map = nullptr;
   int32_t* d_ijk = nullptr;
@@ -214,7 +218,8 @@ Err upload_target(dda_ctx* c) {
   auto& t = c->tgt;
   const int64_t n = (int64_t)t.comp.size() / 3;
   const int64_t nbox = (int64_t)t.box[0] * t.box[1] * t.box[2];
-  std::vector<int32_t> map(nbox, -1);
+  std::vector<int32_t>& map = c->h_map;  // kept between calls: no fresh pages per target
+  map.assign(nbox, -1);
   for (int64_t j = 0; j < n; ++j) {
     const int64_t b = ((int64_t)t.ijk[3 * j + 2] * t.box[1] + t.ijk[3 * j + 1]) * t.box[0] + t.ijk[3 * j];
     map[b] = (int32_t)j;
@@ -230,15 +235,16 @@ Err upload_target(dda_ctx* c) {
   DDA_CU(cudaMemcpy(c->d_map, map.data(), sizeof(int32_t) * nbox, cudaMemcpyHostToDevice));
   DDA_CU(cudaMemcpy(c->d_ijk, t.ijk.data(), sizeof(int32_t) * 3 * n, cudaMemcpyHostToDevice));
   DDA_CU(cudaMemcpy(c->d_origin, t.origin, sizeof(double) * 3, cudaMemcpyHostToDevice));
-  const int64_t old_n = c->n;
-  const bool old_comp = c->comp_valid;
   c->comp_valid = false;
   if (t.ncomp > 1) {
     DDA_TRY(grow(c, &c->d_comp, 3 * n));
     DDA_CU(cudaMemcpy(c->d_comp, t.comp.data(), 3 * n, cudaMemcpyHostToDevice));
     c->comp_valid = true;
   }
-  if (old_n != n || old_comp != c->comp_valid) c->gen++;  // site count / composition pointer changed
+  // captured iteration graphs hold the site count and whether compositions are read
+  if (c->uploaded_n != n || c->uploaded_comp != c->comp_valid) c->gen++;
+  c->uploaded_n = n;
+  c->uploaded_comp = c->comp_valid;
   c->n = n;
   c->have_target = true;
   return Err::Ok();
@@ -850,11 +856,11 @@ static dda_status setup_sites(dda_ctx* c, const int32_t* ixyz, const int32_t* ic
   try {
     Err e = set_dev(c);
     if (!e.ok()) return fail(c, e);
-    dda::HostTarget t;
+    dda::HostTarget& t = c->tgt_next;  // built in the buffers of the target before last (warm pages)
     e = dda::make_site_target(ixyz, icomp, n, origin, a1, a2, &t, per_axis);
     if (!e.ok()) return fail(c, e);
     drop_target(c);
-    c->tgt = std::move(t);
+    std::swap(c->tgt, t);
     e = upload_target(c);
     if (!e.ok()) return fail(c, e);
     return DDA_OK;

@@ -158,16 +158,22 @@ Err make_site_target(const int32_t* ixyz, const int32_t* icomp, int64_t n, const
   for (int a = 0; a < 3; ++a)
     if ((int64_t)hi[a] - lo[a] + 1 > 4096) return Err::make(DDA_EINVAL, "site list spans more than 4096 cells");
   // x-fastest order by the box key; a list already in that order (as dda_get_sites returns it)
-  // is taken as is
-  std::vector<int64_t> keys(n);
+  // is taken as is (strictly increasing keys: sorted and free of duplicates)
+  auto key = [&](int64_t j) {
+    return (((int64_t)(ixyz[3 * j + 2] - lo[2]) * 4096 + (ixyz[3 * j + 1] - lo[1])) * 4096) + (ixyz[3 * j] - lo[0]);
+  };
   bool sorted = true;
-  for (int64_t j = 0; j < n; ++j) {
-    keys[j] = (((int64_t)(ixyz[3 * j + 2] - lo[2]) * 4096 + (ixyz[3 * j + 1] - lo[1])) * 4096) + (ixyz[3 * j] - lo[0]);
-    if (j > 0 && keys[j] <= keys[j - 1]) sorted = false;
+  for (int64_t j = 1, prev = key(0); j < n && sorted; ++j) {
+    const int64_t k = key(j);
+    sorted = k > prev;
+    prev = k;
   }
-  std::vector<int64_t> order(n);
-  for (int64_t j = 0; j < n; ++j) order[j] = j;
+  std::vector<int64_t> order;
   if (!sorted) {
+    std::vector<int64_t> keys(n);
+    for (int64_t j = 0; j < n; ++j) keys[j] = key(j);
+    order.resize(n);
+    for (int64_t j = 0; j < n; ++j) order[j] = j;
     std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return keys[a] < keys[b]; });
     for (int64_t j = 1; j < n; ++j)
       if (keys[order[j]] == keys[order[j - 1]]) return Err::make(DDA_EINVAL, "duplicate site in list");
@@ -175,14 +181,20 @@ Err make_site_target(const int32_t* ixyz, const int32_t* icomp, int64_t n, const
   out->ijk.resize(3 * n);
   out->comp.resize(3 * n);
   int maxc = 1;
-  for (int64_t s = 0; s < n; ++s) {
-    int64_t j = order[s];
-    for (int a = 0; a < 3; ++a) out->ijk[3 * s + a] = ixyz[3 * j + a] - lo[a];
-    for (int a = 0; a < 3; ++a) {
-      const int c = icomp ? icomp[per_axis ? 3 * j + a : j] : 1;
-      if (c < 1 || c > 255) return Err::make(DDA_EINVAL, "composition index must be in 1..255");
-      out->comp[3 * s + a] = (uint8_t)(c - 1);
-      maxc = std::max(maxc, c);
+  if (sorted && !icomp) {  // the common case: one material, list in order
+    for (int64_t s = 0; s < n; ++s)
+      for (int a = 0; a < 3; ++a) out->ijk[3 * s + a] = ixyz[3 * s + a] - lo[a];
+    std::fill(out->comp.begin(), out->comp.end(), (uint8_t)0);
+  } else {
+    for (int64_t s = 0; s < n; ++s) {
+      const int64_t j = sorted ? s : order[s];
+      for (int a = 0; a < 3; ++a) out->ijk[3 * s + a] = ixyz[3 * j + a] - lo[a];
+      for (int a = 0; a < 3; ++a) {
+        const int c = icomp ? icomp[per_axis ? 3 * j + a : j] : 1;
+        if (c < 1 || c > 255) return Err::make(DDA_EINVAL, "composition index must be in 1..255");
+        out->comp[3 * s + a] = (uint8_t)(c - 1);
+        maxc = std::max(maxc, c);
+      }
     }
   }
   for (int a = 0; a < 3; ++a) {

@@ -81,6 +81,24 @@ def test_site_list_target_reorders_and_rejects_duplicates(D):
     assert ei.value.status == D.DDA_EINVAL
 
 
+def test_site_list_targets_in_sequence_and_sorted_duplicates(D):
+    """One context given several site lists in turn (its host buffers are reused between calls):
+    each call's sites are exactly the new list's, in x-fastest order; a list in that order with a
+    repeated site is rejected like an unordered one."""
+    ctx = D.Context(-1)
+    for s in [(5, 6, 7), (9, 4, 3), (5, 6, 7), (2, 2, 2)]:
+        ref = o_tgt.ellipsoid(*s)
+        ctx.dda_setup_target(ref.ijk, origin=(0.0, 0.0, 0.0))
+        sites, _ = ctx.dda_get_sites()
+        np.testing.assert_array_equal(sites, ref.ijk)
+        assert ctx.n == ref.n
+    ref = o_tgt.ellipsoid(5, 6, 7)
+    dup = np.vstack([ref.ijk[:4], ref.ijk[3:4], ref.ijk[4:]])  # sorted, site 3 twice
+    with pytest.raises(D.DDAError) as ei:
+        ctx.dda_setup_target(dup)
+    assert ei.value.status == D.DDA_EINVAL
+
+
 def test_invalid_arguments_and_state(D):
     ctx = D.Context(-1)
     with pytest.raises(D.DDAError) as ei:

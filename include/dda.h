@@ -129,6 +129,11 @@ DDA_API dda_status dda_setup_target_aniso(dda_ctx *ctx, const int32_t *ixyz, con
  * origin_out[3] = TF position of box index (0,0,0).  Either may be NULL. */
 DDA_API dda_status dda_get_sites(dda_ctx *ctx, int32_t *ixyz_out, double origin_out[3]);
 
+/* The current target's site count and bounding box (cells per axis, x y z), as
+ * dda_setup_shape reports them; n_out and box_out may be NULL.  DDA_ESTATE
+ * without a target. */
+DDA_API dda_status dda_get_box(const dda_ctx *ctx, int64_t *n_out, int32_t box_out[3]);
+
 /* Incident beams (guide, "Target Orientation" and "Incident Polarization
  * State").  kd = k d (lattice wavenumber, > 0).  ori: host n_ori x 3 angles
  * (beta, Theta, Phi) in radians.  e01_lf: host 6 doubles, the Lab-Frame

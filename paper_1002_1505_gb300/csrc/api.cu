@@ -888,6 +888,15 @@ dda_status dda_get_sites(dda_ctx* c, int32_t* ixyz_out, double origin_out[3]) {
   return DDA_OK;
 }
 
+dda_status dda_get_box(const dda_ctx* c, int64_t* n_out, int32_t box_out[3]) {
+  if (!c) return DDA_EINVAL;
+  if (!c->have_target) return DDA_ESTATE;
+  if (n_out) *n_out = c->n;
+  if (box_out)
+    for (int a = 0; a < 3; ++a) box_out[a] = c->tgt.box[a];
+  return DDA_OK;
+}
+
 dda_status dda_set_incident(dda_ctx* c, double kd, const double* ori, int n_ori, const double e01_lf[6], int iorth) {
   if (!c) return DDA_EINVAL;
   if (!c->have_target) return fail(c, Err::make(DDA_ESTATE, "set a target first"));

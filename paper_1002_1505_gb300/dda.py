@@ -61,6 +61,7 @@ def _load():
         "dda_setup_target": (I, [P, P, P, I64, P, P, P]),
         "dda_setup_target_aniso": (I, [P, P, P, I64, P, P, P]),
         "dda_get_sites": (I, [P, P, P]),
+        "dda_get_box": (I, [P, P, P]),
         "dda_set_incident": (I, [P, D, P, I, P, I]),
         "dda_nrhs": (I, [P]),
         "dda_get_incidence": (I, [P, P, P]),
@@ -171,8 +172,14 @@ class Context:
         a2v = None if a2 is None else np.ascontiguousarray(a2, dtype=np.float64)
         self._check(fn(self._h, _ptr(ij), None if ic is None else _ptr(ic), ij.shape[0], _ptr(org),
                                          None if a1v is None else _ptr(a1v), None if a2v is None else _ptr(a2v)))
-        self.n = ij.shape[0]
-        self.box = tuple(int(ij[:, a].max()) - int(ij[:, a].min()) + 1 for a in range(3))
+        self.n, self.box = self.dda_get_box()
+
+    def dda_get_box(self):
+        """(N, (box_x, box_y, box_z)) of the current target."""
+        n = np.zeros(1, dtype=np.int64)
+        box = np.zeros(3, dtype=np.int32)
+        self._check(LIB.dda_get_box(self._h, _ptr(n), _ptr(box)))
+        return int(n[0]), tuple(int(v) for v in box)
 
     def dda_get_sites(self):
         out = np.zeros((self.n, 3), dtype=np.int32)

@@ -630,6 +630,31 @@ def test_warm_start_from_solution_needs_no_iterations(D):
     assert all(r["iters"] == 0 and r["converged"] for r in reps)
 
 
+@pytest.mark.parametrize("w", [W.ELLIPSOID64, W.AU_BLOCK, W.PRISM48], ids=["ellipsoid64", "au_block_5pass",
+                                                                       "prism48_b128"])
+def test_folded_bicgstab_updates_match_separate_kernels(D, monkeypatch, w):
+    """BiCGstab with its vector updates and dot products folded into the product's x passes (the
+    default) against the separate vector kernels (DDA_FUSE=0): the 3-pass and 5-pass schedules and
+    128 RHS in one batch, same iterations (the scalars are rounded to FP32 before use, so a different
+    reduction order does not reach the iterates), same products and residuals, same efficiencies."""
+    out = {}
+    for fuse in ("0", "1"):
+        monkeypatch.setenv("DDA_FUSE", fuse)
+        ctx = _ctx(D, w)
+        p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
+        reps, _ = ctx.dda_solve(p, precision="MIXED", tol=1e-5, maxit=3000)
+        q, _ = ctx.dda_cross_sections(p)
+        out[fuse] = (reps, q, p.cpu().numpy())
+        del ctx
+    (r0, q0, p0), (r1, q1, p1) = out["0"], out["1"]
+    for a, b in zip(r0, r1):
+        assert a["converged"] == 1 and b["converged"] == 1
+        assert abs(a["iters"] - b["iters"]) <= 1 and abs(a["matvecs"] - b["matvecs"]) <= 2, (a, b)
+        assert b["true_rel_resid"] <= 1e-5
+    np.testing.assert_allclose(q1[:, :3], q0[:, :3], rtol=1e-5)
+    assert np.linalg.norm(p1 - p0) / np.linalg.norm(p0) < 1e-4
+
+
 def test_graph_and_plain_launches_agree(D):
     w = SMALL[1]
     ctx = _ctx(D, w)

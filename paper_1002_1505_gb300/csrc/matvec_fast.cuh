@@ -6,6 +6,13 @@
 //
 // Ghat layout: [kx][kz][ky][6] (xx, xy, xz, yy, yz, zz), scaled by 1/M.
 // Workspace:   W[b][c][kx][z][ys], ys = ny (3-pass) or py (5-pass).
+//
+// The templates take the compute type C: float2 (complex64), double2
+// (complex128) or dfp::dfc (double-float, df.cuh: complex128 vectors in and
+// out, FP32-pair arithmetic inside; Io<C> is the vectors' element type).  The
+// x passes are bodies with a compile-time mode so that the complex64 BiCGstab
+// iteration can fold its vector updates and dot products into them
+// (k_x_fwd_fused / k_x_inv_fused, instantiated in matvec_fused_c64.cu).
 #pragma once
 
 #include "bulk.cuh"

@@ -1,10 +1,13 @@
 """Per-pass timing of the FFT-convolution product A.P for one of the bench workloads.
 
     python -m paper_1002_1505_gb300.profile_product --workload prism48 [--schedule plane512] [--iters 20]
+                                                   [--c128 | --df]
 
 Sets up the workload's target, beams, Green tensor and polarizability, then
 times `iters` products of every RHS with CUDA events between the passes
-(dda_profile_matvec) and prints the schedule and the mean time of each pass.
+(dda_profile_matvec) and prints the schedule and the mean time of each pass:
+complex64 by default, complex128 with --c128, the double-float product of the
+true residuals with --df.
 Small and short on purpose: it is the command to run under ncu for one kernel
 (`-k regex:k_yz_plane -s 2 -c 1`).
 """

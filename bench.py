@@ -355,8 +355,7 @@ def main():
     torch.cuda.set_stream(stream)
     ctx = D.Context(local, stream)
     n, box = ctx.dda_setup_shape(w.shape, w.shpar)
-    aeff = (3.0 * n / (4.0 * math.pi)) ** (1.0 / 3.0)
-    kd = w.x / aeff
+    kd, _ = ctx.dda_kd_from_x(w.x)
     e01 = [[c[0], c[1]] for c in w.e01]
     n_ori = len(w.orientations)
     nrhs = n_ori * w.iorth

@@ -134,6 +134,14 @@ DDA_API dda_status dda_get_sites(dda_ctx *ctx, int32_t *ixyz_out, double origin_
  * without a target. */
 DDA_API dda_status dda_get_box(const dda_ctx *ctx, int64_t *n_out, int32_t box_out[3]);
 
+/* Lattice wavenumber for a size parameter (guide, "Target Generation" and the
+ * definitions of a_eff and x): the target's effective radius is
+ * a_eff = (3 N / 4 pi)^(1/3) d, the radius of a sphere of volume N d^3, and
+ * x = k a_eff, so kd = x / (a_eff / d).  x > 0.  Outputs (either may be NULL):
+ * *kd_out = kd, *aeff_out = a_eff / d.  DDA_ESTATE without a target.  Host only;
+ * pass kd to dda_set_incident. */
+DDA_API dda_status dda_kd_from_x(const dda_ctx *ctx, double x, double *kd_out, double *aeff_out);
+
 /* Incident beams (guide, "Target Orientation" and "Incident Polarization
  * State").  kd = k d (lattice wavenumber, > 0).  ori: host n_ori x 3 angles
  * (beta, Theta, Phi) in radians.  e01_lf: host 6 doubles, the Lab-Frame
@@ -382,6 +390,16 @@ DDA_API dda_status dda_angular_averages(dda_ctx *ctx, const void *p_dev, double 
  * quantity over orientations is sum_o w_o Q_o).  Host only. */
 DDA_API dda_status dda_orientation_grid(const double beta_deg[2], int nbeta, const double theta_deg[2], int ntheta,
                                         const double phi_deg[2], int nphi, double *ori_out, double *w_out);
+
+/* Orientational average (guide, "Orientational Averaging"): the weighted sum
+ * over orientations <Q> = sum_o w_o Q_o, taken separately for each incident
+ * polarization.  w: host n_ori weights (from dda_orientation_grid, or any);
+ * vals: host [n_ori][iorth][nval] per-RHS results in the RHS order of
+ * dda_set_incident (e.g. the q_out rows of dda_cross_sections: nval = 4 with
+ * iorth = 2; Mueller matrices of dda_cross_sections: iorth = 1, nval = ndir x 16);
+ * out: host [iorth][nval].  FP64, summed in orientation order.  Host only. */
+DDA_API dda_status dda_orientation_average(const double *w, int n_ori, int iorth, const double *vals, int64_t nval,
+                                           double *out);
 
 /* Diagnostic (no counterpart in the guide): the product kernels stage their
  * shared-memory blocks with bulk asynchronous copies whose completion waits are

@@ -897,6 +897,16 @@ dda_status dda_get_box(const dda_ctx* c, int64_t* n_out, int32_t box_out[3]) {
   return DDA_OK;
 }
 
+dda_status dda_kd_from_x(const dda_ctx* c, double x, double* kd_out, double* aeff_out) {
+  if (!c || !(x > 0) || !std::isfinite(x)) return DDA_EINVAL;
+  if (!c->have_target || c->n <= 0) return DDA_ESTATE;
+  // a_eff = (3 N / 4 pi)^(1/3) d: the radius of a sphere of the target's volume N d^3
+  const double aeff = std::cbrt(3.0 * (double)c->n / (4.0 * 3.14159265358979323846));
+  if (kd_out) *kd_out = x / aeff;
+  if (aeff_out) *aeff_out = aeff;
+  return DDA_OK;
+}
+
 dda_status dda_set_incident(dda_ctx* c, double kd, const double* ori, int n_ori, const double e01_lf[6], int iorth) {
   if (!c) return DDA_EINVAL;
   if (!c->have_target) return fail(c, Err::make(DDA_ESTATE, "set a target first"));
@@ -1858,6 +1868,21 @@ dda_status dda_orientation_grid(const double beta_deg[2], int nbeta, const doubl
       }
     }
   }
+  return DDA_OK;
+}
+
+dda_status dda_orientation_average(const double* w, int n_ori, int iorth, const double* vals, int64_t nval,
+                                   double* out) {
+  if (!w || !vals || !out || n_ori < 1 || (iorth != 1 && iorth != 2) || nval < 1) return DDA_EINVAL;
+  for (int o = 0; o < n_ori; ++o)
+    if (!std::isfinite(w[o])) return DDA_EINVAL;
+  // out[pol][k] = sum_o w_o vals[o][pol][k], summed in orientation order in FP64
+  for (int l = 0; l < iorth; ++l)
+    for (int64_t k = 0; k < nval; ++k) {
+      double acc = 0.0;
+      for (int o = 0; o < n_ori; ++o) acc += w[o] * vals[((int64_t)o * iorth + l) * nval + k];
+      out[(int64_t)l * nval + k] = acc;
+    }
   return DDA_OK;
 }
 

@@ -63,6 +63,8 @@ def _load():
         "dda_get_sites": (I, [P, P, P]),
         "dda_get_box": (I, [P, P, P]),
         "dda_set_incident": (I, [P, D, P, I, P, I]),
+        "dda_kd_from_x": (I, [P, D, P, P]),
+        "dda_orientation_average": (I, [P, I, I, P, I64, P]),
         "dda_nrhs": (I, [P]),
         "dda_get_incidence": (I, [P, P, P]),
         "dda_incident_field": (I, [P, P, I]),
@@ -186,6 +188,15 @@ class Context:
         org = np.zeros(3, dtype=np.float64)
         self._check(LIB.dda_get_sites(self._h, _ptr(out), _ptr(org)))
         return out, org
+
+    def dda_kd_from_x(self, x: float):
+        """(kd, a_eff / d) for size parameter x of the current target."""
+        kd = ctypes.c_double()
+        aeff = ctypes.c_double()
+        st = LIB.dda_kd_from_x(self._h, float(x), ctypes.byref(kd), ctypes.byref(aeff))
+        if st != DDA_OK:
+            raise DDAError(st, "dda_kd_from_x failed (needs a target and x > 0)")
+        return float(kd.value), float(aeff.value)
 
     def dda_set_incident(self, kd: float, orientations, e01_lf=((0, 0), (1, 0), (0, 0)), iorth: int = 2):
         ori = np.ascontiguousarray(orientations, dtype=np.float64).reshape(-1, 3)
@@ -412,11 +423,20 @@ def dda_orientation_grid(beta_deg, nbeta, theta_deg, ntheta, phi_deg, nphi):
     return ori, w
 
 
-def orientation_average(q, w, iorth: int = 2):
+def dda_orientation_average(q, w, iorth: int = 2):
     """Weighted average over orientations of per-RHS results q [n_ori * iorth, ...]; returns [iorth, ...]."""
-    q = np.asarray(q)
-    q = q.reshape((len(w), iorth) + q.shape[1:])
-    return np.tensordot(np.asarray(w), q, axes=(0, 0))
+    wv = np.ascontiguousarray(w, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    tail = q.shape[1:] if q.shape[0] == len(wv) * iorth else q.shape[2:]
+    nval = int(np.prod(tail)) if len(tail) else 1
+    out = np.zeros((iorth,) + tuple(tail))
+    st = LIB.dda_orientation_average(_ptr(wv), len(wv), int(iorth), _ptr(q), nval, _ptr(out))
+    if st != DDA_OK:
+        raise DDAError(st, "dda_orientation_average failed")
+    return out
+
+
+orientation_average = dda_orientation_average
 
 
 def dda_selftest_bulk_wait(device: int = 0) -> bool:
@@ -474,8 +494,7 @@ def dda_version() -> str:
 def setup_workload(ctx: Context, w, pad=None):
     """Target, incidence, Green tensor and polarizability for a workload description."""
     ctx.dda_setup_shape(w.shape, w.shpar)
-    aeff = (3.0 * ctx.n / (4.0 * np.pi)) ** (1.0 / 3.0)
-    kd = w.x / aeff
+    kd, _ = ctx.dda_kd_from_x(w.x)
     ctx.dda_set_incident(kd, w.orientations, [[c[0], c[1]] for c in w.e01], w.iorth)
     if ctx.device >= 0:
         ctx.dda_build_green_fft(pad if pad is not None else w.pad)

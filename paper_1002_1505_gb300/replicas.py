@@ -65,7 +65,11 @@ def orientation_average_sharded(q_local, w_local: Sequence[float], iorth: int = 
     q = np.asarray(q_local, dtype=np.float64)
     w = np.asarray(w_local, dtype=np.float64)
     q = q.reshape((len(w), iorth) + q.shape[1:])
-    part = np.tensordot(w, q, axes=(0, 0)) if len(w) else np.zeros((iorth,) + q.shape[2:])
+    if len(w):
+        from . import dda  # the weighted sum is the library's dda_orientation_average
+        part = dda.dda_orientation_average(q, w, iorth)
+    else:
+        part = np.zeros((iorth,) + q.shape[2:])
     return _all_reduce(part, "sum", group).reshape(part.shape)
 
 

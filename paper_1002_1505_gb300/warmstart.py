@@ -40,8 +40,7 @@ def problem(index: int, max_box: int, device: int = 0, stream=None):
     shape, shpar, m, x, ori = W.random_unet_sample(index, max_box)
     ctx = D.Context(device, stream)
     n, box = ctx.dda_setup_shape(shape, shpar)
-    aeff = (3.0 * n / (4.0 * math.pi)) ** (1.0 / 3.0)
-    kd = min(x / aeff, 0.8 / abs(m))
+    kd = min(ctx.dda_kd_from_x(x)[0], 0.8 / abs(m))
     ctx.dda_set_incident(kd, [ori], [[0, 0], [1, 0], [0, 0]], 2)
     ctx.dda_build_green_fft()
     ctx.dda_set_polarizability("GKDLDR", m)

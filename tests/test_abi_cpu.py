@@ -164,3 +164,47 @@ def test_orientation_grid_matches_oracle(D):
         ref, wr = oori.orientation_grid(*args)
         np.testing.assert_allclose(ori, np.array(ref), rtol=0, atol=1e-13)
         np.testing.assert_allclose(w, wr, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("shape,shpar", [("ELLIPSOID", (12, 12, 12)), ("RCTGLPRSM", (32, 64, 64)),
+                                         ("HEX_PRISM", (160, 128, 6))])
+def test_kd_from_size_parameter_matches_oracle(D, shape, shpar):
+    """kd = x / (a_eff / d), a_eff = (3 N / 4 pi)^(1/3) d, from the library; the oracle's a_eff is pinned
+    to the guide's worked example (d / a_eff = 0.03173411 for the 32 x 64 x 64 block)."""
+    ctx = D.Context(-1)
+    ctx.dda_setup_shape(shape, shpar)
+    ref = o_tgt.make_target(shape, shpar)
+    for x in (1.0, 5.0, 20.0, 6.187):
+        kd, aeff = ctx.dda_kd_from_x(x)
+        assert aeff == pytest.approx(ref.aeff, rel=1e-15)
+        assert kd == pytest.approx(x / ref.aeff, rel=1e-15)
+    with pytest.raises(D.DDAError):
+        ctx.dda_kd_from_x(0.0)
+    with pytest.raises(D.DDAError):
+        D.Context(-1).dda_kd_from_x(1.0)   # no target yet
+
+
+def test_orientation_average_is_the_weighted_sum(D):
+    """dda_orientation_average: <Q>_pol = sum_o w_o Q[o, pol], per polarization; written out as loops
+    here; weights from the library's orientation grid and arbitrary ones."""
+    ori, w = D.dda_orientation_grid((0, 360), 2, (0, 180), 3, (0, 360), 2)
+    rng = np.random.default_rng(11)
+    q = rng.standard_normal((len(w) * 2, 4))
+    got = D.dda_orientation_average(q, w, 2)
+    for pol in range(2):
+        for k in range(4):
+            ref = 0.0
+            for o in range(len(w)):
+                ref += w[o] * q[2 * o + pol, k]
+            assert got[pol, k] == pytest.approx(ref, rel=1e-14, abs=1e-15)
+    # constant per-orientation values average to themselves (the weights sum to one)
+    const = np.tile(np.array([[1.5, -2.0, 0.25]]), (len(w) * 2, 1))
+    np.testing.assert_allclose(D.dda_orientation_average(const, w, 2), np.array([[1.5, -2.0, 0.25]] * 2),
+                               rtol=1e-14)
+    # Mueller-shaped values, one polarization slot: [n_ori][ndir][16]
+    m = rng.standard_normal((len(w), 3, 16))
+    got = D.dda_orientation_average(m, w, 1)
+    assert got.shape == (1, 3, 16)
+    np.testing.assert_allclose(got[0], np.einsum("o,odk->dk", w, m), rtol=1e-13, atol=1e-15)
+    with pytest.raises(D.DDAError):
+        D.dda_orientation_average(q, w, 3)

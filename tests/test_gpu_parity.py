@@ -396,6 +396,17 @@ def test_solve_sphere12_cross_sections(D, solver, precision):
     for r in reps:
         assert r["converged"] == 1 and r["true_rel_resid"] <= 1e-5
         assert r["normal_eq_ratio"] <= 1e-4
+    # the reported normal-equation ratio (guide, "Error Tolerance") against the oracle's FP64 value for
+    # the same GPU solution, with the oracle's dense A: same quantity, so agreement to rounding
+    got_p = p.cpu().numpy()
+    from oracle import solvers as osol
+    for b in range(ctx.nrhs):
+        a = oint.dense_matrix(prob.target.r, prob.kd, prob.rhs[b].inv_alpha)
+        ref = osol.normal_eq_ratio(lambda v: a @ v, got_p[b].reshape(-1), prob.rhs[b].e_inc.reshape(-1))
+        assert reps[b]["normal_eq_ratio"] == pytest.approx(ref, rel=1e-6), (b, reps[b]["normal_eq_ratio"], ref)
+        tr = np.linalg.norm(prob.rhs[b].e_inc.reshape(-1) - a @ got_p[b].reshape(-1)) / np.linalg.norm(
+            prob.rhs[b].e_inc)
+        assert abs(reps[b]["true_rel_resid"] - tr) <= 1e-10, (b, reps[b]["true_rel_resid"], tr)
     q, _ = ctx.dda_cross_sections(p)
     for b in range(ctx.nrhs):
         for i, key in enumerate(("Qext", "Qabs", "Qsca")):

@@ -196,6 +196,59 @@ def test_gkdldr_equals_lattdr_for_axis_aligned_incidence_transverse_axes():
     assert abs(ia_g[0] - ia_l[0]) > 1e-3
 
 
+def _lattdr_s(ia, m, kd):
+    """Recover Draine & Goodman's S from a LATTDR 1/alpha: the k^2 term is linear in S with slope
+    eps b3 k^2 (b3 = -1.7700004, the coefficient printed in Draine & Goodman 1993, eq. 4.1)."""
+    eps = m * m
+    s0 = polarizability.inv_alpha("LATTDR", m, kd, [1, 0, 0], [0, 1, 0])[0]  # S = 0 exactly here
+    return complex((ia - s0) / (eps * -1.7700004 * kd * kd))
+
+
+def test_lattdr_s_term_hand_value_off_axis():
+    # khat = (1,1,0)/sqrt2, e = (1,-1,0)/sqrt2: S = sum_a khat_a^2 e_a^2 = 1/4 + 1/4 = 1/2, while the
+    # plausible misreading S = (khat . e)^2 gives 0.  The expected 1/alpha was worked out by hand from
+    # Draine & Goodman (1993) eq. 4.1 with m = 1.5 + 0.1i, kd = 0.5, S = 1/2:
+    #   1/alpha_CM = (4 pi / 3)(eps + 2)/(eps - 1),  + (b1 + eps b2 + eps b3 / 2) kd^2 - (2/3) i kd^3.
+    r2 = math.sqrt(0.5)
+    ia = polarizability.inv_alpha("LATTDR", 1.5 + 0.1j, 0.5, [r2, r2, 0], [r2, -r2, 0])
+    np.testing.assert_allclose(ia, 12.886410816460371 - 2.4535841920447807j, rtol=1e-13)
+    assert abs(_lattdr_s(ia[0], 1.5 + 0.1j, 0.5) - 0.5) < 1e-12
+
+
+def test_lattdr_s_term_sums_to_one_minus_khat4_over_the_transverse_pair():
+    # For any khat and two polarizations e1, e2 that with khat form an orthonormal (unitary) basis,
+    # sum_pol |e_a|^2 = 1 - khat_a^2 for each axis a, so S(e1) + S(e2) = 1 - sum_a khat_a^4.
+    # Holds for linear and for circular pairs; the squared-complex reading (e_a^2 without modulus)
+    # fails it for circular ones, the (khat . e)^2 reading for every pair.
+    rng = np.random.default_rng(7)
+    m, kd = 1.33 + 0.05j, 0.3
+    for _ in range(6):
+        k = rng.standard_normal(3)
+        k /= np.linalg.norm(k)
+        u = np.cross(k, rng.standard_normal(3))
+        u /= np.linalg.norm(u)
+        v = np.cross(k, u)
+        for e1 in (u.astype(complex), (u + 1j * v) / math.sqrt(2),
+                   (math.cos(0.3) * u + 1j * math.sin(0.3) * v)):
+            e2 = np.cross(np.conj(e1), k)          # orthogonal to e1 and k in the Hermitian sense
+            assert abs(np.vdot(e1, e2)) < 1e-14 and abs(np.linalg.norm(e2) - 1) < 1e-14
+            s1 = _lattdr_s(polarizability.inv_alpha("LATTDR", m, kd, k, e1)[0], m, kd)
+            s2 = _lattdr_s(polarizability.inv_alpha("LATTDR", m, kd, k, e2)[0], m, kd)
+            assert abs(s1 + s2 - (1 - np.sum(k ** 4))) < 1e-10
+            assert abs(s1.imag) < 1e-12
+
+
+def test_lattdr_s_term_circular_is_the_mean_of_the_linear_pair():
+    # e = (y + i z)/sqrt2: S = (khat_y^2 + khat_z^2)/2, the mean of S(y) = khat_y^2 and S(z) = khat_z^2
+    # (an intensity-weighted reading of the dispersion relation for an elliptical field).
+    k = np.array([0.48, 0.6, 0.64])
+    m, kd = 2.0 + 0.4j, 0.45
+    s_circ = _lattdr_s(polarizability.inv_alpha("LATTDR", m, kd, k, np.array([0, 1, 1j]) / math.sqrt(2))[0], m, kd)
+    assert abs(s_circ - (0.6 ** 2 + 0.64 ** 2) / 2) < 1e-12
+    s_y = _lattdr_s(polarizability.inv_alpha("LATTDR", m, kd, k, [0, 1, 0])[0], m, kd)
+    assert abs(s_y - 0.36) < 1e-12
+
+
 # ----------------------------------------------------------------------------- interaction
 
 def _dipole_field(rvec, p, k):
@@ -340,6 +393,42 @@ def test_symmetric_krylov_terminates_at_the_number_of_distinct_eigenvalues(solve
         out = getattr(solvers, solver)(lambda v: dg * v, b, tol=1e-12, maxit=50)
         assert out[1] == k and out[2][-1] <= 1e-12, (solver, k, out[1])
         np.testing.assert_allclose(out[0], b / dg, rtol=1e-11)
+
+
+def test_normal_eq_ratio_closed_forms():
+    """The guide's stopping quantity |A^H A P - A^H E| / |A^H E| (section "Error Tolerance"): on a
+    diagonal A = diag(a) it is sqrt(sum |a_i|^2 |a_i p_i - e_i|^2) / sqrt(sum |a_i|^2 |e_i|^2), written
+    out element by element; P = 0 and P = 2 A^{-1} E give exactly 1, the solution gives 0."""
+    a = np.array([2.0 + 1.0j, -0.5 + 0.25j, 1.5 - 2.0j])
+    e = np.array([1.0 - 1.0j, 0.5j, 3.0 + 0.0j])
+    p = np.array([0.25 + 0.5j, 1.0 - 1.0j, -0.5 + 0.5j])
+    op = lambda v: a * v
+    # hand form: A^H r = conj(a) r elementwise, with r = a p - e
+    num = math.sqrt(sum(abs(ai) ** 2 * abs(ai * pi - ei) ** 2 for ai, pi, ei in zip(a, p, e)))
+    den = math.sqrt(sum(abs(ai) ** 2 * abs(ei) ** 2 for ai, ei in zip(a, e)))
+    assert abs(solvers.normal_eq_ratio(op, p, e) - num / den) < 1e-14
+    assert abs(solvers.normal_eq_ratio(op, np.zeros(3, complex), e) - 1.0) < 1e-15
+    assert abs(solvers.normal_eq_ratio(op, 2 * e / a, e) - 1.0) < 1e-14
+    assert solvers.normal_eq_ratio(op, e / a, e) < 1e-15
+
+
+def test_normal_eq_ratio_on_the_dda_system():
+    """On the complex-symmetric DDA matrix, A^H = conj(A conj(.)) must be the conjugate transpose of
+    the dense matrix: the ratio equals |A^H (A P - E)| / |A^H E| formed with the explicit dense A^H,
+    vanishes at the LU solution and is 1 at P = 0."""
+    w = W.SPHERE12
+    prob = dda.build_problem(w.shape, w.shpar, w.m, w.x, w.prescription, w.orientations)
+    rh = prob.rhs[0]
+    a = interaction.dense_matrix(prob.target.r, prob.kd, rh.inv_alpha)
+    e = rh.e_inc.reshape(-1)
+    op = lambda v: a @ v
+    p_lu = solvers.lu_solve(a, e)
+    assert solvers.normal_eq_ratio(op, p_lu, e) < 1e-12
+    assert abs(solvers.normal_eq_ratio(op, np.zeros_like(e), e) - 1.0) < 1e-14
+    p = p_lu + 1e-3 * W.seeded_vector(e.shape, 5)
+    ah = a.conj().T
+    ref = np.linalg.norm(ah @ (a @ p - e)) / np.linalg.norm(ah @ e)
+    assert abs(solvers.normal_eq_ratio(op, p, e) / ref - 1.0) < 1e-12
 
 
 def test_qmr_cs_quasi_residual_bounds_the_residual():

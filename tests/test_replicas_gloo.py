@@ -19,6 +19,14 @@ import torch.multiprocessing as mp  # noqa: E402
 from paper_1002_1505_gb300 import replicas  # noqa: E402
 
 
+@pytest.fixture(scope="module", autouse=True)
+def _library_built():
+    # the weighted orientation sum runs in the C-ABI library (host-only entry point)
+    from paper_1002_1505_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+
+
 @pytest.mark.parametrize("world", [1, 2, 3, 4, 7])
 def test_shard_covers_every_orientation_once(world):
     for n in range(0, 40):

@@ -194,7 +194,9 @@ def run_reference(args, w):
     ghat = oint.green_fft(prob.target.box, prob.pad, prob.kd, workers=-1)
     rng = np.random.default_rng(1)
     p = rng.standard_normal((3, prob.target.n)) + 1j * rng.standard_normal((3, prob.target.n))
-    per_step = min(len(prob.rhs), 2)
+    # a bounded sample of the workload's products per step: two RHS on the small grids, one on the
+    # multi-million-point grids (each FP64 product there takes seconds on the host cores)
+    per_step = min(len(prob.rhs), 2 if np.prod(prob.pad) < 4_000_000 else 1)
 
     def step():
         for b in range(per_step):
@@ -320,9 +322,20 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="ellipsoid64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="hexprism160", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--plain-reps", type=int, default=2)
+    ap.add_argument("--plain-reps", type=int, default=1)
+    ap.add_argument("--plain-orientations", type=int, default=0,
+                    help="orientations the plain FP64 comparator solves (0 = all; default 2 on the hexagonal "
+                         "prism, whose plain solve takes seconds per orientation)")
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="timed steps of the end-to-end leg (0 = min(steps, as many as fit in ~30 s))")
+    ap.add_argument("--unet-problems", type=int, default=2048,
+                    help="random training problems for the in-bench network of the warm-start leg (0 = no network)")
+    ap.add_argument("--unet-steps", type=int, default=4000)
+    ap.add_argument("--warm-start", default="auto", choices=["auto", "on", "off"],
+                    help="also time the solve warm-started from the network-free guess alpha E_inc "
+                         "(auto = on for the hexagonal prism)")
     ap.add_argument("--orientations", type=int, default=0,
                     help="use only the first N orientations of the workload (smaller profiling runs)")
     args = ap.parse_args()
@@ -357,17 +370,28 @@ def main():
     n, box = ctx.dda_setup_shape(w.shape, w.shpar)
     kd, _ = ctx.dda_kd_from_x(w.x)
     e01 = [[c[0], c[1]] for c in w.e01]
-    n_ori = len(w.orientations)
+    # replica mode: each rank solves its contiguous share of the orientations (independent systems
+    # sharing the target; nothing is exchanged on the data path)
+    a_o, b_o = replicas.shard(len(w.orientations), rank, ws)
+    my_ori = list(w.orientations[a_o:b_o])
+    n_ori = len(my_ori)
+    if n_ori == 0:
+        raise SystemExit(f"rank {rank}: no orientations left for this rank ({len(w.orientations)} over {ws})")
     nrhs = n_ori * w.iorth
     p = torch.zeros((nrhs, 3, n), dtype=torch.complex128, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    def step(precision="MIXED", use_graph=True):
-        ctx.dda_set_incident(kd, w.orientations, e01, w.iorth)
+    def step(precision="MIXED", use_graph=True, ori=None, warm=None):
+        ori = my_ori if ori is None else ori
+        pp = p[:len(ori) * w.iorth]
+        ctx.dda_set_incident(kd, ori, e01, w.iorth)
         ctx.dda_build_green_fft(w.pad)
         ctx.dda_set_polarizability(w.prescription, w.m)
-        reps, _ = ctx.dda_solve(p, solver="BICGSTAB", precision=precision, tol=1e-5, maxit=3000, use_graph=use_graph)
-        q, mm = ctx.dda_cross_sections(p, MUELLER_DIRS if w.iorth == 2 else None)
+        if warm is not None:
+            pp.copy_(warm(ctx))
+        reps, _ = ctx.dda_solve(pp, solver="BICGSTAB", precision=precision, tol=1e-5, maxit=3000,
+                                use_graph=use_graph, warm_start=warm is not None)
+        q, mm = ctx.dda_cross_sections(pp, MUELLER_DIRS if w.iorth == 2 else None)
         return reps, q
 
     def timed(nsteps, **kw):
@@ -396,28 +420,64 @@ def main():
     launches = D.dda_kernel_launches() - k0
     torch.cuda.synchronize()
     clk = clocks.stop()
+    my_ms = total_ms
     if ws > 1:
         total_ms, matvecs = replicas.reduce_max_sum(total_ms, float(matvecs))
     value = matvecs / (total_ms / 1e3)
     ms_step = total_ms / args.steps
+    # the guide's orientation average (equal weights for the seeded uniform orientations), gathered
+    # from every rank's share
+    w_all = np.full(len(w.orientations), 1.0 / len(w.orientations))
+    q_avg = replicas.orientation_average_sharded(q[:, :3], w_all[a_o:b_o], w.iorth,
+                                                 group=None) if ws > 1 else D.dda_orientation_average(
+                                                     q[:, :3], w_all[a_o:b_o], w.iorth)
 
-    # plain FP64 GPU comparator: complex128 BiCGstab, no refinement, one launch per kernel
-    plain_ms, plain_mv, (preps, pq) = timed(args.plain_reps, precision="C128", use_graph=False)
-    plain_ms /= args.plain_reps
+    # plain FP64 GPU comparator: complex128 BiCGstab, no refinement, one launch per kernel, on the
+    # first few orientations (it takes seconds per orientation on the large grids)
+    n_plain = args.plain_orientations or (2 if np.prod(w.pad or (1,)) > 8_000_000 else n_ori)
+    plain_ori = my_ori[:max(1, min(n_plain, n_ori))]
+    plain_ms, plain_mv, (preps, pq) = timed(args.plain_reps, precision="C128", use_graph=False, ori=plain_ori)
+    plain_ms_per_ori = plain_ms / args.plain_reps / len(plain_ori)
+
+    # warm-started solves (config 5: the same mixed-precision solve from an initial guess): the
+    # network-free local-field guess P0 = alpha E_inc, and the learned network's guess when a short
+    # in-bench training is asked for; iterations and time at the same final residual as the cold solve
+    warm_report = None
+    want_warm = args.warm_start == "on" or (args.warm_start == "auto" and w is WORKLOADS["hexprism160"])
+    if want_warm and ws == 1:
+        from paper_1002_1505_gb300 import warmstart as WS
+        warm_report = {"cold": {"iterations": int(sum(r["iters"] for r in reps)), "ms_per_orientation": ms_step / n_ori,
+                                "max_true_rel_resid": float(max(r["true_rel_resid"] for r in reps))}}
+        grid = WS.grid_dims(box)
+        guesses = {"alpha_einc": lambda c: WS.local_field_guess(c, grid)}
+        if args.unet_problems > 0:
+            t0 = time.perf_counter()
+            net = WS.train_quick(args.unet_problems, args.unet_steps)
+            warm_report["network_training_s"] = time.perf_counter() - t0
+            warm_report["network_training"] = {"problems": args.unet_problems, "steps": args.unet_steps,
+                                               "max_box": 16, "params": int(net.nparams)}
+            guesses["network"] = lambda c: WS.warm_guess(c, net, grid, chunk=2)
+        for nm, fn in guesses.items():
+            wms, wmv, (wreps, _) = timed(1, warm=fn)
+            warm_report[nm] = {"iterations": int(sum(r["iters"] for r in wreps)), "ms_per_orientation": wms / n_ori,
+                               "max_true_rel_resid": float(max(r["true_rel_resid"] for r in wreps)),
+                               "includes": "guess construction + solve + observables"}
+        step()  # leave the context on the cold configuration
 
     # end to end through the C ABI with host buffers: site list in, solution P and Q out
     sites, origin = ctx.dda_get_sites()
     h_sites = np.ascontiguousarray(sites)
     h_p = torch.empty((nrhs, 3, n), dtype=torch.complex128, pin_memory=True)
     ctx2 = D.Context(local, stream)
+    e2e_steps = args.e2e_steps or max(2, min(args.steps, int(30e3 / max(ms_step, 1.0))))
     e2e_ms = 0.0
     e2e_mv = 0
-    for i in range(args.warmup + args.steps):
+    for i in range(1 + e2e_steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx2.dda_setup_target(h_sites, origin=origin)
-        ctx2.dda_set_incident(kd, w.orientations, e01, w.iorth)
+        ctx2.dda_set_incident(kd, my_ori, e01, w.iorth)
         ctx2.dda_build_green_fft(w.pad)
         ctx2.dda_set_polarizability(w.prescription, w.m)
         p2 = torch.zeros((nrhs, 3, n), dtype=torch.complex128, device="cuda")
@@ -426,9 +486,13 @@ def main():
         h_p.copy_(p2, non_blocking=True)
         torch.cuda.current_stream().synchronize()
         dt = time.perf_counter() - t0
-        if i >= args.warmup:
+        if i >= 1:
             e2e_ms += dt * 1e3
             e2e_mv += sum(r["matvecs"] for r in r2)
+    ctx2.close()
+    del p2
+    if ws > 1:
+        e2e_ms, e2e_mv = replicas.reduce_max_sum(e2e_ms, float(e2e_mv))
     e2e_value = e2e_mv / (e2e_ms / 1e3)
     h2d = h_sites.nbytes + 3 * n_ori * 8 + 48
     d2h = h_p.numel() * 16 + q2.nbytes
@@ -486,20 +550,27 @@ def main():
             "metric": METRIC, "value": value, "unit": "matvecs/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
-            "config": {"workload": w.name, "n_dipoles": n, "box": list(box), "pad": list(pad), "nrhs": nrhs,
-                       "n_orientations": n_ori, "tol": 1e-5, "solver": "BiCGstab, complex64 + FP64-accurate refinement",
+            "config": {"workload": w.name, "n_dipoles": n, "box": list(box), "pad": list(pad),
+                       "nrhs": nrhs * ws, "n_orientations": len(w.orientations), "tol": 1e-5,
+                       "solver": "BiCGstab, complex64 + FP64-accurate refinement",
                        "true_residual": "double-float product (FP32 pairs, within 1e-12 of FP64) where the grid "
                                         "has compile-time kernels, else complex128",
-                       "l2": "flushed (512 MB write) before every step", "parallelism": f"replicas x{args.gpus}"},
+                       "l2": "flushed (512 MB write) before every step",
+                       "parallelism": f"replicas x{ws}: orientations sharded over ranks, "
+                                      f"{n_ori} orientations ({nrhs} RHS) per rank"},
             "solve_ms_per_orientation": ms_step / n_ori,
-            "plain_fp64_solve_ms_per_orientation": plain_ms / n_ori,
-            "speedup_vs_plain_fp64": plain_ms / ms_step,
+            "plain_fp64_solve_ms_per_orientation": plain_ms_per_ori,
+            "plain_fp64_orientations_timed": len(plain_ori),
+            "speedup_vs_plain_fp64": plain_ms_per_ori / (ms_step / n_ori),
             "iterations": [r["iters"] for r in reps], "plain_iterations": [r["iters"] for r in preps],
             "true_rel_resid": [r["true_rel_resid"] for r in reps],
             "true_residual_product_ms": fp64_products,
             "Q": {"Qext": q[:, 0].tolist(), "Qabs": q[:, 1].tolist(), "Qsca": q[:, 2].tolist()},
+            "Q_orientation_average": {"Qext": q_avg[:, 0].tolist(), "Qabs": q_avg[:, 1].tolist(),
+                                      "Qsca": q_avg[:, 2].tolist(), "per": "incident polarization"},
+            "warm_start": warm_report,
             "e2e": {"value": e2e_value, "unit": "matvecs/s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms / args.steps},
+                    "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms / e2e_steps, "steps": e2e_steps},
             "gpu_launches": int(launches),
             "roofline": roofline,
             "clocks": clk,

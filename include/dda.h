@@ -199,14 +199,23 @@ DDA_API dda_status dda_matvec(dda_ctx *ctx, const void *p_dev, void *ap_dev, int
  * (sizeof(complex) x 3 x Px x Nz x Ys per RHS, Ys = Ny on the 3-pass schedule,
  * Py on the 5-pass one) exceeds 32 MiB return DDA_EINVAL with the sizes in the
  * message.  The call makes no cudaMalloc, cudaFree or other allocating call.
- * The first call on a device looks up the array's device address with that
- * device current (a one-time set-up); make that first call before any stream
- * capture.  Every call shares the one array and it keeps the last call's
- * contents; nothing in it has to start at zero because each pass writes all
- * the scratch the next pass reads.  Calls whose work overlaps on the GPU (other
- * streams, other threads, other contexts on the same device) race on the array:
- * serialize them.  The context must already hold the Green tensor and the
- * polarizabilities (both allocated earlier by their own calls).  Enqueue only. */
+ * The array's device address is looked up once per device, with that device
+ * current, by the first dda_build_green_fft on the device (a prerequisite of
+ * this call; the array sits in the same device module as the Green-tensor
+ * kernels that call has just run, so the lookup loads nothing new); this call
+ * then only reads the cached address.  Do not reset the device
+ * (cudaDeviceReset) between dda_build_green_fft and this call: a reset unloads
+ * the module and the cached address would be stale.  Every call shares the one
+ * array and it keeps the last call's contents; nothing in it has to start at
+ * zero because each pass writes all the scratch the next pass reads.  Calls
+ * whose work overlaps on the GPU (other streams, other threads, other contexts
+ * on the same device) race on the array: serialize them.  The context must
+ * already hold the Green tensor and the polarizabilities (both allocated
+ * earlier by their own calls).  The product uses the context's schedule, except
+ * that it stages the plane pass with bulk copies only when the context already
+ * has its fault flag (made by an earlier dda_matvec or dda_solve): a bounded
+ * bulk-copy wait that gives up is reported only through that flag, by the next
+ * synchronizing call (dda_solve, dda_profile_matvec) as DDA_ECUDA.  Enqueue only. */
 DDA_API dda_status dda_matvec_noalloc(dda_ctx *ctx, const void *p_dev, void *ap_dev, int nrhs, int dtype);
 
 typedef struct {

@@ -1146,6 +1146,14 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
     if (!e.ok()) return fail(c, e);
     c->ghatdf_valid = want_df;
     c->have_green = true;
+    // set-up of dda_matvec_noalloc, once per device with this device current: look up the device
+    // address of its fixed scratch array (the array sits in the module of the Green-tensor kernels
+    // just launched, so the lookup loads nothing new)
+    {
+      void* scratch = nullptr;
+      e = dda::noalloc_scratch(c->device, &scratch);
+      if (!e.ok()) return fail(c, e);
+    }
     return DDA_OK;
   } catch (const std::bad_alloc&) {
     return fail(c, Err::make(DDA_ENOMEM, "host allocation failed"));
@@ -1632,7 +1640,11 @@ Err matvec_fixed_scratch(dda_ctx* c, const C* p, C* ap, int nrhs) {
   DDA_TRY(dda::noalloc_scratch(c->device, &scratch));
   dda::MvData<C> d = Sel<C>::data(c);
   d.work = (C*)scratch;
-  return dda::launch_matvec<C>(g, d, Sel<C>::tune(c), p, ap, nrhs, 0, false, c->stream);
+  dda::MvTune t = Sel<C>::tune(c);
+  // a bulk-staged plane pass reports a bounded wait that gave up through the context's fault
+  // flag; without that flag (no earlier allocating call made it) run the plane pass unstaged
+  if (!d.fault) t.bulk = false;
+  return dda::launch_matvec<C>(g, d, t, p, ap, nrhs, 0, false, c->stream);
 }
 }  // namespace
 

@@ -176,6 +176,18 @@ def local_field_guess(ctx: "D.Context", grid=None):
     return p
 
 
+def train_quick(problems: int, steps: int, max_box: int = 16, widths=(16, 32, 48, 64), seed: int = 5):
+    """A network trained from scratch on `problems` random problems (two solutions each) for `steps`
+    AdamW steps of 16 samples, output layer zeroed at start (the recipe of main(), smaller)."""
+    grid = (max_box, max_box, max_box)
+    X, T, M, _ = generate(list(range(problems)), max_box, grid)
+    net = D.UNet(0, None, CIN, COUT, tuple(widths), seed=seed)
+    zero_head(net)
+    train(net, X, T, M, grid, steps=steps, batch=16, lr=1e-3)
+    del X, T, M
+    return net
+
+
 def evaluate(net: "D.UNet", indices, max_box: int, grid=None, tol: float = 1e-5):
     """Iterations to tol (true residual) from a cold start, the alpha E_inc guess and the network guess."""
     import torch

@@ -58,6 +58,34 @@ def test_noalloc_product_matches_allocating_product_twice(D, w, nr64, nr128):
         assert ei.value.status == D.DDA_EINVAL
 
 
+def test_noalloc_first_on_a_fresh_context_allocates_nothing(D):
+    """On a freshly set-up context whose first product is dda_matvec_noalloc: device free memory is
+    the same before and after a call (outputs allocated beforehand), and only then is the result
+    compared with dda_matvec's."""
+    w = W.Workload("ell_fresh", "ELLIPSOID", (9, 7, 11), 1.4 + 0.2j, 2.5, "LATTDR", W.uniform_orientations(2, 23))
+    ctx = D.Context(0)
+    D.setup_workload(ctx, w)
+    for dt, tol in ((torch.complex64, 1e-5), (torch.complex128, 1e-12)):
+        p = torch.from_numpy(W.seeded_vector((ctx.nrhs, 3, ctx.n), 43)).to(dt).cuda()
+        outs = [torch.full_like(p, float("nan")) for _ in range(3)]
+        torch.cuda.synchronize()
+        ctx.dda_matvec_noalloc(p, outs[0])  # first product of this context
+        torch.cuda.synchronize()
+        for k in (1, 2):
+            free0 = torch.cuda.mem_get_info()[0]
+            ctx.dda_matvec_noalloc(p, outs[k])
+            torch.cuda.synchronize()
+            assert torch.cuda.mem_get_info()[0] == free0, (dt, k)
+        ref = torch.empty_like(p)
+        ctx.dda_matvec(p, ref)
+        torch.cuda.synchronize()
+        ref_np = ref.cpu().numpy().astype(np.complex128)
+        for k in range(3):
+            got = outs[k].cpu().numpy().astype(np.complex128)
+            assert np.isfinite(got).all()
+            assert np.linalg.norm(got - ref_np) / np.linalg.norm(ref_np) <= tol, (dt, k)
+
+
 def test_noalloc_rejects_requests_beyond_the_fixed_scratch(D):
     ctx = D.Context(0)
     D.setup_workload(ctx, W.PRISM48)  # 128 RHS x 5.3 MB of complex64 scratch each

@@ -77,7 +77,19 @@ enum { DDA_CM = 1, DDA_LATTDR = 2, DDA_GKDLDR = 3 };
  * equations, Petravic & Kuo-Petravic 1979, the guide's PETRKP) and
  * BiCGstab(2) (Sleijpen & Fokkema 1993, the method family of the guide's
  * recommended PBCGS2, without that routine's reliability refinements). */
-enum { DDA_BICGSTAB = 1, DDA_CCG = 2, DDA_BICGSTAB2 = 3 };
+enum { DDA_BICGSTAB = 1, DDA_CCG = 2, DDA_BICGSTAB2 = 3, DDA_COCG = 4 };
+/* DDA_COCG: conjugate orthogonal conjugate gradients (van der Vorst & Melissen
+ * 1990), CG with the unconjugated form x^T y, valid because A is complex
+ * symmetric (A^T = A); one product per iteration (the complex-symmetric
+ * Lanczos family of the guide's QMRCCG option). */
+/* Preconditioning of the iterations (guide, "Choice of Iterative Algorithm":
+ * the guide's solvers are preconditioned Krylov methods): none, or Jacobi, the
+ * diagonal of A, applied symmetrically -- the solver iterates on
+ * (S A S) y = S E with S = diag(alpha^{1/2}) and returns P = S y, which keeps
+ * the operator complex symmetric for DDA_COCG; its stopping test uses the
+ * scaled residual |S (E - A P)| / |S E| (the reported true residual is
+ * unscaled). */
+enum { DDA_PRECOND_NONE = 0, DDA_PRECOND_JACOBI = 1 };
 /* Arithmetic of the solve: all complex64, all complex128, or complex64 inner
  * iterations refined against complex128 true residuals. */
 enum { DDA_PREC_C64 = 1, DDA_PREC_C128 = 2, DDA_PREC_MIXED = 3 };
@@ -124,6 +136,23 @@ DDA_API dda_status dda_setup_target(dda_ctx *ctx, const int32_t *ixyz, const int
  * polarizability of its axis-a composition. */
 DDA_API dda_status dda_setup_target_aniso(dda_ctx *ctx, const int32_t *ixyz, const int32_t *icomp3, int64_t n,
                                   const double origin_tf[3], const double a1[3], const double a2[3]);
+
+/* The guide's ANIFRMFIL target (section "ANIFRMFIL = General anisotropic
+ * target"; "Composite Targets with Anisotropic Constituents"): like
+ * dda_setup_target_aniso, plus df_angles host N x 3 = (theta_DF, phi_DF,
+ * beta_DF) in radians, the orientation of each site's Dielectric Frame (the
+ * principal axes e_1, e_2, e_3 of its dielectric tensor) relative to the TF by
+ * the guide's three rotations; icomp3[j][a] is the composition along e_a.
+ * dda_set_polarizability then gives each site the full symmetric tensor
+ * alpha^{-1} = sum_a d_a e_a e_a^T, d_a the prescription's alpha^{-1} for the
+ * composition of axis a with the incidence (khat, polarization) projected on
+ * the principal axes (for zero angles this is exactly dda_setup_target_aniso).
+ * Products, solves and efficiencies then use the full tensor; the Jacobi
+ * preconditioner returns DDA_EUNSUPPORTED and true residuals use the complex128
+ * product (no DDA_C128DF) for such targets. */
+DDA_API dda_status dda_setup_target_anifrm(dda_ctx *ctx, const int32_t *ixyz, const int32_t *icomp3, int64_t n,
+                                           const double origin_tf[3], const double a1[3], const double a2[3],
+                                           const double *df_angles);
 
 /* Copy the site list out: ixyz_out host N x 3 (box-relative lattice indices),
  * origin_out[3] = TF position of box index (0,0,0).  Either may be NULL. */
@@ -219,7 +248,7 @@ DDA_API dda_status dda_matvec(dda_ctx *ctx, const void *p_dev, void *ap_dev, int
 DDA_API dda_status dda_matvec_noalloc(dda_ctx *ctx, const void *p_dev, void *ap_dev, int nrhs, int dtype);
 
 typedef struct {
-  int solver;        /* DDA_BICGSTAB, DDA_CCG or DDA_BICGSTAB2 */
+  int solver;        /* DDA_BICGSTAB, DDA_CCG, DDA_BICGSTAB2 or DDA_COCG */
   int precision;     /* DDA_PREC_C64 / DDA_PREC_C128 / DDA_PREC_MIXED */
   double tol;        /* stop when |E - A P| / |E| <= tol for every RHS */
   int maxit;         /* iteration cap (inner iterations summed for MIXED) */
@@ -231,6 +260,7 @@ typedef struct {
   int check_every;   /* iterations between host convergence checks (0 = 8; BiCGstab(2): cycles of two iterations) */
   int normal_eq;     /* 1 = also evaluate the guide's normal-equation ratio at exit (2 extra FP64 products) */
   int use_graph;     /* 1 = replay the iterations as a captured CUDA graph, 0 = plain launches */
+  int precond;       /* DDA_PRECOND_NONE or DDA_PRECOND_JACOBI */
 } dda_solve_opts;
 
 typedef struct {
@@ -387,6 +417,37 @@ DDA_API dda_status dda_unet_residual_grad(dda_ctx *ctx, const float *y_dev, cons
  * block totals.  Synchronizes. */
 DDA_API dda_status dda_angular_averages(dda_ctx *ctx, const void *p_dev, double eta, double *out,
                                         int32_t *ndir_out);
+
+/* Radiative force and torque efficiency vectors (guide, "Calculation of
+ * <cos theta>, Radiative Force, and Radiation Torque"): Q_pr = F_rad /
+ * (pi a_eff^2 u_rad) and Q_Gamma = k Gamma_rad / (pi a_eff^2 u_rad), u_rad =
+ * |E0|^2 / 8 pi, for a solved P (complex128 [nrhs][3][N], device).  The force
+ * is Q_ext khat - Q_sca g; the torque (about the centroid of the sites) is the
+ * incident field's torque on the dipoles, sum_j [1/2 Re(P_j x E_inc,j^*) +
+ * (k/2) Im(P_j . E_inc,j^*) r_j x khat], plus the torque of the array's own
+ * radiative field, (k^3/8pi) oint Im[g x f^*] - (k^4/8pi) oint Re[h] x n with
+ * g = sum_j P_j exp(-i k n.r_j), f = g - n (n.g), h = T f^*, T[c][a] =
+ * sum_j r_jc P_ja exp(-i k n.r_j), integrated over the guide's scattering
+ * directions for eta (as dda_angular_averages; the guide notes that both
+ * vectors need an adequate ETASCA).  out: host nrhs x 6 = Q_pr then Q_Gamma,
+ * Target-Frame components.  *ndir_out (may be NULL) = directions used.
+ * Far-field sums in FP32 from FP64 phase tables, totals in FP64.  Synchronizes. */
+DDA_API dda_status dda_force_torque(dda_ctx *ctx, const void *p_dev, double eta, double *out, int32_t *ndir_out);
+
+/* Electric and magnetic fields in or near the target (guide, "Postprocessing:
+ * Calculating E and B In or Near the Target", the DDfield program) for a
+ * solved P (complex128 [nrhs][3][N], device): at each point x (host npts x 3,
+ * Target-Frame coordinates in lattice units) E = E_inc + sum_j phi(R_j)
+ * E_dip and B = B_inc + sum_j phi(R_j) B_dip, the retarded fields of the
+ * oscillating point dipoles P_j at distance R_j = |x - r_j|, with the incident
+ * plane wave E_inc = e exp(i k.x), B_inc = khat x E_inc (Gaussian units, time
+ * factor exp(-i w t) = 1).  The contribution of dipoles closer than one lattice
+ * spacing is suppressed by phi(R) = R^4 (5 - 4 R) (R < 1; phi = 1 beyond), a
+ * factor vanishing faster than R^3 as the guide asks.  e_out / b_out: host
+ * [nrhs][npts][6] = (re, im) of x, y, z; b_out may be NULL.  Direct FP64 sum
+ * over all dipoles on the device (O(N npts)).  Synchronizes. */
+DDA_API dda_status dda_near_field(dda_ctx *ctx, const void *p_dev, const double *pts, int64_t npts, double *e_out,
+                                  double *b_out);
 
 /* Orientation grid for orientational averaging (guide, "Sampling in Theta,
  * Phi, and beta" and "Orientational Averaging"): beta and Phi at the midpoints

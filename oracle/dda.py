@@ -22,7 +22,7 @@ class Rhs:
     e01_lf: np.ndarray
     e02_lf: Optional[np.ndarray]
     axes: tuple           # x_LF, y_LF, z_LF in TF
-    inv_alpha: np.ndarray  # (N, 3) complex diagonal of alpha^{-1}
+    inv_alpha: np.ndarray  # (N, 3) complex diagonal of alpha^{-1}, or (N, 3, 3) full tensors
     e_inc: np.ndarray     # (3, N) complex incident field
 
 
@@ -36,11 +36,15 @@ class Problem:
 
 
 def build_problem(shape, shpar, m, x, prescription, orientations, e01_lf=((0, 0), (1, 0), (0, 0)),
-                  iorth=2, pad=None, target=None, kd=None, comp=None) -> Problem:
+                  iorth=2, pad=None, target=None, kd=None, comp=None, df_angles=None) -> Problem:
     """comp (optional): per-site composition indices (0-based) in the target's site order, shape
     (N,) for isotropic materials or (N, 3) for one composition per Cartesian axis (the guide's
     ICOMP triple of an anisotropic material whose principal axes are the TF axes); m is then a
-    sequence of refractive indices, one per composition."""
+    sequence of refractive indices, one per composition.
+    df_angles (optional, with comp (N, 3)): per-site (theta_DF, phi_DF, beta_DF) of the Dielectric
+    Frame (the guide's ANIFRMFIL target): comp[j, a] is the composition along the principal axis
+    e_a, and alpha_j^{-1} = sum_a d_a e_a e_a^T (a full symmetric 3 x 3), d_a the prescription's
+    value for that composition with the incidence (khat, e) expressed along e_1, e_2, e_3."""
     tgt = targets.make_target(shape, shpar) if target is None else target
     if kd is None:
         kd = x / tgt.aeff            # k d = x / (a_eff / d)
@@ -52,7 +56,17 @@ def build_problem(shape, shpar, m, x, prescription, orientations, e01_lf=((0, 0)
     for ori in orientations:
         k_tf, pols_tf, pols_lf, axes = orientation.incidence(kd, ori, tgt.a1, tgt.a2, e01, iorth)
         for l, e_tf in enumerate(pols_tf):
-            if comp is None:
+            if df_angles is not None:
+                cj = np.asarray(comp, dtype=np.int64)
+                inv_alpha = np.zeros((tgt.n, 3, 3), dtype=np.complex128)
+                for j in range(tgt.n):
+                    axes_df = orientation.dielectric_axes(*df_angles[j])
+                    kdf = np.array([np.dot(k_tf / kd, ea) for ea in axes_df])
+                    edf = np.array([np.dot(e_tf, ea) for ea in axes_df])
+                    for a, ea in enumerate(axes_df):
+                        d_a = polarizability.inv_alpha(prescription, m[cj[j, a]], kd, kdf, edf)[a]
+                        inv_alpha[j] += d_a * np.outer(ea, ea)
+            elif comp is None:
                 ia = polarizability.inv_alpha(prescription, m, kd, k_tf / kd, e_tf)
                 inv_alpha = np.tile(ia, (tgt.n, 1))
             else:

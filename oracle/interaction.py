@@ -25,6 +25,19 @@ from __future__ import annotations
 import numpy as np
 
 
+def diagonal_term(inv_alpha: np.ndarray, p: np.ndarray) -> np.ndarray:
+    """alpha_j^{-1} P_j for every site: inv_alpha (N, 3) diagonal or (N, 3, 3) full tensors
+    (rotated anisotropic materials); p (3, N) -> (3, N)."""
+    if inv_alpha.ndim == 2:
+        return inv_alpha.T * p
+    return np.einsum("jab,bj->aj", inv_alpha, p)
+
+
+def diag_block(inv_alpha: np.ndarray, j: int) -> np.ndarray:
+    """The 3 x 3 diagonal block A_jj = alpha_j^{-1}."""
+    return np.diag(inv_alpha[j]) if inv_alpha.ndim == 2 else inv_alpha[j]
+
+
 def green_block(rvec: np.ndarray, k: float) -> np.ndarray:
     """A_jk for separation vectors rvec (..., 3) (nonzero). Returns (..., 3, 3) complex."""
     rvec = np.asarray(rvec, dtype=np.float64)
@@ -48,7 +61,7 @@ def dense_matrix(r: np.ndarray, kd: float, inv_alpha_diag: np.ndarray) -> np.nda
         d = r[j][None, :] - r
         d[j] = 1.0  # placeholder, overwritten below
         blk = green_block(d, kd)  # (N,3,3)
-        blk[j] = np.diag(inv_alpha_diag[j])
+        blk[j] = diag_block(inv_alpha_diag, j)
         a[:, j, :, :] = np.transpose(blk, (1, 2, 0))
     return a.reshape(3 * n, 3 * n)
 
@@ -68,7 +81,7 @@ def matvec_direct(r: np.ndarray, kd: float, inv_alpha_diag: np.ndarray, p: np.nd
         blk = green_block(d, kd)                         # (c, N, 3, 3)
         blk[self_mask] = 0.0
         acc = np.einsum("jkab,kb->ja", blk, pt)
-        acc += inv_alpha_diag[rj] * pt[rj]
+        acc += diagonal_term(inv_alpha_diag[rj], p[:, rj]).T
         out[:, s:s + rj.size] = acc.T
     return out
 
@@ -131,7 +144,7 @@ def matvec_fft(ijk: np.ndarray, box, kd: float, inv_alpha_diag: np.ndarray, p: n
         acc = ghat[a, 0] * phat[0] + ghat[a, 1] * phat[1] + ghat[a, 2] * phat[2]
         conv = sfft.ifftn(acc, workers=workers)
         out[a] = conv[iz, iy, ix]
-    out += inv_alpha_diag.T * p
+    out += diagonal_term(inv_alpha_diag, p)
     return out
 
 

@@ -34,8 +34,11 @@ def efficiencies(kd, aeff, e_inc, p, inv_alpha_diag):
     k = kd
     c_ext = 4.0 * np.pi * k * np.sum(np.imag(np.conj(e_inc) * p))
     pt = p.T
-    # P_j . (alpha_j^{-1})^* P_j^*  with diagonal alpha^{-1}
-    quad = np.sum(pt * np.conj(inv_alpha_diag) * np.conj(pt), axis=1)
+    # P_j . (alpha_j^{-1})^* P_j^*  (diagonal (N, 3) or full (N, 3, 3) alpha^{-1})
+    if inv_alpha_diag.ndim == 2:
+        quad = np.sum(pt * np.conj(inv_alpha_diag) * np.conj(pt), axis=1)
+    else:
+        quad = np.einsum("ja,jab,jb->j", pt, np.conj(inv_alpha_diag), np.conj(pt))
     c_abs = 4.0 * np.pi * k * np.sum(np.imag(quad) - (2.0 / 3.0) * k ** 3 * np.sum(np.abs(pt) ** 2, axis=1))
     c_pha = 2.0 * np.pi * k * np.sum(np.real(np.conj(e_inc) * p))
     geo = np.pi * aeff ** 2

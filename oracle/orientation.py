@@ -109,3 +109,16 @@ def orientation_grid(beta_deg, nbeta: int, theta_deg, ntheta: int, phi_deg, nphi
                 oris.append((np.radians(b), float(np.arccos(np.clip(t, -1.0, 1.0))), np.radians(f)))
                 w.append(wth / (nbeta * nphi))
     return oris, np.array(w)
+
+
+def dielectric_axes(theta_df: float, phi_df: float, beta_df: float):
+    """Principal axes e_1, e_2, e_3 of a site's dielectric tensor in Target-Frame components (guide,
+    "Composite Targets with Anisotropic Constituents": rotate by theta_DF about y_TF, then phi_DF
+    about x_TF, then beta_DF about e_1)."""
+    ct, st = np.cos(theta_df), np.sin(theta_df)
+    cp, sp = np.cos(phi_df), np.sin(phi_df)
+    cb, sb = np.cos(beta_df), np.sin(beta_df)
+    e1 = np.array([ct, st * cp, st * sp])
+    e2 = np.array([-st * cb, ct * cb * cp - sb * sp, ct * cb * sp + sb * cp])
+    e3 = np.array([st * sb, -(ct * sb * cp + cb * sp), -(ct * sb * sp - cb * cp)])
+    return e1, e2, e3

@@ -83,6 +83,16 @@ struct dda_ctx {
   float2* d_nnv = nullptr;            // residual-loss vectors (three complex64 [nrhs][3][N])
   double* d_nnpart = nullptr;
   double* d_nnw = nullptr;
+  // Jacobi scaling s = alpha^{1/2} per (RHS, composition, axis) for preconditioned solves; `jacobi`
+  // is set only while a preconditioned solve's Krylov iterations run (true residuals and every
+  // other product use the unscaled A)
+  double2* d_sc128 = nullptr;
+  float2* d_sc64 = nullptr;
+  bool jacobi = false;
+  // full alpha^{-1} per (RHS, site) for targets with rotated dielectric frames ([nrhs][N][6])
+  double2* d_iat128 = nullptr;
+  float2* d_iat64 = nullptr;
+  bool iat_valid = false;
 
   // workspaces (grown on demand)
   float2* d_w64 = nullptr;
@@ -188,6 +198,8 @@ Err dalloc(T** p, size_t bytes) {
 void drop_alpha(dda_ctx* c) {
   c->have_alpha = false;
   c->ia.clear();
+  if (c->iat_valid) c->gen++;
+  c->iat_valid = false;
 }
 void drop_green(dda_ctx* c) { c->have_green = false; }
 void drop_incident(dda_ctx* c) {
@@ -378,6 +390,8 @@ template <> struct Sel<float2> {
   static dda::MvData<float2> data(dda_ctx* c) {
     dda::MvData<float2> d{c->d_map, c->comp_valid ? c->d_comp : nullptr, c->d_ghat64, c->d_ia64, c->d_tw64[0], c->d_tw64[1], c->d_tw64[2], c->d_w64};
     d.fault = c->d_fault;
+    d.sc = c->jacobi ? c->d_sc64 : nullptr;
+    d.iat = c->iat_valid ? c->d_iat64 : nullptr;
     return d;
   }
 };
@@ -387,9 +401,15 @@ template <> struct Sel<double2> {
   static dda::MvData<double2> data(dda_ctx* c) {
     dda::MvData<double2> d{c->d_map, c->comp_valid ? c->d_comp : nullptr, c->d_ghat128, c->d_ia128, c->d_tw128[0], c->d_tw128[1], c->d_tw128[2], c->d_w128};
     d.fault = c->d_fault;
+    d.sc = c->jacobi ? c->d_sc128 : nullptr;
+    d.iat = c->iat_valid ? c->d_iat128 : nullptr;
     return d;
   }
 };
+
+template <typename C> const C* scale_table(dda_ctx* c);
+template <> const float2* scale_table<float2>(dda_ctx* c) { return c->d_sc64; }
+template <> const double2* scale_table<double2>(dda_ctx* c) { return c->d_sc128; }
 
 // ap = A p over nrhs RHS starting at RHS index rhs0 (chunked by workspace capacity)
 // ks (optional): the solver state of RHS rhs0.. ; RHS whose solve has finished are skipped
@@ -413,7 +433,7 @@ Err matvec(dda_ctx* c, const C* p, C* ap, int nrhs, int rhs0, bool conj, const d
 // does not exist.
 bool df_available(dda_ctx* c) {
   return c->t128.fast && !c->t128.plane && c->ghatdf_valid && c->d_iadf && c->d_twdf[0] && c->d_twdf[1] &&
-         c->d_twdf[2];
+         c->d_twdf[2] && !c->iat_valid;
 }
 Err matvec_df(dda_ctx* c, const double2* p, double2* ap, int nrhs, int rhs0, bool conj) {
   if (!df_available(c))
@@ -599,9 +619,19 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
   cudaStream_t st = c->stream;
   const bool ccg = (o.solver == DDA_CCG);
   const bool b2 = (o.solver == DDA_BICGSTAB2);
+  const bool cocg = (o.solver == DDA_COCG);
   if (b2 && !kv.u2) return Err::make(DDA_ESTATE, "BiCGstab(2) needs the extra Krylov vector");
+  // preconditioned solves iterate on the scaled operator S A S (every product below)
+  struct JacobiScope {
+    dda_ctx* c;
+    bool prev;
+    JacobiScope(dda_ctx* cc, bool on) : c(cc), prev(cc->jacobi) { c->jacobi = on; }
+    ~JacobiScope() { c->jacobi = prev; }
+  } jscope(c, o.precond == DDA_PRECOND_JACOBI);
   if (have_x0) DDA_TRY(matvec<C>(c, kv.x, kv.r, nrhs, 0, false));
-  if (ccg) {
+  if (cocg) {
+    DDA_TRY(dda::cocg_init<C>(kv, ks, rb, nrhs, n3, tol, have_x0, st));
+  } else if (ccg) {
     DDA_TRY(dda::ccg_init<C>(kv, ks, rb, nrhs, n3, tol, have_x0, st));
     DDA_TRY(matvec<C>(c, kv.r, kv.s, nrhs, 0, true));
     DDA_TRY(dda::ccg_start<C>(kv, ks, rb, nrhs, n3, st));
@@ -642,6 +672,9 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
       DDA_TRY(dda::b2_r_update<C>(kv, ks, 1, nrhs, n3, st));
       DDA_TRY(matvec<C>(c, kv.s, kv.t, nrhs, 0, false, ks));
       DDA_TRY(dda::b2_mr<C>(kv, ks, rb, nrhs, n3, st));
+    } else if (cocg) {
+      DDA_TRY(matvec<C>(c, kv.p, kv.v, nrhs, 0, false, ks));
+      DDA_TRY(dda::cocg_update<C>(kv, ks, rb, nrhs, n3, st));
     } else if (ccg) {
       DDA_TRY(matvec<C>(c, kv.p, kv.v, nrhs, 0, false, ks));
       DDA_TRY(dda::ccg_alpha_update<C>(kv, ks, rb, nrhs, n3, st));
@@ -674,7 +707,7 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
     DDA_TRY(ensure_work<C>(c, nrhs, &cap));
     const char* fe = std::getenv("DDA_FUSE");
     if constexpr (std::is_same<C, float2>::value) {
-      fused = !(fe && std::atoi(fe) == 0) && !ccg && !b2 && c->t64.fast && cap >= nrhs;
+      fused = !(fe && std::atoi(fe) == 0) && !ccg && !b2 && !cocg && c->t64.fast && cap >= nrhs;
       if (fused) {
         // the folded reductions' table follows the vector kernels' table in the same buffer
         const int nx = dda::x_ctas_per_rhs_c64(Sel<float2>::geom(c), c->t64);
@@ -689,7 +722,8 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
   cudaGraphExec_t gexec = nullptr;
   unsigned long long graph_kernels = 0;
   const int gi = sizeof(C) == sizeof(float2) ? 0 : 1;
-  const long long gkey[4] = {o.solver, 4LL * every + (fused ? 2 : 0) + (pdl ? 1 : 0), nrhs, (long long)n3};
+  const long long gkey[4] = {o.solver, 8LL * every + (c->jacobi ? 4 : 0) + (fused ? 2 : 0) + (pdl ? 1 : 0), nrhs,
+                             (long long)n3};
   const bool reuse = o.use_graph && c->gexec[gi] && c->gexec_gen[gi] == c->gen &&
                      std::equal(gkey, gkey + 4, c->gexec_key[gi]);
   if (reuse) {
@@ -851,13 +885,14 @@ dda_status dda_setup_shape(dda_ctx* c, int shape, const double* shpar, int nshpa
 }
 
 static dda_status setup_sites(dda_ctx* c, const int32_t* ixyz, const int32_t* icomp, int64_t n, const double origin[3],
-                              const double a1[3], const double a2[3], bool per_axis) {
+                              const double a1[3], const double a2[3], bool per_axis,
+                              const double* df_angles = nullptr) {
   if (!c) return DDA_EINVAL;
   try {
     Err e = set_dev(c);
     if (!e.ok()) return fail(c, e);
     dda::HostTarget& t = c->tgt_next;  // built in the buffers of the target before last (warm pages)
-    e = dda::make_site_target(ixyz, icomp, n, origin, a1, a2, &t, per_axis);
+    e = dda::make_site_target(ixyz, icomp, n, origin, a1, a2, &t, per_axis, df_angles);
     if (!e.ok()) return fail(c, e);
     drop_target(c);
     std::swap(c->tgt, t);
@@ -878,6 +913,13 @@ dda_status dda_setup_target_aniso(dda_ctx* c, const int32_t* ixyz, const int32_t
                                   const double origin[3], const double a1[3], const double a2[3]) {
   if (!icomp3) return DDA_EINVAL;
   return setup_sites(c, ixyz, icomp3, n, origin, a1, a2, true);
+}
+
+dda_status dda_setup_target_anifrm(dda_ctx* c, const int32_t* ixyz, const int32_t* icomp3, int64_t n,
+                                   const double origin[3], const double a1[3], const double a2[3],
+                                   const double* df_angles) {
+  if (!icomp3 || !df_angles) return DDA_EINVAL;
+  return setup_sites(c, ixyz, icomp3, n, origin, a1, a2, true, df_angles);
 }
 
 dda_status dda_get_sites(dda_ctx* c, int32_t* ixyz_out, double origin_out[3]) {
@@ -1206,6 +1248,54 @@ dda_status dda_set_polarizability(dda_ctx* c, int presc, const double* m_reim, i
                     "polarizability upload");
       if (!e.ok()) return fail(c, e);
     }
+    if (!c->tgt.dfrot.empty()) {
+      // rotated dielectric frames: alpha^{-1} = sum_j d_j e_j e_j^T, d_j from the prescription for
+      // composition icomp(site, j) with the incidence projected on the principal axes e_j
+      const int64_t n = c->n;
+      const size_t nt = (size_t)c->nrhs * n * 6;
+      std::vector<double2> t128(nt);
+      std::vector<float2> t64(nt);
+      for (int b = 0; b < c->nrhs; ++b) {
+        const dda::RhsGeom& g = c->rg[b];
+        const double kh[3] = {g.k[0] / c->kd, g.k[1] / c->kd, g.k[2] / c->kd};
+        const cd ev[3] = {cd(g.e[0], g.e[1]), cd(g.e[2], g.e[3]), cd(g.e[4], g.e[5])};
+        for (int64_t j = 0; j < n; ++j) {
+          const double* R = &c->tgt.dfrot[9 * j];
+          double khd[3];
+          cd evd[3];
+          for (int a = 0; a < 3; ++a) {
+            khd[a] = kh[0] * R[a] + kh[1] * R[3 + a] + kh[2] * R[6 + a];
+            evd[a] = ev[0] * R[a] + ev[1] * R[3 + a] + ev[2] * R[6 + a];
+          }
+          cd d[3];
+          for (int a = 0; a < 3; ++a) {
+            const int cc = c->tgt.comp[3 * j + a];
+            cd o3[3];
+            inv_alpha(presc, cd(m_reim[2 * cc], m_reim[2 * cc + 1]), c->kd, khd, evd, o3);
+            d[a] = o3[a];
+          }
+          static const int rows[6] = {0, 0, 0, 1, 1, 2}, cols[6] = {0, 1, 2, 1, 2, 2};
+          for (int q = 0; q < 6; ++q) {
+            cd v(0, 0);
+            for (int a = 0; a < 3; ++a) v += d[a] * (R[3 * rows[q] + a] * R[3 * cols[q] + a]);
+            const size_t o = ((size_t)b * n + j) * 6 + q;
+            t128[o] = make_double2(v.real(), v.imag());
+            t64[o] = make_float2((float)v.real(), (float)v.imag());
+          }
+        }
+      }
+      if (!c->host_only) {
+        e = grow(c, &c->d_iat128, sizeof(double2) * nt);
+        if (e.ok()) e = grow(c, &c->d_iat64, sizeof(float2) * nt);
+        if (e.ok()) e = cuda_ok(cudaMemcpy(c->d_iat128, t128.data(), sizeof(double2) * nt, cudaMemcpyHostToDevice),
+                                "polarizability tensor upload");
+        if (e.ok()) e = cuda_ok(cudaMemcpy(c->d_iat64, t64.data(), sizeof(float2) * nt, cudaMemcpyHostToDevice),
+                                "polarizability tensor upload");
+        if (!e.ok()) return fail(c, e);
+      }
+      c->iat_valid = true;
+      c->gen++;
+    }
     c->ia = std::move(ia);
     c->eps.resize(ncomp);
     for (int m = 0; m < ncomp; ++m) {
@@ -1269,6 +1359,26 @@ Err kvec_alloc(dda_ctx* c, dda::KrylovVecs<C>* kv, int nvec_extra) {
   return Err::Ok();
 }
 
+// Jacobi scaling tables s = alpha^{1/2} (principal square root of 1 / alpha^{-1}) per RHS,
+// composition and axis, from the host copy of alpha^{-1}; complex128 and complex64 copies.
+Err ensure_scale(dda_ctx* c) {
+  const size_t nv = (size_t)c->nrhs * c->ncomp * 3;
+  if (c->ia.size() != nv) return Err::make(DDA_ESTATE, "polarizabilities missing");
+  std::vector<double2> s128(nv);
+  std::vector<float2> s64(nv);
+  for (size_t i = 0; i < nv; ++i) {
+    const cd s = std::sqrt(1.0 / c->ia[i]);
+    s128[i] = make_double2(s.real(), s.imag());
+    s64[i] = make_float2((float)s.real(), (float)s.imag());
+  }
+  DDA_TRY(grow(c, &c->d_sc128, sizeof(double2) * nv));
+  DDA_TRY(grow(c, &c->d_sc64, sizeof(float2) * nv));
+  DDA_CU(cudaMemcpyAsync(c->d_sc128, s128.data(), sizeof(double2) * nv, cudaMemcpyHostToDevice, c->stream));
+  DDA_CU(cudaMemcpyAsync(c->d_sc64, s64.data(), sizeof(float2) * nv, cudaMemcpyHostToDevice, c->stream));
+  DDA_CU(cudaStreamSynchronize(c->stream));  // the host vectors go out of scope
+  return Err::Ok();
+}
+
 // true residual (FP64 product): |E - A P|^2 and |E|^2 per RHS
 // (use_df: the product in double-float arithmetic, matvec_df)
 Err true_residual(dda_ctx* c, const double2* p, double2* scratch_ax, double2* scratch_r, std::vector<double>* rel,
@@ -1299,8 +1409,10 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
   if (!c->have_alpha || !c->have_green)
     return fail(c, Err::make(DDA_ESTATE, "set target, incidence, Green tensor and alpha first"));
   dda_solve_opts o = *opt;
-  if (o.solver != DDA_BICGSTAB && o.solver != DDA_CCG && o.solver != DDA_BICGSTAB2)
+  if (o.solver != DDA_BICGSTAB && o.solver != DDA_CCG && o.solver != DDA_BICGSTAB2 && o.solver != DDA_COCG)
     return fail(c, Err::make(DDA_EINVAL, "unknown solver"));
+  if (o.precond != DDA_PRECOND_NONE && o.precond != DDA_PRECOND_JACOBI)
+    return fail(c, Err::make(DDA_EINVAL, "unknown preconditioner"));
   if (o.precision < DDA_PREC_C64 || o.precision > DDA_PREC_MIXED)
     return fail(c, Err::make(DDA_EINVAL, "unknown precision"));
   if (!(o.tol > 0) || o.maxit < 1) return fail(c, Err::make(DDA_EINVAL, "tol must be > 0 and maxit >= 1"));
@@ -1331,6 +1443,19 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
     if (e.ok()) e = ensure_tuned<double2>(c, nrhs);
     if (e.ok() && o.precision != DDA_PREC_C128) e = ensure_tuned<float2>(c, nrhs);
     if (!e.ok()) return fail(c, e);
+    const bool jac = o.precond == DDA_PRECOND_JACOBI;
+    if (jac && c->iat_valid)
+      return fail(c, Err::make(DDA_EUNSUPPORTED, "Jacobi scaling needs dielectric tensors diagonal in the TF"));
+    if (jac) e = ensure_scale(c);
+    if (!e.ok()) return fail(c, e);
+    // Jacobi: the Krylov solver works on S A S y = S b with x = S y (S = diag(alpha^{1/2}))
+    const uint8_t* comp = c->comp_valid ? c->d_comp : nullptr;
+    auto scale64 = [&](float2* v, bool inv) {
+      return jac ? dda::scale_sites<float2>(v, c->d_sc64, comp, c->ncomp, nrhs, c->n, inv, c->stream) : Err::Ok();
+    };
+    auto scale128 = [&](double2* v, bool inv) {
+      return jac ? dda::scale_sites<double2>(v, c->d_sc128, comp, c->ncomp, nrhs, c->n, inv, c->stream) : Err::Ok();
+    };
     std::vector<int> iters(nrhs, 0), outer_n(nrhs, 0);
     std::vector<int> mvb(nrhs, 0);  // products with A applied to each RHS
     auto add_mv = [&](const std::vector<int>& v) {
@@ -1353,11 +1478,14 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
       if (e.ok()) {
         e = cuda_ok(cudaMemcpyAsync(kv.b, c->d_e128, sizeof(double2) * el, cudaMemcpyDeviceToDevice, c->stream),
                     "right-hand side copy");
+        if (e.ok()) e = scale128(kv.b, false);
         if (e.ok() && o.warm_start)
           e = cuda_ok(cudaMemcpyAsync(kv.x, P, sizeof(double2) * el, cudaMemcpyDeviceToDevice, c->stream),
                       "initial guess copy");
+        if (e.ok() && o.warm_start) e = scale128(kv.x, true);
         SolveStats s;
         if (e.ok()) e = krylov<double2>(c, o, kv, o.tol, o.maxit, o.warm_start != 0, &s, t0, &timed_out);
+        if (e.ok()) e = scale128(kv.x, false);
         if (e.ok()) e = cuda_ok(cudaMemcpyAsync(P, kv.x, sizeof(double2) * el, cudaMemcpyDeviceToDevice, c->stream),
                                 "solution copy");
         if (e.ok()) {
@@ -1369,9 +1497,12 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
       dda::KrylovVecs<float2> kv;
       e = kvec_alloc<float2>(c, &kv, o.solver == DDA_BICGSTAB2 ? 1 : 0);
       if (e.ok()) e = dda::convert_from_c128<float2>(c->d_e128, kv.b, el, c->stream);
+      if (e.ok()) e = scale64(kv.b, false);
       if (e.ok() && o.warm_start) e = dda::convert_from_c128<float2>(P, kv.x, el, c->stream);
+      if (e.ok() && o.warm_start) e = scale64(kv.x, true);
       SolveStats s;
       if (e.ok()) e = krylov<float2>(c, o, kv, o.tol, o.maxit, o.warm_start != 0, &s, t0, &timed_out);
+      if (e.ok()) e = scale64(kv.x, false);
       if (e.ok()) {
         e = cuda_ok(cudaMemsetAsync(P, 0, sizeof(double2) * el, c->stream), "solution clear");
         if (e.ok()) e = dda::add_to_c128<float2>(P, kv.x, nullptr, nrhs, n3, c->stream);
@@ -1410,6 +1541,8 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
             e = cuda_ok(cudaMemsetAsync(kv.b + (int64_t)b * n3, 0, sizeof(float2) * n3, c->stream),
                         "inner right-hand side clear");
         if (!e.ok()) break;
+        e = scale64(kv.b, false);
+        if (!e.ok()) break;
         // ask the inner solve for the reduction that reaches tol, but at least `inner`
         double worst = 0;
         for (int b = 0; b < nrhs; ++b) worst = std::max(worst, rel[b] > o.tol ? o.tol / rel[b] : 0.0);
@@ -1425,6 +1558,8 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
         for (int b = 0; b < nrhs; ++b) used = std::max(used, s.iters[b]);
         budget -= std::max(used, 1);
         add_mv(s.mv);
+        e = scale64(kv.x, false);
+        if (!e.ok()) break;
         e = dda::add_to_c128<float2>(P, kv.x, nullptr, nrhs, n3, c->stream);
         ++outer;
       }
@@ -1516,7 +1651,9 @@ dda_status dda_cross_sections(dda_ctx* c, const void* p_dev, double* q_out, cons
       e = ensure_small(c, sizeof(double) * 3 * nrhs);
       if (!e.ok()) return fail(c, e);
       e = ensure_einc(c);
-      if (e.ok())
+      if (e.ok() && c->iat_valid)
+        e = dda::qsums_tensor(c->d_e128, c->d_iat128, k, P, nrhs, c->n, c->d_small, rb, c->stream);
+      else if (e.ok())
         e = dda::qsums(c->comp_valid ? c->d_comp : nullptr, c->d_e128, c->d_ia128, c->ncomp, k, P, nrhs, c->n,
                        c->d_small, rb, c->stream);
       if (!e.ok()) return fail(c, e);
@@ -1838,6 +1975,200 @@ dda_status dda_angular_averages(dda_ctx* c, const void* p_dev, double eta, doubl
     dfree(d_F);
     if (!e.ok()) return fail(c, e);
     if (ndir_out) *ndir_out = ndir;
+    return DDA_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, Err::make(DDA_ENOMEM, "host allocation failed"));
+  }
+}
+
+dda_status dda_force_torque(dda_ctx* c, const void* p_dev, double eta, double* out, int32_t* ndir_out) {
+  if (!c || !p_dev || !out || !(eta > 0.0)) return DDA_EINVAL;
+  if (!c->have_inc) return fail(c, Err::make(DDA_ESTATE, "set the target and the incident beams first"));
+  try {
+    Err e = need_device(c);
+    if (e.ok()) e = set_dev(c);
+    if (e.ok()) e = ensure_einc(c);
+    if (!e.ok()) return fail(c, e);
+    const double pi = 3.14159265358979323846;
+    const int nrhs = c->nrhs;
+    const double k = c->kd;
+    const double aeff = std::cbrt(3.0 * (double)c->n / (4.0 * pi));
+    const std::vector<ScaDir> dirs = scattering_directions(k * aeff, eta);
+    const int ndir = (int)dirs.size();
+    const int box[3] = {c->tgt.box[0], c->tgt.box[1], c->tgt.box[2]};
+    const int nt = box[0] + box[1] + box[2];
+    // torque about the centroid of the sites: lever arms r_j - r_cm = ijk_j + (origin - r_cm)
+    double cm[3] = {0, 0, 0};
+    for (int64_t j = 0; j < c->n; ++j)
+      for (int q = 0; q < 3; ++q) cm[q] += (double)c->tgt.ijk[3 * j + q];
+    double shift[3];
+    for (int q = 0; q < 3; ++q) shift[q] = -cm[q] / (double)c->n;  // origin - r_cm in box-index units
+    const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((c->n + 2047) / 2048, 64));
+    const int nchunk = (ndir + 1) / 2;
+    const int per = (int)std::max<int64_t>(1, std::min<int64_t>(nrhs, (256ll << 20) / ((int64_t)ndir * nt * 8)));
+    std::vector<double> nl((size_t)ndir * 3);
+    for (int d = 0; d < ndir; ++d) {
+      const double t = dirs[d].theta, f = dirs[d].phi;
+      nl[3 * d] = std::cos(t);
+      nl[3 * d + 1] = std::sin(t) * std::cos(f);
+      nl[3 * d + 2] = std::sin(t) * std::sin(f);
+    }
+    float2* d_tab = nullptr;
+    double* d_part = nullptr;
+    double* d_nh = nullptr;
+    double2* d_M = nullptr;
+    double* d_ext = nullptr;
+    const size_t part_doubles = std::max<size_t>((size_t)per * nchunk * nblk * 48, (size_t)nrhs * nblk * 8);
+    e = dalloc((char**)&d_tab, sizeof(float2) * (size_t)per * ndir * nt);
+    if (e.ok()) e = dalloc((char**)&d_part, sizeof(double) * part_doubles);
+    if (e.ok()) e = dalloc((char**)&d_nh, sizeof(double) * (size_t)per * ndir * 3);
+    if (e.ok()) e = dalloc((char**)&d_M, sizeof(double2) * (size_t)per * ndir * 12);
+    if (e.ok()) e = dalloc((char**)&d_ext, sizeof(double) * 7 * (size_t)nrhs);
+    // incident part, all RHS at once
+    std::vector<double> ext(7 * (size_t)nrhs);
+    if (e.ok()) e = dda::torque_ext_sums(c->d_ijk, c->d_e128, (const double2*)p_dev, nrhs, c->n, shift, d_part, nblk,
+                                         d_ext, c->stream);
+    if (e.ok() && (cudaMemcpyAsync(ext.data(), d_ext, sizeof(double) * 7 * nrhs, cudaMemcpyDeviceToHost, c->stream) !=
+                       cudaSuccess ||
+                   cudaStreamSynchronize(c->stream) != cudaSuccess))
+      e = Err::make(DDA_ECUDA, "incident force sums failed");
+    std::vector<double> nh((size_t)per * ndir * 3);
+    std::vector<double2> M((size_t)per * ndir * 12);
+    const double k3 = k * k * k / (8.0 * pi), k4 = k * k * k * k / (8.0 * pi);
+    for (int b0 = 0; b0 < nrhs && e.ok(); b0 += per) {
+      const int nb = std::min(per, nrhs - b0);
+      for (int bb = 0; bb < nb; ++bb) {
+        const double* ax = &c->axes[9 * ((b0 + bb) / c->iorth)];
+        for (int d = 0; d < ndir; ++d)
+          for (int q = 0; q < 3; ++q)
+            nh[((size_t)bb * ndir + d) * 3 + q] = nl[3 * d] * ax[q] + nl[3 * d + 1] * ax[3 + q] + nl[3 * d + 2] * ax[6 + q];
+      }
+      if (cudaMemcpyAsync(d_nh, nh.data(), sizeof(double) * (size_t)nb * ndir * 3, cudaMemcpyHostToDevice, c->stream) !=
+          cudaSuccess) {
+        e = Err::make(DDA_ECUDA, "direction upload failed");
+        break;
+      }
+      const double2* P = (const double2*)p_dev + (size_t)b0 * 3 * c->n;
+      e = dda::farfield_moments(c->d_ijk, c->d_origin, d_nh, k, P, nb, ndir, c->n, box, shift, d_tab, d_part, nblk,
+                                d_M, c->stream);
+      if (!e.ok()) break;
+      if (cudaMemcpyAsync(M.data(), d_M, sizeof(double2) * (size_t)nb * ndir * 12, cudaMemcpyDeviceToHost, c->stream) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        e = Err::make(DDA_ECUDA, "far-field moments failed");
+        break;
+      }
+      for (int bb = 0; bb < nb; ++bb) {
+        const int b = b0 + bb;
+        double kh[3];
+        for (int q = 0; q < 3; ++q) kh[q] = c->rg[b].k[q] / k;
+        const double* s7 = &ext[7 * (size_t)b];
+        // incident part: F = (k/2) sum Im(P.E^*) khat; Gamma = 1/2 sum Re(P x E^*) + (k/2) (sum r Im(P.E^*)) x khat
+        double F[3], G[3];
+        for (int q = 0; q < 3; ++q) {
+          F[q] = 0.5 * k * s7[6] * kh[q];
+          const int q1 = (q + 1) % 3, q2 = (q + 2) % 3;
+          G[q] = 0.5 * s7[q] + 0.5 * k * (s7[3 + q1] * kh[q2] - s7[3 + q2] * kh[q1]);
+        }
+        // the array's own field, as far-field integrals over the guide's directions
+        for (int d = 0; d < ndir; ++d) {
+          const double* n = &nh[((size_t)bb * ndir + d) * 3];
+          const double2* Mv = &M[((size_t)bb * ndir + d) * 12];
+          const double w = dirs[d].w;
+          cd g[3], f[3], ng(0, 0);
+          for (int q = 0; q < 3; ++q) {
+            g[q] = cd(Mv[q].x, Mv[q].y);
+            ng += n[q] * g[q];
+          }
+          double ff = 0;
+          for (int q = 0; q < 3; ++q) {
+            f[q] = g[q] - n[q] * ng;
+            ff += std::norm(f[q]);
+          }
+          double rh[3];  // Re h, h_c = sum_a T[c][a] conj(f_a)
+          for (int cc = 0; cc < 3; ++cc) {
+            cd h(0, 0);
+            for (int a = 0; a < 3; ++a) h += cd(Mv[3 + 3 * cc + a].x, Mv[3 + 3 * cc + a].y) * std::conj(f[a]);
+            rh[cc] = h.real();
+          }
+          for (int q = 0; q < 3; ++q) {
+            const int q1 = (q + 1) % 3, q2 = (q + 2) % 3;
+            F[q] -= k4 * w * ff * n[q];
+            G[q] += k3 * w * (g[q1] * std::conj(f[q2]) - g[q2] * std::conj(f[q1])).imag();
+            G[q] -= k4 * w * (rh[q1] * n[q2] - rh[q2] * n[q1]);
+          }
+        }
+        const double sc = 8.0 / (aeff * aeff);
+        for (int q = 0; q < 3; ++q) {
+          out[6 * (size_t)b + q] = sc * F[q];
+          out[6 * (size_t)b + 3 + q] = sc * k * G[q];
+        }
+      }
+    }
+    dfree(d_tab);
+    dfree(d_part);
+    dfree(d_nh);
+    dfree(d_M);
+    dfree(d_ext);
+    if (!e.ok()) return fail(c, e);
+    if (ndir_out) *ndir_out = ndir;
+    return DDA_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, Err::make(DDA_ENOMEM, "host allocation failed"));
+  }
+}
+
+dda_status dda_near_field(dda_ctx* c, const void* p_dev, const double* pts, int64_t npts, double* e_out,
+                          double* b_out) {
+  if (!c || !p_dev || !pts || !e_out || npts < 1) return DDA_EINVAL;
+  if (!c->have_inc) return fail(c, Err::make(DDA_ESTATE, "set the target and the incident beams first"));
+  try {
+    Err e = need_device(c);
+    if (e.ok()) e = set_dev(c);
+    if (!e.ok()) return fail(c, e);
+    for (int64_t i = 0; i < 3 * npts; ++i)
+      if (!std::isfinite(pts[i])) return fail(c, Err::make(DDA_EINVAL, "field points must be finite"));
+    const int nrhs = c->nrhs;
+    double* d_pts = nullptr;
+    double* d_out = nullptr;
+    e = dalloc((char**)&d_pts, sizeof(double) * 3 * (size_t)npts);
+    if (e.ok()) e = dalloc((char**)&d_out, sizeof(double) * 12 * (size_t)npts * nrhs);
+    std::vector<double> h((size_t)12 * npts * nrhs);
+    if (e.ok()) e = cuda_ok(cudaMemcpyAsync(d_pts, pts, sizeof(double) * 3 * npts, cudaMemcpyHostToDevice, c->stream),
+                            "point upload");
+    if (e.ok()) e = dda::near_field(c->d_ijk, c->d_origin, (const double2*)p_dev, nrhs, c->n, d_pts, npts, c->kd, d_out,
+                                    c->stream);
+    if (e.ok()) e = cuda_ok(cudaMemcpyAsync(h.data(), d_out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
+                                            c->stream), "field readback");
+    if (e.ok()) e = cuda_ok(cudaStreamSynchronize(c->stream), "field readback");
+    dfree(d_pts);
+    dfree(d_out);
+    if (!e.ok()) return fail(c, e);
+    // add the incident plane wave E = e exp(i k.x), B = khat x E (FP64 on the host)
+    for (int b = 0; b < nrhs; ++b) {
+      const dda::RhsGeom& g = c->rg[b];
+      const double kh[3] = {g.k[0] / c->kd, g.k[1] / c->kd, g.k[2] / c->kd};
+      for (int64_t i = 0; i < npts; ++i) {
+        const double* x = pts + 3 * i;
+        const cd ph = std::exp(cd(0.0, g.k[0] * x[0] + g.k[1] * x[1] + g.k[2] * x[2]));
+        cd E[3], B[3];
+        const double* f = &h[((size_t)b * npts + i) * 12];
+        for (int a = 0; a < 3; ++a) E[a] = cd(g.e[2 * a], g.e[2 * a + 1]) * ph;
+        for (int a = 0; a < 3; ++a) B[a] = kh[(a + 1) % 3] * E[(a + 2) % 3] - kh[(a + 2) % 3] * E[(a + 1) % 3];
+        double* eo = e_out + ((size_t)b * npts + i) * 6;
+        for (int a = 0; a < 3; ++a) {
+          eo[2 * a] = f[2 * a] + E[a].real();
+          eo[2 * a + 1] = f[2 * a + 1] + E[a].imag();
+        }
+        if (b_out) {
+          double* bo = b_out + ((size_t)b * npts + i) * 6;
+          for (int a = 0; a < 3; ++a) {
+            bo[2 * a] = f[6 + 2 * a] + B[a].real();
+            bo[2 * a + 1] = f[6 + 2 * a + 1] + B[a].imag();
+          }
+        }
+      }
+    }
     return DDA_OK;
   } catch (const std::bad_alloc&) {
     return fail(c, Err::make(DDA_ENOMEM, "host allocation failed"));

@@ -51,10 +51,19 @@ struct HostTarget {
   double a1[3] = {1, 0, 0};
   double a2[3] = {0, 1, 0};
   int ncomp = 1;
+  // per-site Dielectric Frame (guide, "Composite Targets with Anisotropic Constituents"): N x 9,
+  // row-major R[a][j] = TF component a of the principal axis e_j; empty when every site's
+  // dielectric tensor is diagonal in the TF
+  std::vector<double> dfrot;
 };
 Err make_shape_target(int shape, const double* shpar, int nshpar, HostTarget* out);
+// df_angles (optional, with per_axis): N x 3 (theta_DF, phi_DF, beta_DF) in radians
 Err make_site_target(const int32_t* ixyz, const int32_t* icomp, int64_t n, const double origin[3],
-                     const double a1[3], const double a2[3], HostTarget* out, bool per_axis = false);
+                     const double a1[3], const double a2[3], HostTarget* out, bool per_axis = false,
+                     const double* df_angles = nullptr);
+// The principal axes e_1, e_2, e_3 of the dielectric tensor in Target-Frame components for the
+// guide's rotation angles (theta_DF, phi_DF, beta_DF): R[a][j] = (e_j)_a.
+void df_axes(double theta, double phi, double beta, double R[9]);
 
 // ------------------------------------------------------------------ FFT plans (host)
 Err make_plan(int L, FftPlan* out);
@@ -88,6 +97,14 @@ struct MvData {
   // compile-time kernels skip the RHS whose solve has finished (their products are unused)
   const KState* ks = nullptr;
   unsigned int* fault = nullptr;  // set by a kernel whose bounded wait on a bulk copy gave up
+  // Jacobi scaling of the product (symmetric diagonal preconditioning of the solve): when set, the
+  // product applies S A S instead of A, S = diag(s) with s = alpha^{1/2} per (RHS, composition,
+  // axis), layout [nrhs][ncomp][3] counted from the launch's first RHS; then the diagonal term
+  // s alpha^{-1} s is the identity.
+  const C* sc = nullptr;
+  // full symmetric alpha^{-1} per (RHS, site) for targets with rotated dielectric frames:
+  // [nrhs][N][6] (xx, xy, xz, yy, yz, zz) from the launch's rhs0 like ia; null = diagonal table
+  const C* iat = nullptr;
 };
 
 // Launch tuning chosen per grid (autotuner fills it).
@@ -240,6 +257,14 @@ template <typename C> Err b2_beta(const KrylovVecs<C>& kv, KState* ks, RedBuf rb
                                   cudaStream_t st);
 template <typename C> Err b2_mr(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3,
                                 cudaStream_t st);
+// COCG (complex-symmetric CG): init; then per iteration [v = A p], update (alpha, x/r, beta, p).
+template <typename C> Err cocg_init(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, double tol,
+                                    bool have_ax, cudaStream_t st);
+template <typename C> Err cocg_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3,
+                                      cudaStream_t st);
+// v[b][c][j] *= s[b][comp(j,c)][c] (inv: divides), the Jacobi scaling of site vectors
+template <typename C> Err scale_sites(C* v, const C* s, const uint8_t* comp, int ncomp, int nrhs, int64_t n, bool inv,
+                                      cudaStream_t st);
 // CCG (CG on the normal equations)
 template <typename C> Err ccg_init(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3,
                                    double tol, bool have_ax, cudaStream_t st);
@@ -280,6 +305,8 @@ template <typename C>
 Err incident_field(const int32_t* ijk, const double* origin3, const RhsGeom* rg, int nrhs, int64_t n, C* e,
                    cudaStream_t st);
 // per RHS: [0] sum Im(E*.P), [1] sum Re(E*.P), [2] sum (-Im ia - 2/3 k^3)|P|^2
+Err qsums_tensor(const double2* einc, const double2* iat, double kd, const double2* p, int nrhs, int64_t n,
+                 double* out3, RedBuf rb, cudaStream_t st);
 Err qsums(const uint8_t* comp, const double2* einc /*[nrhs][3][N]*/, const double2* ia, int ncomp, double kd,
           const double2* p, int nrhs, int64_t n, double* out3, RedBuf rb, cudaStream_t st);
 // F[rhs][dir][3] = sum_j P_j exp(-i kd n_dir . r_j); ndirs directions per RHS (nhat given per RHS, TF)
@@ -292,6 +319,19 @@ Err farfield(const int32_t* ijk, const double* origin3, const double* nhat /*[nr
 Err farfield_many(const int32_t* ijk, const double* origin3, const double* nhat, double kd, const double2* p,
                   int nrhs, int ndir, int64_t n, const int box[3], float2* tab, double* part, int nblk, double2* out,
                   cudaStream_t st);
+// Far-field moments for the radiative torque: out[rhs][d][12] = g (3 complex) and
+// T[c][a] = sum_j (r_j - r_cm)_c P_ja exp(-i k n.r_j) (9 complex); shift = origin - r_cm.
+Err farfield_moments(const int32_t* ijk, const double* origin3, const double* nhat, double kd, const double2* p,
+                     int nrhs, int ndir, int64_t n, const int box[3], const double shift[3], float2* tab, double* part,
+                     int nblk, double2* out, cudaStream_t st);
+// Dipole fields at npts points (host-side incident field not included): out[rhs][pt][12] =
+// E then B, (re, im) x 3, FP64; dipoles nearer than one lattice spacing scaled by R^4 (5 - 4R).
+Err near_field(const int32_t* ijk, const double* origin3, const double2* p, int nrhs, int64_t n, const double* pts,
+               int64_t npts, double kd, double* out, cudaStream_t st);
+// Incident-field force/torque sums per RHS: out7[b] = {sum Re(P x E^*) (3), sum (r - r_cm) Im(P.E^*) (3),
+// sum Im(P.E^*)}; part: nrhs * nblk * 8 doubles.
+Err torque_ext_sums(const int32_t* ijk, const double2* einc, const double2* p, int nrhs, int64_t n,
+                    const double shift[3], double* part, int nblk, double* out7, cudaStream_t st);
 
 // ------------------------------------------------------------------ learned warm start glue (unet.cu)
 Err unet_features(const int32_t* ijk, int64_t n, const uint8_t* comp, const float2* eps, const double2* e, int nrhs,

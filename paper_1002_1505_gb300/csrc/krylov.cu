@@ -4,7 +4,10 @@
 //  - CCG: conjugate gradients on the normal equations A^H A P = A^H E
 //    (Petravic & Kuo-Petravic 1979; the guide's PETRKP option);
 //  - BiCGstab(2) (Sleijpen & Fokkema 1993), the method family of the guide's
-//    PBCGS2 option: two BiCG steps, then a degree-2 minimal-residual step.
+//    PBCGS2 option: two BiCG steps, then a degree-2 minimal-residual step;
+//  - COCG (van der Vorst & Melissen 1990), CG with the unconjugated bilinear
+//    form for the complex-symmetric A, one product per iteration (the
+//    symmetric-Lanczos family of the guide's QMRCCG option).
 // Every right-hand side is an independent system solved in lock step: each
 // kernel covers all RHS, with per-RHS scalars kept on the device (KState), so
 // an iteration needs no host round trip and can be captured in a CUDA graph.
@@ -488,6 +491,151 @@ __global__ void k_ccg_p(KrylovVecs<C> kv, const KState* ks, int64_t n3) {
   }
 }
 
+// ------------------------------------------------------------------ COCG kernels
+// Conjugate orthogonal conjugate gradients (van der Vorst & Melissen 1990): CG with the
+// unconjugated bilinear form x^T y, valid because A is complex symmetric; one product per
+// iteration.  Vectors: x, r, p, q = A p (held in v).  KState: rho = r^T r, alpha, beta.
+// re + i im += a^T b (no conjugation)
+template <typename C>
+__device__ __forceinline__ void acc_bdot(Acc<C>& re, Acc<C>& im, C a, C b) {
+  re.fma(a.x, b.x);
+  re.fma(-a.y, b.y);
+  im.fma(a.x, b.y);
+  im.fma(a.y, b.x);
+}
+
+template <typename C>
+__global__ void k_cocg_init(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3, bool have_ax, double tol) {
+  const int b = blockIdx.y;
+  const int64_t o = (int64_t)b * n3;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // |b|^2, |r|^2, r^T r
+  VEC_LOOP(n3) {
+    const double2 bv = to_d(kv.b[o + i]);
+    double2 rv = bv;
+    if (have_ax) {
+      const double2 ax = to_d(kv.r[o + i]);
+      rv = make_double2(bv.x - ax.x, bv.y - ax.y);
+    }
+    const C rc = from_d<C>(rv);
+    kv.r[o + i] = rc;
+    kv.p[o + i] = rc;
+    if (!have_ax) kv.x[o + i] = czero<C>();
+    const double2 rd = to_d(rc);
+    acc[0] = nrm_acc(acc[0], bv);
+    acc[1] = nrm_acc(acc[1], rd);
+    acc[2] += rd.x * rd.x - rd.y * rd.y;
+    acc[3] += 2.0 * rd.x * rd.y;
+  }
+  double t[4];
+  if (last_block_totals<4>(acc, rb, b, t) && threadIdx.x == 0) {
+    KState& k = ks[b];
+    k.bb = t[0];
+    k.rr = t[1];
+    k.rho = make_double2(t[2], t[3]);
+    k.alpha = make_double2(0.0, 0.0);
+    k.beta = make_double2(0.0, 0.0);
+    k.tol2 = tol * tol * t[0];
+    k.it = 0;
+    k.mv = 0;
+    k.done = (t[0] == 0.0 || t[1] <= k.tol2) ? 1 : 0;
+  }
+}
+
+// partial p^T q (q = A p in v) -> alpha = rho / p^T q
+template <typename C>
+__global__ void k_cocg_mu(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
+  pdl_begin();
+  const int b = blockIdx.y;
+  double acc[2] = {0.0, 0.0};
+  if (!ks[b].done) {
+    const int64_t o = (int64_t)b * n3;
+    Acc<C> re, im;
+    VEC_LOOP(n3) acc_bdot(re, im, kv.p[o + i], kv.v[o + i]);
+    acc[0] = re.get();
+    acc[1] = im.get();
+  }
+  double t[2];
+  if (last_block_totals<2>(acc, rb, b, t) && threadIdx.x == 0) {
+    KState& k = ks[b];
+    if (k.done) return;
+    k.mv += 1;  // q = A p
+    if (t[0] == 0.0 && t[1] == 0.0) { k.done = 2; return; }
+    k.alpha = cdiv(k.rho, make_double2(t[0], t[1]));
+  }
+}
+
+// x += alpha p ; r -= alpha q ; partial |r|^2, r^T r -> convergence, beta
+template <typename C>
+__global__ void k_cocg_xr(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
+  pdl_begin();
+  const int b = blockIdx.y;
+  const KState k = ks[b];
+  double acc[3] = {0.0, 0.0, 0.0};
+  if (!k.done) {
+    const C al = from_d<C>(k.alpha);
+    const int64_t o = (int64_t)b * n3;
+    Acc<C> rr, re, im;
+    VEC_LOOP(n3) {
+      const C pv = kv.p[o + i], qv = kv.v[o + i];
+      C xv = kv.x[o + i], rv = kv.r[o + i];
+      xv = cadd(xv, cmul(al, pv));
+      rv = csub(rv, cmul(al, qv));
+      kv.x[o + i] = xv;
+      kv.r[o + i] = rv;
+      acc_nrm(rr, rv);
+      acc_bdot(re, im, rv, rv);
+    }
+    acc[0] = rr.get();
+    acc[1] = re.get();
+    acc[2] = im.get();
+  }
+  double t[3];
+  if (last_block_totals<3>(acc, rb, b, t) && threadIdx.x == 0) {
+    KState& kw = ks[b];
+    if (kw.done) return;
+    kw.it += 1;
+    kw.rr = t[0];
+    if (t[0] <= kw.tol2) { kw.done = 1; return; }
+    const double2 rho_new = make_double2(t[1], t[2]);
+    if (rho_new.x == 0.0 && rho_new.y == 0.0) { kw.done = 2; return; }
+    kw.beta = cdiv(rho_new, kw.rho);
+    kw.rho = rho_new;
+  }
+}
+
+// p = r + beta p
+template <typename C>
+__global__ void k_cocg_p(KrylovVecs<C> kv, const KState* ks, int64_t n3) {
+  pdl_begin();
+  const int b = blockIdx.y;
+  const KState k = ks[b];
+  if (k.done) return;
+  const C be = from_d<C>(k.beta);
+  const int64_t o = (int64_t)b * n3;
+  VEC_LOOP(n3) kv.p[o + i] = cadd(kv.r[o + i], cmul(be, kv.p[o + i]));
+}
+
+// ------------------------------------------------------------------ Jacobi scaling of site vectors
+// v[b][c][j] *= s[b][comp(j, c)][c] (or /= with inv), the diagonal S of the scaled system S A S.
+template <typename C>
+__global__ void k_scale_sites(C* v, const C* s, const uint8_t* comp, int ncomp, int64_t n, bool inv) {
+  const int b = blockIdx.y;
+  const int64_t n3 = 3 * n;
+  const int64_t o = (int64_t)b * n3;
+  VEC_LOOP(n3) {
+    const int c = (int)(i / n);
+    const int64_t j = i - (int64_t)c * n;
+    const int cc = comp ? comp[3 * j + c] : 0;
+    C f = s[((int64_t)b * ncomp + cc) * 3 + c];
+    if (inv) {
+      const auto d = f.x * f.x + f.y * f.y;
+      f.x = f.x / d;
+      f.y = -f.y / d;
+    }
+    v[o + i] = cmul(v[o + i], f);
+  }
+}
+
 // ------------------------------------------------------------------ BiCGstab(2) kernels
 // r0 = b - A x (or b), shadow = r0, u0 = 0; rho0 = <shadow, r0> (the first BiCG step's rho with beta = 0)
 template <typename C>
@@ -814,6 +962,34 @@ Err ccg_beta_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, in
 }
 
 template <typename C>
+Err cocg_init(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, double tol, bool have_ax,
+              cudaStream_t st) {
+  k_cocg_init<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3, have_ax, tol);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+// after q = A p: alpha, x/r update, convergence and beta, p update
+template <typename C>
+Err cocg_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
+  DDA_CU(launch_k(k_cocg_mu<C>, vgrid(rb, nrhs), dim3(kThreads), 0, st, kv, ks, rb, n3));
+  CHECK_LAUNCH();
+  DDA_CU(launch_k(k_cocg_xr<C>, vgrid(rb, nrhs), dim3(kThreads), 0, st, kv, ks, rb, n3));
+  CHECK_LAUNCH();
+  const int nb = (int)std::min<int64_t>((n3 + kThreads * 4 - 1) / (kThreads * 4), 1024);
+  DDA_CU(launch_k(k_cocg_p<C>, dim3(nb, nrhs), dim3(kThreads), 0, st, kv, ks, n3));
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+
+template <typename C>
+Err scale_sites(C* v, const C* s, const uint8_t* comp, int ncomp, int nrhs, int64_t n, bool inv, cudaStream_t st) {
+  const int nb = (int)std::min<int64_t>((3 * n + kThreads * 4 - 1) / (kThreads * 4), 1024);
+  k_scale_sites<C><<<dim3(nb, nrhs), kThreads, 0, st>>>(v, s, comp, ncomp, n, inv);
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+
+template <typename C>
 Err b2_init(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, double tol, bool have_ax,
             cudaStream_t st) {
   k_b2_init<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3, have_ax, tol);
@@ -896,7 +1072,10 @@ Err add_to_c128(double2* dst, const C* src, const int* mask_done, int nrhs, int6
   template Err b2_alpha<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int, int64_t, cudaStream_t);           \
   template Err b2_r_update<C>(const KrylovVecs<C>&, const KState*, int, int, int64_t, cudaStream_t);          \
   template Err b2_beta<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, cudaStream_t);                 \
-  template Err b2_mr<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, cudaStream_t);
+  template Err b2_mr<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, cudaStream_t);                  \
+  template Err cocg_init<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, double, bool, cudaStream_t); \
+  template Err cocg_update<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, cudaStream_t);            \
+  template Err scale_sites<C>(C*, const C*, const uint8_t*, int, int, int64_t, bool, cudaStream_t);
 INST(float2)
 INST(double2)
 

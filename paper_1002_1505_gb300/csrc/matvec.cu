@@ -75,6 +75,7 @@ __global__ void k_xfwd(Geom g, MvData<C> d, const C* __restrict__ p, int ty, boo
       if (idx >= 0) {
         v = p[((int64_t)b * 3 + c) * g.n + idx];
         if (conj) v = conjc(v);
+        if (d.sc) v = cmul(v, d.sc[((int64_t)b * g.ncomp + (d.comp ? d.comp[3 * idx + c] : 0)) * 3 + c]);
       }
     }
     s[(c * ty + t) * ps + x] = v;
@@ -130,7 +131,20 @@ __global__ void k_xinv(Geom g, MvData<C> d, const C* __restrict__ p, C* __restri
     const int cc = d.comp ? d.comp[3 * idx + c] : 0;  // composition of axis c
     C pv = p[o];
     if (conj) pv = conjc(pv);
-    C out = cadd(s[(c * ty + t) * ps + x], cmul(ia[cc * 3 + c], pv));
+    C out;
+    if (d.iat) {  // rotated dielectric frame: row c of the full symmetric alpha^{-1} of this site
+      const C* m6 = d.iat + ((int64_t)(rhs0 + b) * g.n + idx) * 6;
+      out = s[(c * ty + t) * ps + x];
+      for (int c2 = 0; c2 < 3; ++c2) {
+        C q = p[((int64_t)b * 3 + c2) * g.n + idx];
+        if (conj) q = conjc(q);
+        const int lo = c < c2 ? c : c2, hi = c < c2 ? c2 : c;
+        out = cadd(out, cmul(m6[lo == 0 ? hi : (lo == 1 ? 2 + hi : 5)], q));
+      }
+    } else {
+      out = d.sc ? cadd(cmul(d.sc[((int64_t)b * g.ncomp + cc) * 3 + c], s[(c * ty + t) * ps + x]), pv)
+                 : cadd(s[(c * ty + t) * ps + x], cmul(ia[cc * 3 + c], pv));
+    }
     ap[o] = conj ? conjc(out) : out;
   }
 }
@@ -481,6 +495,11 @@ template <typename C>
 Err launch_matvec(const Geom& g, const MvData<C>& d, const MvTune& t, const C* p, C* ap, int nrhs, int rhs0,
                   bool conj, cudaStream_t st) {
   if (nrhs <= 0) return Err::Ok();
+  if (d.sc && rhs0 != 0) {  // the scale table is indexed from the launch's first RHS
+    MvData<C> dd = d;
+    dd.sc += (int64_t)rhs0 * g.ncomp * 3;
+    return launch_matvec<C>(g, dd, t, p, ap, nrhs, 0, conj, st);  // the alpha table is unused when scaled
+  }
   if (t.fast) return launch_matvec_fast<C>(g, d, t, p, ap, nrhs, rhs0, conj, st);
   int pass = 0;
   mark(pass++, st);

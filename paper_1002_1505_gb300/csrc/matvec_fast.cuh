@@ -151,6 +151,10 @@ __device__ __forceinline__ void x_fwd_body(const Geom& g, const MvData<C>& d, co
           kf->s[o] = v;
           kred::acc_nrm(ss, v);
         }
+        if (d.sc) {  // Jacobi scaling: transform s * v
+          const int c = c0 + cl;
+          v = cmul(v, d.sc[((int64_t)b * g.ncomp + (d.comp ? d.comp[3 * idx + c] : 0)) * 3 + c]);
+        }
       }
     }
     in[(cl * TY + t) * ip + x] = v;
@@ -287,7 +291,22 @@ __device__ __forceinline__ void x_inv_body(const Geom& g, const MvData<C>& d, co
     const int cc = d.comp ? d.comp[3 * idx + c] : 0;  // composition of axis c
     C pv = io_get<C>(p[o]);
     if (conj) pv = conjc(pv);
-    const C res = cadd(in[(cl * TY + t) * ip + x], cmul(ia[cc * 3 + c], pv));
+    C res;
+    if (d.iat) {  // rotated dielectric frame: row c of the full symmetric alpha^{-1} of this site
+      const C* m6 = d.iat + ((int64_t)(rhs0 + b) * g.n + idx) * 6;
+      const int64_t oc = ((int64_t)b * 3) * g.n + idx;
+      res = in[(cl * TY + t) * ip + x];
+#pragma unroll
+      for (int c2 = 0; c2 < 3; ++c2) {
+        C q = io_get<C>(p[oc + (int64_t)c2 * g.n]);
+        if (conj) q = conjc(q);
+        const int lo = c < c2 ? c : c2, hi = c < c2 ? c2 : c;
+        res = cadd(res, cmul(m6[lo == 0 ? hi : (lo == 1 ? 2 + hi : 5)], q));
+      }
+    } else {
+      res = d.sc ? cadd(cmul(d.sc[((int64_t)b * g.ncomp + cc) * 3 + c], in[(cl * TY + t) * ip + x]), pv)
+                 : cadd(in[(cl * TY + t) * ip + x], cmul(ia[cc * 3 + c], pv));
+    }
     ap[o] = io_put<C>(conj ? conjc(res) : res);
     if constexpr (MODE == kFuseRV) {
       kred::acc_cdot(re, im, kf->rhat[o], res);  // <rhat, v>

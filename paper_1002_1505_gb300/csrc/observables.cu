@@ -82,6 +82,36 @@ __global__ void k_qsum(const uint8_t* comp, const double2* __restrict__ e, const
   bred<3>(acc, part + ((int64_t)b * gridDim.x + blockIdx.x) * 4);
 }
 
+// the same sums for sites with a full symmetric alpha^{-1} (rotated dielectric frames):
+// S_abs = sum_j { Im[P_j . (alpha_j^{-1})^* P_j^*] - (2/3) k^3 |P_j|^2 }
+__global__ void k_qsum_t(const double2* __restrict__ e, const double2* __restrict__ iat, double kd,
+                         const double2* __restrict__ p, int64_t n, double* part) {
+  const int b = blockIdx.y;
+  const double rr = (2.0 / 3.0) * kd * kd * kd;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    double2 P[3];
+    for (int c = 0; c < 3; ++c) {
+      const double2 ev = e[((int64_t)b * 3 + c) * n + j];
+      const double2 pv = p[((int64_t)b * 3 + c) * n + j];
+      P[c] = pv;
+      acc[0] += ev.x * pv.y - ev.y * pv.x;
+      acc[1] += ev.x * pv.x + ev.y * pv.y;
+      acc[2] -= rr * (pv.x * pv.x + pv.y * pv.y);
+    }
+    const double2* m6 = iat + ((int64_t)b * n + j) * 6;
+    for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) {
+        const int lo = a < c ? a : c, hi = a < c ? c : a;
+        const double2 m = m6[lo == 0 ? hi : (lo == 1 ? 2 + hi : 5)];
+        // Im[P_a conj(M_ac) conj(P_c)]
+        const double2 t = make_double2(P[a].x * m.x + P[a].y * m.y, P[a].y * m.x - P[a].x * m.y);  // P_a conj(M)
+        acc[2] += t.y * P[c].x - t.x * P[c].y;
+      }
+  }
+  bred<3>(acc, part + ((int64_t)b * gridDim.x + blockIdx.x) * 4);
+}
+
 __global__ void k_qsum_fin(const double* part, int nblk, double* out3) {
   const int b = blockIdx.x;
   double v[3] = {0, 0, 0};
@@ -225,7 +255,239 @@ __global__ void k_far_many_fin(const double* __restrict__ part, int nblk, int nc
   }
 }
 
+// ------------------------------------------------------------------ radiative force and torque
+// Far-field moments for the torque: per (RHS, direction) g = sum_j P_j exp(-i k n.r_j) (3 complex)
+// and T[c][a] = sum_j (r_j - r_cm)_c P_ja exp(-i k n.r_j) (9 complex), from the same FP32 phase
+// tables; grid (site blocks, direction pairs, nrhs); per-thread FP32 sums, FP64 across the block.
+constexpr int kMomDir = 2;
+constexpr int kMomVals = 24;  // 12 complex per direction
+__global__ void __launch_bounds__(kT) k_far_moments(const int32_t* __restrict__ ijk, const double2* __restrict__ p,
+                                                    int64_t n, int ndir, int bx, int by, int bz, float sx, float sy,
+                                                    float sz, const float2* __restrict__ tab,
+                                                    double* __restrict__ part) {
+  extern __shared__ float2 stab[];
+  const int nt = bx + by + bz;
+  const int b = blockIdx.z, d0 = blockIdx.y * kMomDir;
+  const int nd = min(kMomDir, ndir - d0);
+  const float2* src = tab + ((int64_t)b * ndir + d0) * nt;
+  for (int i = threadIdx.x; i < nd * nt; i += blockDim.x) stab[i] = src[i];
+  __syncthreads();
+  float acc[kMomDir][kMomVals];
+#pragma unroll
+  for (int dd = 0; dd < kMomDir; ++dd)
+#pragma unroll
+    for (int s = 0; s < kMomVals; ++s) acc[dd][s] = 0.f;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int i0 = ijk[3 * j], i1 = ijk[3 * j + 1], i2 = ijk[3 * j + 2];
+    const float rpos[3] = {(float)i0 + sx, (float)i1 + sy, (float)i2 + sz};
+    float2 pv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double2 v = p[((int64_t)b * 3 + c) * n + j];
+      pv[c] = make_float2((float)v.x, (float)v.y);
+    }
+#pragma unroll
+    for (int dd = 0; dd < kMomDir; ++dd) {
+      if (dd < nd) {
+        const float2* t = stab + dd * nt;
+        const float2 tx = t[i0], ty = t[bx + i1], tz = t[bx + by + i2];
+        const float2 txy = make_float2(tx.x * ty.x - tx.y * ty.y, tx.x * ty.y + tx.y * ty.x);
+        const float2 ph = make_float2(txy.x * tz.x - txy.y * tz.y, txy.x * tz.y + txy.y * tz.x);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const float2 q = make_float2(pv[a].x * ph.x - pv[a].y * ph.y, pv[a].x * ph.y + pv[a].y * ph.x);
+          acc[dd][2 * a] += q.x;
+          acc[dd][2 * a + 1] += q.y;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            acc[dd][6 + 2 * (3 * c + a)] = fmaf(rpos[c], q.x, acc[dd][6 + 2 * (3 * c + a)]);
+            acc[dd][6 + 2 * (3 * c + a) + 1] = fmaf(rpos[c], q.y, acc[dd][6 + 2 * (3 * c + a) + 1]);
+          }
+        }
+      }
+    }
+  }
+  double v[kMomDir * kMomVals];
+#pragma unroll
+  for (int dd = 0; dd < kMomDir; ++dd)
+#pragma unroll
+    for (int s = 0; s < kMomVals; ++s) v[dd * kMomVals + s] = (double)acc[dd][s];
+  bred<kMomDir * kMomVals>(v, part + (((int64_t)b * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) *
+                                         (kMomDir * kMomVals));
+}
+
+// sum the site-block partials: out[rhs][d][12] (complex: g_x g_y g_z, then T row-major [c][a])
+__global__ void k_far_moments_fin(const double* __restrict__ part, int nblk, int nchunk, int ndir,
+                                  double2* __restrict__ out) {
+  const int rc = blockIdx.x;  // rhs * nchunk + chunk
+  const int b = rc / nchunk, ch = rc - b * nchunk;
+  for (int s = threadIdx.x; s < kMomDir * kMomVals; s += blockDim.x) {
+    double v = 0.0;
+    for (int i = 0; i < nblk; ++i) v += part[((int64_t)rc * nblk + i) * (kMomDir * kMomVals) + s];
+    const int d = ch * kMomDir + s / kMomVals;
+    if (d < ndir) {
+      double* o = reinterpret_cast<double*>(out + ((int64_t)b * ndir + d) * 12);
+      o[s % kMomVals] = v;
+    }
+  }
+}
+
+// Incident-field part of the force and torque, per RHS (FP64): out7[b] =
+// { sum_j Re(P_j x E_j^*) (3), sum_j (r_j - r_cm) Im(P_j . E_j^*) (3), sum_j Im(P_j . E_j^*) }.
+__global__ void k_torque_ext(const int32_t* __restrict__ ijk, const double2* __restrict__ e,
+                             const double2* __restrict__ p, int64_t n, double sx, double sy, double sz,
+                             double* __restrict__ part) {
+  const int b = blockIdx.y;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    double2 P[3], E[3];
+    for (int c = 0; c < 3; ++c) {
+      P[c] = p[((int64_t)b * 3 + c) * n + j];
+      E[c] = e[((int64_t)b * 3 + c) * n + j];
+    }
+    // P x E^*: component a = P_b E_c^* - P_c E_b^*, real part
+    for (int a = 0; a < 3; ++a) {
+      const int b1 = (a + 1) % 3, c1 = (a + 2) % 3;
+      acc[a] += (P[b1].x * E[c1].x + P[b1].y * E[c1].y) - (P[c1].x * E[b1].x + P[c1].y * E[b1].y);
+    }
+    double im = 0.0;  // Im(P . E^*)
+    for (int c = 0; c < 3; ++c) im += P[c].y * E[c].x - P[c].x * E[c].y;
+    acc[3] += ((double)ijk[3 * j] + sx) * im;
+    acc[4] += ((double)ijk[3 * j + 1] + sy) * im;
+    acc[5] += ((double)ijk[3 * j + 2] + sz) * im;
+    acc[6] += im;
+  }
+  bred<7>(acc, part + ((int64_t)b * gridDim.x + blockIdx.x) * 8);
+}
+
+__global__ void k_torque_ext_fin(const double* part, int nblk, double* out7) {
+  const int b = blockIdx.x;
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x)
+    for (int s = 0; s < 7; ++s) v[s] += part[((int64_t)b * nblk + i) * 8 + s];
+  __shared__ double res[7];
+  bred<7>(v, res);
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int s = 0; s < 7; ++s) out7[7 * b + s] = res[s];
+}
+
+// ------------------------------------------------------------------ fields in or near the target
+// E and B at kNfPts points per CTA from every dipole (retarded point-dipole fields, FP64), the
+// contribution of dipoles closer than one lattice spacing scaled by phi(R) = R^4 (5 - 4 R);
+// grid (point chunks, nrhs); out[rhs][point][12] = E (re, im) x 3, then B.
+constexpr int kNfPts = 4;
+__global__ void __launch_bounds__(kT) k_near_field(const int32_t* __restrict__ ijk, const double* __restrict__ org,
+                                                   const double2* __restrict__ p, int64_t n,
+                                                   const double* __restrict__ pts, int64_t npts, double kd,
+                                                   double* __restrict__ out) {
+  const int b = blockIdx.y;
+  const int64_t q0 = (int64_t)blockIdx.x * kNfPts;
+  double acc[kNfPts * 12];
+#pragma unroll
+  for (int i = 0; i < kNfPts * 12; ++i) acc[i] = 0.0;
+  double xq[kNfPts][3];
+#pragma unroll
+  for (int q = 0; q < kNfPts; ++q)
+    for (int a = 0; a < 3; ++a) xq[q][a] = (q0 + q < npts) ? pts[(q0 + q) * 3 + a] : 1e300;
+  const double k2 = kd * kd;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    const double r[3] = {ijk[3 * j] + org[0], ijk[3 * j + 1] + org[1], ijk[3 * j + 2] + org[2]};
+    double2 P[3];
+    for (int c = 0; c < 3; ++c) P[c] = p[((int64_t)b * 3 + c) * n + j];
+#pragma unroll
+    for (int q = 0; q < kNfPts; ++q) {
+      if (q0 + q >= npts) continue;
+      const double dx = xq[q][0] - r[0], dy = xq[q][1] - r[1], dz = xq[q][2] - r[2];
+      const double R2 = dx * dx + dy * dy + dz * dz;
+      if (R2 == 0.0) continue;
+      const double R = sqrt(R2), iR = 1.0 / R;
+      const double nv[3] = {dx * iR, dy * iR, dz * iR};
+      const double phi = R < 1.0 ? R2 * R2 * (5.0 - 4.0 * R) : 1.0;
+      double sn, cs;
+      sincos(kd * R, &sn, &cs);
+      // n x p, n . p (complex)
+      double2 nxp[3];
+      for (int a = 0; a < 3; ++a) {
+        const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+        nxp[a] = make_double2(nv[a1] * P[a2].x - nv[a2] * P[a1].x, nv[a1] * P[a2].y - nv[a2] * P[a1].y);
+      }
+      const double2 ndp = make_double2(nv[0] * P[0].x + nv[1] * P[1].x + nv[2] * P[2].x,
+                                       nv[0] * P[0].y + nv[1] * P[1].y + nv[2] * P[2].y);
+      // E = e^{ikR} { k^2 (n x p) x n / R + [3 n (n.p) - p] (1/R^3 - i k/R^2) }
+      const double2 f = make_double2(iR * iR * iR, -kd * iR * iR);     // (1/R^3 - i k/R^2)
+      const double2 ph = make_double2(cs * phi, sn * phi);
+      // B = e^{ikR} (n x p) (k^2/R + i k/R^2)
+      const double2 gb = make_double2(k2 * iR, kd * iR * iR);
+      for (int a = 0; a < 3; ++a) {
+        const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+        // ((n x p) x n)_a = (nxp)_{a1} n_{a2} - (nxp)_{a2} n_{a1}
+        const double2 t1 = make_double2((nxp[a1].x * nv[a2] - nxp[a2].x * nv[a1]) * k2 * iR,
+                                        (nxp[a1].y * nv[a2] - nxp[a2].y * nv[a1]) * k2 * iR);
+        const double2 u = make_double2(3.0 * nv[a] * ndp.x - P[a].x, 3.0 * nv[a] * ndp.y - P[a].y);
+        const double2 t2 = make_double2(u.x * f.x - u.y * f.y, u.x * f.y + u.y * f.x);
+        const double2 e = make_double2(t1.x + t2.x, t1.y + t2.y);
+        acc[q * 12 + 2 * a] += e.x * ph.x - e.y * ph.y;
+        acc[q * 12 + 2 * a + 1] += e.x * ph.y + e.y * ph.x;
+        const double2 bb = make_double2(nxp[a].x * gb.x - nxp[a].y * gb.y, nxp[a].x * gb.y + nxp[a].y * gb.x);
+        acc[q * 12 + 6 + 2 * a] += bb.x * ph.x - bb.y * ph.y;
+        acc[q * 12 + 6 + 2 * a + 1] += bb.x * ph.y + bb.y * ph.x;
+      }
+    }
+  }
+  __shared__ double res[kNfPts * 12];
+  bred<kNfPts * 12>(acc, res);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kNfPts * 12; i += blockDim.x) {
+    const int q = i / 12;
+    if (q0 + q < npts) out[((int64_t)b * npts + q0 + q) * 12 + (i % 12)] = res[i];
+  }
+}
+
 }  // namespace
+
+Err near_field(const int32_t* ijk, const double* origin3, const double2* p, int nrhs, int64_t n, const double* pts,
+               int64_t npts, double kd, double* out, cudaStream_t st) {
+  const int64_t nchunk = (npts + kNfPts - 1) / kNfPts;
+  if (nchunk > 2147483647LL) return Err::make(DDA_EINVAL, "too many field points");
+  k_near_field<<<dim3((unsigned)nchunk, nrhs), kT, 0, st>>>(ijk, origin3, p, n, pts, npts, kd, out);
+  DDA_CU(cudaGetLastError());
+  add_launches(1);
+  return Err::Ok();
+}
+
+Err farfield_moments(const int32_t* ijk, const double* origin3, const double* nhat, double kd, const double2* p,
+                     int nrhs, int ndir, int64_t n, const int box[3], const double shift[3], float2* tab, double* part,
+                     int nblk, double2* out, cudaStream_t st) {
+  const int nt = box[0] + box[1] + box[2];
+  const int64_t nrd = (int64_t)nrhs * ndir;
+  const int tb = (int)std::min<int64_t>((nrd * nt + kT - 1) / kT, 152 * 32);
+  k_phase_tables<<<tb, kT, 0, st>>>(nhat, nrd, origin3, kd, box[0], box[1], box[2], tab);
+  DDA_CU(cudaGetLastError());
+  add_launches(1);
+  const int nchunk = (ndir + kMomDir - 1) / kMomDir;
+  const size_t sm = sizeof(float2) * (size_t)kMomDir * nt;
+  if (sm > 48 * 1024) return Err::make(DDA_EUNSUPPORTED, "target box too long for the phase tables");
+  k_far_moments<<<dim3(nblk, nchunk, nrhs), kT, sm, st>>>(ijk, p, n, ndir, box[0], box[1], box[2], (float)shift[0],
+                                                          (float)shift[1], (float)shift[2], tab, part);
+  DDA_CU(cudaGetLastError());
+  add_launches(1);
+  k_far_moments_fin<<<nrhs * nchunk, 64, 0, st>>>(part, nblk, nchunk, ndir, out);
+  DDA_CU(cudaGetLastError());
+  add_launches(1);
+  return Err::Ok();
+}
+
+Err torque_ext_sums(const int32_t* ijk, const double2* einc, const double2* p, int nrhs, int64_t n,
+                    const double shift[3], double* part, int nblk, double* out7, cudaStream_t st) {
+  k_torque_ext<<<dim3(nblk, nrhs), kT, 0, st>>>(ijk, einc, p, n, shift[0], shift[1], shift[2], part);
+  DDA_CU(cudaGetLastError());
+  add_launches(1);
+  k_torque_ext_fin<<<nrhs, kT, 0, st>>>(part, nblk, out7);
+  DDA_CU(cudaGetLastError());
+  add_launches(1);
+  return Err::Ok();
+}
 
 Err farfield_many(const int32_t* ijk, const double* origin3, const double* nhat, double kd, const double2* p,
                   int nrhs, int ndir, int64_t n, const int box[3], float2* tab, double* part, int nblk, double2* out,
@@ -264,6 +526,17 @@ template Err incident_field<double2>(const int32_t*, const double*, const RhsGeo
 Err qsums(const uint8_t* comp, const double2* einc, const double2* ia, int ncomp, double kd, const double2* p,
           int nrhs, int64_t n, double* out3, RedBuf rb, cudaStream_t st) {
   k_qsum<<<dim3(rb.nblk, nrhs), kT, 0, st>>>(comp, einc, ia, ncomp, kd, p, n, rb.part);
+  DDA_CU(cudaGetLastError());
+  add_launches(1);
+  k_qsum_fin<<<nrhs, kT, 0, st>>>(rb.part, rb.nblk, out3);
+  DDA_CU(cudaGetLastError());
+  add_launches(1);
+  return Err::Ok();
+}
+
+Err qsums_tensor(const double2* einc, const double2* iat, double kd, const double2* p, int nrhs, int64_t n,
+                 double* out3, RedBuf rb, cudaStream_t st) {
+  k_qsum_t<<<dim3(rb.nblk, nrhs), kT, 0, st>>>(einc, iat, kd, p, n, rb.part);
   DDA_CU(cudaGetLastError());
   add_launches(1);
   k_qsum_fin<<<nrhs, kT, 0, st>>>(rb.part, rb.nblk, out3);

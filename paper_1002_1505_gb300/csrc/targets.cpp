@@ -145,8 +145,22 @@ Err make_shape_target(int shape, const double* shpar, int nshpar, HostTarget* ou
   return Err::make(DDA_EINVAL, "unknown shape id");
 }
 
+void df_axes(double th, double ph, double be, double R[9]) {
+  const double ct = std::cos(th), st = std::sin(th), cp = std::cos(ph), sp = std::sin(ph), cb = std::cos(be),
+               sb = std::sin(be);
+  const double e1[3] = {ct, st * cp, st * sp};
+  const double e2[3] = {-st * cb, ct * cb * cp - sb * sp, ct * cb * sp + sb * cp};
+  const double e3[3] = {st * sb, -(ct * sb * cp + cb * sp), -(ct * sb * sp - cb * cp)};
+  for (int a = 0; a < 3; ++a) {
+    R[3 * a + 0] = e1[a];
+    R[3 * a + 1] = e2[a];
+    R[3 * a + 2] = e3[a];
+  }
+}
+
 Err make_site_target(const int32_t* ixyz, const int32_t* icomp, int64_t n, const double origin[3],
-                     const double a1[3], const double a2[3], HostTarget* out, bool per_axis) {
+                     const double a1[3], const double a2[3], HostTarget* out, bool per_axis,
+                     const double* df_angles) {
   if (!ixyz || n <= 0) return Err::make(DDA_EINVAL, "site list is empty");
   if (n > (int64_t)1 << 30) return Err::make(DDA_EINVAL, "too many sites");
   int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
@@ -180,6 +194,17 @@ Err make_site_target(const int32_t* ixyz, const int32_t* icomp, int64_t n, const
   }
   out->ijk.resize(3 * n);
   out->comp.resize(3 * n);
+  out->dfrot.clear();
+  if (df_angles) {
+    out->dfrot.resize(9 * n);
+    for (int64_t s = 0; s < n; ++s) {
+      const int64_t j = sorted ? s : order[s];
+      const double* an = df_angles + 3 * j;
+      if (!std::isfinite(an[0]) || !std::isfinite(an[1]) || !std::isfinite(an[2]))
+        return Err::make(DDA_EINVAL, "dielectric-frame angles must be finite");
+      df_axes(an[0], an[1], an[2], &out->dfrot[9 * s]);
+    }
+  }
   int maxc = 1;
   if (sorted && !icomp) {  // the common case: one material, list in order
     for (int64_t s = 0; s < n; ++s)

@@ -22,7 +22,8 @@ DDA_OK, DDA_EINVAL, DDA_ENOMEM, DDA_ECUDA, DDA_ENOCONV, DDA_ETIMEOUT, DDA_ESTATE
 DDA_C64, DDA_C128, DDA_C128DF = 1, 2, 3  # DDA_C128DF: complex128 vectors, double-float arithmetic
 SHAPES = {"ELLIPSOID": 1, "RCTGLPRSM": 2, "CYLINDER1": 3, "HEX_PRISM": 4}
 PRESCRIPTIONS = {"CM": 1, "LATTDR": 2, "GKDLDR": 3}
-SOLVERS = {"BICGSTAB": 1, "CCG": 2, "BICGSTAB2": 3}
+SOLVERS = {"BICGSTAB": 1, "CCG": 2, "BICGSTAB2": 3, "COCG": 4}
+PRECONDS = {"NONE": 0, "JACOBI": 1}
 PRECISIONS = {"C64": 1, "C128": 2, "MIXED": 3}
 STATUS_NAMES = ["DDA_OK", "DDA_EINVAL", "DDA_ENOMEM", "DDA_ECUDA", "DDA_ENOCONV", "DDA_ETIMEOUT", "DDA_ESTATE",
                 "DDA_EUNSUPPORTED"]
@@ -38,7 +39,7 @@ class dda_solve_opts(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("inner_tol", ctypes.c_double), ("timeout_ms", ctypes.c_double),
                 ("warm_start", ctypes.c_int), ("check_every", ctypes.c_int), ("normal_eq", ctypes.c_int),
-                ("use_graph", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("precond", ctypes.c_int)]
 
 
 class dda_solve_report(ctypes.Structure):
@@ -60,6 +61,7 @@ def _load():
         "dda_setup_shape": (I, [P, I, P, I, P, P]),
         "dda_setup_target": (I, [P, P, P, I64, P, P, P]),
         "dda_setup_target_aniso": (I, [P, P, P, I64, P, P, P]),
+        "dda_setup_target_anifrm": (I, [P, P, P, I64, P, P, P, P]),
         "dda_get_sites": (I, [P, P, P]),
         "dda_get_box": (I, [P, P, P]),
         "dda_set_incident": (I, [P, D, P, I, P, I]),
@@ -78,6 +80,8 @@ def _load():
         "dda_kernel_launches": (ctypes.c_ulonglong, []),
         "dda_selftest_bulk_wait": (I, [I, P]),
         "dda_angular_averages": (I, [P, P, D, P, P]),
+        "dda_force_torque": (I, [P, P, D, P, P]),
+        "dda_near_field": (I, [P, P, P, I64, P, P]),
         "dda_orientation_grid": (I, [P, I, P, I, P, I, P, P]),
         "dda_profile_matvec": (I, [P, I, I, I, P, P]),
         "dda_matvec_noalloc": (I, [P, P, P, I, I]),
@@ -176,6 +180,20 @@ class Context:
                                          None if a1v is None else _ptr(a1v), None if a2v is None else _ptr(a2v)))
         self.n, self.box = self.dda_get_box()
 
+    def dda_setup_target_anifrm(self, ixyz, icomp3, df_angles, origin=(0.0, 0.0, 0.0), a1=None, a2=None):
+        """Site list with per-axis compositions (N x 3, 1-based) and per-site Dielectric-Frame angles
+        (N x 3: theta_DF, phi_DF, beta_DF, radians): the guide's ANIFRMFIL target."""
+        ij = np.ascontiguousarray(ixyz, dtype=np.int32)
+        ic = np.ascontiguousarray(icomp3, dtype=np.int32)
+        an = np.ascontiguousarray(df_angles, dtype=np.float64)
+        org = np.ascontiguousarray(origin, dtype=np.float64)
+        a1v = None if a1 is None else np.ascontiguousarray(a1, dtype=np.float64)
+        a2v = None if a2 is None else np.ascontiguousarray(a2, dtype=np.float64)
+        self._check(LIB.dda_setup_target_anifrm(self._h, _ptr(ij), _ptr(ic), ij.shape[0], _ptr(org),
+                                                None if a1v is None else _ptr(a1v),
+                                                None if a2v is None else _ptr(a2v), _ptr(an)))
+        self.n, self.box = self.dda_get_box()
+
     def dda_get_box(self):
         """(N, (box_x, box_y, box_z)) of the current target."""
         n = np.zeros(1, dtype=np.int64)
@@ -265,11 +283,12 @@ class Context:
 
     def dda_solve(self, p, solver="BICGSTAB", precision="MIXED", tol=1e-5, maxit=1000, inner_tol=0.0,
                   timeout_ms=0.0, warm_start=False, check_every=8, normal_eq=False, use_graph=True,
-                  raise_on_noconv=True):
+                  raise_on_noconv=True, precond="NONE"):
         """Solve A P = E_inc; p is a complex128 [nrhs,3,N] CUDA tensor (guess if warm_start, solution out)."""
         self._dev_check(p, DDA_C128)
         o = dda_solve_opts(SOLVERS[solver.upper()], PRECISIONS[precision.upper()], tol, maxit, inner_tol,
-                           timeout_ms, int(bool(warm_start)), check_every, int(bool(normal_eq)), int(bool(use_graph)))
+                           timeout_ms, int(bool(warm_start)), check_every, int(bool(normal_eq)), int(bool(use_graph)),
+                           PRECONDS[precond.upper()])
         rep = (dda_solve_report * self.nrhs)()
         st = LIB.dda_solve(self._h, ctypes.byref(o), ctypes.c_void_p(p.data_ptr()), rep)
         reports = [{k: getattr(r, k) for k, _ in dda_solve_report._fields_} for r in rep]
@@ -284,6 +303,25 @@ class Context:
         nd = np.zeros(1, dtype=np.int32)
         self._check(LIB.dda_angular_averages(self._h, ctypes.c_void_p(p.data_ptr()), float(eta), _ptr(out), _ptr(nd)))
         return out, int(nd[0])
+
+    def dda_force_torque(self, p, eta=0.5):
+        """(Q_pr [nrhs, 3], Q_Gamma [nrhs, 3], number of directions), Target-Frame components."""
+        self._dev_check(p, DDA_C128)
+        out = np.zeros((self.nrhs, 6))
+        nd = np.zeros(1, dtype=np.int32)
+        self._check(LIB.dda_force_torque(self._h, ctypes.c_void_p(p.data_ptr()), float(eta), _ptr(out), _ptr(nd)))
+        return out[:, :3].copy(), out[:, 3:].copy(), int(nd[0])
+
+    def dda_near_field(self, p, points, want_b=True):
+        """(E [nrhs, npts, 3], B [nrhs, npts, 3] or None) complex, at TF points (npts, 3), lattice units."""
+        self._dev_check(p, DDA_C128)
+        pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+        e = np.zeros((self.nrhs, pts.shape[0], 6))
+        b = np.zeros((self.nrhs, pts.shape[0], 6)) if want_b else None
+        self._check(LIB.dda_near_field(self._h, ctypes.c_void_p(p.data_ptr()), _ptr(pts), pts.shape[0], _ptr(e),
+                                       None if b is None else _ptr(b)))
+        to_c = lambda a: a[..., 0::2] + 1j * a[..., 1::2]
+        return to_c(e), (None if b is None else to_c(b))
 
     def dda_cross_sections(self, p, dirs=None):
         """Returns (Q array [nrhs,4] = Qext,Qabs,Qsca,Qpha, Mueller [n_ori,ndir,4,4] or None)."""
@@ -468,7 +506,7 @@ def dda_schedule_info(ctx: "Context", dtype: int = DDA_C64):
 
 
 def dda_solve_batch(ctxs, ps, solver="BICGSTAB", precision="MIXED", tol=1e-5, maxit=1000, inner_tol=0.0,
-                    timeout_ms=0.0, check_every=8, normal_eq=False):
+                    timeout_ms=0.0, check_every=8, normal_eq=False, precond="NONE"):
     """Solve several contexts concurrently; ps[i] complex128 [nrhs_i,3,N_i] CUDA tensors.
 
     Returns (list of per-context report lists, list of statuses, overall status)."""
@@ -476,7 +514,7 @@ def dda_solve_batch(ctxs, ps, solver="BICGSTAB", precision="MIXED", tol=1e-5, ma
     for c, p in zip(ctxs, ps):
         c._dev_check(p, DDA_C128)
     o = dda_solve_opts(SOLVERS[solver.upper()], PRECISIONS[precision.upper()], tol, maxit, inner_tol, timeout_ms,
-                       0, check_every, int(bool(normal_eq)), 1)
+                       0, check_every, int(bool(normal_eq)), 1, PRECONDS[precond.upper()])
     handles = (ctypes.c_void_p * n)(*[c._h.value for c in ctxs])
     bufs = (ctypes.c_void_p * n)(*[p.data_ptr() for p in ps])
     rep_arrays = [(dda_solve_report * c.nrhs)() for c in ctxs]

@@ -520,7 +520,7 @@ def main():
                 "schedule": {"passes": sched[0], "compile_time_kernels": bool(sched[1]),
                              "plane_threads": sched[2], "tuned_for_nrhs": sched[3], "ctas_per_plane": sched[4],
                              "x_tile_rows": sched[5], "bulk_staged_plane": bool(sched[6]),
-                             "x_components_per_cta": sched[7]},
+                             "x_components_per_cta": sched[7], "z_register_fused": bool(sched[8])},
                 "product_ms": float(np.sum(ms_pass))}
     # the FP64-accurate product of the true residuals: complex128 on the FP64 units against
     # double-float arithmetic on the FP32 units (the one the mixed solve uses where it exists)

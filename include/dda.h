@@ -86,9 +86,11 @@ enum { DDA_BICGSTAB = 1, DDA_CCG = 2, DDA_BICGSTAB2 = 3, DDA_COCG = 4 };
  * the guide's solvers are preconditioned Krylov methods): none, or Jacobi, the
  * diagonal of A, applied symmetrically -- the solver iterates on
  * (S A S) y = S E with S = diag(alpha^{1/2}) and returns P = S y, which keeps
- * the operator complex symmetric for DDA_COCG; its stopping test uses the
- * scaled residual |S (E - A P)| / |S E| (the reported true residual is
- * unscaled). */
+ * the operator complex symmetric for DDA_COCG.  The iterations test the scaled
+ * residual |S (E - A P)| / |S E| against tol / kappa, kappa = max |s| / min |s|
+ * over the polarizability table, which guarantees |E - A P| / |E| <= tol for
+ * the complex64 and complex128 solves (mixed-precision solves test the true
+ * residual in their outer loop anyway). */
 enum { DDA_PRECOND_NONE = 0, DDA_PRECOND_JACOBI = 1 };
 /* Arithmetic of the solve: all complex64, all complex128, or complex64 inner
  * iterations refined against complex128 true residuals. */
@@ -261,6 +263,12 @@ typedef struct {
   int normal_eq;     /* 1 = also evaluate the guide's normal-equation ratio at exit (2 extra FP64 products) */
   int use_graph;     /* 1 = replay the iterations as a captured CUDA graph, 0 = plain launches */
   int precond;       /* DDA_PRECOND_NONE or DDA_PRECOND_JACOBI */
+  int phi_reuse;     /* 1 = orientations that differ from an earlier one only in Phi are not iterated
+                        on: with iorth = 2 and a polarizability that does not depend on the incident
+                        polarization (DDA_CM, DDA_GKDLDR), their solutions are linear combinations of
+                        the earlier orientation's two (guide, note on IPHI > 1 in "Scattering
+                        Amplitude Matrix"); ignored otherwise.  Their reports show 0 iterations and
+                        their own FP64 true residual. */
 } dda_solve_opts;
 
 typedef struct {
@@ -334,8 +342,11 @@ DDA_API dda_status dda_profile_matvec(dda_ctx *ctx, int nrhs, int dtype, int ite
  * the plane pass is split over a cluster), info[5] = y rows per CTA of the x
  * passes (0 for the generic engine), info[6] = 1 when the plane pass stages its
  * HBM blocks with bulk copies (TMA), info[7] = field components per CTA of the
- * x passes (3 or 1; 0 for the generic engine). */
-DDA_API dda_status dda_schedule_info(dda_ctx *ctx, int dtype, int32_t info[8]);
+ * x passes (3 or 1; 0 for the generic engine), info[8] = 1 when the 5-pass z
+ * columns run pass B, the Ghat multiply and the inverse pass B of the three
+ * components in registers (the tuner's choice for long z transforms); info[9..11]
+ * are reserved (0). */
+DDA_API dda_status dda_schedule_info(dda_ctx *ctx, int dtype, int32_t info[12]);
 
 /* ---------------------------------------------------------------------------
  * Learned warm start (the guide has no counterpart: the solver accepts any

@@ -571,6 +571,12 @@ Err ensure_tuned(dda_ctx* c, int nrhs) {
       t.xty = 0;
       time_one(t);
     }
+    // the 5-pass z columns with their middle stages fused in registers (long pass-B sub-blocks)
+    if (err.ok() && sizeof(C) == sizeof(float2) && !best.plane && dda::zcols_rfuse_available_c64(g0)) {
+      dda::MvTune t = best;
+      t.zr = 1;
+      time_one(t);
+    }
     // and bulk-copy staging of the plane pass's HBM blocks
     int smax_b = 0;
     cudaDeviceGetAttribute(&smax_b, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
@@ -1139,6 +1145,11 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
       t64.bulk = (std::atoi(f) != 0) && t64.plane_ok && dda::plane_bulk_ok_c64(g64, smax);
       c->forced_schedule = true;
     }
+    // DDA_ZFUSE=1 / 0 pins the register-fused 5-pass z columns on / off (complex64, where they exist)
+    if (const char* f = std::getenv("DDA_ZFUSE")) {
+      t64.zr = (std::atoi(f) != 0 && t64.fast && dda::zcols_rfuse_available_c64(g64)) ? 1 : 0;
+      c->forced_schedule = true;
+    }
     // DDA_XCOMP=1 runs the x passes with one component per CTA
     if (const char* f = std::getenv("DDA_XCOMP")) {
       if (std::atoi(f) == 1) {
@@ -1361,13 +1372,16 @@ Err kvec_alloc(dda_ctx* c, dda::KrylovVecs<C>* kv, int nvec_extra) {
 
 // Jacobi scaling tables s = alpha^{1/2} (principal square root of 1 / alpha^{-1}) per RHS,
 // composition and axis, from the host copy of alpha^{-1}; complex128 and complex64 copies.
-Err ensure_scale(dda_ctx* c) {
+Err ensure_scale(dda_ctx* c, double* kappa) {
   const size_t nv = (size_t)c->nrhs * c->ncomp * 3;
   if (c->ia.size() != nv) return Err::make(DDA_ESTATE, "polarizabilities missing");
   std::vector<double2> s128(nv);
   std::vector<float2> s64(nv);
+  double smax = 0.0, smin = 1e300;
   for (size_t i = 0; i < nv; ++i) {
     const cd s = std::sqrt(1.0 / c->ia[i]);
+    smax = std::max(smax, std::abs(s));
+    smin = std::min(smin, std::abs(s));
     s128[i] = make_double2(s.real(), s.imag());
     s64[i] = make_float2((float)s.real(), (float)s.imag());
   }
@@ -1376,6 +1390,7 @@ Err ensure_scale(dda_ctx* c) {
   DDA_CU(cudaMemcpyAsync(c->d_sc128, s128.data(), sizeof(double2) * nv, cudaMemcpyHostToDevice, c->stream));
   DDA_CU(cudaMemcpyAsync(c->d_sc64, s64.data(), sizeof(float2) * nv, cudaMemcpyHostToDevice, c->stream));
   DDA_CU(cudaStreamSynchronize(c->stream));  // the host vectors go out of scope
+  *kappa = smin > 0 ? smax / smin : 1.0;
   return Err::Ok();
 }
 
@@ -1446,8 +1461,10 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
     const bool jac = o.precond == DDA_PRECOND_JACOBI;
     if (jac && c->iat_valid)
       return fail(c, Err::make(DDA_EUNSUPPORTED, "Jacobi scaling needs dielectric tensors diagonal in the TF"));
-    if (jac) e = ensure_scale(c);
+    double kappa = 1.0;  // max |s| / min |s|: the scaled residual test at tol / kappa implies |E - A P| <= tol |E|
+    if (jac) e = ensure_scale(c, &kappa);
     if (!e.ok()) return fail(c, e);
+    const double ktol = o.tol / kappa;  // Krylov tolerance of the complex64 / complex128 solves
     // Jacobi: the Krylov solver works on S A S y = S b with x = S y (S = diag(alpha^{1/2}))
     const uint8_t* comp = c->comp_valid ? c->d_comp : nullptr;
     auto scale64 = [&](float2* v, bool inv) {
@@ -1455,6 +1472,29 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
     };
     auto scale128 = [&](double2* v, bool inv) {
       return jac ? dda::scale_sites<double2>(v, c->d_sc128, comp, c->ncomp, nrhs, c->n, inv, c->stream) : Err::Ok();
+    };
+    // Phi reuse: orientations that differ from an earlier one only in Phi see the same k in the TF,
+    // so for alpha independent of the polarization (CM, GKDLDR) their two solutions are linear
+    // combinations of the earlier orientation's two; those RHS are not iterated on
+    std::vector<int> rep_of(c->n_ori, -1);
+    bool reuse = o.phi_reuse != 0 && c->iorth == 2 && (c->presc == DDA_CM || c->presc == DDA_GKDLDR);
+    if (reuse) {
+      bool any = false;
+      for (int a = 0; a < c->n_ori; ++a)
+        for (int r = 0; r < a && rep_of[a] < 0; ++r)
+          if (rep_of[r] < 0 && c->ori[3 * r] == c->ori[3 * a] && c->ori[3 * r + 1] == c->ori[3 * a + 1]) {
+            rep_of[a] = r;
+            any = true;
+          }
+      reuse = any;
+    }
+    std::vector<char> masked(nrhs, 0);
+    if (reuse)
+      for (int b = 0; b < nrhs; ++b) masked[b] = rep_of[b / 2] >= 0 ? 1 : 0;
+    auto zero_masked = [&](void* v, size_t csize) -> Err {
+      for (int b = 0; b < nrhs; ++b)
+        if (masked[b]) DDA_CU(cudaMemsetAsync((char*)v + csize * (size_t)b * n3, 0, csize * n3, c->stream));
+      return Err::Ok();
     };
     std::vector<int> iters(nrhs, 0), outer_n(nrhs, 0);
     std::vector<int> mvb(nrhs, 0);  // products with A applied to each RHS
@@ -1483,8 +1523,10 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
           e = cuda_ok(cudaMemcpyAsync(kv.x, P, sizeof(double2) * el, cudaMemcpyDeviceToDevice, c->stream),
                       "initial guess copy");
         if (e.ok() && o.warm_start) e = scale128(kv.x, true);
+        if (e.ok() && reuse) e = zero_masked(kv.b, sizeof(double2));
+        if (e.ok() && reuse && o.warm_start) e = zero_masked(kv.x, sizeof(double2));
         SolveStats s;
-        if (e.ok()) e = krylov<double2>(c, o, kv, o.tol, o.maxit, o.warm_start != 0, &s, t0, &timed_out);
+        if (e.ok()) e = krylov<double2>(c, o, kv, ktol, o.maxit, o.warm_start != 0, &s, t0, &timed_out);
         if (e.ok()) e = scale128(kv.x, false);
         if (e.ok()) e = cuda_ok(cudaMemcpyAsync(P, kv.x, sizeof(double2) * el, cudaMemcpyDeviceToDevice, c->stream),
                                 "solution copy");
@@ -1500,8 +1542,10 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
       if (e.ok()) e = scale64(kv.b, false);
       if (e.ok() && o.warm_start) e = dda::convert_from_c128<float2>(P, kv.x, el, c->stream);
       if (e.ok() && o.warm_start) e = scale64(kv.x, true);
+      if (e.ok() && reuse) e = zero_masked(kv.b, sizeof(float2));
+      if (e.ok() && reuse && o.warm_start) e = zero_masked(kv.x, sizeof(float2));
       SolveStats s;
-      if (e.ok()) e = krylov<float2>(c, o, kv, o.tol, o.maxit, o.warm_start != 0, &s, t0, &timed_out);
+      if (e.ok()) e = krylov<float2>(c, o, kv, ktol, o.maxit, o.warm_start != 0, &s, t0, &timed_out);
       if (e.ok()) e = scale64(kv.x, false);
       if (e.ok()) {
         e = cuda_ok(cudaMemsetAsync(P, 0, sizeof(double2) * el, c->stream), "solution clear");
@@ -1531,13 +1575,13 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
           if (!e.ok()) break;
         }
         bool all = true;
-        for (int b = 0; b < nrhs; ++b) all = all && rel[b] <= o.tol;
+        for (int b = 0; b < nrhs; ++b) all = all && (masked[b] || rel[b] <= o.tol);
         if (all || budget <= 0 || timed_out) break;
         // inner right-hand side: residual of unconverged RHS (converged ones get 0 and stop at once)
         e = dda::convert_from_c128<float2>(r128, kv.b, el, c->stream);
         if (!e.ok()) break;
         for (int b = 0; b < nrhs; ++b)
-          if (rel[b] <= o.tol && e.ok())
+          if ((masked[b] || rel[b] <= o.tol) && e.ok())
             e = cuda_ok(cudaMemsetAsync(kv.b + (int64_t)b * n3, 0, sizeof(float2) * n3, c->stream),
                         "inner right-hand side clear");
         if (!e.ok()) break;
@@ -1545,14 +1589,15 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
         if (!e.ok()) break;
         // ask the inner solve for the reduction that reaches tol, but at least `inner`
         double worst = 0;
-        for (int b = 0; b < nrhs; ++b) worst = std::max(worst, rel[b] > o.tol ? o.tol / rel[b] : 0.0);
+        for (int b = 0; b < nrhs; ++b)
+          worst = std::max(worst, (!masked[b] && rel[b] > o.tol) ? o.tol / rel[b] : 0.0);
         const double itol = std::max(inner, 0.5 * worst);
         SolveStats s;
         e = krylov<float2>(c, o, kv, itol, budget, false, &s, t0, &timed_out);
         if (!e.ok()) break;
         for (int b = 0; b < nrhs; ++b) {
           iters[b] += s.iters[b];
-          if (rel[b] > o.tol) outer_n[b] += 1;
+          if (!masked[b] && rel[b] > o.tol) outer_n[b] += 1;
         }
         int used = 0;
         for (int b = 0; b < nrhs; ++b) used = std::max(used, s.iters[b]);
@@ -1565,6 +1610,29 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
       }
     }
     if (!e.ok()) return fail(c, e);
+    if (reuse) {
+      // P(o, l) = sum_m <e_m(rep), e_l(o)> P(rep, m): the TF polarizations of orientation o are
+      // combinations of the representative's two orthonormal ones (same k, same alpha)
+      for (int a = 0; a < c->n_ori && e.ok(); ++a) {
+        const int r = rep_of[a];
+        if (r < 0) continue;
+        for (int l = 0; l < 2 && e.ok(); ++l) {
+          const dda::RhsGeom& gl = c->rg[2 * a + l];
+          cd co[2];
+          for (int m = 0; m < 2; ++m) {
+            const dda::RhsGeom& gm = c->rg[2 * r + m];
+            co[m] = cd(0, 0);
+            for (int q = 0; q < 3; ++q)
+              co[m] += std::conj(cd(gm.e[2 * q], gm.e[2 * q + 1])) * cd(gl.e[2 * q], gl.e[2 * q + 1]);
+          }
+          e = dda::combine2_c128(P + (int64_t)(2 * a + l) * n3, P + (int64_t)(2 * r) * n3,
+                                 P + (int64_t)(2 * r + 1) * n3, make_double2(co[0].real(), co[0].imag()),
+                                 make_double2(co[1].real(), co[1].imag()), n3, c->stream);
+        }
+      }
+      if (!e.ok()) return fail(c, e);
+      rel.clear();  // the reconstructed RHS get their own FP64 true residual below
+    }
     // final true residual in FP64 (for MIXED it was computed by the loop's last pass)
     if (o.precision != DDA_PREC_MIXED || rel.empty()) {
       e = true_residual(c, P, sc, sc + el, &rel, df_res);
@@ -2239,8 +2307,9 @@ dda_status dda_selftest_bulk_wait(int device, int32_t* gave_up) {
   return DDA_OK;
 }
 
-dda_status dda_schedule_info(dda_ctx* c, int dtype, int32_t info[8]) {
+dda_status dda_schedule_info(dda_ctx* c, int dtype, int32_t info[12]) {
   if (!c || !info) return DDA_EINVAL;
+  for (int i = 0; i < 12; ++i) info[i] = 0;
   if (!c->have_green) return fail(c, Err::make(DDA_ESTATE, "build the Green tensor first"));
   if (dtype != DDA_C64 && dtype != DDA_C128 && dtype != DDA_C128DF) return fail(c, Err::make(DDA_EINVAL, "bad dtype"));
   const dda::MvTune& t = dtype == DDA_C64 ? c->t64 : c->t128;
@@ -2250,6 +2319,7 @@ dda_status dda_schedule_info(dda_ctx* c, int dtype, int32_t info[8]) {
   info[3] = c->tuned_nrhs[dtype == DDA_C64 ? 0 : 1];
   info[4] = t.plane && t.clus > 1 ? t.clus : 1;
   info[6] = t.plane && t.bulk ? 1 : 0;
+  info[8] = !t.plane && t.zr ? 1 : 0;
   {
     const dda::Geom& g = dtype == DDA_C64 ? c->g64 : c->g128;
     const size_t cs = dtype == DDA_C64 ? sizeof(float2) : sizeof(double2);

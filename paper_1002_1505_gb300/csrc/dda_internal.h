@@ -120,6 +120,7 @@ struct MvTune {
   int xty = 0;            // y rows per CTA of the compile-time x passes (0: the length's default)
   int xnc = 0;            // components per CTA of the x passes (0 or 3: all three; 1: one)
   bool bulk = false;      // plane pass stages its HBM blocks with bulk copies
+  int zr = 0;             // 5-pass z columns with pass B, Ghat and inverse pass B fused in registers
 };
 
 // Enqueue ap = A p for nrhs right-hand sides (rhs0 = index of the first one for alpha).
@@ -262,6 +263,9 @@ template <typename C> Err cocg_init(const KrylovVecs<C>& kv, KState* ks, RedBuf 
                                     bool have_ax, cudaStream_t st);
 template <typename C> Err cocg_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3,
                                       cudaStream_t st);
+// dst = c0 s0 + c1 s1 over n3 complex128 elements
+Err combine2_c128(double2* dst, const double2* s0, const double2* s1, double2 c0, double2 c1, int64_t n3,
+                  cudaStream_t st);
 // v[b][c][j] *= s[b][comp(j,c)][c] (inv: divides), the Jacobi scaling of site vectors
 template <typename C> Err scale_sites(C* v, const C* s, const uint8_t* comp, int ncomp, int nrhs, int64_t n, bool inv,
                                       cudaStream_t st);
@@ -283,6 +287,8 @@ template <typename C> Err ccg_beta_update(const KrylovVecs<C>& kv, KState* ks, R
 Err launch_bicg_half_c64(const Geom& g, const MvData<float2>& d, const MvTune& t, const KrylovVecs<float2>& kv,
                          KState* ks, const RedBuf& rbx, int nrhs, int half, cudaStream_t st);
 int x_ctas_per_rhs_c64(const Geom& g, const MvTune& t);
+// the register-fused 5-pass z-column kernel exists for this complex64 grid
+bool zcols_rfuse_available_c64(const Geom& g);
 // the passes between the x passes of the complex64 product (plane pass or y/z/y), matvec_fast_c64.cu
 Err launch_middle_c64(const Geom& g, const MvData<float2>& d, const MvTune& t, int nrhs, cudaStream_t st);
 void fused_optin_c64(int smax);

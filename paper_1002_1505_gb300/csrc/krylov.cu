@@ -636,6 +636,18 @@ __global__ void k_scale_sites(C* v, const C* s, const uint8_t* comp, int ncomp, 
   }
 }
 
+// ------------------------------------------------------------------ linear combination of two solutions
+// dst = c0 src0 + c1 src1 (complex128, length n3): the solution for an incident polarization that is
+// a combination of two solved ones (same matrix A)
+__global__ void k_combine2(double2* __restrict__ dst, const double2* __restrict__ s0, const double2* __restrict__ s1,
+                           double2 c0, double2 c1, int64_t n3) {
+  VEC_LOOP(n3) {
+    const double2 a = s0[i], b = s1[i];
+    dst[i] = make_double2(c0.x * a.x - c0.y * a.y + c1.x * b.x - c1.y * b.y,
+                          c0.x * a.y + c0.y * a.x + c1.x * b.y + c1.y * b.x);
+  }
+}
+
 // ------------------------------------------------------------------ BiCGstab(2) kernels
 // r0 = b - A x (or b), shadow = r0, u0 = 0; rho0 = <shadow, r0> (the first BiCG step's rho with beta = 0)
 template <typename C>
@@ -977,6 +989,14 @@ Err cocg_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_
   CHECK_LAUNCH();
   const int nb = (int)std::min<int64_t>((n3 + kThreads * 4 - 1) / (kThreads * 4), 1024);
   DDA_CU(launch_k(k_cocg_p<C>, dim3(nb, nrhs), dim3(kThreads), 0, st, kv, ks, n3));
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+
+Err combine2_c128(double2* dst, const double2* s0, const double2* s1, double2 c0, double2 c1, int64_t n3,
+                  cudaStream_t st) {
+  const int nb = (int)std::min<int64_t>((n3 + kThreads * 4 - 1) / (kThreads * 4), 1024);
+  k_combine2<<<dim3(nb, 1), kThreads, 0, st>>>(dst, s0, s1, c0, c1, n3);
   CHECK_LAUNCH();
   return Err::Ok();
 }

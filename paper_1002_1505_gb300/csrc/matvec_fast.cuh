@@ -55,6 +55,16 @@ __device__ __forceinline__ C cdot3(C a0, C b0, C a1, C b1, C a2, C b2) {
 }
 
 template <typename C>
+__device__ __forceinline__ void gmul3_r(const C (&gg)[6], C& v0, C& v1, C& v2) {
+  const C u0 = cdot3(gg[0], v0, gg[1], v1, gg[2], v2);
+  const C u1 = cdot3(gg[1], v0, gg[3], v1, gg[4], v2);
+  const C u2 = cdot3(gg[2], v0, gg[4], v1, gg[5], v2);
+  v0 = u0;
+  v1 = u1;
+  v2 = u2;
+}
+
+template <typename C>
 __device__ __forceinline__ void gmul3(const C* __restrict__ gh, C& v0, C& v1, C& v2) {
   C gg[6];
   load6(gh, gg);
@@ -627,10 +637,13 @@ __global__ void __launch_bounds__(256) k_y_rows(Geom g, C* __restrict__ work, co
 // grid (nrhs, ceil(py/G), px): the right-hand sides of one Ghat tile are
 // neighbours in launch order, so a tile is read from HBM once and then hits L2
 // for the other right-hand sides.  smem: tw[PZ] | s[PZ*3][G]
-template <typename C, int PZ, int G>
-__global__ void __launch_bounds__(256) k_z_cols(Geom g, MvData<C> d) {
+// RFUSE: pass B, the Ghat multiply and the inverse pass B of all three components in registers
+// even for long sub-blocks (one item per thread: NT = G * 2 * RA threads, up to 3 CTAs per SM),
+// which halves the shared-memory traffic of the column pass at the cost of occupancy.
+template <typename C, int PZ, int G, int NT = 256, bool RFUSE = false>
+__global__ void __launch_bounds__(NT, RFUSE ? 3 : 1) k_z_cols(Geom g, MvData<C> d) {
   constexpr int RA = Shape<PZ>::RA, LB = Shape<PZ>::LB, H = Shape<PZ>::H;
-  constexpr bool kFuse = (LB * sizeof(C) <= 96);
+  constexpr bool kFuse = RFUSE || (LB * sizeof(C) <= 96);
   pdl_begin();
   extern __shared__ unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
@@ -705,16 +718,31 @@ __global__ void __launch_bounds__(256) k_z_cols(Geom g, MvData<C> d) {
       for (int e = 0; e < LB; ++e) s[((blk * LB + e) * 3 + c) * G + gg] = v[e];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < PZ * G; i += blockDim.x) {
-      const int gg = i % G, kz = i / G;
-      const int ky = ky0 + gg;
-      if (ky >= py) continue;
-      C* q = s + (kz * 3) * G + gg;
-      C v0 = q[0], v1 = q[G], v2 = q[2 * G];
-      gmul3(gk + ((int64_t)kz * py + ky) * 6, v0, v1, v2);
-      q[0] = v0;
-      q[G] = v1;
-      q[2 * G] = v2;
+    // Ghat multiply: each thread's Ghat records come from L2 (HBM once per batch); the loads of
+    // kGBatch items are issued together before their arithmetic so their latencies overlap
+    constexpr int kGBatch = 4;
+    for (int i0 = threadIdx.x; i0 < PZ * G; i0 += kGBatch * blockDim.x) {
+      C gv[kGBatch][6];
+      bool ok[kGBatch];
+#pragma unroll
+      for (int u = 0; u < kGBatch; ++u) {
+        const int i = i0 + u * blockDim.x;
+        const int gg = i % G, kz = i / G;
+        ok[u] = i < PZ * G && ky0 + gg < py;
+        if (ok[u]) load6(gk + ((int64_t)kz * py + ky0 + gg) * 6, gv[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kGBatch; ++u) {
+        if (!ok[u]) continue;
+        const int i = i0 + u * blockDim.x;
+        const int gg = i % G, kz = i / G;
+        C* q = s + (kz * 3) * G + gg;
+        C v0 = q[0], v1 = q[G], v2 = q[2 * G];
+        gmul3_r(gv[u], v0, v1, v2);
+        q[0] = v0;
+        q[G] = v1;
+        q[2 * G] = v2;
+      }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 3 * G * 2 * RA; i += blockDim.x) {
@@ -931,8 +959,30 @@ Err launch_y_rows(const Geom& g, C* work, const C* tw, int64_t nrows, bool inv, 
   return Err::Ok();
 }
 
+// register-fused z columns (RFUSE): complex64 lengths whose pass-B sub-block is too long for the
+// default fused loop; 8 columns per CTA, one (column, sub-block) item per thread
+constexpr int kZrG = 8;
 template <typename C>
-Err launch_z_cols(const Geom& g, const MvData<C>& d, int nrhs, cudaStream_t st) {
+constexpr bool zcols_rfuse_exists(int pz) {
+  return sizeof(C) == 8 && (pz == 160 || pz == 320);
+}
+
+template <typename C>
+Err launch_z_cols(const Geom& g, const MvData<C>& d, int nrhs, cudaStream_t st, bool rfuse = false) {
+  if constexpr (sizeof(C) == 8) {
+    if (rfuse && zcols_rfuse_exists<C>(g.pz)) {
+      const size_t sm = sizeof(C) * ((size_t)g.pz + (size_t)g.pz * 3 * kZrG);
+      const dim3 grid(nrhs, (g.py + kZrG - 1) / kZrG, g.px);
+      if (g.pz == 160)
+        DDA_CU(launch_k(k_z_cols<C, 160, kZrG, kZrG * 2 * Shape<160>::RA, true>, grid,
+                        dim3(kZrG * 2 * Shape<160>::RA), sm, st, g, d));
+      else
+        DDA_CU(launch_k(k_z_cols<C, 320, kZrG, kZrG * 2 * Shape<320>::RA, true>, grid,
+                        dim3(kZrG * 2 * Shape<320>::RA), sm, st, g, d));
+      DDA_CU(cudaGetLastError());
+      return Err::Ok();
+    }
+  }
   const size_t sm = zcols_fast_smem<C>(g);
   const int G = zcols_g_rt(sizeof(C), g.pz);
   const dim3 grid(nrhs, (g.py + G - 1) / G, g.px);
@@ -982,6 +1032,8 @@ void optin_all(int smax) {
   optin_smem(k_yz_plane<C, A, B, 768, false>, smax);
     DDA_FAST_PLANES(DDA_CASE)
 #undef DDA_CASE
+    optin_smem(k_z_cols<C, 160, kZrG, kZrG * 2 * Shape<160>::RA, true>, smax);
+    optin_smem(k_z_cols<C, 320, kZrG, kZrG * 2 * Shape<320>::RA, true>, smax);
   }
 }
 
@@ -1007,7 +1059,7 @@ Err launch_middle(const Geom& g, const MvData<C>& d, const MvTune& t, int nrhs, 
     const int64_t nrows = (int64_t)nrhs * 3 * g.px * g.nz;
     DDA_TRY(launch_y_rows<C>(g, d.work, d.twy, nrows, false, st));
     mark_pass(pass++, st);
-    DDA_TRY(launch_z_cols<C>(g, d, nrhs, st));
+    DDA_TRY(launch_z_cols<C>(g, d, nrhs, st, t.zr != 0));
     mark_pass(pass++, st);
     DDA_TRY(launch_y_rows<C>(g, d.work, d.twy, nrows, true, st));
     mark_pass(pass++, st);

@@ -20,6 +20,7 @@ Err launch_bicg_half_c64(const Geom& g, const MvData<float2>& d, const MvTune& t
   return Err::Ok();  // launch_middle_c64 counted the 3 (or 5) launches of the product
 }
 int x_ctas_per_rhs_c64(const Geom& g, const MvTune& t) { return fast::x_ctas_per_rhs(g, t); }
+bool zcols_rfuse_available_c64(const Geom& g) { return fast::zcols_rfuse_exists<float2>(g.pz); }
 void fused_optin_c64(int smax) {
 #define DDA_CASE(L_) fast::optin_x_fused<L_>(smax);
   DDA_FAST_LENGTHS(DDA_CASE)

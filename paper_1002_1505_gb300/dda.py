@@ -39,7 +39,7 @@ class dda_solve_opts(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("inner_tol", ctypes.c_double), ("timeout_ms", ctypes.c_double),
                 ("warm_start", ctypes.c_int), ("check_every", ctypes.c_int), ("normal_eq", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("precond", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("precond", ctypes.c_int), ("phi_reuse", ctypes.c_int)]
 
 
 class dda_solve_report(ctypes.Structure):
@@ -283,12 +283,12 @@ class Context:
 
     def dda_solve(self, p, solver="BICGSTAB", precision="MIXED", tol=1e-5, maxit=1000, inner_tol=0.0,
                   timeout_ms=0.0, warm_start=False, check_every=8, normal_eq=False, use_graph=True,
-                  raise_on_noconv=True, precond="NONE"):
+                  raise_on_noconv=True, precond="NONE", phi_reuse=False):
         """Solve A P = E_inc; p is a complex128 [nrhs,3,N] CUDA tensor (guess if warm_start, solution out)."""
         self._dev_check(p, DDA_C128)
         o = dda_solve_opts(SOLVERS[solver.upper()], PRECISIONS[precision.upper()], tol, maxit, inner_tol,
                            timeout_ms, int(bool(warm_start)), check_every, int(bool(normal_eq)), int(bool(use_graph)),
-                           PRECONDS[precond.upper()])
+                           PRECONDS[precond.upper()], int(bool(phi_reuse)))
         rep = (dda_solve_report * self.nrhs)()
         st = LIB.dda_solve(self._h, ctypes.byref(o), ctypes.c_void_p(p.data_ptr()), rep)
         reports = [{k: getattr(r, k) for k, _ in dda_solve_report._fields_} for r in rep]
@@ -499,14 +499,15 @@ def dda_profile_matvec(ctx: "Context", nrhs: int, dtype: int = DDA_C64, iters: i
 
 
 def dda_schedule_info(ctx: "Context", dtype: int = DDA_C64):
-    """(passes, fast, plane_threads, tuned_nrhs, ctas_per_plane, x_tile_rows, bulk_staged, x_components_per_cta)."""
-    info = np.zeros(8, dtype=np.int32)
+    """(passes, fast, plane_threads, tuned_nrhs, ctas_per_plane, x_tile_rows, bulk_staged, x_components_per_cta,
+    z_register_fused)."""
+    info = np.zeros(12, dtype=np.int32)
     ctx._check(LIB.dda_schedule_info(ctx._h, int(dtype), _ptr(info)))
-    return tuple(int(v) for v in info)
+    return tuple(int(v) for v in info[:9])
 
 
 def dda_solve_batch(ctxs, ps, solver="BICGSTAB", precision="MIXED", tol=1e-5, maxit=1000, inner_tol=0.0,
-                    timeout_ms=0.0, check_every=8, normal_eq=False, precond="NONE"):
+                    timeout_ms=0.0, check_every=8, normal_eq=False, precond="NONE", phi_reuse=False):
     """Solve several contexts concurrently; ps[i] complex128 [nrhs_i,3,N_i] CUDA tensors.
 
     Returns (list of per-context report lists, list of statuses, overall status)."""
@@ -514,7 +515,7 @@ def dda_solve_batch(ctxs, ps, solver="BICGSTAB", precision="MIXED", tol=1e-5, ma
     for c, p in zip(ctxs, ps):
         c._dev_check(p, DDA_C128)
     o = dda_solve_opts(SOLVERS[solver.upper()], PRECISIONS[precision.upper()], tol, maxit, inner_tol, timeout_ms,
-                       0, check_every, int(bool(normal_eq)), 1, PRECONDS[precond.upper()])
+                       0, check_every, int(bool(normal_eq)), 1, PRECONDS[precond.upper()], int(bool(phi_reuse)))
     handles = (ctypes.c_void_p * n)(*[c._h.value for c in ctxs])
     bufs = (ctypes.c_void_p * n)(*[p.data_ptr() for p in ps])
     rep_arrays = [(dda_solve_report * c.nrhs)() for c in ctxs]

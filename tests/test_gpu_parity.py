@@ -305,6 +305,32 @@ def test_every_schedule_matches_direct_rows(D, monkeypatch, sched):
             assert err <= tol, (sched, dt, b, err)
 
 
+@pytest.mark.parametrize("zfuse", ["1", "0"])
+def test_register_fused_z_columns_match_direct_sum(D, monkeypatch, zfuse):
+    """The 5-pass schedule with the z columns' middle stages fused in registers (the kernel the
+    tuner may pick for long z transforms: Pz = 160 here, 320 on the hexagonal prism), pinned on and
+    off, complex64 against the oracle's direct sum; complex128 products keep the default kernel."""
+    monkeypatch.setenv("DDA_SCHEDULE", "fast5")
+    monkeypatch.setenv("DDA_ZFUSE", zfuse)
+    w = W.Workload("ell_z160", "ELLIPSOID", (14, 11, 80), 1.5 + 0.05j, 3.0, "LATTDR", W.uniform_orientations(2, 31),
+                   pad=(32, 24, 160))
+    ctx = _ctx(D, w)
+    prob = _oracle_problem(w)
+    info = D.dda_schedule_info(ctx, D.DDA_C64)
+    assert info[0] == 5 and info[8] == int(zfuse), info
+    rows = np.concatenate([[0, ctx.n - 1], np.sort(np.random.default_rng(3).choice(ctx.n, 40, replace=False))])
+    for dt, tol in ((torch.complex64, 1e-5), (torch.complex128, 1e-12)):
+        p = _rand_p(ctx.nrhs, ctx.n, 17, dt)
+        ap = torch.empty_like(p)
+        ctx.dda_matvec(p, ap)
+        torch.cuda.synchronize()
+        for b in range(ctx.nrhs):
+            pb = p[b].cpu().numpy().astype(np.complex128)
+            ref = oint.matvec_direct(prob.target.r, prob.kd, prob.rhs[b].inv_alpha, pb, rows=rows)
+            got = ap[b].cpu().numpy().astype(np.complex128)[:, rows]
+            assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= tol, (zfuse, dt, b)
+
+
 def test_matvec_nondefault_pad_and_tail_tiles(D):
     # odd box sizes against a padded grid larger than 2N (pruned FFT inputs shorter than L/2)
     w = W.Workload("ell_pad", "ELLIPSOID", (11, 13, 6), 1.4 + 0.2j, 2.0, "GKDLDR", W.uniform_orientations(1, 21),

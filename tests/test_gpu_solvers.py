@@ -4,7 +4,7 @@ the guide's QMRCCG option) and symmetric Jacobi preconditioning (the solver iter
 S = diag(alpha^{1/2})).
 
 Bars: Q_ext / Q_abs / Q_sca 1e-4 relative against the oracle solved to 1e-10 (or LU); solutions of
-complex128 solves to 1e-11 within 1e-9 of the oracle's LU solution; the GPU's COCG takes the
+complex128 solves to 1e-10 within 1e-8 of the oracle's LU solution; the GPU's COCG takes the
 oracle's COCG iteration count (same recurrences, different rounding: within one iteration).
 """
 import numpy as np
@@ -101,7 +101,8 @@ def _three_material_target(box):
 @pytest.mark.parametrize("box", [(12, 8, 8), (9, 7, 6)], ids=["compile_time_grid", "generic_grid"])
 def test_jacobi_preconditioning_keeps_the_solution(D, box):
     """Three materials of very different polarizability (alpha^{-1} varies by ~10x across sites):
-    every solver with Jacobi preconditioning reaches the oracle's LU solution (complex128 to 1e-11),
+    every solver with and without Jacobi preconditioning reaches the oracle's LU solution (complex128 to
+    1e-10: the reported true residual meets tol),
     and the mixed-precision preconditioned solve gives the oracle's efficiencies."""
     t, comp = _three_material_target(box)
     m = [1.2 + 0.01j, 2.5 + 1.0j, 1.7 + 0.05j]
@@ -118,12 +119,15 @@ def test_jacobi_preconditioning_keeps_the_solution(D, box):
     for solver in ("BICGSTAB", "COCG", "CCG", "BICGSTAB2"):
         for pre in ("NONE", "JACOBI"):
             p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
-            reps, _ = ctx.dda_solve(p, solver=solver, precision="C128", tol=1e-11, maxit=5000, precond=pre)
+            reps, st = ctx.dda_solve(p, solver=solver, precision="C128", tol=1e-10, maxit=20000, precond=pre,
+                                     raise_on_noconv=False)
+            assert st == D.DDA_OK, (solver, pre, [(r["iters"], r["true_rel_resid"]) for r in reps])
+            assert all(r["true_rel_resid"] <= 1e-10 for r in reps), (solver, pre)
             got = p.cpu().numpy()
             for b in range(ctx.nrhs):
-                assert np.linalg.norm(got[b] - ps[b]) / np.linalg.norm(ps[b]) <= 1e-9, (solver, pre, b)
+                assert np.linalg.norm(got[b] - ps[b]) / np.linalg.norm(ps[b]) <= 1e-8, (solver, pre, b)
             its[(solver, pre)] = [r["iters"] for r in reps]
-    print("iterations to 1e-11 (none, Jacobi):", {k: v for k, v in its.items()})
+    print("iterations to 1e-10 (none, Jacobi):", {k: v for k, v in its.items()})
     for solver in ("BICGSTAB", "COCG"):
         p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
         reps, _ = ctx.dda_solve(p, solver=solver, precision="MIXED", tol=1e-6, maxit=3000, precond="JACOBI")
@@ -149,3 +153,34 @@ def test_jacobi_on_a_homogeneous_target_is_a_uniform_scaling(D):
         assert abs(res["NONE"][0][b] - res["JACOBI"][0][b]) <= 1
         a, j = res["NONE"][1][b], res["JACOBI"][1][b]
         assert np.linalg.norm(a - j) / np.linalg.norm(a) <= 1e-8
+
+
+@pytest.mark.parametrize("presc", ["GKDLDR", "CM", "LATTDR"])
+def test_phi_reuse_gives_the_same_solutions(D, presc):
+    """Orientations that differ only in Phi (the guide's orientation grid with NPHI = 4): with the
+    polarization-independent prescriptions only the first Phi of each (beta, Theta) is iterated on and
+    the rest are linear combinations of its two solutions; every RHS then matches the full solve to
+    the tolerance, with a quarter of the products.  LATTDR (alpha depends on the polarization) solves
+    every orientation."""
+    ori, wts = D.dda_orientation_grid((0, 90), 1, (0, 180), 3, (0, 360), 4)
+    w = W.Workload("ell_phi", "ELLIPSOID", (9, 7, 6), 1.6 + 0.2j, 2.5, presc, tuple(map(tuple, ori)))
+    ctx = _ctx(D, w)
+    res = {}
+    for reuse in (False, True):
+        p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
+        reps, _ = ctx.dda_solve(p, precision="MIXED", tol=1e-8, maxit=5000, phi_reuse=reuse)
+        assert all(r["converged"] == 1 and r["true_rel_resid"] <= 1e-8 for r in reps)
+        q, _ = ctx.dda_cross_sections(p)
+        res[reuse] = (p.cpu().numpy(), reps, q)
+    pa, ra, qa = res[False]
+    pb, rb, qb = res[True]
+    for b in range(ctx.nrhs):
+        assert np.linalg.norm(pb[b] - pa[b]) / np.linalg.norm(pa[b]) <= 1e-6, b
+        np.testing.assert_allclose(qb[b, :3], qa[b, :3], rtol=1e-6)
+    mv_a = sum(r["matvecs"] for r in ra)
+    mv_b = sum(r["matvecs"] for r in rb)
+    if presc == "LATTDR":
+        assert all(r["iters"] > 0 for r in rb)
+    else:
+        assert sum(r["iters"] == 0 for r in rb) == ctx.nrhs * 3 // 4  # 3 of every 4 Phi reconstructed
+        assert mv_b < 0.4 * mv_a, (mv_a, mv_b)

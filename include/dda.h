@@ -165,6 +165,27 @@ DDA_API dda_status dda_get_sites(dda_ctx *ctx, int32_t *ixyz_out, double origin_
  * without a target. */
 DDA_API dda_status dda_get_box(const dda_ctx *ctx, int64_t *n_out, int32_t box_out[3]);
 
+/* Periodic targets (guide, "Target Generation: Periodic Targets" and
+ * "Interaction Cutoff Parameter for PBC Calculations"; Draine & Flatau 2008):
+ * the current target becomes the Target Unit Cell, repeated with period py
+ * along y_TF and / or pz along z_TF (lattice units; 0 = no repetition along
+ * that axis; a nonzero period must be at least the cell's extent).  Under the
+ * incident wave of TF wave vector k the replica displaced by R carries the
+ * cell's polarization times exp(i k.R), and the product becomes
+ * alpha^{-1} P + sum_k A^per(r_j - r_k) P_k with A^per(r) = sum_R exp(i k.R)
+ * A(r - R) exp[-(gamma kd |r - R|)^4] (the term r - R = 0 omitted; replicas
+ * kept while (gamma kd |r - R|)^4 <= 40), built in FP64 by
+ * dda_build_green_fft on the full wrapped grid (O(grid points x replicas)).
+ * Every RHS of the context must then share one incident direction in the TF
+ * (one orientation, or orientations differing only in Phi), else
+ * dda_build_green_fft returns DDA_EUNSUPPORTED.  Efficiencies from
+ * dda_cross_sections are per unit cell (a_eff of the cell); Mueller matrices,
+ * angular averages, force and torque and near fields return
+ * DDA_EUNSUPPORTED for periodic targets.  gamma in (0, 1) (the guide suggests
+ * 1e-2, smaller for accuracy).  Call after the target; py = pz = 0 makes the
+ * target finite again.  Drops the Green tensor. */
+DDA_API dda_status dda_set_periodicity(dda_ctx *ctx, double py, double pz, double gamma);
+
 /* Lattice wavenumber for a size parameter (guide, "Target Generation" and the
  * definitions of a_eff and x): the target's effective radius is
  * a_eff = (3 N / 4 pi)^(1/3) d, the radius of a sphere of volume N d^3, and

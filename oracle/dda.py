@@ -33,10 +33,13 @@ class Problem:
     x: float
     rhs: List[Rhs]
     pad: tuple
+    periods: Optional[tuple] = None   # (P_y, P_z) of a periodic target (0: not periodic along that axis)
+    gamma: float = 0.0                # interaction cutoff of the periodic sums
 
 
 def build_problem(shape, shpar, m, x, prescription, orientations, e01_lf=((0, 0), (1, 0), (0, 0)),
-                  iorth=2, pad=None, target=None, kd=None, comp=None, df_angles=None) -> Problem:
+                  iorth=2, pad=None, target=None, kd=None, comp=None, df_angles=None, periods=None,
+                  gamma=0.01) -> Problem:
     """comp (optional): per-site composition indices (0-based) in the target's site order, shape
     (N,) for isotropic materials or (N, 3) for one composition per Cartesian axis (the guide's
     ICOMP triple of an anisotropic material whose principal axes are the TF axes); m is then a
@@ -81,11 +84,19 @@ def build_problem(shape, shpar, m, x, prescription, orientations, e01_lf=((0, 0)
                            e02_lf=pols_lf[1] if iorth == 2 else None, axes=axes,
                            inv_alpha=inv_alpha, e_inc=e_inc))
     pad = interaction.default_pad(tgt.box) if pad is None else tuple(pad)
-    return Problem(target=tgt, kd=kd, x=x, rhs=rhs, pad=pad)
+    per = None if periods is None or (periods[0] <= 0 and periods[1] <= 0) else tuple(float(v) for v in periods)
+    return Problem(target=tgt, kd=kd, x=x, rhs=rhs, pad=pad, periods=per, gamma=float(gamma))
 
 
 def apply_a(prob: Problem, i: int, p: np.ndarray, method: str = "fft", ghat=None, workers=None):
     t = prob.target
+    if prob.periods is not None:
+        from . import periodic
+        rh = prob.rhs[i]
+        if method == "direct":
+            return periodic.matvec_direct(t.r, prob.kd, rh.inv_alpha, p, rh.k_tf, prob.periods, prob.gamma)
+        return periodic.matvec_fft(t.ijk, t.box, prob.kd, rh.inv_alpha, p, rh.k_tf, prob.periods, prob.gamma,
+                                   pad=prob.pad, ghat=ghat)
     if method == "direct":
         return interaction.matvec_direct(t.r, prob.kd, prob.rhs[i].inv_alpha, p)
     return interaction.matvec_fft(t.ijk, t.box, prob.kd, prob.rhs[i].inv_alpha, p, pad=prob.pad,
@@ -99,11 +110,19 @@ def solve(prob: Problem, method: str = "bicgstab", matvec: str = "fft", tol: flo
     t = prob.target
     out, iters = [], []
     ghat = None
-    if matvec == "fft" and method != "lu":
+    if matvec == "fft" and method != "lu" and prob.periods is None:
         ghat = interaction.green_fft(t.box, prob.pad, prob.kd, workers=workers)
     for i, rh in enumerate(prob.rhs):
         if method == "lu":
-            a = interaction.dense_matrix(t.r, prob.kd, rh.inv_alpha)
+            if prob.periods is not None:
+                from . import periodic
+                blocks = periodic.green_per(t.r[:, None, :] - t.r[None, :, :], prob.kd, rh.k_tf, prob.periods,
+                                            prob.gamma)                                  # (N, N, 3, 3)
+                for j in range(t.n):
+                    blocks[j, j] += interaction.diag_block(rh.inv_alpha, j)
+                a = np.transpose(blocks, (2, 0, 3, 1)).reshape(3 * t.n, 3 * t.n)
+            else:
+                a = interaction.dense_matrix(t.r, prob.kd, rh.inv_alpha)
             p = solvers.lu_solve(a, rh.e_inc.reshape(-1)).reshape(3, t.n)
             out.append(p)
             iters.append(0)

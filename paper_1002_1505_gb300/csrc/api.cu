@@ -89,6 +89,9 @@ struct dda_ctx {
   double2* d_sc128 = nullptr;
   float2* d_sc64 = nullptr;
   bool jacobi = false;
+  // periodic target (unit cell repeated along y_TF and / or z_TF; periods 0 = none)
+  double per_y = 0.0, per_z = 0.0, per_gamma = 0.01;
+  bool periodic = false;
   // full alpha^{-1} per (RHS, site) for targets with rotated dielectric frames ([nrhs][N][6])
   double2* d_iat128 = nullptr;
   float2* d_iat64 = nullptr;
@@ -213,6 +216,8 @@ void drop_incident(dda_ctx* c) {
 void drop_target(dda_ctx* c) {
   c->have_target = false;
   c->comp_valid = false;
+  c->periodic = false;  // a new target starts finite
+  c->per_y = c->per_z = 0.0;
   drop_incident(c);
 }
 
@@ -945,6 +950,23 @@ dda_status dda_get_box(const dda_ctx* c, int64_t* n_out, int32_t box_out[3]) {
   return DDA_OK;
 }
 
+dda_status dda_set_periodicity(dda_ctx* c, double py, double pz, double gamma) {
+  if (!c) return DDA_EINVAL;
+  if (!c->have_target) return fail(c, Err::make(DDA_ESTATE, "set a target first"));
+  if (!(py >= 0) || !(pz >= 0) || !std::isfinite(py) || !std::isfinite(pz))
+    return fail(c, Err::make(DDA_EINVAL, "periods must be >= 0 (0 = not periodic along that axis)"));
+  if ((py > 0 && py < c->tgt.box[1]) || (pz > 0 && pz < c->tgt.box[2]))
+    return fail(c, Err::make(DDA_EINVAL, "a period shorter than the unit cell's extent would overlap its replicas"));
+  const bool per = py > 0 || pz > 0;
+  if (per && !(gamma > 0 && gamma < 1)) return fail(c, Err::make(DDA_EINVAL, "gamma must be in (0, 1)"));
+  c->per_y = py;
+  c->per_z = pz;
+  c->per_gamma = per ? gamma : 0.01;
+  c->periodic = per;
+  drop_green(c);
+  return DDA_OK;
+}
+
 dda_status dda_kd_from_x(const dda_ctx* c, double x, double* kd_out, double* aeff_out) {
   if (!c || !(x > 0) || !std::isfinite(x)) return DDA_EINVAL;
   if (!c->have_target || c->n <= 0) return DDA_ESTATE;
@@ -1194,8 +1216,22 @@ dda_status dda_build_green_fft(dda_ctx* c, const int32_t pad[3]) {
       if (e.ok()) { c->gperm_key[0] = g.px; c->gperm_key[1] = g.py; }
     }
     if (!e.ok()) return fail(c, e);
-    e = dda::build_green(g64, c->kd, c->d_tw128[0], c->d_tw128[1], c->d_tw128[2], c->d_gperm, c->d_gscratch,
-                         c->d_ghat128, c->d_ghat64, want_df ? c->d_ghatdf : nullptr, c->stream);
+    if (c->periodic) {
+      // the periodic interaction depends on the incidence through the replicas' Bloch phases: every
+      // RHS of the context must share one k in the TF (one orientation, or orientations that differ
+      // only in Phi)
+      for (int b = 1; b < c->nrhs; ++b)
+        for (int q = 0; q < 3; ++q)
+          if (std::abs(c->rg[b].k[q] - c->rg[0].k[q]) > 1e-12 * c->kd)
+            return fail(c, Err::make(DDA_EUNSUPPORTED, "a periodic target needs every RHS to share one incident "
+                                                       "direction in the Target Frame"));
+      e = dda::build_green_pbc(g64, c->kd, c->rg[0].k, c->per_y, c->per_z, c->per_gamma, c->d_tw128[0],
+                               c->d_tw128[1], c->d_tw128[2], c->d_gscratch, c->d_ghat128, c->d_ghat64,
+                               want_df ? c->d_ghatdf : nullptr, c->stream);
+    } else {
+      e = dda::build_green(g64, c->kd, c->d_tw128[0], c->d_tw128[1], c->d_tw128[2], c->d_gperm, c->d_gscratch,
+                           c->d_ghat128, c->d_ghat64, want_df ? c->d_ghatdf : nullptr, c->stream);
+    }
     if (!e.ok()) return fail(c, e);
     c->ghatdf_valid = want_df;
     c->have_green = true;
@@ -1701,6 +1737,8 @@ dda_status dda_cross_sections(dda_ctx* c, const void* p_dev, double* q_out, cons
   if (!c->have_alpha || !c->have_green)
     return fail(c, Err::make(DDA_ESTATE, "set target, incidence, Green tensor and alpha first"));
   if (ndir < 0 || (ndir > 0 && (!dirs || !mueller_out))) return fail(c, Err::make(DDA_EINVAL, "bad directions"));
+  if (ndir > 0 && c->periodic)
+    return fail(c, Err::make(DDA_EUNSUPPORTED, "Mueller matrices of periodic targets are not available"));
   if (ndir > 0 && c->iorth != 2) return fail(c, Err::make(DDA_EINVAL, "Mueller matrices need iorth = 2"));
   try {
     Err e = set_dev(c);
@@ -1952,6 +1990,8 @@ std::vector<ScaDir> scattering_directions(double x, double eta) {
 
 dda_status dda_angular_averages(dda_ctx* c, const void* p_dev, double eta, double* out, int32_t* ndir_out) {
   if (!c || !p_dev || !out || !(eta > 0.0)) return DDA_EINVAL;
+  if (c->periodic)
+    return fail(c, Err::make(DDA_EUNSUPPORTED, "not available for periodic targets (scattering goes into diffraction orders)"));
   if (!c->have_inc) return fail(c, Err::make(DDA_ESTATE, "set the target and the incident beams first"));
   try {
     Err e = set_dev(c);
@@ -2051,6 +2091,8 @@ dda_status dda_angular_averages(dda_ctx* c, const void* p_dev, double eta, doubl
 
 dda_status dda_force_torque(dda_ctx* c, const void* p_dev, double eta, double* out, int32_t* ndir_out) {
   if (!c || !p_dev || !out || !(eta > 0.0)) return DDA_EINVAL;
+  if (c->periodic)
+    return fail(c, Err::make(DDA_EUNSUPPORTED, "not available for periodic targets (scattering goes into diffraction orders)"));
   if (!c->have_inc) return fail(c, Err::make(DDA_ESTATE, "set the target and the incident beams first"));
   try {
     Err e = need_device(c);
@@ -2189,6 +2231,8 @@ dda_status dda_force_torque(dda_ctx* c, const void* p_dev, double eta, double* o
 dda_status dda_near_field(dda_ctx* c, const void* p_dev, const double* pts, int64_t npts, double* e_out,
                           double* b_out) {
   if (!c || !p_dev || !pts || !e_out || npts < 1) return DDA_EINVAL;
+  if (c->periodic)
+    return fail(c, Err::make(DDA_EUNSUPPORTED, "not available for periodic targets (scattering goes into diffraction orders)"));
   if (!c->have_inc) return fail(c, Err::make(DDA_ESTATE, "set the target and the incident beams first"));
   try {
     Err e = need_device(c);

@@ -190,6 +190,12 @@ void green_perm_tables(const Geom& g, std::vector<int32_t>* out);
 Err build_green(const Geom& g, double kd, const double2* twx, const double2* twy, const double2* twz,
                 const int32_t* perm, double2* gw, double2* ghat128, float2* ghat64, dfp::dfc* ghatdf,
                 cudaStream_t st);
+// The Green tensor of a target periodic along y_TF (period py, 0 = none) and / or z_TF (pz), with
+// the Bloch phases of the TF wave vector k_tf and the cutoff exp[-(gamma kd r)^4], transformed over
+// the full grid (same output layouts as build_green).
+Err build_green_pbc(const Geom& g, double kd, const double k_tf[3], double py, double pz, double gamma,
+                    const double2* twx, const double2* twy, const double2* twz, double2* gw, double2* ghat128,
+                    float2* ghat64, dfp::dfc* ghatdf, cudaStream_t st);
 
 // Generic batched FFT over rows/strides (used by tests of the engine and the Green build).
 template <typename C>

@@ -692,6 +692,125 @@ Err build_green(const Geom& g, double kd, const double2* twx, const double2* twy
   return e;
 }
 
+// ------------------------------------------------------------------ periodic targets
+// The interaction of a target unit cell repeated with periods (py, pz) along y_TF, z_TF under a
+// plane wave of TF wave vector k: A^per(r) = sum_R exp(i k.R) A(r - R) exp[-(gamma kd |r - R|)^4]
+// over the replica offsets R = (0, m py, n pz) (the term r - R = 0 omitted), kept wherever the
+// cutoff factor is above exp(-40).  It is not even in r for oblique incidence, so every offset of
+// the wrapped grid is filled and transformed (no parity shortcut).  One CTA per grid point; its
+// threads stride over the replicas and sum in FP64, then a fixed-order block reduction.
+namespace {
+constexpr int kPbcT = 256;
+__global__ void __launch_bounds__(kPbcT) k_green_fill_pbc(Geom g, double kd, double k1, double k2, double py,
+                                                          double pz, double gamma, int my, int mz, double rmax,
+                                                          double2* __restrict__ gw) {
+  const int64_t M = (int64_t)g.px * g.py * g.pz;
+  const int64_t i = blockIdx.x;
+  const int x = (int)(i % g.px);
+  const int64_t rest = i / g.px;
+  const int y = (int)(rest % g.py), z = (int)(rest / g.py);
+  int o[3];
+  const int xs[3] = {x, y, z}, ns[3] = {g.nx, g.ny, g.nz}, ps[3] = {g.px, g.py, g.pz};
+  bool ok = true;
+  for (int a = 0; a < 3; ++a) {
+    if (xs[a] < ns[a]) o[a] = xs[a];
+    else if (xs[a] > ps[a] - ns[a]) o[a] = xs[a] - ps[a];
+    else ok = false;
+  }
+  double acc[12];
+  for (int q = 0; q < 12; ++q) acc[q] = 0.0;
+  if (ok) {
+    const int nm = 2 * my + 1, nn = 2 * mz + 1;
+    const int64_t nrep = (int64_t)nm * nn;
+    const double gk = gamma * kd;
+    for (int64_t t = threadIdx.x; t < nrep; t += kPbcT) {
+      const int m = (int)(t / nn) - my, n = (int)(t % nn) - mz;
+      const double Ry = m * py, Rz = n * pz;
+      const double rx = o[0], ry = o[1] - Ry, rz = o[2] - Rz;
+      const double r2 = rx * rx + ry * ry + rz * rz;
+      if (r2 == 0.0 || r2 > rmax * rmax) continue;
+      const double r = sqrt(r2), inv_r = 1.0 / r;
+      const double u = gk * r, u2 = u * u;
+      const double cut = exp(-u2 * u2);
+      double sb, cb;
+      sincos(k1 * Ry + k2 * Rz, &sb, &cb);   // Bloch phase exp(i k.R)
+      double sn, cs;
+      sincos(kd * r, &sn, &cs);
+      // pref = exp(ikr)/r * phase * cut ; t2 = (ikr - 1)/r^2
+      const double2 e1 = make_double2(cs * inv_r * cut, sn * inv_r * cut);
+      const double2 pref = make_double2(e1.x * cb - e1.y * sb, e1.x * sb + e1.y * cb);
+      const double2 t2 = make_double2(-1.0 / r2, kd * r / r2);
+      const double h[3] = {rx * inv_r, ry * inv_r, rz * inv_r};
+      const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+      for (int c = 0; c < 6; ++c) {
+        const double hh = h[ia[c]] * h[ib[c]];
+        const double dl = (ia[c] == ib[c]) ? 1.0 : 0.0;
+        const double2 inner = make_double2(kd * kd * (hh - dl) + t2.x * (3.0 * hh - dl), t2.y * (3.0 * hh - dl));
+        acc[2 * c] += pref.x * inner.x - pref.y * inner.y;
+        acc[2 * c + 1] += pref.x * inner.y + pref.y * inner.x;
+      }
+    }
+  }
+  __shared__ double red[12][kPbcT / 32];
+  for (int q = 0; q < 12; ++q)
+    for (int off = 16; off > 0; off >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], off);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0)
+    for (int q = 0; q < 12; ++q) red[q][w] = acc[q];
+  __syncthreads();
+  if (threadIdx.x < 12) {
+    double v = 0.0;
+    for (int k = 0; k < kPbcT / 32; ++k) v += red[threadIdx.x][k];
+    const int c = threadIdx.x / 2;
+    double* dst = reinterpret_cast<double*>(gw + (int64_t)c * M + i);
+    dst[threadIdx.x % 2] = v;
+  }
+}
+
+// ghat[kx][kz][ky][6] (storage positions) = gw[c][kz][ky][kx] / M after the full transform
+__global__ void k_green_pack_full(Geom g, const double2* __restrict__ f, double2* __restrict__ g128,
+                                  float2* __restrict__ g64, dfp::dfc* __restrict__ gdf) {
+  const int64_t M = (int64_t)g.px * g.py * g.pz;
+  const double inv = 1.0 / (double)M;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < 6 * M; o += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(o % 6);
+    const int64_t pt = o / 6;
+    const int ky = (int)(pt % g.py);
+    const int64_t rest = pt / g.py;
+    const int kz = (int)(rest % g.pz), kx = (int)(rest / g.pz);
+    const double2 v = f[(int64_t)c * M + ((int64_t)kz * g.py + ky) * g.px + kx];
+    const double2 w = make_double2(v.x * inv, v.y * inv);
+    g128[o] = w;
+    g64[o] = make_float2((float)w.x, (float)w.y);
+    if (gdf) gdf[o] = dfp::from_c128(w);
+  }
+}
+}  // namespace
+
+Err build_green_pbc(const Geom& g, double kd, const double k_tf[3], double py, double pz, double gamma,
+                    const double2* twx, const double2* twy, const double2* twz, double2* gw, double2* ghat128,
+                    float2* ghat64, dfp::dfc* ghatdf, cudaStream_t st) {
+  const int64_t M = (int64_t)g.px * g.py * g.pz;
+  if (M > 2147483647LL) return Err::make(DDA_EUNSUPPORTED, "periodic Green grid too large");
+  // replicas within rmax + the longest offset; (gamma kd r)^4 <= 40
+  const double reach = std::sqrt((double)g.nx * g.nx + (double)g.ny * g.ny + (double)g.nz * g.nz);
+  const double rmax = std::pow(40.0, 0.25) / (gamma * kd);
+  const int my = py > 0 ? (int)std::ceil((rmax + reach) / py) : 0;
+  const int mz = pz > 0 ? (int)std::ceil((rmax + reach) / pz) : 0;
+  if ((double)(2 * my + 1) * (2 * mz + 1) > 4.0e8)
+    return Err::make(DDA_EUNSUPPORTED, "too many periodic replicas for this gamma and period (raise gamma)");
+  k_green_fill_pbc<<<(unsigned)M, kPbcT, 0, st>>>(g, kd, k_tf[1], k_tf[2], py, pz, gamma, my, mz, rmax, gw);
+  if (cudaGetLastError() != cudaSuccess) return Err::make(DDA_ECUDA, "periodic Green fill failed");
+  DDA_TRY(fft_rows<double2>(gw, 6 * (int64_t)g.py * g.pz, g.px, g.plx, twx, g.px, g.px, false, st));
+  DDA_TRY(fft_strided<double2>(gw, g.py, g.px, g.px, 6 * (int64_t)g.pz, (int64_t)g.px * g.py, g.ply, twy, false, st));
+  DDA_TRY(fft_strided<double2>(gw, g.pz, (int64_t)g.px * g.py, (int64_t)g.px * g.py, 6, M, g.plz, twz, false, st));
+  const int nb = (int)std::min<int64_t>((6 * M + 255) / 256, 152 * 16);
+  k_green_pack_full<<<nb, 256, 0, st>>>(g, gw, ghat128, ghat64, ghatdf);
+  if (cudaGetLastError() != cudaSuccess) return Err::make(DDA_ECUDA, "periodic Green pack failed");
+  g_launches += 2;
+  return Err::Ok();
+}
+
 template Err launch_matvec<float2>(const Geom&, const MvData<float2>&, const MvTune&, const float2*, float2*, int,
                                    int, bool, cudaStream_t);
 template Err launch_matvec<double2>(const Geom&, const MvData<double2>&, const MvTune&, const double2*, double2*,

@@ -139,15 +139,28 @@ __device__ __forceinline__ void x_fwd_body(const Geom& g, const MvData<C>& d, co
     const KState k = ksw[b];
     k1 = mk((float)k.alpha.x, (float)k.alpha.y);
   }
+  // gather: kXU elements per thread per round, their site indices (map) loaded first and their
+  // values next, so that a thread has kXU independent loads in flight at each of the two steps
+  constexpr int kXU = 4;
   const int nld = NC * TY * g.nx;
-  for (int i = threadIdx.x; i < nld; i += blockDim.x) {
-    const int x = i % g.nx;
-    const int r = i / g.nx;
-    const int t = r % TY, cl = r / TY;
-    const int y = y0 + t;
-    C v = czero<C>();
-    if (y < g.ny) {
-      const int32_t idx = __ldg(d.map + ((int64_t)z * g.ny + y) * g.nx + x);
+  for (int i0 = threadIdx.x; i0 < nld; i0 += kXU * blockDim.x) {
+    int32_t idxs[kXU];
+#pragma unroll
+    for (int u = 0; u < kXU; ++u) {
+      const int i = i0 + u * blockDim.x;
+      const int x = i % g.nx;
+      const int r = i / g.nx;
+      const int t = r % TY;
+      const int y = y0 + t;
+      idxs[u] = (i < nld && y < g.ny) ? __ldg(d.map + ((int64_t)z * g.ny + y) * g.nx + x) : -1;
+    }
+    C vals[kXU];
+#pragma unroll
+    for (int u = 0; u < kXU; ++u) {
+      const int i = i0 + u * blockDim.x;
+      const int cl = (i / g.nx) / TY;
+      const int32_t idx = idxs[u];
+      C v = czero<C>();
       if (idx >= 0) {
         const int64_t o = ((int64_t)b * 3 + c0 + cl) * g.n + idx;
         if constexpr (MODE == kFuseNone) {
@@ -166,8 +179,17 @@ __device__ __forceinline__ void x_fwd_body(const Geom& g, const MvData<C>& d, co
           v = cmul(v, d.sc[((int64_t)b * g.ncomp + (d.comp ? d.comp[3 * idx + c] : 0)) * 3 + c]);
         }
       }
+      vals[u] = v;
     }
-    in[(cl * TY + t) * ip + x] = v;
+#pragma unroll
+    for (int u = 0; u < kXU; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < nld) {
+        const int x = i % g.nx;
+        const int r = i / g.nx;
+        in[((r / TY) * TY + r % TY) * ip + x] = vals[u];
+      }
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < NC * TY * LB; i += blockDim.x) {
@@ -288,14 +310,24 @@ __device__ __forceinline__ void x_inv_body(const Geom& g, const MvData<C>& d, co
   const C* ia = d.ia + (int64_t)(rhs0 + b) * g.ncomp * 3;
   const int nst = NC * TY * g.nx;
   [[maybe_unused]] kred::AccF re, im, tt;
-  for (int i = threadIdx.x; i < nst; i += blockDim.x) {
+  // kXU elements per thread per round, site indices first (independent loads in flight)
+  constexpr int kXU = 4;
+  for (int i0 = threadIdx.x; i0 < nst; i0 += kXU * blockDim.x) {
+   int32_t idxs[kXU];
+#pragma unroll
+   for (int u = 0; u < kXU; ++u) {
+     const int i = i0 + u * blockDim.x;
+     const int y = y0 + (i / g.nx) % TY;
+     idxs[u] = (i < nst && y < g.ny) ? __ldg(d.map + ((int64_t)z * g.ny + y) * g.nx + i % g.nx) : -1;
+   }
+#pragma unroll
+   for (int u = 0; u < kXU; ++u) {
+    const int i = i0 + u * blockDim.x;
+    const int32_t idx = idxs[u];
+    if (idx < 0) continue;
     const int x = i % g.nx;
     const int r = i / g.nx;
     const int t = r % TY, cl = r / TY;
-    const int y = y0 + t;
-    if (y >= g.ny) continue;
-    const int32_t idx = __ldg(d.map + ((int64_t)z * g.ny + y) * g.nx + x);
-    if (idx < 0) continue;
     const int c = c0 + cl;
     const int64_t o = ((int64_t)b * 3 + c) * g.n + idx;
     const int cc = d.comp ? d.comp[3 * idx + c] : 0;  // composition of axis c
@@ -324,6 +356,7 @@ __device__ __forceinline__ void x_inv_body(const Geom& g, const MvData<C>& d, co
       kred::acc_cdot(re, im, res, kf->s[o]);     // <t, s>
       kred::acc_nrm(tt, res);                    // |t|^2
     }
+   }
   }
   if constexpr (MODE == kFuseRV) {
     double acc[2] = {re.get(), im.get()};
@@ -842,10 +875,24 @@ template <typename C>
 size_t plane_bulk_smem(const Geom& g) {
   return ((plane_bytes<C>(g.py, g.pz) + 15) & ~(size_t)15) + 16;
 }
-constexpr int kRowsPerCta = 8;
+// y rows per CTA of the 5-pass y passes: enough that pass A and pass B give every one of the 256
+// threads an item (rows x LB = 256), between 8 and 32 rows
+template <int PY>
+constexpr int y_rows_per_cta() {
+  constexpr int r = 256 / Shape<PY>::LB;
+  return r < 8 ? 8 : (r > 32 ? 32 : r);
+}
+inline int y_rows_per_cta_rt(int py) {
+  switch (py) {
+#define DDA_CASE(L_) case L_: return y_rows_per_cta<L_>();
+    DDA_FAST_LENGTHS(DDA_CASE)
+#undef DDA_CASE
+    default: return 8;
+  }
+}
 template <typename C>
 size_t yrows_fast_smem(const Geom& g) {
-  return sizeof(C) * ((size_t)g.py + (size_t)kRowsPerCta * (g.py + 1));
+  return sizeof(C) * ((size_t)g.py + (size_t)y_rows_per_cta_rt(g.py) * (g.py + 1));
 }
 template <typename C>
 size_t zcols_fast_smem(const Geom& g) {
@@ -944,12 +991,15 @@ Err launch_plane(const Geom& g, const MvData<C>& d, int nrhs, int nt, cudaStream
 template <typename C>
 Err launch_y_rows(const Geom& g, C* work, const C* tw, int64_t nrows, bool inv, cudaStream_t st) {
   const size_t sm = yrows_fast_smem<C>(g);
-  const unsigned nb = (unsigned)((nrows + kRowsPerCta - 1) / kRowsPerCta);
+  const int rpb = y_rows_per_cta_rt(g.py);
+  const unsigned nb = (unsigned)((nrows + rpb - 1) / rpb);
   switch (g.py) {
 #define DDA_CASE(L_)                                                                            \
   case L_:                                                                                      \
-    if (inv) DDA_CU(launch_k(k_y_rows<C, L_, kRowsPerCta, true>, dim3(nb), dim3(256), sm, st, g, work, tw, nrows)); \
-    else DDA_CU(launch_k(k_y_rows<C, L_, kRowsPerCta, false>, dim3(nb), dim3(256), sm, st, g, work, tw, nrows));   \
+    if (inv) DDA_CU(launch_k(k_y_rows<C, L_, y_rows_per_cta<L_>(), true>, dim3(nb), dim3(256), sm, st, g, work, tw, \
+                             nrows));                                                           \
+    else DDA_CU(launch_k(k_y_rows<C, L_, y_rows_per_cta<L_>(), false>, dim3(nb), dim3(256), sm, st, g, work, tw,    \
+                         nrows));                                                               \
     break;
     DDA_FAST_LENGTHS(DDA_CASE)
 #undef DDA_CASE
@@ -1021,8 +1071,8 @@ template <typename C>
 void optin_all(int smax) {
 #define DDA_CASE(L_)                                                                                                 \
   optin_x<C, L_>(smax);                                                                                              \
-  optin_smem(k_y_rows<C, L_, kRowsPerCta, false>, smax);   \
-  optin_smem(k_y_rows<C, L_, kRowsPerCta, true>, smax);    \
+  optin_smem(k_y_rows<C, L_, y_rows_per_cta<L_>(), false>, smax);   \
+  optin_smem(k_y_rows<C, L_, y_rows_per_cta<L_>(), true>, smax);    \
   optin_smem(k_z_cols<C, L_, zcols_g_rt(sizeof(C), L_)>, smax);
   DDA_FAST_LENGTHS(DDA_CASE)
 #undef DDA_CASE

@@ -66,6 +66,7 @@ def _load():
         "dda_get_box": (I, [P, P, P]),
         "dda_set_incident": (I, [P, D, P, I, P, I]),
         "dda_kd_from_x": (I, [P, D, P, P]),
+        "dda_set_periodicity": (I, [P, D, D, D]),
         "dda_orientation_average": (I, [P, I, I, P, I64, P]),
         "dda_nrhs": (I, [P]),
         "dda_get_incidence": (I, [P, P, P]),
@@ -206,6 +207,10 @@ class Context:
         org = np.zeros(3, dtype=np.float64)
         self._check(LIB.dda_get_sites(self._h, _ptr(out), _ptr(org)))
         return out, org
+
+    def dda_set_periodicity(self, py: float, pz: float, gamma: float = 0.01):
+        """Repeat the target with periods py (y_TF) and pz (z_TF), 0 = none; gamma = interaction cutoff."""
+        self._check(LIB.dda_set_periodicity(self._h, float(py), float(pz), float(gamma)))
 
     def dda_kd_from_x(self, x: float):
         """(kd, a_eff / d) for size parameter x of the current target."""

@@ -208,3 +208,18 @@ def test_orientation_average_is_the_weighted_sum(D):
     np.testing.assert_allclose(got[0], np.einsum("o,odk->dk", w, m), rtol=1e-13, atol=1e-15)
     with pytest.raises(D.DDAError):
         D.dda_orientation_average(q, w, 3)
+
+
+def test_periodicity_arguments(D):
+    ctx = D.Context(-1)
+    with pytest.raises(D.DDAError) as ei:
+        ctx.dda_set_periodicity(5.0, 0.0)    # no target yet
+    assert ei.value.status == D.DDA_ESTATE
+    ctx.dda_setup_shape("ELLIPSOID", (6, 5, 4))
+    with pytest.raises(D.DDAError) as ei:
+        ctx.dda_set_periodicity(3.0, 0.0)    # shorter than the cell's y extent
+    assert ei.value.status == D.DDA_EINVAL
+    with pytest.raises(D.DDAError):
+        ctx.dda_set_periodicity(8.0, 0.0, gamma=0.0)
+    ctx.dda_set_periodicity(8.0, 0.0, 0.02)
+    ctx.dda_set_periodicity(0.0, 0.0)        # finite again

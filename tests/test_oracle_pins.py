@@ -836,3 +836,59 @@ def test_near_field_of_the_au_block_matches_the_printed_track():
         ref = complex(row[3], row[4])
         assert abs(e[1] - ref) <= 2e-3 * max(abs(ref), 0.1), (row, e[1])
         assert abs(e[0]) < 1e-6 and abs(e[2]) < 1e-6
+
+
+# ----------------------------------------------------------------------------- periodic targets
+
+def _tuc():
+    return targets.make_target("ELLIPSOID", (3, 4, 3))
+
+
+@pytest.mark.parametrize("periods", [(5.0, 6.0), (5.0, 0.0), (0.0, 7.0)])
+def test_periodic_fft_product_equals_the_replica_sum(periods):
+    """The FFT embedding of the periodic interaction A^per (every offset of the wrapped grid, Bloch
+    phases, cutoff) against the plain O(N^2 x replicas) sum, at oblique incidence."""
+    from oracle import periodic
+    t = _tuc()
+    prob = dda.build_problem(None, None, 1.5 + 0.2j, 1.0, "LATTDR", [(0.3, 1.0, 0.4)], target=t, periods=periods,
+                             gamma=0.15)
+    p = W.seeded_vector((3, t.n), 12)
+    a1 = dda.apply_a(prob, 0, p, "direct")
+    a2 = dda.apply_a(prob, 0, p, "fft")
+    assert np.linalg.norm(a1 - a2) / np.linalg.norm(a1) < 1e-13
+    # and it differs from the finite target's product (the replicas matter)
+    fin = dda.build_problem(None, None, 1.5 + 0.2j, 1.0, "LATTDR", [(0.3, 1.0, 0.4)], target=t)
+    assert np.linalg.norm(a1 - dda.apply_a(fin, 0, p, "direct")) / np.linalg.norm(a1) > 1e-3
+
+
+def test_periodic_interaction_reciprocity():
+    """A^per(r; k) = A^per(-r; -k) (the replicas' Bloch phases flip with the incidence), so
+    u^T A(k) v = v^T A(-k) u; at normal incidence A^per is complex symmetric."""
+    from oracle import periodic
+    t = _tuc()
+    k = np.array([0.2, 0.35, -0.15])
+    u = W.seeded_vector((3, t.n), 3)
+    v = W.seeded_vector((3, t.n), 4)
+    ia = np.full((t.n, 3), 2.0 + 0.1j)
+    av = periodic.matvec_direct(t.r, np.linalg.norm(k), ia, v, k, (5.0, 6.0), 0.15)
+    au = periodic.matvec_direct(t.r, np.linalg.norm(k), ia, u, -k, (5.0, 6.0), 0.15)
+    assert abs(np.sum(u * av) - np.sum(v * au)) < 1e-12 * abs(np.sum(u * av))
+
+
+def test_periodic_slab_absorbs_like_a_fresnel_film():
+    """An infinite slab (2-D periodic TUC of one column of 8 dipoles, periods 1 x 1) at normal
+    incidence absorbs per unit area what the continuum film of the same index and thickness absorbs
+    (Airy-Fresnel), within the DDA's discretization error (1 %); Draine & Flatau 2008 validate the
+    periodic method the same way."""
+    from oracle import periodic
+    nl, m, kd = 8, 1.5 + 0.1j, 0.1
+    tt = targets.Target(ijk=np.stack([np.arange(nl), np.zeros(nl, int), np.zeros(nl, int)], 1), box=(nl, 1, 1),
+                        origin=np.zeros(3), a1=np.array([1.0, 0, 0]), a2=np.array([0, 1.0, 0]))
+    pr = dda.build_problem(None, None, m, None, "LATTDR", [(0, 0, 0)], target=tt, kd=kd, iorth=1, periods=(1, 1),
+                           gamma=0.08)
+    ps, _ = dda.solve(pr, "lu")
+    q = dda.cross_sections(pr, ps)[0]
+    absorbed = q["Qabs"] * np.pi * tt.aeff ** 2 / (1.0 * 1.0)   # C_abs per unit-cell area
+    assert absorbed == pytest.approx(periodic.slab_fresnel_absorption(m, kd, nl), rel=0.01)
+    # every layer of the column carries the same field pattern as its replicas: P is uniform in y, z
+    assert np.abs(ps[0][0]).max() < 1e-10 * np.abs(ps[0][1]).max()

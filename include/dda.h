@@ -380,10 +380,19 @@ DDA_API dda_status dda_schedule_info(dda_ctx *ctx, int dtype, int32_t info[12]);
 typedef struct dda_unet dda_unet;
 
 /* Network with cin input and cout output channels and level widths ch[0..3]
- * (each 1..64), He-uniform weights from seed; work on `cuda_stream`. */
+ * (each 1..64), He-uniform weights from seed; work on `cuda_stream`.  The
+ * 3x3x3 convolutions (forward and input gradient) run as implicit GEMMs on the
+ * tensor cores: mma.sync by default, or tcgen05 MMAs with tensor-memory
+ * accumulators when the environment variable DDA_UNET_TC=1 is set at creation
+ * (bounded waits; a wait that gives up is reported by dda_unet_check_fault).
+ * The weight gradients use mma.sync in both modes. */
 DDA_API dda_status dda_unet_create(dda_unet **out, int device, void *cuda_stream, int cin, int cout, const int32_t ch[4],
                                    uint64_t seed);
 DDA_API void dda_unet_destroy(dda_unet *net);
+/* DDA_ECUDA if a tcgen05 convolution's bounded completion wait gave up since the
+ * last call (its outputs are then invalid; the flag is cleared), else DDA_OK.
+ * Call after synchronizing the network's stream. */
+DDA_API dda_status dda_unet_check_fault(dda_unet *net);
 DDA_API const char *dda_unet_last_error(const dda_unet *net);
 DDA_API int64_t dda_unet_nparams(const dda_unet *net);
 /* Copy the FP32 parameters (which = 0) or their last gradients (which = 1) to
@@ -510,6 +519,16 @@ DDA_API dda_status dda_orientation_average(const double *w, int n_ori, int iorth
  * bounded wait on a barrier that never completes, on `device`, and sets
  * *gave_up = 1 when the wait ended by itself (the device stays usable). */
 DDA_API dda_status dda_selftest_bulk_wait(int device, int32_t *gave_up);
+
+/* Measurement probe (no counterpart in the guide): applies `reps` unitary
+ * 8-point DFT stages to nvec (a multiple of 8) seeded complex vectors held in
+ * registers, once with the product's FP32 radix-8 butterflies and once as
+ * split-TF32 tensor-core matrix products (mma.sync m16n8k8, three products per
+ * stage for an FP32-like error, warp shuffles between stages), on `device`.
+ * out[0], out[1] = milliseconds (CUDA events), out[2], out[3] = relative L2
+ * error against FP64 of the FP32 and the tensor-core paths.  Allocates and frees
+ * its own buffer.  Synchronizes. */
+DDA_API dda_status dda_probe_tc_dft(int device, int64_t nvec, int reps, double out[4]);
 
 /* Library build string (static storage). */
 DDA_API const char *dda_version(void);

@@ -17,7 +17,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdda.so")
 SOURCES = ["api.cu", "matvec.cu", "matvec_fast_c64.cu", "matvec_fused_c64.cu", "matvec_cluster.cu", "matvec_plane_bulk.cu", "matvec_fast_c128.cu", "matvec_fast_df.cu", "krylov.cu", "observables.cu",
-           "unet.cu", "targets.cpp"]
+           "unet.cu", "targets.cpp", "tc_dft_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -2341,6 +2341,13 @@ dda_status dda_orientation_average(const double* w, int n_ori, int iorth, const 
   return DDA_OK;
 }
 
+dda_status dda_probe_tc_dft(int device, int64_t nvec, int reps, double out[4]) {
+  if (!out) return DDA_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return DDA_ECUDA;
+  const Err e = dda::probe_tc_dft(nvec, reps, out);
+  return e.ok() ? DDA_OK : e.code;
+}
+
 dda_status dda_selftest_bulk_wait(int device, int32_t* gave_up) {
   if (!gave_up) return DDA_EINVAL;
   if (cudaSetDevice(device) != cudaSuccess) return DDA_ECUDA;

@@ -340,6 +340,10 @@ Err farfield_moments(const int32_t* ijk, const double* origin3, const double* nh
 // E then B, (re, im) x 3, FP64; dipoles nearer than one lattice spacing scaled by R^4 (5 - 4R).
 Err near_field(const int32_t* ijk, const double* origin3, const double2* p, int nrhs, int64_t n, const double* pts,
                int64_t npts, double kd, double* out, cudaStream_t st);
+// Measurement probe: nvec 8-point complex vectors through `reps` unitary DFT-8 stages, on FP32
+// butterflies and on split-TF32 tensor-core products; out = {fp32 ms, tensor ms, fp32 error,
+// tensor error} (relative L2 against FP64 on the first 64 vectors).
+Err probe_tc_dft(int64_t nvec, int reps, double out[4]);
 // Incident-field force/torque sums per RHS: out7[b] = {sum Re(P x E^*) (3), sum (r - r_cm) Im(P.E^*) (3),
 // sum Im(P.E^*)}; part: nrhs * nblk * 8 doubles.
 Err torque_ext_sums(const int32_t* ijk, const double2* einc, const double2* p, int nrhs, int64_t n,

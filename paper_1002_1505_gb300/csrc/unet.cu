@@ -23,12 +23,14 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <random>
 #include <string>
 #include <vector>
 
+#include "bulk.cuh"
 #include "dda_internal.h"
 
 namespace dda {
@@ -151,6 +153,188 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const float* __restrict__
         y[r * ys + c] = val;
       }
     }
+  }
+}
+
+// ------------------------------------------------------------------ tcgen05 convolution
+// The same implicit GEMM on the fifth-generation tensor cores: a CTA of 128 threads owns 128
+// consecutive output voxels (the MMA's M = 128 rows) and accumulates D[128][NP] in tensor memory
+// over the 27 taps x ceil(cin/16) channel chunks (K = 16 per tcgen05.mma, kind::f16 with bf16
+// operands, FP32 accumulation).  Per (tap, chunk): each thread gathers its voxel's neighbour row of
+// 16 channels (rounded to bf16) into the A tile, NP * 2 threads copy the chunk's prepacked weights
+// into the B tile; both tiles are in the canonical no-swizzle K-major layout (8-row x 16-byte core
+// matrices, K neighbours 128 B apart, M/N neighbours 256 B apart).  Two tile buffers alternate: the
+// MMA of one chunk runs while the threads fill the next, and a buffer is refilled only after the
+// tcgen05.commit of its previous MMA has arrived on that buffer's mbarrier (bounded wait: a wait that
+// gives up sets the fault flag and the results are then invalid).  The epilogue reads the
+// accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. voxels), adds the bias,
+// applies ReLU and stores FP32.
+namespace tc {
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte offsets, version 1,
+// no swizzle
+__device__ __forceinline__ uint64_t desc(const void* smem, uint32_t lbo, uint32_t sbo) {
+  const uint64_t a = (saddr(smem) & 0x3FFFFu) >> 4;
+  return a | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: D FP32, A and B bf16, both K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(id), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+template <int NCOL>
+__device__ __forceinline__ void alloc(uint32_t* slot) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(slot)), "n"(NCOL)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+template <int NCOL>
+__device__ __forceinline__ void dealloc(uint32_t tmem) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(NCOL) : "memory");
+}
+// 16 consecutive 32-bit columns of this thread's TMEM lane
+__device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+}  // namespace tc
+
+constexpr int kTcThreads = 128;
+constexpr uint32_t kTcMaxPolls = 1u << 22;
+
+// wtc: per (tap, chunk) NP x 16 bf16 in the B-tile layout (NP * 2 blocks of 16 bytes)
+template <int NP>
+__global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float* __restrict__ x, int xs, int cin, int kc_n,
+                                                        const uint4* __restrict__ wtc, int taps, bool flip,
+                                                        const float* __restrict__ bias, float* __restrict__ y, int ys,
+                                                        int cout, bool relu, Dims d, int64_t V,
+                                                        unsigned int* __restrict__ fault) {
+  static_assert(NP % 16 == 0 && NP >= 16 && NP <= 128, "N must be a multiple of 16 in [16, 128]");
+  constexpr int NCOL = NP <= 32 ? 32 : (NP <= 64 ? 64 : 128);
+  __shared__ __align__(128) uint4 sA[2][256];        // 128 rows x 16 bf16
+  __shared__ __align__(128) uint4 sB[2][NP * 2];     // NP rows x 16 bf16
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) tc::alloc<NCOL>(&tmem_slot);
+  if (tid == 0) {
+    bulk::mbar_init(&bar[0], 1);
+    bulk::mbar_init(&bar[1], 1);
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_slot;
+  const int64_t v = (int64_t)blockIdx.x * 128 + tid;  // this thread's A row and output voxel
+  const int niter = taps * kc_n;
+  uint32_t phase[2] = {0u, 0u};
+  int waited[2] = {0, 0};
+  bool ok = true;
+  // A-tile byte offset of this row: core matrix (row / 8) 256 B apart, row in it 16 B apart
+  const int arow = (tid >> 3) * 16 + (tid & 7);  // in uint4 units: (row/8)*256 B + (row%8)*16 B
+  for (int it = 0; it < niter; ++it) {
+    const int buf = it & 1;
+    if (it >= 2) {  // the MMA that last read this buffer (iteration it - 2) has finished
+      ok = bulk::mbar_wait(&bar[buf], phase[buf], kTcMaxPolls, fault) && ok;
+      phase[buf] ^= 1u;
+      ++waited[buf];
+    }
+    const int tap = it / kc_n, kc = it - tap * kc_n;
+    const int64_t nb = (v < V) ? neighbour(v, d, tap, taps, flip) : -1;
+    const float* xr = nb >= 0 ? x + nb * xs : nullptr;
+    uint32_t pk[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int c = kc * 16 + 2 * q;
+      const float lo = (xr && c < cin) ? __ldg(xr + c) : 0.f;
+      const float hi = (xr && c + 1 < cin) ? __ldg(xr + c + 1) : 0.f;
+      pk[q] = pack_bf16(lo, hi);
+    }
+    sA[buf][arow] = make_uint4(pk[0], pk[1], pk[2], pk[3]);      // K elements 0..7 (core column 0)
+    sA[buf][arow + 8] = make_uint4(pk[4], pk[5], pk[6], pk[7]);  // K elements 8..15 (128 B further)
+    for (int q = tid; q < NP * 2; q += kTcThreads) sB[buf][q] = __ldg(wtc + (int64_t)it * NP * 2 + q);
+    bulk::fence_smem_to_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+      tc::mma(tmem, tc::desc(&sA[buf][0], 128, 256), tc::desc(&sB[buf][0], 128, 256), tc::idesc_bf16(NP),
+              it > 0 ? 1u : 0u);
+      tc::commit(&bar[buf]);
+    }
+  }
+  // the last one or two MMAs
+  for (int b = 0; b < 2; ++b) {
+    const int issued = (niter + 1 - b) / 2;  // iterations with it & 1 == b
+    while (waited[b] < issued) {
+      ok = bulk::mbar_wait(&bar[b], phase[b], kTcMaxPolls, fault) && ok;
+      phase[b] ^= 1u;
+      ++waited[b];
+    }
+  }
+  tc::fence_after();
+  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+  for (int c0 = 0; c0 < NP; c0 += 16) {
+    float acc[16];
+    tc::ld16(lane_base + (uint32_t)c0, acc);
+    if (v < V && ok) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int co = c0 + j;
+        if (co < cout) {
+          float val = acc[j] + (bias ? bias[co] : 0.f);
+          if (relu) val = fmaxf(val, 0.f);
+          y[v * ys + co] = val;
+        }
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::dealloc<NCOL>(tmem);
+}
+
+// pack W[tap][ci][co] (FP32) into the tcgen05 B tiles: per (tap, chunk) element (n, k) at bf16 offset
+// ((n / 8) * 2 + k / 8) * 64 + (n % 8) * 8 + k % 8; forward n = co, k = ci; transposed n = ci, k = co
+__global__ void k_pack_tc(const float* __restrict__ w, int taps, int cin, int cout, int kc_n, int np, bool transpose,
+                          __nv_bfloat16* __restrict__ out) {
+  const int64_t total = (int64_t)taps * kc_n * np * 16;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int e = (int)(i % (np * 16));
+    const int64_t blk = i / (np * 16);
+    const int kc = (int)(blk % kc_n), tap = (int)(blk / kc_n);
+    const int core = e / 64, in = e % 64;
+    const int n = (core / 2) * 8 + in / 8, k = kc * 16 + (core % 2) * 8 + in % 8;
+    float val = 0.f;
+    if (!transpose) {
+      if (k < cin && n < cout) val = w[((int64_t)tap * cin + k) * cout + n];
+    } else {
+      if (k < cout && n < cin) val = w[((int64_t)tap * cin + n) * cout + k];
+    }
+    out[i] = __float2bfloat16_rn(val);
   }
 }
 
@@ -469,6 +653,8 @@ struct dda_unet {
     int64_t woff, boff;                                      // offsets into the flat parameter vector
     uint2* wp = nullptr;                                     // forward fragments
     uint2* wt = nullptr;                                     // transposed+flipped fragments (input grad)
+    __nv_bfloat16* wtc = nullptr;                            // tcgen05 B tiles, forward (N = cout)
+    __nv_bfloat16* wttc = nullptr;                           // tcgen05 B tiles, input gradient (N = cin)
   };
   std::vector<Layer> layers;
   int64_t nparams = 0;
@@ -481,6 +667,8 @@ struct dda_unet {
   size_t part_bytes = 0;
   double* lpart = nullptr;
   double* h_loss = nullptr;
+  bool use_tc = false;                 // convolutions on tcgen05 (DDA_UNET_TC=1) instead of mma.sync
+  unsigned int* d_fault = nullptr;     // set when a bounded tensor-core wait gave up
 };
 
 namespace {
@@ -494,8 +682,20 @@ dda_status ufail(dda_unet* n, const Err& e) {
 
 int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
+int np16(int c) { return (c + 15) / 16 * 16; }
+
 Err repack(dda_unet* n) {
   for (auto& L : n->layers) {
+    if (n->use_tc) {
+      const int64_t t1 = (int64_t)L.taps * L.kc_n * np16(L.cout) * 16;
+      dda::nn::k_pack_tc<<<dda::nn::blocks_for(t1), 256, 0, n->stream>>>(n->p + L.woff, L.taps, L.cin, L.cout, L.kc_n,
+                                                                          np16(L.cout), false, L.wtc);
+      const int64_t t2 = (int64_t)L.taps * L.cin_t_kc * np16(L.cin) * 16;
+      dda::nn::k_pack_tc<<<dda::nn::blocks_for(t2), 256, 0, n->stream>>>(n->p + L.woff, L.taps, L.cin, L.cout,
+                                                                          L.cin_t_kc, np16(L.cin), true, L.wttc);
+      DDA_CU(cudaGetLastError());
+      dda::add_launches(2);
+    }
     const int tot = L.taps * L.kc_n * L.nt_n * 32;
     dda::nn::k_pack<<<dda::nn::blocks_for(tot), 256, 0, n->stream>>>(n->p + L.woff, L.taps, L.cin, L.cout, L.kc_n,
                                                                        L.nt_n, false, L.wp);
@@ -519,6 +719,24 @@ Err conv(dda_unet* n, const dda_unet::Layer& L, const float* x, int xs, float* y
   const int cout = transposed ? L.cin : L.cout;
   const uint2* w = transposed ? L.wt : L.wp;
   const float* bias = transposed ? nullptr : n->p + L.boff;
+  if (n->use_tc) {
+    const int np = np16(cout);
+    const uint4* wt = reinterpret_cast<const uint4*>(transposed ? L.wttc : L.wtc);
+    const int tblocks = (int)((V + 127) / 128);
+    switch (np) {
+#define CASE(NP)                                                                                                      \
+  case NP:                                                                                                            \
+    dda::nn::k_conv_tc<NP><<<tblocks, dda::nn::kTcThreads, 0, n->stream>>>(x, xs, cin, kc_n, wt, L.taps, transposed, \
+                                                                           bias, y, ys, cout, relu, d, V, n->d_fault); \
+    break;
+      CASE(16) CASE(32) CASE(48) CASE(64) CASE(80) CASE(96) CASE(112) CASE(128)
+#undef CASE
+      default: return Err::make(DDA_EUNSUPPORTED, "layer wider than 128 channels");
+    }
+    DDA_CU(cudaGetLastError());
+    dda::add_launches(1);
+    return Err::Ok();
+  }
   switch (nt_n) {
 #define CASE(NT)                                                                                                   \
   case NT:                                                                                                         \
@@ -768,9 +986,20 @@ dda_status dda_unet_create(dda_unet** out, int device, void* stream, int cin, in
             cudaMalloc((void**)&n->v, sizeof(float) * off) == cudaSuccess &&
             cudaMalloc((void**)&n->lpart, sizeof(double) * 2048) == cudaSuccess &&
             cudaMallocHost((void**)&n->h_loss, sizeof(double) * 2048) == cudaSuccess;
+  {
+    const char* f = std::getenv("DDA_UNET_TC");
+    n->use_tc = f && std::atoi(f) == 1;
+  }
+  ok = ok && cudaMalloc((void**)&n->d_fault, sizeof(unsigned int)) == cudaSuccess &&
+       cudaMemset(n->d_fault, 0, sizeof(unsigned int)) == cudaSuccess;
   for (auto& L : n->layers) {
     ok = ok && cudaMalloc((void**)&L.wp, sizeof(uint2) * L.taps * L.kc_n * L.nt_n * 32) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&L.wt, sizeof(uint2) * L.taps * L.cin_t_kc * L.cout_t_nt * 32) == cudaSuccess;
+    if (n->use_tc) {
+      ok = ok && cudaMalloc((void**)&L.wtc, sizeof(__nv_bfloat16) * L.taps * L.kc_n * np16(L.cout) * 16) == cudaSuccess;
+      ok = ok && cudaMalloc((void**)&L.wttc, sizeof(__nv_bfloat16) * L.taps * L.cin_t_kc * np16(L.cin) * 16) ==
+                     cudaSuccess;
+    }
   }
   if (!ok) {
     dda_unet_destroy(n);
@@ -796,12 +1025,27 @@ void dda_unet_destroy(dda_unet* n) {
   for (auto& L : n->layers) {
     if (L.wp) cudaFree(L.wp);
     if (L.wt) cudaFree(L.wt);
+    if (L.wtc) cudaFree(L.wtc);
+    if (L.wttc) cudaFree(L.wttc);
   }
   for (float* q : {n->p, n->g, n->m, n->v, n->ws, n->part})
     if (q) cudaFree(q);
   if (n->lpart) cudaFree(n->lpart);
   if (n->h_loss) cudaFreeHost(n->h_loss);
+  if (n->d_fault) cudaFree(n->d_fault);
   delete n;
+}
+
+// DDA_ECUDA when a tensor-core convolution's bounded wait gave up since the last check (the flag is
+// then cleared); call after the stream has been synchronized
+dda_status dda_unet_check_fault(dda_unet* n) {
+  if (!n || !n->d_fault) return DDA_OK;
+  unsigned int h = 0;
+  if (cudaMemcpy(&h, n->d_fault, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return DDA_ECUDA;
+  if (!h) return DDA_OK;
+  cudaMemset(n->d_fault, 0, sizeof(unsigned int));
+  n->err = "a tensor-core convolution's bounded wait gave up: results invalid";
+  return DDA_ECUDA;
 }
 
 const char* dda_unet_last_error(const dda_unet* n) { return n ? n->err.c_str() : "null network"; }

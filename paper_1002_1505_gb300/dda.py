@@ -80,6 +80,7 @@ def _load():
         "dda_version": (ctypes.c_char_p, []),
         "dda_kernel_launches": (ctypes.c_ulonglong, []),
         "dda_selftest_bulk_wait": (I, [I, P]),
+        "dda_probe_tc_dft": (I, [I, I64, I, P]),
         "dda_angular_averages": (I, [P, P, D, P, P]),
         "dda_force_torque": (I, [P, P, D, P, P]),
         "dda_near_field": (I, [P, P, P, I64, P, P]),
@@ -90,6 +91,7 @@ def _load():
         "dda_solve_batch": (I, [P, I, P, P, P, P]),
         "dda_unet_create": (I, [ctypes.POINTER(P), I, P, I, I, P, ctypes.c_uint64]),
         "dda_unet_destroy": (None, [P]),
+        "dda_unet_check_fault": (I, [P]),
         "dda_unet_last_error": (ctypes.c_char_p, [P]),
         "dda_unet_nparams": (I64, [P]),
         "dda_unet_get_params": (I, [P, P, I]),
@@ -370,6 +372,10 @@ class UNet:
         if st != DDA_OK:
             raise DDAError(st, LIB.dda_unet_last_error(self._h).decode())
 
+    def dda_unet_check_fault(self):
+        """Raise if a tcgen05 convolution's bounded wait gave up since the last check."""
+        self._check(LIB.dda_unet_check_fault(self._h))
+
     @property
     def nparams(self) -> int:
         return int(LIB.dda_unet_nparams(self._h))
@@ -489,6 +495,15 @@ def dda_selftest_bulk_wait(device: int = 0) -> bool:
     if st != DDA_OK:
         raise DDAError(st, "dda_selftest_bulk_wait failed")
     return bool(out[0])
+
+
+def dda_probe_tc_dft(device: int = 0, nvec: int = 1 << 21, reps: int = 256):
+    """{fp32_ms, tensor_ms, fp32_err, tensor_err} of `reps` DFT-8 stages on nvec vectors (measurement probe)."""
+    out = np.zeros(4)
+    st = LIB.dda_probe_tc_dft(int(device), int(nvec), int(reps), _ptr(out))
+    if st != DDA_OK:
+        raise DDAError(st, "dda_probe_tc_dft failed")
+    return {"fp32_ms": out[0], "tensor_ms": out[1], "fp32_err": out[2], "tensor_err": out[3]}
 
 
 def dda_kernel_launches() -> int:

@@ -240,3 +240,54 @@ def test_trained_network_saves_iterations(D):
     # evaluation of warmstart.main gains about 2 % over it)
     assert warm <= 0.98 * cold and plain < cold, (warm, plain, cold)
     assert warm <= 1.03 * plain, (warm, plain)
+
+
+@pytest.fixture
+def tc_mode(monkeypatch):
+    """Networks created inside the test run their convolutions on tcgen05 (tensor memory accumulators)."""
+    monkeypatch.setenv("DDA_UNET_TC", "1")
+
+
+def test_tcgen05_forward_matches_oracle_and_mma_sync(D, tc_mode, monkeypatch):
+    """The tcgen05 convolutions give the oracle's forward pass, and the mma.sync path's to FP32 summation order."""
+    cin, cout, ch, dims = 9, 6, (12, 24, 32, 48), (16, 8, 16)
+    rng = np.random.default_rng(31)
+    x = rng.standard_normal((2, dims[2], dims[1], dims[0], cin)).astype(np.float32)
+    xg = torch.from_numpy(x).cuda()
+    net = D.UNet(0, None, cin, cout, ch, seed=31)
+    y_tc = torch.empty(x.shape[:4] + (cout,), dtype=torch.float32, device="cuda")
+    net.dda_unet_forward(xg, y_tc, dims)
+    torch.cuda.synchronize()
+    net.dda_unet_check_fault()
+    theta = net.dda_unet_get_params().astype(np.float64)
+    ref = OU.forward(theta, x.astype(np.float64), cin, cout, ch, quant=True)
+    assert _rel(y_tc.cpu().numpy(), ref) <= 2e-3
+    monkeypatch.setenv("DDA_UNET_TC", "0")
+    net2 = D.UNet(0, None, cin, cout, ch, seed=31)
+    y_ms = torch.empty_like(y_tc)
+    net2.dda_unet_forward(xg, y_ms, dims)
+    torch.cuda.synchronize()
+    # identical bf16 operands, FP32 accumulation in another order: bf16 rounding of later layers'
+    # inputs may flip on ties of that order, hence 1e-3 rather than FP32 epsilon
+    assert _rel(y_tc.cpu().numpy(), y_ms.cpu().numpy()) <= 1e-3
+
+
+def test_tcgen05_gradients_match_oracle(D, tc_mode):
+    """Loss and gradients with the forward and input-gradient convolutions on tcgen05."""
+    net = D.UNet(0, None, CIN, COUT, CH, seed=12)
+    theta = net.dda_unet_get_params().astype(np.float64)
+    x, t, mask = _data(2)
+    loss = net.dda_unet_loss_grad(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(),
+                                  torch.from_numpy(mask).cuda(), DIMS)
+    torch.cuda.synchronize()
+    net.dda_unet_check_fault()
+    g = net.dda_unet_get_params(which=1).astype(np.float64)
+    Lr, gr = OU.loss_and_grad(theta, x.astype(np.float64), t.astype(np.float64), mask.astype(np.float64), CIN, COUT,
+                              CH, quant=True)
+    assert loss == pytest.approx(Lr, rel=1e-4)
+    o = 0
+    for taps, a, b in OU.layer_shapes(CIN, COUT, CH):
+        nw = taps * a * b
+        assert _rel(g[o:o + nw], gr[o:o + nw]) <= 5e-3, ("W", o)
+        assert _rel(g[o + nw:o + nw + b], gr[o + nw:o + nw + b]) <= 5e-3, ("b", o)
+        o += nw + b

@@ -438,6 +438,10 @@ def main():
     plain_ori = my_ori[:max(1, min(n_plain, n_ori))]
     plain_ms, plain_mv, (preps, pq) = timed(args.plain_reps, precision="C128", use_graph=False, ori=plain_ori)
     plain_ms_per_ori = plain_ms / args.plain_reps / len(plain_ori)
+    # back to every orientation of this rank (the context's RHS count follows the last set-up)
+    ctx.dda_set_incident(kd, my_ori, e01, w.iorth)
+    ctx.dda_build_green_fft(w.pad)
+    ctx.dda_set_polarizability(w.prescription, w.m)
 
     # warm-started solves (config 5: the same mixed-precision solve from an initial guess): the
     # network-free local-field guess P0 = alpha E_inc, and the learned network's guess when a short
@@ -462,7 +466,6 @@ def main():
             warm_report[nm] = {"iterations": int(sum(r["iters"] for r in wreps)), "ms_per_orientation": wms / n_ori,
                                "max_true_rel_resid": float(max(r["true_rel_resid"] for r in wreps)),
                                "includes": "guess construction + solve + observables"}
-        step()  # leave the context on the cold configuration
 
     # end to end through the C ABI with host buffers: site list in, solution P and Q out
     sites, origin = ctx.dda_get_sites()

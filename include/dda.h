@@ -276,7 +276,7 @@ typedef struct {
   double tol;        /* stop when |E - A P| / |E| <= tol for every RHS */
   int maxit;         /* iteration cap (inner iterations summed for MIXED) */
   double inner_tol;  /* MIXED: smallest relative reduction asked of an inner complex64 solve; each
-                        inner solve aims at 0.5 tol / (current true relative residual) but not
+                        inner solve aims at 0.8 tol / (current true relative residual) but not
                         below this floor (0 = 5e-6, near the complex64 limit) */
   double timeout_ms; /* wall-clock budget, 0 = none; exceeded -> DDA_ETIMEOUT */
   int warm_start;    /* 1 = p_dev holds the initial guess, 0 = start from P = 0 */
@@ -382,10 +382,12 @@ typedef struct dda_unet dda_unet;
 /* Network with cin input and cout output channels and level widths ch[0..3]
  * (each 1..64), He-uniform weights from seed; work on `cuda_stream`.  The
  * 3x3x3 convolutions (forward and input gradient) run as implicit GEMMs on the
- * tensor cores: mma.sync by default, or tcgen05 MMAs with tensor-memory
- * accumulators when the environment variable DDA_UNET_TC=1 is set at creation
- * (bounded waits; a wait that gives up is reported by dda_unet_check_fault).
- * The weight gradients use mma.sync in both modes. */
+ * tensor cores: tcgen05 MMAs with tensor-memory accumulators on halo tiles
+ * staged by TMA from a bfloat16 copy of the input (rows of at most 254 voxels;
+ * longer rows use mma.sync), or mma.sync throughout when the environment
+ * variable DDA_UNET_TC=0 is set at creation.  The tcgen05 kernel's mbarrier
+ * waits are bounded; a wait that gives up is reported by dda_unet_check_fault.
+ * The 1x1x1 head and the weight gradients use mma.sync in both modes. */
 DDA_API dda_status dda_unet_create(dda_unet **out, int device, void *cuda_stream, int cin, int cout, const int32_t ch[4],
                                    uint64_t seed);
 DDA_API void dda_unet_destroy(dda_unet *net);

@@ -1623,11 +1623,13 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
         if (!e.ok()) break;
         e = scale64(kv.b, false);
         if (!e.ok()) break;
-        // ask the inner solve for the reduction that reaches tol, but at least `inner`
+        // ask the inner solve for the reduction that reaches 0.8 tol, but at least `inner`: the true
+        // residual after an inner complex64 solve stays within a few percent of its recursive one,
+        // so 0.8 leaves the margin for one outer pass to end below tol (the true residual decides)
         double worst = 0;
         for (int b = 0; b < nrhs; ++b)
           worst = std::max(worst, (!masked[b] && rel[b] > o.tol) ? o.tol / rel[b] : 0.0);
-        const double itol = std::max(inner, 0.5 * worst);
+        const double itol = std::max(inner, 0.8 * worst);
         SolveStats s;
         e = krylov<float2>(c, o, kv, itol, budget, false, &s, t0, &timed_out);
         if (!e.ok()) break;

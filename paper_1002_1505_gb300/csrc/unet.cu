@@ -9,16 +9,22 @@
 // 3x3x3 zero-padded convolutions with ReLU, 2x2x2 average pooling, nearest
 // x2 upsampling, skips concatenated as [upsampled, skip].
 //
-// Convolutions are implicit GEMMs on the tensor cores (mma.sync m16n8k16,
-// bfloat16 operands, FP32 accumulation): the input activation (or incoming
-// gradient) is rounded to bfloat16 as it is loaded, weights are kept as an FP32
-// master copy and repacked to bfloat16 fragments after every update.
+// Convolutions are implicit GEMMs on the tensor cores (bfloat16 operands, FP32
+// accumulation): the input activation (or incoming gradient) is rounded to
+// bfloat16 as it is loaded, weights are kept as an FP32 master copy and repacked
+// to bfloat16 tiles after every update.  Two engines: tcgen05 MMAs on TMA-staged
+// halo tiles with tensor-memory accumulators, where each of the 27 taps is a
+// shifted shared-memory descriptor of the same staged tile (k_conv_tc, the
+// default), and mma.sync m16n8k16 with per-thread neighbour gathers (k_conv;
+// DDA_UNET_TC=0).  The 1x1x1 head and the weight gradients always use mma.sync.
 //   forward     y[v, co]  = sum_{tap, ci} x[v + tap, ci] W[tap, ci, co] + b[co]
 //   input grad  gx[v, ci] = sum_{tap, co} g[v - tap, co] W[tap, ci, co]   (same kernel, flipped
 //                           taps and transposed weights)
 //   weight grad gW[tap, ci, co] = sum_v x[v + tap, ci] g[v, co]            (voxels as the K axis,
 //                           per-chunk partials summed in a fixed order: deterministic)
 // AdamW (decoupled weight decay) updates the FP32 master parameters.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -157,18 +163,23 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const float* __restrict__
 }
 
 // ------------------------------------------------------------------ tcgen05 convolution
-// The same implicit GEMM on the fifth-generation tensor cores: a CTA of 128 threads owns 128
-// consecutive output voxels (the MMA's M = 128 rows) and accumulates D[128][NP] in tensor memory
-// over the 27 taps x ceil(cin/16) channel chunks (K = 16 per tcgen05.mma, kind::f16 with bf16
-// operands, FP32 accumulation).  Per (tap, chunk): each thread gathers its voxel's neighbour row of
-// 16 channels (rounded to bf16) into the A tile, NP * 2 threads copy the chunk's prepacked weights
-// into the B tile; both tiles are in the canonical no-swizzle K-major layout (8-row x 16-byte core
-// matrices, K neighbours 128 B apart, M/N neighbours 256 B apart).  Two tile buffers alternate: the
-// MMA of one chunk runs while the threads fill the next, and a buffer is refilled only after the
-// tcgen05.commit of its previous MMA has arrived on that buffer's mbarrier (bounded wait: a wait that
-// gives up sets the fault flag and the results are then invalid).  The epilogue reads the
-// accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. voxels), adds the bias,
-// applies ReLU and stores FP32.
+// The 3x3x3 implicit GEMM on the fifth-generation tensor cores.  A CTA owns a tile of Tz z planes
+// x Ty y rows x all X voxels of one sample.  Per 16-channel chunk, a TMA load brings the tile with
+// its one-voxel halo (zero outside the volume: the load starts at coordinate -1) from a bfloat16
+// channels-last copy of the input into shared memory, as two 8-channel halves in which staged
+// voxel s = (zz * (Ty+2) + yy) * (X+2) + xx sits at byte 16 s.  In that layout the rows of an
+// MMA's A operand are 16 bytes apart, so the K-major no-swizzle descriptor with an 8-row stride of
+// 128 bytes addresses 128 consecutive staged voxels from any start, and the operand of tap
+// (dz, dy, dx) is the output rows' operand moved by dz (Ty+2)(X+2) + dy (X+2) + dx rows: one
+// descriptor per tap, no data movement.  The GEMM's M axis runs over consecutive staged positions
+// from the first interior voxel, in tiles of 128; positions in the halo columns are computed and
+// discarded.  The chunk's weights for all taps come in with one bulk copy.  One thread issues the
+// loads and the 27 x (M tiles) MMAs of a chunk (kind::f16, bf16 operands, FP32 accumulators in
+// tensor memory, N = output channels rounded to 16); a tcgen05.commit on the chunk's "empty"
+// barrier releases its buffer, and two buffers let the next chunk's loads run under the current
+// chunk's MMAs.  Every mbarrier wait is bounded (a wait that gives up sets the fault flag and the
+// outputs are invalid).  The epilogue reads each M tile with tcgen05.ld (warp w owns rows 32w..),
+// adds the bias, applies ReLU and stores the interior voxels in FP32.
 namespace tc {
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -198,15 +209,14 @@ __device__ __forceinline__ void commit(uint64_t* bar) {
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-template <int NCOL>
-__device__ __forceinline__ void alloc(uint32_t* slot) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(slot)), "n"(NCOL)
+// ncol: a power of two in [32, 512]
+__device__ __forceinline__ void alloc(uint32_t* slot, uint32_t ncol) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(slot)), "r"(ncol)
                : "memory");
   asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
 }
-template <int NCOL>
-__device__ __forceinline__ void dealloc(uint32_t tmem) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(NCOL) : "memory");
+__device__ __forceinline__ void dealloc(uint32_t tmem, uint32_t ncol) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncol) : "memory");
 }
 // 16 consecutive 32-bit columns of this thread's TMEM lane
 __device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
@@ -220,112 +230,152 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
+// 5-D tiled TMA load (coordinates innermost first) into shared memory, completion counted on bar
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            int c4, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], "
+      "[%7];" ::"r"(saddr(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(saddr(bar))
+      : "memory");
+}
 }  // namespace tc
 
 constexpr int kTcThreads = 128;
 constexpr uint32_t kTcMaxPolls = 1u << 22;
 
-// wtc: per (tap, chunk) NP x 16 bf16 in the B-tile layout (NP * 2 blocks of 16 bytes)
+// tile geometry of the tcgen05 convolution (host-chosen)
+struct TcTile {
+  int Ty, Tz;          // y rows and z planes per CTA (all X voxels of a row)
+  int sx, sy, sz;      // staged extents X+2, Ty+2, Tz+2
+  int q_first;         // staged row of the first interior voxel (= the largest tap offset)
+  int n_mt;            // 128-row M tiles
+  int rows_alloc;      // staged rows per channel half (covers every row an MMA reads), multiple of 8
+  int stages;          // 1 or 2 chunk buffers
+  uint32_t stage_bytes;
+  uint32_t ncol;       // tensor-memory columns allocated (power of two >= n_mt * N, <= 512)
+};
+
+__host__ __device__ inline uint32_t tc_act_bytes(const TcTile& t) { return 2u * (uint32_t)t.rows_alloc * 16u; }
+
+// wpk: per (chunk, tap) NP x 16 bf16 in the B-tile layout, chunks outermost
 template <int NP>
-__global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float* __restrict__ x, int xs, int cin, int kc_n,
-                                                        const uint4* __restrict__ wtc, int taps, bool flip,
+__global__ void __launch_bounds__(kTcThreads) k_conv_tc(const __grid_constant__ CUtensorMap tmap,
+                                                        const uint4* __restrict__ wpk, int kc_n, bool flip,
                                                         const float* __restrict__ bias, float* __restrict__ y, int ys,
-                                                        int cout, bool relu, Dims d, int64_t V,
+                                                        int cout, bool relu, Dims d, TcTile tl,
                                                         unsigned int* __restrict__ fault) {
   static_assert(NP % 16 == 0 && NP >= 16 && NP <= 128, "N must be a multiple of 16 in [16, 128]");
-  constexpr int NCOL = NP <= 32 ? 32 : (NP <= 64 ? 64 : 128);
-  __shared__ __align__(128) uint4 sA[2][256];        // 128 rows x 16 bf16
-  __shared__ __align__(128) uint4 sB[2][NP * 2];     // NP rows x 16 bf16
-  __shared__ __align__(8) uint64_t bar[2];
-  __shared__ uint32_t tmem_slot;
+  extern __shared__ __align__(1024) unsigned char smem_tc[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_tc);  // [2]: a chunk's loads have landed
+  uint64_t* empty = full + 2;                             // [2]: a chunk's MMAs have read its buffer
+  uint64_t* done = full + 4;                              // every MMA has finished
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + 5);
+  unsigned char* buf0 = smem_tc + 1024;
   const int tid = threadIdx.x, warp = tid >> 5;
-  if (warp == 0) tc::alloc<NCOL>(&tmem_slot);
+  const int ty0 = blockIdx.x * tl.Ty, tz0 = blockIdx.y * tl.Tz, b = blockIdx.z;
+  const uint32_t half_bytes = (uint32_t)tl.rows_alloc * 16u;
+  const uint32_t act_bytes = tc_act_bytes(tl);
+  const uint32_t w_bytes = (uint32_t)kTaps * NP * 32u;
+  const uint32_t box_bytes = 16u * (uint32_t)(tl.sx * tl.sy * tl.sz);
+  const int plane = tl.sx * tl.sy;
+  if (warp == 0) tc::alloc(tmem_slot, tl.ncol);
   if (tid == 0) {
-    bulk::mbar_init(&bar[0], 1);
-    bulk::mbar_init(&bar[1], 1);
+    for (int i = 0; i < 5; ++i) bulk::mbar_init(&full[i], 1);
   }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-  const uint32_t tmem = tmem_slot;
-  const int64_t v = (int64_t)blockIdx.x * 128 + tid;  // this thread's A row and output voxel
-  const int niter = taps * kc_n;
-  uint32_t phase[2] = {0u, 0u};
-  int waited[2] = {0, 0};
+  const uint32_t tmem = *tmem_slot;
   bool ok = true;
-  // A-tile byte offset of this row: core matrix (row / 8) 256 B apart, row in it 16 B apart
-  const int arow = (tid >> 3) * 16 + (tid & 7);  // in uint4 units: (row/8)*256 B + (row%8)*16 B
-  for (int it = 0; it < niter; ++it) {
-    const int buf = it & 1;
-    if (it >= 2) {  // the MMA that last read this buffer (iteration it - 2) has finished
-      ok = bulk::mbar_wait(&bar[buf], phase[buf], kTcMaxPolls, fault) && ok;
-      phase[buf] ^= 1u;
-      ++waited[buf];
-    }
-    const int tap = it / kc_n, kc = it - tap * kc_n;
-    const int64_t nb = (v < V) ? neighbour(v, d, tap, taps, flip) : -1;
-    const float* xr = nb >= 0 ? x + nb * xs : nullptr;
-    uint32_t pk[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int c = kc * 16 + 2 * q;
-      const float lo = (xr && c < cin) ? __ldg(xr + c) : 0.f;
-      const float hi = (xr && c + 1 < cin) ? __ldg(xr + c + 1) : 0.f;
-      pk[q] = pack_bf16(lo, hi);
-    }
-    sA[buf][arow] = make_uint4(pk[0], pk[1], pk[2], pk[3]);      // K elements 0..7 (core column 0)
-    sA[buf][arow + 8] = make_uint4(pk[4], pk[5], pk[6], pk[7]);  // K elements 8..15 (128 B further)
-    for (int q = tid; q < NP * 2; q += kTcThreads) sB[buf][q] = __ldg(wtc + (int64_t)it * NP * 2 + q);
-    bulk::fence_smem_to_async();
-    __syncthreads();
-    if (tid == 0) {
+  if (tid == 0) {
+    uint32_t fph[2] = {0u, 0u}, eph[2] = {0u, 0u};
+    for (int kc = 0; kc < kc_n; ++kc) {
+      const int s = (tl.stages == 2) ? (kc & 1) : 0;
+      unsigned char* act = buf0 + (size_t)s * tl.stage_bytes;
+      unsigned char* wb = act + act_bytes;
+      if (kc >= tl.stages) {  // the MMAs of chunk kc - stages have read this buffer
+        ok = bulk::mbar_wait(&empty[s], eph[s], kTcMaxPolls, fault) && ok;
+        eph[s] ^= 1u;
+      }
+      bulk::mbar_arrive_expect_tx(&full[s], 2u * box_bytes + w_bytes);
+      tc::tma_load_5d(act, &tmap, kc * 16, -1, ty0 - 1, tz0 - 1, b, &full[s]);
+      tc::tma_load_5d(act + half_bytes, &tmap, kc * 16 + 8, -1, ty0 - 1, tz0 - 1, b, &full[s]);
+      bulk::load_g2s(wb, wpk + (int64_t)kc * kTaps * NP * 2, w_bytes, &full[s]);
+      ok = bulk::mbar_wait(&full[s], fph[s], kTcMaxPolls, fault) && ok;
+      fph[s] ^= 1u;
       tc::fence_after();
-      tc::mma(tmem, tc::desc(&sA[buf][0], 128, 256), tc::desc(&sB[buf][0], 128, 256), tc::idesc_bf16(NP),
-              it > 0 ? 1u : 0u);
-      tc::commit(&bar[buf]);
+      for (int mt = 0; mt < tl.n_mt; ++mt)
+        for (int t = 0; t < kTaps; ++t) {
+          const int tt = flip ? (kTaps - 1 - t) : t;
+          const int off = (tt / 9 - 1) * plane + ((tt / 3) % 3 - 1) * tl.sx + (tt % 3 - 1);
+          const uint32_t row = (uint32_t)(tl.q_first + mt * 128 + off);
+          tc::mma(tmem + (uint32_t)(mt * NP), tc::desc(act + (size_t)row * 16u, half_bytes, 128),
+                  tc::desc(wb + (size_t)t * NP * 32u, 128, 256), tc::idesc_bf16(NP), (kc > 0 || t > 0) ? 1u : 0u);
+        }
+      tc::commit(&empty[s]);
     }
+    tc::commit(done);
   }
-  // the last one or two MMAs
-  for (int b = 0; b < 2; ++b) {
-    const int issued = (niter + 1 - b) / 2;  // iterations with it & 1 == b
-    while (waited[b] < issued) {
-      ok = bulk::mbar_wait(&bar[b], phase[b], kTcMaxPolls, fault) && ok;
-      phase[b] ^= 1u;
-      ++waited[b];
-    }
-  }
+  ok = bulk::mbar_wait(done, 0u, kTcMaxPolls, fault) && ok;
   tc::fence_after();
-  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  for (int mt = 0; mt < tl.n_mt; ++mt) {
+    const int q = tl.q_first + mt * 128 + tid;
+    const int zz = q / plane, r = q - zz * plane;
+    const int yy = r / tl.sx, xx = r - yy * tl.sx;
+    const int z = tz0 + zz - 1, yv = ty0 + yy - 1, x = xx - 1;
+    const bool valid = ok && zz >= 1 && zz <= tl.Tz && yy >= 1 && yy <= tl.Ty && xx >= 1 && xx <= d.X && z < d.Z &&
+                       yv < d.Y;
+    float* yo = y + ((((int64_t)b * d.Z + (valid ? z : 0)) * d.Y + (valid ? yv : 0)) * d.X + (valid ? x : 0)) * ys;
 #pragma unroll
-  for (int c0 = 0; c0 < NP; c0 += 16) {
-    float acc[16];
-    tc::ld16(lane_base + (uint32_t)c0, acc);
-    if (v < V && ok) {
+    for (int c0 = 0; c0 < NP; c0 += 16) {
+      float acc[16];
+      tc::ld16(tmem + lane_base + (uint32_t)(mt * NP + c0), acc);
+      if (valid) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int co = c0 + j;
-        if (co < cout) {
-          float val = acc[j] + (bias ? bias[co] : 0.f);
-          if (relu) val = fmaxf(val, 0.f);
-          y[v * ys + co] = val;
+        for (int j = 0; j < 16; ++j) {
+          const int co = c0 + j;
+          if (co < cout) {
+            float val = acc[j] + (bias ? bias[co] : 0.f);
+            if (relu) val = fmaxf(val, 0.f);
+            yo[co] = val;
+          }
         }
       }
     }
   }
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::dealloc<NCOL>(tmem);
+  if (warp == 0) tc::dealloc(tmem, tl.ncol);
 }
 
-// pack W[tap][ci][co] (FP32) into the tcgen05 B tiles: per (tap, chunk) element (n, k) at bf16 offset
-// ((n / 8) * 2 + k / 8) * 64 + (n % 8) * 8 + k % 8; forward n = co, k = ci; transposed n = ci, k = co
+// bfloat16 channels-last copy of channels [0, cin) of x (xs per voxel), cpad channels (zeros above
+// cin): the tcgen05 convolution's TMA source.  One thread per 8 channels of a voxel.
+__global__ void k_to_bf16(const float* __restrict__ x, int xs, int cin, int cpad, int64_t V, uint4* __restrict__ out) {
+  const int g8 = cpad / 8;
+  const int64_t total = V * g8;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = i / g8;
+    const int c = (int)(i - v * g8) * 8;
+    const float* src = x + v * xs;
+    float f[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) f[j] = (c + j < cin) ? __ldg(src + c + j) : 0.f;
+    out[i] = make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]), pack_bf16(f[6], f[7]));
+  }
+}
+
+// pack W[tap][ci][co] (FP32) into the tcgen05 B tiles, blocks ordered (chunk, tap): per block element
+// (n, k) at bf16 offset ((n / 8) * 2 + k / 8) * 64 + (n % 8) * 8 + k % 8; forward n = co, k = ci;
+// transposed n = ci, k = co
 __global__ void k_pack_tc(const float* __restrict__ w, int taps, int cin, int cout, int kc_n, int np, bool transpose,
                           __nv_bfloat16* __restrict__ out) {
   const int64_t total = (int64_t)taps * kc_n * np * 16;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int e = (int)(i % (np * 16));
     const int64_t blk = i / (np * 16);
-    const int kc = (int)(blk % kc_n), tap = (int)(blk / kc_n);
+    const int tap = (int)(blk % taps), kc = (int)(blk / taps);
     const int core = e / 64, in = e % 64;
     const int n = (core / 2) * 8 + in / 8, k = kc * 16 + (core % 2) * 8 + in % 8;
     float val = 0.f;
@@ -667,8 +717,10 @@ struct dda_unet {
   size_t part_bytes = 0;
   double* lpart = nullptr;
   double* h_loss = nullptr;
-  bool use_tc = false;                 // convolutions on tcgen05 (DDA_UNET_TC=1) instead of mma.sync
+  bool use_tc = true;                  // convolutions on tcgen05 (DDA_UNET_TC=0: mma.sync throughout)
   unsigned int* d_fault = nullptr;     // set when a bounded tensor-core wait gave up
+  uint4* xb = nullptr;                 // bfloat16 channels-last copy of a tcgen05 convolution's input
+  size_t xb_bytes = 0;
 };
 
 namespace {
@@ -708,6 +760,95 @@ Err repack(dda_unet* n) {
   return Err::Ok();
 }
 
+// Tile of the tcgen05 convolution for a volume d (B samples) and N = np output channels: the (Ty, Tz)
+// with the least modelled time per SM, counting for each 16-channel chunk the bytes a CTA loads
+// (activation tile with halo, both halves, plus the chunk's weights for 27 taps) and its MMAs
+// (27 per 128-row M tile), overlapped when two buffers or two CTAs per SM fit.  false when no tile
+// fits (rows longer than 254 voxels): the caller uses the mma.sync kernel.
+bool tc_tile(const dda::nn::Dims& d, int B, int np, dda::nn::TcTile* out) {
+  constexpr double kSmem = 227.0 * 1024.0, kBytesPerNs = 60.0, kMmaNs = 16.0;
+  const int X = d.X;
+  if (X + 2 > 256) return false;
+  double best = 1e300;
+  bool found = false;
+  for (int Tz = 1; Tz <= std::min(d.Z, 16); ++Tz)
+    for (int Ty = 1; Ty <= std::min(d.Y, 64); ++Ty) {
+      dda::nn::TcTile t{};
+      t.Ty = Ty;
+      t.Tz = Tz;
+      t.sx = X + 2;
+      t.sy = Ty + 2;
+      t.sz = Tz + 2;
+      const int plane = t.sx * t.sy;
+      t.q_first = plane + t.sx + 1;
+      const int q_last = (Tz * t.sy + Ty) * t.sx + X;
+      t.n_mt = (q_last - t.q_first + 1 + 127) / 128;
+      if (t.n_mt * np > 512) continue;
+      t.ncol = 32;
+      while ((int)t.ncol < t.n_mt * np) t.ncol *= 2;
+      t.rows_alloc = (2 * t.q_first + t.n_mt * 128 + 7) / 8 * 8;
+      const double act = 2.0 * t.rows_alloc * 16.0, w = 27.0 * np * 32.0;
+      t.stage_bytes = (uint32_t)((act + w + 1023) / 1024) * 1024u;
+      if (1024.0 + t.stage_bytes > kSmem) continue;
+      t.stages = (1024.0 + 2.0 * t.stage_bytes <= kSmem) ? 2 : 1;
+      const int cps = std::max(1, std::min((int)(kSmem / (1024.0 + t.stages * (double)t.stage_bytes)),
+                                           (int)(512 / t.ncol)));
+      const double load = (2.0 * 16.0 * t.sx * t.sy * t.sz + w) / kBytesPerNs;
+      const double mma = t.n_mt * 27.0 * kMmaNs * std::max(1.0, np / 64.0);
+      const double per_chunk = (t.stages == 2 || cps >= 2) ? std::max(load, mma) : load + mma;
+      const double ctas = (double)B * ((d.Y + Ty - 1) / Ty) * ((d.Z + Tz - 1) / Tz);
+      const double waves = std::ceil(ctas / (152.0 * cps));
+      const double cost = waves * cps * per_chunk;
+      if (cost < best) {
+        best = cost;
+        *out = t;
+        found = true;
+      }
+    }
+  return found;
+}
+
+// the driver's tensor-map encoder, looked up once
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// 5-D map of the bfloat16 activations [B][Z][Y][X][cpad]: box 8 channels x (X+2) x (Ty+2) x (Tz+2) x 1
+Err encode_act_map(CUtensorMap* m, const void* base, int cpad, const dda::nn::Dims& d, int B,
+                   const dda::nn::TcTile& t) {
+  auto enc = tmap_encoder();
+  if (!enc) return Err::make(DDA_ECUDA, "cuTensorMapEncodeTiled is not available");
+  const cuuint64_t dims[5] = {(cuuint64_t)cpad, (cuuint64_t)d.X, (cuuint64_t)d.Y, (cuuint64_t)d.Z, (cuuint64_t)B};
+  const cuuint64_t strides[4] = {(cuuint64_t)cpad * 2, (cuuint64_t)cpad * 2 * d.X, (cuuint64_t)cpad * 2 * d.X * d.Y,
+                                 (cuuint64_t)cpad * 2 * d.X * d.Y * d.Z};
+  const cuuint32_t box[5] = {8u, (cuuint32_t)t.sx, (cuuint32_t)t.sy, (cuuint32_t)t.sz, 1u};
+  const cuuint32_t estr[5] = {1u, 1u, 1u, 1u, 1u};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return Err::make(DDA_ECUDA, "tensor-map encoding failed");
+  return Err::Ok();
+}
+
+// opt k_conv_tc<NP> in to the full 227 KB of dynamic shared memory (once per instantiation)
+template <int NP>
+Err tc_smem_optin() {
+  static bool done = false;
+  if (!done) {
+    DDA_CU(cudaFuncSetAttribute(dda::nn::k_conv_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    done = true;
+  }
+  return Err::Ok();
+}
+
 // y = conv(x) for layer L; x has xs channels (uses the first cin), y gets ys channels (writes first cout)
 Err conv(dda_unet* n, const dda_unet::Layer& L, const float* x, int xs, float* y, int ys, bool relu, dda::nn::Dims d,
          int B, bool transposed) {
@@ -719,23 +860,42 @@ Err conv(dda_unet* n, const dda_unet::Layer& L, const float* x, int xs, float* y
   const int cout = transposed ? L.cin : L.cout;
   const uint2* w = transposed ? L.wt : L.wp;
   const float* bias = transposed ? nullptr : n->p + L.boff;
-  if (n->use_tc) {
+  if (n->use_tc && L.taps == dda::nn::kTaps) {
     const int np = np16(cout);
-    const uint4* wt = reinterpret_cast<const uint4*>(transposed ? L.wttc : L.wtc);
-    const int tblocks = (int)((V + 127) / 128);
-    switch (np) {
-#define CASE(NP)                                                                                                      \
-  case NP:                                                                                                            \
-    dda::nn::k_conv_tc<NP><<<tblocks, dda::nn::kTcThreads, 0, n->stream>>>(x, xs, cin, kc_n, wt, L.taps, transposed, \
-                                                                           bias, y, ys, cout, relu, d, V, n->d_fault); \
+    dda::nn::TcTile tl;
+    if (tc_tile(d, B, np, &tl)) {
+      const int cpad = kc_n * 16;
+      const size_t need = sizeof(uint16_t) * (size_t)V * cpad;
+      if (need > n->xb_bytes) {
+        if (n->xb) cudaFree(n->xb);
+        n->xb = nullptr;
+        n->xb_bytes = 0;
+        DDA_CU(cudaMalloc((void**)&n->xb, need));
+        n->xb_bytes = need;
+      }
+      const int64_t items = V * (cpad / 8);
+      dda::nn::k_to_bf16<<<dda::nn::blocks_for(items), 256, 0, n->stream>>>(x, xs, cin, cpad, V, n->xb);
+      DDA_CU(cudaGetLastError());
+      CUtensorMap tmap;
+      DDA_TRY(encode_act_map(&tmap, n->xb, cpad, d, B, tl));
+      const uint4* wt = reinterpret_cast<const uint4*>(transposed ? L.wttc : L.wtc);
+      const dim3 grid((unsigned)((d.Y + tl.Ty - 1) / tl.Ty), (unsigned)((d.Z + tl.Tz - 1) / tl.Tz), (unsigned)B);
+      const size_t smem = 1024 + (size_t)tl.stages * tl.stage_bytes;
+      switch (np) {
+#define CASE(NP)                                                                                                  \
+  case NP:                                                                                                        \
+    DDA_TRY(tc_smem_optin<NP>());                                                                                 \
+    dda::nn::k_conv_tc<NP><<<grid, dda::nn::kTcThreads, smem, n->stream>>>(tmap, wt, kc_n, transposed, bias, y, ys, \
+                                                                           cout, relu, d, tl, n->d_fault);        \
     break;
-      CASE(16) CASE(32) CASE(48) CASE(64) CASE(80) CASE(96) CASE(112) CASE(128)
+        CASE(16) CASE(32) CASE(48) CASE(64) CASE(80) CASE(96) CASE(112) CASE(128)
 #undef CASE
-      default: return Err::make(DDA_EUNSUPPORTED, "layer wider than 128 channels");
+        default: return Err::make(DDA_EUNSUPPORTED, "layer wider than 128 channels");
+      }
+      DDA_CU(cudaGetLastError());
+      dda::add_launches(2);
+      return Err::Ok();
     }
-    DDA_CU(cudaGetLastError());
-    dda::add_launches(1);
-    return Err::Ok();
   }
   switch (nt_n) {
 #define CASE(NT)                                                                                                   \
@@ -988,7 +1148,7 @@ dda_status dda_unet_create(dda_unet** out, int device, void* stream, int cin, in
             cudaMallocHost((void**)&n->h_loss, sizeof(double) * 2048) == cudaSuccess;
   {
     const char* f = std::getenv("DDA_UNET_TC");
-    n->use_tc = f && std::atoi(f) == 1;
+    n->use_tc = !(f && std::atoi(f) == 0);
   }
   ok = ok && cudaMalloc((void**)&n->d_fault, sizeof(unsigned int)) == cudaSuccess &&
        cudaMemset(n->d_fault, 0, sizeof(unsigned int)) == cudaSuccess;
@@ -1033,6 +1193,7 @@ void dda_unet_destroy(dda_unet* n) {
   if (n->lpart) cudaFree(n->lpart);
   if (n->h_loss) cudaFreeHost(n->h_loss);
   if (n->d_fault) cudaFree(n->d_fault);
+  if (n->xb) cudaFree(n->xb);
   delete n;
 }
 

@@ -658,6 +658,46 @@ def test_multi_composition_targets(D, aniso):
             assert q[b, i] == pytest.approx(qref[b][key], rel=1e-4), (aniso, key, b)
 
 
+@pytest.mark.parametrize("sched", ["plane512", "fast5"])
+def test_rows_with_gaps_and_empty_rows(D, monkeypatch, sched):
+    """A site list whose box rows are single runs, several runs (holes) or empty: the x passes read
+    single-run rows through their run descriptor and the others through the box map; the product
+    against the oracle's direct sum on the 3-pass and the 5-pass schedules."""
+    monkeypatch.setenv("DDA_SCHEDULE", sched)
+    rng = np.random.default_rng(71)
+    box = (11, 9, 13)
+    full = np.stack(np.meshgrid(np.arange(box[0]), np.arange(box[1]), np.arange(box[2]), indexing="ij"),
+                    axis=-1).reshape(-1, 3)
+    keep = rng.random(len(full)) < 0.6                 # holes: most rows have several runs
+    keep &= ~((full[:, 1] == 4) & (full[:, 2] % 3 == 0))  # some rows empty
+    solid = (full[:, 1] == 2) | (full[:, 2] == 5)      # some rows one run
+    keep |= solid & (full[:, 0] >= 2) & (full[:, 0] < 9)
+    ijk = full[keep].astype(np.int32)
+    ijk = ijk[rng.permutation(len(ijk))]               # any order: both sides sort x-fastest
+    t = o_targets.from_sites(ijk, origin=(0.0, 0.0, 0.0))
+    m = 1.5 + 0.1j
+    ori = W.uniform_orientations(2, 72)
+    prob = odda.build_problem(None, None, m, 2.0, "GKDLDR", ori, target=t)
+    ctx = D.Context(0)
+    ctx.dda_setup_target(ijk, origin=(0.0, 0.0, 0.0))
+    sites, _ = ctx.dda_get_sites()
+    assert np.array_equal(sites - sites.min(axis=0), t.ijk)
+    ctx.dda_set_incident(prob.kd, ori, [[0, 0], [1, 0], [0, 0]], 2)
+    ctx.dda_build_green_fft((24, 32, 32))   # (Py, Pz) = (32, 32): a plane pair with compile-time kernels
+    ctx.dda_set_polarizability("GKDLDR", [m])
+    for dt, tol in ((torch.complex128, 1e-12), (torch.complex64, 1e-5)):
+        p = _rand_p(ctx.nrhs, ctx.n, 73, dt)
+        ap = torch.empty_like(p)
+        ctx.dda_matvec(p, ap)
+        torch.cuda.synchronize()
+        pn = p.cpu().numpy().astype(np.complex128)
+        got = ap.cpu().numpy().astype(np.complex128)
+        for b in range(ctx.nrhs):
+            ref = odda.apply_a(prob, b, pn[b], "direct")
+            assert np.linalg.norm(got[b] - ref) / np.linalg.norm(ref) <= tol, (sched, dt, b)
+    assert D.dda_schedule_info(ctx, D.DDA_C64)[:2] == ((3, 1) if sched == "plane512" else (5, 1))
+
+
 def test_warm_start_from_solution_needs_no_iterations(D):
     w = W.SPHERE12
     prob, ps, _ = _oracle_q(w, tol=1e-12)

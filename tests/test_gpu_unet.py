@@ -46,7 +46,14 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def test_forward_matches_oracle(D):
+@pytest.fixture(params=["tcgen05", "mma_sync"])
+def engine(request, monkeypatch):
+    """Networks created in the test use the tcgen05 convolutions (default) or mma.sync throughout."""
+    monkeypatch.setenv("DDA_UNET_TC", "1" if request.param == "tcgen05" else "0")
+    return request.param
+
+
+def test_forward_matches_oracle(D, engine):
     net = D.UNet(0, None, CIN, COUT, CH, seed=11)
     theta = net.dda_unet_get_params().astype(np.float64)
     x, _, _ = _data(1)
@@ -58,7 +65,7 @@ def test_forward_matches_oracle(D):
     assert _rel(yg.cpu().numpy(), ref) <= 2e-3
 
 
-def test_gradients_match_oracle(D):
+def test_gradients_match_oracle(D, engine):
     net = D.UNet(0, None, CIN, COUT, CH, seed=12)
     theta = net.dda_unet_get_params().astype(np.float64)
     x, t, mask = _data(2)
@@ -77,7 +84,7 @@ def test_gradients_match_oracle(D):
         o += nw + b
 
 
-def test_gradients_match_oracle_default_widths(D):
+def test_gradients_match_oracle_default_widths(D, engine):
     """The warm start's own widths: wide concatenated inputs use 10 n-tiles in the input-gradient GEMM."""
     cin, cout, ch, dims = 9, 6, (12, 24, 32, 48), (8, 8, 16)
     net = D.UNet(0, None, cin, cout, ch, seed=21)
@@ -272,22 +279,45 @@ def test_tcgen05_forward_matches_oracle_and_mma_sync(D, tc_mode, monkeypatch):
     assert _rel(y_tc.cpu().numpy(), y_ms.cpu().numpy()) <= 1e-3
 
 
-def test_tcgen05_gradients_match_oracle(D, tc_mode):
-    """Loss and gradients with the forward and input-gradient convolutions on tcgen05."""
-    net = D.UNet(0, None, CIN, COUT, CH, seed=12)
-    theta = net.dda_unet_get_params().astype(np.float64)
-    x, t, mask = _data(2)
-    loss = net.dda_unet_loss_grad(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(),
-                                  torch.from_numpy(mask).cuda(), DIMS)
-    torch.cuda.synchronize()
-    net.dda_unet_check_fault()
-    g = net.dda_unet_get_params(which=1).astype(np.float64)
-    Lr, gr = OU.loss_and_grad(theta, x.astype(np.float64), t.astype(np.float64), mask.astype(np.float64), CIN, COUT,
-                              CH, quant=True)
-    assert loss == pytest.approx(Lr, rel=1e-4)
-    o = 0
-    for taps, a, b in OU.layer_shapes(CIN, COUT, CH):
-        nw = taps * a * b
-        assert _rel(g[o:o + nw], gr[o:o + nw]) <= 5e-3, ("W", o)
-        assert _rel(g[o + nw:o + nw + b], gr[o + nw:o + nw + b]) <= 5e-3, ("b", o)
-        o += nw + b
+def test_tcgen05_long_rows_and_ragged_tiles(D, monkeypatch):
+    """Rows of 128 voxels (staged rows of 130 with the halo, several 128-row M tiles per CTA) and y / z
+    extents that the CTA tiles do not divide: the tcgen05 forward pass against the oracle and against
+    the mma.sync pass.  On volumes this large some bfloat16 roundings of inner activations differ
+    between FP32 (both GPU engines) and FP64 (oracle) sums, and the oracle distance of both engines
+    grows to ~3e-3 (measured: 2.66e-3 for both on 40 x 56 x 24); the engines stay within 1e-3 of
+    each other and the tcgen05 one no farther from the oracle than the mma.sync one."""
+    for dims in ((128, 24, 8), (40, 56, 24)):
+        rng = np.random.default_rng(dims[0])
+        x = rng.standard_normal((1, dims[2], dims[1], dims[0], CIN)).astype(np.float32)
+        out = []
+        for mode in ("1", "0"):
+            monkeypatch.setenv("DDA_UNET_TC", mode)
+            net = D.UNet(0, None, CIN, COUT, CH, seed=5)
+            yv = torch.empty(x.shape[:4] + (COUT,), dtype=torch.float32, device="cuda")
+            net.dda_unet_forward(torch.from_numpy(x).cuda(), yv, dims)
+            torch.cuda.synchronize()
+            net.dda_unet_check_fault()
+            theta = net.dda_unet_get_params().astype(np.float64)
+            out.append(yv.cpu().numpy())
+            net.close()
+        ref = OU.forward(theta, x.astype(np.float64), CIN, COUT, CH, quant=True)
+        e_tc, e_ms = _rel(out[0], ref), _rel(out[1], ref)
+        assert e_tc <= 5e-3 and e_tc <= 1.2 * e_ms + 1e-5, (dims, e_tc, e_ms)
+        assert _rel(out[0], out[1]) <= 1e-3, dims
+    cin, cout, ch = 9, 6, (16, 32, 48, 64)
+    for dims in ((128, 24, 8), (40, 56, 24)):
+        rng = np.random.default_rng(dims[0])
+        x = rng.standard_normal((1, dims[2], dims[1], dims[0], cin)).astype(np.float32)
+        xg = torch.from_numpy(x).cuda()
+        out = []
+        for mode in ("1", "0"):
+            monkeypatch.setenv("DDA_UNET_TC", mode)
+            net = D.UNet(0, None, cin, cout, ch, seed=3)
+            yv = torch.empty(x.shape[:4] + (cout,), dtype=torch.float32, device="cuda")
+            net.dda_unet_forward(xg, yv, dims)
+            torch.cuda.synchronize()
+            net.dda_unet_check_fault()
+            out.append(yv.cpu().numpy())
+            net.close()
+        assert np.isfinite(out[0]).all()
+        assert _rel(out[0], out[1]) <= 3e-3, dims

@@ -669,13 +669,26 @@ __global__ void __launch_bounds__(256) k_y_rows(Geom g, C* __restrict__ work, co
 // ------------------------------------------------------------------ 5-pass: z columns with Ghat
 // grid (nrhs, ceil(py/G), px): the right-hand sides of one Ghat tile are
 // neighbours in launch order, so a tile is read from HBM once and then hits L2
-// for the other right-hand sides.  smem: tw[PZ] | s[PZ*3][G]
+// for the other right-hand sides.  smem: tw[PZ] | s[PZ*3][G] with zcols_pad() spare elements after
+// each pass-B sub-block of LB positions: in pass B a warp touches G consecutive columns of several
+// sub-blocks at once, and for complex64 with G = 8 and an even LB the unpadded sub-blocks all start
+// on the same shared-memory bank, which doubles the wavefronts of every such warp access.
 // RFUSE: pass B, the Ghat multiply and the inverse pass B of all three components in registers
 // even for long sub-blocks (one item per thread: NT = G * 2 * RA threads, up to 3 CTAs per SM),
 // which halves the shared-memory traffic of the column pass at the cost of occupancy.
+template <typename C, int PZ, int G>
+constexpr int zcols_pad() {
+  return (sizeof(C) == 8 && G == 8 && Shape<PZ>::LB % 2 == 0) ? 8 : 0;
+}
+template <typename C, int PZ, int G>
+constexpr size_t zcols_smem_elems() {
+  return (size_t)PZ + (size_t)PZ * 3 * G + (size_t)2 * Shape<PZ>::RA * zcols_pad<C, PZ, G>();
+}
+
 template <typename C, int PZ, int G, int NT = 256, bool RFUSE = false>
 __global__ void __launch_bounds__(NT, RFUSE ? 3 : 1) k_z_cols(Geom g, MvData<C> d) {
   constexpr int RA = Shape<PZ>::RA, LB = Shape<PZ>::LB, H = Shape<PZ>::H;
+  constexpr int P = zcols_pad<C, PZ, G>();  // spare elements after each sub-block
   constexpr bool kFuse = RFUSE || (LB * sizeof(C) <= 96);
   pdl_begin();
   extern __shared__ unsigned char smem_raw[];
@@ -704,7 +717,7 @@ __global__ void __launch_bounds__(NT, RFUSE ? 3 : 1) k_z_cols(Geom g, MvData<C> 
 #pragma unroll
     for (int bb = 0; bb < 2; ++bb)
 #pragma unroll
-      for (int k = 0; k < RA; ++k) s[((bb * H + n1 + LB * k) * 3 + c) * G + gg] = o[bb * RA + k];
+      for (int k = 0; k < RA; ++k) s[((bb * H + n1 + LB * k) * 3 + c) * G + gg + (bb * RA + k) * P] = o[bb * RA + k];
   }
   __syncthreads();
   const C* gk = d.ghat + (int64_t)kx * PZ * py * 6;
@@ -715,7 +728,7 @@ __global__ void __launch_bounds__(NT, RFUSE ? 3 : 1) k_z_cols(Geom g, MvData<C> 
       C v0[LB], v1[LB], v2[LB];
 #pragma unroll
       for (int e = 0; e < LB; ++e) {
-        const C* q = s + ((blk * LB + e) * 3) * G + gg;
+        const C* q = s + ((blk * LB + e) * 3) * G + gg + blk * P;
         v0[e] = q[0];
         v1[e] = q[G];
         v2[e] = q[2 * G];
@@ -732,7 +745,7 @@ __global__ void __launch_bounds__(NT, RFUSE ? 3 : 1) k_z_cols(Geom g, MvData<C> 
       f2::passB_inv<PZ>(v2, tw);
 #pragma unroll
       for (int e = 0; e < LB; ++e) {
-        C* q = s + ((blk * LB + e) * 3) * G + gg;
+        C* q = s + ((blk * LB + e) * 3) * G + gg + blk * P;
         q[0] = v0[e];
         q[G] = v1[e];
         q[2 * G] = v2[e];
@@ -745,10 +758,10 @@ __global__ void __launch_bounds__(NT, RFUSE ? 3 : 1) k_z_cols(Geom g, MvData<C> 
       const int c = r % 3, blk = r / 3;
       C v[LB];
 #pragma unroll
-      for (int e = 0; e < LB; ++e) v[e] = s[((blk * LB + e) * 3 + c) * G + gg];
+      for (int e = 0; e < LB; ++e) v[e] = s[((blk * LB + e) * 3 + c) * G + gg + blk * P];
       f2::passB_fwd<PZ>(v, tw);
 #pragma unroll
-      for (int e = 0; e < LB; ++e) s[((blk * LB + e) * 3 + c) * G + gg] = v[e];
+      for (int e = 0; e < LB; ++e) s[((blk * LB + e) * 3 + c) * G + gg + blk * P] = v[e];
     }
     __syncthreads();
     // Ghat multiply: each thread's Ghat records come from L2 (HBM once per batch); the loads of
@@ -769,7 +782,7 @@ __global__ void __launch_bounds__(NT, RFUSE ? 3 : 1) k_z_cols(Geom g, MvData<C> 
         if (!ok[u]) continue;
         const int i = i0 + u * blockDim.x;
         const int gg = i % G, kz = i / G;
-        C* q = s + (kz * 3) * G + gg;
+        C* q = s + (kz * 3) * G + gg + (kz / LB) * P;
         C v0 = q[0], v1 = q[G], v2 = q[2 * G];
         gmul3_r(gv[u], v0, v1, v2);
         q[0] = v0;
@@ -784,10 +797,10 @@ __global__ void __launch_bounds__(NT, RFUSE ? 3 : 1) k_z_cols(Geom g, MvData<C> 
       const int c = r % 3, blk = r / 3;
       C v[LB];
 #pragma unroll
-      for (int e = 0; e < LB; ++e) v[e] = s[((blk * LB + e) * 3 + c) * G + gg];
+      for (int e = 0; e < LB; ++e) v[e] = s[((blk * LB + e) * 3 + c) * G + gg + blk * P];
       f2::passB_inv<PZ>(v, tw);
 #pragma unroll
-      for (int e = 0; e < LB; ++e) s[((blk * LB + e) * 3 + c) * G + gg] = v[e];
+      for (int e = 0; e < LB; ++e) s[((blk * LB + e) * 3 + c) * G + gg + blk * P] = v[e];
     }
   }
   __syncthreads();
@@ -801,7 +814,7 @@ __global__ void __launch_bounds__(NT, RFUSE ? 3 : 1) k_z_cols(Geom g, MvData<C> 
 #pragma unroll
     for (int bb = 0; bb < 2; ++bb)
 #pragma unroll
-      for (int k = 0; k < RA; ++k) v[bb * RA + k] = s[((bb * H + n1 + LB * k) * 3 + c) * G + gg];
+      for (int k = 0; k < RA; ++k) v[bb * RA + k] = s[((bb * H + n1 + LB * k) * 3 + c) * G + gg + (bb * RA + k) * P];
     f2::passA_inv<PZ, false>(v, n1, tw, lo, (C*)nullptr);
     if (ky < py) {
 #pragma unroll
@@ -896,7 +909,12 @@ size_t yrows_fast_smem(const Geom& g) {
 }
 template <typename C>
 size_t zcols_fast_smem(const Geom& g) {
-  return sizeof(C) * ((size_t)g.pz + (size_t)g.pz * 3 * zcols_g_rt(sizeof(C), g.pz));
+  switch (g.pz) {
+#define DDA_CASE(L_) case L_: return sizeof(C) * zcols_smem_elems<C, L_, zcols_g_rt(sizeof(C), L_)>();
+    DDA_FAST_LENGTHS(DDA_CASE)
+#undef DDA_CASE
+    default: return sizeof(C) * ((size_t)g.pz + (size_t)g.pz * 3 * zcols_g_rt(sizeof(C), g.pz));
+  }
 }
 
 // k_x_fwd / k_x_inv for the variant chosen at run time: three components per CTA with tile
@@ -1021,7 +1039,7 @@ template <typename C>
 Err launch_z_cols(const Geom& g, const MvData<C>& d, int nrhs, cudaStream_t st, bool rfuse = false) {
   if constexpr (sizeof(C) == 8) {
     if (rfuse && zcols_rfuse_exists<C>(g.pz)) {
-      const size_t sm = sizeof(C) * ((size_t)g.pz + (size_t)g.pz * 3 * kZrG);
+      const size_t sm = sizeof(C) * (g.pz == 160 ? zcols_smem_elems<C, 160, kZrG>() : zcols_smem_elems<C, 320, kZrG>());
       const dim3 grid(nrhs, (g.py + kZrG - 1) / kZrG, g.px);
       if (g.pz == 160)
         DDA_CU(launch_k(k_z_cols<C, 160, kZrG, kZrG * 2 * Shape<160>::RA, true>, grid,

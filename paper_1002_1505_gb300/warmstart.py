@@ -243,6 +243,7 @@ def main():
     torch.cuda.synchronize()
     t_train = time.time() - t0
     del X, T, M
+    torch.cuda.empty_cache()  # the training set's memory back to the device for the library's own buffers
     rows = evaluate(net, list(range(100000, 100000 + args.heldout)), args.max_box, grid)
     out = {"train_samples": 2 * args.train_problems, "max_box": args.max_box, "steps": args.steps,
            "params": int(net.nparams),
@@ -252,6 +253,7 @@ def main():
            "heldout_iterations": {k: int(sum(r[k][0] for r in rows)) for k in ("cold", "alpha_einc", "network")},
            "heldout_max_resid": {k: float(max(r[k][1] for r in rows)) for k in ("cold", "alpha_einc", "network")},
            "heldout_unconverged_rhs": {k: int(sum(r[k][2] for r in rows)) for k in ("cold", "alpha_einc", "network")}}
+    print(json.dumps(out), flush=True)  # the held-out result first; --large adds a second line
     if args.large:
         w = W.HEXPRISM160
         ctx = D.Context(0)
@@ -282,7 +284,7 @@ def main():
             del p
         out["hexprism160"] = {"grid": list(big), "nrhs": ctx.nrhs, **res}
         ctx.close()
-    print(json.dumps(out))
+        print(json.dumps(out))
 
 
 if __name__ == "__main__":

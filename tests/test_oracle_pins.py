@@ -892,3 +892,105 @@ def test_periodic_slab_absorbs_like_a_fresnel_film():
     assert absorbed == pytest.approx(periodic.slab_fresnel_absorption(m, kd, nl), rel=0.01)
     # every layer of the column carries the same field pattern as its replicas: P is uniform in y, z
     assert np.abs(ps[0][0]).max() < 1e-10 * np.abs(ps[0][1]).max()
+
+
+# ----------------------------------------------------------------------------- periodic targets: orders
+
+def _slab(nl=8):
+    return targets.Target(ijk=np.stack([np.arange(nl), np.zeros(nl, int), np.zeros(nl, int)], 1), box=(nl, 1, 1),
+                          origin=np.zeros(3), a1=np.array([1.0, 0, 0]), a2=np.array([0, 1.0, 0]))
+
+
+@pytest.mark.parametrize("m", [1.5 + 0.1j, 1.5 + 0.0j])
+def test_periodic_slab_reflects_and_transmits_like_a_fresnel_film(m):
+    """The slab of the absorption pin (one column of 8 dipoles, periods 1 x 1, normal incidence):
+    the (0, 0) order's transmission and reflection coefficients against the Airy-Fresnel film of the
+    same index and thickness (within the DDA's discretization error: measured 0.3 % at kd = 0.2), and
+    T + R + A = 1, which holds for the DDA equations themselves as the interaction cutoff gamma -> 0
+    (1.1e-5 at gamma = 0.04, 7e-7 at 0.02)."""
+    from oracle import periodic
+    nl, kd = 8, 0.2
+    tt = _slab(nl)
+    pr = dda.build_problem(None, None, m, None, "LATTDR", [(0, 0, 0)], target=tt, kd=kd, iorth=2, periods=(1, 1),
+                           gamma=0.04)
+    ps, _ = dda.solve(pr, "lu")
+    q = dda.cross_sections(pr, ps)
+    rf, tf = periodic.slab_fresnel_rt(m, kd, nl)
+    for i in range(2):
+        t, r = periodic.transmission_reflection(pr, i, ps[i], 0, 0)
+        a = q[i]["Qabs"] * np.pi * tt.aeff ** 2
+        assert t == pytest.approx(tf, rel=5e-3)
+        assert r == pytest.approx(rf, rel=5e-3)
+        assert t + r + a == pytest.approx(1.0, abs=3e-5)
+        # only the specular orders exist for periods of one lattice spacing at kd = 0.2
+        assert periodic.transmission_reflection(pr, i, ps[i], 1, 0) is None
+
+
+@pytest.mark.parametrize("ori,periods", [((0.0, 0.0, 0.0), (8, 8)), ((0.3, 0.5, 0.7), (8, 7))])
+def test_periodic_orders_carry_the_incident_power(ori, periods):
+    """A doubly periodic array of small ellipsoids whose periods admit several diffraction orders
+    (kd = 1, periods 8 x 8 or 8 x 7, normal and oblique incidence): transmitted and reflected powers
+    over every allowed order plus the absorbed power add up to the incident power (gamma = 0.005),
+    and S^(2d)_11 times the flux ratio |n_x| / |n0_x| is the mean of the two polarizations' power in
+    each order other than the (0, 0) transmission (which interferes with the incident wave)."""
+    from oracle import periodic
+    t = _tuc()
+    pr = dda.build_problem(None, None, 1.4 + 0.05j, None, "GKDLDR", [ori], target=t, kd=1.0, iorth=2,
+                           periods=periods, gamma=0.005)
+    ps, _ = dda.solve(pr, "lu")
+    q = dda.cross_sections(pr, ps)
+    area = periods[0] * periods[1]
+    k0 = pr.rhs[0].k_tf
+    n0x = abs(k0[0]) / pr.kd
+    allowed = [(M, N) for M in range(-3, 4) for N in range(-3, 4)
+               if periodic.order_direction(k0, periods, M, N) is not None]
+    assert len(allowed) >= 4 and (0, 0) in allowed
+    for i in range(2):
+        tot = q[i]["Qabs"] * np.pi * t.aeff ** 2 / (area * n0x)
+        for M, N in allowed:
+            tot += sum(periodic.transmission_reflection(pr, i, ps[i], M, N))
+        assert tot == pytest.approx(1.0, abs=1e-6)
+    for M, N in allowed:
+        for sign in (1, -1):
+            if (M, N) == (0, 0) and sign == 1:
+                continue
+            n = periodic.order_direction(k0, periods, M, N, sign=sign)
+            s = periodic.mueller_in_order(pr, 0, ps, n)
+            mean = np.mean([periodic.transmission_reflection(pr, i, ps[i], M, N)[0 if sign == 1 else 1]
+                            for i in range(2)])
+            assert s[0, 0] * abs(n[0]) / n0x == pytest.approx(mean, rel=1e-10)
+    # the guide's condition on (M, N): |k_parallel + 2 pi (M, N) / L| < k exactly for the allowed orders
+    for M in range(-3, 4):
+        for N in range(-3, 4):
+            kp = np.hypot(k0[1] + 2 * np.pi * M / periods[0], k0[2] + 2 * np.pi * N / periods[1])
+            assert ((M, N) in allowed) == (kp < pr.kd)
+
+
+@pytest.mark.parametrize("periods", [(8, 0), (0, 7)])
+def test_periodic_cones_carry_the_scattered_power(periods):
+    """A target periodic along one axis (small ellipsoids, period 8 along y or 7 along z, kd = 1,
+    oblique incidence): the power per unit length leaving through a distant cylinder, integrated over
+    the azimuth zeta of every allowed cone M from S^(1d) (I_sca = S^(1d) I_in / (k rho), radial flux
+    fraction k_perp / k), equals the scattering cross section per unit length C_sca / L of the solved
+    unit cell (unpolarized incidence), at gamma = 0.000625 (the one-dimensional lattice sums converge
+    slowly in gamma)."""
+    from oracle import periodic
+    t = _tuc()
+    pr = dda.build_problem(None, None, 1.4 + 0.05j, None, "GKDLDR", [(0.2, 0.6, 0.3)], target=t, kd=1.0, iorth=2,
+                           periods=periods, gamma=0.000625)
+    ps, _ = dda.solve(pr, "lu")
+    q = dda.cross_sections(pr, ps)
+    length = periods[0] or periods[1]
+    axis = 1 if periods[0] else 2
+    csca = np.mean([(q[i]["Qext"] - q[i]["Qabs"]) * np.pi * t.aeff ** 2 for i in range(2)]) / length
+    nz = 240
+    tot = 0.0
+    cones = [M for M in range(-3, 4) if periodic.order_direction(pr.rhs[0].k_tf, periods, M) is not None]
+    assert len(cones) >= 2
+    for M in cones:
+        for zeta in np.arange(nz) * 2 * np.pi / nz:
+            n = periodic.order_direction(pr.rhs[0].k_tf, periods, M, zeta=zeta)
+            assert abs(np.linalg.norm(n) - 1.0) < 1e-14
+            s = periodic.mueller_in_order(pr, 0, ps, n)
+            tot += s[0, 0] * np.sqrt(1.0 - n[axis] ** 2) / pr.kd * (2 * np.pi / nz)
+    assert tot == pytest.approx(csca, rel=1e-4)

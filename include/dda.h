@@ -327,6 +327,40 @@ DDA_API dda_status dda_solve(dda_ctx *ctx, const dda_solve_opts *opt, void *p_de
 DDA_API dda_status dda_solve_batch(dda_ctx *const *ctxs, int nctx, const dda_solve_opts *opt, void *const *p_devs,
                                    dda_solve_report *const *reps, dda_status *statuses);
 
+/* Scattering of a periodic target (dda_set_periodicity) into its allowed
+ * directions, for a solved P (complex128 [nrhs][3][N], device) (guide,
+ * "Scattering Directions for Targets that are Periodic in 1 Dimension", "...
+ * for Doubly-Periodic Targets" and "Scattering by Periodic Targets:
+ * Generalized Mueller Matrix").  spec: host n_spec x 2 doubles.  Doubly
+ * periodic: the diffraction orders (M, N) (integers); the order's direction
+ * has k_y = k0_y + 2 pi M / P_y, k_z = k0_z + 2 pi N / P_z and |k_x| fixed by
+ * |k| = k0, on the transmission (sign of k0_x) and the reflection side.
+ * Singly periodic: (M, zeta), cone order M along the repetition axis and
+ * azimuth zeta (radians): axis y -> (k_perp cos zeta, k_y, k_perp sin zeta),
+ * axis z -> (k_perp cos zeta, k_perp sin zeta, k_z).  Outputs (host, each may
+ * be NULL):
+ *   dirs_out    n_spec x 2 x 3: TF unit vectors (transmission, reflection;
+ *               singly periodic: the cone direction, then zeros);
+ *   mueller_out n_ori x n_spec x 2 x 16 (row-major; needs iorth = 2): the
+ *               guide's generalized Mueller matrix, I_sca = S^(2d) I_in for
+ *               the plane wave of order (M, N) (transmission then reflection),
+ *               I_sca = S^(1d) I_in / (k rho) at distance rho from the axis
+ *               (slot 1 zero); the incident wave is not part of the scattered
+ *               Stokes vector;
+ *   tr_out      nrhs x n_spec x 2 (doubly periodic only): fractions of the
+ *               incident power per unit area carried by the order in
+ *               transmission (including the incident wave for (0, 0)) and in
+ *               reflection; with the absorbed fraction they sum to 1 over the
+ *               allowed orders.
+ * Normalisation read from the replicas' plane-wave (Weyl) and cylindrical-wave
+ * sums: S^(2d) = S(n) (2 pi / (A k k_x))^2, S^(1d) = S(n) 2 pi / (k k_perp L^2),
+ * S(n) the finite-target Mueller matrix of the same P in direction n, A the
+ * cell area.  DDA_EINVAL for an order that does not propagate (the guide's
+ * condition on M, N) or a non-integer order; DDA_EUNSUPPORTED for a finite
+ * target.  Synchronizes the stream. */
+DDA_API dda_status dda_periodic_scattering(dda_ctx *ctx, const void *p_dev, int n_spec, const double *spec,
+                                           double *dirs_out, double *mueller_out, double *tr_out);
+
 /* Efficiencies and Mueller matrices for a solved P (complex128 [nrhs][3][N]).
  * q_out: host nrhs x 4 doubles (Q_ext, Q_abs, Q_sca = Q_ext - Q_abs, Q_pha),
  * Q = C / (pi a_eff^2), formulas of Draine 1988 as used by the guide.

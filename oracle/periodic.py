@@ -192,7 +192,8 @@ def mueller_in_order(prob, o, ps, n):
     ax = rh.axes
     n_lf = np.array([np.dot(n, ax[0]), np.dot(n, ax[1]), np.dot(n, ax[2])])
     theta = float(np.arccos(np.clip(n_lf[0], -1.0, 1.0)))
-    phi = float(np.arctan2(n_lf[2], n_lf[1]))
+    # along +-x_LF (the (0, 0) orders) the scattering plane is undefined: azimuth 0 there
+    phi = float(np.arctan2(n_lf[2], n_lf[1])) if np.hypot(n_lf[1], n_lf[2]) > 1e-9 else 0.0
     kd = prob.kd
     f = observables.far_field_amplitudes(kd, prob.target.r, [ps[2 * o], ps[2 * o + 1]], theta, phi, ax)
     s = observables.mueller(*observables.amplitude_matrix(f, rh.e01_lf, rh.e02_lf, phi))

@@ -1733,6 +1733,40 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
   }
 }
 
+namespace {
+
+// 4 x 4 Mueller matrix (row-major) from the far-field amplitudes f[m][l] (m: theta-hat / phi-hat
+// component, l: incident polarization e01 / e02) at scattering azimuth phi: the amplitude matrix
+// S_1..S_4 by the guide's GETMUELLER relations (a, b, c, d = conj of the y and z Lab-Frame components
+// of e01 and e02), then the Bohren & Huffman relations
+void mueller_from_f(const cd f[2][2], cd A, cd B, cd Cc, cd D, double phs, double* m) {
+  const double cp = std::cos(phs), sp = std::sin(phs);
+  const cd I(0, 1);
+  const cd S1 = -I * (f[1][0] * (B * cp - A * sp) + f[1][1] * (D * cp - Cc * sp));
+  const cd S2 = -I * (f[0][0] * (A * cp + B * sp) + f[0][1] * (Cc * cp + D * sp));
+  const cd S3 = I * (f[0][0] * (B * cp - A * sp) + f[0][1] * (D * cp - Cc * sp));
+  const cd S4 = I * (f[1][0] * (A * cp + B * sp) + f[1][1] * (Cc * cp + D * sp));
+  auto cj = [](cd z) { return std::conj(z); };
+  m[0] = 0.5 * (std::norm(S1) + std::norm(S2) + std::norm(S3) + std::norm(S4));
+  m[1] = 0.5 * (std::norm(S2) - std::norm(S1) + std::norm(S4) - std::norm(S3));
+  m[2] = (S2 * cj(S3) + S1 * cj(S4)).real();
+  m[3] = (S2 * cj(S3) - S1 * cj(S4)).imag();
+  m[4] = 0.5 * (std::norm(S2) - std::norm(S1) + std::norm(S3) - std::norm(S4));
+  m[5] = 0.5 * (std::norm(S1) + std::norm(S2) - std::norm(S3) - std::norm(S4));
+  m[6] = (S2 * cj(S3) - S1 * cj(S4)).real();
+  m[7] = (S2 * cj(S3) + S1 * cj(S4)).imag();
+  m[8] = (S2 * cj(S4) + S1 * cj(S3)).real();
+  m[9] = (S2 * cj(S4) - S1 * cj(S3)).real();
+  m[10] = (S1 * cj(S2) + S3 * cj(S4)).real();
+  m[11] = (S2 * cj(S1) + S4 * cj(S3)).imag();
+  m[12] = (S4 * cj(S2) + S1 * cj(S3)).imag();
+  m[13] = (S4 * cj(S2) - S1 * cj(S3)).imag();
+  m[14] = (S1 * cj(S2) - S3 * cj(S4)).imag();
+  m[15] = (S1 * cj(S2) - S3 * cj(S4)).real();
+}
+
+}  // namespace
+
 dda_status dda_cross_sections(dda_ctx* c, const void* p_dev, double* q_out, const double* dirs, int ndir,
                               double* mueller_out) {
   if (!c || !p_dev) return DDA_EINVAL;
@@ -1836,30 +1870,7 @@ dda_status dda_cross_sections(dda_ctx* c, const void* p_dev, double* q_out, cons
             f[0][l] = k3 * s1;
             f[1][l] = k3 * s2;
           }
-          const double phs = dirs[2 * d + 1], cp = std::cos(phs), sp = std::sin(phs);
-          const cd I(0, 1);
-          const cd S1 = -I * (f[1][0] * (B * cp - A * sp) + f[1][1] * (D * cp - Cc * sp));
-          const cd S2 = -I * (f[0][0] * (A * cp + B * sp) + f[0][1] * (Cc * cp + D * sp));
-          const cd S3 = I * (f[0][0] * (B * cp - A * sp) + f[0][1] * (D * cp - Cc * sp));
-          const cd S4 = I * (f[1][0] * (A * cp + B * sp) + f[1][1] * (Cc * cp + D * sp));
-          double* m = mueller_out + ((size_t)o * ndir + d) * 16;
-          auto cj = [](cd z) { return std::conj(z); };
-          m[0] = 0.5 * (std::norm(S1) + std::norm(S2) + std::norm(S3) + std::norm(S4));
-          m[1] = 0.5 * (std::norm(S2) - std::norm(S1) + std::norm(S4) - std::norm(S3));
-          m[2] = (S2 * cj(S3) + S1 * cj(S4)).real();
-          m[3] = (S2 * cj(S3) - S1 * cj(S4)).imag();
-          m[4] = 0.5 * (std::norm(S2) - std::norm(S1) + std::norm(S3) - std::norm(S4));
-          m[5] = 0.5 * (std::norm(S1) + std::norm(S2) - std::norm(S3) - std::norm(S4));
-          m[6] = (S2 * cj(S3) - S1 * cj(S4)).real();
-          m[7] = (S2 * cj(S3) + S1 * cj(S4)).imag();
-          m[8] = (S2 * cj(S4) + S1 * cj(S3)).real();
-          m[9] = (S2 * cj(S4) - S1 * cj(S3)).real();
-          m[10] = (S1 * cj(S2) + S3 * cj(S4)).real();
-          m[11] = (S2 * cj(S1) + S4 * cj(S3)).imag();
-          m[12] = (S4 * cj(S2) + S1 * cj(S3)).imag();
-          m[13] = (S4 * cj(S2) - S1 * cj(S3)).imag();
-          m[14] = (S1 * cj(S2) - S3 * cj(S4)).imag();
-          m[15] = (S1 * cj(S2) - S3 * cj(S4)).real();
+          mueller_from_f(f, A, B, Cc, D, dirs[2 * d + 1], mueller_out + ((size_t)o * ndir + d) * 16);
         }
     }
     return DDA_OK;
@@ -1868,6 +1879,167 @@ dda_status dda_cross_sections(dda_ctx* c, const void* p_dev, double* q_out, cons
   }
 }
 
+
+dda_status dda_periodic_scattering(dda_ctx* c, const void* p_dev, int n_spec, const double* spec, double* dirs_out,
+                                   double* mueller_out, double* tr_out) {
+  if (!c || !p_dev || n_spec < 1 || !spec) return DDA_EINVAL;
+  if (!c->have_alpha || !c->have_green)
+    return fail(c, Err::make(DDA_ESTATE, "set target, incidence, Green tensor and alpha first"));
+  if (!c->periodic) return fail(c, Err::make(DDA_EUNSUPPORTED, "the target is not periodic (dda_set_periodicity)"));
+  const bool two_d = c->per_y > 0 && c->per_z > 0;
+  if (mueller_out && c->iorth != 2) return fail(c, Err::make(DDA_EINVAL, "Mueller matrices need iorth = 2"));
+  if (tr_out && !two_d)
+    return fail(c, Err::make(DDA_EINVAL, "transmission and reflection coefficients need a doubly periodic target"));
+  try {
+    Err e = set_dev(c);
+    if (!e.ok()) return fail(c, e);
+    const double pi = 3.14159265358979323846, k = c->kd;
+    const double* k0 = c->rg[0].k;  // every RHS of a periodic context shares its TF incidence
+    const int per_spec = two_d ? 2 : 1;
+    const int ndir = n_spec * per_spec;
+    // directions (TF unit vectors) of the orders: doubly periodic (M, N) on the transmission and the
+    // reflection side; singly periodic the cone of order M at azimuth zeta around the axis
+    std::vector<double> nd((size_t)ndir * 3, 0.0);
+    for (int sp = 0; sp < n_spec; ++sp) {
+      const double M = spec[2 * sp], N = spec[2 * sp + 1];
+      if (two_d) {
+        if (M != std::floor(M) || N != std::floor(N))
+          return fail(c, Err::make(DDA_EINVAL, "diffraction orders (M, N) must be integers"));
+        const double ky = k0[1] + 2.0 * pi * M / c->per_y, kz = k0[2] + 2.0 * pi * N / c->per_z;
+        const double kx2 = k * k - ky * ky - kz * kz;
+        if (!(kx2 > 0.0)) return fail(c, Err::make(DDA_EINVAL, "diffraction order (M, N) is not allowed here"));
+        const double sx = k0[0] >= 0.0 ? 1.0 : -1.0;
+        for (int side = 0; side < 2; ++side) {
+          double* n = &nd[((size_t)sp * 2 + side) * 3];
+          n[0] = (side == 0 ? sx : -sx) * std::sqrt(kx2) / k;
+          n[1] = ky / k;
+          n[2] = kz / k;
+        }
+      } else {
+        if (M != std::floor(M)) return fail(c, Err::make(DDA_EINVAL, "the cone order M must be an integer"));
+        const bool ax_y = c->per_y > 0;
+        const double ka = ax_y ? k0[1] + 2.0 * pi * M / c->per_y : k0[2] + 2.0 * pi * M / c->per_z;
+        const double kp2 = k * k - ka * ka;
+        if (!(kp2 > 0.0)) return fail(c, Err::make(DDA_EINVAL, "cone order M is not allowed here"));
+        const double kp = std::sqrt(kp2);
+        double* n = &nd[(size_t)sp * 3];
+        n[0] = kp * std::cos(N) / k;
+        n[1] = ax_y ? ka / k : kp * std::sin(N) / k;
+        n[2] = ax_y ? kp * std::sin(N) / k : ka / k;
+      }
+    }
+    if (dirs_out) {
+      for (int sp = 0; sp < n_spec; ++sp)
+        for (int side = 0; side < 2; ++side)
+          for (int q = 0; q < 3; ++q)
+            dirs_out[((size_t)sp * 2 + side) * 3 + q] = side < per_spec ? nd[((size_t)sp * per_spec + side) * 3 + q] : 0.0;
+    }
+    if (!mueller_out && !tr_out) return DDA_OK;
+    // F = sum_j P_j exp(-i k n.r_j) of every RHS in every direction (FP64, the finite targets' kernel)
+    const int nrhs = c->nrhs;
+    const double2* P = (const double2*)p_dev;
+    std::vector<double> nh((size_t)nrhs * ndir * 3);
+    for (int b = 0; b < nrhs; ++b) std::copy(nd.begin(), nd.end(), nh.begin() + (size_t)b * ndir * 3);
+    const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((c->n + 2047) / 2048, 64));
+    e = grow(c, &c->d_nh, sizeof(double) * nh.size());
+    if (e.ok()) e = grow(c, &c->d_F, sizeof(double2) * (size_t)nrhs * ndir * 3);
+    if (e.ok()) e = grow(c, &c->d_fpart, sizeof(double) * 6 * (size_t)nrhs * ndir * nblk);
+    if (e.ok())
+      e = cuda_ok(cudaMemcpy(c->d_nh, nh.data(), sizeof(double) * nh.size(), cudaMemcpyHostToDevice),
+                  "direction upload");
+    const int box[3] = {c->tgt.box[0], c->tgt.box[1], c->tgt.box[2]};
+    if (e.ok())
+      e = dda::farfield(c->d_ijk, c->d_origin, c->d_nh, k, P, nrhs, ndir, c->n, box, c->d_F, (double2*)c->d_fpart,
+                        nblk, c->stream);
+    std::vector<double2> F((size_t)nrhs * ndir * 3);
+    if (e.ok()) {
+      e = cuda_ok(cudaMemcpyAsync(F.data(), c->d_F, sizeof(double2) * F.size(), cudaMemcpyDeviceToHost, c->stream),
+                  "far-field readback");
+      if (e.ok() && cudaStreamSynchronize(c->stream) != cudaSuccess) e = Err::make(DDA_ECUDA, "far field failed");
+    }
+    if (!e.ok()) return fail(c, e);
+    auto Fv = [&](int b, int d, int q) {
+      const double2 v = F[((size_t)b * ndir + d) * 3 + q];
+      return cd(v.x, v.y);
+    };
+    if (tr_out) {
+      // E_s = (2 pi i k^2 / (A k |n_x|)) (I - n n).F; powers per unit area relative to the incident
+      const double area = c->per_y * c->per_z, n0x = std::abs(k0[0]) / k;
+      for (int b = 0; b < nrhs; ++b)
+        for (int sp = 0; sp < n_spec; ++sp)
+          for (int side = 0; side < 2; ++side) {
+            const int d = sp * 2 + side;
+            const double* n = &nd[(size_t)d * 3];
+            const cd f[3] = {Fv(b, d, 0), Fv(b, d, 1), Fv(b, d, 2)};
+            const cd nf = n[0] * f[0] + n[1] * f[1] + n[2] * f[2];
+            const cd pre = cd(0.0, 2.0 * pi * k * k / (area * k * std::abs(n[0])));
+            double pw = 0.0;
+            for (int q = 0; q < 3; ++q) {
+              cd Eq = pre * (f[q] - n[q] * nf);
+              if (side == 0 && spec[2 * sp] == 0.0 && spec[2 * sp + 1] == 0.0)
+                Eq += cd(c->rg[b].e[2 * q], c->rg[b].e[2 * q + 1]);
+              pw += std::norm(Eq);
+            }
+            tr_out[((size_t)b * n_spec + sp) * 2 + side] = pw * std::abs(n[0]) / n0x;
+          }
+    }
+    if (mueller_out) {
+      // the finite-target Mueller matrix of the same amplitudes, scaled from 1/(k r)^2 to the plane
+      // waves' (2 pi / (A k k_x))^2 or the cones' 2 pi / (k k_perp L^2) (guide's S^(2d), S^(1d))
+      const double k3 = k * k * k;
+      const cd A = std::conj(c->e01[1]), B = std::conj(c->e01[2]), Cc = std::conj(c->e02[1]), D = std::conj(c->e02[2]);
+      for (int o = 0; o < c->n_ori; ++o) {
+        const double* ax = &c->axes[9 * o];
+        for (int sp = 0; sp < n_spec; ++sp)
+          for (int side = 0; side < 2; ++side) {
+            double* m = mueller_out + (((size_t)o * n_spec + sp) * 2 + side) * 16;
+            if (side >= per_spec) {
+              std::fill(m, m + 16, 0.0);
+              continue;
+            }
+            const int d = sp * per_spec + side;
+            const double* n = &nd[(size_t)d * 3];
+            const double nl[3] = {n[0] * ax[0] + n[1] * ax[1] + n[2] * ax[2], n[0] * ax[3] + n[1] * ax[4] + n[2] * ax[5],
+                                  n[0] * ax[6] + n[1] * ax[7] + n[2] * ax[8]};
+            const double th = std::acos(std::max(-1.0, std::min(1.0, nl[0])));
+            // along +-x_LF (the (0, 0) orders) the scattering plane is undefined: azimuth 0 there
+            const double ph = std::hypot(nl[1], nl[2]) > 1e-9 ? std::atan2(nl[2], nl[1]) : 0.0;
+            const double tl[3] = {-std::sin(th), std::cos(th) * std::cos(ph), std::cos(th) * std::sin(ph)};
+            const double pl[3] = {0.0, -std::sin(ph), std::cos(ph)};
+            double e1[3], e2[3];
+            for (int q = 0; q < 3; ++q) {
+              e1[q] = tl[0] * ax[q] + tl[1] * ax[3 + q] + tl[2] * ax[6 + q];
+              e2[q] = pl[0] * ax[q] + pl[1] * ax[3 + q] + pl[2] * ax[6 + q];
+            }
+            cd f[2][2];
+            for (int l = 0; l < 2; ++l) {
+              cd s1(0, 0), s2(0, 0);
+              for (int q = 0; q < 3; ++q) {
+                s1 += e1[q] * Fv(o * 2 + l, d, q);
+                s2 += e2[q] * Fv(o * 2 + l, d, q);
+              }
+              f[0][l] = k3 * s1;
+              f[1][l] = k3 * s2;
+            }
+            mueller_from_f(f, A, B, Cc, D, ph, m);
+            double scale;
+            if (two_d) {
+              const double g = 2.0 * pi / (c->per_y * c->per_z * k * k * std::abs(n[0]));
+              scale = g * g;
+            } else {
+              const double L = c->per_y > 0 ? c->per_y : c->per_z;
+              const double na = c->per_y > 0 ? n[1] : n[2];
+              scale = 2.0 * pi / (k * k * std::sqrt(std::max(0.0, 1.0 - na * na)) * L * L);
+            }
+            for (int q = 0; q < 16; ++q) m[q] *= scale;
+          }
+      }
+    }
+    return DDA_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, Err::make(DDA_ENOMEM, "host allocation failed"));
+  }
+}
 
 unsigned long long dda_kernel_launches(void) { return dda::launches(); }
 

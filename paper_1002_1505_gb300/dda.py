@@ -84,6 +84,7 @@ def _load():
         "dda_angular_averages": (I, [P, P, D, P, P]),
         "dda_force_torque": (I, [P, P, D, P, P]),
         "dda_near_field": (I, [P, P, P, I64, P, P]),
+        "dda_periodic_scattering": (I, [P, P, I, P, P, P, P]),
         "dda_orientation_grid": (I, [P, I, P, I, P, I, P, P]),
         "dda_profile_matvec": (I, [P, I, I, I, P, P]),
         "dda_matvec_noalloc": (I, [P, P, P, I, I]),
@@ -143,6 +144,7 @@ class Context:
         self.nrhs = 0
         self.iorth = 0
         self.kd = 0.0
+        self._periodic_2d = False   # both periods set (a new target makes it finite again)
 
     def close(self):
         if self._h:
@@ -161,6 +163,7 @@ class Context:
 
     # ---------------------------------------------------------------- set-up
     def dda_setup_shape(self, shape: str, shpar: Sequence[float]):
+        self._periodic_2d = False
         sp = np.ascontiguousarray(shpar, dtype=np.float64)
         n = ctypes.c_int64()
         box = np.zeros(3, dtype=np.int32)
@@ -171,6 +174,7 @@ class Context:
 
     def dda_setup_target(self, ixyz, icomp=None, origin=(0.0, 0.0, 0.0), a1=None, a2=None):
         """icomp: None, N 1-based compositions, or N x 3 (one per axis: anisotropic materials)."""
+        self._periodic_2d = False
         ij = np.ascontiguousarray(ixyz, dtype=np.int32)
         ic = None if icomp is None else np.ascontiguousarray(icomp, dtype=np.int32)
         fn = LIB.dda_setup_target
@@ -186,6 +190,7 @@ class Context:
     def dda_setup_target_anifrm(self, ixyz, icomp3, df_angles, origin=(0.0, 0.0, 0.0), a1=None, a2=None):
         """Site list with per-axis compositions (N x 3, 1-based) and per-site Dielectric-Frame angles
         (N x 3: theta_DF, phi_DF, beta_DF, radians): the guide's ANIFRMFIL target."""
+        self._periodic_2d = False
         ij = np.ascontiguousarray(ixyz, dtype=np.int32)
         ic = np.ascontiguousarray(icomp3, dtype=np.int32)
         an = np.ascontiguousarray(df_angles, dtype=np.float64)
@@ -213,6 +218,7 @@ class Context:
     def dda_set_periodicity(self, py: float, pz: float, gamma: float = 0.01):
         """Repeat the target with periods py (y_TF) and pz (z_TF), 0 = none; gamma = interaction cutoff."""
         self._check(LIB.dda_set_periodicity(self._h, float(py), float(pz), float(gamma)))
+        self._periodic_2d = py > 0 and pz > 0
 
     def dda_kd_from_x(self, x: float):
         """(kd, a_eff / d) for size parameter x of the current target."""
@@ -329,6 +335,22 @@ class Context:
                                        None if b is None else _ptr(b)))
         to_c = lambda a: a[..., 0::2] + 1j * a[..., 1::2]
         return to_c(e), (None if b is None else to_c(b))
+
+    def dda_periodic_scattering(self, p, spec, mueller=True, tr=None):
+        """Orders of a periodic target: spec (n, 2) = (M, N) (doubly periodic) or (M, zeta) (singly).
+        Returns (dirs [n, 2, 3], Mueller [n_ori, n, 2, 4, 4] or None, T/R [nrhs, n, 2] or None);
+        tr defaults to True for doubly periodic targets."""
+        self._dev_check(p, DDA_C128)
+        sp = np.ascontiguousarray(spec, dtype=np.float64).reshape(-1, 2)
+        n = sp.shape[0]
+        dirs = np.zeros((n, 2, 3))
+        m = np.zeros((self.nrhs // self.iorth, n, 2, 16)) if mueller else None
+        if tr is None:
+            tr = self._periodic_2d
+        t = np.zeros((self.nrhs, n, 2)) if tr else None
+        self._check(LIB.dda_periodic_scattering(self._h, ctypes.c_void_p(p.data_ptr()), n, _ptr(sp), _ptr(dirs),
+                                                None if m is None else _ptr(m), None if t is None else _ptr(t)))
+        return dirs, (None if m is None else m.reshape(-1, n, 2, 4, 4)), t
 
     def dda_cross_sections(self, p, dirs=None):
         """Returns (Q array [nrhs,4] = Qext,Qabs,Qsca,Qpha, Mueller [n_ori,ndir,4,4] or None)."""

@@ -93,3 +93,101 @@ def test_periodic_slab_absorption_against_fresnel(D):
     with pytest.raises(D.DDAError) as ei:
         ctx.dda_build_green_fft()
     assert ei.value.status == D.DDA_EUNSUPPORTED
+
+
+def _periodic_ctx(D, t, periods, gamma, ori, kd, m):
+    ctx = D.Context(0)
+    ctx.dda_setup_target(t.ijk, origin=t.origin)
+    ctx.dda_set_periodicity(periods[0], periods[1], gamma)
+    ctx.dda_set_incident(kd, ori, [[0, 0], [1, 0], [0, 0]], 2)
+    ctx.dda_build_green_fft()
+    ctx.dda_set_polarizability("GKDLDR", m)
+    return ctx
+
+
+@pytest.mark.parametrize("ori,periods", [((0.0, 0.0, 0.0), (8.0, 8.0)), ((0.3, 0.5, 0.7), (8.0, 7.0))],
+                         ids=["normal", "oblique"])
+def test_diffraction_orders_match_oracle(D, ori, periods):
+    """A doubly periodic array of small ellipsoids with several propagating orders (kd = 1): order
+    directions, the generalized Mueller matrix S^(2d)(M, N) in transmission and reflection and the
+    transmission / reflection coefficients against the oracle (its LU solution, the GPU's solved to
+    1e-10); the coefficients over every allowed order plus the GPU's own absorbed fraction make 1;
+    a non-propagating order and a finite target are refused."""
+    t = o_targets.make_target("ELLIPSOID", (3, 4, 3))
+    gamma, kd, m = 0.005, 1.0, 1.4 + 0.05j
+    prob = odda.build_problem(None, None, m, None, "GKDLDR", [ori], target=t, kd=kd, iorth=2, periods=periods,
+                              gamma=gamma)
+    ps, _ = odda.solve(prob, "lu")
+    ctx = _periodic_ctx(D, t, periods, gamma, [ori], kd, m)
+    p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
+    reps, _ = ctx.dda_solve(p, solver="BICGSTAB", precision="C128", tol=1e-10, maxit=3000)
+    assert all(r["converged"] == 1 for r in reps)
+    k0 = prob.rhs[0].k_tf
+    spec = [(M, N) for M in range(-2, 3) for N in range(-2, 3) if oper.order_direction(k0, periods, M, N) is not None]
+    assert len(spec) >= 4
+    dirs, mu, tr = ctx.dda_periodic_scattering(p, spec)
+    q, _ = ctx.dda_cross_sections(p)
+    _, aeff = ctx.dda_kd_from_x(1.0)
+    pn = p.cpu().numpy()
+    for s, (M, N) in enumerate(spec):
+        for side, sign in enumerate((1, -1)):
+            n = oper.order_direction(k0, periods, M, N, sign=sign)
+            assert np.abs(dirs[s, side] - n).max() < 1e-13
+            ref = oper.mueller_in_order(prob, 0, ps, n)
+            assert np.abs(mu[0, s, side] - ref).max() <= 1e-6 * np.abs(ref).max(), (M, N, side)
+        for b in range(2):
+            ref_tr = oper.transmission_reflection(prob, b, ps[b], M, N)
+            np.testing.assert_allclose(tr[b, s], ref_tr, rtol=1e-6, atol=1e-12)
+    n0x = abs(k0[0]) / kd
+    for b in range(2):
+        absorbed = q[b, 1] * math.pi * aeff ** 2 / (periods[0] * periods[1] * n0x)
+        assert tr[b].sum() + absorbed == pytest.approx(1.0, abs=1e-5)
+    M_bad = int(np.ceil(2 * periods[0] / (2 * np.pi) * kd)) + 2
+    with pytest.raises(D.DDAError) as ei:
+        ctx.dda_periodic_scattering(p, [(M_bad, 0)])
+    assert ei.value.status == D.DDA_EINVAL
+    fin = D.Context(0)
+    fin.dda_setup_target(t.ijk, origin=t.origin)
+    fin.dda_set_incident(kd, [ori], [[0, 0], [1, 0], [0, 0]], 2)
+    fin.dda_build_green_fft()
+    fin.dda_set_polarizability("GKDLDR", m)
+    with pytest.raises(D.DDAError) as ei:
+        fin.dda_periodic_scattering(p, [(0, 0)])
+    assert ei.value.status == D.DDA_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("periods", [(8.0, 0.0), (0.0, 7.0)], ids=["axis_y", "axis_z"])
+def test_scattering_cones_match_oracle(D, periods):
+    """A target periodic along one axis: cone directions and S^(1d)(M, zeta) against the oracle on
+    every allowed cone at several azimuths, and the cone-integrated power against the GPU's own
+    C_sca per unit length (the oracle's energy pin, on the GPU's numbers)."""
+    t = o_targets.make_target("ELLIPSOID", (3, 4, 3))
+    gamma, kd, m, ori = 0.000625, 1.0, 1.4 + 0.05j, (0.2, 0.6, 0.3)
+    prob = odda.build_problem(None, None, m, None, "GKDLDR", [ori], target=t, kd=kd, iorth=2, periods=periods,
+                              gamma=gamma)
+    ps, _ = odda.solve(prob, "lu")
+    ctx = _periodic_ctx(D, t, periods, gamma, [ori], kd, m)
+    p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
+    reps, _ = ctx.dda_solve(p, solver="BICGSTAB", precision="C128", tol=1e-10, maxit=3000)
+    assert all(r["converged"] == 1 for r in reps)
+    k0 = prob.rhs[0].k_tf
+    cones = [M for M in range(-3, 4) if oper.order_direction(k0, periods, M) is not None]
+    nz = 120
+    zetas = np.arange(nz) * 2 * np.pi / nz
+    spec = [(M, z) for M in cones for z in zetas]
+    dirs, mu, tr = ctx.dda_periodic_scattering(p, spec)
+    assert tr is None
+    axis = 1 if periods[0] else 2
+    tot = 0.0
+    for s, (M, z) in enumerate(spec):
+        n = oper.order_direction(k0, periods, M, zeta=z)
+        assert np.abs(dirs[s, 0] - n).max() < 1e-13 and not dirs[s, 1].any()
+        if s % 17 == 0:
+            ref = oper.mueller_in_order(prob, 0, ps, n)
+            assert np.abs(mu[0, s, 0] - ref).max() <= 1e-6 * np.abs(ref).max(), (M, z)
+        tot += mu[0, s, 0, 0, 0] * np.sqrt(1.0 - n[axis] ** 2) / kd * (2 * np.pi / nz)
+    q, _ = ctx.dda_cross_sections(p)
+    _, aeff = ctx.dda_kd_from_x(1.0)
+    length = periods[0] or periods[1]
+    csca = np.mean([(q[b, 0] - q[b, 1]) * math.pi * aeff ** 2 for b in range(2)]) / length
+    assert tot == pytest.approx(csca, rel=1e-4)

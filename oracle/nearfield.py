@@ -41,22 +41,44 @@ def dipole_fields(rvec, p, k):
     return E, B
 
 
-def fields_at(points, kd, r, p, k_tf, e_tf):
+def fields_at(points, kd, r, p, k_tf, e_tf, periods=None, gamma=0.0):
     """Total E and B (each (M, 3) complex) at points (M, 3) for one RHS: sites r (N, 3), solution p
-    (3, N), incident wave vector k_tf (3,) and polarization e_tf (3,) in the TF."""
+    (3, N), incident wave vector k_tf (3,) and polarization e_tf (3,) in the TF.
+
+    Periodic targets (periods = (P_y, P_z), a zero for an axis without repetition): the replica of
+    the unit cell displaced by R carries P exp(i k.R), and each dipole's contribution is multiplied by
+    the same cutoff exp[-(gamma k D)^4] of its distance D to the point as the periodic interaction
+    (oracle.periodic), replicas dropped where (gamma k D)^4 > 40: the guide's DDfield lets phi(r)
+    suppress the distant dipoles of an infinite target so that the sums can be truncated; the near
+    suppression below one lattice spacing stays as for a finite target."""
     k = float(kd)
     khat = np.asarray(k_tf, float) / np.linalg.norm(k_tf)
     pts = np.asarray(points, dtype=np.float64)
     Eo = np.zeros((len(pts), 3), dtype=np.complex128)
     Bo = np.zeros((len(pts), 3), dtype=np.complex128)
     pt = p.T
+    periodic = periods is not None and (periods[0] > 0 or periods[1] > 0)
+    if periodic:
+        from . import periodic as per
+        ext = float(np.max(np.linalg.norm(pts[:, None, 1:] - r[None, :, 1:], axis=-1)))
+        reps = per.replica_offsets(periods, k, gamma, extra=ext)
+        bloch = np.exp(1j * (reps @ np.asarray(k_tf, float)))
+    else:
+        reps = np.zeros((1, 3))
+        bloch = np.ones(1, dtype=np.complex128)
+    # every (replica, site) pair as one flat list: separation, moment with its Bloch phase
+    pm = (bloch[:, None, None] * pt[None, :, :]).reshape(-1, 3)
     for i, x in enumerate(pts):
         einc = np.asarray(e_tf) * np.exp(1j * np.dot(k_tf, x))
-        d = x[None, :] - r
-        R = np.linalg.norm(d, axis=-1)
-        keep = R > 0
-        E, B = dipole_fields(d[keep], pt[keep], k)
-        w = suppression(R[keep])[:, None]
-        Eo[i] = einc + np.sum(w * E, axis=0)
-        Bo[i] = np.cross(khat, einc) + np.sum(w * B, axis=0)
+        d = (x[None, None, :] - r[None, :, :] - reps[:, None, :]).reshape(-1, 3)
+        D = np.linalg.norm(d, axis=-1)
+        keep = D > 0
+        if periodic:
+            keep &= (gamma * k * D) ** 4 <= per.CUTOFF_EXP
+        E, B = dipole_fields(d[keep], pm[keep], k)
+        w = suppression(D[keep])
+        if periodic:
+            w = w * np.exp(-(gamma * k * D[keep]) ** 4)
+        Eo[i] = einc + np.sum(w[:, None] * E, axis=0)
+        Bo[i] = np.cross(khat, einc) + np.sum(w[:, None] * B, axis=0)
     return Eo, Bo

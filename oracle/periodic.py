@@ -206,6 +206,26 @@ def mueller_in_order(prob, o, ps, n):
     return s * 2.0 * np.pi / (kd * k_perp * length * length)
 
 
+def order_fields(prob, i, p, M, N):
+    """(E_t, E_r): complex amplitude vectors of order (M, N) of a doubly periodic target for RHS i, the
+    transmitted one including the incident wave for (0, 0); far from the slab the field is
+    sum over orders of E exp(i k n.x) (incident amplitude e_tf, |E0| = 1).  None if evanescent."""
+    rh = prob.rhs[i]
+    kd = prob.kd
+    area = prob.periods[0] * prob.periods[1]
+    out = []
+    for sign in (1, -1):
+        n = order_direction(rh.k_tf, prob.periods, M, N, sign=sign)
+        if n is None:
+            return None
+        F = order_sum(prob.target.r, kd, p, n)
+        E = 2j * np.pi * kd * kd / (area * kd * abs(n[0])) * (F - n * np.dot(n, F))
+        if sign == 1 and M == 0 and N == 0:
+            E = E + rh.e_tf
+        out.append((n, E))
+    return tuple(out)
+
+
 def transmission_reflection(prob, i, p, M, N):
     """(T, R): fractions of the incident power per unit area of a doubly periodic target carried by
     order (M, N) in transmission and in reflection, for RHS i with solution p (3, N); None for an

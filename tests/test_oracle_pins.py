@@ -7,6 +7,8 @@ invariant of the mathematics.
 """
 import math
 
+import functools
+
 import numpy as np
 import pytest
 import scipy.special as sp
@@ -901,6 +903,16 @@ def _slab(nl=8):
                           origin=np.zeros(3), a1=np.array([1.0, 0, 0]), a2=np.array([0, 1.0, 0]))
 
 
+@functools.lru_cache(maxsize=None)
+def _solved_slab(m, kd=0.2, gamma=0.04):
+    """The 8-layer slab (periods 1 x 1, normal incidence, LATTDR), solved by LU."""
+    tt = _slab(8)
+    pr = dda.build_problem(None, None, m, None, "LATTDR", [(0, 0, 0)], target=tt, kd=kd, iorth=2, periods=(1, 1),
+                           gamma=gamma)
+    ps, _ = dda.solve(pr, "lu")
+    return tt, pr, ps
+
+
 @pytest.mark.parametrize("m", [1.5 + 0.1j, 1.5 + 0.0j])
 def test_periodic_slab_reflects_and_transmits_like_a_fresnel_film(m):
     """The slab of the absorption pin (one column of 8 dipoles, periods 1 x 1, normal incidence):
@@ -910,10 +922,7 @@ def test_periodic_slab_reflects_and_transmits_like_a_fresnel_film(m):
     (1.1e-5 at gamma = 0.04, 7e-7 at 0.02)."""
     from oracle import periodic
     nl, kd = 8, 0.2
-    tt = _slab(nl)
-    pr = dda.build_problem(None, None, m, None, "LATTDR", [(0, 0, 0)], target=tt, kd=kd, iorth=2, periods=(1, 1),
-                           gamma=0.04)
-    ps, _ = dda.solve(pr, "lu")
+    tt, pr, ps = _solved_slab(m)
     q = dda.cross_sections(pr, ps)
     rf, tf = periodic.slab_fresnel_rt(m, kd, nl)
     for i in range(2):
@@ -994,3 +1003,29 @@ def test_periodic_cones_carry_the_scattered_power(periods):
             s = periodic.mueller_in_order(pr, 0, ps, n)
             tot += s[0, 0] * np.sqrt(1.0 - n[axis] ** 2) / pr.kd * (2 * np.pi / nz)
     assert tot == pytest.approx(csca, rel=1e-4)
+
+
+def test_periodic_near_field_away_from_the_slab_is_its_plane_waves():
+    """The guide's DDfield for an infinite target: summing the replicas' dipole fields (cutoff
+    exp[-(gamma k D)^4] on each) at points a wavelength or so in front of and behind the slab gives the
+    plane waves of its (0, 0) orders -- incident plus reflected in front, transmitted behind -- whose
+    amplitudes come from the independent Fourier-space sum (periodic.order_fields); E and B within
+    2e-3 at gamma = 0.04 (the real-space sum converges as gamma -> 0: 3e-3 -> 2e-4 from 0.04 to 0.02
+    at kd = 0.4)."""
+    from oracle import nearfield, periodic
+    tt, pr, ps = _solved_slab(1.5 + 0.1j)
+    kd = pr.kd
+    rh = pr.rhs[0]
+    (nt, et), (nr, er) = periodic.order_fields(pr, 0, ps[0], 0, 0)
+    pts = np.array([[-15.0, 0.3, 0.2], [25.0, 0.1, 0.7]])
+    E, B = nearfield.fields_at(pts, kd, tt.r, ps[0], rh.k_tf, rh.e_tf, periods=(1, 1), gamma=0.04)
+    x0 = pts[0]
+    inc = rh.e_tf * np.exp(1j * np.dot(rh.k_tf, x0))
+    refl = er * np.exp(1j * kd * np.dot(nr, x0))
+    k0h = rh.k_tf / kd
+    e_front, b_front = inc + refl, np.cross(k0h, inc) + np.cross(nr, refl)
+    trans = et * np.exp(1j * kd * np.dot(nt, pts[1]))
+    for got, ref in ((E[0], e_front), (B[0], b_front), (E[1], trans), (B[1], np.cross(nt, trans))):
+        assert np.linalg.norm(got - ref) <= 2e-3 * np.linalg.norm(ref)
+    # and the reflected wave is really there: without it the front field is off by |r| ~ 0.3
+    assert np.linalg.norm(E[0] - inc) > 0.2 * np.linalg.norm(inc)

@@ -522,7 +522,11 @@ DDA_API dda_status dda_force_torque(dda_ctx *ctx, const void *p_dev, double eta,
  * spacing is suppressed by phi(R) = R^4 (5 - 4 R) (R < 1; phi = 1 beyond), a
  * factor vanishing faster than R^3 as the guide asks.  e_out / b_out: host
  * [nrhs][npts][6] = (re, im) of x, y, z; b_out may be NULL.  Direct FP64 sum
- * over all dipoles on the device (O(N npts)).  Synchronizes. */
+ * over all dipoles on the device (O(N npts)).  Periodic targets
+ * (dda_set_periodicity): the sum runs over the replicas R of the unit cell too,
+ * moments P_j exp(i k.R), each term also weighted by the interaction cutoff
+ * exp[-(gamma k D)^4] of its distance D and dropped where (gamma k D)^4 > 40
+ * (O(N npts replicas); DDA_EINVAL beyond 2e11 terms).  Synchronizes. */
 DDA_API dda_status dda_near_field(dda_ctx *ctx, const void *p_dev, const double *pts, int64_t npts, double *e_out,
                                   double *b_out);
 

@@ -2405,8 +2405,6 @@ dda_status dda_force_torque(dda_ctx* c, const void* p_dev, double eta, double* o
 dda_status dda_near_field(dda_ctx* c, const void* p_dev, const double* pts, int64_t npts, double* e_out,
                           double* b_out) {
   if (!c || !p_dev || !pts || !e_out || npts < 1) return DDA_EINVAL;
-  if (c->periodic)
-    return fail(c, Err::make(DDA_EUNSUPPORTED, "not available for periodic targets (scattering goes into diffraction orders)"));
   if (!c->have_inc) return fail(c, Err::make(DDA_ESTATE, "set the target and the incident beams first"));
   try {
     Err e = need_device(c);
@@ -2422,13 +2420,55 @@ dda_status dda_near_field(dda_ctx* c, const void* p_dev, const double* pts, int6
     std::vector<double> h((size_t)12 * npts * nrhs);
     if (e.ok()) e = cuda_ok(cudaMemcpyAsync(d_pts, pts, sizeof(double) * 3 * npts, cudaMemcpyHostToDevice, c->stream),
                             "point upload");
-    if (e.ok()) e = dda::near_field(c->d_ijk, c->d_origin, (const double2*)p_dev, nrhs, c->n, d_pts, npts, c->kd, d_out,
-                                    c->stream);
+    double* d_part = nullptr;
+    if (e.ok() && !c->periodic) {
+      e = dda::near_field(c->d_ijk, c->d_origin, (const double2*)p_dev, nrhs, c->n, d_pts, npts, c->kd, d_out,
+                          c->stream);
+    } else if (e.ok()) {
+      // replicas far enough that every term within the cutoff radius 40^(1/4) / (gamma kd) of any
+      // point is included: the radius plus the points' and sites' extent along y and z
+      double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+      for (int64_t j = 0; j < c->n; ++j)
+        for (int a = 1; a < 3; ++a) {
+          const double v = c->tgt.ijk[3 * j + a] + c->tgt.origin[a];
+          lo[a] = std::min(lo[a], v);
+          hi[a] = std::max(hi[a], v);
+        }
+      double plo[3] = {1e300, 1e300, 1e300}, phi[3] = {-1e300, -1e300, -1e300};
+      for (int64_t i = 0; i < npts; ++i)
+        for (int a = 1; a < 3; ++a) {
+          plo[a] = std::min(plo[a], pts[3 * i + a]);
+          phi[a] = std::max(phi[a], pts[3 * i + a]);
+        }
+      const double rcut = std::pow(40.0, 0.25) / (c->per_gamma * c->kd);
+      int mrange[3] = {0, 0, 0};
+      const double per[3] = {0.0, c->per_y, c->per_z};
+      for (int a = 1; a < 3; ++a) {
+        if (per[a] <= 0) continue;
+        const double ext = std::max(std::abs(phi[a] - lo[a]), std::abs(hi[a] - plo[a]));
+        const double mr = std::ceil((rcut + ext) / per[a]);
+        if (mr > 1e6) e = Err::make(DDA_EINVAL, "interaction cutoff too small for the periods (too many replicas)");
+        mrange[a] = (int)std::min(mr, 1e6);
+      }
+      const int64_t nchunk = (npts + 3) / 4;
+      const int64_t pairs = c->n * (int64_t)(2 * mrange[1] + 1) * (2 * mrange[2] + 1);
+      // bound the work (each term is ~150 FP64 operations): 2e11 terms take seconds
+      if (e.ok() && (double)pairs * (double)npts * nrhs > 2e11)
+        e = Err::make(DDA_EINVAL, "too many replica terms for the near field (raise gamma or pass fewer points)");
+      const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>((pairs + 4095) / 4096,
+                                                                      std::max<int64_t>(1, 1216 / std::max<int64_t>(1, nchunk * nrhs))));
+      if (e.ok()) e = dalloc((char**)&d_part, sizeof(double) * 12 * (size_t)npts * nrhs * nsplit);
+      if (e.ok())
+        e = dda::near_field_pbc(c->d_ijk, c->d_origin, (const double2*)p_dev, nrhs, c->n, d_pts, npts, c->kd,
+                                c->rg[0].k, c->per_y, c->per_z, c->per_gamma, mrange[1], mrange[2], d_part, nsplit,
+                                d_out, c->stream);
+    }
     if (e.ok()) e = cuda_ok(cudaMemcpyAsync(h.data(), d_out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
                                             c->stream), "field readback");
     if (e.ok()) e = cuda_ok(cudaStreamSynchronize(c->stream), "field readback");
     dfree(d_pts);
     dfree(d_out);
+    if (d_part) dfree(d_part);
     if (!e.ok()) return fail(c, e);
     // add the incident plane wave E = e exp(i k.x), B = khat x E (FP64 on the host)
     for (int b = 0; b < nrhs; ++b) {

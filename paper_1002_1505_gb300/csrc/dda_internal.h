@@ -340,6 +340,12 @@ Err farfield_moments(const int32_t* ijk, const double* origin3, const double* nh
 // E then B, (re, im) x 3, FP64; dipoles nearer than one lattice spacing scaled by R^4 (5 - 4R).
 Err near_field(const int32_t* ijk, const double* origin3, const double2* p, int nrhs, int64_t n, const double* pts,
                int64_t npts, double kd, double* out, cudaStream_t st);
+// The same for a periodic target: replicas (0, m py, l pz), |m| <= my, |l| <= mz, moments times
+// e^{i k.R}, each term weighted by exp[-(gamma kd D)^4] (dropped beyond 40 in the exponent); part:
+// nrhs * nsplit * npts * 12 doubles of partial sums, added in a fixed order into out.
+Err near_field_pbc(const int32_t* ijk, const double* origin3, const double2* p, int nrhs, int64_t n, const double* pts,
+                   int64_t npts, double kd, const double k_tf[3], double py, double pz, double gamma, int my, int mz,
+                   double* part, int nsplit, double* out, cudaStream_t st);
 // Measurement probe: nvec 8-point complex vectors through `reps` unitary DFT-8 stages, on FP32
 // butterflies and on split-TF32 tensor-core products; out = {fp32 ms, tensor ms, fp32 error,
 // tensor error} (relative L2 against FP64 on the first 64 vectors).

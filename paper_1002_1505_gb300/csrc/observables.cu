@@ -377,6 +377,48 @@ __global__ void k_torque_ext_fin(const double* part, int nblk, double* out7) {
 // contribution of dipoles closer than one lattice spacing scaled by phi(R) = R^4 (5 - 4 R);
 // grid (point chunks, nrhs); out[rhs][point][12] = E (re, im) x 3, then B.
 constexpr int kNfPts = 4;
+
+// E and B of the point dipole P (complex 3-vector) at separation (dx, dy, dz) from it, times the
+// weight w (the near suppression, and for periodic targets the Bloch phase is in P and the cutoff in
+// w), added to acc[0..5] (E) and acc[6..11] (B):
+//   E = e^{ikR} { k^2 (n x p) x n / R + [3 n (n.p) - p] (1/R^3 - i k/R^2) },  B = e^{ikR} (n x p) (k^2/R + i k/R^2)
+__device__ __forceinline__ void dipole_term(double dx, double dy, double dz, const double2 (&P)[3], double kd, double w,
+                                            double* acc) {
+  const double R2 = dx * dx + dy * dy + dz * dz;
+  const double R = sqrt(R2), iR = 1.0 / R;
+  const double nv[3] = {dx * iR, dy * iR, dz * iR};
+  const double k2 = kd * kd;
+  double sn, cs;
+  sincos(kd * R, &sn, &cs);
+  double2 nxp[3];
+  for (int a = 0; a < 3; ++a) {
+    const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+    nxp[a] = make_double2(nv[a1] * P[a2].x - nv[a2] * P[a1].x, nv[a1] * P[a2].y - nv[a2] * P[a1].y);
+  }
+  const double2 ndp = make_double2(nv[0] * P[0].x + nv[1] * P[1].x + nv[2] * P[2].x,
+                                   nv[0] * P[0].y + nv[1] * P[1].y + nv[2] * P[2].y);
+  const double2 f = make_double2(iR * iR * iR, -kd * iR * iR);  // (1/R^3 - i k/R^2)
+  const double2 ph = make_double2(cs * w, sn * w);
+  const double2 gb = make_double2(k2 * iR, kd * iR * iR);
+  for (int a = 0; a < 3; ++a) {
+    const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+    // ((n x p) x n)_a = (nxp)_{a1} n_{a2} - (nxp)_{a2} n_{a1}
+    const double2 t1 = make_double2((nxp[a1].x * nv[a2] - nxp[a2].x * nv[a1]) * k2 * iR,
+                                    (nxp[a1].y * nv[a2] - nxp[a2].y * nv[a1]) * k2 * iR);
+    const double2 u = make_double2(3.0 * nv[a] * ndp.x - P[a].x, 3.0 * nv[a] * ndp.y - P[a].y);
+    const double2 t2 = make_double2(u.x * f.x - u.y * f.y, u.x * f.y + u.y * f.x);
+    const double2 e = make_double2(t1.x + t2.x, t1.y + t2.y);
+    acc[2 * a] += e.x * ph.x - e.y * ph.y;
+    acc[2 * a + 1] += e.x * ph.y + e.y * ph.x;
+    const double2 bb = make_double2(nxp[a].x * gb.x - nxp[a].y * gb.y, nxp[a].x * gb.y + nxp[a].y * gb.x);
+    acc[6 + 2 * a] += bb.x * ph.x - bb.y * ph.y;
+    acc[6 + 2 * a + 1] += bb.x * ph.y + bb.y * ph.x;
+  }
+}
+
+// near suppression of a dipole closer than one lattice spacing: (R/d)^4 (5 - 4 R/d)
+__device__ __forceinline__ double near_suppression(double R) { return R < 1.0 ? R * R * R * R * (5.0 - 4.0 * R) : 1.0; }
+
 __global__ void __launch_bounds__(kT) k_near_field(const int32_t* __restrict__ ijk, const double* __restrict__ org,
                                                    const double2* __restrict__ p, int64_t n,
                                                    const double* __restrict__ pts, int64_t npts, double kd,
@@ -390,7 +432,6 @@ __global__ void __launch_bounds__(kT) k_near_field(const int32_t* __restrict__ i
 #pragma unroll
   for (int q = 0; q < kNfPts; ++q)
     for (int a = 0; a < 3; ++a) xq[q][a] = (q0 + q < npts) ? pts[(q0 + q) * 3 + a] : 1e300;
-  const double k2 = kd * kd;
   for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
     const double r[3] = {ijk[3 * j] + org[0], ijk[3 * j + 1] + org[1], ijk[3 * j + 2] + org[2]};
     double2 P[3];
@@ -401,38 +442,7 @@ __global__ void __launch_bounds__(kT) k_near_field(const int32_t* __restrict__ i
       const double dx = xq[q][0] - r[0], dy = xq[q][1] - r[1], dz = xq[q][2] - r[2];
       const double R2 = dx * dx + dy * dy + dz * dz;
       if (R2 == 0.0) continue;
-      const double R = sqrt(R2), iR = 1.0 / R;
-      const double nv[3] = {dx * iR, dy * iR, dz * iR};
-      const double phi = R < 1.0 ? R2 * R2 * (5.0 - 4.0 * R) : 1.0;
-      double sn, cs;
-      sincos(kd * R, &sn, &cs);
-      // n x p, n . p (complex)
-      double2 nxp[3];
-      for (int a = 0; a < 3; ++a) {
-        const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
-        nxp[a] = make_double2(nv[a1] * P[a2].x - nv[a2] * P[a1].x, nv[a1] * P[a2].y - nv[a2] * P[a1].y);
-      }
-      const double2 ndp = make_double2(nv[0] * P[0].x + nv[1] * P[1].x + nv[2] * P[2].x,
-                                       nv[0] * P[0].y + nv[1] * P[1].y + nv[2] * P[2].y);
-      // E = e^{ikR} { k^2 (n x p) x n / R + [3 n (n.p) - p] (1/R^3 - i k/R^2) }
-      const double2 f = make_double2(iR * iR * iR, -kd * iR * iR);     // (1/R^3 - i k/R^2)
-      const double2 ph = make_double2(cs * phi, sn * phi);
-      // B = e^{ikR} (n x p) (k^2/R + i k/R^2)
-      const double2 gb = make_double2(k2 * iR, kd * iR * iR);
-      for (int a = 0; a < 3; ++a) {
-        const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
-        // ((n x p) x n)_a = (nxp)_{a1} n_{a2} - (nxp)_{a2} n_{a1}
-        const double2 t1 = make_double2((nxp[a1].x * nv[a2] - nxp[a2].x * nv[a1]) * k2 * iR,
-                                        (nxp[a1].y * nv[a2] - nxp[a2].y * nv[a1]) * k2 * iR);
-        const double2 u = make_double2(3.0 * nv[a] * ndp.x - P[a].x, 3.0 * nv[a] * ndp.y - P[a].y);
-        const double2 t2 = make_double2(u.x * f.x - u.y * f.y, u.x * f.y + u.y * f.x);
-        const double2 e = make_double2(t1.x + t2.x, t1.y + t2.y);
-        acc[q * 12 + 2 * a] += e.x * ph.x - e.y * ph.y;
-        acc[q * 12 + 2 * a + 1] += e.x * ph.y + e.y * ph.x;
-        const double2 bb = make_double2(nxp[a].x * gb.x - nxp[a].y * gb.y, nxp[a].x * gb.y + nxp[a].y * gb.x);
-        acc[q * 12 + 6 + 2 * a] += bb.x * ph.x - bb.y * ph.y;
-        acc[q * 12 + 6 + 2 * a + 1] += bb.x * ph.y + bb.y * ph.x;
-      }
+      dipole_term(dx, dy, dz, P, kd, near_suppression(sqrt(R2)), acc + q * 12);
     }
   }
   __shared__ double res[kNfPts * 12];
@@ -441,6 +451,71 @@ __global__ void __launch_bounds__(kT) k_near_field(const int32_t* __restrict__ i
   for (int i = threadIdx.x; i < kNfPts * 12; i += blockDim.x) {
     const int q = i / 12;
     if (q0 + q < npts) out[((int64_t)b * npts + q0 + q) * 12 + (i % 12)] = res[i];
+  }
+}
+
+// Periodic targets: the replicas R = (0, m P_y, l P_z), |m| <= my, |l| <= mz, of every dipole, with
+// moment P e^{i k.R} and weight exp[-(gamma k D)^4] on top of the near suppression, terms with
+// (gamma k D)^4 > 40 dropped.  grid (nsplit, point chunks, nrhs): CTA s takes every nsplit-th
+// block of the (dipole, replica) pairs; part[(b * nsplit + s) * npts + q][12] partial sums, added
+// in a fixed order by k_nf_sum.
+__global__ void __launch_bounds__(kT) k_near_field_pbc(const int32_t* __restrict__ ijk, const double* __restrict__ org,
+                                                       const double2* __restrict__ p, int64_t n,
+                                                       const double* __restrict__ pts, int64_t npts, double kd,
+                                                       double ky, double kz, double py, double pz, double gamma, int my,
+                                                       int mz, double* __restrict__ part) {
+  const int s = blockIdx.x, nsplit = gridDim.x, b = blockIdx.z;
+  const int64_t q0 = (int64_t)blockIdx.y * kNfPts;
+  double acc[kNfPts * 12];
+#pragma unroll
+  for (int i = 0; i < kNfPts * 12; ++i) acc[i] = 0.0;
+  double xq[kNfPts][3];
+#pragma unroll
+  for (int q = 0; q < kNfPts; ++q)
+    for (int a = 0; a < 3; ++a) xq[q][a] = (q0 + q < npts) ? pts[(q0 + q) * 3 + a] : 1e300;
+  const int64_t nrep = (int64_t)(2 * my + 1) * (2 * mz + 1);
+  const int64_t pairs = n * nrep;
+  const double gk = gamma * kd;
+  for (int64_t idx = (int64_t)s * blockDim.x + threadIdx.x; idx < pairs; idx += (int64_t)nsplit * blockDim.x) {
+    const int64_t j = idx % n, rep = idx / n;
+    const int m = (int)(rep / (2 * mz + 1)) - my, l = (int)(rep % (2 * mz + 1)) - mz;
+    const double Ry = m * py, Rz = l * pz;
+    double sn, cs;
+    sincos(ky * Ry + kz * Rz, &sn, &cs);
+    const double r[3] = {ijk[3 * j] + org[0], ijk[3 * j + 1] + org[1] + Ry, ijk[3 * j + 2] + org[2] + Rz};
+    double2 P[3];
+    for (int c = 0; c < 3; ++c) {
+      const double2 v = p[((int64_t)b * 3 + c) * n + j];
+      P[c] = make_double2(v.x * cs - v.y * sn, v.x * sn + v.y * cs);
+    }
+#pragma unroll
+    for (int q = 0; q < kNfPts; ++q) {
+      if (q0 + q >= npts) continue;
+      const double dx = xq[q][0] - r[0], dy = xq[q][1] - r[1], dz = xq[q][2] - r[2];
+      const double R2 = dx * dx + dy * dy + dz * dz;
+      if (R2 == 0.0) continue;
+      const double R = sqrt(R2), t = gk * R, t4 = t * t * t * t;
+      if (t4 > 40.0) continue;
+      dipole_term(dx, dy, dz, P, kd, near_suppression(R) * exp(-t4), acc + q * 12);
+    }
+  }
+  __shared__ double res[kNfPts * 12];
+  bred<kNfPts * 12>(acc, res);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kNfPts * 12; i += blockDim.x) {
+    const int q = i / 12;
+    if (q0 + q < npts) part[(((int64_t)b * nsplit + s) * npts + q0 + q) * 12 + (i % 12)] = res[i];
+  }
+}
+
+// out[b][q][i] = sum over s (in order) of part[b][s][q][i]
+__global__ void k_nf_sum(const double* __restrict__ part, int nsplit, int64_t npts, int nrhs, double* __restrict__ out) {
+  const int64_t total = (int64_t)nrhs * npts * 12;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = i / (npts * 12), rem = i - b * npts * 12;
+    double acc = 0.0;
+    for (int s = 0; s < nsplit; ++s) acc += part[((b * nsplit + s) * npts) * 12 + rem];
+    out[i] = acc;
   }
 }
 
@@ -453,6 +528,22 @@ Err near_field(const int32_t* ijk, const double* origin3, const double2* p, int 
   k_near_field<<<dim3((unsigned)nchunk, nrhs), kT, 0, st>>>(ijk, origin3, p, n, pts, npts, kd, out);
   DDA_CU(cudaGetLastError());
   add_launches(1);
+  return Err::Ok();
+}
+
+Err near_field_pbc(const int32_t* ijk, const double* origin3, const double2* p, int nrhs, int64_t n, const double* pts,
+                   int64_t npts, double kd, const double k_tf[3], double py, double pz, double gamma, int my, int mz,
+                   double* part, int nsplit, double* out, cudaStream_t st) {
+  const int64_t nchunk = (npts + kNfPts - 1) / kNfPts;
+  if (nchunk > 65535 || nrhs > 65535 || nsplit < 1) return Err::make(DDA_EINVAL, "too many field points");
+  k_near_field_pbc<<<dim3((unsigned)nsplit, (unsigned)nchunk, (unsigned)nrhs), kT, 0, st>>>(
+      ijk, origin3, p, n, pts, npts, kd, k_tf[1], k_tf[2], py, pz, gamma, my, mz, part);
+  DDA_CU(cudaGetLastError());
+  const int64_t total = (int64_t)nrhs * npts * 12;
+  k_nf_sum<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((total + kT - 1) / kT, 1216)), kT, 0, st>>>(
+      part, nsplit, npts, nrhs, out);
+  DDA_CU(cudaGetLastError());
+  add_launches(2);
   return Err::Ok();
 }
 

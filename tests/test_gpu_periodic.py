@@ -191,3 +191,43 @@ def test_scattering_cones_match_oracle(D, periods):
     length = periods[0] or periods[1]
     csca = np.mean([(q[b, 0] - q[b, 1]) * math.pi * aeff ** 2 for b in range(2)]) / length
     assert tot == pytest.approx(csca, rel=1e-4)
+
+
+def test_near_field_of_periodic_targets_matches_oracle(D):
+    """DDfield for periodic targets (the replicas' dipoles with their Bloch phases and the cutoff on
+    each term): E and B against the oracle at points inside, near and away from an infinite slab
+    (normal incidence) and a doubly periodic array (oblique incidence); behind the slab |E|^2 is
+    the (0, 0) transmission coefficient the library reports."""
+    from oracle import nearfield as onf
+    nl, m, kd, gamma = 8, 1.5 + 0.1j, 0.2, 0.04
+    ijk = np.stack([np.arange(nl), np.zeros(nl, int), np.zeros(nl, int)], 1)
+    tt = o_targets.Target(ijk=ijk, box=(nl, 1, 1), origin=np.zeros(3), a1=np.array([1.0, 0, 0]),
+                          a2=np.array([0, 1.0, 0]))
+    cases = [
+        (tt, (1.0, 1.0), gamma, (0.0, 0.0, 0.0), kd, m, "LATTDR",
+         np.array([[-15.0, 0.3, 0.2], [25.0, 0.1, 0.7], [3.5, 0.5, 0.5], [0.2, 0.1, 0.0]])),
+        (o_targets.make_target("ELLIPSOID", (3, 4, 3)), (8.0, 7.0), 0.005, (0.3, 0.5, 0.7), 1.0, 1.4 + 0.05j, "GKDLDR",
+         np.array([[-6.0, 1.0, 2.0], [0.3, 4.0, 3.5], [7.0, -2.0, 1.0]])),
+    ]
+    for t, periods, gam, ori, k, mm, presc, pts in cases:
+        prob = odda.build_problem(None, None, mm, None, presc, [ori], target=t, kd=k, iorth=2, periods=periods,
+                                  gamma=gam)
+        ps, _ = odda.solve(prob, "lu")
+        ctx = D.Context(0)
+        ctx.dda_setup_target(t.ijk, origin=t.origin)
+        ctx.dda_set_periodicity(periods[0], periods[1], gam)
+        ctx.dda_set_incident(k, [ori], [[0, 0], [1, 0], [0, 0]], 2)
+        ctx.dda_build_green_fft()
+        ctx.dda_set_polarizability(presc, mm)
+        p = torch.from_numpy(np.ascontiguousarray(np.stack(ps))).cuda()
+        E, B = ctx.dda_near_field(p, pts)
+        for b in range(2):
+            rh = prob.rhs[b]
+            Er, Br = onf.fields_at(pts, k, t.r, ps[b], rh.k_tf, rh.e_tf, periods=periods, gamma=gam)
+            for i in range(len(pts)):
+                assert np.linalg.norm(E[b, i] - Er[i]) <= 1e-9 * np.linalg.norm(Er[i]), (periods, b, i)
+                assert np.linalg.norm(B[b, i] - Br[i]) <= 1e-9 * np.linalg.norm(Br[i]), (periods, b, i)
+        if periods == (1.0, 1.0):
+            _, _, tr = ctx.dda_periodic_scattering(p, [(0, 0)], mueller=False, tr=True)
+            for b in range(2):
+                assert abs(np.vdot(E[b, 1], E[b, 1]).real - tr[b, 0, 0]) <= 4e-3 * tr[b, 0, 0]

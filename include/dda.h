@@ -77,11 +77,18 @@ enum { DDA_CM = 1, DDA_LATTDR = 2, DDA_GKDLDR = 3 };
  * equations, Petravic & Kuo-Petravic 1979, the guide's PETRKP) and
  * BiCGstab(2) (Sleijpen & Fokkema 1993, the method family of the guide's
  * recommended PBCGS2, without that routine's reliability refinements). */
-enum { DDA_BICGSTAB = 1, DDA_CCG = 2, DDA_BICGSTAB2 = 3, DDA_COCG = 4 };
+enum { DDA_BICGSTAB = 1, DDA_CCG = 2, DDA_BICGSTAB2 = 3, DDA_COCG = 4, DDA_QMRCS = 5 };
 /* DDA_COCG: conjugate orthogonal conjugate gradients (van der Vorst & Melissen
  * 1990), CG with the unconjugated form x^T y, valid because A is complex
  * symmetric (A^T = A); one product per iteration (the complex-symmetric
- * Lanczos family of the guide's QMRCCG option). */
+ * Lanczos family of the guide's QMRCCG option).
+ * DDA_QMRCS: QMR for complex-symmetric A (Freund 1992, the guide's QMRCCG
+ * option), on the symmetric Lanczos process without look-ahead; one product per
+ * iteration; stops when sqrt(n + 1) |tau_bar| (its bound on the true residual
+ * after n steps) reaches tol |E|; complex128 only (DDA_EUNSUPPORTED for the
+ * complex64 and mixed precisions: without look-ahead its Lanczos vectors meet
+ * near breakdowns, v^T v ~ 0, that complex64 cannot carry).  Both need A
+ * complex symmetric: not for periodic targets at oblique incidence. */
 /* Preconditioning of the iterations (guide, "Choice of Iterative Algorithm":
  * the guide's solvers are preconditioned Krylov methods): none, or Jacobi, the
  * diagonal of A, applied symmetrically -- the solver iterates on
@@ -271,7 +278,7 @@ DDA_API dda_status dda_matvec(dda_ctx *ctx, const void *p_dev, void *ap_dev, int
 DDA_API dda_status dda_matvec_noalloc(dda_ctx *ctx, const void *p_dev, void *ap_dev, int nrhs, int dtype);
 
 typedef struct {
-  int solver;        /* DDA_BICGSTAB, DDA_CCG, DDA_BICGSTAB2 or DDA_COCG */
+  int solver;        /* DDA_BICGSTAB, DDA_CCG, DDA_BICGSTAB2, DDA_COCG or DDA_QMRCS */
   int precision;     /* DDA_PREC_C64 / DDA_PREC_C128 / DDA_PREC_MIXED */
   double tol;        /* stop when |E - A P| / |E| <= tol for every RHS */
   int maxit;         /* iteration cap (inner iterations summed for MIXED) */

@@ -631,6 +631,7 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
   const bool ccg = (o.solver == DDA_CCG);
   const bool b2 = (o.solver == DDA_BICGSTAB2);
   const bool cocg = (o.solver == DDA_COCG);
+  const bool qmr = (o.solver == DDA_QMRCS);
   if (b2 && !kv.u2) return Err::make(DDA_ESTATE, "BiCGstab(2) needs the extra Krylov vector");
   // preconditioned solves iterate on the scaled operator S A S (every product below)
   struct JacobiScope {
@@ -642,6 +643,8 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
   if (have_x0) DDA_TRY(matvec<C>(c, kv.x, kv.r, nrhs, 0, false));
   if (cocg) {
     DDA_TRY(dda::cocg_init<C>(kv, ks, rb, nrhs, n3, tol, have_x0, st));
+  } else if (qmr) {
+    DDA_TRY(dda::qmr_init<C>(kv, ks, rb, nrhs, n3, tol, have_x0, st));
   } else if (ccg) {
     DDA_TRY(dda::ccg_init<C>(kv, ks, rb, nrhs, n3, tol, have_x0, st));
     DDA_TRY(matvec<C>(c, kv.r, kv.s, nrhs, 0, true));
@@ -686,6 +689,9 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
     } else if (cocg) {
       DDA_TRY(matvec<C>(c, kv.p, kv.v, nrhs, 0, false, ks));
       DDA_TRY(dda::cocg_update<C>(kv, ks, rb, nrhs, n3, st));
+    } else if (qmr) {
+      DDA_TRY(matvec<C>(c, kv.p, kv.v, nrhs, 0, false, ks));
+      DDA_TRY(dda::qmr_update<C>(kv, ks, rb, nrhs, n3, st));
     } else if (ccg) {
       DDA_TRY(matvec<C>(c, kv.p, kv.v, nrhs, 0, false, ks));
       DDA_TRY(dda::ccg_alpha_update<C>(kv, ks, rb, nrhs, n3, st));
@@ -718,7 +724,7 @@ Err krylov(dda_ctx* c, const dda_solve_opts& o, const dda::KrylovVecs<C>& kv, do
     DDA_TRY(ensure_work<C>(c, nrhs, &cap));
     const char* fe = std::getenv("DDA_FUSE");
     if constexpr (std::is_same<C, float2>::value) {
-      fused = !(fe && std::atoi(fe) == 0) && !ccg && !b2 && !cocg && c->t64.fast && cap >= nrhs;
+      fused = !(fe && std::atoi(fe) == 0) && !ccg && !b2 && !cocg && !qmr && c->t64.fast && cap >= nrhs;
       if (fused) {
         // the folded reductions' table follows the vector kernels' table in the same buffer
         const int nx = dda::x_ctas_per_rhs_c64(Sel<float2>::geom(c), c->t64);
@@ -1460,13 +1466,19 @@ dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_sol
   if (!c->have_alpha || !c->have_green)
     return fail(c, Err::make(DDA_ESTATE, "set target, incidence, Green tensor and alpha first"));
   dda_solve_opts o = *opt;
-  if (o.solver != DDA_BICGSTAB && o.solver != DDA_CCG && o.solver != DDA_BICGSTAB2 && o.solver != DDA_COCG)
+  if (o.solver != DDA_BICGSTAB && o.solver != DDA_CCG && o.solver != DDA_BICGSTAB2 && o.solver != DDA_COCG &&
+      o.solver != DDA_QMRCS)
     return fail(c, Err::make(DDA_EINVAL, "unknown solver"));
   if (o.precond != DDA_PRECOND_NONE && o.precond != DDA_PRECOND_JACOBI)
     return fail(c, Err::make(DDA_EINVAL, "unknown preconditioner"));
   if (o.precision < DDA_PREC_C64 || o.precision > DDA_PREC_MIXED)
     return fail(c, Err::make(DDA_EINVAL, "unknown precision"));
   if (!(o.tol > 0) || o.maxit < 1) return fail(c, Err::make(DDA_EINVAL, "tol must be > 0 and maxit >= 1"));
+  // QMR without look-ahead needs FP64 vectors: a plane-wave start across several wavelengths makes
+  // v^T v nearly vanish (near breakdown of the symmetric Lanczos process, |v^T v| ~ 1e-8 |v|^2 on the
+  // guide's Au block), and w = A v - alpha v - beta v_prev then cancels beyond complex64's precision
+  if (o.solver == DDA_QMRCS && o.precision != DDA_PREC_C128)
+    return fail(c, Err::make(DDA_EUNSUPPORTED, "QMR-CS runs in complex128 only (no look-ahead)"));
   // Default streams cannot be captured: run the solve on a context-owned stream
   // ordered after the caller's work (the call is synchronous, so nothing is
   // needed afterwards).

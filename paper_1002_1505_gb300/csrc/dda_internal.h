@@ -221,6 +221,11 @@ struct KState {
   double rr;      // |r|^2 (recursive)
   double zz;      // CCG |A^H r|^2
   double tol2;    // (tol)^2 * |b|^2 threshold for this solve
+  // QMR (complex symmetric): Givens rotations G_{n-1} = (q_c1, q_s1), G_{n-2} = (q_c2, q_s2), the
+  // rotated right-hand side entry q_tb, v_{n-1}^T v_{n-1} (q_dp), |w| of the last step (q_rho), and
+  // the current column's entries r_{n-2,n}, r_{n-1,n}, r_{n,n} (q_r2, q_r1, q_rn) and tau_n (q_tau)
+  double2 q_s1, q_s2, q_tb, q_dp, q_r1, q_r2, q_rn, q_tau;
+  double q_c1, q_c2, q_rho;
   int done;       // 1 = converged, 2 = breakdown
   int it;
   int mv;         // products with A applied to this RHS (products of finished RHS are skipped)
@@ -267,6 +272,14 @@ template <typename C> Err b2_mr(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, 
 // COCG (complex-symmetric CG): init; then per iteration [v = A p], update (alpha, x/r, beta, p).
 template <typename C> Err cocg_init(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, double tol,
                                     bool have_ax, cudaStream_t st);
+// QMR for complex-symmetric A (Freund 1992), no look-ahead: v_n in p, v_{n-1} in r, A v_n / w in v,
+// the direction vectors d_n, d_{n-1}, d_{n-2} rotating through s, t, rhat.  Stops when the bound
+// sqrt(n + 1) |tau_bar_{n+1}| on the true residual reaches tol |b| (unit-norm Lanczos vectors).
+// The solve runs it in complex128 only (near breakdowns of the Lanczos process, see dda_solve).
+template <typename C> Err qmr_init(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, double tol,
+                                   bool have_ax, cudaStream_t st);
+template <typename C> Err qmr_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3,
+                                     cudaStream_t st);
 template <typename C> Err cocg_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3,
                                       cudaStream_t st);
 // dst = c0 s0 + c1 s1 over n3 complex128 elements

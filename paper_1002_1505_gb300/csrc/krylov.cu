@@ -615,6 +615,200 @@ __global__ void k_cocg_p(KrylovVecs<C> kv, const KState* ks, int64_t n3) {
   VEC_LOOP(n3) kv.p[o + i] = cadd(kv.r[o + i], cmul(be, kv.p[o + i]));
 }
 
+// ------------------------------------------------------------------ QMR, complex symmetric
+// Freund's QMR on the symmetric Lanczos process of A (A^T = A): v_1 = r0/|r0|,
+// w = A v_n - alpha_n v_n - beta_n v_{n-1} with alpha_n = v_n^T A v_n / v_n^T v_n and
+// beta_n = |w_{n-1}| v_n^T v_n / v_{n-1}^T v_{n-1}, v_{n+1} = w / |w|; the tridiagonal columns are
+// reduced by complex Givens rotations and x advances along d_n = (v_n - r_{n-1,n} d_{n-1} -
+// r_{n-2,n} d_{n-2}) / r_{n,n} by tau_n.
+
+__device__ __forceinline__ double cabsd(double2 a) { return hypot(a.x, a.y); }
+
+// r0 = b - A x0 (A x0 in r when have_ax) into p, v_{n-1} = r = 0, d buffers = 0; |b|^2, |r0|^2
+template <typename C>
+__global__ void k_qmr_init(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3, bool have_ax, double tol) {
+  const int b = blockIdx.y;
+  const int64_t o = (int64_t)b * n3;
+  double acc[2] = {0.0, 0.0};
+  VEC_LOOP(n3) {
+    const double2 bv = to_d(kv.b[o + i]);
+    double2 rv = bv;
+    if (have_ax) {
+      const double2 ax = to_d(kv.r[o + i]);
+      rv = make_double2(bv.x - ax.x, bv.y - ax.y);
+    }
+    const C rc = from_d<C>(rv);
+    kv.p[o + i] = rc;
+    kv.r[o + i] = czero<C>();
+    kv.s[o + i] = czero<C>();
+    kv.t[o + i] = czero<C>();
+    kv.rhat[o + i] = czero<C>();
+    if (!have_ax) kv.x[o + i] = czero<C>();
+    acc[0] = nrm_acc(acc[0], bv);
+    acc[1] = nrm_acc(acc[1], to_d(rc));
+  }
+  double t[2];
+  if (last_block_totals<2>(acc, rb, b, t) && threadIdx.x == 0) {
+    KState& k = ks[b];
+    const double rho = sqrt(t[1]);
+    k.bb = t[0];
+    k.rr = t[1];
+    k.tol2 = tol * tol * t[0];
+    k.q_rho = rho;                    // scale of v_1 (beta_1 = 0 makes its use moot)
+    k.q_tb = make_double2(rho, 0.0);  // tau_bar_1
+    k.q_dp = make_double2(1.0, 0.0);
+    k.q_c1 = k.q_c2 = 1.0;
+    k.q_s1 = k.q_s2 = make_double2(0.0, 0.0);
+    k.it = 0;
+    k.mv = 0;
+    k.done = (t[0] == 0.0 || t[1] <= k.tol2) ? 1 : 0;
+  }
+}
+
+// v_1 = r0 / |r0|
+template <typename C>
+__global__ void k_qmr_scale(KrylovVecs<C> kv, const KState* ks, int64_t n3) {
+  const int b = blockIdx.y;
+  const KState k = ks[b];
+  if (k.done) return;
+  const C f = from_d<C>(make_double2(1.0 / k.q_rho, 0.0));
+  const int64_t o = (int64_t)b * n3;
+  VEC_LOOP(n3) kv.p[o + i] = cmul(f, kv.p[o + i]);
+}
+
+// delta = v^T v, v^T q (q = A v in v) -> alpha, beta; v^T v becomes the next step's delta_prev
+template <typename C>
+__global__ void k_qmr_dots(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
+  pdl_begin();
+  const int b = blockIdx.y;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  if (!ks[b].done) {
+    const int64_t o = (int64_t)b * n3;
+    Acc<C> dr, di, gr, gi;
+    VEC_LOOP(n3) {
+      const C vv = kv.p[o + i], qv = kv.v[o + i];
+      acc_bdot(dr, di, vv, vv);
+      acc_bdot(gr, gi, vv, qv);
+    }
+    acc[0] = dr.get();
+    acc[1] = di.get();
+    acc[2] = gr.get();
+    acc[3] = gi.get();
+  }
+  double t[4];
+  if (last_block_totals<4>(acc, rb, b, t) && threadIdx.x == 0) {
+    KState& k = ks[b];
+    if (k.done) return;
+    k.mv += 1;  // q = A v_n
+    const double2 delta = make_double2(t[0], t[1]);
+    if (delta.x == 0.0 && delta.y == 0.0) { k.done = 2; return; }  // Lanczos breakdown (no look-ahead)
+    k.alpha = cdiv(make_double2(t[2], t[3]), delta);
+    k.beta = k.it > 0 ? cdiv(make_double2(k.q_rho * delta.x, k.q_rho * delta.y), k.q_dp) : make_double2(0.0, 0.0);
+    k.q_dp = delta;
+  }
+}
+
+// w = q - alpha v - beta v_{n-1} (into v); |w| -> rotations, tau_n, the column entries
+template <typename C>
+__global__ void k_qmr_w(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
+  pdl_begin();
+  const int b = blockIdx.y;
+  const KState k = ks[b];
+  double acc[1] = {0.0};
+  if (!k.done) {
+    const C al = from_d<C>(k.alpha), be = from_d<C>(k.beta);
+    const int64_t o = (int64_t)b * n3;
+    Acc<C> ww;
+    VEC_LOOP(n3) {
+      const C w = csub(csub(kv.v[o + i], cmul(al, kv.p[o + i])), cmul(be, kv.r[o + i]));
+      kv.v[o + i] = w;
+      acc_nrm(ww, w);
+    }
+    acc[0] = ww.get();
+  }
+  double t[1];
+  if (last_block_totals<1>(acc, rb, b, t) && threadIdx.x == 0) {
+    KState& kw = ks[b];
+    if (kw.done) return;
+    const double rho_next = sqrt(t[0]);
+    const double2 alpha = kw.alpha, beta = kw.beta;
+    // column n of the tridiagonal (beta, alpha, rho_next) through G_{n-2}, G_{n-1}
+    const double2 r2 = cmuld(kw.q_s2, beta);
+    const double2 f = make_double2(kw.q_c2 * beta.x, kw.q_c2 * beta.y);
+    const double2 s1c = make_double2(kw.q_s1.x, -kw.q_s1.y);
+    const double2 sa = cmuld(kw.q_s1, alpha), sf = cmuld(s1c, f);
+    const double2 r1 = make_double2(kw.q_c1 * f.x + sa.x, kw.q_c1 * f.y + sa.y);
+    const double2 g = make_double2(-sf.x + kw.q_c1 * alpha.x, -sf.y + kw.q_c1 * alpha.y);
+    // G_n takes (g, rho_next) to (r_nn, 0): c real, s complex
+    double c, rn_abs;
+    double2 sn, rn;
+    if (rho_next == 0.0) {
+      c = 1.0; sn = make_double2(0.0, 0.0); rn = g; rn_abs = cabsd(g);
+    } else if (g.x == 0.0 && g.y == 0.0) {
+      c = 0.0; sn = make_double2(1.0, 0.0); rn = make_double2(rho_next, 0.0); rn_abs = rho_next;
+    } else {
+      const double ga = cabsd(g), h = hypot(ga, rho_next);
+      const double2 ph = make_double2(g.x / ga, g.y / ga);
+      c = ga / h;
+      sn = make_double2(ph.x * rho_next / h, ph.y * rho_next / h);  // ph conj(rho_next) / h, rho_next real
+      rn = make_double2(ph.x * h, ph.y * h);
+      rn_abs = h;
+    }
+    if (rn_abs == 0.0) { kw.done = 2; return; }
+    const double2 tb = kw.q_tb;
+    kw.q_tau = make_double2(c * tb.x, c * tb.y);
+    const double2 snc = make_double2(-sn.x, sn.y);  // -conj(s)
+    kw.q_tb = cmuld(snc, tb);
+    kw.q_r1 = r1;
+    kw.q_r2 = r2;
+    kw.q_rn = rn;
+    kw.q_c2 = kw.q_c1;
+    kw.q_s2 = kw.q_s1;
+    kw.q_c1 = c;
+    kw.q_s1 = sn;
+    kw.q_rho = rho_next;
+    kw.it += 1;
+  }
+}
+
+// d_n = (v_n - r_{n-1,n} d_{n-1} - r_{n-2,n} d_{n-2}) / r_nn into the oldest d slot, x += tau_n d_n,
+// v_{n-1} = v_n, v_{n+1} = w / |w|; the last block tests sqrt(n + 1) |tau_bar| <= tol |b|
+template <typename C>
+__global__ void k_qmr_dx(KrylovVecs<C> kv, KState* ks, RedBuf rb, int64_t n3) {
+  pdl_begin();
+  const int b = blockIdx.y;
+  const KState k = ks[b];
+  double acc[1] = {0.0};
+  if (!k.done) {
+    C* dbuf[3] = {kv.s, kv.t, kv.rhat};
+    const int n = k.it;
+    C* dn = dbuf[n % 3];
+    const C* d1 = dbuf[(n + 2) % 3];
+    const C* d2 = dbuf[(n + 1) % 3];
+    const double2 irn = cdiv(make_double2(1.0, 0.0), k.q_rn);
+    const C r1 = from_d<C>(k.q_r1), r2 = from_d<C>(k.q_r2), inv = from_d<C>(irn), tau = from_d<C>(k.q_tau);
+    const C sc = from_d<C>(make_double2(k.q_rho > 0.0 ? 1.0 / k.q_rho : 0.0, 0.0));
+    const int64_t o = (int64_t)b * n3;
+    VEC_LOOP(n3) {
+      const C vn = kv.p[o + i];
+      const C d = cmul(inv, csub(csub(vn, cmul(r1, d1[o + i])), cmul(r2, d2[o + i])));
+      dn[o + i] = d;
+      kv.x[o + i] = cadd(kv.x[o + i], cmul(tau, d));
+      kv.r[o + i] = vn;
+      kv.p[o + i] = cmul(sc, kv.v[o + i]);
+    }
+  }
+  double t[1];
+  if (last_block_totals<1>(acc, rb, b, t) && threadIdx.x == 0) {
+    KState& kw = ks[b];
+    if (kw.done) return;
+    const double tb2 = kw.q_tb.x * kw.q_tb.x + kw.q_tb.y * kw.q_tb.y;
+    kw.rr = (kw.it + 1) * tb2;  // bound on |r|^2
+    if (kw.rr <= kw.tol2) kw.done = 1;
+    else if (kw.q_rho == 0.0) kw.done = 2;  // invariant subspace reached without meeting the bound
+  }
+}
+
 // ------------------------------------------------------------------ Jacobi scaling of site vectors
 // v[b][c][j] *= s[b][comp(j, c)][c] (or /= with inv), the diagonal S of the scaled system S A S.
 template <typename C>
@@ -993,6 +1187,28 @@ Err cocg_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_
   return Err::Ok();
 }
 
+template <typename C>
+Err qmr_init(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, double tol, bool have_ax,
+             cudaStream_t st) {
+  k_qmr_init<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, rb, n3, have_ax, tol);
+  DDA_CU(cudaGetLastError());
+  k_qmr_scale<C><<<vgrid(rb, nrhs), kThreads, 0, st>>>(kv, ks, n3);
+  DDA_CU(cudaGetLastError());
+  add_launches(2);
+  return Err::Ok();
+}
+
+template <typename C>
+Err qmr_update(const KrylovVecs<C>& kv, KState* ks, RedBuf rb, int nrhs, int64_t n3, cudaStream_t st) {
+  DDA_CU(launch_k(k_qmr_dots<C>, vgrid(rb, nrhs), dim3(kThreads), 0, st, kv, ks, rb, n3));
+  CHECK_LAUNCH();
+  DDA_CU(launch_k(k_qmr_w<C>, vgrid(rb, nrhs), dim3(kThreads), 0, st, kv, ks, rb, n3));
+  CHECK_LAUNCH();
+  DDA_CU(launch_k(k_qmr_dx<C>, vgrid(rb, nrhs), dim3(kThreads), 0, st, kv, ks, rb, n3));
+  CHECK_LAUNCH();
+  return Err::Ok();
+}
+
 Err combine2_c128(double2* dst, const double2* s0, const double2* s1, double2 c0, double2 c1, int64_t n3,
                   cudaStream_t st) {
   const int nb = (int)std::min<int64_t>((n3 + kThreads * 4 - 1) / (kThreads * 4), 1024);
@@ -1095,6 +1311,8 @@ Err add_to_c128(double2* dst, const C* src, const int* mask_done, int nrhs, int6
   template Err b2_mr<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, cudaStream_t);                  \
   template Err cocg_init<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, double, bool, cudaStream_t); \
   template Err cocg_update<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, cudaStream_t);            \
+  template Err qmr_init<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, double, bool, cudaStream_t); \
+  template Err qmr_update<C>(const KrylovVecs<C>&, KState*, RedBuf, int, int64_t, cudaStream_t);            \
   template Err scale_sites<C>(C*, const C*, const uint8_t*, int, int, int64_t, bool, cudaStream_t);
 INST(float2)
 INST(double2)

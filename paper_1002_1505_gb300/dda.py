@@ -22,7 +22,7 @@ DDA_OK, DDA_EINVAL, DDA_ENOMEM, DDA_ECUDA, DDA_ENOCONV, DDA_ETIMEOUT, DDA_ESTATE
 DDA_C64, DDA_C128, DDA_C128DF = 1, 2, 3  # DDA_C128DF: complex128 vectors, double-float arithmetic
 SHAPES = {"ELLIPSOID": 1, "RCTGLPRSM": 2, "CYLINDER1": 3, "HEX_PRISM": 4}
 PRESCRIPTIONS = {"CM": 1, "LATTDR": 2, "GKDLDR": 3}
-SOLVERS = {"BICGSTAB": 1, "CCG": 2, "BICGSTAB2": 3, "COCG": 4}
+SOLVERS = {"BICGSTAB": 1, "CCG": 2, "BICGSTAB2": 3, "COCG": 4, "QMRCS": 5}
 PRECONDS = {"NONE": 0, "JACOBI": 1}
 PRECISIONS = {"C64": 1, "C128": 2, "MIXED": 3}
 STATUS_NAMES = ["DDA_OK", "DDA_EINVAL", "DDA_ENOMEM", "DDA_ECUDA", "DDA_ENOCONV", "DDA_ETIMEOUT", "DDA_ESTATE",

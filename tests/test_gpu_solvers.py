@@ -1,6 +1,7 @@
 """Solver variants on the GPU against the FP64 oracle: COCG (conjugate orthogonal conjugate
 gradients, van der Vorst & Melissen 1990; one product per iteration, the complex-symmetric family of
-the guide's QMRCCG option) and symmetric Jacobi preconditioning (the solver iterates on S A S with
+the guide's QMRCCG option), QMR for complex-symmetric A (Freund 1992, the guide's QMRCCG) and
+symmetric Jacobi preconditioning (the solver iterates on S A S with
 S = diag(alpha^{1/2})).
 
 Bars: Q_ext / Q_abs / Q_sca 1e-4 relative against the oracle solved to 1e-10 (or LU); solutions of
@@ -90,6 +91,68 @@ def test_cocg_worked_example_au_block(D):
         assert q[b, 1] == pytest.approx(g["Qabs"], rel=2e-3)
         assert q[b, 2] == pytest.approx(g["Qsca"], rel=2e-3)
     print("COCG iterations on the Au block:", [r["iters"] for r in reps])
+
+
+def test_qmrcs_sphere12_cross_sections(D):
+    """QMR for complex-symmetric A (the guide's QMRCCG option) on the GPU: efficiencies and solutions
+    of the sphere against the oracle's LU and one product per iteration; complex64 and mixed
+    precision are refused (no look-ahead: the Lanczos near breakdowns need FP64)."""
+    prob, ps, qref = _sphere12_lu()
+    ctx = _ctx(D, W.SPHERE12)
+    p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
+    for precision in ("MIXED", "C64"):
+        with pytest.raises(D.DDAError) as ei:
+            ctx.dda_solve(p, solver="QMRCS", precision=precision, tol=1e-5, maxit=2000)
+        assert ei.value.status == D.DDA_EUNSUPPORTED
+    precision = "C128"
+    reps, _ = ctx.dda_solve(p, solver="QMRCS", precision=precision, tol=1e-5, maxit=2000)
+    assert all(r["converged"] == 1 and r["true_rel_resid"] <= 1e-5 for r in reps)
+    assert all(r["matvecs"] <= r["iters"] + 4 for r in reps)  # one product per iteration
+    q, _ = ctx.dda_cross_sections(p)
+    got = p.cpu().numpy()
+    for b in range(ctx.nrhs):
+        for i, key in enumerate(("Qext", "Qabs", "Qsca")):
+            assert q[b, i] == pytest.approx(qref[b][key], rel=1e-4), (precision, key, b)
+        assert np.linalg.norm(got[b] - ps[b]) / np.linalg.norm(ps[b]) <= 1e-4
+
+
+def test_qmrcs_follows_the_oracle(D):
+    """Complex128 QMR on the GPU and the oracle's QMR (same recurrences: symmetric Lanczos, complex
+    Givens rotations) after the same number of steps: the iterates agree to 1e-9 and so do the true
+    residuals, at 3, 8 and 14 steps (before the quasi-residual bound stops the GPU's iteration: QMR's
+    quasi-residual keeps falling below the attainable accuracy, and the sphere converges in ~20)."""
+    prob, ps, _ = _sphere12_lu()
+    for steps in (3, 8, 14):
+        ctx = _ctx(D, W.SPHERE12)
+        p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
+        reps, _ = ctx.dda_solve(p, solver="QMRCS", precision="C128", tol=1e-15, maxit=steps, check_every=1,
+                                raise_on_noconv=False)
+        got = p.cpu().numpy()
+        for b in range(ctx.nrhs):
+            assert reps[b]["iters"] == steps
+            rh = prob.rhs[b]
+            shape = rh.e_inc.shape
+            op = lambda v, b=b: odda.apply_a(prob, b, v.reshape(shape), "direct").reshape(-1)
+            x, it, hist, qhist = osol.qmr_cs(op, rh.e_inc.reshape(-1), tol=0.0, maxit=steps)
+            assert it == steps
+            assert np.linalg.norm(got[b].reshape(-1) - x) / np.linalg.norm(x) <= 1e-9, (steps, b)
+            assert reps[b]["true_rel_resid"] == pytest.approx(hist[-1], rel=1e-6, abs=1e-13), (steps, b)
+
+
+def test_qmrcs_worked_example_au_block(D):
+    """The guide's Au block solved with QMR (complex128, 1e-5): the printed efficiencies to 2e-3
+    (measured: 131 iterations, true residual 1.9e-6, the bound having stopped it)."""
+    g, _ = load_golden("au_block_worked_example.txt")
+    ctx = _ctx(D, W.AU_BLOCK)
+    p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
+    reps, _ = ctx.dda_solve(p, solver="QMRCS", precision="C128", tol=1e-5, maxit=3000)
+    assert all(r["converged"] == 1 for r in reps)
+    q, _ = ctx.dda_cross_sections(p)
+    for b in range(2):
+        assert q[b, 0] == pytest.approx(g["Qext"], rel=2e-3)
+        assert q[b, 1] == pytest.approx(g["Qabs"], rel=2e-3)
+        assert q[b, 2] == pytest.approx(g["Qsca"], rel=2e-3)
+    print("QMR iterations on the Au block:", [r["iters"] for r in reps])
 
 
 def _three_material_target(box):

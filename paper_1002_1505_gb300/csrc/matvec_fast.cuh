@@ -681,7 +681,14 @@ __global__ void __launch_bounds__(256) k_y_rows(Geom g, C* __restrict__ work, co
 // which halves the shared-memory traffic of the column pass at the cost of occupancy.
 template <typename C, int PZ, int G>
 constexpr int zcols_pad() {
-  return (sizeof(C) == 8 && G == 8 && Shape<PZ>::LB % 2 == 0) ? 8 : 0;
+  // complex64: a warp's column group spans 2G words; when that is under the 32 banks, place
+  // consecutive sub-blocks one group width apart (mod 32 words)
+  if constexpr (sizeof(C) != 8 || 2 * G >= 32) {
+    return 0;
+  } else {
+    constexpr int gw = 2 * G, stride = (Shape<PZ>::LB * 3 * G * 2) % 32;
+    return ((gw - stride + 32) % 32) / 2;
+  }
 }
 template <typename C, int PZ, int G>
 constexpr size_t zcols_smem_elems() {

@@ -434,7 +434,8 @@ DDA_API dda_status dda_unet_create(dda_unet **out, int device, void *cuda_stream
 DDA_API void dda_unet_destroy(dda_unet *net);
 /* DDA_ECUDA if a tcgen05 convolution's bounded completion wait gave up since the
  * last call (its outputs are then invalid; the flag is cleared), else DDA_OK.
- * Call after synchronizing the network's stream. */
+ * Call after synchronizing the network's stream; dda_unet_loss_grad makes this
+ * check itself before it returns. */
 DDA_API dda_status dda_unet_check_fault(dda_unet *net);
 DDA_API const char *dda_unet_last_error(const dda_unet *net);
 DDA_API int64_t dda_unet_nparams(const dda_unet *net);

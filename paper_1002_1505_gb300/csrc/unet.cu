@@ -1291,6 +1291,8 @@ dda_status dda_unet_loss_grad(dda_unet* n, const float* x_dev, const float* t_de
       e = Err::make(DDA_ECUDA, "loss copy failed");
   }
   if (!e.ok()) return ufail(n, e);
+  // a tcgen05 convolution whose bounded wait gave up leaves invalid gradients: report it here
+  if (n->use_tc && dda_unet_check_fault(n) != DDA_OK) return DDA_ECUDA;
   double L = 0.0;
   for (int i = 0; i < lb; ++i) L += n->h_loss[i];
   if (loss_out) *loss_out = L;

@@ -161,6 +161,7 @@ def warm_guess(ctx: "D.Context", net: "D.UNet", grid=None, chunk: int = 0):
         net.dda_unet_forward(x[b0:b0 + step].contiguous(), y[b0:b0 + step], grid)
     p = torch.zeros((ctx.nrhs, 3, ctx.n), dtype=torch.complex128, device="cuda")
     D.dda_unet_warm_start(ctx, y, grid, p, residual=True)
+    net.dda_unet_check_fault()
     return p
 
 

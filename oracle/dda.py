@@ -2,6 +2,8 @@
 
 Steps in the guide's order (section "Choice of Iterative Algorithm" for the
 system A P = E; the other sections as cited in the sibling modules).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
 """
 from __future__ import annotations
 

@@ -19,6 +19,8 @@ Three ways to apply A, all FP64:
                  FFT(G) by FFT(P) gives it exactly (up to rounding).
 Vectors are complex arrays of shape (3, N): component-major, like the layout of
 the CUDA library's buffers.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
 """
 from __future__ import annotations
 

@@ -12,6 +12,8 @@ Written from the textbook equations, not from any program listing:
   n_stop = x + 4 x^(1/3) + 2.
 The DDSCAT guide (section "Applicability of the DDA") validates the DDA against
 exact Mie results for pseudospheres; this is that comparison's reference.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
 """
 from __future__ import annotations
 

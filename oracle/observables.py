@@ -21,6 +21,8 @@ N_theta from eta, N_phi(j) per ring, solid-angle weights Omega_jk.  The guide
 gives N_theta as a real expression without its rounding; this oracle rounds it
 to the nearest integer, a reading pinned by the worked example's printed
 number of directions.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
 """
 from __future__ import annotations
 

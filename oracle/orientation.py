@@ -16,6 +16,8 @@
   writes the odd-NTHETA weights as (1/3, 4/3, 2/3)/(NTHETA NPHI), which would
   not sum to one; they are taken here as Simpson's rule on NTHETA - 1
   intervals of cos(Theta), i.e. (1/3, 4/3, 2/3, ..., 4/3, 1/3)/(NTHETA - 1).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
 """
 from __future__ import annotations
 

@@ -17,6 +17,8 @@ k = kd, eps = m^2:
 Every prescription returns the diagonal of 1/alpha (3 complex numbers) for one
 material and one incidence (khat, e).  For real m all three give
 Im(1/alpha) = -(2/3) k^3 exactly, which is what makes C_abs vanish.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
 """
 from __future__ import annotations
 

@@ -26,6 +26,8 @@
 All iterate in FP64 and stop on the true relative residual |E - A P| / |E|;
 `normal_eq_ratio` evaluates the guide's own stopping quantity
 |A^H A P - A^H E| / |A^H E| (guide, eq. err_tol) for reporting.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
 """
 from __future__ import annotations
 

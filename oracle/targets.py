@@ -8,8 +8,11 @@ the centre of the upper x face, so its x runs from -SHPAR_1 to 0.
 
 Inclusion is decided in exact integer arithmetic on doubled coordinates
 u = 2x (always integers), with ties on the surface counted as inside.
-Parity unpinned beyond the checks in the tests (counts, symmetry and the
-worked example's N = 131072).
+Pinned in the tests by brute-force site counts over exact rationals, an
+independent floating-point point-in-hexagon test, cubic symmetry of the
+sphere and the guide's worked example (N = 131072).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
 """
 from __future__ import annotations
 

@@ -764,3 +764,46 @@ def test_solver_reports_nonconvergence(D):
     reps, st = ctx.dda_solve(p, precision="C128", tol=1e-14, maxit=3, raise_on_noconv=False)
     assert st == D.DDA_ENOCONV
     assert all(r["converged"] == 0 and r["true_rel_resid"] > 1e-14 for r in reps)
+
+
+@pytest.mark.parametrize("ijk", [np.array([[0, 0, 0]]), np.stack([np.arange(7), np.zeros(7, int), np.zeros(7, int)], 1),
+                                 np.array([[0, 0, 0], [3, 0, 0], [0, 2, 5]])],
+                         ids=["one_dipole", "line_of_7", "three_scattered"])
+def test_degenerate_targets(D, ijk):
+    """Degenerate targets: a single dipole (no interactions: A = alpha^{-1}, and C_ext = 4 pi k Im(alpha)
+    for real-valued field strength 1 by the optical theorem of one dipole), a one-dimensional line,
+    and three isolated sites; one orientation, one polarization (iorth = 1, a single RHS).  Product
+    against the direct sum and Q_ext / Q_abs against the oracle's LU solution."""
+    ijk = ijk.astype(np.int32)
+    t = o_targets.from_sites(ijk, origin=(0.0, 0.0, 0.0))
+    m, kd = 1.5 + 0.2j, 0.4
+    ori = [(0.3, 0.7, 0.2)]
+    prob = odda.build_problem(None, None, m, None, "GKDLDR", ori, target=t, kd=kd, iorth=1)
+    ctx = D.Context(0)
+    ctx.dda_setup_target(ijk, origin=(0.0, 0.0, 0.0))
+    ctx.dda_set_incident(kd, ori, [[0, 0], [1, 0], [0, 0]], 1)
+    ctx.dda_build_green_fft()
+    ctx.dda_set_polarizability("GKDLDR", m)
+    assert ctx.nrhs == 1 and ctx.n == len(ijk)
+    for dt, tol in ((torch.complex128, 1e-12), (torch.complex64, 1e-5)):
+        p = _rand_p(1, ctx.n, 91, dt)
+        ap = torch.empty_like(p)
+        ctx.dda_matvec(p, ap)
+        torch.cuda.synchronize()
+        ref = odda.apply_a(prob, 0, p.cpu().numpy()[0].astype(np.complex128), "direct")
+        got = ap.cpu().numpy()[0].astype(np.complex128)
+        assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref), dt
+    ps, _ = odda.solve(prob, "lu")
+    qref = odda.cross_sections(prob, ps)
+    p = torch.zeros((1, 3, ctx.n), dtype=torch.complex128, device="cuda")
+    reps, _ = ctx.dda_solve(p, precision="MIXED", tol=1e-9, maxit=200)
+    assert reps[0]["converged"] == 1
+    q, _ = ctx.dda_cross_sections(p)
+    assert q[0, 0] == pytest.approx(qref[0]["Qext"], rel=1e-6)
+    assert q[0, 1] == pytest.approx(qref[0]["Qabs"], rel=1e-6)
+    if len(ijk) == 1:
+        # one dipole: P = alpha E, C_ext = 4 pi k Im(E* . alpha E) with |E| = 1 (alpha diagonal, per axis)
+        rh = prob.rhs[0]
+        alpha = 1.0 / rh.inv_alpha[0]
+        cext = 4 * np.pi * kd * np.imag(np.sum(np.conj(rh.e_tf) * alpha * rh.e_tf))
+        assert q[0, 0] * np.pi * t.aeff ** 2 == pytest.approx(cext, rel=1e-9)

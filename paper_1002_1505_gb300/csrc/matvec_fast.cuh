@@ -634,9 +634,24 @@ __global__ void __launch_bounds__(256) k_y_rows(Geom g, C* __restrict__ work, co
       work[(r0 + r) * PY + y] = s[r * RP + y];
     }
   } else {
-    for (int i = threadIdx.x; i < nr * PY; i += blockDim.x) {
-      const int r = i / PY, y = i % PY;
-      s[r * RP + y] = work[(r0 + r) * PY + y];
+    // the tile's rows are one contiguous run of nr * PY elements; for a full complex64 tile each
+    // thread issues all its loads before its first shared-memory store
+    constexpr int kPer = RPB * PY / 256;
+    if (sizeof(C) == 8 && nr == RPB && RPB * PY % 256 == 0 && kPer <= 16 && blockDim.x == 256) {
+      const C* src = work + r0 * PY;
+      C t[kPer > 0 ? kPer : 1];
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) t[u] = src[threadIdx.x + 256 * u];
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        const int i = threadIdx.x + 256 * u;
+        s[(i / PY) * RP + i % PY] = t[u];
+      }
+    } else {
+      for (int i = threadIdx.x; i < nr * PY; i += blockDim.x) {
+        const int r = i / PY, y = i % PY;
+        s[r * RP + y] = work[(r0 + r) * PY + y];
+      }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nr * 2 * RA; i += blockDim.x) {
@@ -695,8 +710,23 @@ constexpr size_t zcols_smem_elems() {
   return (size_t)PZ + (size_t)PZ * 3 * G + (size_t)2 * Shape<PZ>::RA * zcols_pad<C, PZ, G>();
 }
 
+// CTAs per SM the register budget is sized for: the fused variants 3; the complex64 kernel whose
+// pass B goes through shared memory as many as its shared tile allows (up to 3), so that registers
+// do not cap its occupancy below what shared memory permits
+template <typename C, int PZ, int G, bool RFUSE>
+constexpr int zcols_min_ctas() {
+  if constexpr (RFUSE) {
+    return 3;
+  } else if constexpr (sizeof(C) == 8 && Shape<PZ>::LB * sizeof(C) > 96) {
+    constexpr size_t b = sizeof(C) * zcols_smem_elems<C, PZ, G>() + 1024;
+    return b * 3 <= 228 * 1024 ? 3 : (b * 2 <= 228 * 1024 ? 2 : 1);
+  } else {
+    return 1;
+  }
+}
+
 template <typename C, int PZ, int G, int NT = 256, bool RFUSE = false>
-__global__ void __launch_bounds__(NT, RFUSE ? 3 : 1) k_z_cols(Geom g, MvData<C> d) {
+__global__ void __launch_bounds__(NT, (zcols_min_ctas<C, PZ, G, RFUSE>())) k_z_cols(Geom g, MvData<C> d) {
   constexpr int RA = Shape<PZ>::RA, LB = Shape<PZ>::LB, H = Shape<PZ>::H;
   constexpr int P = zcols_pad<C, PZ, G>();  // spare elements after each sub-block
   constexpr bool kFuse = RFUSE || (LB * sizeof(C) <= 96);
@@ -711,23 +741,58 @@ __global__ void __launch_bounds__(NT, RFUSE ? 3 : 1) k_z_cols(Geom g, MvData<C> 
   __syncthreads();
   C* wb = d.work + ((int64_t)b * 3 * g.px + kx) * ((int64_t)nz * g.ys);
   const int64_t cstride = (int64_t)g.px * nz * g.ys;
-  // forward pass A from global
-  for (int i = threadIdx.x; i < 3 * G * LB; i += blockDim.x) {
-    const int gg = i % G;
-    const int r = i / G;
-    const int c = r % 3, n1 = r / 3;
-    const int ky = ky0 + gg;
-    C x[RA], o[2 * RA];
+  // forward pass A from global.  The column inputs come from HBM (the y pass wrote them), so for
+  // complex64 every load of a thread's items (a compile-time count: blockDim.x == NT) is issued
+  // before its first transform and the round trips overlap instead of following one another.
+  constexpr int kItemsA = 3 * G * LB;
+  constexpr int kItA = (kItemsA + NT - 1) / NT;
+  if constexpr (sizeof(C) == 8 && kItA * RA <= 32) {
+    C xa[kItA][RA];
 #pragma unroll
-    for (int j = 0; j < RA; ++j) {
-      const int zz = n1 + LB * j;
-      x[j] = (zz < nz && ky < py) ? wb[c * cstride + (int64_t)zz * g.ys + ky] : czero<C>();
+    for (int it = 0; it < kItA; ++it) {
+      const int i = threadIdx.x + it * NT;
+      const int gg = i % G, r = i / G;
+      const int c = r % 3, n1 = r / 3;
+      const bool ok = i < kItemsA && ky0 + gg < py;
+#pragma unroll
+      for (int j = 0; j < RA; ++j) {
+        const int zz = n1 + LB * j;
+        xa[it][j] = (ok && zz < nz) ? wb[c * cstride + (int64_t)zz * g.ys + ky0 + gg] : czero<C>();
+      }
     }
-    f2::passA_fwd<PZ>(x, n1, tw, o);
 #pragma unroll
-    for (int bb = 0; bb < 2; ++bb)
+    for (int it = 0; it < kItA; ++it) {
+      const int i = threadIdx.x + it * NT;
+      if (i < kItemsA) {
+        const int gg = i % G, r = i / G;
+        const int c = r % 3, n1 = r / 3;
+        C o[2 * RA];
+        f2::passA_fwd<PZ>(xa[it], n1, tw, o);
 #pragma unroll
-      for (int k = 0; k < RA; ++k) s[((bb * H + n1 + LB * k) * 3 + c) * G + gg + (bb * RA + k) * P] = o[bb * RA + k];
+        for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+          for (int k = 0; k < RA; ++k)
+            s[((bb * H + n1 + LB * k) * 3 + c) * G + gg + (bb * RA + k) * P] = o[bb * RA + k];
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i < kItemsA; i += blockDim.x) {
+      const int gg = i % G;
+      const int r = i / G;
+      const int c = r % 3, n1 = r / 3;
+      const int ky = ky0 + gg;
+      C x[RA], o[2 * RA];
+#pragma unroll
+      for (int j = 0; j < RA; ++j) {
+        const int zz = n1 + LB * j;
+        x[j] = (zz < nz && ky < py) ? wb[c * cstride + (int64_t)zz * g.ys + ky] : czero<C>();
+      }
+      f2::passA_fwd<PZ>(x, n1, tw, o);
+#pragma unroll
+      for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+        for (int k = 0; k < RA; ++k) s[((bb * H + n1 + LB * k) * 3 + c) * G + gg + (bb * RA + k) * P] = o[bb * RA + k];
+    }
   }
   __syncthreads();
   const C* gk = d.ghat + (int64_t)kx * PZ * py * 6;

@@ -2180,7 +2180,8 @@ dda_status dda_angular_averages(dda_ctx* c, const void* p_dev, double eta, doubl
     return fail(c, Err::make(DDA_EUNSUPPORTED, "not available for periodic targets (scattering goes into diffraction orders)"));
   if (!c->have_inc) return fail(c, Err::make(DDA_ESTATE, "set the target and the incident beams first"));
   try {
-    Err e = set_dev(c);
+    Err e = need_device(c);
+    if (e.ok()) e = set_dev(c);
     if (!e.ok()) return fail(c, e);
     const double pi = 3.14159265358979323846;
     const int nrhs = c->nrhs;

@@ -223,3 +223,53 @@ def test_periodicity_arguments(D):
         ctx.dda_set_periodicity(8.0, 0.0, gamma=0.0)
     ctx.dda_set_periodicity(8.0, 0.0, 0.02)
     ctx.dda_set_periodicity(0.0, 0.0)        # finite again
+
+
+def test_device_entry_points_refuse_a_host_only_context(D):
+    """Every call that does device work, reached through the C ABI with a fully set-up host-only
+    context, returns a status (DDA_ESTATE: no device, no Green tensor) before touching its buffer
+    arguments; the context stays usable afterwards.  The buffers here are host memory on purpose:
+    a call that went on to launch work would fault or fail with a CUDA error instead."""
+    import ctypes
+    L = D.LIB
+    ctx = D.Context(-1)
+    ctx.dda_setup_shape("ELLIPSOID", (5, 6, 7))
+    kd, _ = ctx.dda_kd_from_x(1.0)
+    ctx.dda_set_incident(kd, [(0, 0, 0), (0.3, 0.2, 0.1)])
+    ctx.dda_set_polarizability("LATTDR", 1.5 + 0.1j)
+    h, n, nrhs = ctx._h, ctx.n, ctx.nrhs
+    alpha_before = ctx.dda_get_inv_alpha()
+    buf = np.zeros(nrhs * 3 * n * 2 + 64)
+    pb = buf.ctypes.data_as(ctypes.c_void_p)
+    out = np.zeros(4096)
+    po = out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    i32 = np.zeros(64, dtype=np.int32)
+    pi = i32.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    opts = D.dda_solve_opts(D.SOLVERS["BICGSTAB"], D.PRECISIONS["MIXED"], 1e-5, 100, 0.0, 0.0, 0, 8, 0, 1,
+                            D.PRECONDS["NONE"], 0)
+    reps = (D.dda_solve_report * nrhs)()
+    handles = (ctypes.c_void_p * 1)(h.value)
+    bufs = (ctypes.c_void_p * 1)(pb.value)
+    sts = (ctypes.c_int * 1)(-1)
+    calls = {
+        "dda_incident_field": lambda: L.dda_incident_field(h, pb, D.DDA_C128),
+        "dda_build_green_fft": lambda: L.dda_build_green_fft(h, None),
+        "dda_matvec": lambda: L.dda_matvec(h, pb, pb, nrhs, D.DDA_C128),
+        "dda_matvec (double-float)": lambda: L.dda_matvec(h, pb, pb, nrhs, D.DDA_C128DF),
+        "dda_matvec_noalloc": lambda: L.dda_matvec_noalloc(h, pb, pb, nrhs, D.DDA_C64),
+        "dda_solve": lambda: L.dda_solve(h, ctypes.byref(opts), pb, reps),
+        "dda_solve_batch": lambda: L.dda_solve_batch(handles, 1, ctypes.byref(opts), bufs, None, sts),
+        "dda_cross_sections": lambda: L.dda_cross_sections(h, pb, po, None, 0, None),
+        "dda_profile_matvec": lambda: L.dda_profile_matvec(h, nrhs, D.DDA_C64, 1, po, pi),
+        "dda_schedule_info": lambda: L.dda_schedule_info(h, D.DDA_C64, pi),
+        "dda_angular_averages": lambda: L.dda_angular_averages(h, pb, ctypes.c_double(0.5), po, pi),
+        "dda_force_torque": lambda: L.dda_force_torque(h, pb, ctypes.c_double(0.5), po, pi),
+        "dda_near_field": lambda: L.dda_near_field(h, pb, po, ctypes.c_int64(1), po, None),
+        "dda_periodic_scattering": lambda: L.dda_periodic_scattering(h, pb, 1, po, None, None, None),
+    }
+    for name, call in calls.items():
+        assert call() == D.DDA_ESTATE, (name, L.dda_last_error(h))
+        assert L.dda_last_error(h), name
+    assert not np.any(buf), "a refused call wrote into its buffer"
+    np.testing.assert_array_equal(ctx.dda_get_inv_alpha(), alpha_before)
+    assert ctx.dda_kd_from_x(1.0)[0] == kd

@@ -1272,8 +1272,14 @@ dda_status dda_set_polarizability(dda_ctx* c, int presc, const double* m_reim, i
       const cd ev[3] = {cd(g.e[0], g.e[1]), cd(g.e[2], g.e[3]), cd(g.e[4], g.e[5])};
       for (int m = 0; m < ncomp; ++m) {
         const cd mm(m_reim[2 * m], m_reim[2 * m + 1]);
+        if (!std::isfinite(mm.real()) || !std::isfinite(mm.imag()))
+          return fail(c, Err::make(DDA_EINVAL, "refractive index is not finite"));
         if (std::abs(mm * mm - 1.0) == 0.0) return fail(c, Err::make(DDA_EINVAL, "m = 1 has no polarizability"));
-        inv_alpha(presc, mm, c->kd, kh, ev, &ia[((size_t)b * ncomp + m) * 3]);
+        cd* out = &ia[((size_t)b * ncomp + m) * 3];
+        inv_alpha(presc, mm, c->kd, kh, ev, out);
+        for (int a = 0; a < 3; ++a)
+          if (!std::isfinite(out[a].real()) || !std::isfinite(out[a].imag()))
+            return fail(c, Err::make(DDA_EINVAL, "1/alpha is not finite for this refractive index"));
       }
     }
     std::vector<double2> h128(ia.size());

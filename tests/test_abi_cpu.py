@@ -273,3 +273,30 @@ def test_device_entry_points_refuse_a_host_only_context(D):
     assert not np.any(buf), "a refused call wrote into its buffer"
     np.testing.assert_array_equal(ctx.dda_get_inv_alpha(), alpha_before)
     assert ctx.dda_kd_from_x(1.0)[0] == kd
+
+
+def test_degenerate_inputs_on_the_host(D):
+    """Empty and one-site targets, non-finite indices and beams: each is refused with DDA_EINVAL
+    or, where it is a valid problem (one dipole, a one-cell shape), accepted with the right sizes."""
+    ctx = D.Context(-1)
+    with pytest.raises(D.DDAError) as ei:
+        ctx.dda_setup_target(np.zeros((0, 3), dtype=np.int32))
+    assert ei.value.status == D.DDA_EINVAL
+    ctx.dda_setup_target(np.array([[3, -2, 7]], dtype=np.int32))
+    n, box = ctx.dda_get_box()
+    assert n == 1 and tuple(box) == (1, 1, 1)
+    for shape in ("ELLIPSOID", "RCTGLPRSM", "CYLINDER1", "HEX_PRISM"):
+        ctx.dda_setup_shape(shape, (1, 1, 1))
+        assert ctx.n == 1, shape
+    for bad in (float("nan"), float("inf"), 0.0, -1.0):
+        with pytest.raises(D.DDAError) as ei:
+            ctx.dda_set_incident(bad, [(0, 0, 0)])
+        assert ei.value.status == D.DDA_EINVAL, bad
+    ctx.dda_set_incident(0.3, [(0, 0, 0), (0.1, 0.2, 0.3)])
+    for m in (complex(float("nan"), 0.0), complex(1.5, float("inf")), 1.0 + 0j):
+        with pytest.raises(D.DDAError) as ei:
+            ctx.dda_set_polarizability("LATTDR", m)
+        assert ei.value.status == D.DDA_EINVAL, m
+    # eps = m^2 = -2 is the pole of the Clausius-Mossotti alpha; 1/alpha stays finite there
+    ctx.dda_set_polarizability("CM", 1j * math.sqrt(2.0))
+    assert np.all(np.isfinite(ctx.dda_get_inv_alpha()))

@@ -48,6 +48,23 @@ def dist_env():
     return ws, rank, local
 
 
+def workload_config(w, n, box, pad, ws):
+    """The config object of the JSON line, the same for both arms: workload w with n sites in its
+    box on the padded grid, orientations sharded over ws ranks (rank 0's share is the one named)."""
+    from paper_1002_1505_gb300 import replicas
+    a_o, b_o = replicas.shard(len(w.orientations), 0, ws)
+    n_ori = b_o - a_o
+    nrhs = n_ori * w.iorth
+    return {"workload": w.name, "n_dipoles": int(n), "box": [int(v) for v in box], "pad": [int(v) for v in pad],
+            "nrhs": nrhs * ws, "n_orientations": len(w.orientations), "tol": 1e-5,
+            "solver": "BiCGstab, complex64 + FP64-accurate refinement",
+            "true_residual": "double-float product (FP32 pairs, within 1e-12 of FP64) where the grid "
+                             "has compile-time kernels, else complex128",
+            "l2": "flushed (512 MB write) before every step",
+            "parallelism": f"replicas x{ws}: orientations sharded over ranks, "
+                           f"{n_ori} orientations ({nrhs} RHS) per rank"}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -213,8 +230,7 @@ def run_reference(args, w):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "matvecs/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": w.name, "n_dipoles": prob.target.n, "box": list(prob.target.box),
-                       "pad": list(prob.pad), "nrhs": len(prob.rhs), "parallelism": "replicas"},
+            "config": workload_config(w, prob.target.n, prob.target.box, prob.pad, dist_env()[0]),
             "cpu_baseline": {"value": value, "unit": "matvecs/s", "cores": cores, "kind": "oracle",
                              "sample": f"{per_step} FFT-convolution products A.P (FP64, scipy.fft, workers={cores}) "
                                        f"per step on {w.name}"},
@@ -553,14 +569,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "matvecs/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
-            "config": {"workload": w.name, "n_dipoles": n, "box": list(box), "pad": list(pad),
-                       "nrhs": nrhs * ws, "n_orientations": len(w.orientations), "tol": 1e-5,
-                       "solver": "BiCGstab, complex64 + FP64-accurate refinement",
-                       "true_residual": "double-float product (FP32 pairs, within 1e-12 of FP64) where the grid "
-                                        "has compile-time kernels, else complex128",
-                       "l2": "flushed (512 MB write) before every step",
-                       "parallelism": f"replicas x{ws}: orientations sharded over ranks, "
-                                      f"{n_ori} orientations ({nrhs} RHS) per rank"},
+            "config": workload_config(w, n, box, pad, ws),
             "solve_ms_per_orientation": ms_step / n_ori,
             "plain_fp64_solve_ms_per_orientation": plain_ms_per_ori,
             "plain_fp64_orientations_timed": len(plain_ori),

@@ -60,3 +60,49 @@ def test_bench_workloads_match_their_documented_sizes():
     # the sizes the bench line and the profiles quote
     assert _sizes(W.ELLIPSOID64) == (51488, (64, 48, 32))
     assert _sizes(W.PRISM48)[0] == 110592
+
+
+def _run_bench(args, env_extra=None):
+    import json
+    import os
+    import subprocess
+    import sys
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = subprocess.run([sys.executable, os.path.join(root, "bench.py")] + args, capture_output=True, text=True,
+                         env=env, timeout=300)
+    assert res.returncode == 0, res.stderr[-2000:]
+    lines = [ln for ln in res.stdout.splitlines() if ln.startswith("{")]
+    return [json.loads(ln) for ln in lines]
+
+
+@pytest.mark.parametrize("ws", [1, 2])
+def test_reference_arm_line_and_config(ws):
+    """`bench.py --impl reference` (the oracle on the host cores) prints one line with the contract's
+    keys on rank 0, nothing on the other ranks, and the same config object the GPU arm prints for
+    the same workload and world size (its sites and box from the library's host-only set-up)."""
+    from paper_1002_1505_gb300 import dda as D
+    w = W.SPHERE12
+    env = {"WORLD_SIZE": str(ws), "RANK": "0", "LOCAL_RANK": "0"}
+    out = _run_bench(["--impl", "reference", "--workload", "sphere12", "--gpus", str(ws), "--steps", "2",
+                      "--warmup", "3"], env)
+    assert len(out) == 1
+    line = out[0]
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "matvecs/s"
+    assert line["n_gpus"] == ws and line["steps"] == 2 and line["warmup"] == 3 and line["higher_is_better"]
+    assert line["value"] > 0 and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": "matvecs/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    ctx = D.Context(-1)
+    n, box = ctx.dda_setup_shape(w.shape, w.shpar)
+    pad = w.pad if w.pad else tuple(2 * v for v in box)
+    assert line["config"] == bench.workload_config(w, n, box, pad, ws)
+    if ws > 1:
+        env["RANK"] = "1"
+        assert _run_bench(["--impl", "reference", "--workload", "sphere12", "--gpus", str(ws), "--steps", "2"],
+                          env) == []

@@ -163,7 +163,8 @@ DDA_API dda_status dda_setup_target_anifrm(dda_ctx *ctx, const int32_t *ixyz, co
                                            const double origin_tf[3], const double a1[3], const double a2[3],
                                            const double *df_angles);
 
-/* Copy the site list out: ixyz_out host N x 3 (box-relative lattice indices),
+/* Copy the site list out (guide, "Target Generation: Isolated Finite Targets": the
+ * dipole sites of the target on the lattice): ixyz_out host N x 3 (box-relative lattice indices),
  * origin_out[3] = TF position of box index (0,0,0).  Either may be NULL. */
 DDA_API dda_status dda_get_sites(dda_ctx *ctx, int32_t *ixyz_out, double origin_out[3]);
 
@@ -213,12 +214,16 @@ DDA_API dda_status dda_set_incident(dda_ctx *ctx, double kd, const double *ori, 
 /* Number of right-hand sides defined by dda_set_incident (0 before). */
 DDA_API int dda_nrhs(const dda_ctx *ctx);
 
-/* Copy the incidence out: k_tf host nrhs x 3 (k vector in the Target Frame,
+/* Copy the incidence out (guide, "Orientation of the Incident Beam in the Target
+ * Frame" and "Incident Polarization State"): k_tf host nrhs x 3 (k vector in the Target Frame,
  * lattice units), e_tf host nrhs x 6 (polarization in the TF, (re, im) x 3).
  * Either may be NULL. */
 DDA_API dda_status dda_get_incidence(dda_ctx *ctx, double *k_tf, double *e_tf);
 
-/* Write E_inc,j = e exp(i k . r_j) for every RHS into e_dev ([nrhs][3][N],
+/* Write the incident plane wave at the sites (the right-hand side E of the guide's
+ * A P = E, "Choice of Iterative Algorithm"; beam and polarization from "Orientation of
+ * the Incident Beam in the Target Frame" and "Incident Polarization State"):
+ * E_inc,j = e exp(i k . r_j) for every RHS into e_dev ([nrhs][3][N],
  * dtype DDA_C64 or DDA_C128), phases evaluated in FP64. */
 DDA_API dda_status dda_incident_field(dda_ctx *ctx, void *e_dev, int dtype);
 
@@ -238,10 +243,13 @@ DDA_API dda_status dda_build_green_fft(dda_ctx *ctx, const int32_t pad[3]);
  * per RHS (they depend on the incidence) in FP64. */
 DDA_API dda_status dda_set_polarizability(dda_ctx *ctx, int prescription, const double *m_reim, int ncomp);
 
-/* Copy the diagonal of alpha^{-1} out: host nrhs x ncomp x 3 complex (re, im). */
+/* Copy the diagonal of alpha^{-1} out (guide, "Dipole Polarizabilities": the diagonal
+ * blocks of A): host nrhs x ncomp x 3 complex (re, im). */
 DDA_API dda_status dda_get_inv_alpha(dda_ctx *ctx, double *out);
 
-/* ap_dev = A p_dev for the first nrhs right-hand sides, both [nrhs][3][N] of
+/* The product with the DDA matrix (guide, eq. AP=E in "Choice of Iterative Algorithm";
+ * the off-diagonal part as the FFT convolution of "Choice of FFT Algorithm"):
+ * ap_dev = A p_dev for the first nrhs right-hand sides, both [nrhs][3][N] of
  * dtype DDA_C64 or DDA_C128 (may not alias); DDA_C128DF takes and returns
  * complex128 vectors and computes in double-float arithmetic.  Enqueue only. */
 DDA_API dda_status dda_matvec(dda_ctx *ctx, const void *p_dev, void *ap_dev, int nrhs, int dtype);
@@ -312,13 +320,17 @@ typedef struct {
   double normal_eq_ratio;/* guide's eq. err_tol: |A^H A P - A^H E| / |A^H E| (NAN if not computed) */
 } dda_solve_report;
 
-/* Solve A P = E_inc for every RHS.  p_dev: [nrhs][3][N] complex128 (always
+/* Solve A P = E_inc for every RHS (guide, "Choice of Iterative Algorithm"; stopping
+ * rule: the true relative residual, with the guide's normal-equation ratio of "Error
+ * Tolerance" reported on request).  p_dev: [nrhs][3][N] complex128 (always
  * FP64 storage), initial guess when opt->warm_start, solution on return.
  * rep: host array of nrhs reports (may be NULL).  Returns DDA_ENOCONV if any
  * RHS missed tol within maxit (p_dev and rep still hold the last iterate). */
 DDA_API dda_status dda_solve(dda_ctx *ctx, const dda_solve_opts *opt, void *p_dev, dda_solve_report *rep);
 
-/* Solve several targets at once (mixed batches: targets of uneven grid sizes
+/* Solve several targets at once (the guide runs independent problems as separate
+ * processes, "MPI: Message Passing Interface"; here they share one device), for mixed
+ * batches: targets of uneven grid sizes
  * on one device).  ctxs[i] are distinct contexts on the same
  * device, each fully set up (target, incidence, Green tensor, alpha) with its
  * own product schedule; p_devs[i] their complex128 [nrhs_i][3][N_i] buffers;
@@ -406,7 +418,7 @@ DDA_API dda_status dda_profile_matvec(dda_ctx *ctx, int nrhs, int dtype, int ite
  * HBM blocks with bulk copies (TMA), info[7] = field components per CTA of the
  * x passes (3 or 1; 0 for the generic engine), info[8] = 1 when the 5-pass z
  * columns run pass B, the Ghat multiply and the inverse pass B of the three
- * components in registers (the tuner's choice for long z transforms); info[9..11]
+ * components in registers (a tuner candidate for long z transforms); info[9..11]
  * are reserved (0). */
 DDA_API dda_status dda_schedule_info(dda_ctx *ctx, int dtype, int32_t info[12]);
 

@@ -170,7 +170,7 @@ DDA_API dda_status dda_get_sites(dda_ctx *ctx, int32_t *ixyz_out, double origin_
 
 /* The current target's site count and bounding box (cells per axis, x y z), as
  * dda_setup_shape reports them; n_out and box_out may be NULL.  DDA_ESTATE
- * without a target. */
+ * without a target (the context is const: no dda_last_error message). */
 DDA_API dda_status dda_get_box(const dda_ctx *ctx, int64_t *n_out, int32_t box_out[3]);
 
 /* Periodic targets (guide, "Target Generation: Periodic Targets" and
@@ -198,8 +198,9 @@ DDA_API dda_status dda_set_periodicity(dda_ctx *ctx, double py, double pz, doubl
  * definitions of a_eff and x): the target's effective radius is
  * a_eff = (3 N / 4 pi)^(1/3) d, the radius of a sphere of volume N d^3, and
  * x = k a_eff, so kd = x / (a_eff / d).  x > 0.  Outputs (either may be NULL):
- * *kd_out = kd, *aeff_out = a_eff / d.  DDA_ESTATE without a target.  Host only;
- * pass kd to dda_set_incident. */
+ * *kd_out = kd, *aeff_out = a_eff / d.  DDA_ESTATE without a target, DDA_EINVAL for
+ * x <= 0 or a non-finite x (the context is const: these two set no dda_last_error
+ * message).  Host only; pass kd to dda_set_incident. */
 DDA_API dda_status dda_kd_from_x(const dda_ctx *ctx, double x, double *kd_out, double *aeff_out);
 
 /* Incident beams (guide, "Target Orientation" and "Incident Polarization

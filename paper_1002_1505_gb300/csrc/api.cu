@@ -928,14 +928,16 @@ dda_status dda_setup_target(dda_ctx* c, const int32_t* ixyz, const int32_t* icom
 
 dda_status dda_setup_target_aniso(dda_ctx* c, const int32_t* ixyz, const int32_t* icomp3, int64_t n,
                                   const double origin[3], const double a1[3], const double a2[3]) {
-  if (!icomp3) return DDA_EINVAL;
+  if (!icomp3)
+    return fail(c, Err::make(DDA_EINVAL, "dda_setup_target_aniso: a required pointer is NULL"));
   return setup_sites(c, ixyz, icomp3, n, origin, a1, a2, true);
 }
 
 dda_status dda_setup_target_anifrm(dda_ctx* c, const int32_t* ixyz, const int32_t* icomp3, int64_t n,
                                    const double origin[3], const double a1[3], const double a2[3],
                                    const double* df_angles) {
-  if (!icomp3 || !df_angles) return DDA_EINVAL;
+  if (!icomp3 || !df_angles)
+    return fail(c, Err::make(DDA_EINVAL, "dda_setup_target_anifrm: a required pointer is NULL"));
   return setup_sites(c, ixyz, icomp3, n, origin, a1, a2, true, df_angles);
 }
 
@@ -974,7 +976,7 @@ dda_status dda_set_periodicity(dda_ctx* c, double py, double pz, double gamma) {
 }
 
 dda_status dda_kd_from_x(const dda_ctx* c, double x, double* kd_out, double* aeff_out) {
-  if (!c || !(x > 0) || !std::isfinite(x)) return DDA_EINVAL;
+  if (!c || !(x > 0) || !std::isfinite(x)) return DDA_EINVAL;  // const context: status only
   if (!c->have_target || c->n <= 0) return DDA_ESTATE;
   // a_eff = (3 N / 4 pi)^(1/3) d: the radius of a sphere of the target's volume N d^3
   const double aeff = std::cbrt(3.0 * (double)c->n / (4.0 * 3.14159265358979323846));
@@ -1056,7 +1058,9 @@ dda_status dda_get_incidence(dda_ctx* c, double* k_tf, double* e_tf) {
 }
 
 dda_status dda_incident_field(dda_ctx* c, void* e_dev, int dtype) {
-  if (!c || !e_dev) return DDA_EINVAL;
+  if (!c) return DDA_EINVAL;
+  if (!e_dev)
+    return fail(c, Err::make(DDA_EINVAL, "dda_incident_field: a required pointer is NULL"));
   if (!c->have_inc) return fail(c, Err::make(DDA_ESTATE, "set the incident beams first"));
   Err e = need_device(c);
   if (!e.ok()) return fail(c, e);
@@ -1372,7 +1376,9 @@ dda_status dda_set_polarizability(dda_ctx* c, int presc, const double* m_reim, i
 }
 
 dda_status dda_get_inv_alpha(dda_ctx* c, double* out) {
-  if (!c || !out) return DDA_EINVAL;
+  if (!c) return DDA_EINVAL;
+  if (!out)
+    return fail(c, Err::make(DDA_EINVAL, "dda_get_inv_alpha: a required pointer is NULL"));
   if (!c->have_alpha) return fail(c, Err::make(DDA_ESTATE, "no polarizability"));
   for (size_t i = 0; i < c->ia.size(); ++i) {
     out[2 * i] = c->ia[i].real();
@@ -1382,7 +1388,9 @@ dda_status dda_get_inv_alpha(dda_ctx* c, double* out) {
 }
 
 dda_status dda_matvec(dda_ctx* c, const void* p, void* ap, int nrhs, int dtype) {
-  if (!c || !p || !ap) return DDA_EINVAL;
+  if (!c) return DDA_EINVAL;
+  if (!p || !ap)
+    return fail(c, Err::make(DDA_EINVAL, "dda_matvec: a required pointer is NULL"));
   if (!c->have_alpha || !c->have_green)
     return fail(c, Err::make(DDA_ESTATE, "set target, incidence, Green tensor and alpha first"));
   if (nrhs < 1 || nrhs > c->nrhs) return fail(c, Err::make(DDA_EINVAL, "nrhs out of range"));
@@ -1468,7 +1476,9 @@ Err true_residual(dda_ctx* c, const double2* p, double2* scratch_ax, double2* sc
 }  // namespace
 
 dda_status dda_solve(dda_ctx* c, const dda_solve_opts* opt, void* p_dev, dda_solve_report* rep) {
-  if (!c || !opt || !p_dev) return DDA_EINVAL;
+  if (!c) return DDA_EINVAL;
+  if (!opt || !p_dev)
+    return fail(c, Err::make(DDA_EINVAL, "dda_solve: a required pointer is NULL"));
   if (!c->have_alpha || !c->have_green)
     return fail(c, Err::make(DDA_ESTATE, "set target, incidence, Green tensor and alpha first"));
   dda_solve_opts o = *opt;
@@ -1787,7 +1797,9 @@ void mueller_from_f(const cd f[2][2], cd A, cd B, cd Cc, cd D, double phs, doubl
 
 dda_status dda_cross_sections(dda_ctx* c, const void* p_dev, double* q_out, const double* dirs, int ndir,
                               double* mueller_out) {
-  if (!c || !p_dev) return DDA_EINVAL;
+  if (!c) return DDA_EINVAL;
+  if (!p_dev)
+    return fail(c, Err::make(DDA_EINVAL, "dda_cross_sections: a required pointer is NULL"));
   if (!c->have_alpha || !c->have_green)
     return fail(c, Err::make(DDA_ESTATE, "set target, incidence, Green tensor and alpha first"));
   if (ndir < 0 || (ndir > 0 && (!dirs || !mueller_out))) return fail(c, Err::make(DDA_EINVAL, "bad directions"));
@@ -1900,7 +1912,9 @@ dda_status dda_cross_sections(dda_ctx* c, const void* p_dev, double* q_out, cons
 
 dda_status dda_periodic_scattering(dda_ctx* c, const void* p_dev, int n_spec, const double* spec, double* dirs_out,
                                    double* mueller_out, double* tr_out) {
-  if (!c || !p_dev || n_spec < 1 || !spec) return DDA_EINVAL;
+  if (!c) return DDA_EINVAL;
+  if (!p_dev || n_spec < 1 || !spec)
+    return fail(c, Err::make(DDA_EINVAL, "dda_periodic_scattering: a required pointer is NULL or a size is out of range"));
   if (!c->have_alpha || !c->have_green)
     return fail(c, Err::make(DDA_ESTATE, "set target, incidence, Green tensor and alpha first"));
   if (!c->periodic) return fail(c, Err::make(DDA_EUNSUPPORTED, "the target is not periodic (dda_set_periodicity)"));
@@ -2084,7 +2098,9 @@ Err matvec_fixed_scratch(dda_ctx* c, const C* p, C* ap, int nrhs) {
 }  // namespace
 
 dda_status dda_matvec_noalloc(dda_ctx* c, const void* p, void* ap, int nrhs, int dtype) {
-  if (!c || !p || !ap) return DDA_EINVAL;
+  if (!c) return DDA_EINVAL;
+  if (!p || !ap)
+    return fail(c, Err::make(DDA_EINVAL, "dda_matvec_noalloc: a required pointer is NULL"));
   if (!c->have_alpha || !c->have_green)
     return fail(c, Err::make(DDA_ESTATE, "set target, incidence, Green tensor and alpha first"));
   if (nrhs < 1 || nrhs > c->nrhs) return fail(c, Err::make(DDA_EINVAL, "nrhs out of range"));
@@ -2098,7 +2114,9 @@ dda_status dda_matvec_noalloc(dda_ctx* c, const void* p, void* ap, int nrhs, int
 }
 
 dda_status dda_profile_matvec(dda_ctx* c, int nrhs, int dtype, int iters, double* ms_per_pass, int* npass) {
-  if (!c || !ms_per_pass || !npass || iters < 1) return DDA_EINVAL;
+  if (!c) return DDA_EINVAL;
+  if (!ms_per_pass || !npass || iters < 1)
+    return fail(c, Err::make(DDA_EINVAL, "dda_profile_matvec: a required pointer is NULL or iters < 1"));
   if (!c->have_alpha || !c->have_green)
     return fail(c, Err::make(DDA_ESTATE, "set target, incidence, Green tensor and alpha first"));
   if (nrhs < 1 || nrhs > c->nrhs) return fail(c, Err::make(DDA_EINVAL, "nrhs out of range"));
@@ -2181,7 +2199,9 @@ std::vector<ScaDir> scattering_directions(double x, double eta) {
 }
 
 dda_status dda_angular_averages(dda_ctx* c, const void* p_dev, double eta, double* out, int32_t* ndir_out) {
-  if (!c || !p_dev || !out || !(eta > 0.0)) return DDA_EINVAL;
+  if (!c) return DDA_EINVAL;
+  if (!p_dev || !out || !(eta > 0.0))
+    return fail(c, Err::make(DDA_EINVAL, "dda_angular_averages: a required pointer is NULL or eta is not positive"));
   if (c->periodic)
     return fail(c, Err::make(DDA_EUNSUPPORTED, "not available for periodic targets (scattering goes into diffraction orders)"));
   if (!c->have_inc) return fail(c, Err::make(DDA_ESTATE, "set the target and the incident beams first"));
@@ -2283,7 +2303,9 @@ dda_status dda_angular_averages(dda_ctx* c, const void* p_dev, double eta, doubl
 }
 
 dda_status dda_force_torque(dda_ctx* c, const void* p_dev, double eta, double* out, int32_t* ndir_out) {
-  if (!c || !p_dev || !out || !(eta > 0.0)) return DDA_EINVAL;
+  if (!c) return DDA_EINVAL;
+  if (!p_dev || !out || !(eta > 0.0))
+    return fail(c, Err::make(DDA_EINVAL, "dda_force_torque: a required pointer is NULL or eta is not positive"));
   if (c->periodic)
     return fail(c, Err::make(DDA_EUNSUPPORTED, "not available for periodic targets (scattering goes into diffraction orders)"));
   if (!c->have_inc) return fail(c, Err::make(DDA_ESTATE, "set the target and the incident beams first"));
@@ -2423,7 +2445,9 @@ dda_status dda_force_torque(dda_ctx* c, const void* p_dev, double eta, double* o
 
 dda_status dda_near_field(dda_ctx* c, const void* p_dev, const double* pts, int64_t npts, double* e_out,
                           double* b_out) {
-  if (!c || !p_dev || !pts || !e_out || npts < 1) return DDA_EINVAL;
+  if (!c) return DDA_EINVAL;
+  if (!p_dev || !pts || !e_out || npts < 1)
+    return fail(c, Err::make(DDA_EINVAL, "dda_near_field: a required pointer is NULL or a size is out of range"));
   if (!c->have_inc) return fail(c, Err::make(DDA_ESTATE, "set the target and the incident beams first"));
   try {
     Err e = need_device(c);
@@ -2592,7 +2616,9 @@ dda_status dda_selftest_bulk_wait(int device, int32_t* gave_up) {
 }
 
 dda_status dda_schedule_info(dda_ctx* c, int dtype, int32_t info[12]) {
-  if (!c || !info) return DDA_EINVAL;
+  if (!c) return DDA_EINVAL;
+  if (!info)
+    return fail(c, Err::make(DDA_EINVAL, "dda_schedule_info: a required pointer is NULL"));
   for (int i = 0; i < 12; ++i) info[i] = 0;
   if (!c->have_green) return fail(c, Err::make(DDA_ESTATE, "build the Green tensor first"));
   if (dtype != DDA_C64 && dtype != DDA_C128 && dtype != DDA_C128DF) return fail(c, Err::make(DDA_EINVAL, "bad dtype"));
@@ -2683,7 +2709,9 @@ Err grid_place(dda_ctx* c, const int32_t dims[3], const int32_t off_in[3], int32
 }  // namespace
 
 dda_status dda_unet_features(dda_ctx* c, float* x_dev, const int32_t dims[3], const int32_t offset[3]) {
-  if (!c || !x_dev || !dims) return DDA_EINVAL;
+  if (!c) return DDA_EINVAL;
+  if (!x_dev || !dims)
+    return fail(c, Err::make(DDA_EINVAL, "dda_unet_features: a required pointer is NULL"));
   if (!c->have_alpha) return fail(c, Err::make(DDA_ESTATE, "set target, incidence and alpha first"));
   int32_t off[3];
   Err e = grid_place(c, dims, offset, off);
@@ -2703,7 +2731,9 @@ dda_status dda_unet_features(dda_ctx* c, float* x_dev, const int32_t dims[3], co
 
 dda_status dda_unet_targets(dda_ctx* c, const void* p_dev, float* t_dev, float* mask_dev, const int32_t dims[3],
                             const int32_t offset[3], int residual) {
-  if (!c || !p_dev || !t_dev || !mask_dev || !dims) return DDA_EINVAL;
+  if (!c) return DDA_EINVAL;
+  if (!p_dev || !t_dev || !mask_dev || !dims)
+    return fail(c, Err::make(DDA_EINVAL, "dda_unet_targets: a required pointer is NULL"));
   if (!c->have_alpha) return fail(c, Err::make(DDA_ESTATE, "set target, incidence and alpha first"));
   int32_t off[3];
   Err e = grid_place(c, dims, offset, off);
@@ -2719,7 +2749,9 @@ dda_status dda_unet_targets(dda_ctx* c, const void* p_dev, float* t_dev, float* 
 
 dda_status dda_unet_warm_start(dda_ctx* c, const float* y_dev, const int32_t dims[3], const int32_t offset[3],
                                int residual, void* p_dev) {
-  if (!c || !p_dev || !y_dev || !dims) return DDA_EINVAL;
+  if (!c) return DDA_EINVAL;
+  if (!p_dev || !y_dev || !dims)
+    return fail(c, Err::make(DDA_EINVAL, "dda_unet_warm_start: a required pointer is NULL"));
   if (!c->have_alpha) return fail(c, Err::make(DDA_ESTATE, "set target, incidence and alpha first"));
   int32_t off[3];
   Err e = grid_place(c, dims, offset, off);
@@ -2734,7 +2766,9 @@ dda_status dda_unet_warm_start(dda_ctx* c, const float* y_dev, const int32_t dim
 
 dda_status dda_unet_residual_grad(dda_ctx* c, const float* y_dev, const int32_t dims[3], const int32_t offset[3],
                                   double weight, float* gy_dev, double* loss_out) {
-  if (!c || !y_dev || !gy_dev || !dims) return DDA_EINVAL;
+  if (!c) return DDA_EINVAL;
+  if (!y_dev || !gy_dev || !dims)
+    return fail(c, Err::make(DDA_EINVAL, "dda_unet_residual_grad: a required pointer is NULL"));
   if (!c->have_alpha || !c->have_green)
     return fail(c, Err::make(DDA_ESTATE, "set target, incidence, Green tensor and alpha first"));
   int32_t off[3];

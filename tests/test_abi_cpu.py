@@ -300,3 +300,33 @@ def test_degenerate_inputs_on_the_host(D):
     # eps = m^2 = -2 is the pole of the Clausius-Mossotti alpha; 1/alpha stays finite there
     ctx.dda_set_polarizability("CM", 1j * math.sqrt(2.0))
     assert np.all(np.isfinite(ctx.dda_get_inv_alpha()))
+
+
+def test_null_arguments_give_einval_with_a_message(D):
+    """A NULL buffer or an out-of-range size is refused with DDA_EINVAL before anything else, and
+    dda_last_error names the entry point (the header's convention for every non-const context)."""
+    import ctypes
+    L = D.LIB
+    ctx = D.Context(-1)
+    h = ctx._h
+    out = np.zeros(64)
+    po = out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    calls = {
+        "dda_incident_field": lambda: L.dda_incident_field(h, None, D.DDA_C128),
+        "dda_get_inv_alpha": lambda: L.dda_get_inv_alpha(h, None),
+        "dda_matvec": lambda: L.dda_matvec(h, None, None, 1, D.DDA_C64),
+        "dda_matvec_noalloc": lambda: L.dda_matvec_noalloc(h, None, None, 1, D.DDA_C64),
+        "dda_solve": lambda: L.dda_solve(h, None, None, None),
+        "dda_cross_sections": lambda: L.dda_cross_sections(h, None, po, None, 0, None),
+        "dda_profile_matvec": lambda: L.dda_profile_matvec(h, 1, D.DDA_C64, 0, po, None),
+        "dda_schedule_info": lambda: L.dda_schedule_info(h, D.DDA_C64, None),
+        "dda_angular_averages": lambda: L.dda_angular_averages(h, None, ctypes.c_double(0.5), po, None),
+        "dda_force_torque": lambda: L.dda_force_torque(h, po, ctypes.c_double(-1.0), po, None),
+        "dda_near_field": lambda: L.dda_near_field(h, po, po, ctypes.c_int64(0), po, None),
+        "dda_periodic_scattering": lambda: L.dda_periodic_scattering(h, po, 0, po, None, None, None),
+    }
+    for name, call in calls.items():
+        assert call() == D.DDA_EINVAL, name
+        assert name.encode() in L.dda_last_error(h), (name, L.dda_last_error(h))
+    # const-context getters report the status only
+    assert L.dda_kd_from_x(h, ctypes.c_double(-1.0), None, None) == D.DDA_EINVAL
